@@ -394,17 +394,18 @@ def solve_grid(grid: Grid, C, kappa, boxbc):
     """(Delta_h - kappa) u = C with the box condition, by DST-II / DCT-II (R1).
 
     1-D eigenvalues: Dirichlet-0 (DST-II mode k = 0..N-1): (2 cos(pi (k+1)/N) - 2)/h^2;
-    Neumann-0 (DCT-II mode k): (2 cos(pi k / N) - 2)/h^2.
+    Neumann-0 (DCT-II mode k): (2 cos(pi k / N) - 2)/h^2, evaluated through the identity
+    2 cos t - 2 = -4 sin^2(t/2), which keeps full relative precision for small t.
     """
     N, h = grid.N, grid.h
     k = np.arange(N, dtype=np.float64)
     if boxbc == BOX_NEUMANN0:
         if kappa == 0.0:
             raise Singular("Neumann box with kappa = 0")
-        lam = (2.0 * np.cos(np.pi * k / N) - 2.0) / (h * h)
+        lam = -4.0 * np.sin(0.5 * np.pi * k / N) ** 2 / (h * h)
         F = sfft.dctn(C, type=2, norm="ortho")
         return sfft.idctn(F / (lam[:, None] + lam[None, :] - kappa), type=2, norm="ortho")
-    lam = (2.0 * np.cos(np.pi * (k + 1.0) / N) - 2.0) / (h * h)
+    lam = -4.0 * np.sin(0.5 * np.pi * (k + 1.0) / N) ** 2 / (h * h)
     F = sfft.dstn(C, type=2, norm="ortho")
     return sfft.idstn(F / (lam[:, None] + lam[None, :] - kappa), type=2, norm="ortho")
 
