@@ -1,0 +1,256 @@
+/*
+ * kfbi.h -- C ABI of libkfbi, a GB300 (sm_103a) implementation of the kernel-free
+ * boundary integral (KFBI) layer-potential apply and the solvers built on it, after
+ * Zhou, Li & Ying, "A Cartesian grid-based boundary integral method for moving
+ * interface problems".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory:     every array argument is a DEVICE pointer owned by the caller (for example
+ *             a torch tensor's data_ptr()); the library never frees or retains it past
+ *             the call. All device workspace is owned by the context.
+ * Ordering:   work is enqueued on the context's stream (kfbi_set_stream; default the
+ *             legacy default stream). kfbi_apply_layer_potential, kfbi_bie_apply,
+ *             kfbi_grid_solve and kfbi_interp_grid are asynchronous. kfbi_set_interface,
+ *             kfbi_solve_bie and kfbi_step synchronise the stream to read counts and
+ *             status flags back.
+ * Grid:       cell-centred N x N cells on a square-celled box [xmin,xmax] x [ymin,ymax];
+ *             cell (i, j) has centre (xmin + (i + 1/2) h, ymin + (j + 1/2) h) and grid
+ *             arrays are row-major [j][i] (y index outer), float64.
+ * Interface:  n nodes X_j = X(alpha_j), alpha_j = 2 pi j / n, counter-clockwise, as
+ *             [n][2] float64 (x, y interleaved). Omega+ is the bounded interior.
+ *             Interface functions (densities) are [n] float64 nodal values; their
+ *             derivatives come from the global trigonometric interpolant.
+ * Errors:     every call returns a kfbi_status; nothing else crosses the ABI. After an
+ *             error other than KFBI_ERR_NOT_CONVERGED the outputs are unspecified.
+ * Precision:  KFBI_FP64 runs every step in float64. KFBI_MIXED runs the grid part of the
+ *             inner applies (jumps, corrections, transforms, interpolation) in float32
+ *             and keeps float64 for GMRES (Arnoldi, Givens, least squares), the outer
+ *             residual and the iterative-refinement update.
+ */
+#ifndef KFBI_H
+#define KFBI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KFBI_OK = 0,
+  KFBI_ERR_ARG = 1,           /* invalid argument (null pointer, bad size or mode) */
+  KFBI_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  KFBI_ERR_OUTSIDE_BOX = 3,   /* interface closer than 3h to the box, or stencil off-grid */
+  KFBI_ERR_UNDERRESOLVED = 4, /* three crossings on one grid arm, or arms inconsistent */
+  KFBI_ERR_NOT_CONVERGED = 5, /* GMRES reached max_iter; the best iterate is returned */
+  KFBI_ERR_SINGULAR = 6,      /* Neumann box with kappa = 0 (constant null space) */
+  KFBI_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+  KFBI_ERR_STATE = 8,         /* call order violated (e.g. apply before set_interface) */
+  KFBI_ERR_CAPACITY = 9       /* more nodes or crossings than the context was created for */
+} kfbi_status;
+
+/* Box boundary condition of the grid problem (Sec. 4.1). */
+enum {
+  KFBI_BOX_DIRICHLET0 = 0,   /* u = 0 on the box: DST-II solve (interior problems) */
+  KFBI_BOX_NEUMANN0 = 1,     /* du/dn = 0 on the box: DCT-II solve (Stefan, Sec. 3.2) */
+  KFBI_BOX_FREESPACE_DL = 2  /* Dirichlet data = free-space double layer by the trapezoidal
+                                rule on the box faces (Hele-Shaw, Sec. 4.1); kappa = 0 only */
+};
+enum { KFBI_FP64 = 0, KFBI_MIXED = 1 };
+/* Layer potentials and their jumps (Table 2). */
+enum { KFBI_SINGLE = 0, KFBI_DOUBLE = 1 };
+/* Boundary integral equations (Sec. 3). */
+enum {
+  KFBI_BIE_INTERIOR_DL = 0,     /* (1/2) phi + D phi = g, interior Dirichlet problem */
+  KFBI_BIE_HS_EXTERIOR_MDL = 1, /* -(1/2) phi + D phi + int phi ds = g (Sec. 3.1) */
+  KFBI_BIE_STEFAN_SL = 2        /* eps_V psi - S psi = g (Sec. 3.2) */
+};
+
+typedef struct kfbi_ctx kfbi_ctx;
+
+typedef struct {
+  int iterations;      /* GMRES operator applies (all refinement sweeps) */
+  int restarts;        /* GMRES restarts */
+  int refinements;     /* float64 residual evaluations of iterative refinement (MIXED) */
+  int status;          /* kfbi_status of the solve */
+  double rel_residual; /* ||b - A x||_2 / ||b||_2 of the returned density, float64 operator */
+} kfbi_solve_info;
+
+/*
+ * kfbi_create -- a context for one grid, box and operator (Delta - kappa) (Sec. 4.2).
+ *   N          cells per side, a power of two in [16, 4096]
+ *   xmin..ymax box; (xmax - xmin) / N must equal (ymax - ymin) / N (square cells)
+ *   kappa      c^2 >= 0 of the modified Helmholtz operator Delta - c^2 (Sec. 3.2;
+ *              kappa = 0 is the Laplacian). Not a curvature.
+ *   boxbc      KFBI_BOX_*; NEUMANN0 needs kappa > 0, FREESPACE_DL needs kappa = 0
+ *   precision  KFBI_FP64 or KFBI_MIXED
+ *   max_nodes  largest interface node count this context will see (>= 8)
+ *   out        receives the context; release it with kfbi_destroy
+ * Errors: ARG, SINGULAR, CUDA (allocation).
+ */
+kfbi_status kfbi_create(int N, double xmin, double xmax, double ymin, double ymax, double kappa,
+                        int boxbc, int precision, int max_nodes, kfbi_ctx** out);
+
+/* Releases the context and all device workspace it owns. NULL is ignored. */
+void kfbi_destroy(kfbi_ctx* ctx);
+
+/* Sets the cudaStream_t (passed as void*) that later calls enqueue on. */
+kfbi_status kfbi_set_stream(kfbi_ctx* ctx, void* stream);
+
+/*
+ * kfbi_set_interface -- geometry of the interface (Sec. 4.2 irregular nodes, Sec. 4.3
+ * interpolation stencils).
+ *   n   node count, 8 <= n <= max_nodes
+ *   xy  device [n][2] float64 node coordinates (read only)
+ * Finds every crossing of the curve with the grid lines (Newton on the trigonometric
+ * interpolant), classifies grid nodes into Omega+/Omega-, lists irregular nodes and
+ * their crossed arms, and builds the 6-point interpolation stencils.
+ * Synchronises the stream. Errors: ARG, OUTSIDE_BOX, UNDERRESOLVED, CAPACITY, CUDA.
+ */
+kfbi_status kfbi_set_interface(kfbi_ctx* ctx, int n, const double* xy);
+
+/*
+ * kfbi_apply_layer_potential -- the KFBI apply (Sec. 4): solves the equivalent interface
+ * problem (Delta - kappa) v = 0 with [v] = Phi, [dv/dn] = Psi from Table 2 by the corrected
+ * five-point scheme and a fast DST/DCT solve, then extracts the boundary operator
+ * (average of the one-sided limits, Sec. 4.3).
+ *   layer    KFBI_SINGLE (S psi: Phi = 0, Psi = -psi) or KFBI_DOUBLE (D phi: Phi = phi)
+ *   density  device [n] float64
+ *   values   device [n] float64 output: (S psi) or (D phi) on the curve
+ *   dnormal  device [n] float64 output or NULL: n . (grad v+ + grad v-)/2
+ *   grid     device [N][N] float64 output or NULL: the grid solution v_h
+ * Asynchronous. FREESPACE_DL contexts accept KFBI_DOUBLE only.
+ * Errors: ARG, STATE, CUDA.
+ */
+kfbi_status kfbi_apply_layer_potential(kfbi_ctx* ctx, int layer, const double* density, double* values,
+                                       double* dnormal, double* grid);
+
+/*
+ * kfbi_bie_apply -- y = A x for the boundary integral operator of `kind` (Sec. 3):
+ *   INTERIOR_DL:       y = x/2 + D x
+ *   HS_EXTERIOR_MDL:   y = -x/2 + D x + int x ds           (Sec. 3.1)
+ *   STEFAN_SL:         y = eps_v .* x - S x                 (Sec. 3.2)
+ *   eps_v  device [n] float64, STEFAN_SL only (else ignored, may be NULL)
+ *   x, y   device [n] float64
+ * Uses the context's precision for the grid part. Asynchronous. Errors: ARG, STATE, CUDA.
+ */
+kfbi_status kfbi_bie_apply(kfbi_ctx* ctx, int kind, const double* eps_v, const double* x, double* y);
+
+/*
+ * kfbi_solve_bie -- matrix-free restarted GMRES for A x = rhs (Sec. 4), one operator
+ * apply per iteration, Arnoldi (two-pass classical Gram-Schmidt), Givens rotations and
+ * the least-squares update all on the device. MIXED contexts run float32 grid applies
+ * inside GMRES and iterative refinement with a float64 residual until
+ * ||rhs - A x|| <= tol ||rhs||.
+ *   kind      KFBI_BIE_*;  eps_v as in kfbi_bie_apply
+ *   rhs       device [n] float64
+ *   tol       relative residual target (> 0)
+ *   max_iter  cap on GMRES applies (>= 1);  restart  Krylov dimension (1..200)
+ *   density   device [n] float64: initial guess in, solution out
+ *   info      host pointer, filled on return (may be NULL)
+ * Synchronises the stream. Errors: ARG, STATE, NOT_CONVERGED (best iterate returned),
+ * TIMEOUT, CUDA.
+ */
+kfbi_status kfbi_solve_bie(kfbi_ctx* ctx, int kind, const double* eps_v, const double* rhs, double tol,
+                           int max_iter, int restart, double* density, kfbi_solve_info* info);
+
+/*
+ * kfbi_grid_solve -- (Delta_h - kappa) u = rhs on the whole grid with the context's box
+ * condition, no interface corrections (the smooth part T1 of Sec. 3.2).
+ *   rhs, u  device [N][N] float64 (may alias). Asynchronous. Errors: ARG, CUDA.
+ */
+kfbi_status kfbi_grid_solve(kfbi_ctx* ctx, const double* rhs, double* u);
+
+/*
+ * kfbi_interp_grid -- values at the interface nodes of a smooth grid function by the
+ * 6-point interpolation of Sec. 4.3 with zero jumps.
+ *   grid    device [N][N] float64;  values  device [n] float64
+ * Asynchronous. Errors: ARG, STATE, CUDA.
+ */
+kfbi_status kfbi_interp_grid(kfbi_ctx* ctx, const double* grid, double* values);
+
+/*
+ * Introspection of the last kfbi_set_interface, for tests:
+ *   kfbi_interface_stats  host ints: crossings, irregular nodes, interpolation probes
+ *   kfbi_copy_sides       device [N][N] uint8: 1 = Omega+, 0 = Omega-
+ *   kfbi_copy_crossings   device outputs for the first `cap` crossings in the order
+ *                         (horizontal lines first, then vertical; by sub-segment, then
+ *                         line): ints [cap][3] = (kind, line, first), doubles [cap][2] =
+ *                         (alpha, coordinate along the line)
+ *   kfbi_copy_irregular   device ints [cap][2] = (j, i), row-major order
+ */
+kfbi_status kfbi_interface_stats(kfbi_ctx* ctx, int* n_crossings, int* n_irregular, int* n_probes);
+kfbi_status kfbi_copy_sides(kfbi_ctx* ctx, uint8_t* sides);
+kfbi_status kfbi_copy_crossings(kfbi_ctx* ctx, int cap, int* kind_line_first, double* alpha_xi);
+kfbi_status kfbi_copy_irregular(kfbi_ctx* ctx, int cap, int* ji);
+
+/*
+ * theta-L interface evolution (Sec. 5): one semi-implicit time step.
+ * The state lives in device memory allocated by kfbi_thetal_create:
+ *   eta[n]     theta - alpha at the nodes (Sec. 5.3 remark)
+ *   scalars    L, Xbar (2), t, and the Adams-Bashforth history M, Q (2), L, N-hat (2n)
+ *   density[n] last BIE density (warm start of the next solve)
+ *   xy[n][2]   nodes of the curve the last step solved on
+ *   T, T_prev  [N][N] grid temperatures (Stefan only)
+ */
+enum { KFBI_STEP_HELE_SHAW = 0, KFBI_STEP_STEFAN = 1 };
+
+typedef struct kfbi_thetal kfbi_thetal;
+
+typedef struct {
+  int kind;          /* KFBI_STEP_* */
+  /* Hele-Shaw (Sec. 2.1, 3.1): surface tension sigma, injection rate J */
+  double sigma, J;
+  /* Stefan (Sec. 2.2, 3.2): undercooling St, eps_C = eps_c (1 - eps_aniso cos(fold
+     (theta - pi/2))), constant eps_V > 0 (small-scale decomposition case I) */
+  double St, eps_c, eps_aniso, eps_v;
+  int fold;
+  /* GMRES controls of the per-step BIE solve */
+  double tol;
+  int max_iter, restart;
+} kfbi_thetal_params;
+
+/*
+ * kfbi_thetal_create -- device state for the context's grid from equal-arclength nodes.
+ *   n         node count;  eta  device [n] float64 (theta - alpha_j);  L  curve length
+ *   xbar      host [2] mean node position
+ * Errors: ARG, CUDA.
+ */
+kfbi_status kfbi_thetal_create(kfbi_ctx* ctx, int n, const double* eta, double L, const double* xbar,
+                               const kfbi_thetal_params* params, kfbi_thetal** out);
+void kfbi_thetal_destroy(kfbi_thetal* st);
+
+/*
+ * kfbi_step -- one time step of size dt (Sec. 5.3): reconstruct the curve from
+ * (eta, L, Xbar), set the interface, solve the BIE (Hele-Shaw: Sec. 3.1; Stefan: Sec. 3.2
+ * with T1 from kfbi_grid_solve), form the normal velocity U and advance (eta, L, Xbar)
+ * with the integrating-factor / Adams-Bashforth scheme. Synchronises the stream.
+ *   info  host pointer or NULL: the step's BIE solve
+ * Errors: those of kfbi_set_interface and kfbi_solve_bie.
+ */
+kfbi_status kfbi_step(kfbi_ctx* ctx, kfbi_thetal* st, double dt, kfbi_solve_info* info);
+
+/*
+ * Read-back of the theta-L state (device outputs): eta [n], xy [n][2] of the last solved
+ * curve, density [n], T [N][N] (Stefan; NULL to skip) and host scalars [8] =
+ * (L, Xbar_x, Xbar_y, t, steps, M_prev, L_prev, 0).
+ */
+kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* density, double* T,
+                             double* scalars);
+
+/* Human-readable name of a status code (static storage). */
+const char* kfbi_status_string(kfbi_status s);
+
+/*
+ * Per-kernel device timing for roofline reports: when enabled, the library records CUDA
+ * events around the column-transform kernel of the fast solve on the context's stream.
+ * kfbi_timing_read returns the summed milliseconds and the launch count since enable.
+ */
+kfbi_status kfbi_timing_enable(kfbi_ctx* ctx, int enable);
+kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* total_ms, int* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KFBI_H */

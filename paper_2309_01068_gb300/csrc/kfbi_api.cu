@@ -1,0 +1,351 @@
+// C ABI of libkfbi (include/kfbi.h): context lifetime, constant tables and the entry
+// points that validate arguments and enqueue the kernels of the other translation units.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "kfbi_internal.cuh"
+
+namespace kfbi {
+
+kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy);
+kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const double* rhs, double tol, int max_iter,
+                           int restart, double* x, kfbi_solve_info* info);
+
+static thread_local char g_last_error[512] = {0};
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s:%d)", cudaGetErrorName(e), what, file, line);
+  if (getenv("KFBI_VERBOSE")) fprintf(stderr, "libkfbi: %s\n", g_last_error);
+}
+
+// sin(pi m / (2N)) for m < 4N; box eigenvalues -4 sin^2(pi (k + s) / (2N)) / h^2 with s = 1
+// (Dirichlet-0, DST-II mode k) or s = 0 (Neumann-0, DCT-II mode k); FFT twiddles
+// e^{-2 pi i m / N} = (cos, -sin)(pi (4m) / (2N)) for m < N/2.
+__global__ void k_init_tables(int N, double h, int neumann, double* tab, float* tab_f, double* lam, float* lam_f,
+                              double* tw, float* tw_f) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < 4 * N) {
+    double s = sinpi((double)m / (2.0 * N));
+    tab[m] = s;
+    tab_f[m] = (float)s;
+  }
+  if (m < N) {
+    double sk = sinpi(((double)m + (neumann ? 0.0 : 1.0)) / (2.0 * N));
+    double l = -4.0 * sk * sk / (h * h);
+    lam[m] = l;
+    lam_f[m] = (float)l;
+  }
+  if (m < N / 2) {
+    double s, c;
+    sincospi(2.0 * (double)m / (double)N, &s, &c);
+    tw[2 * m] = c;
+    tw[2 * m + 1] = -s;
+    tw_f[2 * m] = (float)c;
+    tw_f[2 * m + 1] = (float)-s;
+  }
+}
+
+template <typename P>
+static kfbi_status dalloc(P** p, size_t count) {
+  KFBI_TRY(cudaMalloc((void**)p, sizeof(P) * (count > 0 ? count : 1)));
+  return KFBI_OK;
+}
+
+kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
+  if (ncr <= c->cap_cross) return KFBI_OK;
+  int cap = ncr + ncr / 2 + 64;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->cr_kind); cudaFree(c->cr_line); cudaFree(c->cr_seg); cudaFree(c->cr_first);
+  cudaFree(c->cr_alpha); cudaFree(c->cr_xi); cudaFree(c->tgeo); cudaFree(c->irr);
+  cudaFree(c->jumps); cudaFree(c->cval);
+  c->cr_kind = c->cr_line = c->cr_seg = c->cr_first = nullptr;
+  c->cr_alpha = c->cr_xi = nullptr;
+  c->tgeo = nullptr; c->irr = nullptr; c->jumps = nullptr; c->cval = nullptr;
+  c->cap_cross = c->cap_irr = 0;
+  KFBI_CHECK(dalloc(&c->cr_kind, cap));
+  KFBI_CHECK(dalloc(&c->cr_line, cap));
+  KFBI_CHECK(dalloc(&c->cr_seg, cap));
+  KFBI_CHECK(dalloc(&c->cr_first, cap));
+  KFBI_CHECK(dalloc(&c->cr_alpha, cap));
+  KFBI_CHECK(dalloc(&c->cr_xi, cap));
+  KFBI_CHECK(dalloc(&c->tgeo, (size_t)cap + c->max_nodes));
+  int cap_irr = 2 * cap + 64;
+  KFBI_CHECK(dalloc(&c->irr, cap_irr));
+  KFBI_CHECK(dalloc(&c->jumps, 6 * ((size_t)cap + c->max_nodes)));
+  KFBI_CHECK(dalloc(&c->cval, cap_irr));
+  c->cap_cross = cap;
+  c->cap_irr = cap_irr;
+  return KFBI_OK;
+}
+
+static void free_all(kfbi_ctx* c) {
+  void* ptrs[] = {c->sintab, c->sintab_f, c->lam, c->lam_f, c->twN, c->twN_f, c->xy, c->twn, c->icoef, c->fine,
+                  c->seg_count, c->seg_off, c->cr_kind, c->cr_line, c->cr_seg, c->cr_first, c->cr_alpha, c->cr_xi,
+                  c->tgeo, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->stencil,
+                  c->probe_mark, c->prow_cnt, c->prow_ptr, c->probe_i, c->flags, c->counts, c->dcoef, c->dint,
+                  c->jumps, c->cval, c->boxg, c->spec, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gpart, c->gw,
+                  c->gin, c->gb, c->gx, c->gr, c->zero_flag};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->host_counts) cudaFreeHost(c->host_counts);
+  if (c->host_gctl) cudaFreeHost(c->host_gctl);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+}
+
+static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, double ymax, double kappa, int boxbc,
+                               int precision, int max_nodes, kfbi_ctx** out) {
+  kfbi_ctx* c = new kfbi_ctx();
+  *out = c;
+  c->N = N;
+  c->logN = ilog2(N);
+  c->xmin = xmin; c->xmax = xmax; c->ymin = ymin; c->ymax = ymax;
+  c->h = (xmax - xmin) / N;
+  c->kappa = kappa;
+  c->boxbc = boxbc;
+  c->precision = precision;
+  c->max_nodes = max_nodes;
+  const size_t NN = (size_t)N * N;
+  const int M = SUBSAMPLES * max_nodes;
+  const int nk = max_nodes / 2 + 1;
+  KFBI_CHECK(dalloc(&c->sintab, 4 * (size_t)N));
+  KFBI_CHECK(dalloc(&c->sintab_f, 4 * (size_t)N));
+  KFBI_CHECK(dalloc(&c->lam, N));
+  KFBI_CHECK(dalloc(&c->lam_f, N));
+  KFBI_CHECK(dalloc(&c->twN, N));
+  KFBI_CHECK(dalloc(&c->twN_f, N));
+  KFBI_CHECK(dalloc(&c->xy, 2 * (size_t)max_nodes));
+  KFBI_CHECK(dalloc(&c->twn, 2 * (size_t)max_nodes));
+  KFBI_CHECK(dalloc(&c->icoef, 4 * (size_t)nk));
+  KFBI_CHECK(dalloc(&c->fine, 2 * (size_t)M));
+  KFBI_CHECK(dalloc(&c->seg_count, 2 * (size_t)M + 1));
+  KFBI_CHECK(dalloc(&c->seg_off, 2 * (size_t)M + 1));
+  KFBI_CHECK(dalloc(&c->hcount, NN));
+  KFBI_CHECK(dalloc(&c->vcount, NN));
+  KFBI_CHECK(dalloc(&c->hid, NN));
+  KFBI_CHECK(dalloc(&c->vid, NN));
+  KFBI_CHECK(dalloc(&c->side, NN));
+  KFBI_CHECK(dalloc(&c->rowcnt, N + 1));
+  KFBI_CHECK(dalloc(&c->row_ptr, N + 1));
+  KFBI_CHECK(dalloc(&c->stencil, max_nodes));
+  KFBI_CHECK(dalloc(&c->probe_mark, NN));
+  KFBI_CHECK(dalloc(&c->prow_cnt, N + 1));
+  KFBI_CHECK(dalloc(&c->prow_ptr, N + 1));
+  KFBI_CHECK(dalloc(&c->probe_i, 6 * (size_t)max_nodes));
+  KFBI_CHECK(dalloc(&c->flags, 4));
+  KFBI_CHECK(dalloc(&c->counts, 8));
+  KFBI_TRY(cudaMallocHost((void**)&c->host_counts, 16 * sizeof(int)));
+  KFBI_CHECK(dalloc(&c->dcoef, 2 * (size_t)nk));
+  KFBI_CHECK(dalloc(&c->dint, 8));
+  KFBI_CHECK(dalloc(&c->boxg, 4 * (size_t)N));
+  KFBI_CHECK(dalloc(&c->spec, NN));
+  KFBI_CHECK(dalloc(&c->probe_val, 6 * (size_t)max_nodes));
+  KFBI_CHECK(dalloc(&c->tmp_vals, max_nodes));
+  KFBI_CHECK(dalloc(&c->gctl, 1));
+  KFBI_TRY(cudaMallocHost((void**)&c->host_gctl, sizeof(GmresCtl)));
+  KFBI_CHECK(dalloc(&c->gV, (size_t)(MAX_RESTART + 1) * max_nodes));
+  KFBI_CHECK(dalloc(&c->gpart, (size_t)64 * (MAX_RESTART + 1)));
+  KFBI_CHECK(dalloc(&c->gw, max_nodes));
+  KFBI_CHECK(dalloc(&c->gin, max_nodes));
+  KFBI_CHECK(dalloc(&c->gb, max_nodes));
+  KFBI_CHECK(dalloc(&c->gx, max_nodes));
+  KFBI_CHECK(dalloc(&c->gr, max_nodes));
+  KFBI_CHECK(dalloc(&c->zero_flag, 4));
+  KFBI_TRY(cudaMemset(c->zero_flag, 0, 4 * sizeof(int)));
+  KFBI_TRY(cudaMemset(c->hcount, 0, NN * sizeof(int)));
+  KFBI_TRY(cudaMemset(c->vcount, 0, NN * sizeof(int)));
+  KFBI_TRY(cudaMemset(c->probe_mark, 0, NN * sizeof(int)));
+  KFBI_TRY(cudaMemset(c->gctl, 0, sizeof(GmresCtl)));
+  KFBI_TRY(cudaEventCreate(&c->ev0));
+  KFBI_TRY(cudaEventCreate(&c->ev1));
+  KFBI_CHECK(ensure_cross_capacity(c, 4096));
+  k_init_tables<<<cdiv(4L * N, 256), 256>>>(N, c->h, boxbc == KFBI_BOX_NEUMANN0, c->sintab, c->sintab_f, c->lam,
+                                           c->lam_f, c->twN, c->twN_f);
+  KFBI_TRY(cudaGetLastError());
+  KFBI_TRY(cudaDeviceSynchronize());
+  return KFBI_OK;
+}
+
+static bool ctx_ok(const kfbi_ctx* c) { return c != nullptr; }
+
+}  // namespace kfbi
+
+using namespace kfbi;
+
+extern "C" {
+
+kfbi_status kfbi_create(int N, double xmin, double xmax, double ymin, double ymax, double kappa, int boxbc,
+                        int precision, int max_nodes, kfbi_ctx** out) {
+  if (out == nullptr) return KFBI_ERR_ARG;
+  *out = nullptr;
+  if (N < 16 || N > 4096 || (N & (N - 1)) != 0) return KFBI_ERR_ARG;
+  if (!(xmax > xmin) || !(ymax > ymin)) return KFBI_ERR_ARG;
+  double hx = (xmax - xmin) / N, hy = (ymax - ymin) / N;
+  if (fabs(hx - hy) > 1e-12 * hx) return KFBI_ERR_ARG;
+  if (!(kappa >= 0.0) || !std::isfinite(kappa)) return KFBI_ERR_ARG;
+  if (boxbc < KFBI_BOX_DIRICHLET0 || boxbc > KFBI_BOX_FREESPACE_DL) return KFBI_ERR_ARG;
+  if (precision != KFBI_FP64 && precision != KFBI_MIXED) return KFBI_ERR_ARG;
+  if (max_nodes < 8 || max_nodes > (1 << 16)) return KFBI_ERR_ARG;
+  if (boxbc == KFBI_BOX_NEUMANN0 && kappa == 0.0) return KFBI_ERR_SINGULAR;
+  if (boxbc == KFBI_BOX_FREESPACE_DL && kappa != 0.0) return KFBI_ERR_ARG;
+  kfbi_ctx* c = nullptr;
+  kfbi_status st = create_impl(N, xmin, xmax, ymin, ymax, kappa, boxbc, precision, max_nodes, &c);
+  if (st != KFBI_OK) {
+    if (c) {
+      free_all(c);
+      delete c;
+    }
+    return st;
+  }
+  *out = c;
+  return KFBI_OK;
+}
+
+void kfbi_destroy(kfbi_ctx* c) {
+  if (c == nullptr) return;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+kfbi_status kfbi_set_stream(kfbi_ctx* c, void* stream) {
+  if (!ctx_ok(c)) return KFBI_ERR_ARG;
+  c->stream = (cudaStream_t)stream;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_set_interface(kfbi_ctx* c, int n, const double* xy) {
+  if (!ctx_ok(c) || xy == nullptr) return KFBI_ERR_ARG;
+  if (n < 8) return KFBI_ERR_ARG;
+  if (n > c->max_nodes) return KFBI_ERR_CAPACITY;
+  return set_interface_impl(c, n, xy);
+}
+
+kfbi_status kfbi_apply_layer_potential(kfbi_ctx* c, int layer, const double* density, double* values,
+                                       double* dnormal, double* grid) {
+  if (!ctx_ok(c) || density == nullptr || values == nullptr) return KFBI_ERR_ARG;
+  if (layer != KFBI_SINGLE && layer != KFBI_DOUBLE) return KFBI_ERR_ARG;
+  if (!c->have_iface) return KFBI_ERR_STATE;
+  if (c->boxbc == KFBI_BOX_FREESPACE_DL && layer != KFBI_DOUBLE) return KFBI_ERR_ARG;
+  return apply_enqueue(c, layer, c->precision == KFBI_MIXED, density, values, dnormal, grid, -1, nullptr, nullptr);
+}
+
+kfbi_status kfbi_bie_apply(kfbi_ctx* c, int kind, const double* eps_v, const double* x, double* y) {
+  if (!ctx_ok(c) || x == nullptr || y == nullptr) return KFBI_ERR_ARG;
+  if (kind < KFBI_BIE_INTERIOR_DL || kind > KFBI_BIE_STEFAN_SL) return KFBI_ERR_ARG;
+  if (kind == KFBI_BIE_STEFAN_SL && eps_v == nullptr) return KFBI_ERR_ARG;
+  if (kind == KFBI_BIE_STEFAN_SL && c->boxbc == KFBI_BOX_FREESPACE_DL) return KFBI_ERR_ARG;
+  if (!c->have_iface) return KFBI_ERR_STATE;
+  int layer = kind == KFBI_BIE_STEFAN_SL ? KFBI_SINGLE : KFBI_DOUBLE;
+  return apply_enqueue(c, layer, c->precision == KFBI_MIXED, x, y, nullptr, nullptr, kind, eps_v, nullptr);
+}
+
+kfbi_status kfbi_solve_bie(kfbi_ctx* c, int kind, const double* eps_v, const double* rhs, double tol, int max_iter,
+                           int restart, double* density, kfbi_solve_info* info) {
+  if (!ctx_ok(c) || rhs == nullptr || density == nullptr) return KFBI_ERR_ARG;
+  if (kind < KFBI_BIE_INTERIOR_DL || kind > KFBI_BIE_STEFAN_SL) return KFBI_ERR_ARG;
+  if (kind == KFBI_BIE_STEFAN_SL && eps_v == nullptr) return KFBI_ERR_ARG;
+  if (kind == KFBI_BIE_STEFAN_SL && c->boxbc == KFBI_BOX_FREESPACE_DL) return KFBI_ERR_ARG;
+  if (!(tol > 0.0) || max_iter < 1 || restart < 1 || restart > MAX_RESTART) return KFBI_ERR_ARG;
+  if (!c->have_iface) return KFBI_ERR_STATE;
+  return solve_bie_impl(c, kind, eps_v, rhs, tol, max_iter, restart, density, info);
+}
+
+kfbi_status kfbi_grid_solve(kfbi_ctx* c, const double* rhs, double* u) {
+  if (!ctx_ok(c) || rhs == nullptr || u == nullptr) return KFBI_ERR_ARG;
+  return grid_solve_enqueue(c, rhs, u);
+}
+
+kfbi_status kfbi_interp_grid(kfbi_ctx* c, const double* grid, double* values) {
+  if (!ctx_ok(c) || grid == nullptr || values == nullptr) return KFBI_ERR_ARG;
+  if (!c->have_iface) return KFBI_ERR_STATE;
+  return interp_grid_enqueue(c, grid, values);
+}
+
+kfbi_status kfbi_interface_stats(kfbi_ctx* c, int* n_crossings, int* n_irregular, int* n_probes) {
+  if (!ctx_ok(c)) return KFBI_ERR_ARG;
+  if (!c->have_iface) return KFBI_ERR_STATE;
+  if (n_crossings) *n_crossings = c->n_cross;
+  if (n_irregular) *n_irregular = c->n_irr;
+  if (n_probes) *n_probes = c->n_probe;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_copy_sides(kfbi_ctx* c, uint8_t* sides) {
+  if (!ctx_ok(c) || sides == nullptr) return KFBI_ERR_ARG;
+  if (!c->have_iface) return KFBI_ERR_STATE;
+  KFBI_TRY(cudaMemcpyAsync(sides, c->side, (size_t)c->N * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  return KFBI_OK;
+}
+
+__global__ void k_pack_crossings(int cnt, const int* kind, const int* line, const int* first, const double* alpha,
+                                 const double* xi, int* klf, double* ax) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  klf[3 * t] = kind[t];
+  klf[3 * t + 1] = line[t];
+  klf[3 * t + 2] = first[t];
+  ax[2 * t] = alpha[t];
+  ax[2 * t + 1] = xi[t];
+}
+
+kfbi_status kfbi_copy_crossings(kfbi_ctx* c, int cap, int* kind_line_first, double* alpha_xi) {
+  if (!ctx_ok(c) || kind_line_first == nullptr || alpha_xi == nullptr || cap < 0) return KFBI_ERR_ARG;
+  if (!c->have_iface) return KFBI_ERR_STATE;
+  int cnt = cap < c->n_cross ? cap : c->n_cross;
+  if (cnt > 0)
+    k_pack_crossings<<<cdiv(cnt, 256), 256, 0, c->stream>>>(cnt, c->cr_kind, c->cr_line, c->cr_first, c->cr_alpha,
+                                                            c->cr_xi, kind_line_first, alpha_xi);
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
+__global__ void k_pack_irregular(int cnt, const IrrNode* irr, int* ji) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  ji[2 * t] = irr[t].j;
+  ji[2 * t + 1] = irr[t].i;
+}
+
+kfbi_status kfbi_copy_irregular(kfbi_ctx* c, int cap, int* ji) {
+  if (!ctx_ok(c) || ji == nullptr || cap < 0) return KFBI_ERR_ARG;
+  if (!c->have_iface) return KFBI_ERR_STATE;
+  int cnt = cap < c->n_irr ? cap : c->n_irr;
+  if (cnt > 0) k_pack_irregular<<<cdiv(cnt, 256), 256, 0, c->stream>>>(cnt, c->irr, ji);
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
+const char* kfbi_status_string(kfbi_status s) {
+  switch (s) {
+    case KFBI_OK: return "ok";
+    case KFBI_ERR_ARG: return "invalid argument";
+    case KFBI_ERR_CUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+    case KFBI_ERR_OUTSIDE_BOX: return "interface too close to the box";
+    case KFBI_ERR_UNDERRESOLVED: return "interface under-resolved by the grid";
+    case KFBI_ERR_NOT_CONVERGED: return "GMRES did not converge";
+    case KFBI_ERR_SINGULAR: return "singular operator (Neumann box with kappa = 0)";
+    case KFBI_ERR_TIMEOUT: return "device-side wait gave up";
+    case KFBI_ERR_STATE: return "call order violated";
+    case KFBI_ERR_CAPACITY: return "capacity exceeded";
+  }
+  return "unknown status";
+}
+
+kfbi_status kfbi_timing_enable(kfbi_ctx* c, int enable) {
+  if (!ctx_ok(c)) return KFBI_ERR_ARG;
+  c->timing = enable != 0;
+  c->timing_ms = 0.0;
+  c->timing_launches = 0;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_timing_read(kfbi_ctx* c, double* total_ms, int* launches) {
+  if (!ctx_ok(c)) return KFBI_ERR_ARG;
+  if (total_ms) *total_ms = c->timing_ms;
+  if (launches) *launches = c->timing_launches;
+  return KFBI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,544 @@
+// Interface geometry on the device (kfbi_set_interface): trigonometric interpolant of the
+// nodes, crossings of the curve with the grid lines, node classification, irregular nodes
+// with their crossed arms (Sec. 4.2) and the 6-point interpolation stencils (Sec. 4.3).
+#include <cmath>
+
+#include "kfbi_internal.cuh"
+
+namespace kfbi {
+
+// --------------------------------------------------------------------------- interpolant
+// Real function f(alpha) = c_0 + 2 sum_{k=1}^{K} Re(c_k e^{ik alpha}) + nyq cos(n alpha / 2)
+// with K = (n-1)/2 and nyq = c_{n/2} for even n. A warp evaluates f, f', f'' at one
+// alpha: each lane sums a contiguous block of modes with a rotation recurrence started
+// from sincos(k0 alpha); all lanes return the full sums.
+struct TrigSums {
+  double f, f1, f2;
+};
+
+__device__ __forceinline__ TrigSums trig_warp(const double2* c, int n, double alpha, int lane, bool d2) {
+  const int K = (n - 1) / 2;
+  const int chunk = (K + 31) / 32;
+  int k0 = 1 + lane * chunk;
+  int k1 = min(K + 1, k0 + chunk);
+  double f = 0.0, f1 = 0.0, f2 = 0.0;
+  if (k0 < k1) {
+    double er, ei, sr, si;
+    sincos((double)k0 * alpha, &ei, &er);
+    sincos(alpha, &si, &sr);
+    for (int k = k0; k < k1; ++k) {
+      double2 ck = c[k];
+      double re = ck.x * er - ck.y * ei;
+      double im = ck.x * ei + ck.y * er;
+      f += re;
+      f1 -= (double)k * im;
+      if (d2) f2 -= (double)k * (double)k * re;
+      double t = er * sr - ei * si;
+      ei = er * si + ei * sr;
+      er = t;
+    }
+  }
+  f = 2.0 * warp_sum(f);
+  f1 = 2.0 * warp_sum(f1);
+  if (d2) f2 = 2.0 * warp_sum(f2);
+  f += c[0].x;
+  if ((n & 1) == 0) {
+    double m = 0.5 * n;
+    double nyq = c[n / 2].x;
+    double s, co;
+    sincos(m * alpha, &s, &co);
+    f += nyq * co;
+    f1 -= m * nyq * s;
+    if (d2) f2 -= m * m * nyq * co;
+  }
+  return TrigSums{f, f1, f2};
+}
+
+// twiddles e^{2 pi i m / n}
+__global__ void k_twiddles_n(int n, double2* tw) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double s, c;
+  sincospi(2.0 * (double)m / (double)n, &s, &c);
+  tw[m] = make_double2(c, s);
+}
+
+// c_k = (1/n) sum_j f_j e^{-2 pi i k j / n}, k = 0..n/2, for `nf` functions stored with
+// stride `stride` (function q at f[j*stride + q]); one warp per (function, k).
+__global__ void k_dft_real(const double* f, int stride, int nf, int n, const double2* tw, double2* coef) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  int nk = n / 2 + 1;
+  if (warp >= nk * nf) return;
+  int q = warp / nk, k = warp - q * nk;
+  double re = 0.0, im = 0.0;
+  for (int j = lane; j < n; j += 32) {
+    double v = f[(long)j * stride + q];
+    double2 w = tw[(int)(((long)k * j) % n)];
+    re += v * w.x;
+    im -= v * w.y;
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if (lane == 0) coef[q * nk + k] = make_double2(re / n, im / n);
+}
+
+// fine samples X(alpha_s), alpha_s = 2 pi s / M; flags samples closer than 3h to the box
+__global__ void k_fine_samples(const double2* coef, int n, int M, double* fine, double xlo, double xhi,
+                               double ylo, double yhi, int* flags) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= M) return;
+  int nk = n / 2 + 1;
+  double a = (TWO_PI * (double)warp) / (double)M;
+  TrigSums x = trig_warp(coef, n, a, lane, false);
+  TrigSums y = trig_warp(coef + nk, n, a, lane, false);
+  if (lane == 0) {
+    fine[2 * warp] = x.f;
+    fine[2 * warp + 1] = y.f;
+    if (x.f < xlo || x.f > xhi || y.f < ylo || y.f > yhi) atomicOr(flags, FLAG_OUTSIDE);
+  }
+}
+
+// per fine segment s -> s+1 (cyclic) and kind: number of grid lines crossed.
+// kind 0 = horizontal lines y = y_l (coordinate y), kind 1 = vertical lines x = x_l.
+__global__ void k_seg_count(const double* fine, int M, double xmin, double ymin, double h, int N,
+                            int* seg_count) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * M) return;
+  int kind = t / M, s = t - kind * M;
+  int s1 = (s + 1 == M) ? 0 : s + 1;
+  int ax = kind == 0 ? 1 : 0;
+  double lo = kind == 0 ? ymin : xmin;
+  int c0 = count_le(lo, h, N, fine[2 * s + ax]);
+  int c1 = count_le(lo, h, N, fine[2 * s1 + ax]);
+  seg_count[t] = abs(c0 - c1);
+}
+
+// exclusive scan of `len` ints by one block; out[len] = total
+__global__ void k_scan(const int* in, int* out, int len) {
+  __shared__ int part[1024];
+  int tid = threadIdx.x, nt = blockDim.x;
+  int per = (len + nt - 1) / nt;
+  int b = tid * per, e = min(len, b + per);
+  int s = 0;
+  for (int i = b; i < e; ++i) s += in[i];
+  part[tid] = s;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {
+    int v = tid >= o ? part[tid - o] : 0;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  int run = tid == 0 ? 0 : part[tid - 1];
+  for (int i = b; i < e; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  if (tid == nt - 1) out[len] = part[nt - 1];
+}
+
+__global__ void k_emit_pairs(const double* fine, int M, double xmin, double ymin, double h, int N,
+                             const int* seg_off, int* cr_kind, int* cr_line, int* cr_seg) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * M) return;
+  int kind = t / M, s = t - kind * M;
+  int s1 = (s + 1 == M) ? 0 : s + 1;
+  int ax = kind == 0 ? 1 : 0;
+  double lo = kind == 0 ? ymin : xmin;
+  int c0 = count_le(lo, h, N, fine[2 * s + ax]);
+  int c1 = count_le(lo, h, N, fine[2 * s1 + ax]);
+  int a = min(c0, c1), b = max(c0, c1);
+  int off = seg_off[t];
+  for (int l = a; l < b; ++l) {
+    int slot = off + (l - a);
+    cr_kind[slot] = kind;
+    cr_line[slot] = l;
+    cr_seg[slot] = s;
+  }
+}
+
+// Newton's method with a bisection safeguard on [alpha_s, alpha_s + 2 pi / M] for
+// coordinate(alpha) = line; then the coordinate along the line and the first node past it.
+__global__ void k_newton(const double2* coef, int n, int M, const double* fine, double xmin, double ymin,
+                         double h, int N, int ncr, const int* cr_kind, const int* cr_line, const int* cr_seg,
+                         int* cr_first, double* cr_alpha, double* cr_xi, int* flags) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= ncr) return;
+  int nk = n / 2 + 1;
+  int kind = cr_kind[warp], line = cr_line[warp], seg = cr_seg[warp];
+  int ax = kind == 0 ? 1 : 0;
+  const double2* cc = coef + ax * nk;      // coordinate compared with the line
+  const double2* co = coef + (1 - ax) * nk;  // coordinate along the line
+  double lv = grid_coord(kind == 0 ? ymin : xmin, h, line);
+  double lo = (TWO_PI * (double)seg) / (double)M;
+  double hi = lo + TWO_PI / (double)M;
+  bool pos_lo = fine[2 * seg + ax] >= lv;
+  double t = 0.5 * (lo + hi);
+  for (int it = 0; it < NEWTON_MAXIT; ++it) {
+    TrigSums v = trig_warp(cc, n, t, lane, false);
+    double f = v.f - lv, fp = v.f1;
+    bool same = (f >= 0.0) == pos_lo;
+    if (same) lo = t; else hi = t;
+    double tn = t - f / fp;
+    if (!isfinite(tn) || tn <= lo || tn >= hi) tn = 0.5 * (lo + hi);
+    bool done = fabs(tn - t) <= NEWTON_TOL;
+    t = tn;
+    if (done) break;
+  }
+  TrigSums o = trig_warp(co, n, t, lane, false);
+  if (lane == 0) {
+    int first = count_le(kind == 0 ? xmin : ymin, h, N, o.f);
+    cr_alpha[warp] = t;
+    cr_xi[warp] = o.f;
+    cr_first[warp] = first;
+    if (first <= 0 || first >= N) atomicOr(flags, FLAG_OUTSIDE);
+  }
+}
+
+__global__ void k_arm_count(int ncr, int N, const int* cr_kind, const int* cr_line, const int* cr_first,
+                            int* hcount, int* vcount, int* hid, int* vid) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncr) return;
+  int line = cr_line[c], first = cr_first[c];
+  if (first <= 0 || first >= N) return;
+  if (cr_kind[c] == 0) {
+    long a = (long)line * N + first;
+    atomicAdd(&hcount[a], 1);
+    atomicExch(&hid[a], c);
+  } else {
+    long a = (long)first * N + line;
+    atomicAdd(&vcount[a], 1);
+    atomicExch(&vid[a], c);
+  }
+}
+
+// one warp per row: side = parity of horizontal-arm crossings left of the node
+__global__ void k_classify(int N, const int* hcount, uint8_t* side, int* flags) {
+  int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (j >= N) return;
+  int per = N / 32 > 0 ? N / 32 : 1;
+  int b = lane * per, e = min(N, b + per);
+  const int* row = hcount + (long)j * N;
+  int par = 0, bad = 0;
+  for (int i = b; i < e; ++i) {
+    int c = row[i];
+    par ^= (c & 1);
+    bad |= (c >= 3);
+  }
+  int incl = par;
+  for (int o = 1; o < 32; o <<= 1) {
+    int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl ^= v;
+  }
+  int run = incl ^ par;  // exclusive prefix parity
+  for (int i = b; i < e; ++i) {
+    run ^= (row[i] & 1);
+    side[(long)j * N + i] = (uint8_t)run;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, FLAG_UNDERRES);
+}
+
+__device__ __forceinline__ bool is_irregular(const uint8_t* side, int N, int i, int j) {
+  uint8_t s = side[(long)j * N + i];
+  if (i > 0 && side[(long)j * N + i - 1] != s) return true;
+  if (i < N - 1 && side[(long)j * N + i + 1] != s) return true;
+  if (j > 0 && side[(long)(j - 1) * N + i] != s) return true;
+  if (j < N - 1 && side[(long)(j + 1) * N + i] != s) return true;
+  return false;
+}
+
+// one warp per row: count irregular nodes; check vertical arms against the sides
+__global__ void k_irr_count(int N, const uint8_t* side, const int* vcount, int* rowcnt, int* flags) {
+  int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (j >= N) return;
+  int cnt = 0, bad = 0;
+  for (int i = lane; i < N; i += 32) {
+    cnt += is_irregular(side, N, i, j) ? 1 : 0;
+    if (j >= 1) {
+      int vc = vcount[(long)j * N + i];
+      bool diff = side[(long)j * N + i] != side[(long)(j - 1) * N + i];
+      if (vc >= 3 || diff != ((vc & 1) == 1)) bad = 1;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) rowcnt[j] = cnt;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flags, FLAG_UNDERRES);
+}
+
+__global__ void k_irr_emit(int N, double xmin, double ymin, double h, const uint8_t* side, const int* hcount,
+                           const int* vcount, const int* hid, const int* vid, const double* cr_xi,
+                           const int* row_ptr, IrrNode* irr) {
+  int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (j >= N) return;
+  int base = row_ptr[j];
+  for (int i0 = 0; i0 < N; i0 += 32) {
+    int i = i0 + lane;
+    bool irr_here = i < N && is_irregular(side, N, i, j);
+    unsigned mask = __ballot_sync(0xffffffffu, irr_here);
+    if (irr_here) {
+      int slot = base + __popc(mask & ((1u << lane) - 1u));
+      IrrNode node;
+      node.i = i;
+      node.j = j;
+      node.sign = side[(long)j * N + i] ? -1.0 : 1.0;
+      for (int a = 0; a < 4; ++a) {
+        node.target[a] = -1;
+        node.d[a] = 0.0;
+      }
+      long r = (long)j * N;
+      if (i >= 1 && hcount[r + i] == 1) {  // west arm (i-1,j)-(i,j)
+        int c = hid[r + i];
+        node.target[0] = c;
+        node.d[0] = grid_coord(xmin, h, i - 1) - cr_xi[c];
+      }
+      if (i + 1 <= N - 1 && hcount[r + i + 1] == 1) {  // east arm (i,j)-(i+1,j)
+        int c = hid[r + i + 1];
+        node.target[1] = c;
+        node.d[1] = grid_coord(xmin, h, i + 1) - cr_xi[c];
+      }
+      if (j >= 1 && vcount[r + i] == 1) {  // south arm (i,j-1)-(i,j)
+        int c = vid[r + i];
+        node.target[2] = c;
+        node.d[2] = grid_coord(ymin, h, j - 1) - cr_xi[c];
+      }
+      if (j + 1 <= N - 1 && vcount[r + N + i] == 1) {  // north arm (i,j)-(i,j+1)
+        int c = vid[r + N + i];
+        node.target[3] = c;
+        node.d[3] = grid_coord(ymin, h, j + 1) - cr_xi[c];
+      }
+      irr[slot] = node;
+    }
+    base += __popc(mask);
+  }
+}
+
+// geometry at every target (crossings, then nodes) and the inverse 3x3 jump matrix
+__global__ void k_target_geo(const double2* coef, int n, int ncr, const double* cr_alpha, TargetGeo* tg) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= ncr + n) return;
+  int nk = n / 2 + 1;
+  double a = warp < ncr ? cr_alpha[warp] : (TWO_PI * (double)(warp - ncr)) / (double)n;
+  TrigSums x = trig_warp(coef, n, a, lane, true);
+  TrigSums y = trig_warp(coef + nk, n, a, lane, true);
+  if (lane != 0) return;
+  TargetGeo g;
+  g.alpha = a;
+  g.xa = x.f1;
+  g.ya = y.f1;
+  g.xaa = x.f2;
+  g.yaa = y.f2;
+  g.sa = sqrt(g.xa * g.xa + g.ya * g.ya);
+  g.saa = (g.xa * g.xaa + g.ya * g.yaa) / g.sa;
+  double A[9] = {g.xa * g.xa, g.ya * g.ya, 2.0 * g.xa * g.ya,
+                 g.xa * g.ya, -g.xa * g.ya, g.ya * g.ya - g.xa * g.xa,
+                 1.0, 1.0, 0.0};
+  double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+  double c10 = A[2] * A[7] - A[1] * A[8], c11 = A[0] * A[8] - A[2] * A[6], c12 = A[1] * A[6] - A[0] * A[7];
+  double c20 = A[1] * A[5] - A[2] * A[4], c21 = A[2] * A[3] - A[0] * A[5], c22 = A[0] * A[4] - A[1] * A[3];
+  double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+  double id = 1.0 / det;
+  g.A3i[0] = c00 * id; g.A3i[1] = c10 * id; g.A3i[2] = c20 * id;
+  g.A3i[3] = c01 * id; g.A3i[4] = c11 * id; g.A3i[5] = c21 * id;
+  g.A3i[6] = c02 * id; g.A3i[7] = c12 * id; g.A3i[8] = c22 * id;
+  tg[warp] = g;
+}
+
+// 6-point stencil per node: closest node, d1/d2, sides, scaled 6x6 LU -> inverse rows 0..2
+__global__ void k_stencil(int n, const double* xy, double xmin, double ymin, double h, int N, const uint8_t* side,
+                          const TargetGeo* tg_nodes, Stencil* st, int* probe_mark, int* flags) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double px = xy[2 * p], py = xy[2 * p + 1];
+  double x0 = grid_coord(xmin, h, 0), y0 = grid_coord(ymin, h, 0);
+  int i0 = (int)floor(__dadd_rn(__ddiv_rn(__dsub_rn(px, x0), h), 0.5));
+  int j0 = (int)floor(__dadd_rn(__ddiv_rn(__dsub_rn(py, y0), h), 0.5));
+  int d1 = (i0 >= 0 && i0 < N && px > grid_coord(xmin, h, i0)) ? 1 : -1;
+  int d2 = (j0 >= 0 && j0 < N && py > grid_coord(ymin, h, j0)) ? 1 : -1;
+  const int rr[6] = {0, 1, 0, 0, -1, d1};
+  const int ss[6] = {0, 0, 1, -1, 0, d2};
+  Stencil S;
+  double M[6][6];
+  bool ok = true;
+  for (int m = 0; m < 6; ++m) {
+    int qi = i0 + rr[m], qj = j0 + ss[m];
+    if (qi < 0 || qj < 0 || qi >= N || qj >= N) {
+      ok = false;
+      qi = 0;
+      qj = 0;
+    }
+    S.probe[m] = qj * N + qi;  // temporarily the flat grid index
+    S.minus[m] = side[(long)qj * N + qi] == 0 ? 1 : 0;
+    S.dx[m] = __dsub_rn(grid_coord(xmin, h, qi), px);
+    S.dy[m] = __dsub_rn(grid_coord(ymin, h, qj), py);
+    double a = S.dx[m] / h, b = S.dy[m] / h;
+    M[m][0] = 1.0; M[m][1] = a; M[m][2] = b;
+    M[m][3] = 0.5 * a * a; M[m][4] = a * b; M[m][5] = 0.5 * b * b;
+  }
+  if (!ok) atomicOr(flags, FLAG_OUTSIDE);
+  // rows r of inv(M) solve M^T z = e_r; LU of M^T with partial pivoting
+  double A[6][6];
+  int piv[6];
+  for (int r = 0; r < 6; ++r)
+    for (int c = 0; c < 6; ++c) A[r][c] = M[c][r];
+  for (int k = 0; k < 6; ++k) {
+    int pr = k;
+    double best = fabs(A[k][k]);
+    for (int r = k + 1; r < 6; ++r)
+      if (fabs(A[r][k]) > best) { best = fabs(A[r][k]); pr = r; }
+    piv[k] = pr;
+    if (pr != k)
+      for (int c = 0; c < 6; ++c) { double t = A[k][c]; A[k][c] = A[pr][c]; A[pr][c] = t; }
+    double d = A[k][k];
+    for (int r = k + 1; r < 6; ++r) {
+      double l = A[r][k] / d;
+      A[r][k] = l;
+      for (int c = k + 1; c < 6; ++c) A[r][c] -= l * A[k][c];
+    }
+  }
+  for (int row = 0; row < 3; ++row) {
+    double z[6] = {0, 0, 0, 0, 0, 0};
+    z[row] = 1.0;
+    for (int k = 0; k < 6; ++k) {
+      int pr = piv[k];
+      if (pr != k) { double t = z[k]; z[k] = z[pr]; z[pr] = t; }
+    }
+    for (int r = 1; r < 6; ++r)
+      for (int c = 0; c < r; ++c) z[r] -= A[r][c] * z[c];
+    for (int r = 5; r >= 0; --r) {
+      for (int c = r + 1; c < 6; ++c) z[r] -= A[r][c] * z[c];
+      z[r] /= A[r][r];
+    }
+    double scale = row == 0 ? 1.0 : 1.0 / h;
+    for (int m = 0; m < 6; ++m) {
+      double v = z[m] * scale;
+      if (row == 0) S.r0[m] = v; else if (row == 1) S.r1[m] = v; else S.r2[m] = v;
+    }
+  }
+  const TargetGeo& g = tg_nodes[p];
+  S.nx = g.ya / g.sa;
+  S.ny = -g.xa / g.sa;
+  S.w = g.sa * TWO_PI / (double)n;
+  st[p] = S;
+  if (ok)
+    for (int m = 0; m < 6; ++m) probe_mark[S.probe[m]] = 1;
+}
+
+__global__ void k_probe_count(int N, const int* probe_mark, int* cnt) {
+  int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (j >= N) return;
+  int c = 0;
+  for (int i = lane; i < N; i += 32) c += probe_mark[(long)j * N + i] != 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) cnt[j] = c;
+}
+
+__global__ void k_probe_emit(int N, int* probe_mark, const int* prow_ptr, int* probe_i) {
+  int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (j >= N) return;
+  int base = prow_ptr[j];
+  for (int i0 = 0; i0 < N; i0 += 32) {
+    int i = i0 + lane;
+    bool on = i < N && probe_mark[(long)j * N + i] != 0;
+    unsigned mask = __ballot_sync(0xffffffffu, on);
+    if (on) {
+      int slot = base + __popc(mask & ((1u << lane) - 1u));
+      probe_i[slot] = i;
+      probe_mark[(long)j * N + i] = slot + 1;
+    }
+    base += __popc(mask);
+  }
+}
+
+__global__ void k_stencil_map(int n, const int* probe_mark, Stencil* st) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  for (int m = 0; m < 6; ++m) st[p].probe[m] = probe_mark[st[p].probe[m]] - 1;
+}
+
+// --------------------------------------------------------------------------- host driver
+kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
+  cudaStream_t s = c->stream;
+  const int N = c->N;
+  const double h = c->h;
+  const int M = SUBSAMPLES * n;
+  const int nk = n / 2 + 1;
+  c->have_iface = false;
+
+  KFBI_TRY(cudaMemcpyAsync(c->xy, xy_in, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
+  KFBI_TRY(cudaMemsetAsync(c->flags, 0, sizeof(int), s));
+  size_t NN = (size_t)N * N;
+  KFBI_TRY(cudaMemsetAsync(c->hcount, 0, NN * sizeof(int), s));
+  KFBI_TRY(cudaMemsetAsync(c->vcount, 0, NN * sizeof(int), s));
+  KFBI_TRY(cudaMemsetAsync(c->probe_mark, 0, NN * sizeof(int), s));
+
+  k_twiddles_n<<<cdiv(n, 256), 256, 0, s>>>(n, (double2*)c->twn);
+  k_dft_real<<<cdiv((long)2 * nk * 32, 256), 256, 0, s>>>(c->xy, 2, 2, n, (const double2*)c->twn,
+                                                          (double2*)c->icoef);
+  double mg = BOX_MARGIN * h;
+  k_fine_samples<<<cdiv((long)M * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, M, c->fine,
+                                                         c->xmin + mg, c->xmax - mg, c->ymin + mg,
+                                                         c->ymax - mg, c->flags);
+  k_seg_count<<<cdiv(2 * M, 256), 256, 0, s>>>(c->fine, M, c->xmin, c->ymin, h, N, c->seg_count);
+  k_scan<<<1, 1024, 0, s>>>(c->seg_count, c->seg_off, 2 * M);
+  KFBI_TRY(cudaMemcpyAsync(&c->host_counts[0], c->seg_off + 2 * M, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KFBI_TRY(cudaMemcpyAsync(&c->host_counts[1], c->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KFBI_TRY(cudaStreamSynchronize(s));
+  if (c->host_counts[1] & FLAG_OUTSIDE) return KFBI_ERR_OUTSIDE_BOX;
+  int ncr = c->host_counts[0];
+  KFBI_CHECK(ensure_cross_capacity(c, ncr));
+  c->n_cross = ncr;
+
+  k_emit_pairs<<<cdiv(2 * M, 256), 256, 0, s>>>(c->fine, M, c->xmin, c->ymin, h, N, c->seg_off, c->cr_kind,
+                                                c->cr_line, c->cr_seg);
+  if (ncr > 0) {
+    k_newton<<<cdiv((long)ncr * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, M, c->fine, c->xmin, c->ymin,
+                                                       h, N, ncr, c->cr_kind, c->cr_line, c->cr_seg, c->cr_first,
+                                                       c->cr_alpha, c->cr_xi, c->flags);
+    k_arm_count<<<cdiv(ncr, 256), 256, 0, s>>>(ncr, N, c->cr_kind, c->cr_line, c->cr_first, c->hcount,
+                                              c->vcount, c->hid, c->vid);
+  }
+  int wblocks = cdiv((long)N * 32, 256);
+  k_classify<<<wblocks, 256, 0, s>>>(N, c->hcount, c->side, c->flags);
+  k_irr_count<<<wblocks, 256, 0, s>>>(N, c->side, c->vcount, c->rowcnt, c->flags);
+  k_scan<<<1, 1024, 0, s>>>(c->rowcnt, c->row_ptr, N);
+  KFBI_TRY(cudaMemcpyAsync(&c->host_counts[0], c->row_ptr + N, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KFBI_TRY(cudaMemcpyAsync(&c->host_counts[1], c->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KFBI_TRY(cudaStreamSynchronize(s));
+  if (c->host_counts[1] & FLAG_OUTSIDE) return KFBI_ERR_OUTSIDE_BOX;
+  if (c->host_counts[1] & FLAG_UNDERRES) return KFBI_ERR_UNDERRESOLVED;
+  int nirr = c->host_counts[0];
+  if (nirr > c->cap_irr) return KFBI_ERR_CAPACITY;
+  c->n_irr = nirr;
+
+  k_irr_emit<<<wblocks, 256, 0, s>>>(N, c->xmin, c->ymin, h, c->side, c->hcount, c->vcount, c->hid, c->vid,
+                                     c->cr_xi, c->row_ptr, c->irr);
+  k_target_geo<<<cdiv((long)(ncr + n) * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, ncr, c->cr_alpha,
+                                                               c->tgeo);
+  k_stencil<<<cdiv(n, 128), 128, 0, s>>>(n, c->xy, c->xmin, c->ymin, h, N, c->side, c->tgeo + ncr, c->stencil,
+                                         c->probe_mark, c->flags);
+  k_probe_count<<<wblocks, 256, 0, s>>>(N, c->probe_mark, c->prow_cnt);
+  k_scan<<<1, 1024, 0, s>>>(c->prow_cnt, c->prow_ptr, N);
+  k_probe_emit<<<wblocks, 256, 0, s>>>(N, c->probe_mark, c->prow_ptr, c->probe_i);
+  k_stencil_map<<<cdiv(n, 128), 128, 0, s>>>(n, c->probe_mark, c->stencil);
+  KFBI_TRY(cudaGetLastError());
+  KFBI_TRY(cudaMemcpyAsync(&c->host_counts[0], c->prow_ptr + N, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KFBI_TRY(cudaMemcpyAsync(&c->host_counts[1], c->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KFBI_TRY(cudaStreamSynchronize(s));
+  if (c->host_counts[1] & FLAG_OUTSIDE) return KFBI_ERR_OUTSIDE_BOX;
+  if (c->host_counts[1] & FLAG_UNDERRES) return KFBI_ERR_UNDERRESOLVED;
+  c->n_probe = c->host_counts[0];
+  c->n = n;
+  c->have_iface = true;
+  return KFBI_OK;
+}
+
+}  // namespace kfbi

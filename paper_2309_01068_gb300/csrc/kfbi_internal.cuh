@@ -1,0 +1,224 @@
+// Internal declarations of libkfbi: the context layout and device helpers shared by the
+// translation units. Nothing here is part of the C ABI (include/kfbi.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "kfbi.h"
+
+#define KFBI_TRY(call)                                        \
+  do {                                                        \
+    cudaError_t kfbi_e_ = (call);                             \
+    if (kfbi_e_ != cudaSuccess) {                             \
+      kfbi::note_cuda_error(kfbi_e_, #call, __FILE__, __LINE__); \
+      return KFBI_ERR_CUDA;                                   \
+    }                                                         \
+  } while (0)
+
+#define KFBI_CHECK(st)                    \
+  do {                                    \
+    kfbi_status kfbi_s_ = (st);           \
+    if (kfbi_s_ != KFBI_OK) return kfbi_s_; \
+  } while (0)
+
+namespace kfbi {
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+constexpr double PI = 3.14159265358979323846;
+constexpr double TWO_PI = 6.28318530717958647692;
+constexpr int SUBSAMPLES = 8;        // fine samples per node interval for the crossing search
+constexpr int NEWTON_MAXIT = 60;
+constexpr double NEWTON_TOL = 1e-15;
+constexpr double BOX_MARGIN = 3.0;   // interface must stay 3h inside the box
+constexpr int MAX_RESTART = 200;
+
+// device error flags (bitmask in Iface::flags)
+enum : int { FLAG_OUTSIDE = 1, FLAG_UNDERRES = 2, FLAG_CAPACITY = 4 };
+
+// per-target geometry: crossings first, then the interface nodes
+struct TargetGeo {
+  double alpha;
+  double xa, ya, xaa, yaa, sa, saa;
+  double A3i[9];  // inverse of the 3x3 second-jump matrix (App. A.1), row-major
+};
+
+// one irregular node and its (up to) four crossed arms: W, E, S, N
+struct IrrNode {
+  int i, j;
+  int target[4];   // crossing index per arm, -1 if the arm is not crossed
+  double d[4];     // neighbour minus crossing along the arm
+  double sign;     // -1 for an Omega+ node, +1 for Omega- (times 1/h^2 applied later)
+};
+
+// one interface node's interpolation stencil (Sec. 4.3)
+struct Stencil {
+  int probe[6];    // index into the probe-value array
+  int minus[6];    // 1 if the point is in Omega-
+  double dx[6], dy[6];
+  double r0[6], r1[6], r2[6];  // rows 0..2 of the inverse 6x6 matrix (value, d/dx, d/dy)
+  double nx, ny;   // unit outward normal at the node
+  double w;        // s_alpha * 2 pi / n (trapezoidal arclength weight)
+};
+
+// GMRES control block in device memory. The scalar header comes first so that the host
+// can poll it without copying the arrays.
+struct GmresCtl {
+  int phase;        // PH_*
+  int next_phase;
+  int done;         // 1 once the solve has finished (read by every kernel of a body)
+  int action;       // ACT_* decided for the elementwise follow-up kernel
+  int j;            // current Arnoldi column
+  int k_end;        // columns used at the end of a cycle
+  int its;          // Arnoldi applies
+  int cycles;       // completed cycles
+  int max_iter, m;
+  int status;       // kfbi_status when done
+  int ticket;       // last-block ticket for reductions
+  int breakdown;
+  int trust;        // finish on the Givens estimate without a true-residual apply
+  double tol, bnorm, beta, hnorm, res_est;
+  double g[MAX_RESTART + 1];
+  double cs[MAX_RESTART], sn[MAX_RESTART];
+  double y[MAX_RESTART];
+  double hcol[MAX_RESTART + 1];   // Gram-Schmidt coefficients of the current pass
+  double H[(MAX_RESTART + 1) * MAX_RESTART];  // column-major, leading dim m+1
+};
+enum : int { PH_RESID = 0, PH_ARNOLDI = 1, PH_DONE = 2 };
+
+}  // namespace kfbi
+
+struct kfbi_ctx {
+  // grid
+  int N = 0, logN = 0;
+  double xmin = 0, xmax = 0, ymin = 0, ymax = 0, h = 0;
+  double kappa = 0;
+  int boxbc = 0, precision = 0, max_nodes = 0;
+  cudaStream_t stream = nullptr;
+
+  // constant tables
+  double* sintab = nullptr;   // [4N] sin(pi m / (2N))
+  float* sintab_f = nullptr;
+  double* lam = nullptr;      // [N] 1-D eigenvalues of the box operator
+  float* lam_f = nullptr;
+  double* twN = nullptr;      // [N] complex: e^{-2 pi i m / N}, m < N/2
+  float* twN_f = nullptr;
+
+  // interface
+  int n = 0;
+  bool have_iface = false;
+  int n_cross = 0, n_irr = 0, n_probe = 0;
+  int cap_cross = 0, cap_irr = 0;
+  double* xy = nullptr;         // [max_nodes][2]
+  double* twn = nullptr;        // [max_nodes] complex e^{2 pi i m / n}
+  double* icoef = nullptr;      // [2][max_nodes/2+1] complex Fourier coefficients of x, y
+  double* fine = nullptr;       // [SUBSAMPLES*max_nodes][2]
+  int* seg_count = nullptr;     // [2*M + 1]
+  int* seg_off = nullptr;       // [2*M + 1]
+  int* cr_kind = nullptr;       // [cap_cross]
+  int* cr_line = nullptr;
+  int* cr_seg = nullptr;
+  int* cr_first = nullptr;
+  double* cr_alpha = nullptr;
+  double* cr_xi = nullptr;
+  kfbi::TargetGeo* tgeo = nullptr;  // [cap_cross + max_nodes]
+  int* hcount = nullptr;        // [N][N] crossings per horizontal arm (i-1,j)-(i,j)
+  int* vcount = nullptr;        // [N][N] crossings per vertical arm (i,j-1)-(i,j)
+  int* hid = nullptr;           // [N][N] crossing index on the arm (if exactly one)
+  int* vid = nullptr;
+  uint8_t* side = nullptr;      // [N][N]
+  int* rowcnt = nullptr;        // [N + 1]
+  int* row_ptr = nullptr;       // [N + 1]
+  kfbi::IrrNode* irr = nullptr; // [cap_irr]
+  kfbi::Stencil* stencil = nullptr;  // [max_nodes]
+  int* probe_mark = nullptr;    // [N][N] probe index + 1 (0 = not a probe)
+  int* prow_cnt = nullptr;      // [N + 1]
+  int* prow_ptr = nullptr;      // [N + 1]
+  int* probe_i = nullptr;       // [6*max_nodes] column of each probe (row from prow_ptr)
+  int* flags = nullptr;         // device error flags
+  int* counts = nullptr;        // device counters [8]
+  int* host_counts = nullptr;   // pinned [8]
+
+  // per-apply work buffers
+  double* dcoef = nullptr;      // [max_nodes/2+1] complex density coefficients
+  double* dint = nullptr;       // [1] integral of the density
+  double* jumps = nullptr;      // [targets][6]
+  double* cval = nullptr;       // [cap_irr] corrections (T)
+  double* boxg = nullptr;       // [4N] free-space box data
+  double* spec = nullptr;       // [N][N] row-transformed grid (T)
+  double* probe_val = nullptr;  // [6*max_nodes] (T)
+  double* tmp_vals = nullptr;   // [max_nodes]
+
+  // GMRES
+  kfbi::GmresCtl* gctl = nullptr;
+  kfbi::GmresCtl* host_gctl = nullptr;  // pinned
+  double* gV = nullptr;         // [(MAX_RESTART+1)][max_nodes]
+  double* gpart = nullptr;      // [blocks][MAX_RESTART+1]
+  double* gw = nullptr;         // apply output / Arnoldi vector w  [max_nodes]
+  double* gin = nullptr;        // apply input [max_nodes]
+  double* gb = nullptr;         // right-hand side copy [max_nodes]
+  double* gx = nullptr;         // iterate [max_nodes]
+  double* gr = nullptr;         // outer residual / correction (refinement) [max_nodes]
+  int* zero_flag = nullptr;     // device int 0
+
+  // timing
+  bool timing = false;
+  double timing_ms = 0.0;
+  int timing_launches = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace kfbi {
+
+// --------------------------------------------------------------------------- helpers
+// Grid coordinate lo + (l + 1/2) h with separate rounding of the product and the sum
+// (no fused multiply-add), so that comparisons against it are reproducible.
+__device__ __forceinline__ double grid_coord(double lo, double h, int l) {
+  return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)l, 0.5), h));
+}
+
+// number of grid coordinates lo + (l+1/2)h (l = 0..N-1) that are <= c
+__device__ __forceinline__ int count_le(double lo, double h, int N, double c) {
+  double t = (c - lo) / h - 0.5;
+  int l = (int)floor(t) + 1;  // candidate count
+  if (l < 0) l = 0;
+  if (l > N) l = N;
+  while (l < N && grid_coord(lo, h, l) <= c) ++l;
+  while (l > 0 && !(grid_coord(lo, h, l - 1) <= c)) --l;
+  return l;
+}
+
+template <typename T>
+struct Cplx {
+  T re, im;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+inline int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+// host-side helpers implemented in the .cu files
+kfbi_status ensure_cross_capacity(kfbi_ctx* c, int n_cross);
+kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* density, double* values,
+                          double* dnormal, double* grid, int bie_kind, const double* eps_v,
+                          const int* skip_flag);
+kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u);
+kfbi_status interp_grid_enqueue(kfbi_ctx* c, const double* grid, double* values);
+
+}  // namespace kfbi

@@ -1,0 +1,301 @@
+"""Thin Python binding of libkfbi (include/kfbi.h) over ctypes.
+
+Argument marshalling only: tensors are passed as device pointers on torch's current
+CUDA stream; every step of the method runs in the library's CUDA kernels. There is no
+CPU fallback: if libkfbi.so is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkfbi.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "kfbi.h")
+
+# codes mirrored from include/kfbi.h
+OK, ERR_ARG, ERR_CUDA, ERR_OUTSIDE_BOX, ERR_UNDERRESOLVED, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
+ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
+BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2
+FP64, MIXED = 0, 1
+SINGLE, DOUBLE = 0, 1
+BIE_INTERIOR_DL, BIE_HS_EXTERIOR_MDL, BIE_STEFAN_SL = 0, 1, 2
+STEP_HELE_SHAW, STEP_STEFAN = 0, 1
+
+
+class KfbiError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {_status_string(status)} (status {status})")
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("status", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ThetaLParams(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("sigma", ctypes.c_double), ("J", ctypes.c_double),
+                ("St", ctypes.c_double), ("eps_c", ctypes.c_double), ("eps_aniso", ctypes.c_double),
+                ("eps_v", ctypes.c_double), ("fold", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("restart", ctypes.c_int)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+_SIGNATURES = {
+    "kfbi_create": (_I, [_I, _D, _D, _D, _D, _D, _I, _I, _I, ctypes.POINTER(_P)]),
+    "kfbi_destroy": (None, [_P]),
+    "kfbi_set_stream": (_I, [_P, _P]),
+    "kfbi_set_interface": (_I, [_P, _I, _P]),
+    "kfbi_apply_layer_potential": (_I, [_P, _I, _P, _P, _P, _P]),
+    "kfbi_bie_apply": (_I, [_P, _I, _P, _P, _P]),
+    "kfbi_solve_bie": (_I, [_P, _I, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
+    "kfbi_grid_solve": (_I, [_P, _P, _P]),
+    "kfbi_interp_grid": (_I, [_P, _P, _P]),
+    "kfbi_interface_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "kfbi_copy_sides": (_I, [_P, _P]),
+    "kfbi_copy_crossings": (_I, [_P, _I, _P, _P]),
+    "kfbi_copy_irregular": (_I, [_P, _I, _P]),
+    "kfbi_thetal_create": (_I, [_P, _I, _P, _D, ctypes.POINTER(_D), ctypes.POINTER(ThetaLParams),
+                                ctypes.POINTER(_P)]),
+    "kfbi_thetal_destroy": (None, [_P]),
+    "kfbi_step": (_I, [_P, _P, _D, ctypes.POINTER(SolveInfo)]),
+    "kfbi_thetal_read": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_D)]),
+    "kfbi_status_string": (ctypes.c_char_p, [_I]),
+    "kfbi_timing_enable": (_I, [_P, _I]),
+    "kfbi_timing_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+}
+
+
+def header_functions():
+    """Names of the functions include/kfbi.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kfbi_\w+)\s*\(", text)))
+
+
+def load():
+    """Load libkfbi.so (built in-tree by build.py) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2309_01068_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _status_string(s):
+    try:
+        return load().kfbi_status_string(s).decode()
+    except Exception:  # noqa: BLE001 - best effort message
+        return "status"
+
+
+def _check(status, where, allow=()):
+    if status != OK and status not in allow:
+        raise KfbiError(status, where)
+    return status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("libkfbi takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f64(t, shape):
+    if t.dtype != torch.float64 or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected float64 tensor of shape {shape}, got {t.dtype} {tuple(t.shape)}")
+    return _ptr(t)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """kfbi_create / kfbi_destroy and the calls on one grid."""
+
+    def __init__(self, N, box, kappa=0.0, boxbc=BOX_DIRICHLET0, precision=FP64, max_nodes=1024):
+        self.lib = load()
+        self.N = int(N)
+        self.box = tuple(float(b) for b in box)
+        self.kappa = float(kappa)
+        self.boxbc = int(boxbc)
+        self.precision = int(precision)
+        self.max_nodes = int(max_nodes)
+        self.n = 0
+        h = ctypes.c_void_p()
+        _check(self.lib.kfbi_create(self.N, *self.box, self.kappa, self.boxbc, self.precision, self.max_nodes,
+                                    ctypes.byref(h)), "kfbi_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.kfbi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def _sync_stream(self):
+        _check(self.lib.kfbi_set_stream(self.handle, _stream()), "kfbi_set_stream")
+
+    def set_interface(self, xy):
+        self._sync_stream()
+        n = xy.shape[0]
+        _check(self.lib.kfbi_set_interface(self.handle, n, _f64(xy, (n, 2))), "kfbi_set_interface")
+        self.n = n
+
+    def apply(self, layer, density, dnormal=False, grid=False):
+        self._sync_stream()
+        n = self.n
+        vals = torch.empty(n, dtype=torch.float64, device=density.device)
+        dn = torch.empty(n, dtype=torch.float64, device=density.device) if dnormal else None
+        g = torch.empty((self.N, self.N), dtype=torch.float64, device=density.device) if grid else None
+        _check(self.lib.kfbi_apply_layer_potential(self.handle, layer, _f64(density, (n,)), _ptr(vals), _ptr(dn),
+                                                   _ptr(g)), "kfbi_apply_layer_potential")
+        return vals, dn, g
+
+    def apply_into(self, layer, density, values, dnormal=None, grid=None):
+        self._sync_stream()
+        _check(self.lib.kfbi_apply_layer_potential(self.handle, layer, _ptr(density), _ptr(values), _ptr(dnormal),
+                                                   _ptr(grid)), "kfbi_apply_layer_potential")
+
+    def bie_apply(self, kind, x, eps_v=None, out=None):
+        self._sync_stream()
+        y = out if out is not None else torch.empty_like(x)
+        _check(self.lib.kfbi_bie_apply(self.handle, kind, _ptr(eps_v), _f64(x, (self.n,)), _ptr(y)), "kfbi_bie_apply")
+        return y
+
+    def solve_bie(self, kind, rhs, density=None, tol=1e-10, max_iter=500, restart=100, eps_v=None):
+        """Returns (density, info dict); density is updated in place when given."""
+        self._sync_stream()
+        x = density if density is not None else torch.zeros_like(rhs)
+        info = SolveInfo()
+        _check(self.lib.kfbi_solve_bie(self.handle, kind, _ptr(eps_v), _f64(rhs, (self.n,)), float(tol),
+                                       int(max_iter), int(restart), _f64(x, (self.n,)), ctypes.byref(info)),
+               "kfbi_solve_bie", allow=(ERR_NOT_CONVERGED,))
+        return x, info.as_dict()
+
+    def grid_solve(self, rhs, out=None):
+        self._sync_stream()
+        u = out if out is not None else torch.empty_like(rhs)
+        _check(self.lib.kfbi_grid_solve(self.handle, _f64(rhs, (self.N, self.N)), _ptr(u)), "kfbi_grid_solve")
+        return u
+
+    def interp_grid(self, grid):
+        self._sync_stream()
+        v = torch.empty(self.n, dtype=torch.float64, device=grid.device)
+        _check(self.lib.kfbi_interp_grid(self.handle, _f64(grid, (self.N, self.N)), _ptr(v)), "kfbi_interp_grid")
+        return v
+
+    def stats(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.kfbi_interface_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "kfbi_interface_stats")
+        return dict(crossings=a.value, irregular=b.value, probes=c.value)
+
+    def sides(self):
+        self._sync_stream()
+        s = torch.empty((self.N, self.N), dtype=torch.uint8, device="cuda")
+        _check(self.lib.kfbi_copy_sides(self.handle, _ptr(s)), "kfbi_copy_sides")
+        return s
+
+    def crossings(self):
+        self._sync_stream()
+        cnt = self.stats()["crossings"]
+        klf = torch.empty((max(cnt, 1), 3), dtype=torch.int32, device="cuda")
+        ax = torch.empty((max(cnt, 1), 2), dtype=torch.float64, device="cuda")
+        _check(self.lib.kfbi_copy_crossings(self.handle, cnt, _ptr(klf), _ptr(ax)), "kfbi_copy_crossings")
+        return klf[:cnt], ax[:cnt]
+
+    def irregular(self):
+        self._sync_stream()
+        cnt = self.stats()["irregular"]
+        ji = torch.empty((max(cnt, 1), 2), dtype=torch.int32, device="cuda")
+        _check(self.lib.kfbi_copy_irregular(self.handle, cnt, _ptr(ji)), "kfbi_copy_irregular")
+        return ji[:cnt]
+
+    def timing(self, enable=None):
+        if enable is not None:
+            _check(self.lib.kfbi_timing_enable(self.handle, 1 if enable else 0), "kfbi_timing_enable")
+            return None
+        ms, cnt = ctypes.c_double(), ctypes.c_int()
+        _check(self.lib.kfbi_timing_read(self.handle, ctypes.byref(ms), ctypes.byref(cnt)), "kfbi_timing_read")
+        return ms.value, cnt.value
+
+
+class ThetaL:
+    """kfbi_thetal_create / kfbi_step / kfbi_thetal_read on a context."""
+
+    def __init__(self, ctx: Context, eta, L, xbar, kind, tol=1e-8, max_iter=500, restart=100, sigma=0.0, J=0.0,
+                 St=0.0, eps_c=0.0, eps_aniso=0.0, eps_v=0.0, fold=4):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.n = eta.shape[0]
+        p = ThetaLParams(kind=kind, sigma=sigma, J=J, St=St, eps_c=eps_c, eps_aniso=eps_aniso, eps_v=eps_v,
+                         fold=fold, tol=tol, max_iter=max_iter, restart=restart)
+        xb = (ctypes.c_double * 2)(float(xbar[0]), float(xbar[1]))
+        h = ctypes.c_void_p()
+        ctx._sync_stream()
+        _check(self.lib.kfbi_thetal_create(ctx.handle, self.n, _f64(eta, (self.n,)), float(L), xb, ctypes.byref(p),
+                                           ctypes.byref(h)), "kfbi_thetal_create")
+        self.handle = h
+
+    def step(self, dt):
+        self.ctx._sync_stream()
+        info = SolveInfo()
+        _check(self.lib.kfbi_step(self.ctx.handle, self.handle, float(dt), ctypes.byref(info)), "kfbi_step",
+               allow=(ERR_NOT_CONVERGED,))
+        return info.as_dict()
+
+    def read(self):
+        self.ctx._sync_stream()
+        n, N = self.n, self.ctx.N
+        eta = torch.empty(n, dtype=torch.float64, device="cuda")
+        xy = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+        dens = torch.empty(n, dtype=torch.float64, device="cuda")
+        T = torch.empty((N, N), dtype=torch.float64, device="cuda")
+        sc = (ctypes.c_double * 8)()
+        _check(self.lib.kfbi_thetal_read(self.handle, _ptr(eta), _ptr(xy), _ptr(dens), _ptr(T), sc),
+               "kfbi_thetal_read")
+        torch.cuda.synchronize()
+        return dict(eta=eta, xy=xy, density=dens, T=T, L=sc[0], Xbar=(sc[1], sc[2]), t=sc[3], steps=int(sc[4]),
+                    M_prev=sc[5], L_prev=sc[6])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.kfbi_thetal_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

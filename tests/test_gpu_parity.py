@@ -1,0 +1,256 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (FP64 mode): integer and index work is bit-exact (sides, crossing kinds,
+lines and arms, irregular-node lists); floating point agrees to 1e-11 relative for the
+apply (rounding order of sums and of the FFT vs scipy), and GMRES densities solved at
+tol 1e-13 agree to 1e-10 relative (the target stated for interface densities).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import kfbi as OK
+from oracle import thetal as OT
+from oracle.gmres import gmres
+
+pytestmark = pytest.mark.gpu
+
+K = pytest.importorskip("paper_2309_01068_gb300.kfbi")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_01068_gb300 import build
+
+    build.build()
+    K.load()
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def make(p, boxbc, precision=0, kappa=None):
+    kappa = p.kappa if kappa is None else kappa
+    ctx = K.Context(p.N, p.box, kappa, boxbc, precision, max_nodes=max(p.n, 64))
+    ctx.set_interface(dev(p.xy))
+    ref = OK.Kfbi(p.N, p.box, kappa, boxbc).set_interface(p.xy)
+    return ctx, ref
+
+
+# ------------------------------------------------------------------- fast solver
+@pytest.mark.parametrize("N", [16, 64, 256, 1024])
+@pytest.mark.parametrize("boxbc,kappa", [(0, 0.0), (0, 37.0), (1, 2.5)])
+def test_grid_solve(N, boxbc, kappa):
+    rng = np.random.default_rng(N + boxbc)
+    C = rng.standard_normal((N, N))
+    ctx = K.Context(N, (-1.0, 1.0, -1.0, 1.0), kappa, boxbc, 0, max_nodes=64)
+    u = ctx.grid_solve(dev(C)).cpu().numpy()
+    ref = OK.solve_grid(OK.Grid(N, (-1, 1, -1, 1)), C, kappa, boxbc)
+    assert rel(u, ref) < 1e-12
+
+
+# ------------------------------------------------------------------- geometry
+@pytest.mark.parametrize("seed,N,n", [(1, 64, 64), (2, 128, 100), (3, 128, 257), (4, 256, 128), (5, 32, 33)])
+def test_geometry_bit_exact(seed, N, n):
+    p = W.random_problem(seed, N=N, n=n)
+    ctx, ref = make(p, OK.BOX_DIRICHLET0)
+    st = ctx.stats()
+    assert st["crossings"] == len(ref.cr)
+    klf, ax = ctx.crossings()
+    klf = klf.cpu().numpy()
+    ax = ax.cpu().numpy()
+    assert np.array_equal(klf[:, 0], ref.cr.kind)
+    assert np.array_equal(klf[:, 1], ref.cr.line)
+    assert np.array_equal(klf[:, 2], ref.cr.first)
+    assert np.abs(ax[:, 0] - ref.cr.alpha).max() < 1e-12
+    assert np.abs(ax[:, 1] - ref.cr.xi).max() < 1e-12
+    assert np.array_equal(ctx.sides().cpu().numpy(), ref.cl.side)
+    ji = ctx.irregular().cpu().numpy()
+    assert np.array_equal(ji, OK.irregular_list(ref.cl))
+
+
+# ------------------------------------------------------------------- apply
+@pytest.mark.parametrize("boxbc,kappa,layer", [(0, 0.0, 1), (0, 0.0, 0), (0, 50.0, 1), (1, 30.0, 0), (1, 30.0, 1),
+                                               (2, 0.0, 1)])
+@pytest.mark.parametrize("seed,N,n", [(7, 64, 64), (8, 128, 96), (9, 128, 131)])
+def test_apply_parity(boxbc, kappa, layer, seed, N, n):
+    p = W.random_problem(seed, N=N, n=n, box=1.0 if boxbc != 2 else 1.5)
+    ctx, ref = make(p, boxbc, kappa=kappa)
+    dens = W.random_density(seed + 100, n)
+    vals, dn, g = ctx.apply(layer, dev(dens), dnormal=True, grid=True)
+    rv, rdn, ru = ref.apply(layer, dens, want_dnormal=True)
+    assert rel(vals.cpu().numpy(), rv) < 1e-11
+    assert rel(dn.cpu().numpy(), rdn) < 1e-10
+    assert rel(g.cpu().numpy(), ru) < 1e-11
+
+
+def test_double_layer_of_one_is_half():
+    p = W.random_problem(21, N=128, n=128)
+    ctx, _ = make(p, OK.BOX_DIRICHLET0)
+    vals, dn, g = ctx.apply(K.DOUBLE, dev(np.ones(p.n)), dnormal=True, grid=True)
+    side = ctx.sides().cpu().numpy()
+    assert np.abs(vals.cpu().numpy() - 0.5).max() < 1e-12
+    assert np.abs(g.cpu().numpy() - side).max() < 1e-12
+
+
+# ------------------------------------------------------------------- BIE operators and GMRES
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_bie_apply_parity(kind):
+    boxbc = {0: 0, 1: 2, 2: 1}[kind]
+    kappa = 40.0 if kind == 2 else 0.0
+    p = W.random_problem(31 + kind, N=128, n=120, box=1.0 if kind != 1 else 1.5)
+    ctx, ref = make(p, boxbc, kappa=kappa)
+    x = W.random_density(5, p.n)
+    ev = np.full(p.n, 0.3)
+    y = ctx.bie_apply(kind, dev(x), eps_v=dev(ev) if kind == 2 else None).cpu().numpy()
+    r = ref.bie_matvec(kind, x, eps_v=ev)
+    assert rel(y, r) < 1e-11
+
+
+def test_solve_interior_laplace_config_small():
+    """Ellipse 0.6 x 0.4 in [-1,1]^2, 128^2, 128 nodes, data e^x sin y (FP64)."""
+    p = W.config_small_laplace()
+    ctx, ref = make(p, OK.BOX_DIRICHLET0)
+    phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=1e-13, max_iter=300, restart=100)
+    rphi, rinfo = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), p.rhs, tol=1e-13)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-13
+    assert rel(phi.cpu().numpy(), rphi) < 1e-10
+    assert abs(info["iterations"] - rinfo["iterations"]) <= 1
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_solve_parity_hs_and_stefan(kind):
+    boxbc = 2 if kind == 1 else 1
+    kappa = 0.0 if kind == 1 else 60.0
+    p = W.random_problem(41 + kind, N=128, n=128, box=1.5 if kind == 1 else 1.0)
+    ctx, ref = make(p, boxbc, kappa=kappa)
+    ev = np.full(p.n, 0.2)
+    rhs = W.random_density(9, p.n)
+    phi, info = ctx.solve_bie(kind, dev(rhs), tol=1e-13, max_iter=300, eps_v=dev(ev) if kind == 2 else None)
+    rphi, _ = gmres(lambda v: ref.bie_matvec(kind, v, eps_v=ev), rhs, tol=1e-13)
+    assert info["status"] == 0
+    assert rel(phi.cpu().numpy(), rphi) < 1e-10
+
+
+def test_gmres_restart_and_not_converged():
+    p = W.config_small_laplace(N=64, n=64)
+    ctx, ref = make(p, OK.BOX_DIRICHLET0)
+    phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=1e-12, max_iter=200, restart=3)
+    rphi, rinfo = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), p.rhs, tol=1e-12, restart=3)
+    assert info["status"] == 0 and info["restarts"] > 0
+    assert rel(phi.cpu().numpy(), rphi) < 1e-9
+    x0 = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    _, info2 = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), density=x0, tol=1e-14, max_iter=2, restart=50)
+    assert info2["status"] == K.ERR_NOT_CONVERGED and info2["iterations"] == 2
+
+
+def test_mixed_precision_refinement():
+    """FP32 grid applies inside GMRES, FP64 residual and refinement: density within 1e-9 of FP64."""
+    p = W.config_small_laplace()
+    ctx, ref = make(p, OK.BOX_DIRICHLET0, precision=K.MIXED)
+    phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=1e-10, max_iter=300, restart=100)
+    rphi, _ = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), p.rhs, tol=1e-13)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-10
+    assert info["refinements"] >= 2
+    assert rel(phi.cpu().numpy(), rphi) < 1e-9
+
+
+def test_interp_grid_and_box_solve_neumann():
+    p = W.random_problem(51, N=128, n=96)
+    ctx, ref = make(p, OK.BOX_NEUMANN0, kappa=20.0)
+    rng = np.random.default_rng(3)
+    C = rng.standard_normal((p.N, p.N))
+    u = ctx.grid_solve(dev(C))
+    v = ctx.interp_grid(u).cpu().numpy()
+    ru = OK.solve_grid(ref.grid, C, 20.0, OK.BOX_NEUMANN0)
+    assert rel(v, ref.interp_smooth(ru)) < 1e-11
+
+
+# ------------------------------------------------------------------- full size (Hele-Shaw bubble)
+def test_hele_shaw_full_size_apply():
+    """1024^2 grid, 1024 nodes, free-space box data: the whole apply vs the oracle."""
+    p = W.config_hele_shaw()
+    ctx, ref = make(p, OK.BOX_FREESPACE_DL)
+    dens = W.random_density(77, p.n, modes=20)
+    vals, dn, _ = ctx.apply(K.DOUBLE, dev(dens), dnormal=True)
+    rv, rdn, _ = ref.apply(OK.LAYER_DOUBLE, dens, want_dnormal=True)
+    assert ctx.stats()["crossings"] == len(ref.cr)
+    assert np.array_equal(ctx.sides().cpu().numpy(), ref.cl.side)
+    assert rel(vals.cpu().numpy(), rv) < 1e-11
+    assert rel(dn.cpu().numpy(), rdn) < 1e-9
+
+
+# ------------------------------------------------------------------- time steps
+def test_hele_shaw_step_parity():
+    p = W.config_hele_shaw(N=256, n=128, box=3.0)
+    ctx = K.Context(p.N, p.box, 0.0, K.BOX_FREESPACE_DL, K.FP64, max_nodes=p.n)
+    alpha = 2 * math.pi * np.arange(p.n) / p.n
+    eta = p.theta - alpha
+    xbar = p.xy.mean(0)
+    st = K.ThetaL(ctx, dev(eta), p.L, xbar, K.STEP_HELE_SHAW, tol=1e-12, sigma=1e-2, J=1.0)
+    ref = OK.Kfbi(p.N, p.box, 0.0, OK.BOX_FREESPACE_DL)
+    rst = OT.state_from_nodes(p.xy, p.theta, p.L)
+    for _ in range(3):
+        st.step(1e-3)
+        OT.hs_step(ref, rst, 1e-3, 1e-2, 1.0, tol=1e-12)
+    out = st.read()
+    assert abs(out["L"] - rst.L) < 1e-10 * rst.L
+    assert np.abs(out["eta"].cpu().numpy() - rst.eta).max() < 1e-9
+    assert np.abs(out["Xbar"] - rst.Xbar).max() < 1e-10
+    assert rel(out["density"].cpu().numpy(), rst.density) < 1e-8
+
+
+def test_stefan_step_parity():
+    p = W.config_stefan(N=128, n=128, box=0.5, dt=1e-3)
+    e = p.extra
+    ctx = K.Context(p.N, p.box, p.kappa, K.BOX_NEUMANN0, K.FP64, max_nodes=p.n)
+    alpha = 2 * math.pi * np.arange(p.n) / p.n
+    st = K.ThetaL(ctx, dev(p.theta - alpha), p.L, p.xy.mean(0), K.STEP_STEFAN, tol=1e-12, St=e["St"],
+                  eps_c=e["eps_c"], eps_aniso=e["eps_aniso"], eps_v=e["eps_v"], fold=e["fold"])
+    ref = OK.Kfbi(p.N, p.box, p.kappa, OK.BOX_NEUMANN0)
+    rst = OT.state_from_nodes(p.xy, p.theta, p.L)
+    for _ in range(2):
+        st.step(e["dt"])
+        OT.stefan_step(ref, rst, e["dt"], e["St"], e["eps_c"], e["eps_aniso"], e["fold"], e["eps_v"], tol=1e-12)
+    out = st.read()
+    assert abs(out["L"] - rst.L) < 1e-10 * rst.L
+    assert np.abs(out["eta"].cpu().numpy() - rst.eta).max() < 1e-9
+    assert rel(out["T"].cpu().numpy(), rst.T) < 1e-9
+
+
+# ------------------------------------------------------------------- errors
+def test_errors():
+    with pytest.raises(K.KfbiError) as e:
+        K.Context(48, (-1, 1, -1, 1))
+    assert e.value.status == K.ERR_ARG
+    with pytest.raises(K.KfbiError) as e:
+        K.Context(64, (-1, 1, -1, 1), 0.0, K.BOX_NEUMANN0)
+    assert e.value.status == K.ERR_SINGULAR
+    ctx = K.Context(32, (-1, 1, -1, 1), max_nodes=64)
+    with pytest.raises(K.KfbiError) as e:
+        ctx.apply(K.DOUBLE, torch.ones(64, dtype=torch.float64, device="cuda"))
+    assert e.value.status == K.ERR_STATE
+    t = 2 * math.pi * np.arange(64) / 64
+    with pytest.raises(K.KfbiError) as e:
+        ctx.set_interface(dev(np.stack([0.95 * np.cos(t), 0.5 * np.sin(t)], -1)))
+    assert e.value.status == K.ERR_OUTSIDE_BOX
+    nodes = W.equal_arclength(W.polar(0.5, [(11, 0.45, 0.0)]), 256)
+    ctx2 = K.Context(16, (-1, 1, -1, 1), max_nodes=256)
+    with pytest.raises(K.KfbiError) as e:
+        ctx2.set_interface(dev(nodes["xy"]))
+    assert e.value.status in (K.ERR_UNDERRESOLVED, K.ERR_OUTSIDE_BOX)
+    with pytest.raises(K.KfbiError) as e:
+        ctx.set_interface(dev(np.zeros((65, 2))))
+    assert e.value.status == K.ERR_CAPACITY
