@@ -232,23 +232,37 @@ void kfbi_thetal_destroy(kfbi_thetal* st);
 kfbi_status kfbi_step(kfbi_ctx* ctx, kfbi_thetal* st, double dt, kfbi_solve_info* info);
 
 /*
- * Read-back of the theta-L state (device outputs): eta [n], xy [n][2] of the last solved
- * curve, density [n], T [N][N] (Stefan; NULL to skip) and host scalars [8] =
- * (L, Xbar_x, Xbar_y, t, steps, M_prev, L_prev, 0).
+ * Checkpoint and resume of the theta-L state. Device buffers, NULL skips an item:
+ *   eta [n], xy [n][2] nodes of the last solved curve (read only), density [n],
+ *   nhat [(n/2+1)][2] the Adams-Bashforth history of N-hat (complex), T and T_prev
+ *   [N][N] (Stefan only). `scalars` is a HOST array of KFBI_THETAL_SCALARS doubles:
+ *   (L, Xbar_x, Xbar_y, t, steps, M_prev, Q_prev_x, Q_prev_y, L_prev, then work slots).
+ * Writing back what was read restores the state exactly. kfbi_thetal_read synchronises
+ * the stream when `scalars` is given. Errors: ARG, CUDA.
  */
-kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* density, double* T,
-                             double* scalars);
+#define KFBI_THETAL_SCALARS 16
+kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* density, double* nhat, double* T,
+                             double* T_prev, double* scalars);
+kfbi_status kfbi_thetal_write(kfbi_thetal* st, const double* eta, const double* density, const double* nhat,
+                              const double* T, const double* T_prev, const double* scalars);
 
 /* Human-readable name of a status code (static storage). */
 const char* kfbi_status_string(kfbi_status s);
 
 /*
- * Per-kernel device timing for roofline reports: when enabled, the library records CUDA
- * events around the column-transform kernel of the fast solve on the context's stream.
- * kfbi_timing_read returns the summed milliseconds and the launch count since enable.
+ * Per-kernel device timing for roofline reports. When enabled, the library records a pair
+ * of CUDA events on the context's stream around every launch of the column kernel of the
+ * fast solve (the dominant grid kernel), without synchronising. kfbi_timing_read
+ * synchronises the stream and returns the summed milliseconds and launch counts since
+ * enable, separately for the float64 and float32 instantiations (host outputs; NULL skips).
+ * At most 8192 launches are recorded per enable.
  */
 kfbi_status kfbi_timing_enable(kfbi_ctx* ctx, int enable);
-kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* total_ms, int* launches);
+kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64, double* ms_fp32,
+                             int* launches_fp32);
+
+/* Number of kernels this context has launched since creation (host output). */
+kfbi_status kfbi_launch_count(kfbi_ctx* ctx, long long* count);
 
 #ifdef __cplusplus
 }

@@ -90,8 +90,12 @@ static void free_all(kfbi_ctx* c) {
     if (p) cudaFree(p);
   if (c->host_counts) cudaFreeHost(c->host_counts);
   if (c->host_gctl) cudaFreeHost(c->host_gctl);
-  if (c->ev0) cudaEventDestroy(c->ev0);
-  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->tev) {
+    for (int i = 0; i < 2 * TIMING_CAP; ++i)
+      if (c->tev[i]) cudaEventDestroy(c->tev[i]);
+    delete[] c->tev;
+  }
+  delete[] c->tprec;
 }
 
 static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, double ymax, double kappa, int boxbc,
@@ -157,9 +161,8 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_TRY(cudaMemset(c->vcount, 0, NN * sizeof(int)));
   KFBI_TRY(cudaMemset(c->probe_mark, 0, NN * sizeof(int)));
   KFBI_TRY(cudaMemset(c->gctl, 0, sizeof(GmresCtl)));
-  KFBI_TRY(cudaEventCreate(&c->ev0));
-  KFBI_TRY(cudaEventCreate(&c->ev1));
   KFBI_CHECK(ensure_cross_capacity(c, 4096));
+  launched(c, 1);
   k_init_tables<<<cdiv(4L * N, 256), 256>>>(N, c->h, boxbc == KFBI_BOX_NEUMANN0, c->sintab, c->sintab_f, c->lam,
                                            c->lam_f, c->twN, c->twN_f);
   KFBI_TRY(cudaGetLastError());
@@ -294,6 +297,7 @@ kfbi_status kfbi_copy_crossings(kfbi_ctx* c, int cap, int* kind_line_first, doub
   if (!ctx_ok(c) || kind_line_first == nullptr || alpha_xi == nullptr || cap < 0) return KFBI_ERR_ARG;
   if (!c->have_iface) return KFBI_ERR_STATE;
   int cnt = cap < c->n_cross ? cap : c->n_cross;
+  if (cnt > 0) launched(c, 1);
   if (cnt > 0)
     k_pack_crossings<<<cdiv(cnt, 256), 256, 0, c->stream>>>(cnt, c->cr_kind, c->cr_line, c->cr_first, c->cr_alpha,
                                                             c->cr_xi, kind_line_first, alpha_xi);
@@ -312,6 +316,7 @@ kfbi_status kfbi_copy_irregular(kfbi_ctx* c, int cap, int* ji) {
   if (!ctx_ok(c) || ji == nullptr || cap < 0) return KFBI_ERR_ARG;
   if (!c->have_iface) return KFBI_ERR_STATE;
   int cnt = cap < c->n_irr ? cap : c->n_irr;
+  if (cnt > 0) launched(c, 1);
   if (cnt > 0) k_pack_irregular<<<cdiv(cnt, 256), 256, 0, c->stream>>>(cnt, c->irr, ji);
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -335,16 +340,39 @@ const char* kfbi_status_string(kfbi_status s) {
 
 kfbi_status kfbi_timing_enable(kfbi_ctx* c, int enable) {
   if (!ctx_ok(c)) return KFBI_ERR_ARG;
+  if (enable && c->tev == nullptr) {
+    c->tev = new cudaEvent_t[2 * TIMING_CAP]();
+    c->tprec = new uint8_t[TIMING_CAP]();
+    for (int i = 0; i < 2 * TIMING_CAP; ++i) KFBI_TRY(cudaEventCreate(&c->tev[i]));
+  }
   c->timing = enable != 0;
-  c->timing_ms = 0.0;
-  c->timing_launches = 0;
+  c->timing_used = 0;
   return KFBI_OK;
 }
 
-kfbi_status kfbi_timing_read(kfbi_ctx* c, double* total_ms, int* launches) {
+kfbi_status kfbi_timing_read(kfbi_ctx* c, double* ms_fp64, int* launches_fp64, double* ms_fp32, int* launches_fp32) {
   if (!ctx_ok(c)) return KFBI_ERR_ARG;
-  if (total_ms) *total_ms = c->timing_ms;
-  if (launches) *launches = c->timing_launches;
+  double ms[2] = {0.0, 0.0};
+  int cnt[2] = {0, 0};
+  if (c->timing_used > 0) {
+    KFBI_TRY(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < c->timing_used; ++i) {
+      float t = 0.f;
+      KFBI_TRY(cudaEventElapsedTime(&t, c->tev[2 * i], c->tev[2 * i + 1]));
+      ms[c->tprec[i]] += t;
+      cnt[c->tprec[i]] += 1;
+    }
+  }
+  if (ms_fp64) *ms_fp64 = ms[0];
+  if (launches_fp64) *launches_fp64 = cnt[0];
+  if (ms_fp32) *ms_fp32 = ms[1];
+  if (launches_fp32) *launches_fp32 = cnt[1];
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_launch_count(kfbi_ctx* c, long long* count) {
+  if (!ctx_ok(c) || count == nullptr) return KFBI_ERR_ARG;
+  *count = c->launches;
   return KFBI_OK;
 }
 

@@ -534,16 +534,15 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
   KFBI_TRY(cudaFuncSetAttribute(k_col_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int threads = 256;
   while (CP * (N / 2 + 1) > 8 * threads && threads < 1024) threads *= 2;
-  if (c->timing) KFBI_TRY(cudaEventRecord(c->ev0, c->stream));
+  const bool rec = c->timing && c->timing_used < TIMING_CAP;
+  if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
   k_col_solve<T><<<N / (2 * CP), threads, smem, c->stream>>>(N, c->logN, CP, c->boxbc == KFBI_BOX_NEUMANN0, tw,
                                                             tab, lam, c->kappa, spec, skip);
-  if (c->timing) {
-    KFBI_TRY(cudaEventRecord(c->ev1, c->stream));
-    KFBI_TRY(cudaEventSynchronize(c->ev1));
-    float ms = 0.f;
-    KFBI_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-    c->timing_ms += ms;
-    c->timing_launches += 1;
+  launched(c, 1);
+  if (rec) {
+    KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used + 1], c->stream));
+    c->tprec[c->timing_used] = sizeof(T) == 4 ? 1 : 0;
+    c->timing_used += 1;
   }
   return KFBI_OK;
 }
@@ -563,6 +562,7 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   T* pval = (T*)c->probe_val;
   const int nk = n / 2 + 1;
   bool want_int = bie_kind == KFBI_BIE_HS_EXTERIOR_MDL;
+  launched(c, 5 + (c->n_irr > 0) + (c->boxbc == KFBI_BOX_FREESPACE_DL) + (grid != nullptr));  // col solve counts itself
   k_dens_coef<T><<<cdiv((long)nk * 32, 256), 256, 0, s>>>(density, n, (const double2*)c->twn, c->stencil, coef,
                                                           want_int ? c->dint : nullptr, skip);
   k_target_jumps<T><<<cdiv((long)ntg * 32, 256), 256, 0, s>>>(coef, n, ntg, c->tgeo, layer, c->kappa, J, skip);
@@ -615,6 +615,7 @@ static kfbi_status grid_solve_t(kfbi_ctx* c, const double* rhs, double* u) {
   size_t sm3 = sizeof(V2<T>) * N;
   KFBI_TRY(cudaFuncSetAttribute(k_row_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
   k_row_dense<T><<<N / 2, 256, sm3, s>>>(N, c->logN, dct, 0, tw, tab, rhs, spec, nullptr);
+  launched(c, 2);
   KFBI_CHECK(launch_col_solve<T>(c, spec, c->zero_flag));
   k_row_dense<T><<<N / 2, 256, sm3, s>>>(N, c->logN, dct, 1, tw, tab, nullptr, spec, u);
   KFBI_TRY(cudaGetLastError());
@@ -635,6 +636,7 @@ __global__ void k_gather_probes(int N, const int* prow_ptr, const int* probe_i, 
 kfbi_status interp_grid_enqueue(kfbi_ctx* c, const double* grid, double* values) {
   cudaStream_t s = c->stream;
   double* pval = c->probe_val;
+  launched(c, 2);
   k_gather_probes<<<c->N, 128, 0, s>>>(c->N, c->prow_ptr, c->probe_i, grid, pval);
   k_interp<double><<<cdiv(c->n, 128), 128, 0, s>>>(c->n, c->stencil, pval, nullptr, nullptr, nullptr, 0.0, 1.0, 0.0,
                                                     nullptr, values, nullptr, c->zero_flag);

@@ -481,6 +481,7 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   KFBI_TRY(cudaMemsetAsync(c->probe_mark, 0, NN * sizeof(int), s));
 
   k_twiddles_n<<<cdiv(n, 256), 256, 0, s>>>(n, (double2*)c->twn);
+  launched(c, 5);
   k_dft_real<<<cdiv((long)2 * nk * 32, 256), 256, 0, s>>>(c->xy, 2, 2, n, (const double2*)c->twn,
                                                           (double2*)c->icoef);
   double mg = BOX_MARGIN * h;
@@ -497,6 +498,7 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   KFBI_CHECK(ensure_cross_capacity(c, ncr));
   c->n_cross = ncr;
 
+  launched(c, 4 + (ncr > 0 ? 2 : 0));
   k_emit_pairs<<<cdiv(2 * M, 256), 256, 0, s>>>(c->fine, M, c->xmin, c->ymin, h, N, c->seg_off, c->cr_kind,
                                                 c->cr_line, c->cr_seg);
   if (ncr > 0) {
@@ -519,6 +521,7 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   if (nirr > c->cap_irr) return KFBI_ERR_CAPACITY;
   c->n_irr = nirr;
 
+  launched(c, 7);
   k_irr_emit<<<wblocks, 256, 0, s>>>(N, c->xmin, c->ymin, h, c->side, c->hcount, c->vcount, c->hid, c->vid,
                                      c->cr_xi, c->row_ptr, c->irr);
   k_target_geo<<<cdiv((long)(ncr + n) * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, ncr, c->cr_alpha,

@@ -317,6 +317,7 @@ static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, c
   int layer = kind == KFBI_BIE_STEFAN_SL ? KFBI_SINGLE : KFBI_DOUBLE;
   KFBI_CHECK(apply_enqueue(c, layer, fp32, c->gin, c->gw, nullptr, nullptr, kind, eps_v, done));
   const int ldv = c->max_nodes;
+  launched(c, 5);
   k_gm_dots<<<GM_BLOCKS, GM_THREADS, 0, s>>>(c->gctl, c->gV, ldv, c->gw, b, c->gr, n, c->gpart, 0);
   k_gm_update<<<GM_BLOCKS, GM_THREADS, 0, s>>>(c->gctl, c->gV, ldv, c->gw, n, c->gpart, 0);
   k_gm_dots<<<GM_BLOCKS, GM_THREADS, 0, s>>>(c->gctl, c->gV, ldv, c->gw, b, c->gr, n, c->gpart, 1);
@@ -336,6 +337,7 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   int m = restart < n ? restart : n;
   if (m > MAX_RESTART) m = MAX_RESTART;
   if (m < 1) m = 1;
+  launched(c, 2);
   k_gm_init<<<1, 32, 0, s>>>(c->gctl, tol, max_iter, m, trust ? 1 : 0);
   k_gm_start<<<1, 1024, 0, s>>>(b, x, c->gin, c->gV, n, c->gctl, zero_guess ? 1 : 0);
   const int cap = 2 * max_iter + 2 * (max_iter / m) + 8;
@@ -386,6 +388,7 @@ kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const dou
       int layer = kind == KFBI_BIE_STEFAN_SL ? KFBI_SINGLE : KFBI_DOUBLE;
       KFBI_CHECK(apply_enqueue(c, layer, false, x, y, nullptr, nullptr, kind, eps_v, nullptr));
       k_resid<<<1, 1024, 0, s>>>(rhs, y, r, n, c->dint + 1);
+      launched(c, 1);
       KFBI_TRY(cudaMemcpyAsync(hres, c->dint + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       KFBI_TRY(cudaStreamSynchronize(s));
       sweeps += 1;
@@ -404,6 +407,7 @@ kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const dou
       total_its += its;
       total_cyc += cyc;
       k_axpy_zero<<<cdiv(n, 256), 256, 0, s>>>(x, d, n);
+      launched(c, 1);
     }
     out.iterations = total_its;
     out.restarts = total_cyc > sweeps - 1 ? total_cyc - (sweeps - 1) : 0;

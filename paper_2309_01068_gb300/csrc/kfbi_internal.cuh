@@ -35,6 +35,7 @@ constexpr int NEWTON_MAXIT = 60;
 constexpr double NEWTON_TOL = 1e-15;
 constexpr double BOX_MARGIN = 3.0;   // interface must stay 3h inside the box
 constexpr int MAX_RESTART = 200;
+constexpr int TIMING_CAP = 8192;
 
 // device error flags (bitmask in Iface::flags)
 enum : int { FLAG_OUTSIDE = 1, FLAG_UNDERRES = 2, FLAG_CAPACITY = 4 };
@@ -164,11 +165,12 @@ struct kfbi_ctx {
   double* gr = nullptr;         // outer residual / correction (refinement) [max_nodes]
   int* zero_flag = nullptr;     // device int 0
 
-  // timing
+  // timing of the column kernel: event pairs recorded without synchronising
   bool timing = false;
-  double timing_ms = 0.0;
-  int timing_launches = 0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int timing_used = 0;
+  cudaEvent_t* tev = nullptr;   // [2 * TIMING_CAP]
+  uint8_t* tprec = nullptr;     // [TIMING_CAP] 1 = float32 launch
+  long long launches = 0;       // kernels launched by this context
 };
 
 namespace kfbi {
@@ -212,6 +214,8 @@ inline int ilog2(int v) {
 }
 
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+inline void launched(kfbi_ctx* c, int k) { c->launches += k; }
 
 // host-side helpers implemented in the .cu files
 kfbi_status ensure_cross_capacity(kfbi_ctx* c, int n_cross);

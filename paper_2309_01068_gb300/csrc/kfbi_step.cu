@@ -327,6 +327,7 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
   double2* coef = (double2*)st->coef;
   const kfbi_thetal_params& P = st->prm;
   const int tb = cdiv(n, 256);
+  launched(c, 22);
   // 1. reconstruct the curve from (eta, L, Xbar)
   k_st_xa<<<tb, 256, 0, s>>>(st->eta, n, st->scal, st->work);
   k_st_dft<<<wb(2L * nk), 256, 0, s>>>(st->work, 2, 2, n, tw, coef);
@@ -343,6 +344,7 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
   kfbi_status sst;
   const double* ratio = nullptr;
   if (P.kind == KFBI_STEP_HELE_SHAW) {
+    launched(c, 2);
     k_st_hs_rhs<<<tb, 256, 0, s>>>(st->xy, st->th_a, n, st->scal, P.sigma, P.J, st->rhs);
     sst = solve_bie_impl(c, KFBI_BIE_HS_EXTERIOR_MDL, nullptr, st->rhs, P.tol, P.max_iter, P.restart, st->density,
                          &si);
@@ -357,6 +359,7 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
     KFBI_TRY(cudaMemcpyAsync(&steps, st->scal + SC_STEPS, sizeof(double), cudaMemcpyDeviceToHost, s));
     KFBI_TRY(cudaStreamSynchronize(s));
     if (steps == 0.0) k_st_T0<<<gb, 256, 0, s>>>(c->side, NN, P.St, st->T, st->Tprev);
+    launched(c, (steps == 0.0) + 3);
     k_st_bdf_rhs<<<gb, 256, 0, s>>>(st->T, st->Tprev, NN, dt, st->Tw);
     KFBI_CHECK(grid_solve_enqueue(c, st->Tw, st->Tw));  // T1 in Tw
     KFBI_CHECK(interp_grid_enqueue(c, st->Tw, st->dn));  // T1 at the nodes
@@ -498,26 +501,44 @@ kfbi_status kfbi_step(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve_info* 
   return thetal_step_impl(c, st, dt, info);
 }
 
-kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* density, double* T, double* scalars) {
+kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* density, double* nhat, double* T,
+                             double* T_prev, double* scalars) {
   if (st == nullptr) return KFBI_ERR_ARG;
   cudaStream_t s = st->ctx->stream;
   const int n = st->n;
+  const size_t NN = (size_t)st->ctx->N * st->ctx->N;
+  const size_t nk = (size_t)(n / 2 + 1);
   if (eta) KFBI_TRY(cudaMemcpyAsync(eta, st->eta, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (xy) KFBI_TRY(cudaMemcpyAsync(xy, st->xy, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (density) KFBI_TRY(cudaMemcpyAsync(density, st->density, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  if (T && st->T)
-    KFBI_TRY(cudaMemcpyAsync(T, st->T, (size_t)st->ctx->N * st->ctx->N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (nhat) KFBI_TRY(cudaMemcpyAsync(nhat, st->Nprev_h, 2 * nk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (T && st->T) KFBI_TRY(cudaMemcpyAsync(T, st->T, NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (T_prev && st->Tprev) KFBI_TRY(cudaMemcpyAsync(T_prev, st->Tprev, NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (scalars) {
     KFBI_TRY(cudaMemcpyAsync(st->host_scal, st->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
     KFBI_TRY(cudaStreamSynchronize(s));
-    scalars[0] = st->host_scal[SC_L];
-    scalars[1] = st->host_scal[SC_XB0];
-    scalars[2] = st->host_scal[SC_XB1];
-    scalars[3] = st->host_scal[SC_T];
-    scalars[4] = st->host_scal[SC_STEPS];
-    scalars[5] = st->host_scal[SC_MPREV];
-    scalars[6] = st->host_scal[SC_LPREV];
-    scalars[7] = 0.0;
+    for (int i = 0; i < SC_COUNT; ++i) scalars[i] = st->host_scal[i];
+  }
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_thetal_write(kfbi_thetal* st, const double* eta, const double* density, const double* nhat,
+                              const double* T, const double* T_prev, const double* scalars) {
+  if (st == nullptr) return KFBI_ERR_ARG;
+  cudaStream_t s = st->ctx->stream;
+  const int n = st->n;
+  const size_t NN = (size_t)st->ctx->N * st->ctx->N;
+  const size_t nk = (size_t)(n / 2 + 1);
+  if (eta) KFBI_TRY(cudaMemcpyAsync(st->eta, eta, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (density) KFBI_TRY(cudaMemcpyAsync(st->density, density, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (nhat) KFBI_TRY(cudaMemcpyAsync(st->Nprev_h, nhat, 2 * nk * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (T && st->T) KFBI_TRY(cudaMemcpyAsync(st->T, T, NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (T_prev && st->Tprev) KFBI_TRY(cudaMemcpyAsync(st->Tprev, T_prev, NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (scalars) {
+    KFBI_TRY(cudaStreamSynchronize(s));
+    for (int i = 0; i < SC_COUNT; ++i) st->host_scal[i] = scalars[i];
+    KFBI_TRY(cudaMemcpyAsync(st->scal, st->host_scal, SC_COUNT * sizeof(double), cudaMemcpyHostToDevice, s));
+    KFBI_TRY(cudaStreamSynchronize(s));
   }
   return KFBI_OK;
 }

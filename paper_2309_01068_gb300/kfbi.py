@@ -70,10 +70,12 @@ _SIGNATURES = {
                                 ctypes.POINTER(_P)]),
     "kfbi_thetal_destroy": (None, [_P]),
     "kfbi_step": (_I, [_P, _P, _D, ctypes.POINTER(SolveInfo)]),
-    "kfbi_thetal_read": (_I, [_P, _P, _P, _P, _P, ctypes.POINTER(_D)]),
+    "kfbi_thetal_read": (_I, [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(_D)]),
+    "kfbi_thetal_write": (_I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(_D)]),
     "kfbi_status_string": (ctypes.c_char_p, [_I]),
     "kfbi_timing_enable": (_I, [_P, _I]),
-    "kfbi_timing_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    "kfbi_timing_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    "kfbi_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
 }
 
 
@@ -175,11 +177,12 @@ class Context:
     def apply(self, layer, density, dnormal=False, grid=False):
         self._sync_stream()
         n = self.n
-        vals = torch.empty(n, dtype=torch.float64, device=density.device)
+        vals = torch.empty(max(n, 1), dtype=torch.float64, device=density.device)[:n]
         dn = torch.empty(n, dtype=torch.float64, device=density.device) if dnormal else None
         g = torch.empty((self.N, self.N), dtype=torch.float64, device=density.device) if grid else None
-        _check(self.lib.kfbi_apply_layer_potential(self.handle, layer, _f64(density, (n,)), _ptr(vals), _ptr(dn),
-                                                   _ptr(g)), "kfbi_apply_layer_potential")
+        dptr = _f64(density, (n,)) if n > 0 else _ptr(density)  # no interface yet: the library reports it
+        _check(self.lib.kfbi_apply_layer_potential(self.handle, layer, dptr, _ptr(vals), _ptr(dn), _ptr(g)),
+               "kfbi_apply_layer_potential")
         return vals, dn, g
 
     def apply_into(self, layer, density, values, dnormal=None, grid=None):
@@ -243,12 +246,20 @@ class Context:
         return ji[:cnt]
 
     def timing(self, enable=None):
+        """timing(True/False) switches column-kernel event timing; timing() returns
+        dict(fp64_ms, fp64_launches, fp32_ms, fp32_launches)."""
         if enable is not None:
             _check(self.lib.kfbi_timing_enable(self.handle, 1 if enable else 0), "kfbi_timing_enable")
             return None
-        ms, cnt = ctypes.c_double(), ctypes.c_int()
-        _check(self.lib.kfbi_timing_read(self.handle, ctypes.byref(ms), ctypes.byref(cnt)), "kfbi_timing_read")
-        return ms.value, cnt.value
+        a, b, c, d = ctypes.c_double(), ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+        _check(self.lib.kfbi_timing_read(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                         ctypes.byref(d)), "kfbi_timing_read")
+        return dict(fp64_ms=a.value, fp64_launches=b.value, fp32_ms=c.value, fp32_launches=d.value)
+
+    def launch_count(self):
+        v = ctypes.c_longlong()
+        _check(self.lib.kfbi_launch_count(self.handle, ctypes.byref(v)), "kfbi_launch_count")
+        return v.value
 
 
 class ThetaL:
@@ -275,19 +286,33 @@ class ThetaL:
                allow=(ERR_NOT_CONVERGED,))
         return info.as_dict()
 
-    def read(self):
+    SCALARS = 16
+
+    def read(self, T=True):
+        """State as device tensors plus the host scalars (checkpoint)."""
         self.ctx._sync_stream()
         n, N = self.n, self.ctx.N
         eta = torch.empty(n, dtype=torch.float64, device="cuda")
         xy = torch.empty((n, 2), dtype=torch.float64, device="cuda")
         dens = torch.empty(n, dtype=torch.float64, device="cuda")
-        T = torch.empty((N, N), dtype=torch.float64, device="cuda")
-        sc = (ctypes.c_double * 8)()
-        _check(self.lib.kfbi_thetal_read(self.handle, _ptr(eta), _ptr(xy), _ptr(dens), _ptr(T), sc),
-               "kfbi_thetal_read")
-        torch.cuda.synchronize()
-        return dict(eta=eta, xy=xy, density=dens, T=T, L=sc[0], Xbar=(sc[1], sc[2]), t=sc[3], steps=int(sc[4]),
-                    M_prev=sc[5], L_prev=sc[6])
+        nhat = torch.empty((n // 2 + 1, 2), dtype=torch.float64, device="cuda")
+        Tg = torch.empty((N, N), dtype=torch.float64, device="cuda") if T else None
+        Tp = torch.empty((N, N), dtype=torch.float64, device="cuda") if T else None
+        sc = (ctypes.c_double * self.SCALARS)()
+        _check(self.lib.kfbi_thetal_read(self.handle, _ptr(eta), _ptr(xy), _ptr(dens), _ptr(nhat), _ptr(Tg), _ptr(Tp),
+                                         sc), "kfbi_thetal_read")
+        torch.cuda.current_stream().synchronize()
+        return dict(eta=eta, xy=xy, density=dens, nhat=nhat, T=Tg, T_prev=Tp, scalars=list(sc), L=sc[0],
+                    Xbar=(sc[1], sc[2]), t=sc[3], steps=int(sc[4]))
+
+    def write(self, eta=None, density=None, nhat=None, T=None, T_prev=None, scalars=None):
+        """Restore (part of) the state; arguments are device tensors and a host list."""
+        self.ctx._sync_stream()
+        sc = None
+        if scalars is not None:
+            sc = (ctypes.c_double * self.SCALARS)(*[float(v) for v in scalars])
+        _check(self.lib.kfbi_thetal_write(self.handle, _ptr(eta), _ptr(density), _ptr(nhat), _ptr(T), _ptr(T_prev),
+                                          sc), "kfbi_thetal_write")
 
     def close(self):
         if getattr(self, "handle", None):
