@@ -305,6 +305,8 @@ def main():
         total_s = float(tt.item())
     iters = [i["iterations"] for i in infos]
     value = world * args.steps / total_s
+    print(f"[bench] mixed: {1e3 * total_s / args.steps:.3f} ms/step, GMRES its {np.mean(iters):.1f}, "
+          f"col kernel {tim}", file=sys.stderr)
     mixed_applies = time_applies(torch, K, ctx)
 
     # ---- end to end through the public API with host buffers

@@ -227,9 +227,10 @@ kfbi_status kfbi_set_interface(kfbi_ctx* c, int n, const double* xy) {
 
 kfbi_status kfbi_apply_layer_potential(kfbi_ctx* c, int layer, const double* density, double* values,
                                        double* dnormal, double* grid) {
-  if (!ctx_ok(c) || density == nullptr || values == nullptr) return KFBI_ERR_ARG;
-  if (layer != KFBI_SINGLE && layer != KFBI_DOUBLE) return KFBI_ERR_ARG;
+  if (!ctx_ok(c)) return KFBI_ERR_ARG;
   if (!c->have_iface) return KFBI_ERR_STATE;
+  if (density == nullptr || values == nullptr) return KFBI_ERR_ARG;
+  if (layer != KFBI_SINGLE && layer != KFBI_DOUBLE) return KFBI_ERR_ARG;
   if (c->boxbc == KFBI_BOX_FREESPACE_DL && layer != KFBI_DOUBLE) return KFBI_ERR_ARG;
   return apply_enqueue(c, layer, c->precision == KFBI_MIXED, density, values, dnormal, grid, -1, nullptr, nullptr);
 }

@@ -284,6 +284,7 @@ class ThetaL:
         info = SolveInfo()
         _check(self.lib.kfbi_step(self.ctx.handle, self.handle, float(dt), ctypes.byref(info)), "kfbi_step",
                allow=(ERR_NOT_CONVERGED,))
+        self.ctx.n = self.n  # the step set the context's interface
         return info.as_dict()
 
     SCALARS = 16
