@@ -250,6 +250,28 @@ kfbi_status kfbi_thetal_write(kfbi_thetal* st, const double* eta, const double* 
 const char* kfbi_status_string(kfbi_status s);
 
 /*
+ * kfbi_grid_solve_noalloc -- the same box solve as kfbi_grid_solve, (Delta_h - kappa) u = rhs
+ * with a Dirichlet-0 (DST-II) or Neumann-0 (DCT-II) box, for callers that cannot allocate
+ * device memory: an application that hands all device memory to its own pool at start-up,
+ * or a loop with a fixed latency budget that must not call cudaMalloc (which can
+ * synchronise the device and take unbounded time). No context is needed; this entry point
+ * makes no allocation of any kind (no cudaMalloc, cudaFree or allocating library routine).
+ * The paper has no counterpart: it is an interface convenience of this library.
+ *   N      cells per side, a power of two in [16, 512] (larger N: KFBI_ERR_CAPACITY)
+ *   h      cell width (> 0);  kappa  c^2 >= 0;  boxbc  KFBI_BOX_* (FREESPACE_DL solves as
+ *          DIRICHLET0: the plain solve has no interface data)
+ *   rhs, u device [N][N] float64 (may alias);  stream  cudaStream_t as void*
+ * Scratch: one static device array of about 2.1 MB in libkfbi, which every GPU that loads
+ * the library holds until the process exits. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture. All calls share the array and each call rewrites it
+ * completely, so calls that overlap on the GPU (different streams or host threads) race:
+ * serialise them. Asynchronous. Errors: ARG, CAPACITY, SINGULAR, CUDA.
+ */
+kfbi_status kfbi_grid_solve_noalloc(int N, double h, double kappa, int boxbc, const double* rhs, double* u,
+                                    void* stream);
+
+/*
  * Per-kernel device timing for roofline reports. When enabled, the library records a pair
  * of CUDA events on the context's stream around every launch of the column kernel of the
  * fast solve (the dominant grid kernel), without synchronising. kfbi_timing_read

@@ -4,6 +4,7 @@
 // grid arithmetic type T (double for KFBI_FP64, float for the inner applies of
 // KFBI_MIXED); interface inputs and outputs stay float64.
 #include <cmath>
+#include <mutex>
 
 #include "kfbi_internal.cuh"
 
@@ -644,4 +645,94 @@ kfbi_status interp_grid_enqueue(kfbi_ctx* c, const double* grid, double* values)
   return KFBI_OK;
 }
 
+// --------------------------------------------------------------------------- allocation-free solve
+// kfbi_grid_solve_noalloc: the plain box solve of kfbi_grid_solve for callers that cannot
+// allocate device memory (see include/kfbi.h). Its scratch lives in one file-scope device
+// array: one slot holding the column kernel's skip flag (cleared by every call before the
+// kernel reads it), then the spectral grid (N^2), the sine table (4N), the eigenvalues (N) and
+// the FFT twiddles (N). Every call rewrites all of it before reading it. The array is shared
+// by every call in the process.
+constexpr int NOALLOC_MAX_N = 512;
+constexpr size_t NOALLOC_HEAD = 32;  // doubles reserved for flags, keeps the grid 256-byte aligned
+constexpr size_t NOALLOC_DOUBLES = NOALLOC_HEAD + (size_t)NOALLOC_MAX_N * NOALLOC_MAX_N + 6 * (size_t)NOALLOC_MAX_N;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+__global__ void k_noalloc_tables(int N, double h, int neumann, double* tab, double* lam, double* tw, int* flag) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m == 0) *flag = 0;
+  if (m < 4 * N) tab[m] = sinpi((double)m / (2.0 * N));
+  if (m < N) {
+    double sk = sinpi(((double)m + (neumann ? 0.0 : 1.0)) / (2.0 * N));
+    lam[m] = -4.0 * sk * sk / (h * h);
+  }
+  if (m < N / 2) {
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)N, &sn, &cs);
+    tw[2 * m] = cs;
+    tw[2 * m + 1] = -sn;
+  }
+}
+
+// device address of the scratch array, looked up once per device (host code may not use the
+// array's name as a device pointer)
+static double* noalloc_scratch(kfbi_status* st) {
+  static std::mutex mu;
+  static double* addr[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    *st = KFBI_ERR_CUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (addr[dev] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      note_cuda_error(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+      *st = KFBI_ERR_CUDA;
+      return nullptr;
+    }
+    addr[dev] = (double*)p;
+  }
+  *st = KFBI_OK;
+  return addr[dev];
+}
+
+static kfbi_status grid_solve_noalloc_impl(int N, double h, double kappa, int boxbc, const double* rhs, double* u,
+                                           cudaStream_t s) {
+  kfbi_status st = KFBI_OK;
+  double* base = noalloc_scratch(&st);
+  if (st != KFBI_OK) return st;
+  int* flag = (int*)base;
+  double* spec = base + NOALLOC_HEAD;
+  double* tab = spec + (size_t)N * N;
+  double* lam = tab + 4 * (size_t)N;
+  double* tw = lam + N;
+  const int logN = ilog2(N);
+  const int dct = boxbc == KFBI_BOX_NEUMANN0;
+  k_noalloc_tables<<<cdiv(4L * N, 256), 256, 0, s>>>(N, h, dct, tab, lam, tw, flag);
+  size_t sm_row = sizeof(V2<double>) * N;
+  k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 0, (const V2<double>*)tw, tab, rhs, spec, nullptr);
+  int CP = 2;
+  if (2 * CP > N) CP = N / 2;
+  int threads = 256;
+  while (CP * (N / 2 + 1) > 8 * threads && threads < 1024) threads *= 2;
+  size_t sm_col = sizeof(V2<double>) * (size_t)CP * N;
+  k_col_solve<double><<<N / (2 * CP), threads, sm_col, s>>>(N, logN, CP, dct, (const V2<double>*)tw, tab, lam, kappa,
+                                                             spec, flag);
+  k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 1, (const V2<double>*)tw, tab, nullptr, spec, u);
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
 }  // namespace kfbi
+
+extern "C" kfbi_status kfbi_grid_solve_noalloc(int N, double h, double kappa, int boxbc, const double* rhs, double* u,
+                                               void* stream) {
+  if (N < 16 || (N & (N - 1)) != 0 || rhs == nullptr || u == nullptr) return KFBI_ERR_ARG;
+  if (N > kfbi::NOALLOC_MAX_N) return KFBI_ERR_CAPACITY;
+  if (!(h > 0.0) || !(kappa >= 0.0) || boxbc < KFBI_BOX_DIRICHLET0 || boxbc > KFBI_BOX_FREESPACE_DL)
+    return KFBI_ERR_ARG;
+  if (boxbc == KFBI_BOX_NEUMANN0 && kappa == 0.0) return KFBI_ERR_SINGULAR;
+  return kfbi::grid_solve_noalloc_impl(N, h, kappa, boxbc, rhs, u, (cudaStream_t)stream);
+}

@@ -76,6 +76,7 @@ _SIGNATURES = {
     "kfbi_timing_enable": (_I, [_P, _I]),
     "kfbi_timing_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "kfbi_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "kfbi_grid_solve_noalloc": (_I, [_I, _D, _D, _I, _P, _P, _P]),
 }
 
 
@@ -260,6 +261,17 @@ class Context:
         v = ctypes.c_longlong()
         _check(self.lib.kfbi_launch_count(self.handle, ctypes.byref(v)), "kfbi_launch_count")
         return v.value
+
+
+def grid_solve_noalloc(rhs, h, kappa=0.0, boxbc=BOX_DIRICHLET0, out=None):
+    """kfbi_grid_solve_noalloc: the box solve without any device allocation in the library
+    (its scratch is a static device array; N <= 512). `out` may be preallocated."""
+    lib = load()
+    N = rhs.shape[0]
+    u = out if out is not None else torch.empty_like(rhs)
+    _check(lib.kfbi_grid_solve_noalloc(N, float(h), float(kappa), int(boxbc), _f64(rhs, (N, N)), _ptr(u), _stream()),
+           "kfbi_grid_solve_noalloc")
+    return u
 
 
 class ThetaL:
