@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="kfbi", choices=["kfbi", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="timed steps only (for short profiler runs): no e2e, applies, fp64 or cpu legs")
     return ap.parse_args()
 
 
@@ -281,7 +283,6 @@ def main():
     run_steps(torch, ctx, st, args.warmup, flush)
     st.write(eta=ckpt["eta"], density=ckpt["density"], nhat=ckpt["nhat"], scalars=ckpt["scalars"])
     torch.cuda.synchronize()
-    ctx.timing(True)
     launches0 = ctx.launch_count()
     sampler = ClockSampler(local)
     sampler.start()
@@ -296,22 +297,31 @@ def main():
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     launches = ctx.launch_count() - launches0
-    tim = ctx.timing()
-    ctx.timing(False)
     total_s = sum(ms) / 1e3
     if pg:
         tt = torch.tensor([total_s], device="cuda")
         pg.all_reduce(tt, op=pg.ReduceOp.MAX)
         total_s = float(tt.item())
+    # kernel timing pass: the same steps again from the same state with per-launch CUDA events
+    # around the column kernel (event timing runs the solver's stream-launched form; the
+    # kernels are the same as in the graph form timed above)
+    st.write(eta=ckpt["eta"], density=ckpt["density"], nhat=ckpt["nhat"], scalars=ckpt["scalars"])
+    ctx.timing(True)
+    run_steps(torch, ctx, st, min(args.steps, 10), flush)
+    tim = ctx.timing()
+    ctx.timing(False)
     iters = [i["iterations"] for i in infos]
     value = world * args.steps / total_s
     print(f"[bench] mixed: {1e3 * total_s / args.steps:.3f} ms/step, GMRES its {np.mean(iters):.1f}, "
           f"col kernel {tim}", file=sys.stderr)
-    mixed_applies = time_applies(torch, K, ctx)
+    if args.profile:
+        args.no_fp64 = True
+        args.no_cpu_baseline = True
+    mixed_applies = None if args.profile else time_applies(torch, K, ctx)
 
     # ---- end to end through the public API with host buffers
     e2e = None
-    if True:
+    if not args.profile:
         n = p.n
         host_eta = ckpt["eta"].cpu().pin_memory()
         host_dens = ckpt["density"].cpu().pin_memory()

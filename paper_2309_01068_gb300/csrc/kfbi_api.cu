@@ -21,7 +21,7 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
 
 // sin(pi m / (2N)) for m < 4N; box eigenvalues -4 sin^2(pi (k + s) / (2N)) / h^2 with s = 1
 // (Dirichlet-0, DST-II mode k) or s = 0 (Neumann-0, DCT-II mode k); FFT twiddles
-// e^{-2 pi i m / N} = (cos, -sin)(pi (4m) / (2N)) for m < N/2.
+// e^{-2 pi i m / N} for m < N.
 __global__ void k_init_tables(int N, double h, int neumann, double* tab, float* tab_f, double* lam, float* lam_f,
                               double* tw, float* tw_f) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,7 +36,7 @@ __global__ void k_init_tables(int N, double h, int neumann, double* tab, float* 
     lam[m] = l;
     lam_f[m] = (float)l;
   }
-  if (m < N / 2) {
+  if (m < N) {
     double s, c;
     sincospi(2.0 * (double)m / (double)N, &s, &c);
     tw[2 * m] = c;
@@ -44,6 +44,17 @@ __global__ void k_init_tables(int N, double h, int neumann, double* tab, float* 
     tw_f[2 * m] = (float)c;
     tw_f[2 * m + 1] = (float)-s;
   }
+}
+
+__global__ void k_stage_twiddles(int N, int Ns, int off, const double* tw, double* out, float* out_f) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * Ns) return;
+  int r = t / Ns + 1, jm = t - (r - 1) * Ns;
+  long m = (long)r * jm * (N / (4 * Ns));  // < N
+  out[2 * (off + t)] = tw[2 * m];
+  out[2 * (off + t) + 1] = tw[2 * m + 1];
+  out_f[2 * (off + t)] = (float)tw[2 * m];
+  out_f[2 * (off + t) + 1] = (float)tw[2 * m + 1];
 }
 
 template <typename P>
@@ -57,11 +68,12 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
   int cap = ncr + ncr / 2 + 64;
   cudaStreamSynchronize(c->stream);
   cudaFree(c->cr_kind); cudaFree(c->cr_line); cudaFree(c->cr_seg); cudaFree(c->cr_first);
-  cudaFree(c->cr_alpha); cudaFree(c->cr_xi); cudaFree(c->tgeo); cudaFree(c->irr);
-  cudaFree(c->jumps); cudaFree(c->cval);
+  cudaFree(c->cr_alpha); cudaFree(c->cr_xi); cudaFree(c->tgeo); cudaFree(c->tgeo_f); cudaFree(c->irr);
+  cudaFree(c->tstart); cudaFree(c->tstart_f); cudaFree(c->jumps);
   c->cr_kind = c->cr_line = c->cr_seg = c->cr_first = nullptr;
   c->cr_alpha = c->cr_xi = nullptr;
-  c->tgeo = nullptr; c->irr = nullptr; c->jumps = nullptr; c->cval = nullptr;
+  c->tgeo = nullptr; c->tgeo_f = nullptr; c->irr = nullptr;
+  c->tstart = nullptr; c->tstart_f = nullptr; c->jumps = nullptr;
   c->cap_cross = c->cap_irr = 0;
   KFBI_CHECK(dalloc(&c->cr_kind, cap));
   KFBI_CHECK(dalloc(&c->cr_line, cap));
@@ -70,10 +82,12 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
   KFBI_CHECK(dalloc(&c->cr_alpha, cap));
   KFBI_CHECK(dalloc(&c->cr_xi, cap));
   KFBI_CHECK(dalloc(&c->tgeo, (size_t)cap + c->max_nodes));
+  KFBI_CHECK(dalloc(&c->tgeo_f, (size_t)cap + c->max_nodes));
   int cap_irr = 2 * cap + 64;
   KFBI_CHECK(dalloc(&c->irr, cap_irr));
+  KFBI_CHECK(dalloc(&c->tstart, 2 * (size_t)TSTART_STRIDE * ((size_t)cap + c->max_nodes)));
+  KFBI_CHECK(dalloc(&c->tstart_f, 2 * (size_t)TSTART_STRIDE * ((size_t)cap + c->max_nodes)));
   KFBI_CHECK(dalloc(&c->jumps, 6 * ((size_t)cap + c->max_nodes)));
-  KFBI_CHECK(dalloc(&c->cval, cap_irr));
   c->cap_cross = cap;
   c->cap_irr = cap_irr;
   return KFBI_OK;
@@ -82,14 +96,27 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
 static void free_all(kfbi_ctx* c) {
   void* ptrs[] = {c->sintab, c->sintab_f, c->lam, c->lam_f, c->twN, c->twN_f, c->xy, c->twn, c->icoef, c->fine,
                   c->seg_count, c->seg_off, c->cr_kind, c->cr_line, c->cr_seg, c->cr_first, c->cr_alpha, c->cr_xi,
-                  c->tgeo, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->stencil,
+                  c->tgeo, c->tgeo_f, c->stencil_f, c->dens_f, c->stw, c->stw_d, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->stencil,
                   c->probe_mark, c->prow_cnt, c->prow_ptr, c->probe_i, c->flags, c->counts, c->dcoef, c->dint,
-                  c->jumps, c->cval, c->boxg, c->spec, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gpart, c->gw,
-                  c->gin, c->gb, c->gx, c->gr, c->zero_flag};
+                  c->boxg, c->facespec, c->spec, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack,
+                  c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gpart, c->gw,
+                  c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->host_counts) cudaFreeHost(c->host_counts);
   if (c->host_gctl) cudaFreeHost(c->host_gctl);
+  for (auto& row : c->sgraph)
+    for (auto& g : row) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
+    }
+  if (c->gev) cudaFree(c->gev);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->aux) cudaStreamDestroy(c->aux);
+  if (c->own) cudaStreamDestroy(c->own);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->tev) {
     for (int i = 0; i < 2 * TIMING_CAP; ++i)
       if (c->tev[i]) cudaEventDestroy(c->tev[i]);
@@ -117,10 +144,15 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->sintab_f, 4 * (size_t)N));
   KFBI_CHECK(dalloc(&c->lam, N));
   KFBI_CHECK(dalloc(&c->lam_f, N));
-  KFBI_CHECK(dalloc(&c->twN, N));
-  KFBI_CHECK(dalloc(&c->twN_f, N));
+  KFBI_CHECK(dalloc(&c->twN, 2 * (size_t)N));
+  KFBI_CHECK(dalloc(&c->twN_f, 2 * (size_t)N));
   KFBI_CHECK(dalloc(&c->xy, 2 * (size_t)max_nodes));
   KFBI_CHECK(dalloc(&c->twn, 2 * (size_t)max_nodes));
+  KFBI_CHECK(dalloc(&c->twn_f, 2 * (size_t)max_nodes));
+  KFBI_CHECK(dalloc(&c->npack, 4 * (size_t)max_nodes));
+  KFBI_CHECK(dalloc(&c->npack_f, 4 * (size_t)max_nodes));
+  KFBI_CHECK(dalloc(&c->prow_list, N + 1));
+  KFBI_CHECK(dalloc(&c->facespec, 2 * (size_t)N));
   KFBI_CHECK(dalloc(&c->icoef, 4 * (size_t)nk));
   KFBI_CHECK(dalloc(&c->fine, 2 * (size_t)M));
   KFBI_CHECK(dalloc(&c->seg_count, 2 * (size_t)M + 1));
@@ -133,6 +165,10 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->rowcnt, N + 1));
   KFBI_CHECK(dalloc(&c->row_ptr, N + 1));
   KFBI_CHECK(dalloc(&c->stencil, max_nodes));
+  KFBI_CHECK(dalloc(&c->stencil_f, max_nodes));
+  KFBI_CHECK(dalloc(&c->dens_f, max_nodes));
+  KFBI_CHECK(dalloc(&c->stw, 2 * (size_t)N));
+  KFBI_CHECK(dalloc(&c->stw_d, 2 * (size_t)N));
   KFBI_CHECK(dalloc(&c->probe_mark, NN));
   KFBI_CHECK(dalloc(&c->prow_cnt, N + 1));
   KFBI_CHECK(dalloc(&c->prow_ptr, N + 1));
@@ -149,9 +185,10 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->gctl, 1));
   KFBI_TRY(cudaMallocHost((void**)&c->host_gctl, sizeof(GmresCtl)));
   KFBI_CHECK(dalloc(&c->gV, (size_t)(MAX_RESTART + 1) * max_nodes));
-  KFBI_CHECK(dalloc(&c->gpart, (size_t)64 * (MAX_RESTART + 1)));
+  KFBI_CHECK(dalloc(&c->gpart, ((size_t)max_nodes / 32 + MAX_RESTART + 2) * (MAX_RESTART + 1)));
   KFBI_CHECK(dalloc(&c->gw, max_nodes));
   KFBI_CHECK(dalloc(&c->gin, max_nodes));
+  KFBI_CHECK(dalloc(&c->gin_f, max_nodes));
   KFBI_CHECK(dalloc(&c->gb, max_nodes));
   KFBI_CHECK(dalloc(&c->gx, max_nodes));
   KFBI_CHECK(dalloc(&c->gr, max_nodes));
@@ -161,12 +198,34 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_TRY(cudaMemset(c->vcount, 0, NN * sizeof(int)));
   KFBI_TRY(cudaMemset(c->probe_mark, 0, NN * sizeof(int)));
   KFBI_TRY(cudaMemset(c->gctl, 0, sizeof(GmresCtl)));
+  KFBI_TRY(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking));
+  KFBI_TRY(cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking));
+  KFBI_TRY(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+  KFBI_TRY(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  c->user = cudaStreamLegacy;
+  c->user_default = true;
+  c->stream = c->own;
+  KFBI_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  KFBI_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   KFBI_CHECK(ensure_cross_capacity(c, 4096));
+  KFBI_CHECK(dalloc(&c->gev, max_nodes));
+  KFBI_CHECK(apply_setup_attributes(c));
   launched(c, 1);
-  k_init_tables<<<cdiv(4L * N, 256), 256>>>(N, c->h, boxbc == KFBI_BOX_NEUMANN0, c->sintab, c->sintab_f, c->lam,
-                                           c->lam_f, c->twN, c->twN_f);
+  k_init_tables<<<cdiv(4L * N, 256), 256, 0, c->own>>>(N, c->h, boxbc == KFBI_BOX_NEUMANN0, c->sintab, c->sintab_f,
+                                                     c->lam, c->lam_f, c->twN, c->twN_f);
   KFBI_TRY(cudaGetLastError());
-  KFBI_TRY(cudaDeviceSynchronize());
+  // staged twiddles of the Stockham FFT: for each radix-4 stage with span Ns (first stage
+  // radix 2 when log2 N is odd), w^{r jm N / (4 Ns)} at [off + (r-1) Ns + jm], r = 1..3
+  {
+    int off = 0;
+    for (int Ns = (c->logN & 1) ? 2 : 1; Ns < N; Ns <<= 2) {
+      k_stage_twiddles<<<cdiv(3L * Ns, 256), 256, 0, c->own>>>(N, Ns, off, c->twN, c->stw_d, c->stw);
+      launched(c, 1);
+      off += 3 * Ns;
+    }
+  }
+  KFBI_TRY(cudaGetLastError());
+  KFBI_TRY(cudaStreamSynchronize(c->own));
   return KFBI_OK;
 }
 
@@ -207,14 +266,18 @@ kfbi_status kfbi_create(int N, double xmin, double xmax, double ymin, double yma
 
 void kfbi_destroy(kfbi_ctx* c) {
   if (c == nullptr) return;
-  cudaStreamSynchronize(c->stream);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->aux) cudaStreamSynchronize(c->aux);
   free_all(c);
   delete c;
 }
 
 kfbi_status kfbi_set_stream(kfbi_ctx* c, void* stream) {
   if (!ctx_ok(c)) return KFBI_ERR_ARG;
-  c->stream = (cudaStream_t)stream;
+  cudaStream_t st = (cudaStream_t)stream;
+  c->user_default = st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
+  c->user = st == nullptr ? cudaStreamLegacy : st;
+  c->stream = c->user_default ? c->own : st;
   return KFBI_OK;
 }
 
@@ -222,7 +285,10 @@ kfbi_status kfbi_set_interface(kfbi_ctx* c, int n, const double* xy) {
   if (!ctx_ok(c) || xy == nullptr) return KFBI_ERR_ARG;
   if (n < 8) return KFBI_ERR_ARG;
   if (n > c->max_nodes) return KFBI_ERR_CAPACITY;
-  return set_interface_impl(c, n, xy);
+  KFBI_TRY(stream_enter(c));
+  kfbi_status st = set_interface_impl(c, n, xy);
+  KFBI_TRY(stream_exit(c));
+  return st;
 }
 
 kfbi_status kfbi_apply_layer_potential(kfbi_ctx* c, int layer, const double* density, double* values,
@@ -232,7 +298,11 @@ kfbi_status kfbi_apply_layer_potential(kfbi_ctx* c, int layer, const double* den
   if (density == nullptr || values == nullptr) return KFBI_ERR_ARG;
   if (layer != KFBI_SINGLE && layer != KFBI_DOUBLE) return KFBI_ERR_ARG;
   if (c->boxbc == KFBI_BOX_FREESPACE_DL && layer != KFBI_DOUBLE) return KFBI_ERR_ARG;
-  return apply_enqueue(c, layer, c->precision == KFBI_MIXED, density, values, dnormal, grid, -1, nullptr, nullptr);
+  KFBI_TRY(stream_enter(c));
+  kfbi_status st = apply_enqueue(c, layer, c->precision == KFBI_MIXED, density, values, dnormal, grid, -1, nullptr,
+                                 nullptr);
+  KFBI_TRY(stream_exit(c));
+  return st;
 }
 
 kfbi_status kfbi_bie_apply(kfbi_ctx* c, int kind, const double* eps_v, const double* x, double* y) {
@@ -242,7 +312,10 @@ kfbi_status kfbi_bie_apply(kfbi_ctx* c, int kind, const double* eps_v, const dou
   if (kind == KFBI_BIE_STEFAN_SL && c->boxbc == KFBI_BOX_FREESPACE_DL) return KFBI_ERR_ARG;
   if (!c->have_iface) return KFBI_ERR_STATE;
   int layer = kind == KFBI_BIE_STEFAN_SL ? KFBI_SINGLE : KFBI_DOUBLE;
-  return apply_enqueue(c, layer, c->precision == KFBI_MIXED, x, y, nullptr, nullptr, kind, eps_v, nullptr);
+  KFBI_TRY(stream_enter(c));
+  kfbi_status st = apply_enqueue(c, layer, c->precision == KFBI_MIXED, x, y, nullptr, nullptr, kind, eps_v, nullptr);
+  KFBI_TRY(stream_exit(c));
+  return st;
 }
 
 kfbi_status kfbi_solve_bie(kfbi_ctx* c, int kind, const double* eps_v, const double* rhs, double tol, int max_iter,
@@ -253,18 +326,27 @@ kfbi_status kfbi_solve_bie(kfbi_ctx* c, int kind, const double* eps_v, const dou
   if (kind == KFBI_BIE_STEFAN_SL && c->boxbc == KFBI_BOX_FREESPACE_DL) return KFBI_ERR_ARG;
   if (!(tol > 0.0) || max_iter < 1 || restart < 1 || restart > MAX_RESTART) return KFBI_ERR_ARG;
   if (!c->have_iface) return KFBI_ERR_STATE;
-  return solve_bie_impl(c, kind, eps_v, rhs, tol, max_iter, restart, density, info);
+  KFBI_TRY(stream_enter(c));
+  kfbi_status st = solve_bie_impl(c, kind, eps_v, rhs, tol, max_iter, restart, density, info);
+  KFBI_TRY(stream_exit(c));
+  return st;
 }
 
 kfbi_status kfbi_grid_solve(kfbi_ctx* c, const double* rhs, double* u) {
   if (!ctx_ok(c) || rhs == nullptr || u == nullptr) return KFBI_ERR_ARG;
-  return grid_solve_enqueue(c, rhs, u);
+  KFBI_TRY(stream_enter(c));
+  kfbi_status st = grid_solve_enqueue(c, rhs, u);
+  KFBI_TRY(stream_exit(c));
+  return st;
 }
 
 kfbi_status kfbi_interp_grid(kfbi_ctx* c, const double* grid, double* values) {
   if (!ctx_ok(c) || grid == nullptr || values == nullptr) return KFBI_ERR_ARG;
   if (!c->have_iface) return KFBI_ERR_STATE;
-  return interp_grid_enqueue(c, grid, values);
+  KFBI_TRY(stream_enter(c));
+  kfbi_status st = interp_grid_enqueue(c, grid, values);
+  KFBI_TRY(stream_exit(c));
+  return st;
 }
 
 kfbi_status kfbi_interface_stats(kfbi_ctx* c, int* n_crossings, int* n_irregular, int* n_probes) {
@@ -279,7 +361,9 @@ kfbi_status kfbi_interface_stats(kfbi_ctx* c, int* n_crossings, int* n_irregular
 kfbi_status kfbi_copy_sides(kfbi_ctx* c, uint8_t* sides) {
   if (!ctx_ok(c) || sides == nullptr) return KFBI_ERR_ARG;
   if (!c->have_iface) return KFBI_ERR_STATE;
+  KFBI_TRY(stream_enter(c));
   KFBI_TRY(cudaMemcpyAsync(sides, c->side, (size_t)c->N * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  KFBI_TRY(stream_exit(c));
   return KFBI_OK;
 }
 
@@ -298,11 +382,13 @@ kfbi_status kfbi_copy_crossings(kfbi_ctx* c, int cap, int* kind_line_first, doub
   if (!ctx_ok(c) || kind_line_first == nullptr || alpha_xi == nullptr || cap < 0) return KFBI_ERR_ARG;
   if (!c->have_iface) return KFBI_ERR_STATE;
   int cnt = cap < c->n_cross ? cap : c->n_cross;
+  KFBI_TRY(stream_enter(c));
   if (cnt > 0) launched(c, 1);
   if (cnt > 0)
     k_pack_crossings<<<cdiv(cnt, 256), 256, 0, c->stream>>>(cnt, c->cr_kind, c->cr_line, c->cr_first, c->cr_alpha,
                                                             c->cr_xi, kind_line_first, alpha_xi);
   KFBI_TRY(cudaGetLastError());
+  KFBI_TRY(stream_exit(c));
   return KFBI_OK;
 }
 
@@ -317,9 +403,11 @@ kfbi_status kfbi_copy_irregular(kfbi_ctx* c, int cap, int* ji) {
   if (!ctx_ok(c) || ji == nullptr || cap < 0) return KFBI_ERR_ARG;
   if (!c->have_iface) return KFBI_ERR_STATE;
   int cnt = cap < c->n_irr ? cap : c->n_irr;
+  KFBI_TRY(stream_enter(c));
   if (cnt > 0) launched(c, 1);
   if (cnt > 0) k_pack_irregular<<<cdiv(cnt, 256), 256, 0, c->stream>>>(cnt, c->irr, ji);
   KFBI_TRY(cudaGetLastError());
+  KFBI_TRY(stream_exit(c));
   return KFBI_OK;
 }
 

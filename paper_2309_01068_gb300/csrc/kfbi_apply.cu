@@ -3,8 +3,19 @@
 // the jump-corrected 6-point interpolation (Sec. 4.3). Every kernel is templated on the
 // grid arithmetic type T (double for KFBI_FP64, float for the inner applies of
 // KFBI_MIXED); interface inputs and outputs stay float64.
+//
+// Data flow of one apply (N x N grid, spectral grid `spec` row-major [j][k]):
+//   k_dens_coef      density Fourier coefficients (DFT, exact twiddle indexing)
+//   k_target_jumps   jumps at every crossing and node from the coefficients
+//   k_box_data       free-space box data on the four faces (Hele-Shaw box only)
+//   k_face_dst       DST-II along x of the two dense face rows (Hele-Shaw box only)
+//   k_row_forward    per row: corrections at its irregular nodes + box terms -> DST along x
+//   k_col_solve      per column: DST along y, divide by the eigenvalue, inverse along y
+//   k_probe_values   inverse along x only at the interpolation points
+//   k_interp         6-point jump-corrected interpolation -> boundary operator values
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "kfbi_internal.cuh"
 
@@ -19,9 +30,14 @@ template <typename T>
 __device__ __forceinline__ V2<T> cmul(V2<T> a, V2<T> b) {
   return V2<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-
-__device__ __forceinline__ void sincos_t(double a, double* s, double* c) { sincos(a, s, c); }
-__device__ __forceinline__ void sincos_t(float a, float* s, float* c) { sincosf(a, s, c); }
+template <typename T>
+__device__ __forceinline__ V2<T> cadd(V2<T> a, V2<T> b) {
+  return V2<T>{a.x + b.x, a.y + b.y};
+}
+template <typename T>
+__device__ __forceinline__ V2<T> csub(V2<T> a, V2<T> b) {
+  return V2<T>{a.x - b.x, a.y - b.y};
+}
 
 template <typename T>
 __device__ __forceinline__ T wsum(T v) {
@@ -29,96 +45,148 @@ __device__ __forceinline__ T wsum(T v) {
   return v;
 }
 
-// --------------------------------------------------------------------------- density
-// c_k = (1/n) sum_j phi_j e^{-2 pi i k j / n} (k = 0..n/2) in T; the warp of k = 0 also
-// forms int phi ds = sum_j phi_j s_a,j 2 pi / n (trapezoidal rule).
+__device__ __forceinline__ float fdiv_t(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv_t(double a, double b) { return a / b; }
+
+// largest dynamic shared memory a kernel stages its inputs in (bytes); larger inputs are read
+// from global memory
+constexpr size_t SMEM_STAGE_MAX = 96 * 1024;
+
 template <typename T>
-__global__ void k_dens_coef(const double* phi, int n, const double2* tw, const Stencil* st, V2<T>* coef,
+struct Tabs;  // typed views of the context's tables and geometry
+template <>
+struct Tabs<double> {
+  static const double* sin(const kfbi_ctx* c) { return c->sintab; }
+  static const double* lam(const kfbi_ctx* c) { return c->lam; }
+  static const V2<double>* twN(const kfbi_ctx* c) { return (const V2<double>*)c->twN; }
+  static const V2<double>* stw(const kfbi_ctx* c) { return (const V2<double>*)c->stw_d; }
+  static const TargetGeo* geo(const kfbi_ctx* c) { return c->tgeo; }
+  static const Stencil* stencil(const kfbi_ctx* c) { return c->stencil; }
+  static const V2<double>* twn(const kfbi_ctx* c) { return (const V2<double>*)c->twn; }
+  static const V2<double>* tstart(const kfbi_ctx* c) { return (const V2<double>*)c->tstart; }
+  static const double4_32a* npack(const kfbi_ctx* c) { return (const double4_32a*)c->npack; }
+};
+template <>
+struct Tabs<float> {
+  static const float* sin(const kfbi_ctx* c) { return c->sintab_f; }
+  static const float* lam(const kfbi_ctx* c) { return c->lam_f; }
+  static const V2<float>* twN(const kfbi_ctx* c) { return (const V2<float>*)c->twN_f; }
+  static const V2<float>* stw(const kfbi_ctx* c) { return (const V2<float>*)c->stw; }
+  static const TargetGeoF* geo(const kfbi_ctx* c) { return c->tgeo_f; }
+  static const StencilF* stencil(const kfbi_ctx* c) { return c->stencil_f; }
+  static const V2<float>* twn(const kfbi_ctx* c) { return (const V2<float>*)c->twn_f; }
+  static const V2<float>* tstart(const kfbi_ctx* c) { return (const V2<float>*)c->tstart_f; }
+  static const float4* npack(const kfbi_ctx* c) { return (const float4*)c->npack_f; }
+};
+
+// sin(pi m / (2N)) for an integer m (4N-periodic): the table in float64; in float32 the SFU
+// sine after exact integer reduction of the argument to (-pi, pi] (absolute error < 4e-7)
+__device__ __forceinline__ double tsin(const double* tab, int m, int N, float) { return tab[m & (4 * N - 1)]; }
+__device__ __forceinline__ float tsin(const float*, int m, int N, float scale) {
+  int r = m & (4 * N - 1);
+  if (r > 2 * N) r -= 4 * N;
+  return __sinf((float)r * scale);
+}
+
+// per-type fields of an irregular node
+__device__ __forceinline__ double irr_d(const IrrNode& q, int a, double) { return q.d[a]; }
+__device__ __forceinline__ float irr_d(const IrrNode& q, int a, float) { return q.df[a]; }
+__device__ __forceinline__ double irr_sign(const IrrNode& q, double) { return q.sign; }
+__device__ __forceinline__ float irr_sign(const IrrNode& q, float) { return q.signf; }
+
+__global__ void k_to_float(const double* a, float* b, int n, const int* skip) {
+  if (*skip) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// --------------------------------------------------------------------------- density
+// c_k = (1/n) sum_j phi_j e^{-2 pi i k j / n} (k = 0..n/2): one warp per k, twiddle index
+// k j mod n advanced incrementally; the block stages the density and the twiddles in shared
+// memory (SMEM = true) or reads them from global memory (large n). The warp of k = 0 also
+// forms int phi ds = sum_j phi_j s_a,j 2 pi / n (trapezoidal rule) for the Hele-Shaw operator.
+template <typename T, bool SMEM>
+__global__ void k_dens_coef(const T* phi, const double* phi64, int n, const V2<T>* tw, const Stencil* st, V2<T>* coef,
                             double* dint, const int* skip) {
   if (*skip) return;
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  extern __shared__ unsigned char smem_raw[];
+  V2<T>* stw = (V2<T>*)smem_raw;
+  T* sphi = (T*)(stw + n);
+  if (SMEM) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      stw[j] = tw[j];
+      sphi[j] = phi[j];
+    }
+    __syncthreads();
+  }
+  int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  int nk = n / 2 + 1;
-  if (warp >= nk) return;
-  int k = warp;
+  if (k > n / 2) return;
+  int idx = (int)(((long)k * lane) % n);
+  const int step = (int)(((long)k * 32) % n);
   T re = 0, im = 0;
   for (int j = lane; j < n; j += 32) {
-    T v = (T)phi[j];
-    double2 w = tw[(int)(((long)k * j) % n)];
-    re += v * (T)w.x;
-    im -= v * (T)w.y;
+    T v = SMEM ? sphi[j] : phi[j];
+    V2<T> w = SMEM ? stw[idx] : tw[idx];
+    re += v * w.x;
+    im -= v * w.y;
+    idx += step;
+    if (idx >= n) idx -= n;
   }
   re = wsum(re);
   im = wsum(im);
   if (lane == 0) coef[k] = V2<T>{re / (T)n, im / (T)n};
   if (k == 0 && dint != nullptr) {
     double s = 0.0;
-    for (int j = lane; j < n; j += 32) s += phi[j] * st[j].w;
+    for (int j = lane; j < n; j += 32) s += phi64[j] * st[j].w;
     s = wsum(s);
     if (lane == 0) *dint = s;
   }
 }
 
-// f, f', f'' of the density interpolant at alpha (warp-cooperative, see trig_warp)
-template <typename T>
-__device__ __forceinline__ void dens_eval(const V2<T>* c, int n, double alpha, int lane, T& f, T& f1, T& f2) {
+// Warp-level jumps at one target (App. A.1, Table 2): the warp sums the density interpolant
+// and its first two derivatives from the precomputed twiddle starts `ts` (lane l sums the
+// modes [k0_l, k0_l + chunk) from e^{i k0_l alpha}, rotating by e^{i alpha}; the Nyquist term
+// uses e^{i n alpha / 2}), then every lane solves the 2x2 and 3x3 systems and holds
+// J = ([u], [u_x], [u_y], [u_xx], [u_yy], [u_xy]).
+template <typename T, typename G>
+__device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, const V2<T>* ts, const G& g, int layer,
+                                          double kappa, int lane, T J[6]) {
   const int K = (n - 1) / 2;
   const int chunk = (K + 31) / 32;
   int k0 = 1 + lane * chunk;
   int k1 = min(K + 1, k0 + chunk);
   T a = 0, b = 0, d = 0;
   if (k0 < k1) {
-    double es, ec, ss, sc;
-    sincos((double)k0 * alpha, &es, &ec);
-    sincos(alpha, &ss, &sc);
-    T er = (T)ec, ei = (T)es, sr = (T)sc, si = (T)ss;
+    V2<T> e = ts[lane];
+    const V2<T> s = ts[32];
     for (int k = k0; k < k1; ++k) {
-      V2<T> ck = c[k];
-      T re = ck.x * er - ck.y * ei;
-      T im = ck.x * ei + ck.y * er;
+      V2<T> ck = coef[k];
+      T re = ck.x * e.x - ck.y * e.y;
+      T im = ck.x * e.y + ck.y * e.x;
+      T kk = (T)k;
       a += re;
-      b -= (T)k * im;
-      d -= (T)k * (T)k * re;
-      T t = er * sr - ei * si;
-      ei = er * si + ei * sr;
-      er = t;
+      b -= kk * im;
+      d -= kk * kk * re;
+      e = cmul(e, s);
     }
   }
-  a = (T)2 * wsum(a);
+  a = (T)2 * wsum(a) + coef[0].x;
   b = (T)2 * wsum(b);
   d = (T)2 * wsum(d);
-  a += c[0].x;
   if ((n & 1) == 0) {
-    double m = 0.5 * n;
-    T nyq = c[n / 2].x;
-    double s, co;
-    sincos(m * alpha, &s, &co);
-    a += nyq * (T)co;
-    b -= (T)m * nyq * (T)s;
-    d -= (T)(m * m) * nyq * (T)co;
+    const V2<T> q = ts[33];
+    T m = (T)(n / 2);
+    T nyq = coef[n / 2].x;
+    a += nyq * q.x;
+    b -= m * nyq * q.y;
+    d -= m * m * nyq * q.x;
   }
-  f = a;
-  f1 = b;
-  f2 = d;
-}
-
-// jumps ([u], [u_x], [u_y], [u_xx], [u_yy], [u_xy]) at every target (App. A.1, Table 2)
-template <typename T>
-__global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const TargetGeo* tg, int layer, double kappa,
-                               T* J, const int* skip) {
-  if (*skip) return;
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (warp >= ntg) return;
-  const TargetGeo& g = tg[warp];
-  T f, f1, f2;
-  dens_eval<T>(coef, n, g.alpha, lane, f, f1, f2);
-  if (lane != 0) return;
   T Phi, Phia, Phiaa, Psi, Psia;
   if (layer == KFBI_DOUBLE) {
-    Phi = f; Phia = f1; Phiaa = f2; Psi = 0; Psia = 0;
+    Phi = a; Phia = b; Phiaa = d; Psi = 0; Psia = 0;
   } else {
-    Phi = 0; Phia = 0; Phiaa = 0; Psi = -f; Psia = -f1;
+    Phi = 0; Phia = 0; Phiaa = 0; Psi = -a; Psia = -b;
   }
   T xa = (T)g.xa, ya = (T)g.ya, xaa = (T)g.xaa, yaa = (T)g.yaa, sa = (T)g.sa, saa = (T)g.saa;
   T is2 = (T)1 / (sa * sa);
@@ -127,181 +195,171 @@ __global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const TargetGe
   T b0 = Phiaa - xaa * ux - yaa * uy;
   T b1 = saa * Psi + sa * Psia - yaa * ux + xaa * uy;
   T b2 = (T)kappa * Phi;
-  T* o = J + (long)warp * 6;
-  o[0] = Phi;
-  o[1] = ux;
-  o[2] = uy;
-  o[3] = (T)g.A3i[0] * b0 + (T)g.A3i[1] * b1 + (T)g.A3i[2] * b2;
-  o[4] = (T)g.A3i[3] * b0 + (T)g.A3i[4] * b1 + (T)g.A3i[5] * b2;
-  o[5] = (T)g.A3i[6] * b0 + (T)g.A3i[7] * b1 + (T)g.A3i[8] * b2;
+  J[0] = Phi;
+  J[1] = ux;
+  J[2] = uy;
+  J[3] = (T)g.A3i[0] * b0 + (T)g.A3i[1] * b1 + (T)g.A3i[2] * b2;
+  J[4] = (T)g.A3i[3] * b0 + (T)g.A3i[4] * b1 + (T)g.A3i[5] * b2;
+  J[5] = (T)g.A3i[6] * b0 + (T)g.A3i[7] * b1 + (T)g.A3i[8] * b2;
 }
 
-// C at every irregular node: sum over crossed arms of sign * (J0 + d J1 + d^2/2 J2) / h^2,
-// J1, J2 = [u_x], [u_xx] on horizontal arms and [u_y], [u_yy] on vertical arms (Sec. 4.2)
-template <typename T>
-__global__ void k_corrections(int nirr, const IrrNode* irr, const T* J, double inv_h2, T* cval, const int* skip) {
+// Jumps at every target (crossings, then nodes), one warp per target; the block stages the
+// density coefficients in shared memory first (SMEM = true; large n reads them from global memory). J[t] = ([u], [u_x], [u_y], [u_xx], [u_yy], [u_xy]).
+template <typename T, typename G, bool SMEM>
+__global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const G* tg, const V2<T>* tstart, int layer,
+                               double kappa, T* Jout, const int* skip) {
   if (*skip) return;
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nirr) return;
-  const IrrNode& node = irr[q];
-  T acc = 0;
-  for (int a = 0; a < 4; ++a) {
-    int t = node.target[a];
-    if (t < 0) continue;
-    const T* j = J + (long)t * 6;
-    T d = (T)node.d[a];
-    T j1 = a < 2 ? j[1] : j[2];
-    T j2 = a < 2 ? j[3] : j[4];
-    acc += j[0] + d * j1 + (T)0.5 * d * d * j2;
+  extern __shared__ unsigned char smem_raw[];
+  const V2<T>* sc = coef;
+  if (SMEM) {
+    V2<T>* w = (V2<T>*)smem_raw;
+    const int nk = n / 2 + 1;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) w[k] = coef[k];
+    __syncthreads();
+    sc = w;
   }
-  cval[q] = (T)(node.sign * inv_h2) * acc;
+  int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (t >= ntg) return;
+  T J[6];
+  jump_eval<T, G>(sc, n, tstart + (long)t * TSTART_STRIDE, tg[t], layer, kappa, lane, J);
+  if (lane < 6) Jout[(long)t * 6 + lane] = J[lane];
 }
 
 // Free-space box data (Sec. 4.1): g(p) = (1/n) sum_l phi_l (X_l - p).(y_a, -x_a)_l / |X_l - p|^2
-// at the 4N face midpoints, stored pre-scaled as the right-hand side term -2 g / h^2.
-template <typename T>
-__global__ void k_box_data(const double* phi, int n, const double* xy, const TargetGeo* tg_nodes, int N,
-                           double xmin, double xmax, double ymin, double ymax, double h, T* boxg, const int* skip) {
+// at the 4N face midpoints (west, east, south, north), stored pre-scaled as the
+// right-hand side term -2 g / h^2. npack[l] = (x, y, y_a, -x_a) of node l.
+template <typename T, typename T4, bool SMEM>
+__global__ void k_box_data(const T* phi, int n, const T4* npack, int N, double xmin, double xmax, double ymin,
+                           double ymax, double h, T* boxg, const int* skip) {
   if (*skip) return;
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  extern __shared__ unsigned char smem_raw[];
+  T4* sp = (T4*)smem_raw;  // (x, y, phi y_a, -phi x_a)
+  if (SMEM) {
+    for (int l = threadIdx.x; l < n; l += blockDim.x) {
+      T4 q = npack[l];
+      T f = phi[l];
+      q.z *= f;
+      q.w *= f;
+      sp[l] = q;
+    }
+    __syncthreads();
+  }
+  int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (warp >= 4 * N) return;
-  int face = warp / N, idx = warp - face * N;
+  if (w >= 4 * N) return;
+  int face = w / N, idx = w - face * N;
   double px, py;
   if (face == 0) { px = xmin; py = grid_coord(ymin, h, idx); }
   else if (face == 1) { px = xmax; py = grid_coord(ymin, h, idx); }
   else if (face == 2) { px = grid_coord(xmin, h, idx); py = ymin; }
   else { px = grid_coord(xmin, h, idx); py = ymax; }
   T acc = 0;
-  T tpx = (T)px, tpy = (T)py;
+  const T tpx = (T)px, tpy = (T)py;
   for (int l = lane; l < n; l += 32) {
-    T dx = (T)xy[2 * l] - tpx, dy = (T)xy[2 * l + 1] - tpy;
-    T num = dx * (T)tg_nodes[l].ya - dy * (T)tg_nodes[l].xa;
-    acc += (T)phi[l] * num / (dx * dx + dy * dy);
+    T4 q;
+    if (SMEM) {
+      q = sp[l];
+    } else {
+      q = npack[l];
+      T f = phi[l];
+      q.z *= f;
+      q.w *= f;
+    }
+    T dx = q.x - tpx, dy = q.y - tpy;
+    acc += fdiv_t(dx * q.z + dy * q.w, dx * dx + dy * dy);
   }
   acc = wsum(acc);
-  if (lane == 0) boxg[warp] = (T)(-2.0 / (h * h * (double)n)) * acc;
-}
-
-// --------------------------------------------------------------------------- row transforms
-// Sparse forward transform along x of one row (Sec. 4.2 right-hand side is zero away
-// from irregular nodes and, for free-space box data, the boundary cells):
-//   spec[j][k] = sum_i C[j][i] S_k(i),  S_k(i) = sin(pi (k+1)(2i+1)/(2N)) (DST-II) or
-//   cos(pi k (2i+1)/(2N)) (DCT-II), from the table sin(pi m / (2N)), m mod 4N.
-template <typename T>
-__global__ void k_row_forward(int N, int dct, const int* row_ptr, const IrrNode* irr, const T* cval,
-                              const T* boxg, const T* tab, T* spec, const int* skip) {
-  if (*skip) return;
-  extern __shared__ unsigned char smem_raw[];
-  int* si = (int*)smem_raw;
-  T* sv = (T*)(smem_raw + sizeof(int) * 1024);
-  int j = blockIdx.y;
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int mask = 4 * N - 1;
-  int b = row_ptr[j], e = row_ptr[j + 1];
-  T acc = 0;
-  // irregular-node entries, staged through shared memory in chunks
-  for (int c0 = b; c0 < e; c0 += 1024) {
-    int cnt = min(1024, e - c0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-      si[t] = 2 * irr[c0 + t].i + 1;
-      sv[t] = cval[c0 + t];
-    }
-    __syncthreads();
-    if (k < N) {
-      if (dct)
-        for (int t = 0; t < cnt; ++t) acc += sv[t] * tab[(k * si[t] + N) & mask];
-      else
-        for (int t = 0; t < cnt; ++t) acc += sv[t] * tab[((k + 1) * si[t]) & mask];
-    }
-  }
-  if (boxg != nullptr && k < N) {
-    // west (i = 0) and east (i = N-1) faces of this row
-    T w = boxg[j], ea = boxg[N + j];
-    if (dct) {
-      acc += w * tab[(k + N) & mask] + ea * tab[(k * (2 * N - 1) + N) & mask];
-    } else {
-      acc += w * tab[(k + 1) & mask] + ea * tab[((k + 1) * (2 * N - 1)) & mask];
-    }
-    if (j == 0 || j == N - 1) {  // south / north face: a dense row
-      const T* g = boxg + (j == 0 ? 2 * N : 3 * N);
-      if (dct)
-        for (int i = 0; i < N; ++i) acc += g[i] * tab[(k * (2 * i + 1) + N) & mask];
-      else
-        for (int i = 0; i < N; ++i) acc += g[i] * tab[((k + 1) * (2 * i + 1)) & mask];
-    }
-  }
-  if (k < N) spec[(long)j * N + k] = acc;
+  if (lane == 0) boxg[w] = (T)(-2.0 / (h * h * (double)n)) * acc;
 }
 
 // --------------------------------------------------------------------------- FFT core
-// In-place radix-2 decimation-in-frequency FFT of P length-N sequences in shared memory,
-// natural order in, bit-reversed order out. tw[m] = e^{-2 pi i m / N}, m < N/2; the
-// inverse uses the conjugate twiddles (no 1/N scaling here).
+// Stockham autosort FFT of P length-N sequences in shared memory (natural order in and
+// out): one radix-2 stage when log2 N is odd, then radix-4 stages. Stage with span Ns and
+// radix R: item j reads src[j + r N/R], multiplies by w^{r (j mod Ns) N/(Ns R)}, does the
+// R-point DFT and writes dst[(j/Ns) Ns R + (j mod Ns) + r Ns]. stw holds, stage by stage,
+// w^{r jm N / (4 Ns)} at [off + (r-1) Ns + jm] (w = e^{-2 pi i / N}, r = 1..3, off advancing by
+// 3 Ns per stage) so that neighbouring threads read neighbouring twiddles; the inverse
+// conjugates them (no 1/N). Returns the buffer with the result.
 template <typename T>
-__device__ void fft_dif(V2<T>* z, int P, int N, int logN, const V2<T>* tw, bool inverse) {
-  const int halfN = N >> 1;
-  for (int lh = logN - 1, ls = 0; lh >= 0; --lh, ++ls) {
-    const int half = 1 << lh;
-    for (int t = threadIdx.x; t < P * halfN; t += blockDim.x) {
-      int p = t >> (logN - 1);
-      int b = t & (halfN - 1);
-      int grp = b >> lh, pos = b & (half - 1);
-      int i0 = (grp << (lh + 1)) + pos, i1 = i0 + half;
-      V2<T>* zz = z + (long)p * N;
-      V2<T> a = zz[i0], c = zz[i1];
-      V2<T> w = tw[pos << ls];
-      if (inverse) w.y = -w.y;
-      zz[i0] = V2<T>{a.x + c.x, a.y + c.y};
-      zz[i1] = cmul(V2<T>{a.x - c.x, a.y - c.y}, w);
+__device__ V2<T>* fft_stockham(V2<T>* a, V2<T>* b, int P, int N, int logN, const V2<T>* stw, bool inverse) {
+  V2<T>* src = a;
+  V2<T>* dst = b;
+  int Ns = 1;
+  if (logN & 1) {
+    const int h = N >> 1;
+    for (int t = threadIdx.x; t < P * h; t += blockDim.x) {
+      int p = t >> (logN - 1), j = t & (h - 1);
+      const V2<T>* s = src + (long)p * N;
+      V2<T>* d = dst + (long)p * N;
+      V2<T> v0 = s[j], v1 = s[j + h];
+      d[2 * j] = cadd(v0, v1);
+      d[2 * j + 1] = csub(v0, v1);
     }
     __syncthreads();
+    V2<T>* tmp = src; src = dst; dst = tmp;
+    Ns = 2;
   }
+  const int q = N >> 2;
+  const int lq = logN - 2;
+  int off = 0;
+  for (; Ns < N; off += 3 * Ns, Ns <<= 2) {
+    const int lNs = __ffs(Ns) - 1;
+    for (int t = threadIdx.x; t < P * q; t += blockDim.x) {
+      int p = t >> lq, j = t & (q - 1);
+      const V2<T>* s = src + (long)p * N;
+      V2<T>* d = dst + (long)p * N;
+      int jm = j & (Ns - 1);
+      V2<T> v0 = s[j], v1 = s[j + q], v2 = s[j + 2 * q], v3 = s[j + 3 * q];
+      if (jm != 0) {
+        V2<T> w1 = stw[off + jm], w2 = stw[off + Ns + jm], w3 = stw[off + 2 * Ns + jm];
+        if (inverse) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; }
+        v1 = cmul(v1, w1);
+        v2 = cmul(v2, w2);
+        v3 = cmul(v3, w3);
+      }
+      V2<T> a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), t3 = csub(v1, v3);
+      V2<T> a3 = inverse ? V2<T>{-t3.y, t3.x} : V2<T>{t3.y, -t3.x};  // (+/- i)(v1 - v3)
+      int o = ((j >> lNs) << (lNs + 2)) + jm;
+      d[o] = cadd(a0, a2);
+      d[o + Ns] = cadd(a1, a3);
+      d[o + 2 * Ns] = csub(a0, a2);
+      d[o + 3 * Ns] = csub(a1, a3);
+    }
+    __syncthreads();
+    V2<T>* tmp = src; src = dst; dst = tmp;
+  }
+  return src;
 }
-
-__device__ __forceinline__ int bitrev(int k, int logN) { return (int)(__brev((unsigned)k) >> (32 - logN)); }
 
 // position of sample j in the Makhoul reordering v[n] = x[2n], v[N-1-n] = x[2n+1]
 __device__ __forceinline__ int mk_pos(int j, int N) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
 
-// Forward real-to-real transform of pair p (sequence a in .x, b in .y) already reordered
-// and FFT'd in z (bit-reversed). For m in [0, N/2] the thread handling m also handles N-m.
-// X'[m] = Re(e^{-i pi m/(2N)} V[m]) is the DCT-II of the stored sequence; for DST-II the
-// caller stored (-1)^j x_j and mode l corresponds to m = N-1-l.
+// DCT-II from the FFT of the reordered pair (sequence a in .x, b in .y), at m and N - m:
+// V_a[m] = (Z[m] + conj Z[N-m]) / 2, V_b[m] = (Z[m] - conj Z[N-m]) / (2i),
+// X'[m] = Re(e^{-i pi m / (2N)} V[m]); V[N-m] = conj V[m] for each real sequence.
+// For DST-II the caller stored (-1)^j x_j and mode l is DCT index N-1-l.
 template <typename T>
-__device__ __forceinline__ void dct_post(const V2<T>* z, int N, int logN, int m, const T* tab, V2<T>& Xm,
-                                         V2<T>& XNm) {
+__device__ __forceinline__ void dct_post(const V2<T>* z, int N, int m, const T* tab, V2<T>& Xm, V2<T>& XNm) {
   const int mask = 4 * N - 1;
-  int mN = (N - m) & (N - 1);
-  V2<T> Z = z[bitrev(m, logN)];
-  V2<T> Zr = z[bitrev(mN, logN)];
-  // V_a[m] = (Z[m] + conj Z[N-m]) / 2, V_b[m] = (Z[m] - conj Z[N-m]) / (2i)
+  V2<T> Z = z[m];
+  V2<T> Zr = z[(N - m) & (N - 1)];
   V2<T> Va{(T)0.5 * (Z.x + Zr.x), (T)0.5 * (Z.y - Zr.y)};
   V2<T> Vb{(T)0.5 * (Z.y + Zr.y), (T)-0.5 * (Z.x - Zr.x)};
-  T c = tab[(m + N) & mask], s = tab[m & mask];  // cos, sin of pi m / (2N)
+  T c = tab[(m + N) & mask], s = tab[m & mask];
   Xm = V2<T>{c * Va.x + s * Va.y, c * Vb.x + s * Vb.y};
-  // the same for N - m (V[N-m] = conj V[m] for each real sequence)
-  V2<T> Vra{Va.x, -Va.y}, Vrb{Vb.x, -Vb.y};
   T c2 = tab[((N - m) + N) & mask], s2 = tab[(N - m) & mask];
-  XNm = V2<T>{c2 * Vra.x + s2 * Vra.y, c2 * Vrb.x + s2 * Vrb.y};
+  XNm = V2<T>{c2 * Va.x - s2 * Va.y, c2 * Vb.x - s2 * Vb.y};
 }
 
-// Inverse preprocessing: from G (DCT-domain coefficients of a and b at m and N-m) build
-// V[m] = e^{i pi m/(2N)} (G[m] - i G[N-m]) for each sequence and pack a + i b.
+// inverse of dct_post: V[m] = e^{i pi m/(2N)} (G[m] - i G[N-m]) per sequence, packed a + i b
 template <typename T>
 __device__ __forceinline__ void dct_pre(int N, int m, const T* tab, V2<T> Gm, V2<T> GNm, V2<T>& Zm, V2<T>& ZNm) {
   const int mask = 4 * N - 1;
   T c = tab[(m + N) & mask], s = tab[m & mask];
-  // sequence a: (Gm.x - i GNm.x) * (c + i s)
   V2<T> Va{c * Gm.x + s * GNm.x, s * Gm.x - c * GNm.x};
   V2<T> Vb{c * Gm.y + s * GNm.y, s * Gm.y - c * GNm.y};
   Zm = V2<T>{Va.x - Vb.y, Va.y + Vb.x};
-  if (m == 0) {  // G[N] = 0
-    Va = V2<T>{Gm.x, 0};
-    Vb = V2<T>{Gm.y, 0};
-    Zm = V2<T>{Va.x - Vb.y, Va.y + Vb.x};
-  }
   int mm = N - m;
   T c2 = tab[(mm + N) & mask], s2 = tab[mm & mask];
   V2<T> Wa{c2 * GNm.x + s2 * Gm.x, s2 * GNm.x - c2 * Gm.x};
@@ -309,80 +367,172 @@ __device__ __forceinline__ void dct_pre(int N, int m, const T* tab, V2<T> Gm, V2
   ZNm = V2<T>{Wa.x - Wb.y, Wa.y + Wb.x};
 }
 
+// --------------------------------------------------------------------------- face rows
+// DST-II / DCT-II along x of the south and north face data (two dense rows of the free-space
+// right-hand side), one block; out[0..N) = south, out[N..2N) = north, in mode order.
+template <typename T>
+__global__ void k_face_dst(int N, int logN, int dct, const V2<T>* tw, const T* tab, const T* boxg, T* out,
+                           const int* skip) {
+  if (*skip) return;
+  extern __shared__ unsigned char smem_raw[];
+  V2<T>* A = (V2<T>*)smem_raw;
+  V2<T>* B = A + N;
+  const T* gs = boxg + 2 * N;
+  const T* gn = boxg + 3 * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    T a = gs[i], b = gn[i];
+    if (!dct && (i & 1)) { a = -a; b = -b; }
+    A[mk_pos(i, N)] = V2<T>{a, b};
+  }
+  __syncthreads();
+  V2<T>* X = fft_stockham<T>(A, B, 1, N, logN, tw, false);
+  for (int m = threadIdx.x; m <= N / 2; m += blockDim.x) {
+    V2<T> Xm, XNm;
+    dct_post<T>(X, N, m, tab, Xm, XNm);
+    int km = dct ? m : N - 1 - m;
+    out[km] = Xm.x;
+    out[N + km] = Xm.y;
+    if (m > 0 && m < N / 2) {
+      int kNm = dct ? N - m : m - 1;
+      out[kNm] = XNm.x;
+      out[N + kNm] = XNm.y;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------- row transform
+// Sparse forward transform along x of row j (Sec. 4.2: the corrected right-hand side is zero
+// away from irregular nodes and, for free-space box data, the boundary cells):
+//   spec[j][k] = sum_i C[j][i] S_k(i),  S_k(i) = sin(pi (k+1)(2i+1)/(2N)) (DST-II) or
+//   cos(pi k (2i+1)/(2N)) (DCT-II), from the table sin(pi m / (2N)), m mod 4N.
+// The corrections of the row's irregular nodes are formed here from the crossing jumps:
+//   C = sign/h^2 sum_arms (J0 + d J1 + d^2/2 J2), J1, J2 = ([u_x], [u_xx]) on horizontal
+//   arms and ([u_y], [u_yy]) on vertical arms, sign = -1 at an Omega+ node, +1 at Omega-.
+constexpr int ROW_CAP = 512;
+constexpr int ROW_THREADS = 256;  // N <= 4096 gives at most 16 outputs per thread
+
+template <typename T>
+__global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, const int* row_ptr, const IrrNode* irr,
+                                                            const T* J, double inv_h2, const T* boxg,
+                                                            const T* facespec, const T* tab, float scale, T* spec,
+                                                            const int* skip) {
+  if (*skip) return;
+  __shared__ int si[ROW_CAP];
+  __shared__ T sv[ROW_CAP];
+  const int j = blockIdx.x;
+  const int b = row_ptr[j], e = row_ptr[j + 1];
+  const int per = (N + ROW_THREADS - 1) / ROW_THREADS;
+  T acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0;
+  for (int c0 = b; c0 < e; c0 += ROW_CAP) {
+    int cnt = min(ROW_CAP, e - c0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += ROW_THREADS) {
+      const IrrNode& node = irr[c0 + t];
+      T sum = 0;
+      for (int a = 0; a < 4; ++a) {
+        int tg = node.target[a];
+        if (tg < 0) continue;
+        const T* jj = J + (long)tg * 6;
+        T d = irr_d(node, a, T(0));
+        T j1 = a < 2 ? jj[1] : jj[2];
+        T j2 = a < 2 ? jj[3] : jj[4];
+        sum += jj[0] + d * j1 + (T)0.5 * d * d * j2;
+      }
+      si[t] = 2 * node.i + 1;
+      sv[t] = irr_sign(node, T(0)) * (T)inv_h2 * sum;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      if (q >= per) break;
+      int k = threadIdx.x + q * ROW_THREADS;
+      T a = acc[q];
+      if (k < N) {
+        if (dct)
+          for (int t = 0; t < cnt; ++t) a += sv[t] * tsin(tab, k * si[t] + N, N, scale);
+        else
+          for (int t = 0; t < cnt; ++t) a += sv[t] * tsin(tab, (k + 1) * si[t], N, scale);
+      }
+      acc[q] = a;
+    }
+  }
+  T w = 0, ea = 0;
+  const T* face = nullptr;
+  if (boxg != nullptr) {
+    w = boxg[j];
+    ea = boxg[N + j];
+    if (j == 0) face = facespec;
+    else if (j == N - 1) face = facespec + N;
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    if (q >= per) break;
+    int k = threadIdx.x + q * ROW_THREADS;
+    if (k >= N) break;
+    T a = acc[q];
+    if (boxg != nullptr) {
+      if (dct) a += w * tsin(tab, k + N, N, scale) + ea * tsin(tab, k * (2 * N - 1) + N, N, scale);
+      else a += w * tsin(tab, k + 1, N, scale) + ea * tsin(tab, (k + 1) * (2 * N - 1), N, scale);
+      if (face != nullptr) a += face[k];
+    }
+    spec[(long)j * N + k] = a;
+  }
+}
+
 // --------------------------------------------------------------------------- column solve
 // For each column k of spec (x-mode k): forward transform along y, divide by
-// lam_y(l) + lam_x(k) - kappa, inverse transform along y. A block owns CP column pairs;
-// pair p holds columns (k0 + 2p, k0 + 2p + 1) as the real and imaginary parts of one
-// complex FFT. spec is overwritten with the result.
+// lam_y(l) + lam_x(k) - kappa, inverse transform along y, in place. A block owns P column
+// pairs; pair p holds columns (k0 + 2p, k0 + 2p + 1) as the real and imaginary parts of
+// one complex FFT. Two shared buffers alternate between the FFT stages.
 template <typename T>
-__global__ void k_col_solve(int N, int logN, int CP, int dct, const V2<T>* tw, const T* tab, const T* lam,
+__global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, const T* tab, const T* lam,
                             double kappa, T* spec, const int* skip) {
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
-  V2<T>* z = (V2<T>*)smem_raw;
-  const int k0 = blockIdx.x * (2 * CP);
-  const int W = 2 * CP;
-  // load + reorder (+ (-1)^j for DST)
+  V2<T>* A = (V2<T>*)smem_raw;
+  V2<T>* B = A + (long)P * N;
+  const int k0 = blockIdx.x * (2 * P);
+  const int W = 2 * P;
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
     int j = t / W, c = t - j * W;
     T v = spec[(long)j * N + k0 + c];
     if (!dct && (j & 1)) v = -v;
-    int p = c >> 1;
-    T* dst = (T*)&z[(long)p * N + mk_pos(j, N)];
-    dst[c & 1] = v;
+    ((T*)&A[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] = v;
   }
   __syncthreads();
-  fft_dif<T>(z, CP, N, logN, tw, false);
-  // post-process, divide, pre-process; stage through registers because output positions
-  // are read by other threads
-  const int halfN = N >> 1;
-  const int per = (CP * (halfN + 1) + blockDim.x - 1) / blockDim.x;
-  V2<T> outA[8], outB[8];
-  int outP[8], outM[8];
-  int cnt = 0;
-  for (int t = threadIdx.x; t < CP * (halfN + 1); t += blockDim.x) {
-    int p = t / (halfN + 1), m = t - p * (halfN + 1);
-    const V2<T>* zz = z + (long)p * N;
+  V2<T>* X = fft_stockham<T>(A, B, P, N, logN, tw, false);
+  V2<T>* Y = X == A ? B : A;
+  const int half = N >> 1;
+  const T kap = (T)kappa;
+  for (int t = threadIdx.x; t < P * (half + 1); t += blockDim.x) {
+    int p = t / (half + 1), m = t - p * (half + 1);
+    const V2<T>* x = X + (long)p * N;
+    V2<T>* y = Y + (long)p * N;
     V2<T> Xm, XNm;
-    dct_post<T>(zz, N, logN, m, tab, Xm, XNm);
-    T lx0 = lam[k0 + 2 * p], lx1 = lam[k0 + 2 * p + 1];
-    // eigen-mode index along y of DCT-domain index m
-    int lm = dct ? m : N - 1 - m;
-    int lNm = dct ? ((N - m) & (N - 1)) : m - 1;  // for m = 0, N-m = N is not a mode
-    T ly = lam[lm];
-    V2<T> Gm{Xm.x / (ly + lx0 - (T)kappa), Xm.y / (ly + lx1 - (T)kappa)};
+    dct_post<T>(x, N, m, tab, Xm, XNm);
+    T lx0 = lam[k0 + 2 * p] - kap, lx1 = lam[k0 + 2 * p + 1] - kap;
+    T ly = lam[dct ? m : N - 1 - m];
+    V2<T> Gm{Xm.x / (ly + lx0), Xm.y / (ly + lx1)};
     V2<T> GNm{0, 0};
-    if (m > 0) {
-      T ly2 = lam[lNm];
-      GNm = V2<T>{XNm.x / (ly2 + lx0 - (T)kappa), XNm.y / (ly2 + lx1 - (T)kappa)};
+    if (m == half) {
+      GNm = Gm;
+    } else if (m > 0) {
+      T ly2 = lam[dct ? N - m : m - 1];
+      GNm = V2<T>{XNm.x / (ly2 + lx0), XNm.y / (ly2 + lx1)};
     }
-    if (m == halfN) GNm = Gm;
     V2<T> Zm, ZNm;
     dct_pre<T>(N, m, tab, Gm, GNm, Zm, ZNm);
-    if (cnt < 8) {
-      outA[cnt] = Zm;
-      outB[cnt] = ZNm;
-      outP[cnt] = p;
-      outM[cnt] = m;
-    }
-    ++cnt;
-  }
-  (void)per;
-  __syncthreads();
-  for (int q = 0; q < cnt && q < 8; ++q) {
-    V2<T>* zz = z + (long)outP[q] * N;
-    int m = outM[q];
-    zz[m] = outA[q];
-    if (m > 0 && m < halfN) zz[N - m] = outB[q];
+    y[m] = Zm;
+    if (m > 0 && m < half) y[N - m] = ZNm;
   }
   __syncthreads();
-  fft_dif<T>(z, CP, N, logN, tw, true);
+  V2<T>* Z = fft_stockham<T>(Y, X, P, N, logN, tw, true);
   const T invN = (T)1 / (T)N;
   for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
     int j = t / W, c = t - j * W;
-    int p = c >> 1;
-    const T* src = (const T*)&z[(long)p * N + bitrev(mk_pos(j, N), logN)];
-    T v = src[c & 1] * invN;
+    T v = ((const T*)&Z[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] * invN;
     if (!dct && (j & 1)) v = -v;
     spec[(long)j * N + k0 + c] = v;
   }
@@ -390,86 +540,92 @@ __global__ void k_col_solve(int N, int logN, int CP, int dct, const V2<T>* tw, c
 
 // Probe values: inverse transform along x evaluated only at the interpolation points,
 //   u[j][i] = (2/N) sum_k w_k spec[j][k] sin(pi (k+1)(2i+1)/(2N)), w_{N-1} = 1/2  (DST-III)
-//   u[j][i] = (1/N) (spec[j][0] + 2 sum_{k>=1} spec[j][k] cos(pi k (2i+1)/(2N)))  (DCT-III)
-// one block per grid row, one warp per probe of that row.
+//   u[j][i] = (2/N) sum_k w_k spec[j][k] cos(pi k (2i+1)/(2N)), w_0 = 1/2        (DCT-III)
+// one block per grid row that holds probes, one warp per probe.
 template <typename T>
-__global__ void k_probe_values(int N, int dct, const int* prow_ptr, const int* probe_i, const T* spec, const T* tab,
-                               T* pval, const int* skip) {
+__global__ void k_probe_values(int N, int dct, const int* prow_list, const int* prow_ptr, const int* probe_i,
+                               const T* spec, const T* tab, float scale, T* pval, const int* skip) {
   if (*skip) return;
-  int j = blockIdx.x;
-  int b = prow_ptr[j], e = prow_ptr[j + 1];
-  if (b == e) return;
+  const int j = prow_list[blockIdx.x];
+  const int b = prow_ptr[j], e = prow_ptr[j + 1];
   extern __shared__ unsigned char smem_raw[];
   T* row = (T*)smem_raw;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) row[k] = spec[(long)j * N + k];
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    T v = spec[(long)j * N + k];
+    if ((dct && k == 0) || (!dct && k == N - 1)) v *= (T)0.5;
+    row[k] = v;
+  }
   __syncthreads();
   const int mask = 4 * N - 1;
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int q = b + wid; q < e; q += nw) {
-    int m = 2 * probe_i[q] + 1;
+    const int m = 2 * probe_i[q] + 1;
+    const int step = (32 * m) & mask;
+    int idx = dct ? ((lane * m + N) & mask) : (((lane + 1) * m) & mask);
     T acc = 0;
-    if (dct) {
-      for (int k = lane; k < N; k += 32) acc += (k == 0 ? (T)0.5 : (T)1) * row[k] * tab[(k * m + N) & mask];
-    } else {
-      for (int k = lane; k < N; k += 32) acc += (k == N - 1 ? (T)0.5 : (T)1) * row[k] * tab[((k + 1) * m) & mask];
+    for (int k = lane; k < N; k += 32) {
+      acc += row[k] * tsin(tab, idx, N, scale);
+      idx = (idx + step) & mask;
     }
     acc = wsum(acc);
     if (lane == 0) pval[q] = acc * ((T)2 / (T)N);
   }
 }
 
-// Dense transforms along x of row pairs (for grid output and the plain box solve).
-// forward: spec[j][.] = DST-II/DCT-II of rhs[j][.] (rhs float64);
+// Dense transforms along x of row pairs (grid output and the plain box solve).
+// forward: spec[j][.] = DST-II/DCT-II of rhs[j][.] (rhs float64, mode order);
 // inverse: out[j][.] = exact inverse of spec[j][.] (out float64).
 template <typename T>
-__global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* tw, const T* tab,
-                            const double* rhs, T* spec, double* out) {
+__global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* tw, const T* tab, const double* rhs,
+                            T* spec, double* out) {
   extern __shared__ unsigned char smem_raw[];
-  V2<T>* z = (V2<T>*)smem_raw;
-  const int j0 = 2 * blockIdx.x;  // rows j0 (real part), j0+1 (imag part)
-  const int halfN = N >> 1;
+  V2<T>* A = (V2<T>*)smem_raw;
+  V2<T>* B = A + N;
+  const int j0 = 2 * blockIdx.x;  // rows j0 (real part), j0 + 1 (imaginary part)
+  const int half = N >> 1;
   if (!inverse) {
     for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
       int r = t / N, i = t - r * N;
       T v = (T)rhs[(long)(j0 + r) * N + i];
       if (!dct && (i & 1)) v = -v;
-      ((T*)&z[mk_pos(i, N)])[r] = v;
+      ((T*)&A[mk_pos(i, N)])[r] = v;
     }
     __syncthreads();
-    fft_dif<T>(z, 1, N, logN, tw, false);
-    for (int m = threadIdx.x; m <= halfN; m += blockDim.x) {
+    V2<T>* X = fft_stockham<T>(A, B, 1, N, logN, tw, false);
+    for (int m = threadIdx.x; m <= half; m += blockDim.x) {
       V2<T> Xm, XNm;
-      dct_post<T>(z, N, logN, m, tab, Xm, XNm);
-      // DCT index m -> mode (DCT: m; DST: N-1-m)
+      dct_post<T>(X, N, m, tab, Xm, XNm);
       int km = dct ? m : N - 1 - m;
       spec[(long)j0 * N + km] = Xm.x;
       spec[(long)(j0 + 1) * N + km] = Xm.y;
-      if (m > 0 && m < halfN) {
+      if (m > 0 && m < half) {
         int kNm = dct ? N - m : m - 1;
         spec[(long)j0 * N + kNm] = XNm.x;
         spec[(long)(j0 + 1) * N + kNm] = XNm.y;
       }
     }
   } else {
-    for (int m = threadIdx.x; m <= halfN; m += blockDim.x) {
+    for (int m = threadIdx.x; m <= half; m += blockDim.x) {
       int km = dct ? m : N - 1 - m;
       V2<T> Gm{spec[(long)j0 * N + km], spec[(long)(j0 + 1) * N + km]};
       V2<T> GNm{0, 0};
-      if (m > 0) {
+      if (m == half) {
+        GNm = Gm;
+      } else if (m > 0) {
         int kNm = dct ? N - m : m - 1;
         GNm = V2<T>{spec[(long)j0 * N + kNm], spec[(long)(j0 + 1) * N + kNm]};
       }
       V2<T> Zm, ZNm;
       dct_pre<T>(N, m, tab, Gm, GNm, Zm, ZNm);
-      z[m] = Zm;
-      if (m > 0 && m < halfN) z[N - m] = ZNm;
+      A[m] = Zm;
+      if (m > 0 && m < half) A[N - m] = ZNm;
     }
     __syncthreads();
-    fft_dif<T>(z, 1, N, logN, tw, true);
+    V2<T>* Z = fft_stockham<T>(A, B, 1, N, logN, tw, true);
     const T invN = (T)1 / (T)N;
     for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
       int r = t / N, i = t - r * N;
-      T v = ((const T*)&z[bitrev(mk_pos(i, N), logN)])[r] * invN;
+      T v = ((const T*)&Z[mk_pos(i, N)])[r] * invN;
       if (!dct && (i & 1)) v = -v;
       out[(long)(j0 + r) * N + i] = (double)v;
     }
@@ -478,67 +634,75 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
 
 // --------------------------------------------------------------------------- interpolation
 // Per node (Sec. 4.3): b_m = u(q_m) + [q_m in Omega-] C(q_m), v+ = r0.b, grad v+ = (r1.b, r2.b);
-// value (v+ + v-)/2 = v+ - [v]/2; dnormal = n.(grad v+ - [grad v]/2). The result is written as
+// value (v+ + v-)/2 = v+ - [v]/2; dnormal = n.(grad v+ - [grad v]/2). One warp per node,
+// lane m < 6 handles stencil point m. The result is written as
 //   out = a x + b value + c int(x) ds   (a, b, c select the boundary integral operator)
-template <typename T>
-__global__ void k_interp(int n, const Stencil* st, const T* pval, const T* Jn, const double* x_in,
+template <typename T, typename S_t>
+__global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const double* x_in,
                          const double* eps_v, double ca, double cb, double cc, const double* dint, double* out,
                          double* dnormal, const int* skip) {
   if (*skip) return;
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
   if (p >= n) return;
-  const Stencil& S = st[p];
+  const S_t& S = st[p];
   const T* J = Jn ? Jn + (long)p * 6 : nullptr;
   T v = 0, gx = 0, gy = 0;
-  for (int m = 0; m < 6; ++m) {
+  if (lane < 6) {
+    const int m = lane;
     T u = pval[S.probe[m]];
     if (J != nullptr && S.minus[m]) {
       T dx = (T)S.dx[m], dy = (T)S.dy[m];
       u += J[0] + dx * J[1] + dy * J[2] + (T)0.5 * dx * dx * J[3] + dx * dy * J[5] + (T)0.5 * dy * dy * J[4];
     }
-    v += (T)S.r0[m] * u;
-    gx += (T)S.r1[m] * u;
-    gy += (T)S.r2[m] * u;
+    v = (T)S.r0[m] * u;
+    gx = (T)S.r1[m] * u;
+    gy = (T)S.r2[m] * u;
   }
-  double val = (double)v, dn = 0.0;
+  for (int o = 4; o > 0; o >>= 1) {
+    v += __shfl_down_sync(0xffffffffu, v, o);
+    gx += __shfl_down_sync(0xffffffffu, gx, o);
+    gy += __shfl_down_sync(0xffffffffu, gy, o);
+  }
+  if (lane != 0) return;
+  double val = (double)v;
   if (J != nullptr) {
     val -= 0.5 * (double)J[0];
     gx -= (T)0.5 * J[1];
     gy -= (T)0.5 * J[2];
   }
-  dn = S.nx * (double)gx + S.ny * (double)gy;
   double a = eps_v != nullptr ? eps_v[p] : ca;
   double xin = x_in != nullptr ? x_in[p] : 0.0;
   double o = a * xin + cb * val;
   if (dint != nullptr) o += cc * (*dint);
   out[p] = o;
-  if (dnormal != nullptr) dnormal[p] = dn;
+  if (dnormal != nullptr) dnormal[p] = (double)S.nx * (double)gx + (double)S.ny * (double)gy;
 }
 
 // --------------------------------------------------------------------------- host side
 template <typename T>
-static int col_pairs_per_block() {
-  return sizeof(T) == 8 ? 2 : 4;
+static int col_pairs(int N) {
+  int P = sizeof(T) == 8 ? 1 : 2;
+  while (2 * P > N) P /= 2;
+  return P < 1 ? 1 : P;
+}
+
+// one radix-4 item per thread and stage: P N / 4 threads (at least a warp, at most 1024)
+static int col_threads(int N, int P) {
+  int t = P * N / 4;
+  return t < 32 ? 32 : (t > 1024 ? 1024 : t);
 }
 
 template <typename T>
 static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
   const int N = c->N;
-  int CP = col_pairs_per_block<T>();
-  if (2 * CP > N) CP = N / 2;
-  // the register staging in k_col_solve holds at most 8 (m, N-m) pairs per thread
-  while (CP > 1 && CP * (N / 2 + 1) > 8 * 1024) CP /= 2;
-  size_t smem = sizeof(V2<T>) * (size_t)CP * N;
-  const T* tab = sizeof(T) == 8 ? (const T*)c->sintab : (const T*)c->sintab_f;
-  const T* lam = sizeof(T) == 8 ? (const T*)c->lam : (const T*)c->lam_f;
-  const V2<T>* tw = sizeof(T) == 8 ? (const V2<T>*)c->twN : (const V2<T>*)c->twN_f;
-  KFBI_TRY(cudaFuncSetAttribute(k_col_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int threads = 256;
-  while (CP * (N / 2 + 1) > 8 * threads && threads < 1024) threads *= 2;
-  const bool rec = c->timing && c->timing_used < TIMING_CAP;
+  const int P = col_pairs<T>(N);
+  size_t smem = 2 * sizeof(V2<T>) * (size_t)P * N;
+  const bool rec = c->timing && !c->capturing && c->timing_used < TIMING_CAP;
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
-  k_col_solve<T><<<N / (2 * CP), threads, smem, c->stream>>>(N, c->logN, CP, c->boxbc == KFBI_BOX_NEUMANN0, tw,
-                                                            tab, lam, c->kappa, spec, skip);
+  k_col_solve<T><<<N / (2 * P), col_threads(N, P), smem, c->stream>>>(N, c->logN, P, c->boxbc == KFBI_BOX_NEUMANN0,
+                                                                  Tabs<T>::stw(c), Tabs<T>::sin(c), Tabs<T>::lam(c),
+                                                                  c->kappa, spec, skip);
   launched(c, 1);
   if (rec) {
     KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used + 1], c->stream));
@@ -549,82 +713,150 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
 }
 
 template <typename T>
+static kfbi_status launch_row_dense(kfbi_ctx* c, int inverse, const double* rhs, T* spec, double* out) {
+  const int N = c->N;
+  size_t smem = 2 * sizeof(V2<T>) * (size_t)N;
+  k_row_dense<T><<<N / 2, 256, smem, c->stream>>>(N, c->logN, c->boxbc == KFBI_BOX_NEUMANN0, inverse, Tabs<T>::stw(c),
+                                                 Tabs<T>::sin(c), rhs, spec, out);
+  launched(c, 1);
+  return KFBI_OK;
+}
+
+template <typename T>
 static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double* values, double* dnormal,
-                           double* grid, int bie_kind, const double* eps_v, const int* skip) {
+                           double* grid, int bie_kind, const double* eps_v, const int* skip, const float* density_f) {
+  const long long l0 = c->launches;
+  using T4 = typename std::conditional<sizeof(T) == 8, double4_32a, float4>::type;
   cudaStream_t s = c->stream;
-  const int N = c->N, n = c->n, ncr = c->n_cross, ntg = ncr + n;
-  const bool dct = c->boxbc == KFBI_BOX_NEUMANN0;
-  const T* tab = sizeof(T) == 8 ? (const T*)c->sintab : (const T*)c->sintab_f;
+  const int N = c->N, n = c->n, ncr = c->n_cross;
+  const int dct = c->boxbc == KFBI_BOX_NEUMANN0;
+  const bool fs = c->boxbc == KFBI_BOX_FREESPACE_DL;
+  const T* tab = Tabs<T>::sin(c);
   V2<T>* coef = (V2<T>*)c->dcoef;
-  T* J = (T*)c->jumps;
-  T* cval = (T*)c->cval;
   T* boxg = (T*)c->boxg;
+  T* face = (T*)c->facespec;
   T* spec = (T*)c->spec;
+  T* J = (T*)c->jumps;
   T* pval = (T*)c->probe_val;
   const int nk = n / 2 + 1;
-  bool want_int = bie_kind == KFBI_BIE_HS_EXTERIOR_MDL;
-  launched(c, 5 + (c->n_irr > 0) + (c->boxbc == KFBI_BOX_FREESPACE_DL) + (grid != nullptr));  // col solve counts itself
-  k_dens_coef<T><<<cdiv((long)nk * 32, 256), 256, 0, s>>>(density, n, (const double2*)c->twn, c->stencil, coef,
-                                                          want_int ? c->dint : nullptr, skip);
-  k_target_jumps<T><<<cdiv((long)ntg * 32, 256), 256, 0, s>>>(coef, n, ntg, c->tgeo, layer, c->kappa, J, skip);
-  if (c->n_irr > 0)
-    k_corrections<T><<<cdiv(c->n_irr, 256), 256, 0, s>>>(c->n_irr, c->irr, J, 1.0 / (c->h * c->h), cval, skip);
-  bool fs = c->boxbc == KFBI_BOX_FREESPACE_DL;
-  if (fs)
-    k_box_data<T><<<cdiv((long)4 * N * 32, 256), 256, 0, s>>>(density, n, c->xy, c->tgeo + ncr, N, c->xmin, c->xmax,
-                                                              c->ymin, c->ymax, c->h, boxg, skip);
-  dim3 g1(cdiv(N, 256), N);
-  size_t sm1 = 1024 * (sizeof(int) + sizeof(T));
-  k_row_forward<T><<<g1, 256, sm1, s>>>(N, dct, c->row_ptr, c->irr, cval, fs ? boxg : nullptr, tab, spec, skip);
-  KFBI_CHECK(launch_col_solve<T>(c, spec, skip));
-  size_t sm2 = sizeof(T) * N;
-  k_probe_values<T><<<N, 256, sm2, s>>>(N, dct, c->prow_ptr, c->probe_i, spec, tab, pval, skip);
-  if (grid != nullptr) {
-    size_t sm3 = sizeof(V2<T>) * N;
-    const V2<T>* tw = sizeof(T) == 8 ? (const V2<T>*)c->twN : (const V2<T>*)c->twN_f;
-    KFBI_TRY(cudaFuncSetAttribute(k_row_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    k_row_dense<T><<<N / 2, 256, sm3, s>>>(N, c->logN, dct, 1, tw, tab, nullptr, spec, grid);
+  const bool want_int = bie_kind == KFBI_BIE_HS_EXTERIOR_MDL;
+  const float scale = (float)(PI / (2.0 * N));
+  // the density in the grid precision (float32 inner applies use the caller's float copy or
+  // convert it here once)
+  const T* dens_t;
+  if (sizeof(T) == 4) {
+    if (density_f == nullptr) {
+      k_to_float<<<cdiv(n, 256), 256, 0, s>>>(density, c->dens_f, n, skip);
+      launched(c, 1);
+      density_f = c->dens_f;
+    }
+    dens_t = (const T*)density_f;
+  } else {
+    dens_t = (const T*)density;
   }
+  if (fs) {
+    // the box quadrature and its face transform depend only on the density: they run on the
+    // side stream while the coefficients and jumps are formed, and join before the row transform
+    cudaStream_t s2 = c->aux;
+    KFBI_TRY(cudaEventRecord(c->ev_fork, s));
+    KFBI_TRY(cudaStreamWaitEvent(s2, c->ev_fork, 0));
+    const size_t smb = (size_t)n * sizeof(T4);
+    if (smb <= SMEM_STAGE_MAX)
+      k_box_data<T, T4, true><<<cdiv((long)4 * N * 32, 256), 256, smb, s2>>>(
+          dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, boxg, skip);
+    else
+      k_box_data<T, T4, false><<<cdiv((long)4 * N * 32, 256), 256, 0, s2>>>(
+          dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, boxg, skip);
+    size_t smf = 2 * sizeof(V2<T>) * (size_t)N;
+    k_face_dst<T><<<1, 256, smf, s2>>>(N, c->logN, dct, Tabs<T>::stw(c), tab, boxg, face, skip);
+    KFBI_TRY(cudaEventRecord(c->ev_join, s2));
+    launched(c, 2);
+  }
+  const size_t smd = (size_t)n * (sizeof(V2<T>) + sizeof(T));
+  if (smd <= SMEM_STAGE_MAX) {
+    k_dens_coef<T, true><<<cdiv((long)nk * 32, 256), 256, smd, s>>>(dens_t, density, n, Tabs<T>::twn(c), c->stencil,
+                                                                    coef, want_int ? c->dint : nullptr, skip);
+  } else {
+    k_dens_coef<T, false><<<cdiv((long)nk * 32, 256), 256, 0, s>>>(dens_t, density, n, Tabs<T>::twn(c), c->stencil,
+                                                                   coef, want_int ? c->dint : nullptr, skip);
+  }
+  const int ntg = ncr + n;
+  using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
+  const size_t smj = (size_t)nk * sizeof(V2<T>);
+  if (smj <= SMEM_STAGE_MAX)
+    k_target_jumps<T, G, true><<<cdiv((long)ntg * 32, 256), 256, smj, s>>>(coef, n, ntg, Tabs<T>::geo(c),
+                                                                          Tabs<T>::tstart(c), layer, c->kappa, J, skip);
+  else
+    k_target_jumps<T, G, false><<<cdiv((long)ntg * 32, 256), 256, 0, s>>>(coef, n, ntg, Tabs<T>::geo(c),
+                                                                         Tabs<T>::tstart(c), layer, c->kappa, J, skip);
+  launched(c, 2);
+  if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
+  k_row_forward<T><<<N, ROW_THREADS, 0, s>>>(N, dct, c->row_ptr, c->irr, J, 1.0 / (c->h * c->h), fs ? boxg : nullptr,
+                                             face, tab, scale, spec, skip);
+  launched(c, 1);
+  KFBI_CHECK(launch_col_solve<T>(c, spec, skip));
+  if (c->n_prow > 0) {
+    k_probe_values<T><<<c->n_prow, 256, sizeof(T) * (size_t)N, s>>>(N, dct, c->prow_list, c->prow_ptr, c->probe_i,
+                                                                     spec, tab, scale, pval, skip);
+    launched(c, 1);
+  }
+  if (grid != nullptr) KFBI_CHECK(launch_row_dense<T>(c, 1, nullptr, spec, grid));
   double ca = 0.0, cb = 1.0, cc = 0.0;
   const double* ev = nullptr;
   const double* xin = nullptr;
   if (bie_kind == KFBI_BIE_INTERIOR_DL) { ca = 0.5; xin = density; }
   else if (bie_kind == KFBI_BIE_HS_EXTERIOR_MDL) { ca = -0.5; cc = 1.0; xin = density; }
   else if (bie_kind == KFBI_BIE_STEFAN_SL) { cb = -1.0; ev = eps_v; xin = density; }
-  k_interp<T><<<cdiv(n, 128), 128, 0, s>>>(n, c->stencil, pval, J + (long)ncr * 6, xin, ev, ca, cb, cc,
-                                           want_int ? c->dint : nullptr, values, dnormal, skip);
+  k_interp<T><<<cdiv((long)n * 32, 256), 256, 0, s>>>(n, Tabs<T>::stencil(c), pval, J + (long)ncr * 6, xin, ev, ca, cb,
+                                                      cc, want_int ? c->dint : nullptr, values, dnormal, skip);
+  launched(c, 1);
+  c->per_apply_launches[sizeof(T) == 4 ? 1 : 0] = (int)(c->launches - l0);
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
+}
+
+// shared-memory limits of the kernels whose dynamic shared memory may exceed 48 KB, set once
+// per context for its N and node capacity (no attribute calls during graph capture)
+template <typename T>
+static kfbi_status setup_t(kfbi_ctx* c) {
+  const int N = c->N;
+  int col = (int)(2 * sizeof(V2<T>) * (size_t)col_pairs<T>(N) * N);
+  int row = (int)(2 * sizeof(V2<T>) * (size_t)N);
+  using T4 = typename std::conditional<sizeof(T) == 8, double4_32a, float4>::type;
+  using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
+  auto clampm = [](size_t b) { return (int)(b > SMEM_STAGE_MAX ? SMEM_STAGE_MAX : b); };
+  int dens = clampm((size_t)c->max_nodes * (sizeof(V2<T>) + sizeof(T)));
+  int box = clampm((size_t)c->max_nodes * sizeof(T4));
+  int jmp = clampm(((size_t)c->max_nodes / 2 + 1) * sizeof(V2<T>));
+  KFBI_TRY(cudaFuncSetAttribute(k_col_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, col));
+  KFBI_TRY(cudaFuncSetAttribute(k_row_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
+  KFBI_TRY(cudaFuncSetAttribute(k_face_dst<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
+  KFBI_TRY(cudaFuncSetAttribute(k_dens_coef<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dens));
+  KFBI_TRY(cudaFuncSetAttribute(k_box_data<T, T4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, box));
+  KFBI_TRY(cudaFuncSetAttribute(k_target_jumps<T, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, jmp));
+  return KFBI_OK;
+}
+
+kfbi_status apply_setup_attributes(kfbi_ctx* c) {
+  KFBI_CHECK(setup_t<double>(c));
+  return setup_t<float>(c);
 }
 
 // bie_kind < 0: plain layer potential
 kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* density, double* values, double* dnormal,
-                          double* grid, int bie_kind, const double* eps_v, const int* skip) {
+                          double* grid, int bie_kind, const double* eps_v, const int* skip, const float* density_f) {
   if (skip == nullptr) skip = c->zero_flag;
-  if (fp32) return apply_t<float>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip);
-  return apply_t<double>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip);
-}
-
-template <typename T>
-static kfbi_status grid_solve_t(kfbi_ctx* c, const double* rhs, double* u) {
-  cudaStream_t s = c->stream;
-  const int N = c->N;
-  const bool dct = c->boxbc == KFBI_BOX_NEUMANN0;
-  const T* tab = sizeof(T) == 8 ? (const T*)c->sintab : (const T*)c->sintab_f;
-  const V2<T>* tw = sizeof(T) == 8 ? (const V2<T>*)c->twN : (const V2<T>*)c->twN_f;
-  T* spec = (T*)c->spec;
-  size_t sm3 = sizeof(V2<T>) * N;
-  KFBI_TRY(cudaFuncSetAttribute(k_row_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-  k_row_dense<T><<<N / 2, 256, sm3, s>>>(N, c->logN, dct, 0, tw, tab, rhs, spec, nullptr);
-  launched(c, 2);
-  KFBI_CHECK(launch_col_solve<T>(c, spec, c->zero_flag));
-  k_row_dense<T><<<N / 2, 256, sm3, s>>>(N, c->logN, dct, 1, tw, tab, nullptr, spec, u);
-  KFBI_TRY(cudaGetLastError());
-  return KFBI_OK;
+  if (fp32) return apply_t<float>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip, density_f);
+  return apply_t<double>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip, nullptr);
 }
 
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u) {
-  return grid_solve_t<double>(c, rhs, u);
+  double* spec = c->spec;
+  KFBI_CHECK(launch_row_dense<double>(c, 0, rhs, spec, nullptr));
+  KFBI_CHECK(launch_col_solve<double>(c, spec, c->zero_flag));
+  KFBI_CHECK(launch_row_dense<double>(c, 1, nullptr, spec, u));
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
 }
 
 // gather a dense grid at the probes, then interpolate with zero jumps
@@ -639,8 +871,8 @@ kfbi_status interp_grid_enqueue(kfbi_ctx* c, const double* grid, double* values)
   double* pval = c->probe_val;
   launched(c, 2);
   k_gather_probes<<<c->N, 128, 0, s>>>(c->N, c->prow_ptr, c->probe_i, grid, pval);
-  k_interp<double><<<cdiv(c->n, 128), 128, 0, s>>>(c->n, c->stencil, pval, nullptr, nullptr, nullptr, 0.0, 1.0, 0.0,
-                                                    nullptr, values, nullptr, c->zero_flag);
+  k_interp<double><<<cdiv((long)c->n * 32, 256), 256, 0, s>>>(c->n, c->stencil, pval, nullptr, nullptr, nullptr, 0.0,
+                                                               1.0, 0.0, nullptr, values, nullptr, c->zero_flag);
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
 }
@@ -650,26 +882,42 @@ kfbi_status interp_grid_enqueue(kfbi_ctx* c, const double* grid, double* values)
 // allocate device memory (see include/kfbi.h). Its scratch lives in one file-scope device
 // array: one slot holding the column kernel's skip flag (cleared by every call before the
 // kernel reads it), then the spectral grid (N^2), the sine table (4N), the eigenvalues (N) and
-// the FFT twiddles (N). Every call rewrites all of it before reading it. The array is shared
+// the staged FFT twiddles (2N). Every call rewrites all of it before reading it. The array is shared
 // by every call in the process.
 constexpr int NOALLOC_MAX_N = 512;
 constexpr size_t NOALLOC_HEAD = 32;  // doubles reserved for flags, keeps the grid 256-byte aligned
-constexpr size_t NOALLOC_DOUBLES = NOALLOC_HEAD + (size_t)NOALLOC_MAX_N * NOALLOC_MAX_N + 6 * (size_t)NOALLOC_MAX_N;
+constexpr size_t NOALLOC_DOUBLES = NOALLOC_HEAD + (size_t)NOALLOC_MAX_N * NOALLOC_MAX_N + 8 * (size_t)NOALLOC_MAX_N;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
-__global__ void k_noalloc_tables(int N, double h, int neumann, double* tab, double* lam, double* tw, int* flag) {
+// staged Stockham twiddle t (layout of fft_stockham): w^{r jm N / (4 Ns)} = e^{-i pi r jm / (2 Ns)}
+__device__ bool staged_twiddle(int N, int logN, int t, double* re, double* im) {
+  int off = 0;
+  for (int Ns = (logN & 1) ? 2 : 1; Ns < N; Ns <<= 2) {
+    if (t < off + 3 * Ns) {
+      int r = (t - off) / Ns + 1, jm = (t - off) % Ns;
+      double sn, cs;
+      sincospi((double)(r * jm) / (2.0 * Ns), &sn, &cs);
+      *re = cs;
+      *im = -sn;
+      return true;
+    }
+    off += 3 * Ns;
+  }
+  return false;
+}
+
+__global__ void k_noalloc_tables(int N, int logN, double h, int neumann, double* tab, double* lam, double* tw,
+                                 int* flag) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m == 0) *flag = 0;
   if (m < 4 * N) tab[m] = sinpi((double)m / (2.0 * N));
   if (m < N) {
     double sk = sinpi(((double)m + (neumann ? 0.0 : 1.0)) / (2.0 * N));
     lam[m] = -4.0 * sk * sk / (h * h);
-  }
-  if (m < N / 2) {
-    double sn, cs;
-    sincospi(2.0 * (double)m / (double)N, &sn, &cs);
-    tw[2 * m] = cs;
-    tw[2 * m + 1] = -sn;
+    double re = 0.0, im = 0.0;
+    staged_twiddle(N, logN, m, &re, &im);
+    tw[2 * m] = re;
+    tw[2 * m + 1] = im;
   }
 }
 
@@ -710,16 +958,13 @@ static kfbi_status grid_solve_noalloc_impl(int N, double h, double kappa, int bo
   double* tw = lam + N;
   const int logN = ilog2(N);
   const int dct = boxbc == KFBI_BOX_NEUMANN0;
-  k_noalloc_tables<<<cdiv(4L * N, 256), 256, 0, s>>>(N, h, dct, tab, lam, tw, flag);
-  size_t sm_row = sizeof(V2<double>) * N;
+  k_noalloc_tables<<<cdiv(4L * N, 256), 256, 0, s>>>(N, logN, h, dct, tab, lam, tw, flag);
+  size_t sm_row = 2 * sizeof(V2<double>) * N;  // <= 16 KB for N <= 512
   k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 0, (const V2<double>*)tw, tab, rhs, spec, nullptr);
-  int CP = 2;
-  if (2 * CP > N) CP = N / 2;
-  int threads = 256;
-  while (CP * (N / 2 + 1) > 8 * threads && threads < 1024) threads *= 2;
-  size_t sm_col = sizeof(V2<double>) * (size_t)CP * N;
-  k_col_solve<double><<<N / (2 * CP), threads, sm_col, s>>>(N, logN, CP, dct, (const V2<double>*)tw, tab, lam, kappa,
-                                                             spec, flag);
+  const int P = col_pairs<double>(N);
+  size_t sm_col = 2 * sizeof(V2<double>) * (size_t)P * N;  // <= 16 KB for N <= 512
+  k_col_solve<double><<<N / (2 * P), col_threads(N, P), sm_col, s>>>(N, logN, P, dct, (const V2<double>*)tw, tab, lam,
+                                                                  kappa, spec, flag);
   k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 1, (const V2<double>*)tw, tab, nullptr, spec, u);
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;

@@ -54,13 +54,14 @@ __device__ __forceinline__ TrigSums trig_warp(const double2* c, int n, double al
   return TrigSums{f, f1, f2};
 }
 
-// twiddles e^{2 pi i m / n}
-__global__ void k_twiddles_n(int n, double2* tw) {
+// twiddles e^{2 pi i m / n} in float64 and float32
+__global__ void k_twiddles_n(int n, double2* tw, float2* tw_f) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
   double s, c;
   sincospi(2.0 * (double)m / (double)n, &s, &c);
   tw[m] = make_double2(c, s);
+  tw_f[m] = make_float2((float)c, (float)s);
 }
 
 // c_k = (1/n) sum_j f_j e^{-2 pi i k j / n}, k = 0..n/2, for `nf` functions stored with
@@ -312,6 +313,9 @@ __global__ void k_irr_emit(int N, double xmin, double ymin, double h, const uint
         node.target[3] = c;
         node.d[3] = grid_coord(ymin, h, j + 1) - cr_xi[c];
       }
+      for (int a = 0; a < 4; ++a) node.df[a] = (float)node.d[a];
+      node.signf = (float)node.sign;
+      node.pad = 0;
       irr[slot] = node;
     }
     base += __popc(mask);
@@ -319,7 +323,11 @@ __global__ void k_irr_emit(int N, double xmin, double ymin, double h, const uint
 }
 
 // geometry at every target (crossings, then nodes) and the inverse 3x3 jump matrix
-__global__ void k_target_geo(const double2* coef, int n, int ncr, const double* cr_alpha, TargetGeo* tg) {
+// Also stores, per target, the twiddle starts of the per-apply density evaluation: lane l's
+// e^{i k0_l alpha} (k0_l = 1 + l chunk, chunk = ceil(K / 32)), then e^{i alpha} and
+// e^{i n alpha / 2}, in float64 and float32.
+__global__ void k_target_geo(const double2* coef, int n, int ncr, const double* cr_alpha, TargetGeo* tg,
+                             TargetGeoF* tg_f, double2* tstart, float2* tstart_f) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= ncr + n) return;
@@ -327,6 +335,23 @@ __global__ void k_target_geo(const double2* coef, int n, int ncr, const double* 
   double a = warp < ncr ? cr_alpha[warp] : (TWO_PI * (double)(warp - ncr)) / (double)n;
   TrigSums x = trig_warp(coef, n, a, lane, true);
   TrigSums y = trig_warp(coef + nk, n, a, lane, true);
+  {
+    const int K = (n - 1) / 2;
+    const int chunk = (K + 31) / 32;
+    double sn, cs;
+    sincos((double)(1 + lane * chunk) * a, &sn, &cs);
+    long base = (long)warp * TSTART_STRIDE;
+    tstart[base + lane] = make_double2(cs, sn);
+    tstart_f[base + lane] = make_float2((float)cs, (float)sn);
+    if (lane == 0) {
+      sincos(a, &sn, &cs);
+      tstart[base + 32] = make_double2(cs, sn);
+      tstart_f[base + 32] = make_float2((float)cs, (float)sn);
+      sincos(0.5 * (double)n * a, &sn, &cs);
+      tstart[base + 33] = make_double2(cs, sn);
+      tstart_f[base + 33] = make_float2((float)cs, (float)sn);
+    }
+  }
   if (lane != 0) return;
   TargetGeo g;
   g.alpha = a;
@@ -348,11 +373,18 @@ __global__ void k_target_geo(const double2* coef, int n, int ncr, const double* 
   g.A3i[3] = c01 * id; g.A3i[4] = c11 * id; g.A3i[5] = c21 * id;
   g.A3i[6] = c02 * id; g.A3i[7] = c12 * id; g.A3i[8] = c22 * id;
   tg[warp] = g;
+  TargetGeoF f;
+  f.alpha = (float)g.alpha;
+  f.xa = (float)g.xa; f.ya = (float)g.ya; f.xaa = (float)g.xaa; f.yaa = (float)g.yaa;
+  f.sa = (float)g.sa; f.saa = (float)g.saa;
+  for (int q = 0; q < 9; ++q) f.A3i[q] = (float)g.A3i[q];
+  tg_f[warp] = f;
 }
 
 // 6-point stencil per node: closest node, d1/d2, sides, scaled 6x6 LU -> inverse rows 0..2
 __global__ void k_stencil(int n, const double* xy, double xmin, double ymin, double h, int N, const uint8_t* side,
                           const TargetGeo* tg_nodes, Stencil* st, int* probe_mark, int* flags) {
+  // (the float32 copy is written by k_stencil_map once the probe ids are final)
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   double px = xy[2 * p], py = xy[2 * p + 1];
@@ -373,7 +405,8 @@ __global__ void k_stencil(int n, const double* xy, double xmin, double ymin, dou
       qi = 0;
       qj = 0;
     }
-    S.probe[m] = qj * N + qi;  // temporarily the flat grid index
+    S.q[m] = qj * N + qi;
+    S.probe[m] = qj * N + qi;  // the flat grid index until the probes are numbered
     S.minus[m] = side[(long)qj * N + qi] == 0 ? 1 : 0;
     S.dx[m] = __dsub_rn(grid_coord(xmin, h, qi), px);
     S.dy[m] = __dsub_rn(grid_coord(ymin, h, qj), py);
@@ -458,10 +491,53 @@ __global__ void k_probe_emit(int N, int* probe_mark, const int* prow_ptr, int* p
   }
 }
 
-__global__ void k_stencil_map(int n, const int* probe_mark, Stencil* st) {
+__global__ void k_stencil_map(int n, const int* probe_mark, Stencil* st, StencilF* stf) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  for (int m = 0; m < 6; ++m) st[p].probe[m] = probe_mark[st[p].probe[m]] - 1;
+  Stencil S = st[p];
+  StencilF F;
+  for (int m = 0; m < 6; ++m) {
+    S.probe[m] = probe_mark[S.probe[m]] - 1;
+    F.q[m] = S.q[m];
+    F.probe[m] = S.probe[m];
+    F.minus[m] = S.minus[m];
+    F.dx[m] = (float)S.dx[m];
+    F.dy[m] = (float)S.dy[m];
+    F.r0[m] = (float)S.r0[m];
+    F.r1[m] = (float)S.r1[m];
+    F.r2[m] = (float)S.r2[m];
+  }
+  F.nx = (float)S.nx;
+  F.ny = (float)S.ny;
+  st[p] = S;
+  stf[p] = F;
+}
+
+// packed node data (x, y, y_a, -x_a) for the free-space box quadrature
+__global__ void k_npack(int n, const double* xy, const TargetGeo* tg_nodes, double4_32a* np, float4* np_f) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double4_32a v;
+  v.x = xy[2 * p];
+  v.y = xy[2 * p + 1];
+  v.z = tg_nodes[p].ya;
+  v.w = -tg_nodes[p].xa;
+  np[p] = v;
+  np_f[p] = make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
+}
+
+// rows that hold at least one interpolation probe, in order; count in *cnt (one warp)
+__global__ void k_prow_list(int N, const int* prow_cnt, int* list, int* cnt) {
+  int lane = threadIdx.x & 31;
+  int base = 0;
+  for (int j0 = 0; j0 < N; j0 += 32) {
+    int j = j0 + lane;
+    bool on = j < N && prow_cnt[j] > 0;
+    unsigned mask = __ballot_sync(0xffffffffu, on);
+    if (on) list[base + __popc(mask & ((1u << lane) - 1u))] = j;
+    base += __popc(mask);
+  }
+  if (lane == 0) *cnt = base;
 }
 
 // --------------------------------------------------------------------------- host driver
@@ -480,7 +556,7 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   KFBI_TRY(cudaMemsetAsync(c->vcount, 0, NN * sizeof(int), s));
   KFBI_TRY(cudaMemsetAsync(c->probe_mark, 0, NN * sizeof(int), s));
 
-  k_twiddles_n<<<cdiv(n, 256), 256, 0, s>>>(n, (double2*)c->twn);
+  k_twiddles_n<<<cdiv(n, 256), 256, 0, s>>>(n, (double2*)c->twn, (float2*)c->twn_f);
   launched(c, 5);
   k_dft_real<<<cdiv((long)2 * nk * 32, 256), 256, 0, s>>>(c->xy, 2, 2, n, (const double2*)c->twn,
                                                           (double2*)c->icoef);
@@ -525,22 +601,29 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   k_irr_emit<<<wblocks, 256, 0, s>>>(N, c->xmin, c->ymin, h, c->side, c->hcount, c->vcount, c->hid, c->vid,
                                      c->cr_xi, c->row_ptr, c->irr);
   k_target_geo<<<cdiv((long)(ncr + n) * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, ncr, c->cr_alpha,
-                                                               c->tgeo);
+                                                               c->tgeo, c->tgeo_f, (double2*)c->tstart,
+                                                               (float2*)c->tstart_f);
   k_stencil<<<cdiv(n, 128), 128, 0, s>>>(n, c->xy, c->xmin, c->ymin, h, N, c->side, c->tgeo + ncr, c->stencil,
                                          c->probe_mark, c->flags);
   k_probe_count<<<wblocks, 256, 0, s>>>(N, c->probe_mark, c->prow_cnt);
   k_scan<<<1, 1024, 0, s>>>(c->prow_cnt, c->prow_ptr, N);
   k_probe_emit<<<wblocks, 256, 0, s>>>(N, c->probe_mark, c->prow_ptr, c->probe_i);
-  k_stencil_map<<<cdiv(n, 128), 128, 0, s>>>(n, c->probe_mark, c->stencil);
+  k_stencil_map<<<cdiv(n, 128), 128, 0, s>>>(n, c->probe_mark, c->stencil, c->stencil_f);
+  k_npack<<<cdiv(n, 128), 128, 0, s>>>(n, c->xy, c->tgeo + ncr, (double4_32a*)c->npack, (float4*)c->npack_f);
+  k_prow_list<<<1, 32, 0, s>>>(N, c->prow_cnt, c->prow_list, c->counts);
+  launched(c, 2);
   KFBI_TRY(cudaGetLastError());
   KFBI_TRY(cudaMemcpyAsync(&c->host_counts[0], c->prow_ptr + N, sizeof(int), cudaMemcpyDeviceToHost, s));
   KFBI_TRY(cudaMemcpyAsync(&c->host_counts[1], c->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  KFBI_TRY(cudaMemcpyAsync(&c->host_counts[2], c->counts, sizeof(int), cudaMemcpyDeviceToHost, s));
   KFBI_TRY(cudaStreamSynchronize(s));
   if (c->host_counts[1] & FLAG_OUTSIDE) return KFBI_ERR_OUTSIDE_BOX;
   if (c->host_counts[1] & FLAG_UNDERRES) return KFBI_ERR_UNDERRESOLVED;
   c->n_probe = c->host_counts[0];
+  c->n_prow = c->host_counts[2];
   c->n = n;
   c->have_iface = true;
+  c->iface_version += 1;
   return KFBI_OK;
 }
 

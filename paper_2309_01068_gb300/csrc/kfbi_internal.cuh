@@ -36,6 +36,7 @@ constexpr double NEWTON_TOL = 1e-15;
 constexpr double BOX_MARGIN = 3.0;   // interface must stay 3h inside the box
 constexpr int MAX_RESTART = 200;
 constexpr int TIMING_CAP = 8192;
+constexpr int TSTART_STRIDE = 34;  // per target: 32 lane start twiddles, e^{i alpha}, e^{i n alpha / 2}
 
 // device error flags (bitmask in Iface::flags)
 enum : int { FLAG_OUTSIDE = 1, FLAG_UNDERRES = 2, FLAG_CAPACITY = 4 };
@@ -47,22 +48,43 @@ struct TargetGeo {
   double A3i[9];  // inverse of the 3x3 second-jump matrix (App. A.1), row-major
 };
 
+// float32 copy of the per-target geometry for the float32 kernels
+struct TargetGeoF {
+  float alpha;
+  float xa, ya, xaa, yaa, sa, saa;
+  float A3i[9];
+};
+
 // one irregular node and its (up to) four crossed arms: W, E, S, N
 struct IrrNode {
   int i, j;
   int target[4];   // crossing index per arm, -1 if the arm is not crossed
   double d[4];     // neighbour minus crossing along the arm
   double sign;     // -1 for an Omega+ node, +1 for Omega- (times 1/h^2 applied later)
+  float df[4];     // float32 copies of d and sign
+  float signf;
+  int pad;
 };
 
 // one interface node's interpolation stencil (Sec. 4.3)
 struct Stencil {
+  int q[6];        // flat grid index j * N + i of each point
   int probe[6];    // index into the probe-value array
   int minus[6];    // 1 if the point is in Omega-
   double dx[6], dy[6];
   double r0[6], r1[6], r2[6];  // rows 0..2 of the inverse 6x6 matrix (value, d/dx, d/dy)
   double nx, ny;   // unit outward normal at the node
   double w;        // s_alpha * 2 pi / n (trapezoidal arclength weight)
+};
+
+// float32 copy of a stencil for the float32 interpolation
+struct StencilF {
+  int q[6];
+  int probe[6];
+  int minus[6];
+  float dx[6], dy[6];
+  float r0[6], r1[6], r2[6];
+  float nx, ny;
 };
 
 // GMRES control block in device memory. The scalar header comes first so that the host
@@ -81,6 +103,7 @@ struct GmresCtl {
   int ticket;       // last-block ticket for reductions
   int breakdown;
   int trust;        // finish on the Givens estimate without a true-residual apply
+  int bodies;       // bodies executed (bounded by the loop cap)
   double tol, bnorm, beta, hnorm, res_est;
   double g[MAX_RESTART + 1];
   double cs[MAX_RESTART], sn[MAX_RESTART];
@@ -99,13 +122,19 @@ struct kfbi_ctx {
   double kappa = 0;
   int boxbc = 0, precision = 0, max_nodes = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;   // side stream for work independent of the main chain
+  cudaStream_t own = nullptr;   // the context's stream when the caller uses a default stream
+  cudaStream_t user = nullptr;  // the stream set by the caller
+  bool user_default = true;     // caller's stream is the legacy or per-thread default stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // constant tables
   double* sintab = nullptr;   // [4N] sin(pi m / (2N))
   float* sintab_f = nullptr;
   double* lam = nullptr;      // [N] 1-D eigenvalues of the box operator
   float* lam_f = nullptr;
-  double* twN = nullptr;      // [N] complex: e^{-2 pi i m / N}, m < N/2
+  double* twN = nullptr;      // [N] complex: e^{-2 pi i m / N}, m < N
   float* twN_f = nullptr;
 
   // interface
@@ -115,6 +144,13 @@ struct kfbi_ctx {
   int cap_cross = 0, cap_irr = 0;
   double* xy = nullptr;         // [max_nodes][2]
   double* twn = nullptr;        // [max_nodes] complex e^{2 pi i m / n}
+  float* twn_f = nullptr;       // the same in float32
+  double* tstart = nullptr;     // [cap_cross + max_nodes][TSTART_STRIDE] complex twiddle starts
+  float* tstart_f = nullptr;
+  double* npack = nullptr;      // [max_nodes] double4 (x, y, y_a, -x_a) for the box quadrature
+  float* npack_f = nullptr;     // float4 copy
+  int* prow_list = nullptr;     // [N] rows that hold interpolation probes
+  int n_prow = 0;
   double* icoef = nullptr;      // [2][max_nodes/2+1] complex Fourier coefficients of x, y
   double* fine = nullptr;       // [SUBSAMPLES*max_nodes][2]
   int* seg_count = nullptr;     // [2*M + 1]
@@ -126,6 +162,7 @@ struct kfbi_ctx {
   double* cr_alpha = nullptr;
   double* cr_xi = nullptr;
   kfbi::TargetGeo* tgeo = nullptr;  // [cap_cross + max_nodes]
+  kfbi::TargetGeoF* tgeo_f = nullptr;
   int* hcount = nullptr;        // [N][N] crossings per horizontal arm (i-1,j)-(i,j)
   int* vcount = nullptr;        // [N][N] crossings per vertical arm (i,j-1)-(i,j)
   int* hid = nullptr;           // [N][N] crossing index on the arm (if exactly one)
@@ -135,6 +172,10 @@ struct kfbi_ctx {
   int* row_ptr = nullptr;       // [N + 1]
   kfbi::IrrNode* irr = nullptr; // [cap_irr]
   kfbi::Stencil* stencil = nullptr;  // [max_nodes]
+  kfbi::StencilF* stencil_f = nullptr;
+  float* dens_f = nullptr;      // [max_nodes] float32 copy of the apply's density
+  float* stw = nullptr;         // staged FFT twiddles per radix-4 stage, float32 [N]
+  double* stw_d = nullptr;      // the same in float64
   int* probe_mark = nullptr;    // [N][N] probe index + 1 (0 = not a probe)
   int* prow_cnt = nullptr;      // [N + 1]
   int* prow_ptr = nullptr;      // [N + 1]
@@ -146,9 +187,9 @@ struct kfbi_ctx {
   // per-apply work buffers
   double* dcoef = nullptr;      // [max_nodes/2+1] complex density coefficients
   double* dint = nullptr;       // [1] integral of the density
-  double* jumps = nullptr;      // [targets][6]
-  double* cval = nullptr;       // [cap_irr] corrections (T)
   double* boxg = nullptr;       // [4N] free-space box data
+  double* facespec = nullptr;   // [2N] transformed south / north face rows
+  double* jumps = nullptr;      // [cap_cross + max_nodes][6] jumps at the targets (T)
   double* spec = nullptr;       // [N][N] row-transformed grid (T)
   double* probe_val = nullptr;  // [6*max_nodes] (T)
   double* tmp_vals = nullptr;   // [max_nodes]
@@ -157,13 +198,28 @@ struct kfbi_ctx {
   kfbi::GmresCtl* gctl = nullptr;
   kfbi::GmresCtl* host_gctl = nullptr;  // pinned
   double* gV = nullptr;         // [(MAX_RESTART+1)][max_nodes]
-  double* gpart = nullptr;      // [blocks][MAX_RESTART+1]
+  double* gpart = nullptr;      // [max_nodes/32 + MAX_RESTART + 2][MAX_RESTART+1] block partials
+  int gm_m = 1;                 // restart length of the running GMRES
   double* gw = nullptr;         // apply output / Arnoldi vector w  [max_nodes]
   double* gin = nullptr;        // apply input [max_nodes]
+  float* gin_f = nullptr;       // float32 copy of the apply input
   double* gb = nullptr;         // right-hand side copy [max_nodes]
   double* gx = nullptr;         // iterate [max_nodes]
   double* gr = nullptr;         // outer residual / correction (refinement) [max_nodes]
   int* zero_flag = nullptr;     // device int 0
+
+  // solve graphs: one CUDA graph per (BIE kind, apply precision) holding a conditional
+  // WHILE node whose body is one GMRES iteration; rebuilt when the interface changes
+  struct SolveGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long version = -1;
+    int m = 0;
+  } sgraph[3][2];
+  long iface_version = 0;
+  bool use_graphs = true;
+  bool capturing = false;
+  double* gev = nullptr;        // [max_nodes] eps_V copy for the Stefan operator
 
   // timing of the column kernel: event pairs recorded without synchronising
   bool timing = false;
@@ -171,6 +227,7 @@ struct kfbi_ctx {
   cudaEvent_t* tev = nullptr;   // [2 * TIMING_CAP]
   uint8_t* tprec = nullptr;     // [TIMING_CAP] 1 = float32 launch
   long long launches = 0;       // kernels launched by this context
+  int per_apply_launches[2] = {0, 0};  // kernels of one apply (float64, float32), for graph replays
 };
 
 namespace kfbi {
@@ -217,11 +274,28 @@ inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
 inline void launched(kfbi_ctx* c, int k) { c->launches += k; }
 
+// Work runs on c->stream. When the caller's stream is a default stream (which cannot be
+// captured into a graph), c->stream is the context's own stream, ordered after the caller's
+// prior work on entry and before the caller's later work on exit.
+inline cudaError_t stream_enter(kfbi_ctx* c) {
+  if (!c->user_default) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(c->ev_in, c->user);
+  if (e != cudaSuccess) return e;
+  return cudaStreamWaitEvent(c->own, c->ev_in, 0);
+}
+inline cudaError_t stream_exit(kfbi_ctx* c) {
+  if (!c->user_default) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(c->ev_out, c->own);
+  if (e != cudaSuccess) return e;
+  return cudaStreamWaitEvent(c->user, c->ev_out, 0);
+}
+kfbi_status apply_setup_attributes(kfbi_ctx* c);
+
 // host-side helpers implemented in the .cu files
 kfbi_status ensure_cross_capacity(kfbi_ctx* c, int n_cross);
 kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* density, double* values,
                           double* dnormal, double* grid, int bie_kind, const double* eps_v,
-                          const int* skip_flag);
+                          const int* skip_flag, const float* density_f = nullptr);
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u);
 kfbi_status interp_grid_enqueue(kfbi_ctx* c, const double* grid, double* values);
 

@@ -454,11 +454,13 @@ static kfbi_status thetal_create_impl(kfbi_ctx* c, int n, const double* eta, dou
   st->host_scal[SC_L] = L;
   st->host_scal[SC_XB0] = xbar[0];
   st->host_scal[SC_XB1] = xbar[1];
+  KFBI_TRY(stream_enter(c));
   KFBI_TRY(cudaMemcpyAsync(st->scal, st->host_scal, SC_COUNT * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   KFBI_TRY(cudaMemcpyAsync(st->eta, eta, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   k_twiddles_n_step<<<cdiv(n, 256), 256, 0, c->stream>>>(n, (double2*)st->tw);
   KFBI_TRY(cudaGetLastError());
   KFBI_TRY(cudaStreamSynchronize(c->stream));
+  KFBI_TRY(stream_exit(c));
   return KFBI_OK;
 }
 
@@ -498,7 +500,10 @@ kfbi_status kfbi_step(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve_info* 
     double want = 3.0 / (2.0 * dt);
     if (fabs(want - c->kappa) > 1e-12 * want) return KFBI_ERR_ARG;
   }
-  return thetal_step_impl(c, st, dt, info);
+  KFBI_TRY(stream_enter(c));
+  kfbi_status s = thetal_step_impl(c, st, dt, info);
+  KFBI_TRY(stream_exit(c));
+  return s;
 }
 
 kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* density, double* nhat, double* T,
@@ -508,6 +513,7 @@ kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* d
   const int n = st->n;
   const size_t NN = (size_t)st->ctx->N * st->ctx->N;
   const size_t nk = (size_t)(n / 2 + 1);
+  KFBI_TRY(stream_enter(st->ctx));
   if (eta) KFBI_TRY(cudaMemcpyAsync(eta, st->eta, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (xy) KFBI_TRY(cudaMemcpyAsync(xy, st->xy, 2 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (density) KFBI_TRY(cudaMemcpyAsync(density, st->density, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -519,6 +525,7 @@ kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* d
     KFBI_TRY(cudaStreamSynchronize(s));
     for (int i = 0; i < SC_COUNT; ++i) scalars[i] = st->host_scal[i];
   }
+  KFBI_TRY(stream_exit(st->ctx));
   return KFBI_OK;
 }
 
@@ -529,6 +536,7 @@ kfbi_status kfbi_thetal_write(kfbi_thetal* st, const double* eta, const double* 
   const int n = st->n;
   const size_t NN = (size_t)st->ctx->N * st->ctx->N;
   const size_t nk = (size_t)(n / 2 + 1);
+  KFBI_TRY(stream_enter(st->ctx));
   if (eta) KFBI_TRY(cudaMemcpyAsync(st->eta, eta, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (density) KFBI_TRY(cudaMemcpyAsync(st->density, density, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (nhat) KFBI_TRY(cudaMemcpyAsync(st->Nprev_h, nhat, 2 * nk * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -540,6 +548,7 @@ kfbi_status kfbi_thetal_write(kfbi_thetal* st, const double* eta, const double* 
     KFBI_TRY(cudaMemcpyAsync(st->scal, st->host_scal, SC_COUNT * sizeof(double), cudaMemcpyHostToDevice, s));
     KFBI_TRY(cudaStreamSynchronize(s));
   }
+  KFBI_TRY(stream_exit(st->ctx));
   return KFBI_OK;
 }
 
