@@ -283,6 +283,25 @@ kfbi_status kfbi_timing_enable(kfbi_ctx* ctx, int enable);
 kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64, double* ms_fp32,
                              int* launches_fp32);
 
+/*
+ * Execution options of a context (none changes a result beyond rounding order):
+ *   KFBI_OPT_CUDA_GRAPHS      1 (default): a GMRES run is one CUDA graph launch whose
+ *                             conditional WHILE node replays one iteration until the device
+ *                             decides the run is over; 0: the host enqueues iterations in
+ *                             chunks and polls the device between chunks.
+ *   KFBI_OPT_CLUSTER_GMRES    1 (default): the Gram-Schmidt step of an iteration is one
+ *                             launch of a thread-block cluster (16 or 8 CTAs, selected by
+ *                             node count, restart length and shared-memory capacity) when the
+ *                             device can schedule it; 0: the five-kernel form.
+ *   KFBI_OPT_LAST_CLUSTER     read only: cluster size used by the last GMRES run (0 = the
+ *                             five-kernel form).
+ * kfbi_set_option: value 0 or 1. kfbi_get_option writes the value to *value (host).
+ * Errors: ARG (unknown option, bad value, NULL, read-only option).
+ */
+enum { KFBI_OPT_CUDA_GRAPHS = 1, KFBI_OPT_CLUSTER_GMRES = 2, KFBI_OPT_LAST_CLUSTER = 3 };
+kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
+kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);
+
 /* Number of kernels this context has launched since creation (host output). */
 kfbi_status kfbi_launch_count(kfbi_ctx* ctx, long long* count);
 

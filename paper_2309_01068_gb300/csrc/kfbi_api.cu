@@ -427,6 +427,28 @@ const char* kfbi_status_string(kfbi_status s) {
   return "unknown status";
 }
 
+kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
+  if (!ctx_ok(c) || (value != 0 && value != 1)) return KFBI_ERR_ARG;
+  if (option == KFBI_OPT_CUDA_GRAPHS) {
+    c->use_graphs = value != 0;
+  } else if (option == KFBI_OPT_CLUSTER_GMRES) {
+    c->gm_cluster = value != 0;
+    c->gmf = kfbi_ctx::GmfConfig{};
+  } else {
+    return KFBI_ERR_ARG;
+  }
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
+  if (!ctx_ok(c) || value == nullptr) return KFBI_ERR_ARG;
+  if (option == KFBI_OPT_CUDA_GRAPHS) *value = c->use_graphs ? 1 : 0;
+  else if (option == KFBI_OPT_CLUSTER_GMRES) *value = c->gm_cluster ? 1 : 0;
+  else if (option == KFBI_OPT_LAST_CLUSTER) *value = c->gmf_last_cs;
+  else return KFBI_ERR_ARG;
+  return KFBI_OK;
+}
+
 kfbi_status kfbi_timing_enable(kfbi_ctx* c, int enable) {
   if (!ctx_ok(c)) return KFBI_ERR_ARG;
   if (enable && c->tev == nullptr) {

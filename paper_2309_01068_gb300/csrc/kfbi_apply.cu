@@ -103,13 +103,15 @@ __global__ void k_to_float(const double* a, float* b, int n, const int* skip) {
 // --------------------------------------------------------------------------- density
 // c_k = (1/n) sum_j phi_j e^{-2 pi i k j / n} (k = 0..n/2): one warp per k, twiddle index
 // k j mod n advanced incrementally; the block stages the density and the twiddles in shared
-// memory (SMEM = true) or reads them from global memory (large n). The warp of k = 0 also
-// forms int phi ds = sum_j phi_j s_a,j 2 pi / n (trapezoidal rule) for the Hele-Shaw operator.
-template <typename T, bool SMEM>
-__global__ void k_dens_coef(const T* phi, const double* phi64, int n, const V2<T>* tw, const Stencil* st, V2<T>* coef,
-                            double* dint, const int* skip) {
+// memory (SMEM = true) or reads them from global memory (large n). Block 0 also forms
+// int phi ds = sum_j phi_j s_a,j 2 pi / n (trapezoidal rule) for the Hele-Shaw operator, as a
+// block-wide tree so that its dependency depth stays logarithmic in n.
+template <typename T, bool SMEM, typename S_t>
+__global__ void k_dens_coef(const T* phi, int n, const V2<T>* tw, const S_t* st, V2<T>* coef, T* dint,
+                            const int* skip) {
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
+  __shared__ T red[32];
   V2<T>* stw = (V2<T>*)smem_raw;
   T* sphi = (T*)(stw + n);
   if (SMEM) {
@@ -121,6 +123,23 @@ __global__ void k_dens_coef(const T* phi, const double* phi64, int n, const V2<T
   }
   int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && dint != nullptr) {
+    T s0 = 0, s1 = 0;
+    int j = threadIdx.x;
+    for (; j + (int)blockDim.x < n; j += 2 * blockDim.x) {
+      s0 += (SMEM ? sphi[j] : phi[j]) * (T)st[j].w;
+      s1 += (SMEM ? sphi[j + blockDim.x] : phi[j + blockDim.x]) * (T)st[j + blockDim.x].w;
+    }
+    if (j < n) s0 += (SMEM ? sphi[j] : phi[j]) * (T)st[j].w;
+    T s = wsum(s0 + s1);
+    if (lane == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      T t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : (T)0;
+      t = wsum(t);
+      if (threadIdx.x == 0) *dint = t;
+    }
+  }
   if (k > n / 2) return;
   int idx = (int)(((long)k * lane) % n);
   const int step = (int)(((long)k * 32) % n);
@@ -136,12 +155,6 @@ __global__ void k_dens_coef(const T* phi, const double* phi64, int n, const V2<T
   re = wsum(re);
   im = wsum(im);
   if (lane == 0) coef[k] = V2<T>{re / (T)n, im / (T)n};
-  if (k == 0 && dint != nullptr) {
-    double s = 0.0;
-    for (int j = lane; j < n; j += 32) s += phi64[j] * st[j].w;
-    s = wsum(s);
-    if (lane == 0) *dint = s;
-  }
 }
 
 // Warp-level jumps at one target (App. A.1, Table 2): the warp sums the density interpolant
@@ -151,7 +164,7 @@ __global__ void k_dens_coef(const T* phi, const double* phi64, int n, const V2<T
 // J = ([u], [u_x], [u_y], [u_xx], [u_yy], [u_xy]).
 template <typename T, typename G>
 __device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, const V2<T>* ts, const G& g, int layer,
-                                          double kappa, int lane, T J[6]) {
+                                          T kappa, int lane, T J[6]) {
   const int K = (n - 1) / 2;
   const int chunk = (K + 31) / 32;
   int k0 = 1 + lane * chunk;
@@ -194,7 +207,7 @@ __device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, const V2<T>*
   T uy = (ya * Phia - xa * sa * Psi) * is2;
   T b0 = Phiaa - xaa * ux - yaa * uy;
   T b1 = saa * Psi + sa * Psia - yaa * ux + xaa * uy;
-  T b2 = (T)kappa * Phi;
+  T b2 = kappa * Phi;
   J[0] = Phi;
   J[1] = ux;
   J[2] = uy;
@@ -207,7 +220,7 @@ __device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, const V2<T>*
 // density coefficients in shared memory first (SMEM = true; large n reads them from global memory). J[t] = ([u], [u_x], [u_y], [u_xx], [u_yy], [u_xy]).
 template <typename T, typename G, bool SMEM>
 __global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const G* tg, const V2<T>* tstart, int layer,
-                               double kappa, T* Jout, const int* skip) {
+                               T kappa, T* Jout, const int* skip) {
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   const V2<T>* sc = coef;
@@ -231,7 +244,7 @@ __global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const G* tg, c
 // right-hand side term -2 g / h^2. npack[l] = (x, y, y_a, -x_a) of node l.
 template <typename T, typename T4, bool SMEM>
 __global__ void k_box_data(const T* phi, int n, const T4* npack, int N, double xmin, double xmax, double ymin,
-                           double ymax, double h, T* boxg, const int* skip) {
+                           double ymax, double h, T scale, T* boxg, const int* skip) {
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   T4* sp = (T4*)smem_raw;  // (x, y, phi y_a, -phi x_a)
@@ -249,13 +262,22 @@ __global__ void k_box_data(const T* phi, int n, const T4* npack, int N, double x
   int lane = threadIdx.x & 31;
   if (w >= 4 * N) return;
   int face = w / N, idx = w - face * N;
-  double px, py;
-  if (face == 0) { px = xmin; py = grid_coord(ymin, h, idx); }
-  else if (face == 1) { px = xmax; py = grid_coord(ymin, h, idx); }
-  else if (face == 2) { px = grid_coord(xmin, h, idx); py = ymin; }
-  else { px = grid_coord(xmin, h, idx); py = ymax; }
+  // face midpoint: float64 rounding as the oracle's grid; float32 arithmetic in the float32
+  // apply (the float64 pipe is slow and its precision is not needed there)
+  T tpx, tpy;
+  if constexpr (sizeof(T) == 8) {
+    if (face == 0) { tpx = xmin; tpy = grid_coord(ymin, h, idx); }
+    else if (face == 1) { tpx = xmax; tpy = grid_coord(ymin, h, idx); }
+    else if (face == 2) { tpx = grid_coord(xmin, h, idx); tpy = ymin; }
+    else { tpx = grid_coord(xmin, h, idx); tpy = ymax; }
+  } else {
+    const T c = ((T)idx + (T)0.5) * (T)h;
+    if (face == 0) { tpx = (T)xmin; tpy = (T)ymin + c; }
+    else if (face == 1) { tpx = (T)xmax; tpy = (T)ymin + c; }
+    else if (face == 2) { tpx = (T)xmin + c; tpy = (T)ymin; }
+    else { tpx = (T)xmin + c; tpy = (T)ymax; }
+  }
   T acc = 0;
-  const T tpx = (T)px, tpy = (T)py;
   for (int l = lane; l < n; l += 32) {
     T4 q;
     if (SMEM) {
@@ -270,7 +292,7 @@ __global__ void k_box_data(const T* phi, int n, const T4* npack, int N, double x
     acc += fdiv_t(dx * q.z + dy * q.w, dx * dx + dy * dy);
   }
   acc = wsum(acc);
-  if (lane == 0) boxg[w] = (T)(-2.0 / (h * h * (double)n)) * acc;
+  if (lane == 0) boxg[w] = scale * acc;
 }
 
 // --------------------------------------------------------------------------- FFT core
@@ -413,7 +435,7 @@ constexpr int ROW_THREADS = 256;  // N <= 4096 gives at most 16 outputs per thre
 
 template <typename T>
 __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, const int* row_ptr, const IrrNode* irr,
-                                                            const T* J, double inv_h2, const T* boxg,
+                                                            const T* J, T inv_h2, const T* boxg,
                                                             const T* facespec, const T* tab, float scale, T* spec,
                                                             const int* skip) {
   if (*skip) return;
@@ -441,7 +463,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
         sum += jj[0] + d * j1 + (T)0.5 * d * d * j2;
       }
       si[t] = 2 * node.i + 1;
-      sv[t] = irr_sign(node, T(0)) * (T)inv_h2 * sum;
+      sv[t] = irr_sign(node, T(0)) * inv_h2 * sum;
     }
     __syncthreads();
 #pragma unroll
@@ -488,7 +510,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
 // one complex FFT. Two shared buffers alternate between the FFT stages.
 template <typename T>
 __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, const T* tab, const T* lam,
-                            double kappa, T* spec, const int* skip) {
+                            T kappa, T* spec, const int* skip) {
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
@@ -505,7 +527,7 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
   V2<T>* X = fft_stockham<T>(A, B, P, N, logN, tw, false);
   V2<T>* Y = X == A ? B : A;
   const int half = N >> 1;
-  const T kap = (T)kappa;
+  const T kap = kappa;
   for (int t = threadIdx.x; t < P * (half + 1); t += blockDim.x) {
     int p = t / (half + 1), m = t - p * (half + 1);
     const V2<T>* x = X + (long)p * N;
@@ -637,10 +659,10 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
 // value (v+ + v-)/2 = v+ - [v]/2; dnormal = n.(grad v+ - [grad v]/2). One warp per node,
 // lane m < 6 handles stencil point m. The result is written as
 //   out = a x + b value + c int(x) ds   (a, b, c select the boundary integral operator)
+// in the arithmetic type T (a = eps_v[p] when eps_v is given) and stored as float64.
 template <typename T, typename S_t>
-__global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const double* x_in,
-                         const double* eps_v, double ca, double cb, double cc, const double* dint, double* out,
-                         double* dnormal, const int* skip) {
+__global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const T* x_in, const double* eps_v, T ca,
+                         T cb, T cc, const T* dint, double* out, double* dnormal, const int* skip) {
   if (*skip) return;
   int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
@@ -665,18 +687,16 @@ __global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const
     gy += __shfl_down_sync(0xffffffffu, gy, o);
   }
   if (lane != 0) return;
-  double val = (double)v;
   if (J != nullptr) {
-    val -= 0.5 * (double)J[0];
+    v -= (T)0.5 * J[0];
     gx -= (T)0.5 * J[1];
     gy -= (T)0.5 * J[2];
   }
-  double a = eps_v != nullptr ? eps_v[p] : ca;
-  double xin = x_in != nullptr ? x_in[p] : 0.0;
-  double o = a * xin + cb * val;
+  T o = cb * v;
+  if (x_in != nullptr) o += (eps_v != nullptr ? (T)eps_v[p] : ca) * x_in[p];
   if (dint != nullptr) o += cc * (*dint);
-  out[p] = o;
-  if (dnormal != nullptr) dnormal[p] = (double)S.nx * (double)gx + (double)S.ny * (double)gy;
+  out[p] = (double)o;
+  if (dnormal != nullptr) dnormal[p] = (double)((T)S.nx * gx + (T)S.ny * gy);
 }
 
 // --------------------------------------------------------------------------- host side
@@ -702,7 +722,7 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
   k_col_solve<T><<<N / (2 * P), col_threads(N, P), smem, c->stream>>>(N, c->logN, P, c->boxbc == KFBI_BOX_NEUMANN0,
                                                                   Tabs<T>::stw(c), Tabs<T>::sin(c), Tabs<T>::lam(c),
-                                                                  c->kappa, spec, skip);
+                                                                  (T)c->kappa, spec, skip);
   launched(c, 1);
   if (rec) {
     KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used + 1], c->stream));
@@ -737,6 +757,9 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   T* face = (T*)c->facespec;
   T* spec = (T*)c->spec;
   T* J = (T*)c->jumps;
+  // the density integral of the Hele-Shaw operator, in the apply's type (float64 slot 0 or a
+  // float32 slot in the same buffer)
+  T* dint_t = sizeof(T) == 8 ? (T*)c->dint : (T*)(c->dint + 4);
   T* pval = (T*)c->probe_val;
   const int nk = n / 2 + 1;
   const bool want_int = bie_kind == KFBI_BIE_HS_EXTERIOR_MDL;
@@ -761,12 +784,13 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     KFBI_TRY(cudaEventRecord(c->ev_fork, s));
     KFBI_TRY(cudaStreamWaitEvent(s2, c->ev_fork, 0));
     const size_t smb = (size_t)n * sizeof(T4);
+    const T bscale = (T)(-2.0 / (c->h * c->h * (double)n));
     if (smb <= SMEM_STAGE_MAX)
       k_box_data<T, T4, true><<<cdiv((long)4 * N * 32, 256), 256, smb, s2>>>(
-          dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, boxg, skip);
+          dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, bscale, boxg, skip);
     else
       k_box_data<T, T4, false><<<cdiv((long)4 * N * 32, 256), 256, 0, s2>>>(
-          dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, boxg, skip);
+          dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, bscale, boxg, skip);
     size_t smf = 2 * sizeof(V2<T>) * (size_t)N;
     k_face_dst<T><<<1, 256, smf, s2>>>(N, c->logN, dct, Tabs<T>::stw(c), tab, boxg, face, skip);
     KFBI_TRY(cudaEventRecord(c->ev_join, s2));
@@ -774,24 +798,24 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   }
   const size_t smd = (size_t)n * (sizeof(V2<T>) + sizeof(T));
   if (smd <= SMEM_STAGE_MAX) {
-    k_dens_coef<T, true><<<cdiv((long)nk * 32, 256), 256, smd, s>>>(dens_t, density, n, Tabs<T>::twn(c), c->stencil,
-                                                                    coef, want_int ? c->dint : nullptr, skip);
+    k_dens_coef<T, true><<<cdiv((long)nk * 32, 256), 256, smd, s>>>(dens_t, n, Tabs<T>::twn(c), Tabs<T>::stencil(c),
+                                                                    coef, want_int ? dint_t : nullptr, skip);
   } else {
-    k_dens_coef<T, false><<<cdiv((long)nk * 32, 256), 256, 0, s>>>(dens_t, density, n, Tabs<T>::twn(c), c->stencil,
-                                                                   coef, want_int ? c->dint : nullptr, skip);
+    k_dens_coef<T, false><<<cdiv((long)nk * 32, 256), 256, 0, s>>>(dens_t, n, Tabs<T>::twn(c), Tabs<T>::stencil(c),
+                                                                   coef, want_int ? dint_t : nullptr, skip);
   }
   const int ntg = ncr + n;
   using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
   const size_t smj = (size_t)nk * sizeof(V2<T>);
   if (smj <= SMEM_STAGE_MAX)
     k_target_jumps<T, G, true><<<cdiv((long)ntg * 32, 256), 256, smj, s>>>(coef, n, ntg, Tabs<T>::geo(c),
-                                                                          Tabs<T>::tstart(c), layer, c->kappa, J, skip);
+                                                                          Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip);
   else
     k_target_jumps<T, G, false><<<cdiv((long)ntg * 32, 256), 256, 0, s>>>(coef, n, ntg, Tabs<T>::geo(c),
-                                                                         Tabs<T>::tstart(c), layer, c->kappa, J, skip);
+                                                                         Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip);
   launched(c, 2);
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
-  k_row_forward<T><<<N, ROW_THREADS, 0, s>>>(N, dct, c->row_ptr, c->irr, J, 1.0 / (c->h * c->h), fs ? boxg : nullptr,
+  k_row_forward<T><<<N, ROW_THREADS, 0, s>>>(N, dct, c->row_ptr, c->irr, J, (T)(1.0 / (c->h * c->h)), fs ? boxg : nullptr,
                                              face, tab, scale, spec, skip);
   launched(c, 1);
   KFBI_CHECK(launch_col_solve<T>(c, spec, skip));
@@ -801,14 +825,14 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     launched(c, 1);
   }
   if (grid != nullptr) KFBI_CHECK(launch_row_dense<T>(c, 1, nullptr, spec, grid));
-  double ca = 0.0, cb = 1.0, cc = 0.0;
+  T ca = 0, cb = 1, cc = 0;
   const double* ev = nullptr;
-  const double* xin = nullptr;
-  if (bie_kind == KFBI_BIE_INTERIOR_DL) { ca = 0.5; xin = density; }
-  else if (bie_kind == KFBI_BIE_HS_EXTERIOR_MDL) { ca = -0.5; cc = 1.0; xin = density; }
-  else if (bie_kind == KFBI_BIE_STEFAN_SL) { cb = -1.0; ev = eps_v; xin = density; }
+  const T* xin = nullptr;
+  if (bie_kind == KFBI_BIE_INTERIOR_DL) { ca = (T)0.5; xin = dens_t; }
+  else if (bie_kind == KFBI_BIE_HS_EXTERIOR_MDL) { ca = (T)-0.5; cc = 1; xin = dens_t; }
+  else if (bie_kind == KFBI_BIE_STEFAN_SL) { cb = -1; ev = eps_v; xin = dens_t; }
   k_interp<T><<<cdiv((long)n * 32, 256), 256, 0, s>>>(n, Tabs<T>::stencil(c), pval, J + (long)ncr * 6, xin, ev, ca, cb,
-                                                      cc, want_int ? c->dint : nullptr, values, dnormal, skip);
+                                                      cc, want_int ? dint_t : nullptr, values, dnormal, skip);
   launched(c, 1);
   c->per_apply_launches[sizeof(T) == 4 ? 1 : 0] = (int)(c->launches - l0);
   KFBI_TRY(cudaGetLastError());
@@ -831,7 +855,8 @@ static kfbi_status setup_t(kfbi_ctx* c) {
   KFBI_TRY(cudaFuncSetAttribute(k_col_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, col));
   KFBI_TRY(cudaFuncSetAttribute(k_row_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
   KFBI_TRY(cudaFuncSetAttribute(k_face_dst<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
-  KFBI_TRY(cudaFuncSetAttribute(k_dens_coef<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, dens));
+  using S_t = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(c))>::type>::type;
+  KFBI_TRY(cudaFuncSetAttribute(k_dens_coef<T, true, S_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, dens));
   KFBI_TRY(cudaFuncSetAttribute(k_box_data<T, T4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, box));
   KFBI_TRY(cudaFuncSetAttribute(k_target_jumps<T, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, jmp));
   return KFBI_OK;

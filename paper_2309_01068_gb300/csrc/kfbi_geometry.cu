@@ -508,6 +508,7 @@ __global__ void k_stencil_map(int n, const int* probe_mark, Stencil* st, Stencil
     F.r2[m] = (float)S.r2[m];
   }
   F.nx = (float)S.nx;
+  F.w = (float)S.w;
   F.ny = (float)S.ny;
   st[p] = S;
   stf[p] = F;

@@ -364,14 +364,565 @@ __global__ void k_gm_cond(GmresCtl* ctl, cudaGraphConditionalHandle h, int cap) 
   cudaGraphSetConditional(h, ctl->done ? 0u : 1u);
 }
 
+// --------------------------------------------------------------------------- cluster form
+// One GMRES body after the apply in a single launch of one thread-block cluster. CTA c of
+// the cluster owns the rows [c R, (c + 1) R) of the Krylov basis and of every vector: it
+// stages its slice of V[0..j] and of w in shared memory, forms its partial Gram-Schmidt
+// coefficients, and every CTA sums the partials of all CTAs through distributed shared
+// memory in the same order, so the Hessenberg column, the Givens rotations and every
+// decision are identical in all CTAs without a broadcast. CTA 0 writes the control block.
+// Float64 throughout; both Gram-Schmidt passes (CGS2) as in the multi-kernel form. The
+// float64 pipe is narrow, so dependent float64 chains are kept short: the rotations of the
+// new Hessenberg column run as a warp scan, sums as shuffle trees, and ||w||^2 after the
+// second pass comes from the second pass's own reduction,
+//   ||w' - V h2||^2 = ||w'||^2 - ||h2||^2   (V orthonormal, h2 = V^T w'),
+// with an explicit reduction when that difference cancels (below half of ||w'||^2).
+constexpr int GMF_THREADS = 512;
+constexpr int GMF_PART = MAX_RESTART + 2;
+
+// row stride of the staged V slice: >= R and 4 mod 16 doubles, so that the lane patterns of
+// the dot and combine steps touch each shared-memory bank at most twice per warp access
+__host__ __device__ inline int gmf_row_stride(int R) { return R + ((20 - R % 16) % 16); }
+
+__device__ __forceinline__ unsigned cl_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cl_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// barrier over every thread of every CTA in the cluster; orders shared-memory writes before
+// it with distributed shared-memory reads after it
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+__device__ __forceinline__ double cl_load(const double* p, unsigned rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(r) : "memory");
+  return v;
+}
+
+// out[0..L) = sum over the cluster's CTAs (rank order) of part[0..L) in each CTA. Thread t
+// loads entry t / cs of CTA t % cs; a half-warp (cs = 16) or an 8-lane group (cs = 8) sums
+// its loads by a fixed shuffle tree.
+__device__ __forceinline__ void cl_reduce(const double* part, double* out, int L, unsigned cs) {
+  cl_sync();
+  const int per = GMF_THREADS / (int)cs;
+  for (int base = 0; base < L; base += per) {
+    const int idx = base + (int)(threadIdx.x / cs);
+    const unsigned c = threadIdx.x % cs;
+    double v = idx < L ? cl_load(part + idx, c) : 0.0;
+    for (unsigned o = cs >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (c == 0 && idx < L) out[idx] = v;
+  }
+  __syncthreads();
+}
+
+// sum of v over the CTA by shuffle trees; the result is returned in every thread
+__device__ __forceinline__ double cta_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = lane < GMF_THREADS / 32 ? sh[lane] : 0.0;
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  __syncthreads();
+  return t;
+}
+
+// largest power of two <= min(32, x) (x >= 1)
+__device__ __forceinline__ int lanes_pow2(int x) {
+  int g = 1;
+  while (2 * g <= x && g < 32) g <<= 1;
+  return g;
+}
+
+// p[k] = sum_i sV[k][i] w[i] for k < K over this CTA's rows, and p[K] = sum_i w[i]^2 when
+// with_norm. G adjacent lanes share one k: lane g sums i = g, g + G, ... with four
+// accumulators, then a shuffle tree over the G lanes.
+__device__ __forceinline__ void cta_dots(const double* sV, int Rp, const double* w, int len, int K, bool with_norm,
+                                         double* p) {
+  const int Kt = K + (with_norm ? 1 : 0);
+  const int G = lanes_pow2(GMF_THREADS / Kt);
+  const int total = Kt * G;
+  for (int base = 0; base < total; base += GMF_THREADS) {
+    const int t = base + (int)threadIdx.x;
+    const int k = t / G, g = t % G;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (t < total) {
+      const double* row = k < K ? sV + k * Rp : w;
+      int i = g;
+      for (; i + 3 * G < len; i += 4 * G) {
+        a0 += row[i] * w[i];
+        a1 += row[i + G] * w[i + G];
+        a2 += row[i + 2 * G] * w[i + 2 * G];
+        a3 += row[i + 3 * G] * w[i + 3 * G];
+      }
+      for (; i < len; i += G) a0 += row[i] * w[i];
+    }
+    double v = (a0 + a1) + (a2 + a3);
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (t < total && g == 0) p[k] = v;
+  }
+  __syncthreads();
+}
+
+// w[i] += sign * sum_k sV[k][i] h[k] over this CTA's rows. G adjacent lanes share one i:
+// lane g sums k = g, g + G, ... with four accumulators, then a shuffle tree.
+__device__ __forceinline__ void cta_combine(const double* sV, int Rp, const double* h, int K, int len, double* w,
+                                            double sign) {
+  const int G = lanes_pow2(GMF_THREADS / (len > 0 ? len : 1));
+  const int total = len * G;
+  for (int base = 0; base < total; base += GMF_THREADS) {
+    const int t = base + (int)threadIdx.x;
+    const int i = t / G, g = t % G;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (t < total) {
+      int k = g;
+      for (; k + 3 * G < K; k += 4 * G) {
+        a0 += sV[k * Rp + i] * h[k];
+        a1 += sV[(k + G) * Rp + i] * h[k + G];
+        a2 += sV[(k + 2 * G) * Rp + i] * h[k + 2 * G];
+        a3 += sV[(k + 3 * G) * Rp + i] * h[k + 3 * G];
+      }
+      for (; k < K; k += G) a0 += sV[k * Rp + i] * h[k];
+    }
+    double v = (a0 + a1) + (a2 + a3);
+    for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (t < total && g == 0) w[i] = fma(sign, v, w[i]);
+  }
+  __syncthreads();
+}
+
+// Applies the j previous Givens rotations to the column hc[0..j] in one warp. With the
+// carried entry x_0 = hc[0], rotation i maps (x_i, hc[i+1]) to
+//   out_i = c_i x_i + s_i hc[i+1],   x_{i+1} = -s_i x_i + c_i hc[i+1],
+// an affine recurrence x_{i+1} = A_i x_i + B_i (A_i = -s_i, B_i = c_i hc[i+1]). Lane l takes
+// the rotations [l C, (l+1) C), composes its maps, an inclusive shuffle scan composes the
+// lanes' maps, and each lane replays its rotations from its starting x. On return hc[0..j-1]
+// hold out_i and hc[j] holds x_j. Warp 0 only; j <= 32 * GIV_CHUNK.
+constexpr int GIV_CHUNK = (MAX_RESTART + 31) / 32;
+__device__ __forceinline__ void givens_scan(double* hc, const double* cs_, const double* sn_, int j) {
+  const int lane = threadIdx.x & 31;
+  const int C = (j + 31) / 32;
+  const int i0 = lane * C;
+  double c[GIV_CHUNK], s[GIV_CHUNK], h[GIV_CHUNK];
+  double A = 1.0, B = 0.0;
+#pragma unroll
+  for (int u = 0; u < GIV_CHUNK; ++u) {
+    const int i = i0 + u;
+    const bool ok = u < C && i < j;
+    c[u] = ok ? cs_[i] : 1.0;
+    s[u] = ok ? sn_[i] : 0.0;
+    h[u] = ok ? hc[i + 1] : 0.0;
+  }
+  const double x0 = hc[0];
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < GIV_CHUNK; ++u) {
+    if (u < C && i0 + u < j) {
+      const double cb = c[u] * h[u];
+      B = fma(-s[u], B, cb);
+      A = -s[u] * A;
+    }
+  }
+  // inclusive scan of lane maps: (A, B) <- (A, B) o (A', B') of lane l - d
+  for (int d = 1; d < 32; d <<= 1) {
+    const double Ap = __shfl_up_sync(0xffffffffu, A, d);
+    const double Bp = __shfl_up_sync(0xffffffffu, B, d);
+    if (lane >= d) {
+      B = fma(A, Bp, B);
+      A = A * Ap;
+    }
+  }
+  // exclusive prefix applied to x_0 gives this lane's starting x
+  double Ae = __shfl_up_sync(0xffffffffu, A, 1);
+  double Be = __shfl_up_sync(0xffffffffu, B, 1);
+  double x = lane == 0 ? x0 : fma(Ae, x0, Be);
+#pragma unroll
+  for (int u = 0; u < GIV_CHUNK; ++u) {
+    const int i = i0 + u;
+    if (u < C && i < j) {
+      const double sh = s[u] * h[u], ch = c[u] * h[u];
+      hc[i] = fma(c[u], x, sh);
+      x = fma(-s[u], x, ch);
+      if (i == j - 1) hc[j] = x;
+    }
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void gmf_close(GmresCtl* ctl, unsigned rank, cudaGraphConditionalHandle hcond,
+                                          int use_cond, int cap, int done) {
+  if (rank != 0 || threadIdx.x != 0) return;
+  const int b = ++ctl->bodies;
+  if (!done && b >= cap) {
+    ctl->status = KFBI_ERR_TIMEOUT;
+    ctl->phase = PH_DONE;
+    ctl->done = 1;
+    done = 1;
+  }
+  if (use_cond) cudaGraphSetConditional(hcond, done ? 0u : 1u);
+}
+
+// Dynamic shared memory: sV[(m+1) Rp] | sH[(m+1)(m+1)] (hsmem) | sw[Rp]
+__global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, double* V, int ldv, const double* w,
+                                                            const double* b, double* x, double* gin, float* gin_f,
+                                                            int n, int R, int hsmem, cudaGraphConditionalHandle hcond,
+                                                            int use_cond, int cap) {
+  extern __shared__ double dsm[];
+  __shared__ double part[2][GMF_PART];
+  __shared__ double h1[GMF_PART], h2[GMF_PART], hcol[GMF_PART];
+  __shared__ double scs[MAX_RESTART], ssn[MAX_RESTART], gy[MAX_RESTART + 1];
+  __shared__ double red[GMF_THREADS / 32];
+  __shared__ int s_done, s_phase, s_j, s_m, s_its, s_maxit, s_trust, s_cycles, s_end;
+  __shared__ double s_tol, s_bnorm, s_gj, s_gj1, s_hn2, s_inv, s_rd;
+  const unsigned rank = cl_rank(), cs = cl_size();
+  const int Rp = gmf_row_stride(R);
+  const int i0 = (int)rank * R;
+  const int len = max(0, min(n, i0 + R) - i0);
+  if (threadIdx.x == 0) {
+    s_done = ctl->done;
+    s_phase = ctl->phase;
+    s_j = ctl->j;
+    s_m = ctl->m;
+    s_its = ctl->its;
+    s_maxit = ctl->max_iter;
+    s_trust = ctl->trust;
+    s_cycles = ctl->cycles;
+    s_tol = ctl->tol;
+    s_bnorm = ctl->bnorm;
+  }
+  __syncthreads();
+  if (s_done) {
+    gmf_close(ctl, rank, hcond, use_cond, cap, 1);
+    return;
+  }
+  const int m = s_m;
+  double* sV = dsm;
+  double* sH = sV + (size_t)(m + 1) * Rp;
+  double* sw = sH + (hsmem ? (size_t)(m + 1) * (m + 1) : 0);
+  const double tolb = s_tol * s_bnorm;
+  int done = 0;
+  if (s_phase == PH_RESID) {
+    // r = b - A x, ||r||; restart from r / ||r|| unless converged or out of iterations
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
+      double r = b[i0 + i] - w[i0 + i];
+      sw[i] = r;
+      ss += r * r;
+    }
+    ss = cta_sum(ss, red);
+    if (threadIdx.x == 0) part[0][0] = ss;
+    cl_reduce(part[0], h1, 1, cs);
+    cl_arrive();  // the last read of another CTA's shared memory is done
+    if (threadIdx.x == 0) {
+      const double q = h1[0];
+      const double r = q > 0.0 ? rsqrt(q) : 0.0;
+      s_gj = q * r;  // ||r||
+      s_gj1 = r;     // 1 / ||r||
+    }
+    __syncthreads();
+    const double beta = s_gj;
+    int status = KFBI_OK;
+    if (beta <= tolb) {
+      done = 1;
+    } else if (s_its >= s_maxit) {
+      done = 1;
+      status = KFBI_ERR_NOT_CONVERGED;
+    } else {
+      const double inv = s_gj1;
+      for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
+        double v = sw[i] * inv;
+        V[i0 + i] = v;
+        gin[i0 + i] = v;
+        gin_f[i0 + i] = (float)v;
+      }
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+      ctl->beta = beta;
+      if (done) {
+        ctl->status = status;
+        ctl->phase = PH_DONE;
+        ctl->done = 1;
+      } else {
+        ctl->g[0] = beta;
+        for (int k = 1; k <= m; ++k) ctl->g[k] = 0.0;
+        ctl->j = 0;
+        ctl->phase = PH_ARNOLDI;
+      }
+      ctl->action = ACT_NONE;
+    }
+    cl_wait();  // no CTA leaves while another still reads its shared memory
+    gmf_close(ctl, rank, hcond, use_cond, cap, done);
+    return;
+  }
+  // Arnoldi step j: w = A v_j against V[0..j]
+  const int j = s_j;
+  const int K = j + 1;
+  {
+    const int tot = K * len;
+    for (int t0 = 0; t0 < tot; t0 += 8 * GMF_THREADS) {
+      double buf[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * GMF_THREADS + (int)threadIdx.x;
+        if (t < tot) {
+          const int k = t / len, i = t - k * len;
+          buf[u] = V[(long)k * ldv + i0 + i];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * GMF_THREADS + (int)threadIdx.x;
+        if (t < tot) {
+          const int k = t / len, i = t - k * len;
+          sV[k * Rp + i] = buf[u];
+        }
+      }
+    }
+  }
+  for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = w[i0 + i];
+  for (int i = threadIdx.x; i < j; i += GMF_THREADS) {
+    scs[i] = ctl->cs[i];
+    ssn[i] = ctl->sn[i];
+  }
+  if (threadIdx.x == 0) s_gj = ctl->g[j];
+  __syncthreads();
+  // two passes of classical Gram-Schmidt; the second also reduces ||w'||^2 (entry K)
+  cta_dots(sV, Rp, sw, len, K, false, part[0]);
+  cl_reduce(part[0], h1, K, cs);
+  cta_combine(sV, Rp, h1, K, len, sw, -1.0);
+  cta_dots(sV, Rp, sw, len, K, true, part[1]);
+  cl_reduce(part[1], h2, K + 1, cs);
+  cta_combine(sV, Rp, h2, K, len, sw, -1.0);
+  // concurrently: warp 0 forms ||w''||^2 = ||w'||^2 - ||h2||^2, warp 1 applies the previous
+  // rotations to the Hessenberg column h1 + h2
+  if (threadIdx.x < 32) {
+    double q0 = 0.0, q1 = 0.0;
+    int k = threadIdx.x;
+    for (; k + 32 < K; k += 64) {
+      q0 += h2[k] * h2[k];
+      q1 += h2[k + 32] * h2[k + 32];
+    }
+    if (k < K) q0 += h2[k] * h2[k];
+    const double q = warp_sum(q0 + q1);
+    if (threadIdx.x == 0) s_hn2 = h2[K] - q;
+  } else if (threadIdx.x < 64) {
+    for (int k = threadIdx.x - 32; k < K; k += 32) hcol[k] = h1[k] + h2[k];
+    __syncwarp();
+    if (j > 0) givens_scan(hcol, scs, ssn, j);
+  }
+  __syncthreads();
+  if (!(s_hn2 > 0.5 * h2[K])) {
+    // cancellation (w nearly in the span of V): reduce ||w''||^2 explicitly
+    double ss = 0.0;
+    for (int i = threadIdx.x; i < len; i += GMF_THREADS) ss += sw[i] * sw[i];
+    ss = cta_sum(ss, red);
+    if (threadIdx.x == 0) part[0][0] = ss;
+    cl_reduce(part[0], &s_hn2, 1, cs);
+  }
+  cl_arrive();  // the last read of another CTA's shared memory is done
+  // the new rotation from (hcol[j], ||w''||), with reciprocal square roots only:
+  //   hn = ||w''||, den = sqrt(hcol[j]^2 + hn^2), c = hcol[j] / den, s = hn / den
+  if (threadIdx.x == 0) {
+    const double hn2 = s_hn2 > 0.0 ? s_hn2 : 0.0;
+    const double rh = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
+    const double hn = hn2 * rh;
+    const double a = hcol[j];
+    const double d2 = fma(a, a, hn2);
+    const double rd = d2 > 0.0 ? rsqrt(d2) : 0.0;
+    const double den = d2 * rd;
+    const int brk = hn2 == 0.0;
+    const double cj = d2 > 0.0 ? a * rd : 1.0, sj = hn * rd;
+    hcol[j] = den;
+    hcol[j + 1] = 0.0;
+    const double gj = s_gj;
+    gy[j] = cj * gj;
+    const double gj1 = -sj * gj;
+    s_gj1 = gj1;
+    s_inv = rh;
+    s_rd = rd;
+    const int its = s_its + 1;
+    const double res = fabs(gj1);
+    s_end = (res <= tolb || its >= s_maxit || brk || j + 1 == m) ? 1 : 0;
+    if (rank == 0) {
+      double* Hc = ctl->H + (long)j * (m + 1);
+      for (int k = 0; k <= j + 1; ++k) Hc[k] = hcol[k];
+      ctl->cs[j] = cj;
+      ctl->sn[j] = sj;
+      ctl->rinv[j] = rd;
+      ctl->g[j] = gy[j];
+      ctl->g[j + 1] = gj1;
+      ctl->its = its;
+      ctl->res_est = res;
+      ctl->hnorm = hn;
+      ctl->breakdown = brk;
+    }
+  }
+  __syncthreads();
+  if (!s_end) {
+    const double inv = s_inv;
+    for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
+      double v = sw[i] * inv;
+      V[(long)(j + 1) * ldv + i0 + i] = v;
+      gin[i0 + i] = v;
+      gin_f[i0 + i] = (float)v;
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+      ctl->j = j + 1;
+      ctl->phase = PH_ARNOLDI;
+      ctl->action = ACT_NONE;
+    }
+  } else {
+    // end of the cycle: y = R^{-1} g by column-oriented back substitution (every CTA, with
+    // the stored reciprocals of the diagonal), then x += V y over this CTA's rows
+    const double res = fabs(s_gj1);
+    for (int i = threadIdx.x; i < j; i += GMF_THREADS) {
+      gy[i] = ctl->g[i];
+      scs[i] = ctl->rinv[i];
+    }
+    if (threadIdx.x == 0) scs[j] = s_rd;
+    if (hsmem)
+      for (int t = threadIdx.x; t < j * (m + 1); t += GMF_THREADS) sH[t] = ctl->H[t];
+    __syncthreads();
+    for (int i = K - 1; i >= 0; --i) {
+      const double* Hi = i == j ? hcol : (hsmem ? sH : ctl->H) + (long)i * (m + 1);
+      const double yi = gy[i] * scs[i];
+      __syncthreads();
+      for (int q = threadIdx.x; q < i; q += GMF_THREADS) gy[q] = fma(-Hi[q], yi, gy[q]);
+      if (threadIdx.x == 0) gy[i] = yi;
+      __syncthreads();
+    }
+    // x slice into sw (w is no longer needed), x += V y, then the next apply's input
+    for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = x[i0 + i];
+    __syncthreads();
+    cta_combine(sV, Rp, gy, K, len, sw, 1.0);
+    for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
+      double v = sw[i];
+      x[i0 + i] = v;
+      gin[i0 + i] = v;
+      gin_f[i0 + i] = (float)v;
+    }
+    const bool conv = s_trust && res <= tolb;
+    if (rank == 0 && threadIdx.x == 0) {
+      for (int i = 0; i < K; ++i) ctl->y[i] = gy[i];
+      ctl->k_end = K;
+      ctl->cycles = s_cycles + 1;
+      ctl->action = ACT_NONE;
+      if (conv) {
+        ctl->status = KFBI_OK;
+        ctl->beta = res;
+        ctl->phase = PH_DONE;
+        ctl->done = 1;
+      } else {
+        ctl->phase = PH_RESID;
+      }
+    }
+    done = conv ? 1 : 0;
+  }
+  cl_wait();  // no CTA leaves while another still reads its shared memory
+  gmf_close(ctl, rank, hcond, use_cond, cap, done);
+}
+
 // --------------------------------------------------------------------------- host side
-static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, const double* b, double* x) {
+// Largest dynamic shared memory the cluster kernel may use (set once per context).
+static size_t gmf_smem_limit(kfbi_ctx* c) {
+  if (c->gmf_smem_max == 0) {
+    cudaFuncAttributes fa{};
+    int optin = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_gm_cluster) != cudaSuccess) {
+      cudaGetLastError();
+      c->gmf_smem_max = 1;
+      return 0;
+    }
+    size_t lim = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+    if (cudaFuncSetAttribute(k_gm_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) != cudaSuccess ||
+        cudaFuncSetAttribute(k_gm_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      lim = 0;
+    }
+    c->gmf_smem_max = lim > 0 ? lim : 1;
+  }
+  return c->gmf_smem_max > 1 ? c->gmf_smem_max : 0;
+}
+
+static cudaLaunchConfig_t gmf_launch_config(kfbi_ctx* c, const kfbi_ctx::GmfConfig& g, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(g.cs, 1, 1);
+  cfg.blockDim = dim3(GMF_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = g.smem;
+  cfg.stream = c->stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = g.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Cluster form for n nodes and restart m: 16 CTAs (else 8) whose slices of V (and, when it
+// fits, the Hessenberg matrix for the back substitution) fit in shared memory and that the
+// device can co-schedule. cs = 0: the multi-kernel form.
+static kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m) {
+  kfbi_ctx::GmfConfig none{};
+  if (!c->gm_cluster) return none;
+  if (c->gmf.n == n && c->gmf.m == m) return c->gmf;
+  const size_t lim = gmf_smem_limit(c);
+  kfbi_ctx::GmfConfig pick{};
+  pick.n = n;
+  pick.m = m;
+  for (int cs : {16, 8}) {
+    if (pick.cs) break;
+    const int R = cdiv(n, cs), Rp = gmf_row_stride(R);
+    const size_t base = sizeof(double) * ((size_t)(m + 1) * Rp + Rp);
+    for (int hs : {1, 0}) {
+      const size_t smem = base + (hs ? sizeof(double) * (size_t)(m + 1) * (m + 1) : 0);
+      if (smem > lim) continue;
+      kfbi_ctx::GmfConfig g{n, m, cs, R, hs, smem};
+      cudaLaunchAttribute attr[1];
+      cudaLaunchConfig_t cfg = gmf_launch_config(c, g, attr);
+      int nc = 0;
+      if (cudaOccupancyMaxActiveClusters(&nc, k_gm_cluster, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        nc = 0;
+      }
+      if (nc >= 1) {
+        pick = g;
+        break;
+      }
+    }
+  }
+  c->gmf = pick;
+  return pick;
+}
+
+static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, const double* b, double* x,
+                        const kfbi_ctx::GmfConfig& gf, cudaGraphConditionalHandle hcond, int use_cond, int cap) {
   cudaStream_t s = c->stream;
   const int n = c->n;
   const int* done = &c->gctl->done;
   int layer = kind == KFBI_BIE_STEFAN_SL ? KFBI_SINGLE : KFBI_DOUBLE;
   KFBI_CHECK(apply_enqueue(c, layer, fp32, c->gin, c->gw, nullptr, nullptr, kind, eps_v, done, c->gin_f));
   const int ldv = c->max_nodes;
+  if (gf.cs > 0) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = gmf_launch_config(c, gf, attr);
+    launched(c, 1);
+    KFBI_TRY(cudaLaunchKernelEx(&cfg, k_gm_cluster, c->gctl, c->gV, ldv, (const double*)c->gw, b, x, c->gin,
+                                c->gin_f, n, gf.R, gf.hsmem, hcond, use_cond, cap));
+    return KFBI_OK;
+  }
   const int dblocks = c->gm_m + 1;
   const int ublocks = cdiv(n, 32);
   launched(c, 5);
@@ -380,6 +931,10 @@ static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, c
   k_gm_dots<<<dblocks, GM_THREADS, 0, s>>>(c->gctl, c->gV, ldv, c->gw, b, c->gr, n, c->gpart, 1);
   k_gm_update<<<ublocks, 32 * UPD_WARPS, 0, s>>>(c->gctl, c->gV, ldv, c->gw, n, c->gpart, 1);
   k_gm_finish<<<GM_BLOCKS, GM_THREADS, 0, s>>>(c->gctl, c->gV, ldv, c->gw, c->gr, x, c->gin, c->gin_f, n);
+  if (use_cond) {
+    launched(c, 1);
+    k_gm_cond<<<1, 32, 0, s>>>(c->gctl, hcond, cap);
+  }
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
 }
@@ -389,7 +944,7 @@ static int body_cap(int max_iter, int m) { return 2 * max_iter + 2 * (max_iter /
 // Builds the graph of one solve: a conditional WHILE node whose body (captured from the
 // stream) is one GMRES iteration followed by k_gm_cond.
 static kfbi_status build_graph(kfbi_ctx* c, kfbi_ctx::SolveGraph& G, int kind, bool fp32, const double* eps_v,
-                               const double* b, double* x, int cap) {
+                               const double* b, double* x, int cap, const kfbi_ctx::GmfConfig& gf) {
   if (G.exec) cudaGraphExecDestroy(G.exec);
   if (G.graph) cudaGraphDestroy(G.graph);
   G.exec = nullptr;
@@ -410,8 +965,8 @@ static kfbi_status build_graph(kfbi_ctx* c, kfbi_ctx::SolveGraph& G, int kind, b
   KFBI_TRY(cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
   c->capturing = true;
   const long long l0 = c->launches;
-  kfbi_status st = body(c, kind, fp32, eps_v, b, x);
-  if (st == KFBI_OK) k_gm_cond<<<1, 32, 0, s>>>(c->gctl, h, cap);
+  kfbi_status st = body(c, kind, fp32, eps_v, b, x, gf, h, 1, cap);
+  G.body_launches = (int)(c->launches - l0);
   c->launches = l0;  // capture launches nothing; replays are counted per body
   c->capturing = false;
   cudaGraph_t out = nullptr;
@@ -436,6 +991,8 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   if (m < 1) m = 1;
   c->gm_m = m;
   const int cap = body_cap(max_iter, m);
+  const kfbi_ctx::GmfConfig gf = gmf_select(c, n, m);
+  c->gmf_last_cs = gf.cs;
   const size_t hdr = offsetof(GmresCtl, g);
   launched(c, 2);
   k_gm_init<<<1, 32, 0, s>>>(c->gctl, tol, max_iter, m, trust ? 1 : 0);
@@ -444,9 +1001,10 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   if (c->use_graphs && !c->timing) {
     kfbi_ctx::SolveGraph& G = c->sgraph[kind][fp32 ? 1 : 0];
     kfbi_status st = KFBI_OK;
-    if (G.exec == nullptr || G.version != c->iface_version || G.m != m) {
-      st = build_graph(c, G, kind, fp32, eps_v, b, x, cap);
+    if (G.exec == nullptr || G.version != c->iface_version || G.m != m || G.cs != gf.cs) {
+      st = build_graph(c, G, kind, fp32, eps_v, b, x, cap, gf);
       G.m = m;
+      G.cs = gf.cs;
     }
     if (st == KFBI_OK && cudaGraphLaunch(G.exec, s) == cudaSuccess) {
       graphed = true;
@@ -458,12 +1016,12 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   if (graphed) {
     KFBI_TRY(cudaMemcpyAsync(c->host_gctl, c->gctl, hdr, cudaMemcpyDeviceToHost, s));
     KFBI_TRY(cudaStreamSynchronize(s));
-    // bodies replayed by the graph: one apply plus five Gram-Schmidt kernels and the loop test
-    c->launches += (long long)c->host_gctl->bodies * (c->per_apply_launches[fp32 ? 1 : 0] + 6);
+    // bodies replayed by the graph: one apply, the Gram-Schmidt kernel(s) and the loop test
+    c->launches += (long long)c->host_gctl->bodies * c->sgraph[kind][fp32 ? 1 : 0].body_launches;
   } else {
     int launched_bodies = 0, chunk = 2;
     while (true) {
-      for (int q = 0; q < chunk; ++q) KFBI_CHECK(body(c, kind, fp32, eps_v, b, x));
+      for (int q = 0; q < chunk; ++q) KFBI_CHECK(body(c, kind, fp32, eps_v, b, x, gf, 0, 0, cap));
       launched_bodies += chunk;
       KFBI_TRY(cudaMemcpyAsync(c->host_gctl, c->gctl, hdr, cudaMemcpyDeviceToHost, s));
       KFBI_TRY(cudaStreamSynchronize(s));

@@ -85,6 +85,7 @@ struct StencilF {
   float dx[6], dy[6];
   float r0[6], r1[6], r2[6];
   float nx, ny;
+  float w;
 };
 
 // GMRES control block in device memory. The scalar header comes first so that the host
@@ -108,6 +109,7 @@ struct GmresCtl {
   double g[MAX_RESTART + 1];
   double cs[MAX_RESTART], sn[MAX_RESTART];
   double y[MAX_RESTART];
+  double rinv[MAX_RESTART];       // 1 / R[i][i] of the rotated Hessenberg matrix (cluster form)
   double hcol[MAX_RESTART + 1];   // Gram-Schmidt coefficients of the current pass
   double H[(MAX_RESTART + 1) * MAX_RESTART];  // column-major, leading dim m+1
 };
@@ -215,7 +217,18 @@ struct kfbi_ctx {
     cudaGraphExec_t exec = nullptr;
     long version = -1;
     int m = 0;
+    int cs = 0;             // cluster size of the Gram-Schmidt kernel (0: multi-kernel form)
+    int body_launches = 0;  // kernels per replayed body
   } sgraph[3][2];
+  // cluster form of the GMRES body (k_gm_cluster) for the last (n, m); cs = 0: multi-kernel
+  struct GmfConfig {
+    int n = -1, m = -1;
+    int cs = 0, R = 0, hsmem = 0;
+    size_t smem = 0;
+  } gmf;
+  bool gm_cluster = true;       // allow the cluster form
+  int gmf_last_cs = 0;          // cluster size used by the last GMRES run
+  size_t gmf_smem_max = 0;      // 0 = not queried yet, 1 = unavailable
   long iface_version = 0;
   bool use_graphs = true;
   bool capturing = false;

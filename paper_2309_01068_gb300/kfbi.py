@@ -18,6 +18,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "kfbi.h")
 
 # codes mirrored from include/kfbi.h
 OK, ERR_ARG, ERR_CUDA, ERR_OUTSIDE_BOX, ERR_UNDERRESOLVED, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
+OPT_CUDA_GRAPHS, OPT_CLUSTER_GMRES, OPT_LAST_CLUSTER = 1, 2, 3
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2
 FP64, MIXED = 0, 1
@@ -76,6 +77,8 @@ _SIGNATURES = {
     "kfbi_timing_enable": (_I, [_P, _I]),
     "kfbi_timing_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "kfbi_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    "kfbi_set_option": (_I, [_P, _I, _I]),
+    "kfbi_get_option": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "kfbi_grid_solve_noalloc": (_I, [_I, _D, _D, _I, _P, _P, _P]),
 }
 
@@ -256,6 +259,16 @@ class Context:
         _check(self.lib.kfbi_timing_read(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                          ctypes.byref(d)), "kfbi_timing_read")
         return dict(fp64_ms=a.value, fp64_launches=b.value, fp32_ms=c.value, fp32_launches=d.value)
+
+    def set_option(self, option, value):
+        """kfbi_set_option: OPT_CUDA_GRAPHS or OPT_CLUSTER_GMRES to 0 / 1."""
+        _check(self.lib.kfbi_set_option(self.handle, int(option), int(value)), "kfbi_set_option")
+
+    def get_option(self, option):
+        """kfbi_get_option: OPT_CUDA_GRAPHS, OPT_CLUSTER_GMRES or OPT_LAST_CLUSTER."""
+        v = ctypes.c_int()
+        _check(self.lib.kfbi_get_option(self.handle, int(option), ctypes.byref(v)), "kfbi_get_option")
+        return v.value
 
     def launch_count(self):
         v = ctypes.c_longlong()

@@ -156,6 +156,42 @@ def test_gmres_restart_and_not_converged():
     assert info2["status"] == K.ERR_NOT_CONVERGED and info2["iterations"] == 2
 
 
+@pytest.mark.parametrize("graphs,cluster", [(1, 1), (1, 0), (0, 1), (0, 0)])
+@pytest.mark.parametrize("precision,restart", [(0, 100), (0, 10), (1, 100)])
+def test_gmres_forms_agree_with_oracle(graphs, cluster, precision, restart):
+    """The graph loop and the host-polled loop, the cluster and the five-kernel Gram-Schmidt
+    step: each reaches the oracle's GMRES density (n = 131 leaves the last cluster slices
+    ragged or empty)."""
+    p = W.random_problem(61, N=128, n=131)
+    ctx, ref = make(p, OK.BOX_DIRICHLET0, precision=precision)
+    ctx.set_option(K.OPT_CUDA_GRAPHS, graphs)
+    ctx.set_option(K.OPT_CLUSTER_GMRES, cluster)
+    assert ctx.get_option(K.OPT_CUDA_GRAPHS) == graphs
+    rhs = W.random_density(5, p.n)
+    tol = 1e-12 if precision == 0 else 1e-10
+    phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(rhs), tol=tol, max_iter=400, restart=restart)
+    cs = ctx.get_option(K.OPT_LAST_CLUSTER)
+    assert (cs in (8, 16)) if cluster else cs == 0
+    rphi, rinfo = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), rhs, tol=1e-13, restart=restart)
+    assert info["status"] == 0 and info["rel_residual"] <= tol
+    if restart < 100:
+        assert info["restarts"] > 0
+    assert rel(phi.cpu().numpy(), rphi) < (1e-9 if precision == 0 else 1e-8)
+
+
+def test_gmres_cluster_long_restart_without_staged_hessenberg():
+    """Restart 200: the Hessenberg matrix does not fit in the cluster's shared memory beside
+    V, so the back substitution reads it from global memory; density vs the oracle."""
+    p = W.random_problem(62, N=256, n=256)
+    ctx, ref = make(p, OK.BOX_DIRICHLET0)
+    rhs = W.random_density(6, p.n)
+    phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(rhs), tol=1e-12, max_iter=400, restart=200)
+    assert ctx.get_option(K.OPT_LAST_CLUSTER) in (8, 16)
+    rphi, _ = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), rhs, tol=1e-13, restart=200)
+    assert info["status"] == 0
+    assert rel(phi.cpu().numpy(), rphi) < 1e-9
+
+
 def test_mixed_precision_refinement():
     """FP32 grid applies inside GMRES, FP64 residual and refinement: density within 1e-9 of FP64."""
     p = W.config_small_laplace()
