@@ -295,10 +295,14 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             device can schedule it; 0: the five-kernel form.
  *   KFBI_OPT_LAST_CLUSTER     read only: cluster size used by the last GMRES run (0 = the
  *                             five-kernel form).
+ *   KFBI_OPT_PDL              1 (default): consecutive kernels of an apply and of a GMRES
+ *                             iteration use programmatic dependent launch (a kernel starts
+ *                             while its predecessor finishes and waits on the device before
+ *                             it reads the predecessor's output); 0: plain stream order.
  * kfbi_set_option: value 0 or 1. kfbi_get_option writes the value to *value (host).
  * Errors: ARG (unknown option, bad value, NULL, read-only option).
  */
-enum { KFBI_OPT_CUDA_GRAPHS = 1, KFBI_OPT_CLUSTER_GMRES = 2, KFBI_OPT_LAST_CLUSTER = 3 };
+enum { KFBI_OPT_CUDA_GRAPHS = 1, KFBI_OPT_CLUSTER_GMRES = 2, KFBI_OPT_LAST_CLUSTER = 3, KFBI_OPT_PDL = 4 };
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);
 

@@ -10,7 +10,8 @@ namespace kfbi {
 
 kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy);
 kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const double* rhs, double tol, int max_iter,
-                           int restart, double* x, kfbi_solve_info* info);
+                           int restart, double* x, kfbi_solve_info* info,
+                           double* dnormal = nullptr);
 
 static thread_local char g_last_error[512] = {0};
 
@@ -94,7 +95,7 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
 }
 
 static void free_all(kfbi_ctx* c) {
-  void* ptrs[] = {c->sintab, c->sintab_f, c->lam, c->lam_f, c->twN, c->twN_f, c->xy, c->twn, c->icoef, c->fine,
+  void* ptrs[] = {c->sintab, c->sintab_f, c->lam, c->lam_f, c->twN, c->twN_f, c->xy, c->twn, c->icoef, c->fine, c->twM,
                   c->seg_count, c->seg_off, c->cr_kind, c->cr_line, c->cr_seg, c->cr_first, c->cr_alpha, c->cr_xi,
                   c->tgeo, c->tgeo_f, c->stencil_f, c->dens_f, c->stw, c->stw_d, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->stencil,
                   c->probe_mark, c->prow_cnt, c->prow_ptr, c->probe_i, c->flags, c->counts, c->dcoef, c->dint,
@@ -155,6 +156,7 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->facespec, 2 * (size_t)N));
   KFBI_CHECK(dalloc(&c->icoef, 4 * (size_t)nk));
   KFBI_CHECK(dalloc(&c->fine, 2 * (size_t)M));
+  KFBI_CHECK(dalloc(&c->twM, 2 * (size_t)M));
   KFBI_CHECK(dalloc(&c->seg_count, 2 * (size_t)M + 1));
   KFBI_CHECK(dalloc(&c->seg_off, 2 * (size_t)M + 1));
   KFBI_CHECK(dalloc(&c->hcount, NN));
@@ -434,6 +436,8 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
   } else if (option == KFBI_OPT_CLUSTER_GMRES) {
     c->gm_cluster = value != 0;
     c->gmf = kfbi_ctx::GmfConfig{};
+  } else if (option == KFBI_OPT_PDL) {
+    c->use_pdl = value != 0;
   } else {
     return KFBI_ERR_ARG;
   }
@@ -445,6 +449,7 @@ kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
   if (option == KFBI_OPT_CUDA_GRAPHS) *value = c->use_graphs ? 1 : 0;
   else if (option == KFBI_OPT_CLUSTER_GMRES) *value = c->gm_cluster ? 1 : 0;
   else if (option == KFBI_OPT_LAST_CLUSTER) *value = c->gmf_last_cs;
+  else if (option == KFBI_OPT_PDL) *value = c->use_pdl ? 1 : 0;
   else return KFBI_ERR_ARG;
   return KFBI_OK;
 }

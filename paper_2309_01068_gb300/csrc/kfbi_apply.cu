@@ -95,6 +95,8 @@ __device__ __forceinline__ double irr_sign(const IrrNode& q, double) { return q.
 __device__ __forceinline__ float irr_sign(const IrrNode& q, float) { return q.signf; }
 
 __global__ void k_to_float(const double* a, float* b, int n, const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -109,6 +111,8 @@ __global__ void k_to_float(const double* a, float* b, int n, const int* skip) {
 template <typename T, bool SMEM, typename S_t>
 __global__ void k_dens_coef(const T* phi, int n, const V2<T>* tw, const S_t* st, V2<T>* coef, T* dint,
                             const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   __shared__ T red[32];
@@ -158,21 +162,21 @@ __global__ void k_dens_coef(const T* phi, int n, const V2<T>* tw, const S_t* st,
 }
 
 // Warp-level jumps at one target (App. A.1, Table 2): the warp sums the density interpolant
-// and its first two derivatives from the precomputed twiddle starts `ts` (lane l sums the
-// modes [k0_l, k0_l + chunk) from e^{i k0_l alpha}, rotating by e^{i alpha}; the Nyquist term
-// uses e^{i n alpha / 2}), then every lane solves the 2x2 and 3x3 systems and holds
+// and its first two derivatives from the precomputed twiddle starts (lane l sums the modes
+// [k0_l, k0_l + chunk) from e0 = e^{i k0_l alpha}, rotating by s1 = e^{i alpha}; the Nyquist
+// term uses q = e^{i n alpha / 2}), then every lane solves the 2x2 and 3x3 systems and holds
 // J = ([u], [u_x], [u_y], [u_xx], [u_yy], [u_xy]).
 template <typename T, typename G>
-__device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, const V2<T>* ts, const G& g, int layer,
-                                          T kappa, int lane, T J[6]) {
+__device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, V2<T> e0, V2<T> s1, V2<T> q, const G& g,
+                                          int layer, T kappa, int lane, T J[6]) {
   const int K = (n - 1) / 2;
   const int chunk = (K + 31) / 32;
   int k0 = 1 + lane * chunk;
   int k1 = min(K + 1, k0 + chunk);
   T a = 0, b = 0, d = 0;
   if (k0 < k1) {
-    V2<T> e = ts[lane];
-    const V2<T> s = ts[32];
+    V2<T> e = e0;
+    const V2<T> s = s1;
     for (int k = k0; k < k1; ++k) {
       V2<T> ck = coef[k];
       T re = ck.x * e.x - ck.y * e.y;
@@ -188,7 +192,6 @@ __device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, const V2<T>*
   b = (T)2 * wsum(b);
   d = (T)2 * wsum(d);
   if ((n & 1) == 0) {
-    const V2<T> q = ts[33];
     T m = (T)(n / 2);
     T nyq = coef[n / 2].x;
     a += nyq * q.x;
@@ -221,6 +224,20 @@ __device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, const V2<T>*
 template <typename T, typename G, bool SMEM>
 __global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const G* tg, const V2<T>* tstart, int layer,
                                T kappa, T* Jout, const int* skip) {
+  int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  // geometry and twiddle starts of this target (set with the interface) before the wait
+  G geo{};
+  V2<T> e0{}, s1{}, q{};
+  if (t < ntg) {
+    geo = tg[t];
+    const V2<T>* ts = tstart + (long)t * TSTART_STRIDE;
+    e0 = ts[lane];
+    s1 = ts[32];
+    q = ts[33];
+  }
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   const V2<T>* sc = coef;
@@ -231,11 +248,9 @@ __global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const G* tg, c
     __syncthreads();
     sc = w;
   }
-  int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
   if (t >= ntg) return;
   T J[6];
-  jump_eval<T, G>(sc, n, tstart + (long)t * TSTART_STRIDE, tg[t], layer, kappa, lane, J);
+  jump_eval<T, G>(sc, n, e0, s1, q, geo, layer, kappa, lane, J);
   if (lane < 6) Jout[(long)t * 6 + lane] = J[lane];
 }
 
@@ -245,6 +260,8 @@ __global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const G* tg, c
 template <typename T, typename T4, bool SMEM>
 __global__ void k_box_data(const T* phi, int n, const T4* npack, int N, double xmin, double xmax, double ymin,
                            double ymax, double h, T scale, T* boxg, const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   T4* sp = (T4*)smem_raw;  // (x, y, phi y_a, -phi x_a)
@@ -395,6 +412,8 @@ __device__ __forceinline__ void dct_pre(int N, int m, const T* tab, V2<T> Gm, V2
 template <typename T>
 __global__ void k_face_dst(int N, int logN, int dct, const V2<T>* tw, const T* tab, const T* boxg, T* out,
                            const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
@@ -438,6 +457,8 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
                                                             const T* J, T inv_h2, const T* boxg,
                                                             const T* facespec, const T* tab, float scale, T* spec,
                                                             const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   __shared__ int si[ROW_CAP];
   __shared__ T sv[ROW_CAP];
@@ -511,6 +532,8 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
 template <typename T>
 __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, const T* tab, const T* lam,
                             T kappa, T* spec, const int* skip) {
+  pdl_wait();
+  pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
@@ -567,9 +590,11 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
 template <typename T>
 __global__ void k_probe_values(int N, int dct, const int* prow_list, const int* prow_ptr, const int* probe_i,
                                const T* spec, const T* tab, float scale, T* pval, const int* skip) {
-  if (*skip) return;
   const int j = prow_list[blockIdx.x];
   const int b = prow_ptr[j], e = prow_ptr[j + 1];
+  pdl_wait();
+  pdl_trigger();
+  if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   T* row = (T*)smem_raw;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -663,23 +688,42 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
 template <typename T, typename S_t>
 __global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const T* x_in, const double* eps_v, T ca,
                          T cb, T cc, const T* dint, double* out, double* dnormal, const int* skip) {
-  if (*skip) return;
   int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
+  // this lane's stencil point (set with the interface) before the wait
+  const int m = lane;
+  int probe = 0, minus = 0;
+  T dx = 0, dy = 0, r0 = 0, r1 = 0, r2 = 0, nx = 0, ny = 0;
+  if (p < n) {
+    const S_t& S = st[p];
+    if (m < 6) {
+      probe = S.probe[m];
+      minus = S.minus[m];
+      dx = (T)S.dx[m];
+      dy = (T)S.dy[m];
+      r0 = (T)S.r0[m];
+      r1 = (T)S.r1[m];
+      r2 = (T)S.r2[m];
+    }
+    if (m == 0) {
+      nx = (T)S.nx;
+      ny = (T)S.ny;
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (*skip) return;
   if (p >= n) return;
-  const S_t& S = st[p];
   const T* J = Jn ? Jn + (long)p * 6 : nullptr;
   T v = 0, gx = 0, gy = 0;
-  if (lane < 6) {
-    const int m = lane;
-    T u = pval[S.probe[m]];
-    if (J != nullptr && S.minus[m]) {
-      T dx = (T)S.dx[m], dy = (T)S.dy[m];
+  if (m < 6) {
+    T u = pval[probe];
+    if (J != nullptr && minus) {
       u += J[0] + dx * J[1] + dy * J[2] + (T)0.5 * dx * dx * J[3] + dx * dy * J[5] + (T)0.5 * dy * dy * J[4];
     }
-    v = (T)S.r0[m] * u;
-    gx = (T)S.r1[m] * u;
-    gy = (T)S.r2[m] * u;
+    v = r0 * u;
+    gx = r1 * u;
+    gy = r2 * u;
   }
   for (int o = 4; o > 0; o >>= 1) {
     v += __shfl_down_sync(0xffffffffu, v, o);
@@ -696,7 +740,7 @@ __global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const
   if (x_in != nullptr) o += (eps_v != nullptr ? (T)eps_v[p] : ca) * x_in[p];
   if (dint != nullptr) o += cc * (*dint);
   out[p] = (double)o;
-  if (dnormal != nullptr) dnormal[p] = (double)((T)S.nx * gx + (T)S.ny * gy);
+  if (dnormal != nullptr) dnormal[p] = (double)(nx * gx + ny * gy);
 }
 
 // --------------------------------------------------------------------------- host side
@@ -720,9 +764,9 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
   size_t smem = 2 * sizeof(V2<T>) * (size_t)P * N;
   const bool rec = c->timing && !c->capturing && c->timing_used < TIMING_CAP;
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
-  k_col_solve<T><<<N / (2 * P), col_threads(N, P), smem, c->stream>>>(N, c->logN, P, c->boxbc == KFBI_BOX_NEUMANN0,
-                                                                  Tabs<T>::stw(c), Tabs<T>::sin(c), Tabs<T>::lam(c),
-                                                                  (T)c->kappa, spec, skip);
+  KFBI_TRY(launch_k(c->use_pdl && !rec, k_col_solve<T>, dim3(N / (2 * P)), dim3(col_threads(N, P)), smem, c->stream, N,
+                    c->logN, P, (int)(c->boxbc == KFBI_BOX_NEUMANN0), Tabs<T>::stw(c), Tabs<T>::sin(c), Tabs<T>::lam(c),
+                    (T)c->kappa, spec, skip));
   launched(c, 1);
   if (rec) {
     KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used + 1], c->stream));
@@ -792,7 +836,8 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
       k_box_data<T, T4, false><<<cdiv((long)4 * N * 32, 256), 256, 0, s2>>>(
           dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, bscale, boxg, skip);
     size_t smf = 2 * sizeof(V2<T>) * (size_t)N;
-    k_face_dst<T><<<1, 256, smf, s2>>>(N, c->logN, dct, Tabs<T>::stw(c), tab, boxg, face, skip);
+    KFBI_TRY(launch_k(c->use_pdl, k_face_dst<T>, dim3(1), dim3(256), smf, s2, N, c->logN, dct, Tabs<T>::stw(c), tab,
+                      (const T*)boxg, face, skip));
     KFBI_TRY(cudaEventRecord(c->ev_join, s2));
     launched(c, 2);
   }
@@ -808,11 +853,11 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
   const size_t smj = (size_t)nk * sizeof(V2<T>);
   if (smj <= SMEM_STAGE_MAX)
-    k_target_jumps<T, G, true><<<cdiv((long)ntg * 32, 256), 256, smj, s>>>(coef, n, ntg, Tabs<T>::geo(c),
-                                                                          Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip);
+    KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, true>, dim3(cdiv((long)ntg * 32, 256)), dim3(256), smj, s,
+                      (const V2<T>*)coef, n, ntg, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
   else
-    k_target_jumps<T, G, false><<<cdiv((long)ntg * 32, 256), 256, 0, s>>>(coef, n, ntg, Tabs<T>::geo(c),
-                                                                         Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip);
+    KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, false>, dim3(cdiv((long)ntg * 32, 256)), dim3(256), 0, s,
+                      (const V2<T>*)coef, n, ntg, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
   launched(c, 2);
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   k_row_forward<T><<<N, ROW_THREADS, 0, s>>>(N, dct, c->row_ptr, c->irr, J, (T)(1.0 / (c->h * c->h)), fs ? boxg : nullptr,
@@ -820,19 +865,22 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   launched(c, 1);
   KFBI_CHECK(launch_col_solve<T>(c, spec, skip));
   if (c->n_prow > 0) {
-    k_probe_values<T><<<c->n_prow, 256, sizeof(T) * (size_t)N, s>>>(N, dct, c->prow_list, c->prow_ptr, c->probe_i,
-                                                                     spec, tab, scale, pval, skip);
+    KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(c->n_prow), dim3(256), sizeof(T) * (size_t)N, s, N, dct,
+                      (const int*)c->prow_list, (const int*)c->prow_ptr, (const int*)c->probe_i, (const T*)spec, tab,
+                      scale, pval, skip));
     launched(c, 1);
   }
   if (grid != nullptr) KFBI_CHECK(launch_row_dense<T>(c, 1, nullptr, spec, grid));
+  using S_t = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(c))>::type>::type;
   T ca = 0, cb = 1, cc = 0;
   const double* ev = nullptr;
   const T* xin = nullptr;
   if (bie_kind == KFBI_BIE_INTERIOR_DL) { ca = (T)0.5; xin = dens_t; }
   else if (bie_kind == KFBI_BIE_HS_EXTERIOR_MDL) { ca = (T)-0.5; cc = 1; xin = dens_t; }
   else if (bie_kind == KFBI_BIE_STEFAN_SL) { cb = -1; ev = eps_v; xin = dens_t; }
-  k_interp<T><<<cdiv((long)n * 32, 256), 256, 0, s>>>(n, Tabs<T>::stencil(c), pval, J + (long)ncr * 6, xin, ev, ca, cb,
-                                                      cc, want_int ? dint_t : nullptr, values, dnormal, skip);
+  KFBI_TRY(launch_k(c->use_pdl, k_interp<T, S_t>, dim3(cdiv((long)n * 32, 256)), dim3(256), 0, s, n,
+                    Tabs<T>::stencil(c), (const T*)pval, (const T*)(J + (long)ncr * 6), xin, ev, ca, cb, cc,
+                    (const T*)(want_int ? dint_t : nullptr), values, dnormal, skip));
   launched(c, 1);
   c->per_apply_launches[sizeof(T) == 4 ? 1 : 0] = (int)(c->launches - l0);
   KFBI_TRY(cudaGetLastError());

@@ -10,48 +10,103 @@ namespace kfbi {
 // --------------------------------------------------------------------------- interpolant
 // Real function f(alpha) = c_0 + 2 sum_{k=1}^{K} Re(c_k e^{ik alpha}) + nyq cos(n alpha / 2)
 // with K = (n-1)/2 and nyq = c_{n/2} for even n. A warp evaluates f, f', f'' at one
-// alpha: each lane sums a contiguous block of modes with a rotation recurrence started
-// from sincos(k0 alpha); all lanes return the full sums.
+// alpha: lane l sums the modes [k0_l, k0_l + chunk) (k0_l = 1 + l chunk) from its start
+// e^{i k0_l alpha}; all lanes return the full sums. The float64 pipe has a long latency,
+// so the rotation runs as four interleaved recurrences (phases k0 + q, q = 0..3, advanced
+// by e^{4 i alpha}) instead of one.
 struct TrigSums {
   double f, f1, f2;
 };
 
-__device__ __forceinline__ TrigSums trig_warp(const double2* c, int n, double alpha, int lane, bool d2) {
+// e^{i k0_l alpha} of this lane, e^{i alpha} and e^{i n alpha / 2}
+struct TrigStart {
+  double2 e0, s1, q;
+};
+
+__device__ __forceinline__ int trig_k0(int n, int lane) {
+  const int K = (n - 1) / 2;
+  return 1 + lane * ((K + 31) / 32);
+}
+
+// starts from sincos at an arbitrary alpha
+__device__ __forceinline__ TrigStart trig_start(int n, double alpha, int lane) {
+  TrigStart t;
+  double sn, cs;
+  sincos((double)trig_k0(n, lane) * alpha, &sn, &cs);
+  t.e0 = make_double2(cs, sn);
+  sincos(alpha, &sn, &cs);
+  t.s1 = make_double2(cs, sn);
+  sincos(0.5 * (double)n * alpha, &sn, &cs);
+  t.q = make_double2(cs, sn);
+  return t;
+}
+
+// starts at alpha = 2 pi s / M from the table tw[m] = e^{2 pi i m / M} (exact index arithmetic)
+__device__ __forceinline__ TrigStart trig_start_table(const double2* tw, int M, long s, int n, int lane) {
+  TrigStart t;
+  t.e0 = tw[((long)trig_k0(n, lane) * s) % M];
+  t.s1 = tw[s % M];
+  t.q = tw[((long)(n / 2) * s) % M];
+  return t;
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ TrigSums trig_sums(const double2* c, int n, const TrigStart& st, int lane, bool d2) {
   const int K = (n - 1) / 2;
   const int chunk = (K + 31) / 32;
-  int k0 = 1 + lane * chunk;
-  int k1 = min(K + 1, k0 + chunk);
-  double f = 0.0, f1 = 0.0, f2 = 0.0;
+  const int k0 = 1 + lane * chunk;
+  const int k1 = min(K + 1, k0 + chunk);
+  double f[4] = {0.0, 0.0, 0.0, 0.0}, g[4] = {0.0, 0.0, 0.0, 0.0}, h[4] = {0.0, 0.0, 0.0, 0.0};
   if (k0 < k1) {
-    double er, ei, sr, si;
-    sincos((double)k0 * alpha, &ei, &er);
-    sincos(alpha, &si, &sr);
-    for (int k = k0; k < k1; ++k) {
-      double2 ck = c[k];
-      double re = ck.x * er - ck.y * ei;
-      double im = ck.x * ei + ck.y * er;
-      f += re;
-      f1 -= (double)k * im;
-      if (d2) f2 -= (double)k * (double)k * re;
-      double t = er * sr - ei * si;
-      ei = er * si + ei * sr;
-      er = t;
+    const double2 s1 = st.s1;
+    const double2 s2 = zmul(s1, s1);
+    const double2 s3 = zmul(s2, s1);
+    const double2 s4 = zmul(s2, s2);
+    double2 e[4] = {st.e0, zmul(st.e0, s1), zmul(st.e0, s2), zmul(st.e0, s3)};
+    for (int k = k0; k < k1; k += 4) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int kk = k + q;
+        if (kk < k1) {
+          const double2 ck = c[kk];
+          const double re = ck.x * e[q].x - ck.y * e[q].y;
+          const double im = ck.x * e[q].y + ck.y * e[q].x;
+          f[q] += re;
+          g[q] -= (double)kk * im;
+          if (d2) h[q] -= (double)kk * (double)kk * re;
+          e[q] = zmul(e[q], s4);
+        }
+      }
     }
   }
-  f = 2.0 * warp_sum(f);
-  f1 = 2.0 * warp_sum(f1);
-  if (d2) f2 = 2.0 * warp_sum(f2);
-  f += c[0].x;
+  double F = 2.0 * warp_sum((f[0] + f[1]) + (f[2] + f[3]));
+  double F1 = 2.0 * warp_sum((g[0] + g[1]) + (g[2] + g[3]));
+  double F2 = d2 ? 2.0 * warp_sum((h[0] + h[1]) + (h[2] + h[3])) : 0.0;
+  F += c[0].x;
   if ((n & 1) == 0) {
-    double m = 0.5 * n;
-    double nyq = c[n / 2].x;
-    double s, co;
-    sincos(m * alpha, &s, &co);
-    f += nyq * co;
-    f1 -= m * nyq * s;
-    if (d2) f2 -= m * m * nyq * co;
+    const double m = 0.5 * n;
+    const double nyq = c[n / 2].x;
+    F += nyq * st.q.x;
+    F1 -= m * nyq * st.q.y;
+    if (d2) F2 -= m * m * nyq * st.q.x;
   }
-  return TrigSums{f, f1, f2};
+  return TrigSums{F, F1, F2};
+}
+
+__device__ __forceinline__ TrigSums trig_warp(const double2* c, int n, double alpha, int lane, bool d2) {
+  return trig_sums(c, n, trig_start(n, alpha, lane), lane, d2);
+}
+
+// fine-grid twiddles e^{2 pi i m / M}
+__global__ void k_twiddles_M(int M, double2* tw) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  double s, c;
+  sincospi(2.0 * (double)m / (double)M, &s, &c);
+  tw[m] = make_double2(c, s);
 }
 
 // twiddles e^{2 pi i m / n} in float64 and float32
@@ -85,15 +140,15 @@ __global__ void k_dft_real(const double* f, int stride, int nf, int n, const dou
 }
 
 // fine samples X(alpha_s), alpha_s = 2 pi s / M; flags samples closer than 3h to the box
-__global__ void k_fine_samples(const double2* coef, int n, int M, double* fine, double xlo, double xhi,
-                               double ylo, double yhi, int* flags) {
+__global__ void k_fine_samples(const double2* coef, int n, int M, const double2* twM, double* fine, double xlo,
+                               double xhi, double ylo, double yhi, int* flags) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= M) return;
   int nk = n / 2 + 1;
-  double a = (TWO_PI * (double)warp) / (double)M;
-  TrigSums x = trig_warp(coef, n, a, lane, false);
-  TrigSums y = trig_warp(coef + nk, n, a, lane, false);
+  const TrigStart st = trig_start_table(twM, M, warp, n, lane);
+  TrigSums x = trig_sums(coef, n, st, lane, false);
+  TrigSums y = trig_sums(coef + nk, n, st, lane, false);
   if (lane == 0) {
     fine[2 * warp] = x.f;
     fine[2 * warp + 1] = y.f;
@@ -176,16 +231,31 @@ __global__ void k_newton(const double2* coef, int n, int M, const double* fine, 
   double lv = grid_coord(kind == 0 ? ymin : xmin, h, line);
   double lo = (TWO_PI * (double)seg) / (double)M;
   double hi = lo + TWO_PI / (double)M;
-  bool pos_lo = fine[2 * seg + ax] >= lv;
-  double t = 0.5 * (lo + hi);
+  const int seg1 = seg + 1 == M ? 0 : seg + 1;
+  const double flo = fine[2 * seg + ax], fhi = fine[2 * seg1 + ax];
+  bool pos_lo = flo >= lv;
+  // start from the secant through the bracketing fine samples (the midpoint if degenerate)
+  double t = lo + (lv - flo) / (fhi - flo) * (hi - lo);
+  if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+  double prev = 1.0;
   for (int it = 0; it < NEWTON_MAXIT; ++it) {
     TrigSums v = trig_warp(cc, n, t, lane, false);
     double f = v.f - lv, fp = v.f1;
+    if (f == 0.0) break;  // exactly on the line: t is the root (no step, no bisection)
     bool same = (f >= 0.0) == pos_lo;
     if (same) lo = t; else hi = t;
     double tn = t - f / fp;
+    // a Newton step within the tolerance ends the iteration before the bracket test (a
+    // rounding-level step may land just outside a bracket whose other end is still far)
+    if (isfinite(tn) && fabs(tn - t) <= NEWTON_TOL) {
+      if (tn > lo && tn < hi) t = tn;
+      break;
+    }
     if (!isfinite(tn) || tn <= lo || tn >= hi) tn = 0.5 * (lo + hi);
-    bool done = fabs(tn - t) <= NEWTON_TOL;
+    // converged, or in the rounding-noise regime (a step below 1e-12 that no longer shrinks)
+    const double step = fabs(tn - t);
+    bool done = step <= NEWTON_TOL || (step < 1e-12 && step >= 0.5 * prev);
+    prev = step;
     t = tn;
     if (done) break;
   }
@@ -326,30 +396,26 @@ __global__ void k_irr_emit(int N, double xmin, double ymin, double h, const uint
 // Also stores, per target, the twiddle starts of the per-apply density evaluation: lane l's
 // e^{i k0_l alpha} (k0_l = 1 + l chunk, chunk = ceil(K / 32)), then e^{i alpha} and
 // e^{i n alpha / 2}, in float64 and float32.
-__global__ void k_target_geo(const double2* coef, int n, int ncr, const double* cr_alpha, TargetGeo* tg,
-                             TargetGeoF* tg_f, double2* tstart, float2* tstart_f) {
+__global__ void k_target_geo(const double2* coef, int n, int ncr, const double* cr_alpha, const double2* twn,
+                             TargetGeo* tg, TargetGeoF* tg_f, double2* tstart, float2* tstart_f) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (warp >= ncr + n) return;
   int nk = n / 2 + 1;
   double a = warp < ncr ? cr_alpha[warp] : (TWO_PI * (double)(warp - ncr)) / (double)n;
-  TrigSums x = trig_warp(coef, n, a, lane, true);
-  TrigSums y = trig_warp(coef + nk, n, a, lane, true);
+  // crossings: sincos at alpha; nodes alpha_j = 2 pi j / n: the node twiddle table
+  const TrigStart st = warp < ncr ? trig_start(n, a, lane) : trig_start_table(twn, n, warp - ncr, n, lane);
+  TrigSums x = trig_sums(coef, n, st, lane, true);
+  TrigSums y = trig_sums(coef + nk, n, st, lane, true);
   {
-    const int K = (n - 1) / 2;
-    const int chunk = (K + 31) / 32;
-    double sn, cs;
-    sincos((double)(1 + lane * chunk) * a, &sn, &cs);
     long base = (long)warp * TSTART_STRIDE;
-    tstart[base + lane] = make_double2(cs, sn);
-    tstart_f[base + lane] = make_float2((float)cs, (float)sn);
+    tstart[base + lane] = st.e0;
+    tstart_f[base + lane] = make_float2((float)st.e0.x, (float)st.e0.y);
     if (lane == 0) {
-      sincos(a, &sn, &cs);
-      tstart[base + 32] = make_double2(cs, sn);
-      tstart_f[base + 32] = make_float2((float)cs, (float)sn);
-      sincos(0.5 * (double)n * a, &sn, &cs);
-      tstart[base + 33] = make_double2(cs, sn);
-      tstart_f[base + 33] = make_float2((float)cs, (float)sn);
+      tstart[base + 32] = st.s1;
+      tstart_f[base + 32] = make_float2((float)st.s1.x, (float)st.s1.y);
+      tstart[base + 33] = st.q;
+      tstart_f[base + 33] = make_float2((float)st.q.x, (float)st.q.y);
     }
   }
   if (lane != 0) return;
@@ -558,11 +624,12 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   KFBI_TRY(cudaMemsetAsync(c->probe_mark, 0, NN * sizeof(int), s));
 
   k_twiddles_n<<<cdiv(n, 256), 256, 0, s>>>(n, (double2*)c->twn, (float2*)c->twn_f);
-  launched(c, 5);
+  k_twiddles_M<<<cdiv(M, 256), 256, 0, s>>>(M, (double2*)c->twM);
+  launched(c, 6);
   k_dft_real<<<cdiv((long)2 * nk * 32, 256), 256, 0, s>>>(c->xy, 2, 2, n, (const double2*)c->twn,
                                                           (double2*)c->icoef);
   double mg = BOX_MARGIN * h;
-  k_fine_samples<<<cdiv((long)M * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, M, c->fine,
+  k_fine_samples<<<cdiv((long)M * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, M, (const double2*)c->twM, c->fine,
                                                          c->xmin + mg, c->xmax - mg, c->ymin + mg,
                                                          c->ymax - mg, c->flags);
   k_seg_count<<<cdiv(2 * M, 256), 256, 0, s>>>(c->fine, M, c->xmin, c->ymin, h, N, c->seg_count);
@@ -602,7 +669,8 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   k_irr_emit<<<wblocks, 256, 0, s>>>(N, c->xmin, c->ymin, h, c->side, c->hcount, c->vcount, c->hid, c->vid,
                                      c->cr_xi, c->row_ptr, c->irr);
   k_target_geo<<<cdiv((long)(ncr + n) * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, ncr, c->cr_alpha,
-                                                               c->tgeo, c->tgeo_f, (double2*)c->tstart,
+                                                               (const double2*)c->twn, c->tgeo, c->tgeo_f,
+                                                               (double2*)c->tstart,
                                                                (float2*)c->tstart_f);
   k_stencil<<<cdiv(n, 128), 128, 0, s>>>(n, c->xy, c->xmin, c->ymin, h, N, c->side, c->tgeo + ncr, c->stencil,
                                          c->probe_mark, c->flags);

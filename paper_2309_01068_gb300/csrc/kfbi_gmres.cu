@@ -602,6 +602,7 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
   }
   __syncthreads();
   if (s_done) {
+    pdl_wait();
     gmf_close(ctl, rank, hcond, use_cond, cap, 1);
     return;
   }
@@ -613,6 +614,7 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
   int done = 0;
   if (s_phase == PH_RESID) {
     // r = b - A x, ||r||; restart from r / ||r|| unless converged or out of iterations
+    pdl_wait();
     double ss = 0.0;
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
       double r = b[i0 + i] - w[i0 + i];
@@ -689,12 +691,14 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
       }
     }
   }
-  for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = w[i0 + i];
   for (int i = threadIdx.x; i < j; i += GMF_THREADS) {
     scs[i] = ctl->cs[i];
     ssn[i] = ctl->sn[i];
   }
   if (threadIdx.x == 0) s_gj = ctl->g[j];
+  // everything above was complete before the apply started; w is the apply's output
+  pdl_wait();
+  for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = w[i0 + i];
   __syncthreads();
   // two passes of classical Gram-Schmidt; the second also reduces ||w'||^2 (entry K)
   cta_dots(sV, Rp, sw, len, K, false, part[0]);
@@ -866,8 +870,10 @@ static cudaLaunchConfig_t gmf_launch_config(kfbi_ctx* c, const kfbi_ctx::GmfConf
   attr[0].val.clusterDim.x = g.cs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = c->use_pdl ? 2 : 1;
   return cfg;
 }
 
@@ -890,7 +896,7 @@ static kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m) {
       const size_t smem = base + (hs ? sizeof(double) * (size_t)(m + 1) * (m + 1) : 0);
       if (smem > lim) continue;
       kfbi_ctx::GmfConfig g{n, m, cs, R, hs, smem};
-      cudaLaunchAttribute attr[1];
+      cudaLaunchAttribute attr[2];
       cudaLaunchConfig_t cfg = gmf_launch_config(c, g, attr);
       int nc = 0;
       if (cudaOccupancyMaxActiveClusters(&nc, k_gm_cluster, &cfg) != cudaSuccess) {
@@ -916,7 +922,7 @@ static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, c
   KFBI_CHECK(apply_enqueue(c, layer, fp32, c->gin, c->gw, nullptr, nullptr, kind, eps_v, done, c->gin_f));
   const int ldv = c->max_nodes;
   if (gf.cs > 0) {
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     cudaLaunchConfig_t cfg = gmf_launch_config(c, gf, attr);
     launched(c, 1);
     KFBI_TRY(cudaLaunchKernelEx(&cfg, k_gm_cluster, c->gctl, c->gV, ldv, (const double*)c->gw, b, x, c->gin,
@@ -1001,10 +1007,11 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   if (c->use_graphs && !c->timing) {
     kfbi_ctx::SolveGraph& G = c->sgraph[kind][fp32 ? 1 : 0];
     kfbi_status st = KFBI_OK;
-    if (G.exec == nullptr || G.version != c->iface_version || G.m != m || G.cs != gf.cs) {
+    if (G.exec == nullptr || G.version != c->iface_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl) {
       st = build_graph(c, G, kind, fp32, eps_v, b, x, cap, gf);
       G.m = m;
       G.cs = gf.cs;
+      G.pdl = c->use_pdl;
     }
     if (st == KFBI_OK && cudaGraphLaunch(G.exec, s) == cudaSuccess) {
       graphed = true;
@@ -1038,8 +1045,11 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   return KFBI_OK;
 }
 
+// dnormal (optional, mixed precision only): the refinement's float64 applies also write the
+// normal derivative of the layer potential of the iterate; the last one belongs to the
+// returned density. Set to nullptr on return when it was not produced.
 kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const double* rhs, double tol, int max_iter,
-                           int restart, double* x, kfbi_solve_info* info) {
+                           int restart, double* x, kfbi_solve_info* info, double* dnormal) {
   cudaStream_t s = c->stream;
   const int n = c->n;
   const size_t bytes = sizeof(double) * n;
@@ -1071,7 +1081,7 @@ kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const dou
     const int max_sweeps = 12;
     int layer = kind == KFBI_BIE_STEFAN_SL ? KFBI_SINGLE : KFBI_DOUBLE;
     while (true) {
-      KFBI_CHECK(apply_enqueue(c, layer, false, x, y, nullptr, nullptr, kind, ev, nullptr));
+      KFBI_CHECK(apply_enqueue(c, layer, false, x, y, dnormal, nullptr, kind, ev, nullptr));
       k_resid<<<1, 1024, 0, s>>>(rhs, y, c->gb, n, c->dint + 1);
       launched(c, 1);
       KFBI_TRY(cudaMemcpyAsync(hres, c->dint + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));

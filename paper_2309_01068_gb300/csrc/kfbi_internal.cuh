@@ -155,6 +155,7 @@ struct kfbi_ctx {
   int n_prow = 0;
   double* icoef = nullptr;      // [2][max_nodes/2+1] complex Fourier coefficients of x, y
   double* fine = nullptr;       // [SUBSAMPLES*max_nodes][2]
+  double* twM = nullptr;        // [SUBSAMPLES*max_nodes] complex e^{2 pi i m / M}, M = SUBSAMPLES n
   int* seg_count = nullptr;     // [2*M + 1]
   int* seg_off = nullptr;       // [2*M + 1]
   int* cr_kind = nullptr;       // [cap_cross]
@@ -218,6 +219,7 @@ struct kfbi_ctx {
     long version = -1;
     int m = 0;
     int cs = 0;             // cluster size of the Gram-Schmidt kernel (0: multi-kernel form)
+    bool pdl = false;       // built with programmatic dependent launch
     int body_launches = 0;  // kernels per replayed body
   } sgraph[3][2];
   // cluster form of the GMRES body (k_gm_cluster) for the last (n, m); cs = 0: multi-kernel
@@ -227,6 +229,7 @@ struct kfbi_ctx {
     size_t smem = 0;
   } gmf;
   bool gm_cluster = true;       // allow the cluster form
+  bool use_pdl = true;          // programmatic dependent launch between the kernels of a body
   int gmf_last_cs = 0;          // cluster size used by the last GMRES run
   size_t gmf_smem_max = 0;      // 0 = not queried yet, 1 = unavailable
   long iface_version = 0;
@@ -286,6 +289,32 @@ inline int ilog2(int v) {
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
 inline void launched(kfbi_ctx* c, int k) { c->launches += k; }
+
+// Programmatic dependent launch: a kernel launched with launch_k(pdl = true) may start while
+// the previous kernel in its stream is still running. It first reads only data that was
+// complete before that kernel started (tables, geometry, the control block), then waits with
+// pdl_wait() for the previous kernel to finish and its writes to be visible, and lets its own
+// successor start with pdl_trigger(). Every kernel calls pdl_wait() before it reads or writes
+// anything its predecessor touches and before it returns, so a finished kernel implies that
+// all kernels before it have finished. Without the attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                            Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // Work runs on c->stream. When the caller's stream is a default stream (which cannot be
 // captured into a graph), c->stream is the context's own stream, ordered after the caller's

@@ -13,7 +13,8 @@
 namespace kfbi {
 kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy);
 kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const double* rhs, double tol, int max_iter,
-                           int restart, double* x, kfbi_solve_info* info);
+                           int restart, double* x, kfbi_solve_info* info,
+                           double* dnormal = nullptr);
 }  // namespace kfbi
 
 // scalar slots of the device state
@@ -346,10 +347,14 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
   if (P.kind == KFBI_STEP_HELE_SHAW) {
     launched(c, 2);
     k_st_hs_rhs<<<tb, 256, 0, s>>>(st->xy, st->th_a, n, st->scal, P.sigma, P.J, st->rhs);
+    // mixed precision: the refinement's last float64 apply, at the returned density, also
+    // gives the normal derivative of its double layer; float64: one more apply
+    const bool dn_from_solve = c->precision == KFBI_MIXED;
     sst = solve_bie_impl(c, KFBI_BIE_HS_EXTERIOR_MDL, nullptr, st->rhs, P.tol, P.max_iter, P.restart, st->density,
-                         &si);
+                         &si, dn_from_solve ? st->dn : nullptr);
     if (sst != KFBI_OK && sst != KFBI_ERR_NOT_CONVERGED) return sst;
-    KFBI_CHECK(apply_enqueue(c, KFBI_DOUBLE, false, st->density, st->V, st->dn, nullptr, -1, nullptr, nullptr));
+    if (!dn_from_solve)
+      KFBI_CHECK(apply_enqueue(c, KFBI_DOUBLE, false, st->density, st->V, st->dn, nullptr, -1, nullptr, nullptr));
     k_st_hs_velocity<<<tb, 256, 0, s>>>(st->xy, st->eta, st->dn, n, P.J, st->U);
   } else {
     const int N = c->N;
