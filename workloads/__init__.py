@@ -245,3 +245,57 @@ def random_grid(seed, N, smooth=True):
     rng = np.random.default_rng(seed)
     g = rng.standard_normal((N, N))
     return np.ascontiguousarray(g)
+
+
+# ----------------------------------------------------------------------------- learned warm start
+def random_harmonic(seed):
+    """A random harmonic function u(x, y) for the boundary data of interior Laplace problems:
+    a sum of e^{k x'} cos(k y' + b) terms in randomly rotated coordinates (each harmonic) plus a
+    random harmonic quadratic a (x^2 - y^2) + c x y + d."""
+    rng = np.random.default_rng(seed)
+    terms = []
+    for _ in range(int(rng.integers(1, 4))):
+        th = rng.uniform(0.0, 2.0 * math.pi)
+        k = rng.uniform(0.3, 2.5)
+        terms.append((math.cos(th), math.sin(th), k, rng.uniform(0.0, 2.0 * math.pi), rng.normal()))
+    a, c, d = rng.normal(), rng.normal(), rng.normal()
+
+    def u(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64)
+        out = a * (x * x - y * y) + c * x * y + d
+        for ct, st, k, b, w in terms:
+            xr, yr = ct * x + st * y, -st * x + ct * y
+            out = out + w * np.exp(k * xr) * np.cos(k * yr + b)
+        return out
+
+    return u
+
+
+def warmstart_problem(seed, N=128, n=None):
+    """An interior Dirichlet Laplace problem for warm-start training and tests: a random star
+    (config-4 shape family) in [-1, 1]^2 with random harmonic boundary data; n nodes
+    (default: uniform in [64, 512])."""
+    rng = np.random.default_rng(seed)
+    shape = random_star(rng)
+    if n is None:
+        n = int(rng.integers(64, 513))
+    nodes = equal_arclength(shape, n)
+    u = random_harmonic(seed + 7919)
+    rhs = u(nodes["xy"][:, 0], nodes["xy"][:, 1])
+    return Problem(f"warmstart_{seed}", N, (-1.0, 1.0, -1.0, 1.0), 0.0, BOX_DIRICHLET0, nodes["xy"], nodes["theta"],
+                   nodes["L"], rhs)
+
+
+def mlp_init(seed, features=39, hidden=256):
+    """Initial weights of the warm-start network (He-normal scaling by fan-in, zero biases),
+    float32; drawn on the host so both the device path and the oracle start from them."""
+    rng = np.random.default_rng(seed)
+    return dict(
+        W1=rng.normal(0.0, math.sqrt(2.0 / features), (hidden, features)).astype(np.float32),
+        b1=np.zeros(hidden, dtype=np.float32),
+        W2=rng.normal(0.0, math.sqrt(2.0 / hidden), (hidden, hidden)).astype(np.float32),
+        b2=np.zeros(hidden, dtype=np.float32),
+        w3=rng.normal(0.0, math.sqrt(1.0 / hidden), hidden).astype(np.float32),
+        b3=np.float32(0.0),
+    )
