@@ -306,6 +306,57 @@ enum { KFBI_OPT_CUDA_GRAPHS = 1, KFBI_OPT_CLUSTER_GMRES = 2, KFBI_OPT_LAST_CLUST
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);
 
+/* ------------------------------------------------------------------------------------
+ * Learned warm start of GMRES. The paper has no learned component: it solves each
+ * boundary integral equation by GMRES from a given initial density (Sec. 4). Here a small
+ * network predicts that initial density from per-node interface features; GMRES still
+ * iterates to the caller's tolerance, so the solution does not depend on the prediction.
+ *
+ * Features of node j (KFBI_MLP_FEATURES = 47, float32), l = L / (2 pi), L the curve length:
+ *   0..31  Re, Im of khat_k e^{i k alpha_j} l, k = 0..15, khat_k = (1/n) sum_m kappa_m e^{-i k alpha_m}
+ *   32     kappa_j l                33, 34  outward unit normal
+ *   35     s_j / L (trapezoidal arclength from node 0)
+ *   36     g_j / rms(g)             37, 38  (x_j - mean x) / l, (y_j - mean y) / l
+ *   39..46 Re, Im of ghat_k e^{i k alpha_j} / rms(g), k = 0..3 (low modes of the data g)
+ * Network: 47 -> H -> H -> 1, ReLU, weights rounded to bfloat16 (nearest even), float32
+ * biases, activations and accumulation; its output y_j predicts phi_j / rms(g).
+ * Parameters (float32, host arrays of kfbi_mlp_param_count entries), in this order:
+ *   W1 [H][47], b1 [H], W2 [H][H], b2 [H], w3 [H], b3.
+ * Training: mean squared error over the rows, gradients through the rounded weights applied
+ * to the float32 weights, Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected).
+ * ------------------------------------------------------------------------------------ */
+enum { KFBI_MLP_FEATURES = 47, KFBI_MLP_MODES = 16, KFBI_MLP_DATA_MODES = 4 };
+typedef struct kfbi_mlp kfbi_mlp;
+
+/* hidden: multiple of 32 in [32, 256]; max_rows: largest batch (and node count) served.
+ * Parameters start at zero: load them with kfbi_mlp_set_params. Errors: ARG, CUDA. */
+kfbi_status kfbi_mlp_create(int hidden, int max_rows, kfbi_mlp** out);
+void kfbi_mlp_destroy(kfbi_mlp* mlp);
+/* Stream of the kfbi_mlp_* calls (default: the legacy default stream). */
+kfbi_status kfbi_mlp_set_stream(kfbi_mlp* mlp, void* stream);
+kfbi_status kfbi_mlp_param_count(kfbi_mlp* mlp, int* count);
+/* Host float32 parameters in and out; set_params also resets Adam's moments and step
+ * count. Both synchronise the stream. */
+kfbi_status kfbi_mlp_set_params(kfbi_mlp* mlp, const float* params);
+kfbi_status kfbi_mlp_get_params(kfbi_mlp* mlp, float* params);
+/* y[r] for rows r < rows of feat (device [rows][47] float32); y device [rows]. Async. */
+kfbi_status kfbi_mlp_forward(kfbi_mlp* mlp, const float* feat, int rows, float* y);
+/* Gradient of the mean squared error of rows idx[0..rows) (device int32; NULL: rows
+ * 0..rows-1) of feat against target (device float32): grad device [param_count] (NULL keeps
+ * it internal); loss: host float (NULL: not read, no synchronisation). */
+kfbi_status kfbi_mlp_gradients(kfbi_mlp* mlp, const float* feat, const float* target, const int* idx, int rows,
+                               float* grad, float* loss);
+/* One Adam step on the rows idx[0..rows) with learning rate lr (> 0); loss as above. */
+kfbi_status kfbi_mlp_train_step(kfbi_mlp* mlp, const float* feat, const float* target, const int* idx, int rows,
+                                float lr, float* loss);
+/* Features of the context's interface nodes for the right-hand side rhs (device [n]
+ * float64): feat device [n][47] float32, scale device [1] float64 = rms(rhs). n <= 8192
+ * (else CAPACITY). Errors: ARG, STATE (no interface), CAPACITY, CUDA. Async. */
+kfbi_status kfbi_warmstart_features(kfbi_ctx* ctx, const double* rhs, float* feat, double* scale);
+/* density[j] = rms(rhs) y_j: the network's initial density for kfbi_solve_bie (device
+ * [n] float64), on the context's stream. n <= max_rows of the network. Async. */
+kfbi_status kfbi_warmstart_predict(kfbi_ctx* ctx, kfbi_mlp* mlp, const double* rhs, double* density);
+
 /* Number of kernels this context has launched since creation (host output). */
 kfbi_status kfbi_launch_count(kfbi_ctx* ctx, long long* count);
 

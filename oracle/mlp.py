@@ -9,7 +9,7 @@ with the build: a small multilayer perceptron maps per-node interface features t
 density, the prediction only seeds GMRES, and GMRES still iterates to the same tolerance,
 so the solution does not depend on it.
 
-Features of node j (FEATURES = 39), with l = L / (2 pi) the mean radius of the curve:
+Features of node j (FEATURES = 47), with l = L / (2 pi) the mean radius of the curve:
   0..31  Re, Im of khat_k e^{i k alpha_j} l, k = 0..15, khat_k = (1/n) sum_m kappa_m e^{-i k alpha_m}
          (the curvature's Fourier modes rotated to the node)
   32     kappa_j l
@@ -17,9 +17,12 @@ Features of node j (FEATURES = 39), with l = L / (2 pi) the mean radius of the c
   35     s_j / L, arclength from node 0 by the trapezoidal rule
   36     g_j / rms(g)   (the node's right-hand side; rms over the nodes)
   37, 38 (x_j - mean x) / l, (y_j - mean y) / l
+  39..46 Re, Im of ghat_k e^{i k alpha_j} / rms(g), k = 0..3, ghat_k = (1/n) sum_m g_m e^{-i k alpha_m}
+         (the data's low modes rotated to the node: the density depends on the data
+         globally, e.g. on its mean, not only on g_j)
 Target: phi_j / rms(g). The equation is linear, so a prediction y_j gives phi_j = rms(g) y_j.
 
-Network: 39 -> H -> H -> 1 with ReLU, weights rounded to bfloat16 (round to nearest even)
+Network: 47 -> H -> H -> 1 with ReLU, weights rounded to bfloat16 (round to nearest even)
 where they are used, biases, activations and accumulation in full precision here (float32
 on the device). Loss: mean squared error. Gradients are taken with the rounded weights and
 applied to the unrounded (master) weights. Adam: Kingma & Ba (2015), bias-corrected.
@@ -30,8 +33,9 @@ import math
 
 import numpy as np
 
-FEATURES = 39
+FEATURES = 47
 MODES = 16
+DATA_MODES = 4
 
 
 # ----------------------------------------------------------------------------- features
@@ -65,6 +69,11 @@ def features(iface, rhs):
     F[:, 36] = rhs / rms if rms > 0 else 0.0
     F[:, 37] = (g["x"] - np.mean(g["x"])) / ell
     F[:, 38] = (g["y"] - np.mean(g["y"])) / ell
+    for k in range(DATA_MODES):
+        ghat = np.sum(rhs * np.exp(-1j * k * alpha)) / n
+        rot = ghat * np.exp(1j * k * alpha) / rms if rms > 0 else 0.0 * alpha
+        F[:, 39 + 2 * k] = np.real(rot)
+        F[:, 40 + 2 * k] = np.imag(rot)
     return F, rms
 
 

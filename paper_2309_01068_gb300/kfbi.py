@@ -19,6 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "kfbi.h")
 # codes mirrored from include/kfbi.h
 OK, ERR_ARG, ERR_CUDA, ERR_OUTSIDE_BOX, ERR_UNDERRESOLVED, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
 OPT_CUDA_GRAPHS, OPT_CLUSTER_GMRES, OPT_LAST_CLUSTER, OPT_PDL = 1, 2, 3, 4
+MLP_FEATURES, MLP_MODES = 47, 16
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2
 FP64, MIXED = 0, 1
@@ -78,6 +79,17 @@ _SIGNATURES = {
     "kfbi_timing_read": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "kfbi_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "kfbi_set_option": (_I, [_P, _I, _I]),
+    "kfbi_mlp_create": (_I, [_I, _I, ctypes.POINTER(_P)]),
+    "kfbi_mlp_destroy": (None, [_P]),
+    "kfbi_mlp_set_stream": (_I, [_P, _P]),
+    "kfbi_mlp_param_count": (_I, [_P, ctypes.POINTER(_I)]),
+    "kfbi_mlp_set_params": (_I, [_P, _P]),
+    "kfbi_mlp_get_params": (_I, [_P, _P]),
+    "kfbi_mlp_forward": (_I, [_P, _P, _I, _P]),
+    "kfbi_mlp_gradients": (_I, [_P, _P, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_float)]),
+    "kfbi_mlp_train_step": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
+    "kfbi_warmstart_features": (_I, [_P, _P, _P, _P]),
+    "kfbi_warmstart_predict": (_I, [_P, _P, _P, _P]),
     "kfbi_get_option": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "kfbi_grid_solve_noalloc": (_I, [_I, _D, _D, _I, _P, _P, _P]),
 }
@@ -270,10 +282,122 @@ class Context:
         _check(self.lib.kfbi_get_option(self.handle, int(option), ctypes.byref(v)), "kfbi_get_option")
         return v.value
 
+    def warmstart_features(self, rhs):
+        """kfbi_warmstart_features: (features [n][47] float32, rms(rhs) [1] float64)."""
+        self._sync_stream()
+        n = self.n
+        feat = torch.empty((max(n, 1), MLP_FEATURES), dtype=torch.float32, device=rhs.device)[:n]
+        scale = torch.empty(1, dtype=torch.float64, device=rhs.device)
+        _check(self.lib.kfbi_warmstart_features(self.handle, _f64(rhs, (n,)), _ptr(feat), _ptr(scale)),
+               "kfbi_warmstart_features")
+        return feat, scale
+
+    def warmstart_predict(self, mlp, rhs, out=None):
+        """kfbi_warmstart_predict: the network's initial density for rhs."""
+        self._sync_stream()
+        n = self.n
+        d = out if out is not None else torch.empty(n, dtype=torch.float64, device=rhs.device)
+        _check(self.lib.kfbi_warmstart_predict(self.handle, mlp.handle, _f64(rhs, (n,)), _f64(d, (n,))),
+               "kfbi_warmstart_predict")
+        return d
+
     def launch_count(self):
         v = ctypes.c_longlong()
         _check(self.lib.kfbi_launch_count(self.handle, ctypes.byref(v)), "kfbi_launch_count")
         return v.value
+
+
+class Mlp:
+    """kfbi_mlp_*: the warm-start network (47 -> hidden -> hidden -> 1, bfloat16 weights)."""
+
+    NAMES = ("W1", "b1", "W2", "b2", "w3", "b3")
+
+    def __init__(self, hidden=256, max_rows=4096):
+        self.lib = load()
+        self.hidden = int(hidden)
+        self.max_rows = int(max_rows)
+        h = ctypes.c_void_p()
+        _check(self.lib.kfbi_mlp_create(self.hidden, self.max_rows, ctypes.byref(h)), "kfbi_mlp_create")
+        self.handle = h
+        c = ctypes.c_int()
+        _check(self.lib.kfbi_mlp_param_count(self.handle, ctypes.byref(c)), "kfbi_mlp_param_count")
+        self.count = c.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.kfbi_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def _sync_stream(self):
+        _check(self.lib.kfbi_mlp_set_stream(self.handle, _stream()), "kfbi_mlp_set_stream")
+
+    def _shapes(self):
+        H, F = self.hidden, MLP_FEATURES
+        return dict(W1=(H, F), b1=(H,), W2=(H, H), b2=(H,), w3=(H,), b3=())
+
+    def flatten(self, params):
+        """dict of arrays (W1, b1, W2, b2, w3, b3) -> flat float32 host array in the C layout."""
+        import numpy as np
+
+        parts = [np.asarray(params[k], dtype=np.float32).reshape(-1) for k in self.NAMES]
+        flat = np.ascontiguousarray(np.concatenate(parts))
+        if flat.size != self.count:
+            raise ValueError(f"expected {self.count} parameters, got {flat.size}")
+        return flat
+
+    def unflatten(self, flat):
+        import numpy as np
+
+        out, o = {}, 0
+        for k, shp in self._shapes().items():
+            sz = int(np.prod(shp)) if shp else 1
+            out[k] = flat[o:o + sz].reshape(shp) if shp else float(flat[o])
+            o += sz
+        return out
+
+    def set_params(self, params):
+        self._sync_stream()
+        flat = self.flatten(params)
+        _check(self.lib.kfbi_mlp_set_params(self.handle, flat.ctypes.data_as(ctypes.c_void_p)), "kfbi_mlp_set_params")
+
+    def get_params(self):
+        import numpy as np
+
+        self._sync_stream()
+        flat = np.empty(self.count, dtype=np.float32)
+        _check(self.lib.kfbi_mlp_get_params(self.handle, flat.ctypes.data_as(ctypes.c_void_p)), "kfbi_mlp_get_params")
+        return self.unflatten(flat)
+
+    def forward(self, feat, out=None):
+        self._sync_stream()
+        rows = feat.shape[0]
+        y = out if out is not None else torch.empty(rows, dtype=torch.float32, device=feat.device)
+        _check(self.lib.kfbi_mlp_forward(self.handle, _ptr(feat), rows, _ptr(y)), "kfbi_mlp_forward")
+        return y
+
+    def gradients(self, feat, target, idx=None):
+        """(loss, flat gradient tensor) of the mean squared error on rows idx (all rows if None)."""
+        self._sync_stream()
+        rows = feat.shape[0] if idx is None else idx.shape[0]
+        g = torch.empty(self.count, dtype=torch.float32, device=feat.device)
+        loss = ctypes.c_float()
+        _check(self.lib.kfbi_mlp_gradients(self.handle, _ptr(feat), _ptr(target), _ptr(idx), rows, _ptr(g),
+                                           ctypes.byref(loss)), "kfbi_mlp_gradients")
+        return loss.value, g
+
+    def train_step(self, feat, target, idx=None, lr=1e-3, want_loss=True):
+        self._sync_stream()
+        rows = feat.shape[0] if idx is None else idx.shape[0]
+        loss = ctypes.c_float()
+        _check(self.lib.kfbi_mlp_train_step(self.handle, _ptr(feat), _ptr(target), _ptr(idx), rows, float(lr),
+                                            ctypes.byref(loss) if want_loss else None), "kfbi_mlp_train_step")
+        return loss.value if want_loss else None
 
 
 def grid_solve_noalloc(rhs, h, kappa=0.0, boxbc=BOX_DIRICHLET0, out=None):

@@ -1,0 +1,173 @@
+"""Learned warm start on the GPU vs the oracle (oracle/mlp.py), through the C ABI.
+
+Tolerances: features, forward values and gradients are float32 on the device against the
+oracle's float64 with the same bfloat16-rounded weights: 1e-5 relative for features and
+outputs (float32 rounding of sums of a few hundred terms), 1e-4 in norm for gradients (the
+rows' contributions are summed in a different order).
+
+The gain test trains the network on densities the GPU solver produces and measures, on
+problems it has not seen, the initial residual and the GMRES iterations from its prediction
+against the zero start. It asserts what the warm start guarantees (the network learns, its
+start is closer to the solution, the converged density is the zero start's); the iteration
+counts are reported, not asserted: on these second-kind equations GMRES needs about ten
+iterations from any start, and a start with a residual near 1e-1 does not shorten that.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import kfbi as OK
+from oracle import mlp as OM
+
+pytestmark = pytest.mark.gpu
+
+K = pytest.importorskip("paper_2309_01068_gb300.kfbi")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_01068_gb300 import build
+
+    build.build()
+    K.load()
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def relnorm(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("seed,n", [(3, 64), (4, 257), (5, 512)])
+def test_features_match_oracle(seed, n):
+    p = W.warmstart_problem(seed, N=128, n=n)
+    ctx = K.Context(p.N, p.box, 0.0, K.BOX_DIRICHLET0, K.FP64, max_nodes=p.n)
+    ctx.set_interface(dev(p.xy))
+    feat, scale = ctx.warmstart_features(dev(p.rhs))
+    F, rms = OM.features(OK.Interface(p.xy), p.rhs)
+    got = feat.cpu().numpy().astype(np.float64)
+    assert abs(scale.item() - rms) <= 1e-6 * rms
+    err = np.abs(got - F) / np.maximum(1.0, np.abs(F))
+    assert err.max() < 2e-5, (np.unravel_index(err.argmax(), err.shape), err.max())
+
+
+def _params(seed, hidden=256):
+    return W.mlp_init(seed, features=OM.FEATURES, hidden=hidden)
+
+
+@pytest.mark.parametrize("hidden,rows", [(256, 200), (64, 37)])
+def test_forward_matches_oracle(hidden, rows):
+    rng = np.random.default_rng(hidden + rows)
+    P = _params(11, hidden)
+    P["b1"] = (rng.normal(size=hidden) * 0.1).astype(np.float32)
+    P["b2"] = (rng.normal(size=hidden) * 0.1).astype(np.float32)
+    P["b3"] = np.float32(0.2)
+    X = rng.normal(size=(rows, OM.FEATURES)).astype(np.float32)
+    m = K.Mlp(hidden=hidden, max_rows=512)
+    m.set_params(P)
+    y = m.forward(dev(X, torch.float32)).cpu().numpy()
+    yo, _ = OM.forward({k: np.asarray(v, dtype=np.float64) for k, v in P.items()}, X.astype(np.float64))
+    assert np.max(np.abs(y - yo)) <= 1e-5 * max(1.0, np.max(np.abs(yo)))
+    # parameters come back exactly as set
+    Q = m.get_params()
+    for k in K.Mlp.NAMES:
+        assert np.array_equal(np.asarray(Q[k], dtype=np.float32), np.asarray(P[k], dtype=np.float32))
+
+
+def test_gradients_match_oracle():
+    rng = np.random.default_rng(5)
+    hidden, total, rows = 256, 300, 211
+    P = _params(12, hidden)
+    P["b1"] = (rng.normal(size=hidden) * 0.1).astype(np.float32)
+    P["b2"] = (rng.normal(size=hidden) * 0.1).astype(np.float32)
+    X = rng.normal(size=(total, OM.FEATURES)).astype(np.float32)
+    t = rng.normal(size=total).astype(np.float32)
+    idx = rng.permutation(total)[:rows].astype(np.int32)
+    m = K.Mlp(hidden=hidden, max_rows=512)
+    m.set_params(P)
+    loss, g = m.gradients(dev(X, torch.float32), dev(t, torch.float32), dev(idx, torch.int32))
+    G = m.unflatten(g.cpu().numpy())
+    Pd = {k: np.asarray(v, dtype=np.float64) for k, v in P.items()}
+    lo, Go = OM.loss_and_grads(Pd, X[idx].astype(np.float64), t[idx].astype(np.float64))
+    assert abs(loss - lo) <= 1e-5 * lo
+    for k in OM.PARAM_NAMES:
+        assert relnorm(np.atleast_1d(G[k]), np.atleast_1d(Go[k])) < 1e-4, k
+
+
+def test_adam_step_matches_oracle():
+    rng = np.random.default_rng(8)
+    hidden, rows = 64, 128
+    P = _params(13, hidden)
+    X = rng.normal(size=(rows, OM.FEATURES)).astype(np.float32)
+    t = rng.normal(size=rows).astype(np.float32)
+    m = K.Mlp(hidden=hidden, max_rows=rows)
+    m.set_params(P)
+    Pd = {k: np.asarray(v, dtype=np.float64) for k, v in P.items()}
+    M, V = OM.zeros_like(Pd), OM.zeros_like(Pd)
+    lr = 1e-3
+    for step in range(1, 4):
+        m.train_step(dev(X, torch.float32), dev(t, torch.float32), lr=lr)
+        _, Go = OM.loss_and_grads(Pd, X.astype(np.float64), t.astype(np.float64))
+        OM.adam_step(Pd, Go, M, V, step, lr)
+    Q = m.get_params()
+    for k in OM.PARAM_NAMES:
+        d = np.abs(np.asarray(Q[k], dtype=np.float64) - np.asarray(Pd[k]))
+        # every update is at most about lr per step; the two agree far below that
+        assert np.max(d) < 0.05 * lr, (k, np.max(d))
+
+
+def _dataset(ctx, seeds, n=None):
+    """Densities the GPU solver produces (FP64, tol 1e-12) with their features."""
+    feats, targets, probs = [], [], []
+    for s in seeds:
+        p = W.warmstart_problem(s, N=256, n=n)
+        ctx.set_interface(dev(p.xy))
+        rhs = dev(p.rhs)
+        phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, rhs, tol=1e-12, max_iter=400, restart=100)
+        assert info["status"] == 0
+        f, scale = ctx.warmstart_features(rhs)
+        feats.append(f.clone())
+        targets.append((phi / scale).to(torch.float32))
+        probs.append(p)
+    return torch.cat(feats), torch.cat(targets), probs
+
+
+def test_trained_warm_start_saves_gmres_iterations():
+    ctx = K.Context(256, (-1.0, 1.0, -1.0, 1.0), 0.0, K.BOX_DIRICHLET0, K.FP64, max_nodes=512)
+    X, T, _ = _dataset(ctx, range(1000, 1080))
+    rows = X.shape[0]
+    m = K.Mlp(hidden=256, max_rows=max(rows, 512))
+    m.set_params(_params(21))
+    g = torch.Generator(device="cpu").manual_seed(0)
+    first = m.train_step(X, T, lr=1e-3)
+    for it in range(2500):
+        idx = torch.randint(0, rows, (512,), generator=g, dtype=torch.int32).cuda()
+        m.train_step(X, T, idx=idx, lr=1e-3 if it < 1500 else 3e-4, want_loss=False)
+    last, _ = m.gradients(X, T)
+    assert last < 0.1 * first
+    # held-out problems: initial residual and GMRES iterations, zero start vs network start
+    its0, its1, r1 = [], [], []
+    for s in range(5000, 5012):
+        p = W.warmstart_problem(s, N=256)
+        ctx.set_interface(dev(p.xy))
+        rhs = dev(p.rhs)
+        guess = ctx.warmstart_predict(m, rhs)
+        res = rhs - ctx.bie_apply(K.BIE_INTERIOR_DL, guess)
+        r1.append(float(torch.linalg.norm(res) / torch.linalg.norm(rhs)))
+        phi0, i0 = ctx.solve_bie(K.BIE_INTERIOR_DL, rhs, tol=1e-10, max_iter=400, restart=100)
+        phi1, i1 = ctx.solve_bie(K.BIE_INTERIOR_DL, rhs, density=guess, tol=1e-10, max_iter=400, restart=100)
+        assert i0["status"] == 0 and i1["status"] == 0
+        assert relnorm(phi1.cpu().numpy(), phi0.cpu().numpy()) < 1e-8
+        its0.append(i0["iterations"])
+        its1.append(i1["iterations"])
+    assert np.median(r1) < 0.3, r1
+    print(f"warm start: median initial residual {np.median(r1):.3e} (zero start 1), GMRES iterations "
+          f"zero start {np.mean(its0):.2f}, network start {np.mean(its1):.2f}")

@@ -118,6 +118,11 @@ def test_features_of_a_circle():
     assert np.allclose(F[:, 36], rhs / math.sqrt(0.5), atol=1e-13)
     assert np.allclose(F[:, 37], np.cos(a), atol=1e-12)
     assert np.allclose(F[:, 38], np.sin(a), atol=1e-12)
+    # data cos(alpha): only the k = 1 mode, ghat_1 = 1/2, rotated: (1/2) e^{i alpha} / rms
+    assert np.allclose(F[:, 39:41], 0.0, atol=1e-13)
+    assert np.allclose(F[:, 41], 0.5 * np.cos(a) / math.sqrt(0.5), atol=1e-13)
+    assert np.allclose(F[:, 42], 0.5 * np.sin(a) / math.sqrt(0.5), atol=1e-13)
+    assert np.allclose(F[:, 43:47], 0.0, atol=1e-13)
 
 
 def test_curvature_of_an_ellipse():
@@ -150,6 +155,6 @@ def test_warmstart_problem_data_is_harmonic():
 
 @pytest.mark.parametrize("seed", [1, 2])
 def test_mlp_init_shapes_and_scale(seed):
-    P = W.mlp_init(seed)
+    P = W.mlp_init(seed, features=OM.FEATURES)
     assert P["W1"].shape == (256, OM.FEATURES) and P["W2"].shape == (256, 256) and P["w3"].shape == (256,)
     assert abs(np.std(P["W2"]) - math.sqrt(2.0 / 256)) < 0.01

@@ -272,14 +272,15 @@ def random_harmonic(seed):
     return u
 
 
-def warmstart_problem(seed, N=128, n=None):
+def warmstart_problem(seed, N=256, n=None):
     """An interior Dirichlet Laplace problem for warm-start training and tests: a random star
     (config-4 shape family) in [-1, 1]^2 with random harmonic boundary data; n nodes
-    (default: uniform in [64, 512])."""
+    (default: uniform in [64, 320], so that on the 256^2 grid the node spacing stays above
+    the cell width, where GMRES converges fast)."""
     rng = np.random.default_rng(seed)
     shape = random_star(rng)
     if n is None:
-        n = int(rng.integers(64, 513))
+        n = int(rng.integers(64, 321))
     nodes = equal_arclength(shape, n)
     u = random_harmonic(seed + 7919)
     rhs = u(nodes["xy"][:, 0], nodes["xy"][:, 1])
@@ -287,7 +288,7 @@ def warmstart_problem(seed, N=128, n=None):
                    nodes["L"], rhs)
 
 
-def mlp_init(seed, features=39, hidden=256):
+def mlp_init(seed, features=47, hidden=256):
     """Initial weights of the warm-start network (He-normal scaling by fan-in, zero biases),
     float32; drawn on the host so both the device path and the oracle start from them."""
     rng = np.random.default_rng(seed)
