@@ -295,14 +295,26 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             device can schedule it; 0: the five-kernel form.
  *   KFBI_OPT_LAST_CLUSTER     read only: cluster size used by the last GMRES run (0 = the
  *                             five-kernel form).
- *   KFBI_OPT_PDL              1 (default): consecutive kernels of an apply and of a GMRES
- *                             iteration use programmatic dependent launch (a kernel starts
- *                             while its predecessor finishes and waits on the device before
- *                             it reads the predecessor's output); 0: plain stream order.
- * kfbi_set_option: value 0 or 1. kfbi_get_option writes the value to *value (host).
+ *   KFBI_OPT_CLUSTER_SIZE     0 (default): the cluster form takes 16 CTAs, else 8; 8 or 16:
+ *                             only that size (the five-kernel form when it does not fit).
+ *   KFBI_OPT_COL_PAIRS        0 (default, 2): column pairs per block of the float32 column
+ *                             transform kernel, 1, 2 or 4 (bounded by its shared memory).
+ *   KFBI_OPT_PDL              0 (default): plain stream order; 1: consecutive kernels of an
+ *                             apply and of a GMRES iteration use programmatic dependent launch
+ *                             (a kernel starts while its predecessor finishes and waits on the
+ *                             device before it reads the predecessor's output). Batch graphs
+ *                             are always built without it.
+ * kfbi_set_option: value 0 or 1 unless stated. kfbi_get_option writes the value to *value (host).
  * Errors: ARG (unknown option, bad value, NULL, read-only option).
  */
-enum { KFBI_OPT_CUDA_GRAPHS = 1, KFBI_OPT_CLUSTER_GMRES = 2, KFBI_OPT_LAST_CLUSTER = 3, KFBI_OPT_PDL = 4 };
+enum {
+  KFBI_OPT_CUDA_GRAPHS = 1,
+  KFBI_OPT_CLUSTER_GMRES = 2,
+  KFBI_OPT_LAST_CLUSTER = 3,
+  KFBI_OPT_PDL = 4,
+  KFBI_OPT_CLUSTER_SIZE = 5,
+  KFBI_OPT_COL_PAIRS = 6
+};
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);
 
@@ -356,6 +368,51 @@ kfbi_status kfbi_warmstart_features(kfbi_ctx* ctx, const double* rhs, float* fea
 /* density[j] = rms(rhs) y_j: the network's initial density for kfbi_solve_bie (device
  * [n] float64), on the context's stream. n <= max_rows of the network. Async. */
 kfbi_status kfbi_warmstart_predict(kfbi_ctx* ctx, kfbi_mlp* mlp, const double* rhs, double* density);
+
+/* ------------------------------------------------------------------------------------
+ * Batched solves: many independent interface problems (each its own grid, box, kappa,
+ * interface and right-hand side) solved by one CUDA graph launch. Each instance runs exactly
+ * the method of kfbi_solve_bie (the paper solves one problem at a time, Sec. 4); the batch
+ * only puts all instances' solves into one graph as independent branches and gathers their
+ * results, so the host synchronises once per batch.
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+  int N;                          /* cells per side (as kfbi_create) */
+  double xmin, xmax, ymin, ymax;  /* square cells */
+  double kappa;                   /* c^2 >= 0 */
+  int boxbc;                      /* KFBI_BOX_* */
+  int max_nodes;                  /* interface node capacity */
+} kfbi_instance_desc;
+typedef struct kfbi_batch kfbi_batch;
+
+/* Creates count contexts (one per descriptor) in one precision (KFBI_FP64 or KFBI_MIXED).
+ * Errors: ARG, CAPACITY, CUDA (as kfbi_create). */
+kfbi_status kfbi_batch_create(int count, const kfbi_instance_desc* descs, int precision, kfbi_batch** out);
+/* Destroys the batch and its contexts. NULL is ignored. */
+void kfbi_batch_destroy(kfbi_batch* batch);
+/* Context of instance i (owned by the batch): set its interface with kfbi_set_interface, use
+ * any single-instance call on it. Errors: ARG. */
+kfbi_status kfbi_batch_context(kfbi_batch* batch, int i, kfbi_ctx** ctx);
+/* Stream the batch solve is ordered after (default: the legacy default stream). */
+kfbi_status kfbi_batch_set_stream(kfbi_batch* batch, void* stream);
+/* Solves every instance: rhs[i], density[i] device float64 [n_i] (host arrays of count
+ * pointers); density[i] holds the initial guess and receives the solution. kind:
+ * KFBI_BIE_INTERIOR_DL or KFBI_BIE_HS_EXTERIOR_MDL. tol, max_iter, restart as kfbi_solve_bie,
+ * the same for all instances. infos: host [count] (NULL skips). The graph is rebuilt when an
+ * interface, an option, a buffer pointer or tol / max_iter changed since the last call.
+ * Synchronises once. Returns OK when every instance converged, else the first failing
+ * status (NOT_CONVERGED before others); per-instance statuses are in infos.
+ * Errors: ARG, STATE (an instance without interface), CUDA. */
+kfbi_status kfbi_batch_solve(kfbi_batch* batch, int kind, const double* const* rhs, double* const* density,
+                             double tol, int max_iter, int restart, kfbi_solve_info* infos);
+/* Autotuner: for each grid size N of the batch, chooses the Gram-Schmidt form (16-CTA
+ * cluster, 8-CTA cluster, five kernels) and the column pairs per block of the float32 column
+ * transform (1, 2, 4) by timing whole batch solves of rhs from zero (coordinate search, the
+ * second of two launches timed) and leaves the fastest set on every context (read them back
+ * with kfbi_get_option). best_ms (host, NULL skips): batch solve time of the final choice.
+ * Errors: ARG, STATE, CUDA. */
+kfbi_status kfbi_batch_autotune(kfbi_batch* batch, int kind, const double* const* rhs, double tol, int max_iter,
+                                int restart, double* best_ms);
 
 /* Number of kernels this context has launched since creation (host output). */
 kfbi_status kfbi_launch_count(kfbi_ctx* ctx, long long* count);

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkfbi.so")
-SOURCES = ["kfbi_api.cu", "kfbi_geometry.cu", "kfbi_apply.cu", "kfbi_gmres.cu", "kfbi_step.cu", "kfbi_mlp.cu"]
+SOURCES = ["kfbi_api.cu", "kfbi_geometry.cu", "kfbi_apply.cu", "kfbi_gmres.cu", "kfbi_step.cu", "kfbi_mlp.cu", "kfbi_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

@@ -101,11 +101,17 @@ static void free_all(kfbi_ctx* c) {
                   c->probe_mark, c->prow_cnt, c->prow_ptr, c->probe_i, c->flags, c->counts, c->dcoef, c->dint,
                   c->boxg, c->facespec, c->spec, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack,
                   c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gpart, c->gw,
-                  c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag};
+                  c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag, c->irctl, c->ir_b, c->ir_x, c->ir_dn};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->host_counts) cudaFreeHost(c->host_counts);
   if (c->host_gctl) cudaFreeHost(c->host_gctl);
+  if (c->host_irctl) cudaFreeHost(c->host_irctl);
+  for (auto& row : c->irgraph)
+    for (auto& g : row) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
+    }
   for (auto& row : c->sgraph)
     for (auto& g : row) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -194,6 +200,11 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->gb, max_nodes));
   KFBI_CHECK(dalloc(&c->gx, max_nodes));
   KFBI_CHECK(dalloc(&c->gr, max_nodes));
+  KFBI_CHECK(dalloc(&c->irctl, 1));
+  KFBI_TRY(cudaMallocHost((void**)&c->host_irctl, sizeof(IrCtl)));
+  KFBI_CHECK(dalloc(&c->ir_b, max_nodes));
+  KFBI_CHECK(dalloc(&c->ir_x, max_nodes));
+  KFBI_CHECK(dalloc(&c->ir_dn, max_nodes));
   KFBI_CHECK(dalloc(&c->zero_flag, 4));
   KFBI_TRY(cudaMemset(c->zero_flag, 0, 4 * sizeof(int)));
   KFBI_TRY(cudaMemset(c->hcount, 0, NN * sizeof(int)));
@@ -430,7 +441,21 @@ const char* kfbi_status_string(kfbi_status s) {
 }
 
 kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
-  if (!ctx_ok(c) || (value != 0 && value != 1)) return KFBI_ERR_ARG;
+  if (!ctx_ok(c)) return KFBI_ERR_ARG;
+  if (option == KFBI_OPT_CLUSTER_SIZE) {
+    if (value != 0 && value != 8 && value != 16) return KFBI_ERR_ARG;
+    c->force_cs = value;
+    c->gmf = kfbi_ctx::GmfConfig{};
+    c->cfg_version += 1;
+    return KFBI_OK;
+  }
+  if (option == KFBI_OPT_COL_PAIRS) {
+    if (value != 0 && value != 1 && value != 2 && value != 4) return KFBI_ERR_ARG;
+    c->col_P = value;
+    c->cfg_version += 1;
+    return KFBI_OK;
+  }
+  if (value != 0 && value != 1) return KFBI_ERR_ARG;
   if (option == KFBI_OPT_CUDA_GRAPHS) {
     c->use_graphs = value != 0;
   } else if (option == KFBI_OPT_CLUSTER_GMRES) {
@@ -441,6 +466,7 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
   } else {
     return KFBI_ERR_ARG;
   }
+  c->cfg_version += 1;
   return KFBI_OK;
 }
 
@@ -450,6 +476,8 @@ kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
   else if (option == KFBI_OPT_CLUSTER_GMRES) *value = c->gm_cluster ? 1 : 0;
   else if (option == KFBI_OPT_LAST_CLUSTER) *value = c->gmf_last_cs;
   else if (option == KFBI_OPT_PDL) *value = c->use_pdl ? 1 : 0;
+  else if (option == KFBI_OPT_CLUSTER_SIZE) *value = c->force_cs;
+  else if (option == KFBI_OPT_COL_PAIRS) *value = c->col_P;
   else return KFBI_ERR_ARG;
   return KFBI_OK;
 }

@@ -744,9 +744,21 @@ __global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const
 }
 
 // --------------------------------------------------------------------------- host side
+// largest column-pair count whose double buffer fits the shared-memory budget
+constexpr size_t COL_SMEM_MAX = 200 * 1024;
 template <typename T>
-static int col_pairs(int N) {
-  int P = sizeof(T) == 8 ? 1 : 2;
+static int col_pairs_max(int N) {
+  int P = 4;
+  while (P > 1 && (2 * P > N || 2 * sizeof(V2<T>) * (size_t)P * N > COL_SMEM_MAX)) P /= 2;
+  return P;
+}
+
+// column pairs per block: float64 1, float32 2 unless overridden (kfbi_set_option)
+template <typename T>
+static int col_pairs(int N, int override_P = 0) {
+  int P = sizeof(T) == 8 ? 1 : (override_P > 0 ? override_P : 2);
+  const int pm = col_pairs_max<T>(N);
+  if (P > pm) P = pm;
   while (2 * P > N) P /= 2;
   return P < 1 ? 1 : P;
 }
@@ -760,7 +772,7 @@ static int col_threads(int N, int P) {
 template <typename T>
 static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
   const int N = c->N;
-  const int P = col_pairs<T>(N);
+  const int P = col_pairs<T>(N, c->col_P);
   size_t smem = 2 * sizeof(V2<T>) * (size_t)P * N;
   const bool rec = c->timing && !c->capturing && c->timing_used < TIMING_CAP;
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
@@ -887,26 +899,30 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   return KFBI_OK;
 }
 
-// shared-memory limits of the kernels whose dynamic shared memory may exceed 48 KB, set once
-// per context for its N and node capacity (no attribute calls during graph capture)
+// Shared-memory limits of the kernels whose dynamic shared memory may exceed 48 KB. The limit
+// is a property of the kernel for the whole process, not of a context, so it is set to the
+// largest size any context can launch with (grids up to 4096 cells, staged inputs up to
+// SMEM_STAGE_MAX); a launch still reserves only the shared memory it asks for.
+constexpr int MAX_GRID_N = 4096;
 template <typename T>
-static kfbi_status setup_t(kfbi_ctx* c) {
-  const int N = c->N;
-  int col = (int)(2 * sizeof(V2<T>) * (size_t)col_pairs<T>(N) * N);
-  int row = (int)(2 * sizeof(V2<T>) * (size_t)N);
+static kfbi_status setup_t(kfbi_ctx*) {
+  int col = 0;
+  for (int N = 16; N <= MAX_GRID_N; N *= 2) {
+    const int P = sizeof(T) == 8 ? 1 : col_pairs_max<T>(N);
+    const int b = (int)(2 * sizeof(V2<T>) * (size_t)P * N);
+    col = b > col ? b : col;
+  }
+  const int row = (int)(2 * sizeof(V2<T>) * (size_t)MAX_GRID_N);
   using T4 = typename std::conditional<sizeof(T) == 8, double4_32a, float4>::type;
-  using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
-  auto clampm = [](size_t b) { return (int)(b > SMEM_STAGE_MAX ? SMEM_STAGE_MAX : b); };
-  int dens = clampm((size_t)c->max_nodes * (sizeof(V2<T>) + sizeof(T)));
-  int box = clampm((size_t)c->max_nodes * sizeof(T4));
-  int jmp = clampm(((size_t)c->max_nodes / 2 + 1) * sizeof(V2<T>));
+  using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(nullptr))>::type>::type;
+  using S_t = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(nullptr))>::type>::type;
+  const int stage = (int)SMEM_STAGE_MAX;
   KFBI_TRY(cudaFuncSetAttribute(k_col_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, col));
   KFBI_TRY(cudaFuncSetAttribute(k_row_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
   KFBI_TRY(cudaFuncSetAttribute(k_face_dst<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
-  using S_t = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(c))>::type>::type;
-  KFBI_TRY(cudaFuncSetAttribute(k_dens_coef<T, true, S_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, dens));
-  KFBI_TRY(cudaFuncSetAttribute(k_box_data<T, T4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, box));
-  KFBI_TRY(cudaFuncSetAttribute(k_target_jumps<T, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, jmp));
+  KFBI_TRY(cudaFuncSetAttribute(k_dens_coef<T, true, S_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
+  KFBI_TRY(cudaFuncSetAttribute(k_box_data<T, T4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
+  KFBI_TRY(cudaFuncSetAttribute(k_target_jumps<T, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
   return KFBI_OK;
 }
 

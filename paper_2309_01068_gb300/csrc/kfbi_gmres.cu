@@ -12,6 +12,7 @@
 // flag), so extra bodies cost only their launches.
 #include <cmath>
 #include <cstddef>
+#include <vector>
 
 #include "kfbi_internal.cuh"
 
@@ -836,6 +837,131 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
   gmf_close(ctl, rank, hcond, use_cond, cap, done);
 }
 
+// --------------------------------------------------------------------------- device-driven refinement
+__global__ void k_ir_init(IrCtl* ir, double tol, int max_iter, int max_sweeps, int cap_outer) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ir->done = 0;
+  ir->status = KFBI_OK;
+  ir->sweeps = 0;
+  ir->total_its = 0;
+  ir->total_cycles = 0;
+  ir->inner_bodies = 0;
+  ir->run_inner = 0;
+  ir->outer_bodies = 0;
+  ir->max_iter = max_iter;
+  ir->max_sweeps = max_sweeps;
+  ir->cap_outer = cap_outer;
+  ir->tol = tol;
+  ir->rel = 1.0;
+}
+
+// r = b - y (y = A64 x), ||r|| / ||b||, the decision of the sweep, and for another sweep the
+// start of the inner float32 GMRES on A d = r from d = 0 (tolerance 0.5 tol / rel clamped to
+// [1e-5, 0.5]; the inner GMRES trusts its Givens estimate). One block.
+__global__ void k_ir_decide(IrCtl* ir, GmresCtl* g, const double* b, const double* y, double* r, double* V,
+                            double* d, double* gin, float* gin_f, int n, int m, cudaGraphConditionalHandle h_inner) {
+  __shared__ double sh[32];
+  __shared__ double s_rr;
+  __shared__ int s_run;
+  __shared__ double s_inv;
+  double rr = 0.0, bb = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double ri = b[i] - y[i];
+    r[i] = ri;
+    rr += ri * ri;
+    bb += b[i] * b[i];
+  }
+  rr = block_sum(rr, sh);
+  if (threadIdx.x == 0) s_rr = rr;
+  __syncthreads();
+  bb = block_sum(bb, sh);
+  if (threadIdx.x == 0) {
+    rr = s_rr;
+    const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    ir->rel = rel;
+    ir->sweeps += 1;
+    int run = 0;
+    if (rel <= ir->tol) {
+      ir->done = 1;
+      ir->status = KFBI_OK;
+    } else if (ir->total_its >= ir->max_iter || ir->sweeps > ir->max_sweeps) {
+      ir->done = 1;
+      ir->status = KFBI_ERR_NOT_CONVERGED;
+    } else {
+      run = 1;
+      double inner = 0.5 * ir->tol / rel;
+      inner = inner < 1e-5 ? 1e-5 : (inner > 0.5 ? 0.5 : inner);
+      const double bn = sqrt(rr);
+      g->phase = PH_ARNOLDI;
+      g->next_phase = PH_ARNOLDI;
+      g->done = 0;
+      g->action = ACT_NONE;
+      g->j = 0;
+      g->k_end = 0;
+      g->its = 0;
+      g->cycles = 0;
+      g->max_iter = ir->max_iter - ir->total_its;
+      g->m = m;
+      g->status = KFBI_OK;
+      g->ticket = 0;
+      g->breakdown = 0;
+      g->trust = 1;
+      g->bodies = 0;
+      g->tol = inner;
+      g->bnorm = bn;
+      g->beta = bn;
+      g->hnorm = 0.0;
+      g->res_est = 0.0;
+      g->g[0] = bn;
+      for (int k = 1; k <= m; ++k) g->g[k] = 0.0;
+      s_inv = 1.0 / bn;
+    }
+    ir->run_inner = run;
+    s_run = run;
+    cudaGraphSetConditional(h_inner, run ? 1u : 0u);
+  }
+  __syncthreads();
+  if (!s_run) return;
+  const double inv = s_inv;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = r[i] * inv;
+    V[i] = v;
+    gin[i] = v;
+    gin_f[i] = (float)v;
+    d[i] = 0.0;
+  }
+}
+
+// after the inner GMRES: x += d, d = 0, iteration totals, the loop condition of the sweeps
+__global__ void k_ir_finish(IrCtl* ir, const GmresCtl* g, double* x, double* d, int n,
+                            cudaGraphConditionalHandle h_outer) {
+  __shared__ int s_run;
+  if (threadIdx.x == 0) s_run = ir->run_inner;
+  __syncthreads();
+  if (s_run)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      x[i] += d[i];
+      d[i] = 0.0;
+    }
+  if (threadIdx.x != 0) return;
+  if (s_run) {
+    ir->total_its += g->its;
+    ir->total_cycles += g->cycles;
+    ir->inner_bodies += g->bodies;
+    if (g->status == KFBI_ERR_TIMEOUT) {
+      ir->done = 1;
+      ir->status = KFBI_ERR_TIMEOUT;
+    }
+    ir->run_inner = 0;
+  }
+  ir->outer_bodies += 1;
+  if (!ir->done && ir->outer_bodies >= ir->cap_outer) {
+    ir->done = 1;
+    ir->status = KFBI_ERR_TIMEOUT;
+  }
+  cudaGraphSetConditional(h_outer, ir->done ? 0u : 1u);
+}
+
 // --------------------------------------------------------------------------- host side
 // Largest dynamic shared memory the cluster kernel may use (set once per context).
 static size_t gmf_smem_limit(kfbi_ctx* c) {
@@ -880,7 +1006,7 @@ static cudaLaunchConfig_t gmf_launch_config(kfbi_ctx* c, const kfbi_ctx::GmfConf
 // Cluster form for n nodes and restart m: 16 CTAs (else 8) whose slices of V (and, when it
 // fits, the Hessenberg matrix for the back substitution) fit in shared memory and that the
 // device can co-schedule. cs = 0: the multi-kernel form.
-static kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m) {
+kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m) {
   kfbi_ctx::GmfConfig none{};
   if (!c->gm_cluster) return none;
   if (c->gmf.n == n && c->gmf.m == m) return c->gmf;
@@ -890,6 +1016,7 @@ static kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m) {
   pick.m = m;
   for (int cs : {16, 8}) {
     if (pick.cs) break;
+    if (c->force_cs != 0 && cs != c->force_cs) continue;
     const int R = cdiv(n, cs), Rp = gmf_row_stride(R);
     const size_t base = sizeof(double) * ((size_t)(m + 1) * Rp + Rp);
     for (int hs : {1, 0}) {
@@ -945,10 +1072,33 @@ static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, c
   return KFBI_OK;
 }
 
-static int body_cap(int max_iter, int m) { return 2 * max_iter + 2 * (max_iter / m) + 8; }
+int body_cap(int max_iter, int m) { return 2 * max_iter + 2 * (max_iter / m) + 8; }
 
-// Builds the graph of one solve: a conditional WHILE node whose body (captured from the
-// stream) is one GMRES iteration followed by k_gm_cond.
+kfbi_status cap_begin(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd);
+kfbi_status cap_end(kfbi_ctx* c, std::vector<cudaGraphNode_t>* sinks);
+kfbi_status add_while(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, cudaGraphConditionalHandle h,
+                             cudaGraphNode_t* node, cudaGraph_t* body);
+
+// Adds to graph g (after deps) the GMRES loop of one solve: a conditional WHILE node whose
+// body (captured from the context's stream) is one GMRES iteration that also sets the loop
+// condition. k_gm_init and k_gm_start must run before it.
+kfbi_status add_gmres_nodes(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, int kind, bool fp32,
+                            const double* eps_v, const double* b, double* x, int cap, const kfbi_ctx::GmfConfig& gf,
+                            cudaGraphNode_t* node, int* body_launches) {
+  cudaGraphConditionalHandle h;
+  KFBI_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+  cudaGraph_t bodyg;
+  KFBI_CHECK(add_while(g, deps, nd, h, node, &bodyg));
+  KFBI_CHECK(cap_begin(c, bodyg, nullptr, 0));
+  const long long l0 = c->launches;
+  kfbi_status st = body(c, kind, fp32, eps_v, b, x, gf, h, 1, cap);
+  *body_launches = (int)(c->launches - l0);
+  c->launches = l0;  // capture launches nothing; replays are counted per body
+  kfbi_status st2 = cap_end(c, nullptr);
+  KFBI_CHECK(st);
+  return st2;
+}
+
 static kfbi_status build_graph(kfbi_ctx* c, kfbi_ctx::SolveGraph& G, int kind, bool fp32, const double* eps_v,
                                const double* b, double* x, int cap, const kfbi_ctx::GmfConfig& gf) {
   if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -957,31 +1107,35 @@ static kfbi_status build_graph(kfbi_ctx* c, kfbi_ctx::SolveGraph& G, int kind, b
   G.graph = nullptr;
   G.version = -1;
   KFBI_TRY(cudaGraphCreate(&G.graph, 0));
-  cudaGraphConditionalHandle h;
-  KFBI_TRY(cudaGraphConditionalHandleCreate(&h, G.graph, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = h;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
   cudaGraphNode_t node;
-  KFBI_TRY(cudaGraphAddNode(&node, G.graph, nullptr, nullptr, 0, &cp));
-  cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
-  cudaStream_t s = c->stream;
-  KFBI_TRY(cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-  c->capturing = true;
-  const long long l0 = c->launches;
-  kfbi_status st = body(c, kind, fp32, eps_v, b, x, gf, h, 1, cap);
-  G.body_launches = (int)(c->launches - l0);
-  c->launches = l0;  // capture launches nothing; replays are counted per body
-  c->capturing = false;
-  cudaGraph_t out = nullptr;
-  cudaError_t e = cudaStreamEndCapture(s, &out);
-  if (st != KFBI_OK) return st;
-  KFBI_TRY(e);
-  KFBI_TRY(cudaGetLastError());
-  KFBI_TRY(cudaGraphInstantiate(&G.exec, G.graph, 0));
+  kfbi_status st = add_gmres_nodes(c, G.graph, nullptr, 0, kind, fp32, eps_v, b, x, cap, gf, &node, &G.body_launches);
+  if (st == KFBI_OK && cudaGraphInstantiate(&G.exec, G.graph, 0) != cudaSuccess) st = KFBI_ERR_CUDA;
+  if (st != KFBI_OK) {
+    G.graph = nullptr;  // released without cudaGraphDestroy (see solve_ir_graph)
+    G.exec = nullptr;
+    cudaGetLastError();
+    return st;
+  }
   G.version = c->iface_version;
+  return KFBI_OK;
+}
+
+int restart_length(int restart, int n) {
+  int m = restart < n ? restart : n;
+  if (m > MAX_RESTART) m = MAX_RESTART;
+  return m < 1 ? 1 : m;
+}
+
+kfbi_status gmres_start_enqueue(kfbi_ctx* c, double tol, int max_iter, int m) {
+  k_gm_init<<<1, 32, 0, c->stream>>>(c->gctl, tol, max_iter, m, 0);
+  k_gm_start<<<1, 1024, 0, c->stream>>>(c->gb, c->gx, c->gin, c->gin_f, c->gV, c->n, c->gctl, 0);
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
+kfbi_status ir_start_enqueue(kfbi_ctx* c, double tol, int max_iter) {
+  k_ir_init<<<1, 32, 0, c->stream>>>(c->irctl, tol, max_iter, IR_MAX_SWEEPS, IR_MAX_SWEEPS + 2);
+  KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
 }
 
@@ -1007,11 +1161,13 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   if (c->use_graphs && !c->timing) {
     kfbi_ctx::SolveGraph& G = c->sgraph[kind][fp32 ? 1 : 0];
     kfbi_status st = KFBI_OK;
-    if (G.exec == nullptr || G.version != c->iface_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl) {
+    if (G.exec == nullptr || G.version != c->iface_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
+        G.cfg != c->cfg_version) {
       st = build_graph(c, G, kind, fp32, eps_v, b, x, cap, gf);
       G.m = m;
       G.cs = gf.cs;
       G.pdl = c->use_pdl;
+      G.cfg = c->cfg_version;
     }
     if (st == KFBI_OK && cudaGraphLaunch(G.exec, s) == cudaSuccess) {
       graphed = true;
@@ -1045,6 +1201,160 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   return KFBI_OK;
 }
 
+// ---- device-driven refinement as one graph: a WHILE node over the sweeps whose body is
+//   [float64 apply of x] -> k_ir_decide -> WHILE node over the inner GMRES bodies -> k_ir_finish
+// (nested conditional nodes), so a mixed-precision solve is one graph launch.
+kfbi_status cap_begin(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd) {
+  KFBI_TRY(cudaStreamBeginCaptureToGraph(c->stream, g, deps, nullptr, nd, cudaStreamCaptureModeRelaxed));
+  c->capturing = true;
+  return KFBI_OK;
+}
+
+// ends the capture; sinks (optional) receives the capture's last nodes
+kfbi_status cap_end(kfbi_ctx* c, std::vector<cudaGraphNode_t>* sinks) {
+  cudaError_t e = cudaSuccess;
+  if (sinks != nullptr) {
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(c->stream, &cst, nullptr, nullptr, &deps, nullptr, &nd);
+    if (e == cudaSuccess) sinks->assign(deps, deps + nd);
+  }
+  c->capturing = false;
+  cudaGraph_t out = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(c->stream, &out);
+  KFBI_TRY(e);
+  KFBI_TRY(e2);
+  return KFBI_OK;
+}
+
+kfbi_status add_while(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, cudaGraphConditionalHandle h,
+                      cudaGraphNode_t* node, cudaGraph_t* body) {
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  KFBI_TRY(cudaGraphAddNode(node, g, deps, nullptr, nd, &cp));
+  *body = cp.conditional.phGraph_out[0];
+  return KFBI_OK;
+}
+
+// Adds the refinement loop of context c to graph g (a root node). The loop works on the
+// context's copies ir_b (rhs) and ir_x (iterate), ir_dn (normal derivative of the last float64
+// apply, when want_dn); k_ir_init must run before each launch.
+kfbi_status add_ir_nodes(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, int kind, bool want_dn,
+                         int m, const kfbi_ctx::GmfConfig& gf, int cap_inner, cudaGraphNode_t* node,
+                         int* inner_body_launches) {
+  const int n = c->n;
+  const double* ev = kind == KFBI_BIE_STEFAN_SL ? c->gev : nullptr;
+  const int layer = kind == KFBI_BIE_STEFAN_SL ? KFBI_SINGLE : KFBI_DOUBLE;
+  cudaGraphConditionalHandle h_outer, h_inner;
+  KFBI_TRY(cudaGraphConditionalHandleCreate(&h_outer, g, 1, cudaGraphCondAssignDefault));
+  KFBI_TRY(cudaGraphConditionalHandleCreate(&h_inner, g, 0, cudaGraphCondAssignDefault));
+  cudaGraphNode_t n_outer, n_inner;
+  cudaGraph_t b_outer, b_inner;
+  KFBI_CHECK(add_while(g, deps, nd, h_outer, &n_outer, &b_outer));
+  *node = n_outer;
+  const long long l0 = c->launches;
+  // sweep part 1: float64 apply of the iterate, residual and decision
+  KFBI_CHECK(cap_begin(c, b_outer, nullptr, 0));
+  kfbi_status st = apply_enqueue(c, layer, false, c->ir_x, c->tmp_vals, want_dn ? c->ir_dn : nullptr, nullptr, kind,
+                                 ev, c->zero_flag, nullptr);
+  if (st == KFBI_OK) {
+    k_ir_decide<<<1, 1024, 0, c->stream>>>(c->irctl, c->gctl, c->ir_b, c->tmp_vals, c->gb, c->gV, c->gx, c->gin,
+                                           c->gin_f, n, m, h_inner);
+    if (cudaGetLastError() != cudaSuccess) st = KFBI_ERR_CUDA;
+  }
+  std::vector<cudaGraphNode_t> sinks;
+  kfbi_status st2 = cap_end(c, &sinks);
+  KFBI_CHECK(st);
+  KFBI_CHECK(st2);
+  // inner GMRES loop
+  KFBI_CHECK(add_while(b_outer, sinks.data(), sinks.size(), h_inner, &n_inner, &b_inner));
+  KFBI_CHECK(cap_begin(c, b_inner, nullptr, 0));
+  const long long l1 = c->launches;
+  st = body(c, kind, true, ev, c->gb, c->gx, gf, h_inner, 1, cap_inner);
+  *inner_body_launches = (int)(c->launches - l1);
+  st2 = cap_end(c, nullptr);
+  KFBI_CHECK(st);
+  KFBI_CHECK(st2);
+  // sweep part 2: x += d and the loop condition
+  KFBI_CHECK(cap_begin(c, b_outer, &n_inner, 1));
+  k_ir_finish<<<1, 256, 0, c->stream>>>(c->irctl, c->gctl, c->ir_x, c->gx, n, h_outer);
+  st = cudaGetLastError() == cudaSuccess ? KFBI_OK : KFBI_ERR_CUDA;
+  st2 = cap_end(c, nullptr);
+  c->launches = l0;  // capture launches nothing
+  KFBI_CHECK(st);
+  return st2;
+}
+
+// One mixed-precision solve as a graph launch. *used = false: the graph form is unavailable
+// (the caller runs the host-driven loop instead).
+static kfbi_status solve_ir_graph(kfbi_ctx* c, int kind, const double* rhs, double tol, int max_iter, int restart,
+                                  double* x, double* dnormal, kfbi_solve_info* out, bool* used) {
+  *used = false;
+  cudaStream_t s = c->stream;
+  const int n = c->n;
+  int m = restart < n ? restart : n;
+  if (m > MAX_RESTART) m = MAX_RESTART;
+  if (m < 1) m = 1;
+  c->gm_m = m;
+  const kfbi_ctx::GmfConfig gf = gmf_select(c, n, m);
+  c->gmf_last_cs = gf.cs;
+  const int cap = body_cap(max_iter, m);
+  const int max_sweeps = IR_MAX_SWEEPS;
+  kfbi_ctx::IrGraph& G = c->irgraph[kind][dnormal != nullptr ? 1 : 0];
+  if (G.exec == nullptr || G.version != c->iface_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
+      G.cap != cap || G.cfg != c->cfg_version) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G.exec = nullptr;
+    G.graph = nullptr;
+    G.version = -1;
+    kfbi_status st = cudaGraphCreate(&G.graph, 0) == cudaSuccess ? KFBI_OK : KFBI_ERR_CUDA;
+    cudaGraphNode_t node;
+    if (st == KFBI_OK)
+      st = add_ir_nodes(c, G.graph, nullptr, 0, kind, dnormal != nullptr, m, gf, cap, &node, &G.inner_body_launches);
+    if (st == KFBI_OK && cudaGraphInstantiate(&G.exec, G.graph, 0) != cudaSuccess) st = KFBI_ERR_CUDA;
+    if (st != KFBI_OK) {
+      // released without cudaGraphDestroy (a graph whose capture failed crashed the driver on
+      // destruction); the host-driven loop takes over
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+      G.graph = nullptr;
+      cudaGetLastError();
+      return KFBI_OK;  // not used
+    }
+    G.version = c->iface_version;
+    G.m = m;
+    G.cs = gf.cs;
+    G.pdl = c->use_pdl;
+    G.cap = cap;
+    G.cfg = c->cfg_version;
+  }
+  const size_t bytes = sizeof(double) * n;
+  KFBI_TRY(cudaMemcpyAsync(c->ir_b, rhs, bytes, cudaMemcpyDeviceToDevice, s));
+  KFBI_TRY(cudaMemcpyAsync(c->ir_x, x, bytes, cudaMemcpyDeviceToDevice, s));
+  k_ir_init<<<1, 32, 0, s>>>(c->irctl, tol, max_iter, max_sweeps, max_sweeps + 2);
+  KFBI_TRY(cudaGetLastError());
+  KFBI_TRY(cudaGraphLaunch(G.exec, s));
+  *used = true;
+  KFBI_TRY(cudaMemcpyAsync(x, c->ir_x, bytes, cudaMemcpyDeviceToDevice, s));
+  if (dnormal != nullptr) KFBI_TRY(cudaMemcpyAsync(dnormal, c->ir_dn, bytes, cudaMemcpyDeviceToDevice, s));
+  KFBI_TRY(cudaMemcpyAsync(c->host_irctl, c->irctl, sizeof(IrCtl), cudaMemcpyDeviceToHost, s));
+  KFBI_TRY(cudaStreamSynchronize(s));
+  const IrCtl& h = *c->host_irctl;
+  c->launches += 1 + (long long)h.sweeps * (c->per_apply_launches[0] + 2) +
+                 (long long)h.inner_bodies * G.inner_body_launches;
+  out->iterations = h.total_its;
+  out->restarts = h.total_cycles > h.sweeps - 1 ? h.total_cycles - (h.sweeps - 1) : 0;
+  out->refinements = h.sweeps;
+  out->rel_residual = h.rel;
+  out->status = h.status;
+  return KFBI_OK;
+}
+
 // dnormal (optional, mixed precision only): the refinement's float64 applies also write the
 // normal derivative of the layer potential of the iterate; the last one belongs to the
 // returned density. Set to nullptr on return when it was not produced.
@@ -1072,13 +1382,22 @@ kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const dou
     out.rel_residual = rel;
     out.status = st;
   } else {
+    if (c->use_graphs && !c->timing) {
+      bool used = false;
+      KFBI_CHECK(solve_ir_graph(c, kind, rhs, tol, max_iter, restart, x, dnormal, &out, &used));
+      if (used) {
+        if (info) *info = out;
+        return (kfbi_status)out.status;
+      }
+      c->use_graphs = false;  // keep the host-driven loops from now on
+    }
     // iterative refinement: r = b - A64 x (float64 apply); solve A32 d = r by GMRES with
     // float32 grid applies from d = 0 to a tolerance the float32 operator resolves; x += d
     double* y = c->tmp_vals;                 // A64 x
     double* hres = (double*)c->host_counts;  // pinned scratch (2 doubles)
     int total_its = 0, total_cyc = 0, sweeps = 0, st = KFBI_OK;
     double rel = 1.0;
-    const int max_sweeps = 12;
+    const int max_sweeps = IR_MAX_SWEEPS;
     int layer = kind == KFBI_BIE_STEFAN_SL ? KFBI_SINGLE : KFBI_DOUBLE;
     while (true) {
       KFBI_CHECK(apply_enqueue(c, layer, false, x, y, dnormal, nullptr, kind, ev, nullptr));

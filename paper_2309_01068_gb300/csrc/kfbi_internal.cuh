@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 #include "kfbi.h"
 
@@ -115,6 +116,14 @@ struct GmresCtl {
 };
 enum : int { PH_RESID = 0, PH_ARNOLDI = 1, PH_DONE = 2 };
 
+// Control block of the device-driven iterative refinement (mixed precision): one float64
+// apply and residual per sweep, then an inner float32 GMRES run on the residual.
+struct IrCtl {
+  int done, status, sweeps, total_its, total_cycles, inner_bodies, run_inner, outer_bodies;
+  int max_iter, max_sweeps, cap_outer, pad;
+  double tol, rel;
+};
+
 }  // namespace kfbi
 
 struct kfbi_ctx {
@@ -220,6 +229,7 @@ struct kfbi_ctx {
     int m = 0;
     int cs = 0;             // cluster size of the Gram-Schmidt kernel (0: multi-kernel form)
     bool pdl = false;       // built with programmatic dependent launch
+    int cfg = -1;           // cfg_version it was built with
     int body_launches = 0;  // kernels per replayed body
   } sgraph[3][2];
   // cluster form of the GMRES body (k_gm_cluster) for the last (n, m); cs = 0: multi-kernel
@@ -228,8 +238,26 @@ struct kfbi_ctx {
     int cs = 0, R = 0, hsmem = 0;
     size_t smem = 0;
   } gmf;
+  // device-driven refinement: control block, rhs / iterate / normal-derivative copies, and
+  // one graph per (BIE kind, with normal derivative) holding the nested refinement loop
+  kfbi::IrCtl* irctl = nullptr;
+  kfbi::IrCtl* host_irctl = nullptr;  // pinned
+  double* ir_b = nullptr;       // [max_nodes]
+  double* ir_x = nullptr;       // [max_nodes]
+  double* ir_dn = nullptr;      // [max_nodes]
+  struct IrGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long version = -1;
+    int m = 0, cs = 0, cap = 0, cfg = -1;
+    bool pdl = false;
+    int inner_body_launches = 0;
+  } irgraph[3][2];
   bool gm_cluster = true;       // allow the cluster form
-  bool use_pdl = true;          // programmatic dependent launch between the kernels of a body
+  bool use_pdl = false;         // programmatic dependent launch between the kernels of a body
+  int force_cs = 0;             // cluster size of the Gram-Schmidt kernel: 0 automatic, 8 or 16
+  int col_P = 0;                // column pairs per block of the float32 column kernel (0 automatic)
+  int cfg_version = 0;          // bumped by every option that changes the launched kernels
   int gmf_last_cs = 0;          // cluster size used by the last GMRES run
   size_t gmf_smem_max = 0;      // 0 = not queried yet, 1 = unavailable
   long iface_version = 0;
@@ -339,6 +367,24 @@ kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* densi
                           double* dnormal, double* grid, int bie_kind, const double* eps_v,
                           const int* skip_flag, const float* density_f = nullptr);
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u);
+
+// graph building blocks shared by the single solve and the batch (kfbi_gmres.cu)
+kfbi_status cap_begin(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd);
+kfbi_status cap_end(kfbi_ctx* c, std::vector<cudaGraphNode_t>* sinks);
+kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m);
+int body_cap(int max_iter, int m);
+int restart_length(int restart, int n);
+kfbi_status add_gmres_nodes(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, int kind, bool fp32,
+                            const double* eps_v, const double* b, double* x, int cap, const kfbi_ctx::GmfConfig& gf,
+                            cudaGraphNode_t* node, int* body_launches);
+kfbi_status add_ir_nodes(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, int kind, bool want_dn,
+                         int m, const kfbi_ctx::GmfConfig& gf, int cap_inner, cudaGraphNode_t* node,
+                         int* inner_body_launches);
+// enqueue on c->stream: the start of a float64 GMRES run on (gb, gx) with gx the initial guess,
+// or the start of a refinement run on (ir_b, ir_x)
+kfbi_status gmres_start_enqueue(kfbi_ctx* c, double tol, int max_iter, int m);
+kfbi_status ir_start_enqueue(kfbi_ctx* c, double tol, int max_iter);
+constexpr int IR_MAX_SWEEPS = 12;
 kfbi_status interp_grid_enqueue(kfbi_ctx* c, const double* grid, double* values);
 
 }  // namespace kfbi

@@ -398,10 +398,12 @@ __global__ void k_ws_scale(int n, const float* y, const double* scale, double* o
 }
 
 // --------------------------------------------------------------------------- host side
-static size_t rows_smem(const kfbi_mlp* m) {
-  return sizeof(__nv_bfloat16) * (size_t)m->H * (m->H + 2) +
-         sizeof(float) * ((size_t)MLP_ROWS * m->F + 2 * (size_t)MLP_ROWS * m->H);
+static size_t rows_smem_h(int F, int H) {
+  return sizeof(__nv_bfloat16) * (size_t)H * (H + 2) + sizeof(float) * ((size_t)MLP_ROWS * F + 2 * (size_t)MLP_ROWS * H);
 }
+static size_t rows_smem(const kfbi_mlp* m) { return rows_smem_h(m->F, m->H); }
+// the kernel's shared-memory limit is process-wide: set for the widest network
+static size_t rows_smem_max() { return rows_smem_h(KFBI_MLP_FEATURES, MLP_MAX_H); }
 
 static kfbi_status run_rows(kfbi_mlp* m, const float* X, const int* idx, int rows, const float* target, float* y) {
   const int nb = cdiv(rows, MLP_ROWS);
@@ -488,7 +490,7 @@ kfbi_status kfbi_mlp_create(int hidden, int max_rows, kfbi_mlp** out) {
   }
   cudaError_t e = cudaMallocHost((void**)&m->host_loss, sizeof(float));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_mlp_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem(m));
+    e = cudaFuncSetAttribute(k_mlp_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem_max());
   if (e != cudaSuccess) {
     note_cuda_error(e, "kfbi_mlp_create", __FILE__, __LINE__);
     mlp_free(m);
@@ -568,7 +570,8 @@ kfbi_status kfbi_warmstart_features(kfbi_ctx* c, const double* rhs, float* feat,
   const int n = c->n;
   if (n > FEAT_MAX_N) return KFBI_ERR_CAPACITY;
   const size_t smem = sizeof(float) * 3 * (size_t)n;
-  KFBI_TRY(cudaFuncSetAttribute(k_ws_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KFBI_TRY(cudaFuncSetAttribute(k_ws_features, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(float) * 3 * (size_t)FEAT_MAX_N)));
   KFBI_TRY(stream_enter(c));
   launched(c, 1);
   k_ws_features<<<1, FEAT_THREADS, smem, c->stream>>>(n, c->tgeo + c->n_cross, c->xy, (const double2*)c->twn, rhs,
@@ -584,7 +587,8 @@ kfbi_status kfbi_warmstart_predict(kfbi_ctx* c, kfbi_mlp* m, const double* rhs, 
   const int n = c->n;
   if (n > m->max_rows || n > FEAT_MAX_N) return KFBI_ERR_CAPACITY;
   const size_t smem = sizeof(float) * 3 * (size_t)n;
-  KFBI_TRY(cudaFuncSetAttribute(k_ws_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  KFBI_TRY(cudaFuncSetAttribute(k_ws_features, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(float) * 3 * (size_t)FEAT_MAX_N)));
   // features, network and scaling all run on the context's stream
   KFBI_TRY(stream_enter(c));
   launched(c, 3);

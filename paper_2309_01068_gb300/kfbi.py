@@ -18,7 +18,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "kfbi.h")
 
 # codes mirrored from include/kfbi.h
 OK, ERR_ARG, ERR_CUDA, ERR_OUTSIDE_BOX, ERR_UNDERRESOLVED, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
-OPT_CUDA_GRAPHS, OPT_CLUSTER_GMRES, OPT_LAST_CLUSTER, OPT_PDL = 1, 2, 3, 4
+OPT_CUDA_GRAPHS, OPT_CLUSTER_GMRES, OPT_LAST_CLUSTER, OPT_PDL, OPT_CLUSTER_SIZE, OPT_COL_PAIRS = 1, 2, 3, 4, 5, 6
 MLP_FEATURES, MLP_MODES = 47, 16
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2
@@ -40,6 +40,12 @@ class SolveInfo(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class InstanceDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("ymin", ctypes.c_double), ("ymax", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("boxbc", ctypes.c_int), ("max_nodes", ctypes.c_int)]
 
 
 class ThetaLParams(ctypes.Structure):
@@ -90,6 +96,12 @@ _SIGNATURES = {
     "kfbi_mlp_train_step": (_I, [_P, _P, _P, _P, _I, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]),
     "kfbi_warmstart_features": (_I, [_P, _P, _P, _P]),
     "kfbi_warmstart_predict": (_I, [_P, _P, _P, _P]),
+    "kfbi_batch_create": (_I, [_I, _P, _I, ctypes.POINTER(_P)]),
+    "kfbi_batch_destroy": (None, [_P]),
+    "kfbi_batch_context": (_I, [_P, _I, ctypes.POINTER(_P)]),
+    "kfbi_batch_set_stream": (_I, [_P, _P]),
+    "kfbi_batch_solve": (_I, [_P, _I, _P, _P, _D, _I, _I, _P]),
+    "kfbi_batch_autotune": (_I, [_P, _I, _P, _D, _I, _I, ctypes.POINTER(_D)]),
     "kfbi_get_option": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "kfbi_grid_solve_noalloc": (_I, [_I, _D, _D, _I, _P, _P, _P]),
 }
@@ -170,9 +182,22 @@ class Context:
                                     ctypes.byref(h)), "kfbi_create")
         self.handle = h
 
+    @classmethod
+    def borrowed(cls, handle, N, box, kappa, boxbc, precision, max_nodes):
+        """A Context view of a context owned elsewhere (a batch instance); close() leaves it."""
+        self = cls.__new__(cls)
+        self.lib = load()
+        self.N, self.box, self.kappa = int(N), tuple(float(b) for b in box), float(kappa)
+        self.boxbc, self.precision, self.max_nodes = int(boxbc), int(precision), int(max_nodes)
+        self.n = 0
+        self.handle = handle
+        self._borrowed = True
+        return self
+
     def close(self):
         if getattr(self, "handle", None):
-            self.lib.kfbi_destroy(self.handle)
+            if not getattr(self, "_borrowed", False):
+                self.lib.kfbi_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -398,6 +423,71 @@ class Mlp:
         _check(self.lib.kfbi_mlp_train_step(self.handle, _ptr(feat), _ptr(target), _ptr(idx), rows, float(lr),
                                             ctypes.byref(loss) if want_loss else None), "kfbi_mlp_train_step")
         return loss.value if want_loss else None
+
+
+class Batch:
+    """kfbi_batch_*: many independent instances solved by one graph launch."""
+
+    def __init__(self, descs, precision=MIXED):
+        """descs: list of dict(N, box=(xmin, xmax, ymin, ymax), kappa, boxbc, max_nodes)."""
+        self.lib = load()
+        self.count = len(descs)
+        self.precision = int(precision)
+        arr = (InstanceDesc * self.count)()
+        for i, d in enumerate(descs):
+            x0, x1, y0, y1 = (float(v) for v in d["box"])
+            arr[i] = InstanceDesc(int(d["N"]), x0, x1, y0, y1, float(d.get("kappa", 0.0)),
+                                  int(d.get("boxbc", BOX_DIRICHLET0)), int(d["max_nodes"]))
+        h = ctypes.c_void_p()
+        _check(self.lib.kfbi_batch_create(self.count, ctypes.cast(arr, ctypes.c_void_p), self.precision,
+                                          ctypes.byref(h)), "kfbi_batch_create")
+        self.handle = h
+        self.contexts = []
+        for i, d in enumerate(descs):
+            c = ctypes.c_void_p()
+            _check(self.lib.kfbi_batch_context(self.handle, i, ctypes.byref(c)), "kfbi_batch_context")
+            self.contexts.append(Context.borrowed(c, d["N"], d["box"], d.get("kappa", 0.0),
+                                                  d.get("boxbc", BOX_DIRICHLET0), self.precision, d["max_nodes"]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            for c in self.contexts:
+                c.handle = None
+            self.lib.kfbi_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def _ptrs(self, tensors):
+        arr = (ctypes.c_void_p * self.count)()
+        for i, t in enumerate(tensors):
+            arr[i] = _ptr(t).value
+        return arr
+
+    def solve(self, kind, rhs, density, tol=1e-8, max_iter=500, restart=100):
+        """rhs, density: lists of device float64 tensors; density holds the guess, gets the
+        solution. Returns (status, list of info dicts)."""
+        _check(self.lib.kfbi_batch_set_stream(self.handle, _stream()), "kfbi_batch_set_stream")
+        infos = (SolveInfo * self.count)()
+        rp, dp = self._ptrs(rhs), self._ptrs(density)  # kept alive across the call
+        st = self.lib.kfbi_batch_solve(self.handle, int(kind), ctypes.cast(rp, ctypes.c_void_p),
+                                       ctypes.cast(dp, ctypes.c_void_p), float(tol), int(max_iter), int(restart),
+                                       ctypes.cast(infos, ctypes.c_void_p))
+        _check(st, "kfbi_batch_solve", allow=(ERR_NOT_CONVERGED,))
+        return st, [infos[i].as_dict() for i in range(self.count)]
+
+    def autotune(self, kind, rhs, tol=1e-8, max_iter=500, restart=100):
+        _check(self.lib.kfbi_batch_set_stream(self.handle, _stream()), "kfbi_batch_set_stream")
+        ms = ctypes.c_double()
+        rp = self._ptrs(rhs)
+        _check(self.lib.kfbi_batch_autotune(self.handle, int(kind), ctypes.cast(rp, ctypes.c_void_p),
+                                            float(tol), int(max_iter), int(restart), ctypes.byref(ms)),
+               "kfbi_batch_autotune")
+        return ms.value
 
 
 def grid_solve_noalloc(rhs, h, kappa=0.0, boxbc=BOX_DIRICHLET0, out=None):

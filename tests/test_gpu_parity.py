@@ -194,15 +194,23 @@ def test_gmres_cluster_long_restart_without_staged_hessenberg():
     assert rel(phi.cpu().numpy(), rphi) < 1e-9
 
 
-def test_mixed_precision_refinement():
-    """FP32 grid applies inside GMRES, FP64 residual and refinement: density within 1e-9 of FP64."""
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_mixed_precision_refinement(graphs):
+    """FP32 grid applies inside GMRES, FP64 residual and refinement: density within 1e-9 of
+    FP64. graphs = 1: the whole refinement is one graph launch (nested conditional loops);
+    0: the host-driven sweeps."""
     p = W.config_small_laplace()
     ctx, ref = make(p, OK.BOX_DIRICHLET0, precision=K.MIXED)
+    ctx.set_option(K.OPT_CUDA_GRAPHS, graphs)
     phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=1e-10, max_iter=300, restart=100)
+    assert ctx.get_option(K.OPT_CUDA_GRAPHS) == graphs  # the graph form ran, no fallback
     rphi, _ = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), p.rhs, tol=1e-13)
     assert info["status"] == 0 and info["rel_residual"] <= 1e-10
     assert info["refinements"] >= 2
     assert rel(phi.cpu().numpy(), rphi) < 1e-9
+    # not converged within max_iter: the sweeps stop with the best iterate
+    _, info2 = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=1e-14, max_iter=3, restart=100)
+    assert info2["status"] == K.ERR_NOT_CONVERGED
 
 
 def test_interp_grid_and_box_solve_neumann():
@@ -316,3 +324,21 @@ def test_checkpoint_resume_bit_exact():
     b = st.read(T=False)
     assert torch.equal(a["eta"], b["eta"]) and torch.equal(a["density"], b["density"])
     assert a["scalars"][:9] == b["scalars"][:9]
+
+
+def test_contexts_of_different_sizes_coexist():
+    """A large context keeps working after a smaller one is created (kernel launch limits
+    are process-wide, so no context may lower them for another)."""
+    big = W.random_problem(71, N=256, n=250)
+    ctx_big, ref_big = make(big, OK.BOX_DIRICHLET0, precision=K.MIXED)
+    small = W.random_problem(72, N=32, n=24)
+    ctx_small, _ = make(small, OK.BOX_DIRICHLET0, precision=K.MIXED)
+    m = K.Mlp(hidden=32, max_rows=16)  # a narrow network after a wide one is used elsewhere
+    del m
+    dens = W.random_density(8, big.n)
+    vals, _, _ = ctx_big.apply(K.DOUBLE, dev(dens))
+    rv, _, _ = ref_big.apply(OK.LAYER_DOUBLE, dens)
+    assert rel(vals.cpu().numpy(), rv) < 1e-5  # float32 grid apply of the mixed context
+    phi, info = ctx_big.solve_bie(K.BIE_INTERIOR_DL, dev(big.rhs), tol=1e-10, max_iter=300)
+    assert info["status"] == 0
+    ctx_small.close()
