@@ -33,6 +33,31 @@ DT, SIGMA, J, TOL = 1e-3, 1e-3, 1.0, 1e-8
 L2_FLUSH_BYTES = 512 << 20
 
 
+def slowest_rank_seconds(total_s, dist_mod=None, device="cpu"):
+    """The timed region's length for the whole job: the maximum over the ranks (each rank
+    timed its own replica between two barriers)."""
+    if dist_mod is None:
+        return float(total_s)
+    import torch
+
+    t = torch.tensor([float(total_s)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, slowest_s):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / slowest_s
+
+
+def shard(count, rank, world):
+    """Instances of a batch owned by one rank (contiguous, sizes differ by at most one): the
+    instances are independent, so ranks share no data and need no collective."""
+    base, extra = divmod(count, world)
+    start = rank * base + min(rank, extra)
+    return list(range(start, start + base + (1 if rank < extra else 0)))
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -41,6 +66,8 @@ def parse():
     ap.add_argument("--impl", default="kfbi", choices=["kfbi", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (256 instances), warm-start and Stefan measurements")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (for short profiler runs): no e2e, applies, fp64 or cpu legs")
     return ap.parse_args()
@@ -177,6 +204,157 @@ def traffic_record(kernel_src):
     return rec
 
 
+def batched_leg(torch, K, flush, reps=3):
+    """256 uneven interior Dirichlet instances (N in {128, 256, 512}, n in [64, 512],
+    kappa in {0, 10, 100}), mixed precision, tol 1e-8: autotuned (untimed), then whole-batch
+    solves from zero (one graph launch each, L2 flushed before each) against the same
+    instances solved one after another with kfbi_solve_bie."""
+    import numpy as np
+
+    import workloads as W
+
+    probs = W.config_batched(256)
+    descs = [dict(N=p.N, box=p.box, kappa=p.kappa, boxbc=K.BOX_DIRICHLET0, max_nodes=p.n) for p in probs]
+    t0 = time.perf_counter()
+    b = K.Batch(descs, K.MIXED)
+    for c, p in zip(b.contexts, probs):
+        c.set_interface(torch.tensor(p.xy, dtype=torch.float64, device="cuda"))
+    rhs = [torch.tensor(p.rhs, dtype=torch.float64, device="cuda") for p in probs]
+    dens = [torch.zeros(p.n, dtype=torch.float64, device="cuda") for p in probs]
+    setup_s = time.perf_counter() - t0
+    tol, max_iter, restart = 1e-8, 1000, 100
+    t0 = time.perf_counter()
+    tuned_ms = b.autotune(K.BIE_INTERIOR_DL, rhs, tol=tol, max_iter=max_iter, restart=restart)
+    tune_s = time.perf_counter() - t0
+    choice = {}
+    for c in b.contexts:
+        choice.setdefault(c.N, (c.get_option(K.OPT_CLUSTER_GMRES), c.get_option(K.OPT_CLUSTER_SIZE),
+                                c.get_option(K.OPT_COL_PAIRS)))
+    b.solve(K.BIE_INTERIOR_DL, rhs, dens, tol=tol, max_iter=max_iter, restart=restart)  # graph build
+    ms = []
+    infos = None
+    for _ in range(reps):
+        for d in dens:
+            d.zero_()
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, infos = b.solve(K.BIE_INTERIOR_DL, rhs, dens, tol=tol, max_iter=max_iter, restart=restart)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    # the same instances one at a time (each a graph launch and a synchronisation)
+    for d in dens:
+        d.zero_()
+    flush.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, r, d in zip(b.contexts, rhs, dens):
+        c.solve_bie(K.BIE_INTERIOR_DL, r, density=d, tol=tol, max_iter=max_iter, restart=restart)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    its = [i["iterations"] for i in infos]
+    out = dict(workload="batched_256_uneven_N128-512_n64-512_kappa0-10-100", instances=len(probs),
+               precision="mixed (f32 grid applies, f64 GMRES/refinement)", tol=tol,
+               instances_per_s=len(probs) / (float(np.median(ms)) / 1e3), ms_per_batch=float(np.median(ms)),
+               sequential_instances_per_s=len(probs) / seq_s,
+               converged=int(sum(1 for i in infos if i["status"] == 0)),
+               mean_iterations=float(np.mean(its)), max_iterations=int(max(its)),
+               max_rel_residual=float(max(i["rel_residual"] for i in infos)),
+               autotune=dict(seconds=tune_s, best_ms=tuned_ms,
+                             choice={str(k): dict(cluster=v[0], cluster_size=v[1], col_pairs=v[2])
+                                     for k, v in sorted(choice.items())}),
+               setup_s=setup_s, l2="flushed before every timed batch")
+    b.close()
+    return out
+
+
+def warmstart_leg(torch, K):
+    """The learned warm start: trained on 80 interior Laplace problems solved by the GPU
+    method (FP64, 256^2 grid), evaluated on 12 others: initial residual and GMRES iterations
+    from the network's density against the zero start."""
+    import numpy as np
+
+    import workloads as W
+
+    ctx = K.Context(256, (-1.0, 1.0, -1.0, 1.0), 0.0, K.BOX_DIRICHLET0, K.FP64, max_nodes=512)
+    feats, targets = [], []
+    t0 = time.perf_counter()
+    for s in range(1000, 1080):
+        p = W.warmstart_problem(s)
+        ctx.set_interface(torch.tensor(p.xy, dtype=torch.float64, device="cuda"))
+        r = torch.tensor(p.rhs, dtype=torch.float64, device="cuda")
+        phi, _ = ctx.solve_bie(K.BIE_INTERIOR_DL, r, tol=1e-12, max_iter=400, restart=100)
+        f, scale = ctx.warmstart_features(r)
+        feats.append(f.clone())
+        targets.append((phi / scale).to(torch.float32))
+    X, T = torch.cat(feats), torch.cat(targets)
+    data_s = time.perf_counter() - t0
+    m = K.Mlp(hidden=256, max_rows=max(X.shape[0], 512))
+    m.set_params(W.mlp_init(21))
+    g = torch.Generator(device="cpu").manual_seed(0)
+    first, _ = m.gradients(X, T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    steps = 2500
+    for it in range(steps):
+        idx = torch.randint(0, X.shape[0], (512,), generator=g, dtype=torch.int32).cuda()
+        m.train_step(X, T, idx=idx, lr=1e-3 if it < 1500 else 3e-4, want_loss=False)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    last, _ = m.gradients(X, T)
+    its0, its1, r1 = [], [], []
+    for s in range(5000, 5012):
+        p = W.warmstart_problem(s)
+        ctx.set_interface(torch.tensor(p.xy, dtype=torch.float64, device="cuda"))
+        r = torch.tensor(p.rhs, dtype=torch.float64, device="cuda")
+        guess = ctx.warmstart_predict(m, r)
+        res = r - ctx.bie_apply(K.BIE_INTERIOR_DL, guess)
+        r1.append(float(torch.linalg.norm(res) / torch.linalg.norm(r)))
+        _, i0 = ctx.solve_bie(K.BIE_INTERIOR_DL, r, tol=1e-10, max_iter=400, restart=100)
+        _, i1 = ctx.solve_bie(K.BIE_INTERIOR_DL, r, density=guess, tol=1e-10, max_iter=400, restart=100)
+        its0.append(i0["iterations"])
+        its1.append(i1["iterations"])
+    ctx.close()
+    return dict(training_rows=int(X.shape[0]), data_s=data_s, train_steps=steps, train_s=train_s,
+                loss_first=first, loss_last=last, held_out=12,
+                median_initial_residual=dict(zero=1.0, network=float(np.median(r1))),
+                mean_gmres_iterations=dict(zero=float(np.mean(its0)), network=float(np.mean(its1))))
+
+
+def stefan_leg(torch, K, steps=3, n=2048):
+    """Stefan dendrite steps on the 2048^2 Neumann grid (seed r = 0.1 (1 + 0.2 cos 4a),
+    undercooling -0.5, 4-fold anisotropy, dt = 5e-4), mixed precision to 1e-9."""
+    import numpy as np
+
+    import workloads as W
+
+    p = W.config_stefan(N=2048, n=n)
+    x = p.extra
+    ctx = K.Context(p.N, p.box, p.kappa, K.BOX_NEUMANN0, K.MIXED, max_nodes=p.n)
+    eta = torch.tensor(p.theta - alpha_array(p.n), dtype=torch.float64, device="cuda")
+    st = K.ThetaL(ctx, eta, p.L, p.xy.mean(0), K.STEP_STEFAN, tol=1e-9, max_iter=3000, restart=150,
+                  St=x["St"], eps_c=x["eps_c"], eps_aniso=x["eps_aniso"], eps_v=x["eps_v"], fold=x["fold"])
+    st.step(x["dt"])
+    torch.cuda.synchronize()
+    ms, infos = [], []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos.append(st.step(x["dt"]))
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    st.close()
+    ctx.close()
+    return dict(workload=f"stefan_2048x2048_n{n}", steps=steps, ms_per_step=float(np.mean(ms)),
+                steps_per_s=1e3 / float(np.mean(ms)),
+                mean_gmres_iterations=float(np.mean([i["iterations"] for i in infos])),
+                max_rel_residual=float(max(i["rel_residual"] for i in infos)),
+                statuses=[i["status"] for i in infos])
+
+
 def cpu_baseline(iters_per_solve, budget_s=25.0):
     """The oracle as it stands on the host cores: a bounded sample of the same workload."""
     import numpy as np
@@ -297,11 +475,7 @@ def main():
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
     launches = ctx.launch_count() - launches0
-    total_s = sum(ms) / 1e3
-    if pg:
-        tt = torch.tensor([total_s], device="cuda")
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        total_s = float(tt.item())
+    total_s = slowest_rank_seconds(sum(ms) / 1e3, pg, "cuda")
     # kernel timing pass: the same steps again from the same state with per-launch CUDA events
     # around the column kernel (event timing runs the solver's stream-launched form; the
     # kernels are the same as in the graph form timed above)
@@ -311,7 +485,7 @@ def main():
     tim = ctx.timing()
     ctx.timing(False)
     iters = [i["iterations"] for i in infos]
-    value = world * args.steps / total_s
+    value = job_throughput(args.steps, world, total_s)
     print(f"[bench] mixed: {1e3 * total_s / args.steps:.3f} ms/step, GMRES its {np.mean(iters):.1f}, "
           f"col kernel {tim}", file=sys.stderr)
     if args.profile:
@@ -398,6 +572,17 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(float(np.mean(iters)))
 
+    # ---- further workloads (reported beside the headline, never part of it)
+    extras = {}
+    if rank == 0 and not args.profile and not args.no_extras:
+        for name, leg in (("batched", lambda: batched_leg(torch, K, flush)), ("warm_start", lambda: warmstart_leg(torch, K)),
+                          ("stefan", lambda: stefan_leg(torch, K))):
+            try:
+                extras[name] = leg()
+            except Exception as exc:  # noqa: BLE001 - a failing extra must not lose the headline
+                extras[name] = dict(error=f"{type(exc).__name__}: {exc}")
+            print(f"[bench] {name}: {extras[name]}", file=sys.stderr)
+
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="solves/s", n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=1e3 * total_s / args.steps, higher_is_better=True,
@@ -412,7 +597,7 @@ def main():
                                max_rel_residual=float(max(i["rel_residual"] for i in infos)),
                                refinements=float(np.mean([i["refinements"] for i in infos]))),
                     wall_s=t_wall, roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
-                    clocks=clocks)
+                    clocks=clocks, **extras)
         print(json.dumps(line))
     st.close()
     ctx.close()
