@@ -374,36 +374,53 @@ __device__ V2<T>* fft_stockham(V2<T>* a, V2<T>* b, int P, int N, int logN, const
 // position of sample j in the Makhoul reordering v[n] = x[2n], v[N-1-n] = x[2n+1]
 __device__ __forceinline__ int mk_pos(int j, int N) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
 
+// pi / (2N) in float32, the argument unit of tsin
+__device__ __forceinline__ float qscale(int N) { return 1.57079632679489662f / (float)N; }
+
+// number of staged twiddles of fft_stockham for N = 2^logN (at most N)
+__host__ __device__ inline int staged_count(int N, int logN) {
+  int c = 0;
+  for (int Ns = (logN & 1) ? 2 : 1; Ns < N; Ns <<= 2) c += 3 * Ns;
+  return c;
+}
+
+// copies the staged twiddles to shared memory (before the block's first __syncthreads)
+template <typename T>
+__device__ __forceinline__ void stage_twiddles(const V2<T>* tw, V2<T>* sTw, int cnt) {
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) sTw[t] = tw[t];
+}
+
 // DCT-II from the FFT of the reordered pair (sequence a in .x, b in .y), at m and N - m:
 // V_a[m] = (Z[m] + conj Z[N-m]) / 2, V_b[m] = (Z[m] - conj Z[N-m]) / (2i),
 // X'[m] = Re(e^{-i pi m / (2N)} V[m]); V[N-m] = conj V[m] for each real sequence.
 // For DST-II the caller stored (-1)^j x_j and mode l is DCT index N-1-l.
+// (c, s) = (cos, sin)(pi m / (2N)); the rotation at N - m is (sin, cos) of the same angle.
 template <typename T>
-__device__ __forceinline__ void dct_post(const V2<T>* z, int N, int m, const T* tab, V2<T>& Xm, V2<T>& XNm) {
-  const int mask = 4 * N - 1;
+__device__ __forceinline__ void dct_post(const V2<T>* z, int N, int m, T c, T s, V2<T>& Xm, V2<T>& XNm) {
   V2<T> Z = z[m];
   V2<T> Zr = z[(N - m) & (N - 1)];
   V2<T> Va{(T)0.5 * (Z.x + Zr.x), (T)0.5 * (Z.y - Zr.y)};
   V2<T> Vb{(T)0.5 * (Z.y + Zr.y), (T)-0.5 * (Z.x - Zr.x)};
-  T c = tab[(m + N) & mask], s = tab[m & mask];
   Xm = V2<T>{c * Va.x + s * Va.y, c * Vb.x + s * Vb.y};
-  T c2 = tab[((N - m) + N) & mask], s2 = tab[(N - m) & mask];
-  XNm = V2<T>{c2 * Va.x - s2 * Va.y, c2 * Vb.x - s2 * Vb.y};
+  XNm = V2<T>{s * Va.x - c * Va.y, s * Vb.x - c * Vb.y};
 }
 
 // inverse of dct_post: V[m] = e^{i pi m/(2N)} (G[m] - i G[N-m]) per sequence, packed a + i b
 template <typename T>
-__device__ __forceinline__ void dct_pre(int N, int m, const T* tab, V2<T> Gm, V2<T> GNm, V2<T>& Zm, V2<T>& ZNm) {
-  const int mask = 4 * N - 1;
-  T c = tab[(m + N) & mask], s = tab[m & mask];
+__device__ __forceinline__ void dct_pre(int N, int m, T c, T s, V2<T> Gm, V2<T> GNm, V2<T>& Zm, V2<T>& ZNm) {
   V2<T> Va{c * Gm.x + s * GNm.x, s * Gm.x - c * GNm.x};
   V2<T> Vb{c * Gm.y + s * GNm.y, s * Gm.y - c * GNm.y};
   Zm = V2<T>{Va.x - Vb.y, Va.y + Vb.x};
-  int mm = N - m;
-  T c2 = tab[(mm + N) & mask], s2 = tab[mm & mask];
-  V2<T> Wa{c2 * GNm.x + s2 * Gm.x, s2 * GNm.x - c2 * Gm.x};
-  V2<T> Wb{c2 * GNm.y + s2 * Gm.y, s2 * GNm.y - c2 * Gm.y};
+  V2<T> Wa{s * GNm.x + c * Gm.x, c * GNm.x - s * Gm.x};
+  V2<T> Wb{s * GNm.y + c * Gm.y, c * GNm.y - s * Gm.y};
   ZNm = V2<T>{Wa.x - Wb.y, Wa.y + Wb.x};
+}
+
+// (cos, sin)(pi m / (2N)) from the sine table (float64) or the SFU (float32)
+template <typename T>
+__device__ __forceinline__ void dct_cs(const T* tab, int N, int m, T& c, T& s) {
+  c = tsin(tab, m + N, N, qscale(N));
+  s = tsin(tab, m, N, qscale(N));
 }
 
 // --------------------------------------------------------------------------- face rows
@@ -418,6 +435,8 @@ __global__ void k_face_dst(int N, int logN, int dct, const V2<T>* tw, const T* t
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
   V2<T>* B = A + N;
+  V2<T>* sTw = B + N;  // staged twiddles (one global round trip instead of one per stage)
+  stage_twiddles(tw, sTw, staged_count(N, logN));
   const T* gs = boxg + 2 * N;
   const T* gn = boxg + 3 * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -426,10 +445,12 @@ __global__ void k_face_dst(int N, int logN, int dct, const V2<T>* tw, const T* t
     A[mk_pos(i, N)] = V2<T>{a, b};
   }
   __syncthreads();
-  V2<T>* X = fft_stockham<T>(A, B, 1, N, logN, tw, false);
+  V2<T>* X = fft_stockham<T>(A, B, 1, N, logN, sTw, false);
   for (int m = threadIdx.x; m <= N / 2; m += blockDim.x) {
     V2<T> Xm, XNm;
-    dct_post<T>(X, N, m, tab, Xm, XNm);
+    T cm, sm;
+    dct_cs<T>(tab, N, m, cm, sm);
+    dct_post<T>(X, N, m, cm, sm, Xm, XNm);
     int km = dct ? m : N - 1 - m;
     out[km] = Xm.x;
     out[N + km] = Xm.y;
@@ -538,45 +559,76 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
   V2<T>* B = A + (long)P * N;
+  V2<T>* sTw = B + (long)P * N;       // staged FFT twiddles
+  const int nst = staged_count(N, logN);
+  constexpr bool STAGE = sizeof(T) == 4;
+  V2<T>* sCs = sTw + nst;             // float32: (cos, sin)(pi m / 2N), m = 0..N/2
+  const T* sLam = STAGE ? (const T*)(sCs + N / 2 + 1) : lam;  // eigenvalues
   const int k0 = blockIdx.x * (2 * P);
-  const int W = 2 * P;
-  for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
-    int j = t / W, c = t - j * W;
-    T v = spec[(long)j * N + k0 + c];
-    if (!dct && (j & 1)) v = -v;
-    ((T*)&A[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] = v;
+  const int W = 2 * P, lw = __ffs(W) - 1;
+  // every global read of the block is issued here, before the first barrier: the column
+  // data through a register buffer (eight loads in flight per thread), the twiddles and
+  // the eigenvalues straight into shared memory
+  stage_twiddles(tw, sTw, nst);
+  if (STAGE) {
+    T* w = (T*)(sCs + N / 2 + 1);
+    for (int t = threadIdx.x; t < N; t += blockDim.x) w[t] = lam[t];
+    for (int m = threadIdx.x; m <= N / 2; m += blockDim.x) dct_cs<T>(tab, N, m, sCs[m].x, sCs[m].y);
+  }
+  const int tot = N * W;
+  for (int t0 = 0; t0 < tot; t0 += 8 * (int)blockDim.x) {
+    T buf[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * (int)blockDim.x + (int)threadIdx.x;
+      if (t < tot) buf[u] = spec[(long)(t >> lw) * N + k0 + (t & (W - 1))];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * (int)blockDim.x + (int)threadIdx.x;
+      if (t < tot) {
+        const int j = t >> lw, c = t & (W - 1);
+        T v = buf[u];
+        if (!dct && (j & 1)) v = -v;
+        ((T*)&A[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] = v;
+      }
+    }
   }
   __syncthreads();
-  V2<T>* X = fft_stockham<T>(A, B, P, N, logN, tw, false);
+  V2<T>* X = fft_stockham<T>(A, B, P, N, logN, sTw, false);
   V2<T>* Y = X == A ? B : A;
   const int half = N >> 1;
   const T kap = kappa;
-  for (int t = threadIdx.x; t < P * (half + 1); t += blockDim.x) {
-    int p = t / (half + 1), m = t - p * (half + 1);
+  for (int p = 0; p < P; ++p) {
     const V2<T>* x = X + (long)p * N;
     V2<T>* y = Y + (long)p * N;
-    V2<T> Xm, XNm;
-    dct_post<T>(x, N, m, tab, Xm, XNm);
-    T lx0 = lam[k0 + 2 * p] - kap, lx1 = lam[k0 + 2 * p + 1] - kap;
-    T ly = lam[dct ? m : N - 1 - m];
-    V2<T> Gm{Xm.x / (ly + lx0), Xm.y / (ly + lx1)};
-    V2<T> GNm{0, 0};
-    if (m == half) {
-      GNm = Gm;
-    } else if (m > 0) {
-      T ly2 = lam[dct ? N - m : m - 1];
-      GNm = V2<T>{XNm.x / (ly2 + lx0), XNm.y / (ly2 + lx1)};
+    const T lx0 = sLam[k0 + 2 * p] - kap, lx1 = sLam[k0 + 2 * p + 1] - kap;
+    for (int m = threadIdx.x; m <= half; m += blockDim.x) {
+      V2<T> cs;
+      if (STAGE) cs = sCs[m];
+      else dct_cs<T>(tab, N, m, cs.x, cs.y);
+      V2<T> Xm, XNm;
+      dct_post<T>(x, N, m, cs.x, cs.y, Xm, XNm);
+      const T ly = sLam[dct ? m : N - 1 - m];
+      V2<T> Gm{fdiv_t(Xm.x, ly + lx0), fdiv_t(Xm.y, ly + lx1)};
+      V2<T> GNm{0, 0};
+      if (m == half) {
+        GNm = Gm;
+      } else if (m > 0) {
+        const T ly2 = sLam[dct ? N - m : m - 1];
+        GNm = V2<T>{fdiv_t(XNm.x, ly2 + lx0), fdiv_t(XNm.y, ly2 + lx1)};
+      }
+      V2<T> Zm, ZNm;
+      dct_pre<T>(N, m, cs.x, cs.y, Gm, GNm, Zm, ZNm);
+      y[m] = Zm;
+      if (m > 0 && m < half) y[N - m] = ZNm;
     }
-    V2<T> Zm, ZNm;
-    dct_pre<T>(N, m, tab, Gm, GNm, Zm, ZNm);
-    y[m] = Zm;
-    if (m > 0 && m < half) y[N - m] = ZNm;
   }
   __syncthreads();
-  V2<T>* Z = fft_stockham<T>(Y, X, P, N, logN, tw, true);
+  V2<T>* Z = fft_stockham<T>(Y, X, P, N, logN, sTw, true);
   const T invN = (T)1 / (T)N;
-  for (int t = threadIdx.x; t < N * W; t += blockDim.x) {
-    int j = t / W, c = t - j * W;
+  for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int j = t >> lw, c = t & (W - 1);
     T v = ((const T*)&Z[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] * invN;
     if (!dct && (j & 1)) v = -v;
     spec[(long)j * N + k0 + c] = v;
@@ -641,7 +693,9 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
     V2<T>* X = fft_stockham<T>(A, B, 1, N, logN, tw, false);
     for (int m = threadIdx.x; m <= half; m += blockDim.x) {
       V2<T> Xm, XNm;
-      dct_post<T>(X, N, m, tab, Xm, XNm);
+      T cm, sm;
+    dct_cs<T>(tab, N, m, cm, sm);
+    dct_post<T>(X, N, m, cm, sm, Xm, XNm);
       int km = dct ? m : N - 1 - m;
       spec[(long)j0 * N + km] = Xm.x;
       spec[(long)(j0 + 1) * N + km] = Xm.y;
@@ -663,7 +717,9 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
         GNm = V2<T>{spec[(long)j0 * N + kNm], spec[(long)(j0 + 1) * N + kNm]};
       }
       V2<T> Zm, ZNm;
-      dct_pre<T>(N, m, tab, Gm, GNm, Zm, ZNm);
+      T cm, sm;
+      dct_cs<T>(tab, N, m, cm, sm);
+      dct_pre<T>(N, m, cm, sm, Gm, GNm, Zm, ZNm);
       A[m] = Zm;
       if (m > 0 && m < half) A[N - m] = ZNm;
     }
@@ -744,12 +800,23 @@ __global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const
 }
 
 // --------------------------------------------------------------------------- host side
-// largest column-pair count whose double buffer fits the shared-memory budget
+// shared memory of k_col_solve: two P x N complex buffers, the staged twiddles (<= N) and, in
+// float32, the N/2 + 1 rotations of the DCT pre/post-processing and the N eigenvalues (float64
+// reads those two from global memory: it is bound by its float64 arithmetic, and N = 4096
+// would not fit)
+template <typename T>
+static size_t col_smem(int N, int P) {
+  size_t b = 2 * sizeof(V2<T>) * (size_t)P * N + sizeof(V2<T>) * (size_t)N;
+  if (sizeof(T) == 4) b += sizeof(V2<T>) * (size_t)(N / 2 + 1) + sizeof(T) * (size_t)N;
+  return b;
+}
+
+// largest column-pair count whose buffers fit the shared-memory budget
 constexpr size_t COL_SMEM_MAX = 200 * 1024;
 template <typename T>
 static int col_pairs_max(int N) {
   int P = 4;
-  while (P > 1 && (2 * P > N || 2 * sizeof(V2<T>) * (size_t)P * N > COL_SMEM_MAX)) P /= 2;
+  while (P > 1 && (2 * P > N || col_smem<T>(N, P) > COL_SMEM_MAX)) P /= 2;
   return P;
 }
 
@@ -773,7 +840,7 @@ template <typename T>
 static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
   const int N = c->N;
   const int P = col_pairs<T>(N, c->col_P);
-  size_t smem = 2 * sizeof(V2<T>) * (size_t)P * N;
+  size_t smem = col_smem<T>(N, P);
   const bool rec = c->timing && !c->capturing && c->timing_used < TIMING_CAP;
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
   KFBI_TRY(launch_k(c->use_pdl && !rec, k_col_solve<T>, dim3(N / (2 * P)), dim3(col_threads(N, P)), smem, c->stream, N,
@@ -847,7 +914,7 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     else
       k_box_data<T, T4, false><<<cdiv((long)4 * N * 32, 256), 256, 0, s2>>>(
           dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, bscale, boxg, skip);
-    size_t smf = 2 * sizeof(V2<T>) * (size_t)N;
+    size_t smf = 3 * sizeof(V2<T>) * (size_t)N;
     KFBI_TRY(launch_k(c->use_pdl, k_face_dst<T>, dim3(1), dim3(256), smf, s2, N, c->logN, dct, Tabs<T>::stw(c), tab,
                       (const T*)boxg, face, skip));
     KFBI_TRY(cudaEventRecord(c->ev_join, s2));
@@ -909,10 +976,10 @@ static kfbi_status setup_t(kfbi_ctx*) {
   int col = 0;
   for (int N = 16; N <= MAX_GRID_N; N *= 2) {
     const int P = sizeof(T) == 8 ? 1 : col_pairs_max<T>(N);
-    const int b = (int)(2 * sizeof(V2<T>) * (size_t)P * N);
+    const int b = (int)col_smem<T>(N, P);
     col = b > col ? b : col;
   }
-  const int row = (int)(2 * sizeof(V2<T>) * (size_t)MAX_GRID_N);
+  const int row = (int)(3 * sizeof(V2<T>) * (size_t)MAX_GRID_N);  // k_face_dst: A, B, twiddles
   using T4 = typename std::conditional<sizeof(T) == 8, double4_32a, float4>::type;
   using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(nullptr))>::type>::type;
   using S_t = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(nullptr))>::type>::type;
@@ -1051,7 +1118,7 @@ static kfbi_status grid_solve_noalloc_impl(int N, double h, double kappa, int bo
   size_t sm_row = 2 * sizeof(V2<double>) * N;  // <= 16 KB for N <= 512
   k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 0, (const V2<double>*)tw, tab, rhs, spec, nullptr);
   const int P = col_pairs<double>(N);
-  size_t sm_col = 2 * sizeof(V2<double>) * (size_t)P * N;  // <= 16 KB for N <= 512
+  size_t sm_col = col_smem<double>(N, P);  // <= 28 KB for N <= 512
   k_col_solve<double><<<N / (2 * P), col_threads(N, P), sm_col, s>>>(N, logN, P, dct, (const V2<double>*)tw, tab, lam,
                                                                   kappa, spec, flag);
   k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 1, (const V2<double>*)tw, tab, nullptr, spec, u);
