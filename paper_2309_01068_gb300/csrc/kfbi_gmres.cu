@@ -857,7 +857,7 @@ __global__ void k_ir_init(IrCtl* ir, double tol, int max_iter, int max_sweeps, i
 
 // r = b - y (y = A64 x), ||r|| / ||b||, the decision of the sweep, and for another sweep the
 // start of the inner float32 GMRES on A d = r from d = 0 (tolerance 0.5 tol / rel clamped to
-// [1e-5, 0.5]; the inner GMRES trusts its Givens estimate). One block.
+// [1e-7, 0.5]; the inner GMRES trusts its Givens estimate). One block.
 __global__ void k_ir_decide(IrCtl* ir, GmresCtl* g, const double* b, const double* y, double* r, double* V,
                             double* d, double* gin, float* gin_f, int n, int m, cudaGraphConditionalHandle h_inner) {
   __shared__ double sh[32];
@@ -890,7 +890,7 @@ __global__ void k_ir_decide(IrCtl* ir, GmresCtl* g, const double* b, const doubl
     } else {
       run = 1;
       double inner = 0.5 * ir->tol / rel;
-      inner = inner < 1e-5 ? 1e-5 : (inner > 0.5 ? 0.5 : inner);
+      inner = inner < 1e-7 ? 1e-7 : (inner > 0.5 ? 0.5 : inner);
       const double bn = sqrt(rr);
       g->phase = PH_ARNOLDI;
       g->next_phase = PH_ARNOLDI;
@@ -1411,7 +1411,7 @@ kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const dou
       if (rel <= tol) { st = KFBI_OK; break; }
       if (total_its >= max_iter || sweeps > max_sweeps) { st = KFBI_ERR_NOT_CONVERGED; break; }
       double inner = 0.5 * tol / rel;
-      if (inner < 1e-5) inner = 1e-5;
+      if (inner < 1e-7) inner = 1e-7;
       if (inner > 0.5) inner = 0.5;
       int its = 0, cyc = 0, ist = 0;
       double irel = 0.0;
