@@ -304,6 +304,19 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             (a kernel starts while its predecessor finishes and waits on the
  *                             device before it reads the predecessor's output). Batch graphs
  *                             are always built without it.
+ *   KFBI_OPT_BOX_MATRIX       1 (default): with KFBI_BOX_FREESPACE_DL, kfbi_set_interface
+ *                             tabulates the box quadrature's kernel between the interface
+ *                             nodes and the 4 N face points (4 N max_nodes values in float64
+ *                             and float32, allocated by kfbi_create when they take at most
+ *                             1 GiB), and every apply forms the box data as one product of
+ *                             that table with the density; 0: every apply evaluates the
+ *                             quadrature directly. Setting 1 on a context without the table
+ *                             returns CAPACITY; reading gives 1 only when the table is in use.
+ *   KFBI_OPT_FP32_ARNOLDI     1 (default): in KFBI_MIXED, the inner GMRES of the refinement
+ *                             (whose operator is the float32 apply) stores its basis and does
+ *                             its Gram-Schmidt passes, rotations and update in float32 when
+ *                             the cluster form runs; 0: in float64. The float64 refinement
+ *                             decides convergence either way.
  * kfbi_set_option: value 0 or 1 unless stated. kfbi_get_option writes the value to *value (host).
  * Errors: ARG (unknown option, bad value, NULL, read-only option).
  */
@@ -313,7 +326,9 @@ enum {
   KFBI_OPT_LAST_CLUSTER = 3,
   KFBI_OPT_PDL = 4,
   KFBI_OPT_CLUSTER_SIZE = 5,
-  KFBI_OPT_COL_PAIRS = 6
+  KFBI_OPT_COL_PAIRS = 6,
+  KFBI_OPT_BOX_MATRIX = 7,
+  KFBI_OPT_FP32_ARNOLDI = 8
 };
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);

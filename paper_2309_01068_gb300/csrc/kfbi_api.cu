@@ -99,8 +99,8 @@ static void free_all(kfbi_ctx* c) {
                   c->seg_count, c->seg_off, c->cr_kind, c->cr_line, c->cr_seg, c->cr_first, c->cr_alpha, c->cr_xi,
                   c->tgeo, c->tgeo_f, c->stencil_f, c->dens_f, c->stw, c->stw_d, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->stencil,
                   c->probe_mark, c->prow_cnt, c->prow_ptr, c->probe_i, c->flags, c->counts, c->dcoef, c->dint,
-                  c->boxg, c->facespec, c->spec, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack,
-                  c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gpart, c->gw,
+                  c->boxg, c->facespec, c->spec, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack, c->boxK, c->boxK_f,
+                  c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gVf, c->gpart, c->gw,
                   c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag, c->irctl, c->ir_b, c->ir_x, c->ir_dn};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -158,6 +158,10 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->twn_f, 2 * (size_t)max_nodes));
   KFBI_CHECK(dalloc(&c->npack, 4 * (size_t)max_nodes));
   KFBI_CHECK(dalloc(&c->npack_f, 4 * (size_t)max_nodes));
+  if (boxbc == KFBI_BOX_FREESPACE_DL && (size_t)4 * N * max_nodes * 12 <= BOXK_MAX_BYTES) {
+    KFBI_CHECK(dalloc(&c->boxK, (size_t)4 * N * max_nodes));
+    KFBI_CHECK(dalloc(&c->boxK_f, (size_t)4 * N * max_nodes));
+  }
   KFBI_CHECK(dalloc(&c->prow_list, N + 1));
   KFBI_CHECK(dalloc(&c->facespec, 2 * (size_t)N));
   KFBI_CHECK(dalloc(&c->icoef, 4 * (size_t)nk));
@@ -193,6 +197,7 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->gctl, 1));
   KFBI_TRY(cudaMallocHost((void**)&c->host_gctl, sizeof(GmresCtl)));
   KFBI_CHECK(dalloc(&c->gV, (size_t)(MAX_RESTART + 1) * max_nodes));
+  if (precision == KFBI_MIXED) KFBI_CHECK(dalloc(&c->gVf, (size_t)(MAX_RESTART + 1) * max_nodes));
   KFBI_CHECK(dalloc(&c->gpart, ((size_t)max_nodes / 32 + MAX_RESTART + 2) * (MAX_RESTART + 1)));
   KFBI_CHECK(dalloc(&c->gw, max_nodes));
   KFBI_CHECK(dalloc(&c->gin, max_nodes));
@@ -445,7 +450,7 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
   if (option == KFBI_OPT_CLUSTER_SIZE) {
     if (value != 0 && value != 8 && value != 16) return KFBI_ERR_ARG;
     c->force_cs = value;
-    c->gmf = kfbi_ctx::GmfConfig{};
+    c->gmf = c->gmf32 = kfbi_ctx::GmfConfig{};
     c->cfg_version += 1;
     return KFBI_OK;
   }
@@ -456,11 +461,16 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
     return KFBI_OK;
   }
   if (value != 0 && value != 1) return KFBI_ERR_ARG;
-  if (option == KFBI_OPT_CUDA_GRAPHS) {
+  if (option == KFBI_OPT_BOX_MATRIX) {
+    if (value == 1 && c->boxK == nullptr) return KFBI_ERR_CAPACITY;
+    c->use_boxK = value != 0;
+  } else if (option == KFBI_OPT_FP32_ARNOLDI) {
+    c->arn32 = value != 0;
+  } else if (option == KFBI_OPT_CUDA_GRAPHS) {
     c->use_graphs = value != 0;
   } else if (option == KFBI_OPT_CLUSTER_GMRES) {
     c->gm_cluster = value != 0;
-    c->gmf = kfbi_ctx::GmfConfig{};
+    c->gmf = c->gmf32 = kfbi_ctx::GmfConfig{};
   } else if (option == KFBI_OPT_PDL) {
     c->use_pdl = value != 0;
   } else {
@@ -478,6 +488,8 @@ kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
   else if (option == KFBI_OPT_PDL) *value = c->use_pdl ? 1 : 0;
   else if (option == KFBI_OPT_CLUSTER_SIZE) *value = c->force_cs;
   else if (option == KFBI_OPT_COL_PAIRS) *value = c->col_P;
+  else if (option == KFBI_OPT_BOX_MATRIX) *value = (c->boxK != nullptr && c->use_boxK) ? 1 : 0;
+  else if (option == KFBI_OPT_FP32_ARNOLDI) *value = c->arn32 ? 1 : 0;
   else return KFBI_ERR_ARG;
   return KFBI_OK;
 }

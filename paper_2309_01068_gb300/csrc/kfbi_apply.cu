@@ -312,6 +312,53 @@ __global__ void k_box_data(const T* phi, int n, const T4* npack, int N, double x
   if (lane == 0) boxg[w] = scale * acc;
 }
 
+// Free-space box data as a product with a kernel fixed by the interface: for face point w
+// (west, east, south, north faces, N each) and node l,
+//   K[w][l] = -2 / (h^2 n) ((X_l - p_w).(y_a, -x_a)_l) / |X_l - p_w|^2
+// (the trapezoidal double layer of Sec. 4.1 at p_w, pre-scaled as the right-hand side term
+// -2 g / h^2), so that boxg = K phi. Computed once per interface in float64 with a float32
+// copy; every apply then reads it (4N n values) instead of re-evaluating it.
+__global__ void k_box_matrix(int N, int n, const double4_32a* npack, double xmin, double xmax, double ymin,
+                             double ymax, double h, double scale, double* K, float* Kf) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)4 * N * n) return;
+  const int w = (int)(t / n), l = (int)(t - (long)w * n);
+  const int face = w / N, idx = w - face * N;
+  double px, py;
+  if (face == 0) { px = xmin; py = grid_coord(ymin, h, idx); }
+  else if (face == 1) { px = xmax; py = grid_coord(ymin, h, idx); }
+  else if (face == 2) { px = grid_coord(xmin, h, idx); py = ymin; }
+  else { px = grid_coord(xmin, h, idx); py = ymax; }
+  const double4_32a q = npack[l];
+  const double dx = q.x - px, dy = q.y - py;
+  const double k = scale * (dx * q.z + dy * q.w) / (dx * dx + dy * dy);
+  K[t] = k;
+  Kf[t] = (float)k;
+}
+
+// boxg[w] = sum_l K[w][l] phi_l: one warp per face point, coalesced rows, four accumulators
+template <typename T>
+__global__ void k_box_gemv(const T* K, const T* phi, int n, int rows, T* boxg, const int* skip) {
+  pdl_wait();
+  pdl_trigger();
+  if (*skip) return;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  const T* row = K + (long)w * n;
+  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  int l = lane;
+  for (; l + 96 < n; l += 128) {
+    a0 += row[l] * phi[l];
+    a1 += row[l + 32] * phi[l + 32];
+    a2 += row[l + 64] * phi[l + 64];
+    a3 += row[l + 96] * phi[l + 96];
+  }
+  for (; l < n; l += 32) a0 += row[l] * phi[l];
+  T a = wsum((a0 + a1) + (a2 + a3));
+  if (lane == 0) boxg[w] = a;
+}
+
 // --------------------------------------------------------------------------- FFT core
 // Stockham autosort FFT of P length-N sequences in shared memory (natural order in and
 // out): one radix-2 stage when log2 N is odd, then radix-4 stages. Stage with span Ns and
@@ -908,7 +955,10 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     KFBI_TRY(cudaStreamWaitEvent(s2, c->ev_fork, 0));
     const size_t smb = (size_t)n * sizeof(T4);
     const T bscale = (T)(-2.0 / (c->h * c->h * (double)n));
-    if (smb <= SMEM_STAGE_MAX)
+    if (c->boxK_ok && c->use_boxK)
+      k_box_gemv<T><<<cdiv((long)4 * N * 32, 256), 256, 0, s2>>>(
+          sizeof(T) == 8 ? (const T*)c->boxK : (const T*)c->boxK_f, dens_t, n, 4 * N, boxg, skip);
+    else if (smb <= SMEM_STAGE_MAX)
       k_box_data<T, T4, true><<<cdiv((long)4 * N * 32, 256), 256, smb, s2>>>(
           dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, bscale, boxg, skip);
     else
@@ -1004,6 +1054,16 @@ kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* densi
   if (skip == nullptr) skip = c->zero_flag;
   if (fp32) return apply_t<float>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip, density_f);
   return apply_t<double>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip, nullptr);
+}
+
+kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n) {
+  const long tot = (long)4 * c->N * n;
+  launched(c, 1);
+  k_box_matrix<<<cdiv(tot, 256), 256, 0, c->stream>>>(c->N, n, (const double4_32a*)c->npack, c->xmin, c->xmax,
+                                                       c->ymin, c->ymax, c->h, -2.0 / (c->h * c->h * (double)n),
+                                                       c->boxK, c->boxK_f);
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
 }
 
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u) {

@@ -73,13 +73,13 @@ struct kfbi_batch {
   // what the cached graph was built for
   struct Key {
     long version;
-    int cfg, m, cs, cap, n;
+    int cfg, m, cs, cap, n, f32;
     bool pdl;
     const double* rhs;
     double* x;
     bool operator==(const Key& o) const {
       return version == o.version && cfg == o.cfg && m == o.m && cs == o.cs && cap == o.cap && n == o.n &&
-             pdl == o.pdl && rhs == o.rhs && x == o.x;
+             f32 == o.f32 && pdl == o.pdl && rhs == o.rhs && x == o.x;
     }
   };
   std::vector<Key> keys;
@@ -102,7 +102,9 @@ static kfbi_batch::Key batch_key(kfbi_ctx* c, int restart, int max_iter, const d
   k.cfg = c->cfg_version;
   k.n = c->have_iface ? c->n : 0;
   k.m = k.n > 0 ? restart_length(restart, k.n) : 0;
-  k.cs = k.n > 0 ? gmf_select(c, k.n, k.m).cs : 0;
+  const kfbi_ctx::GmfConfig gf = k.n > 0 ? gmf_select(c, k.n, k.m, c->precision == KFBI_MIXED) : kfbi_ctx::GmfConfig{};
+  k.cs = gf.cs;
+  k.f32 = gf.f32;
   k.cap = k.m > 0 ? body_cap(max_iter, k.m) : 0;
   k.pdl = false;
   k.rhs = rhs;
@@ -126,7 +128,7 @@ static kfbi_status batch_build(kfbi_batch* b, int kind, const double* const* rhs
     keys.push_back(batch_key(c, restart, max_iter, rhs[i], x[i]));
     if (!c->have_iface || c->n < 1) continue;
     const kfbi_batch::Key& k = keys.back();
-    const kfbi_ctx::GmfConfig gf = gmf_select(c, k.n, k.m);
+    const kfbi_ctx::GmfConfig gf = gmf_select(c, k.n, k.m, mixed);
     c->gm_m = k.m;
     c->gmf_last_cs = gf.cs;
     cudaStream_t saved = c->stream;

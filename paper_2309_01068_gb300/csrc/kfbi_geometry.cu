@@ -690,6 +690,11 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   if (c->host_counts[1] & FLAG_UNDERRES) return KFBI_ERR_UNDERRESOLVED;
   c->n_probe = c->host_counts[0];
   c->n_prow = c->host_counts[2];
+  c->boxK_ok = false;
+  if (c->boxK != nullptr) {
+    KFBI_CHECK(box_matrix_enqueue(c, n));
+    c->boxK_ok = true;
+  }
   c->n = n;
   c->have_iface = true;
   c->iface_version += 1;

@@ -80,8 +80,8 @@ __global__ void k_gm_init(GmresCtl* ctl, double tol, int max_iter, int m, int tr
 
 // ||b||; with a zero initial guess the first Arnoldi vector is b / ||b|| (r = b needs no
 // apply), otherwise gin = x and the first body evaluates A x for the initial residual
-__global__ void k_gm_start(const double* b, double* x, double* gin, float* gin_f, double* V, int n, GmresCtl* ctl,
-                           int zero_guess) {
+__global__ void k_gm_start(const double* b, double* x, double* gin, float* gin_f, double* V, float* Vf, int n,
+                           GmresCtl* ctl, int zero_guess) {
   __shared__ double sh[32];
   __shared__ double bn;
   double s = 0.0;
@@ -111,6 +111,7 @@ __global__ void k_gm_start(const double* b, double* x, double* gin, float* gin_f
       x[i] = 0.0;
       g = b[i] / bn;
       V[i] = g;
+      if (Vf) Vf[i] = (float)g;
     } else {
       g = x[i];
     }
@@ -409,17 +410,27 @@ __device__ __forceinline__ double cl_load(const double* p, unsigned rank) {
   asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(r) : "memory");
   return v;
 }
+__device__ __forceinline__ float cl_load(const float* p, unsigned rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(r) : "memory");
+  return v;
+}
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 
 // out[0..L) = sum over the cluster's CTAs (rank order) of part[0..L) in each CTA. Thread t
 // loads entry t / cs of CTA t % cs; a half-warp (cs = 16) or an 8-lane group (cs = 8) sums
 // its loads by a fixed shuffle tree.
-__device__ __forceinline__ void cl_reduce(const double* part, double* out, int L, unsigned cs) {
+template <typename T>
+__device__ __forceinline__ void cl_reduce(const T* part, T* out, int L, unsigned cs) {
   cl_sync();
   const int per = GMF_THREADS / (int)cs;
   for (int base = 0; base < L; base += per) {
     const int idx = base + (int)(threadIdx.x / cs);
     const unsigned c = threadIdx.x % cs;
-    double v = idx < L ? cl_load(part + idx, c) : 0.0;
+    T v = idx < L ? cl_load(part + idx, c) : (T)0;
     for (unsigned o = cs >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (c == 0 && idx < L) out[idx] = v;
   }
@@ -427,12 +438,13 @@ __device__ __forceinline__ void cl_reduce(const double* part, double* out, int L
 }
 
 // sum of v over the CTA by shuffle trees; the result is returned in every thread
-__device__ __forceinline__ double cta_sum(double v, double* sh) {
+template <typename T>
+__device__ __forceinline__ T cta_sum(T v, T* sh) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) sh[wid] = v;
   __syncthreads();
-  double t = lane < GMF_THREADS / 32 ? sh[lane] : 0.0;
+  T t = lane < GMF_THREADS / 32 ? sh[lane] : (T)0;
   for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
   __syncthreads();
   return t;
@@ -448,17 +460,17 @@ __device__ __forceinline__ int lanes_pow2(int x) {
 // p[k] = sum_i sV[k][i] w[i] for k < K over this CTA's rows, and p[K] = sum_i w[i]^2 when
 // with_norm. G adjacent lanes share one k: lane g sums i = g, g + G, ... with four
 // accumulators, then a shuffle tree over the G lanes.
-__device__ __forceinline__ void cta_dots(const double* sV, int Rp, const double* w, int len, int K, bool with_norm,
-                                         double* p) {
+template <typename T>
+__device__ __forceinline__ void cta_dots(const T* sV, int Rp, const T* w, int len, int K, bool with_norm, T* p) {
   const int Kt = K + (with_norm ? 1 : 0);
   const int G = lanes_pow2(GMF_THREADS / Kt);
   const int total = Kt * G;
   for (int base = 0; base < total; base += GMF_THREADS) {
     const int t = base + (int)threadIdx.x;
     const int k = t / G, g = t % G;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     if (t < total) {
-      const double* row = k < K ? sV + k * Rp : w;
+      const T* row = k < K ? sV + k * Rp : w;
       int i = g;
       for (; i + 3 * G < len; i += 4 * G) {
         a0 += row[i] * w[i];
@@ -468,7 +480,7 @@ __device__ __forceinline__ void cta_dots(const double* sV, int Rp, const double*
       }
       for (; i < len; i += G) a0 += row[i] * w[i];
     }
-    double v = (a0 + a1) + (a2 + a3);
+    T v = (a0 + a1) + (a2 + a3);
     for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (t < total && g == 0) p[k] = v;
   }
@@ -477,14 +489,14 @@ __device__ __forceinline__ void cta_dots(const double* sV, int Rp, const double*
 
 // w[i] += sign * sum_k sV[k][i] h[k] over this CTA's rows. G adjacent lanes share one i:
 // lane g sums k = g, g + G, ... with four accumulators, then a shuffle tree.
-__device__ __forceinline__ void cta_combine(const double* sV, int Rp, const double* h, int K, int len, double* w,
-                                            double sign) {
+template <typename T>
+__device__ __forceinline__ void cta_combine(const T* sV, int Rp, const T* h, int K, int len, T* w, T sign) {
   const int G = lanes_pow2(GMF_THREADS / (len > 0 ? len : 1));
   const int total = len * G;
   for (int base = 0; base < total; base += GMF_THREADS) {
     const int t = base + (int)threadIdx.x;
     const int i = t / G, g = t % G;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     if (t < total) {
       int k = g;
       for (; k + 3 * G < K; k += 4 * G) {
@@ -495,7 +507,7 @@ __device__ __forceinline__ void cta_combine(const double* sV, int Rp, const doub
       }
       for (; k < K; k += G) a0 += sV[k * Rp + i] * h[k];
     }
-    double v = (a0 + a1) + (a2 + a3);
+    T v = (a0 + a1) + (a2 + a3);
     for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (t < total && g == 0) w[i] = fma(sign, v, w[i]);
   }
@@ -510,48 +522,49 @@ __device__ __forceinline__ void cta_combine(const double* sV, int Rp, const doub
 // lanes' maps, and each lane replays its rotations from its starting x. On return hc[0..j-1]
 // hold out_i and hc[j] holds x_j. Warp 0 only; j <= 32 * GIV_CHUNK.
 constexpr int GIV_CHUNK = (MAX_RESTART + 31) / 32;
-__device__ __forceinline__ void givens_scan(double* hc, const double* cs_, const double* sn_, int j) {
+template <typename T>
+__device__ __forceinline__ void givens_scan(T* hc, const T* cs_, const T* sn_, int j) {
   const int lane = threadIdx.x & 31;
   const int C = (j + 31) / 32;
   const int i0 = lane * C;
-  double c[GIV_CHUNK], s[GIV_CHUNK], h[GIV_CHUNK];
-  double A = 1.0, B = 0.0;
+  T c[GIV_CHUNK], s[GIV_CHUNK], h[GIV_CHUNK];
+  T A = 1, B = 0;
 #pragma unroll
   for (int u = 0; u < GIV_CHUNK; ++u) {
     const int i = i0 + u;
     const bool ok = u < C && i < j;
-    c[u] = ok ? cs_[i] : 1.0;
-    s[u] = ok ? sn_[i] : 0.0;
-    h[u] = ok ? hc[i + 1] : 0.0;
+    c[u] = ok ? cs_[i] : (T)1;
+    s[u] = ok ? sn_[i] : (T)0;
+    h[u] = ok ? hc[i + 1] : (T)0;
   }
-  const double x0 = hc[0];
+  const T x0 = hc[0];
   __syncwarp();
 #pragma unroll
   for (int u = 0; u < GIV_CHUNK; ++u) {
     if (u < C && i0 + u < j) {
-      const double cb = c[u] * h[u];
+      const T cb = c[u] * h[u];
       B = fma(-s[u], B, cb);
       A = -s[u] * A;
     }
   }
   // inclusive scan of lane maps: (A, B) <- (A, B) o (A', B') of lane l - d
   for (int d = 1; d < 32; d <<= 1) {
-    const double Ap = __shfl_up_sync(0xffffffffu, A, d);
-    const double Bp = __shfl_up_sync(0xffffffffu, B, d);
+    const T Ap = __shfl_up_sync(0xffffffffu, A, d);
+    const T Bp = __shfl_up_sync(0xffffffffu, B, d);
     if (lane >= d) {
       B = fma(A, Bp, B);
       A = A * Ap;
     }
   }
   // exclusive prefix applied to x_0 gives this lane's starting x
-  double Ae = __shfl_up_sync(0xffffffffu, A, 1);
-  double Be = __shfl_up_sync(0xffffffffu, B, 1);
-  double x = lane == 0 ? x0 : fma(Ae, x0, Be);
+  T Ae = __shfl_up_sync(0xffffffffu, A, 1);
+  T Be = __shfl_up_sync(0xffffffffu, B, 1);
+  T x = lane == 0 ? x0 : fma(Ae, x0, Be);
 #pragma unroll
   for (int u = 0; u < GIV_CHUNK; ++u) {
     const int i = i0 + u;
     if (u < C && i < j) {
-      const double sh = s[u] * h[u], ch = c[u] * h[u];
+      const T sh = s[u] * h[u], ch = c[u] * h[u];
       hc[i] = fma(c[u], x, sh);
       x = fma(-s[u], x, ch);
       if (i == j - 1) hc[j] = x;
@@ -573,18 +586,24 @@ __device__ __forceinline__ void gmf_close(GmresCtl* ctl, unsigned rank, cudaGrap
   if (use_cond) cudaGraphSetConditional(hcond, done ? 0u : 1u);
 }
 
-// Dynamic shared memory: sV[(m+1) Rp] | sH[(m+1)(m+1)] (hsmem) | sw[Rp]
-__global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, double* V, int ldv, const double* w,
+// Dynamic shared memory: sV[(m+1) Rp] | sH[(m+1)(m+1)] (hsmem) | sw[Rp], elements of T.
+// T is the arithmetic of the Gram-Schmidt passes, the rotations and the update of x, and the
+// type of the stored basis V: double, or float for the inner solve of the mixed-precision
+// refinement (its operator is the float32 apply; the control block stays double).
+template <typename T>
+__global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V, int ldv, const double* w,
                                                             const double* b, double* x, double* gin, float* gin_f,
                                                             int n, int R, int hsmem, cudaGraphConditionalHandle hcond,
                                                             int use_cond, int cap) {
-  extern __shared__ double dsm[];
-  __shared__ double part[2][GMF_PART];
-  __shared__ double h1[GMF_PART], h2[GMF_PART], hcol[GMF_PART];
-  __shared__ double scs[MAX_RESTART], ssn[MAX_RESTART], gy[MAX_RESTART + 1];
-  __shared__ double red[GMF_THREADS / 32];
+  extern __shared__ __align__(16) unsigned char gmf_dyn[];
+  T* dsm = (T*)gmf_dyn;
+  __shared__ T part[2][GMF_PART];
+  __shared__ T h1[GMF_PART], h2[GMF_PART], hcol[GMF_PART];
+  __shared__ T scs[MAX_RESTART], ssn[MAX_RESTART], gy[MAX_RESTART + 1];
+  __shared__ T red[GMF_THREADS / 32];
   __shared__ int s_done, s_phase, s_j, s_m, s_its, s_maxit, s_trust, s_cycles, s_end;
-  __shared__ double s_tol, s_bnorm, s_gj, s_gj1, s_hn2, s_inv, s_rd;
+  __shared__ double s_tol, s_bnorm;
+  __shared__ T s_gj, s_gj1, s_hn2, s_inv, s_rd;
   const unsigned rank = cl_rank(), cs = cl_size();
   const int Rp = gmf_row_stride(R);
   const int i0 = (int)rank * R;
@@ -608,17 +627,17 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
     return;
   }
   const int m = s_m;
-  double* sV = dsm;
-  double* sH = sV + (size_t)(m + 1) * Rp;
-  double* sw = sH + (hsmem ? (size_t)(m + 1) * (m + 1) : 0);
-  const double tolb = s_tol * s_bnorm;
+  T* sV = dsm;
+  T* sH = sV + (size_t)(m + 1) * Rp;
+  T* sw = sH + (hsmem ? (size_t)(m + 1) * (m + 1) : 0);
+  const T tolb = (T)(s_tol * s_bnorm);
   int done = 0;
   if (s_phase == PH_RESID) {
     // r = b - A x, ||r||; restart from r / ||r|| unless converged or out of iterations
     pdl_wait();
-    double ss = 0.0;
+    T ss = 0;
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
-      double r = b[i0 + i] - w[i0 + i];
+      const T r = (T)(b[i0 + i] - w[i0 + i]);
       sw[i] = r;
       ss += r * r;
     }
@@ -627,13 +646,13 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
     cl_reduce(part[0], h1, 1, cs);
     cl_arrive();  // the last read of another CTA's shared memory is done
     if (threadIdx.x == 0) {
-      const double q = h1[0];
-      const double r = q > 0.0 ? rsqrt(q) : 0.0;
+      const T q = h1[0];
+      const T r = q > (T)0 ? rsqrt_t(q) : (T)0;
       s_gj = q * r;  // ||r||
       s_gj1 = r;     // 1 / ||r||
     }
     __syncthreads();
-    const double beta = s_gj;
+    const T beta = s_gj;
     int status = KFBI_OK;
     if (beta <= tolb) {
       done = 1;
@@ -641,9 +660,9 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
       done = 1;
       status = KFBI_ERR_NOT_CONVERGED;
     } else {
-      const double inv = s_gj1;
+      const T inv = s_gj1;
       for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
-        double v = sw[i] * inv;
+        const T v = sw[i] * inv;
         V[i0 + i] = v;
         gin[i0 + i] = v;
         gin_f[i0 + i] = (float)v;
@@ -673,7 +692,7 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
   {
     const int tot = K * len;
     for (int t0 = 0; t0 < tot; t0 += 8 * GMF_THREADS) {
-      double buf[8];
+      T buf[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int t = t0 + u * GMF_THREADS + (int)threadIdx.x;
@@ -693,32 +712,32 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
     }
   }
   for (int i = threadIdx.x; i < j; i += GMF_THREADS) {
-    scs[i] = ctl->cs[i];
-    ssn[i] = ctl->sn[i];
+    scs[i] = (T)ctl->cs[i];
+    ssn[i] = (T)ctl->sn[i];
   }
-  if (threadIdx.x == 0) s_gj = ctl->g[j];
+  if (threadIdx.x == 0) s_gj = (T)ctl->g[j];
   // everything above was complete before the apply started; w is the apply's output
   pdl_wait();
-  for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = w[i0 + i];
+  for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = (T)w[i0 + i];
   __syncthreads();
   // two passes of classical Gram-Schmidt; the second also reduces ||w'||^2 (entry K)
   cta_dots(sV, Rp, sw, len, K, false, part[0]);
   cl_reduce(part[0], h1, K, cs);
-  cta_combine(sV, Rp, h1, K, len, sw, -1.0);
+  cta_combine(sV, Rp, h1, K, len, sw, (T)-1);
   cta_dots(sV, Rp, sw, len, K, true, part[1]);
   cl_reduce(part[1], h2, K + 1, cs);
-  cta_combine(sV, Rp, h2, K, len, sw, -1.0);
+  cta_combine(sV, Rp, h2, K, len, sw, (T)-1);
   // concurrently: warp 0 forms ||w''||^2 = ||w'||^2 - ||h2||^2, warp 1 applies the previous
   // rotations to the Hessenberg column h1 + h2
   if (threadIdx.x < 32) {
-    double q0 = 0.0, q1 = 0.0;
+    T q0 = 0, q1 = 0;
     int k = threadIdx.x;
     for (; k + 32 < K; k += 64) {
       q0 += h2[k] * h2[k];
       q1 += h2[k + 32] * h2[k + 32];
     }
     if (k < K) q0 += h2[k] * h2[k];
-    const double q = warp_sum(q0 + q1);
+    const T q = warp_sum(q0 + q1);
     if (threadIdx.x == 0) s_hn2 = h2[K] - q;
   } else if (threadIdx.x < 64) {
     for (int k = threadIdx.x - 32; k < K; k += 32) hcol[k] = h1[k] + h2[k];
@@ -726,9 +745,9 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
     if (j > 0) givens_scan(hcol, scs, ssn, j);
   }
   __syncthreads();
-  if (!(s_hn2 > 0.5 * h2[K])) {
+  if (!(s_hn2 > (T)0.5 * h2[K])) {
     // cancellation (w nearly in the span of V): reduce ||w''||^2 explicitly
-    double ss = 0.0;
+    T ss = 0;
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) ss += sw[i] * sw[i];
     ss = cta_sum(ss, red);
     if (threadIdx.x == 0) part[0][0] = ss;
@@ -738,25 +757,25 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
   // the new rotation from (hcol[j], ||w''||), with reciprocal square roots only:
   //   hn = ||w''||, den = sqrt(hcol[j]^2 + hn^2), c = hcol[j] / den, s = hn / den
   if (threadIdx.x == 0) {
-    const double hn2 = s_hn2 > 0.0 ? s_hn2 : 0.0;
-    const double rh = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
-    const double hn = hn2 * rh;
-    const double a = hcol[j];
-    const double d2 = fma(a, a, hn2);
-    const double rd = d2 > 0.0 ? rsqrt(d2) : 0.0;
-    const double den = d2 * rd;
-    const int brk = hn2 == 0.0;
-    const double cj = d2 > 0.0 ? a * rd : 1.0, sj = hn * rd;
+    const T hn2 = s_hn2 > (T)0 ? s_hn2 : (T)0;
+    const T rh = hn2 > (T)0 ? rsqrt_t(hn2) : (T)0;
+    const T hn = hn2 * rh;
+    const T a = hcol[j];
+    const T d2 = fma(a, a, hn2);
+    const T rd = d2 > (T)0 ? rsqrt_t(d2) : (T)0;
+    const T den = d2 * rd;
+    const int brk = hn2 == (T)0;
+    const T cj = d2 > (T)0 ? a * rd : (T)1, sj = hn * rd;
     hcol[j] = den;
-    hcol[j + 1] = 0.0;
-    const double gj = s_gj;
+    hcol[j + 1] = 0;
+    const T gj = s_gj;
     gy[j] = cj * gj;
-    const double gj1 = -sj * gj;
+    const T gj1 = -sj * gj;
     s_gj1 = gj1;
     s_inv = rh;
     s_rd = rd;
     const int its = s_its + 1;
-    const double res = fabs(gj1);
+    const T res = fabs(gj1);
     s_end = (res <= tolb || its >= s_maxit || brk || j + 1 == m) ? 1 : 0;
     if (rank == 0) {
       double* Hc = ctl->H + (long)j * (m + 1);
@@ -774,9 +793,9 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
   }
   __syncthreads();
   if (!s_end) {
-    const double inv = s_inv;
+    const T inv = s_inv;
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
-      double v = sw[i] * inv;
+      const T v = sw[i] * inv;
       V[(long)(j + 1) * ldv + i0 + i] = v;
       gin[i0 + i] = v;
       gin_f[i0 + i] = (float)v;
@@ -789,29 +808,35 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
   } else {
     // end of the cycle: y = R^{-1} g by column-oriented back substitution (every CTA, with
     // the stored reciprocals of the diagonal), then x += V y over this CTA's rows
-    const double res = fabs(s_gj1);
+    const T res = fabs(s_gj1);
     for (int i = threadIdx.x; i < j; i += GMF_THREADS) {
-      gy[i] = ctl->g[i];
-      scs[i] = ctl->rinv[i];
+      gy[i] = (T)ctl->g[i];
+      scs[i] = (T)ctl->rinv[i];
     }
     if (threadIdx.x == 0) scs[j] = s_rd;
     if (hsmem)
-      for (int t = threadIdx.x; t < j * (m + 1); t += GMF_THREADS) sH[t] = ctl->H[t];
+      for (int t = threadIdx.x; t < j * (m + 1); t += GMF_THREADS) sH[t] = (T)ctl->H[t];
     __syncthreads();
     for (int i = K - 1; i >= 0; --i) {
-      const double* Hi = i == j ? hcol : (hsmem ? sH : ctl->H) + (long)i * (m + 1);
-      const double yi = gy[i] * scs[i];
+      const T yi = gy[i] * scs[i];
       __syncthreads();
-      for (int q = threadIdx.x; q < i; q += GMF_THREADS) gy[q] = fma(-Hi[q], yi, gy[q]);
+      if (i == j || hsmem) {
+        const T* Hi = i == j ? hcol : sH + (long)i * (m + 1);
+        for (int q = threadIdx.x; q < i; q += GMF_THREADS) gy[q] = fma(-Hi[q], yi, gy[q]);
+      } else {
+        const double* Hi = ctl->H + (long)i * (m + 1);
+        for (int q = threadIdx.x; q < i; q += GMF_THREADS) gy[q] = fma(-(T)Hi[q], yi, gy[q]);
+      }
       if (threadIdx.x == 0) gy[i] = yi;
       __syncthreads();
     }
-    // x slice into sw (w is no longer needed), x += V y, then the next apply's input
-    for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = x[i0 + i];
+    // x += V y over this CTA's rows (w is no longer needed), then the next apply's input.
+    // In float32 the product V y is formed alone and added to the float64 x.
+    for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = sizeof(T) == 8 ? (T)x[i0 + i] : (T)0;
     __syncthreads();
-    cta_combine(sV, Rp, gy, K, len, sw, 1.0);
+    cta_combine(sV, Rp, gy, K, len, sw, (T)1);
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
-      double v = sw[i];
+      const double v = sizeof(T) == 8 ? (double)sw[i] : x[i0 + i] + (double)sw[i];
       x[i0 + i] = v;
       gin[i0 + i] = v;
       gin_f[i0 + i] = (float)v;
@@ -836,7 +861,6 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, doubl
   cl_wait();  // no CTA leaves while another still reads its shared memory
   gmf_close(ctl, rank, hcond, use_cond, cap, done);
 }
-
 // --------------------------------------------------------------------------- device-driven refinement
 __global__ void k_ir_init(IrCtl* ir, double tol, int max_iter, int max_sweeps, int cap_outer) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -859,7 +883,8 @@ __global__ void k_ir_init(IrCtl* ir, double tol, int max_iter, int max_sweeps, i
 // start of the inner float32 GMRES on A d = r from d = 0 (tolerance 0.5 tol / rel clamped to
 // [1e-7, 0.5]; the inner GMRES trusts its Givens estimate). One block.
 __global__ void k_ir_decide(IrCtl* ir, GmresCtl* g, const double* b, const double* y, double* r, double* V,
-                            double* d, double* gin, float* gin_f, int n, int m, cudaGraphConditionalHandle h_inner) {
+                            float* Vf, double* d, double* gin, float* gin_f, int n, int m,
+                            cudaGraphConditionalHandle h_inner) {
   __shared__ double sh[32];
   __shared__ double s_rr;
   __shared__ int s_run;
@@ -926,6 +951,7 @@ __global__ void k_ir_decide(IrCtl* ir, GmresCtl* g, const double* b, const doubl
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double v = r[i] * inv;
     V[i] = v;
+    if (Vf) Vf[i] = (float)v;
     gin[i] = v;
     gin_f[i] = (float)v;
     d[i] = 0.0;
@@ -963,27 +989,31 @@ __global__ void k_ir_finish(IrCtl* ir, const GmresCtl* g, double* x, double* d, 
 }
 
 // --------------------------------------------------------------------------- host side
-// Largest dynamic shared memory the cluster kernel may use (set once per context).
+// Largest dynamic shared memory the cluster kernel of element type T may use (queried and
+// set once per context; the attribute is the function's largest possible value, the same
+// for every context).
+template <typename T>
 static size_t gmf_smem_limit(kfbi_ctx* c) {
-  if (c->gmf_smem_max == 0) {
+  size_t& mx = c->gmf_smem_max[sizeof(T) == 4 ? 1 : 0];
+  if (mx == 0) {
     cudaFuncAttributes fa{};
     int optin = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, k_gm_cluster) != cudaSuccess) {
+        cudaFuncGetAttributes(&fa, k_gm_cluster<T>) != cudaSuccess) {
       cudaGetLastError();
-      c->gmf_smem_max = 1;
+      mx = 1;
       return 0;
     }
     size_t lim = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
-    if (cudaFuncSetAttribute(k_gm_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) != cudaSuccess ||
-        cudaFuncSetAttribute(k_gm_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_gm_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) != cudaSuccess ||
+        cudaFuncSetAttribute(k_gm_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
       cudaGetLastError();
       lim = 0;
     }
-    c->gmf_smem_max = lim > 0 ? lim : 1;
+    mx = lim > 0 ? lim : 1;
   }
-  return c->gmf_smem_max > 1 ? c->gmf_smem_max : 0;
+  return mx > 1 ? mx : 0;
 }
 
 static cudaLaunchConfig_t gmf_launch_config(kfbi_ctx* c, const kfbi_ctx::GmfConfig& g, cudaLaunchAttribute* attr) {
@@ -1006,11 +1036,11 @@ static cudaLaunchConfig_t gmf_launch_config(kfbi_ctx* c, const kfbi_ctx::GmfConf
 // Cluster form for n nodes and restart m: 16 CTAs (else 8) whose slices of V (and, when it
 // fits, the Hessenberg matrix for the back substitution) fit in shared memory and that the
 // device can co-schedule. cs = 0: the multi-kernel form.
-kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m) {
-  kfbi_ctx::GmfConfig none{};
-  if (!c->gm_cluster) return none;
-  if (c->gmf.n == n && c->gmf.m == m) return c->gmf;
-  const size_t lim = gmf_smem_limit(c);
+template <typename T>
+static kfbi_ctx::GmfConfig gmf_select_t(kfbi_ctx* c, int n, int m) {
+  kfbi_ctx::GmfConfig& cache = sizeof(T) == 4 ? c->gmf32 : c->gmf;
+  if (cache.n == n && cache.m == m) return cache;
+  const size_t lim = gmf_smem_limit<T>(c);
   kfbi_ctx::GmfConfig pick{};
   pick.n = n;
   pick.m = m;
@@ -1018,15 +1048,15 @@ kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m) {
     if (pick.cs) break;
     if (c->force_cs != 0 && cs != c->force_cs) continue;
     const int R = cdiv(n, cs), Rp = gmf_row_stride(R);
-    const size_t base = sizeof(double) * ((size_t)(m + 1) * Rp + Rp);
+    const size_t base = sizeof(T) * ((size_t)(m + 1) * Rp + Rp);
     for (int hs : {1, 0}) {
-      const size_t smem = base + (hs ? sizeof(double) * (size_t)(m + 1) * (m + 1) : 0);
+      const size_t smem = base + (hs ? sizeof(T) * (size_t)(m + 1) * (m + 1) : 0);
       if (smem > lim) continue;
-      kfbi_ctx::GmfConfig g{n, m, cs, R, hs, smem};
+      kfbi_ctx::GmfConfig g{n, m, cs, R, hs, smem, sizeof(T) == 4 ? 1 : 0};
       cudaLaunchAttribute attr[2];
       cudaLaunchConfig_t cfg = gmf_launch_config(c, g, attr);
       int nc = 0;
-      if (cudaOccupancyMaxActiveClusters(&nc, k_gm_cluster, &cfg) != cudaSuccess) {
+      if (cudaOccupancyMaxActiveClusters(&nc, k_gm_cluster<T>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         nc = 0;
       }
@@ -1036,8 +1066,20 @@ kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m) {
       }
     }
   }
-  c->gmf = pick;
+  cache = pick;
   return pick;
+}
+
+// inner = true: the inner solve of the mixed-precision refinement, whose Gram-Schmidt runs in
+// float32 when the context allows it (KFBI_OPT_FP32_ARNOLDI) and has the float32 basis
+kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m, bool inner) {
+  kfbi_ctx::GmfConfig none{};
+  if (!c->gm_cluster) return none;
+  if (inner && c->arn32 && c->gVf != nullptr) {
+    kfbi_ctx::GmfConfig g = gmf_select_t<float>(c, n, m);
+    if (g.cs > 0) return g;
+  }
+  return gmf_select_t<double>(c, n, m);
 }
 
 static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, const double* b, double* x,
@@ -1052,8 +1094,12 @@ static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, c
     cudaLaunchAttribute attr[2];
     cudaLaunchConfig_t cfg = gmf_launch_config(c, gf, attr);
     launched(c, 1);
-    KFBI_TRY(cudaLaunchKernelEx(&cfg, k_gm_cluster, c->gctl, c->gV, ldv, (const double*)c->gw, b, x, c->gin,
-                                c->gin_f, n, gf.R, gf.hsmem, hcond, use_cond, cap));
+    if (gf.f32)
+      KFBI_TRY(cudaLaunchKernelEx(&cfg, k_gm_cluster<float>, c->gctl, c->gVf, ldv, (const double*)c->gw, b, x,
+                                  c->gin, c->gin_f, n, gf.R, gf.hsmem, hcond, use_cond, cap));
+    else
+      KFBI_TRY(cudaLaunchKernelEx(&cfg, k_gm_cluster<double>, c->gctl, c->gV, ldv, (const double*)c->gw, b, x,
+                                  c->gin, c->gin_f, n, gf.R, gf.hsmem, hcond, use_cond, cap));
     return KFBI_OK;
   }
   const int dblocks = c->gm_m + 1;
@@ -1128,7 +1174,7 @@ int restart_length(int restart, int n) {
 
 kfbi_status gmres_start_enqueue(kfbi_ctx* c, double tol, int max_iter, int m) {
   k_gm_init<<<1, 32, 0, c->stream>>>(c->gctl, tol, max_iter, m, 0);
-  k_gm_start<<<1, 1024, 0, c->stream>>>(c->gb, c->gx, c->gin, c->gin_f, c->gV, c->n, c->gctl, 0);
+  k_gm_start<<<1, 1024, 0, c->stream>>>(c->gb, c->gx, c->gin, c->gin_f, c->gV, nullptr, c->n, c->gctl, 0);
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
 }
@@ -1151,23 +1197,25 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   if (m < 1) m = 1;
   c->gm_m = m;
   const int cap = body_cap(max_iter, m);
-  const kfbi_ctx::GmfConfig gf = gmf_select(c, n, m);
+  const kfbi_ctx::GmfConfig gf = gmf_select(c, n, m, fp32);
   c->gmf_last_cs = gf.cs;
   const size_t hdr = offsetof(GmresCtl, g);
   launched(c, 2);
   k_gm_init<<<1, 32, 0, s>>>(c->gctl, tol, max_iter, m, trust ? 1 : 0);
-  k_gm_start<<<1, 1024, 0, s>>>(b, x, c->gin, c->gin_f, c->gV, n, c->gctl, zero_guess ? 1 : 0);
+  k_gm_start<<<1, 1024, 0, s>>>(b, x, c->gin, c->gin_f, c->gV, gf.f32 ? c->gVf : nullptr, n, c->gctl,
+                                zero_guess ? 1 : 0);
   bool graphed = false;
   if (c->use_graphs && !c->timing) {
     kfbi_ctx::SolveGraph& G = c->sgraph[kind][fp32 ? 1 : 0];
     kfbi_status st = KFBI_OK;
     if (G.exec == nullptr || G.version != c->iface_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
-        G.cfg != c->cfg_version) {
+        G.cfg != c->cfg_version || G.f32 != gf.f32) {
       st = build_graph(c, G, kind, fp32, eps_v, b, x, cap, gf);
       G.m = m;
       G.cs = gf.cs;
       G.pdl = c->use_pdl;
       G.cfg = c->cfg_version;
+      G.f32 = gf.f32;
     }
     if (st == KFBI_OK && cudaGraphLaunch(G.exec, s) == cudaSuccess) {
       graphed = true;
@@ -1262,8 +1310,8 @@ kfbi_status add_ir_nodes(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps
   kfbi_status st = apply_enqueue(c, layer, false, c->ir_x, c->tmp_vals, want_dn ? c->ir_dn : nullptr, nullptr, kind,
                                  ev, c->zero_flag, nullptr);
   if (st == KFBI_OK) {
-    k_ir_decide<<<1, 1024, 0, c->stream>>>(c->irctl, c->gctl, c->ir_b, c->tmp_vals, c->gb, c->gV, c->gx, c->gin,
-                                           c->gin_f, n, m, h_inner);
+    k_ir_decide<<<1, 1024, 0, c->stream>>>(c->irctl, c->gctl, c->ir_b, c->tmp_vals, c->gb, c->gV,
+                                           gf.f32 ? c->gVf : nullptr, c->gx, c->gin, c->gin_f, n, m, h_inner);
     if (cudaGetLastError() != cudaSuccess) st = KFBI_ERR_CUDA;
   }
   std::vector<cudaGraphNode_t> sinks;
@@ -1300,13 +1348,13 @@ static kfbi_status solve_ir_graph(kfbi_ctx* c, int kind, const double* rhs, doub
   if (m > MAX_RESTART) m = MAX_RESTART;
   if (m < 1) m = 1;
   c->gm_m = m;
-  const kfbi_ctx::GmfConfig gf = gmf_select(c, n, m);
+  const kfbi_ctx::GmfConfig gf = gmf_select(c, n, m, true);
   c->gmf_last_cs = gf.cs;
   const int cap = body_cap(max_iter, m);
   const int max_sweeps = IR_MAX_SWEEPS;
   kfbi_ctx::IrGraph& G = c->irgraph[kind][dnormal != nullptr ? 1 : 0];
   if (G.exec == nullptr || G.version != c->iface_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
-      G.cap != cap || G.cfg != c->cfg_version) {
+      G.cap != cap || G.cfg != c->cfg_version || G.f32 != gf.f32) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
     if (G.graph) cudaGraphDestroy(G.graph);
     G.exec = nullptr;
@@ -1332,6 +1380,7 @@ static kfbi_status solve_ir_graph(kfbi_ctx* c, int kind, const double* rhs, doub
     G.pdl = c->use_pdl;
     G.cap = cap;
     G.cfg = c->cfg_version;
+    G.f32 = gf.f32;
   }
   const size_t bytes = sizeof(double) * n;
   KFBI_TRY(cudaMemcpyAsync(c->ir_b, rhs, bytes, cudaMemcpyDeviceToDevice, s));

@@ -160,6 +160,13 @@ struct kfbi_ctx {
   float* tstart_f = nullptr;
   double* npack = nullptr;      // [max_nodes] double4 (x, y, y_a, -x_a) for the box quadrature
   float* npack_f = nullptr;     // float4 copy
+  // free-space box: the box quadrature's kernel for the current interface, [4N][n] row-major
+  // (face point, node), scale folded in, so that the box data of an apply is one product with
+  // the density; allocated when 4N max_nodes 12 B fits BOXK_MAX_BYTES
+  double* boxK = nullptr;
+  float* boxK_f = nullptr;
+  bool boxK_ok = false;         // filled for the current interface
+  bool use_boxK = true;         // KFBI_OPT_BOX_MATRIX
   int* prow_list = nullptr;     // [N] rows that hold interpolation probes
   int n_prow = 0;
   double* icoef = nullptr;      // [2][max_nodes/2+1] complex Fourier coefficients of x, y
@@ -231,13 +238,17 @@ struct kfbi_ctx {
     bool pdl = false;       // built with programmatic dependent launch
     int cfg = -1;           // cfg_version it was built with
     int body_launches = 0;  // kernels per replayed body
+    int f32 = 0;            // built with the float32 Gram-Schmidt kernel
   } sgraph[3][2];
   // cluster form of the GMRES body (k_gm_cluster) for the last (n, m); cs = 0: multi-kernel
   struct GmfConfig {
     int n = -1, m = -1;
     int cs = 0, R = 0, hsmem = 0;
     size_t smem = 0;
-  } gmf;
+    int f32 = 0;                // float32 Gram-Schmidt (k_gm_cluster<float>, basis gVf)
+  } gmf, gmf32;                 // float64 and float32 forms
+  float* gVf = nullptr;         // [(MAX_RESTART+1)][max_nodes] float32 basis (mixed precision)
+  bool arn32 = true;            // KFBI_OPT_FP32_ARNOLDI
   // device-driven refinement: control block, rhs / iterate / normal-derivative copies, and
   // one graph per (BIE kind, with normal derivative) holding the nested refinement loop
   kfbi::IrCtl* irctl = nullptr;
@@ -252,6 +263,7 @@ struct kfbi_ctx {
     int m = 0, cs = 0, cap = 0, cfg = -1;
     bool pdl = false;
     int inner_body_launches = 0;
+    int f32 = 0;
   } irgraph[3][2];
   bool gm_cluster = true;       // allow the cluster form
   bool use_pdl = false;         // programmatic dependent launch between the kernels of a body
@@ -259,7 +271,7 @@ struct kfbi_ctx {
   int col_P = 0;                // column pairs per block of the float32 column kernel (0 automatic)
   int cfg_version = 0;          // bumped by every option that changes the launched kernels
   int gmf_last_cs = 0;          // cluster size used by the last GMRES run
-  size_t gmf_smem_max = 0;      // 0 = not queried yet, 1 = unavailable
+  size_t gmf_smem_max[2] = {0, 0};  // per element type (double, float): 0 = not queried, 1 = unavailable
   long iface_version = 0;
   bool use_graphs = true;
   bool capturing = false;
@@ -367,11 +379,14 @@ kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* densi
                           double* dnormal, double* grid, int bie_kind, const double* eps_v,
                           const int* skip_flag, const float* density_f = nullptr);
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u);
+// free-space box: fills boxK / boxK_f for the current interface (after the node data)
+constexpr size_t BOXK_MAX_BYTES = (size_t)1 << 30;
+kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n);
 
 // graph building blocks shared by the single solve and the batch (kfbi_gmres.cu)
 kfbi_status cap_begin(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd);
 kfbi_status cap_end(kfbi_ctx* c, std::vector<cudaGraphNode_t>* sinks);
-kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m);
+kfbi_ctx::GmfConfig gmf_select(kfbi_ctx* c, int n, int m, bool inner = false);
 int body_cap(int max_iter, int m);
 int restart_length(int restart, int n);
 kfbi_status add_gmres_nodes(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, int kind, bool fp32,

@@ -19,6 +19,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "kfbi.h")
 # codes mirrored from include/kfbi.h
 OK, ERR_ARG, ERR_CUDA, ERR_OUTSIDE_BOX, ERR_UNDERRESOLVED, ERR_NOT_CONVERGED = 0, 1, 2, 3, 4, 5
 OPT_CUDA_GRAPHS, OPT_CLUSTER_GMRES, OPT_LAST_CLUSTER, OPT_PDL, OPT_CLUSTER_SIZE, OPT_COL_PAIRS = 1, 2, 3, 4, 5, 6
+OPT_BOX_MATRIX = 7
+OPT_FP32_ARNOLDI = 8
 MLP_FEATURES, MLP_MODES = 47, 16
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2
@@ -298,11 +300,11 @@ class Context:
         return dict(fp64_ms=a.value, fp64_launches=b.value, fp32_ms=c.value, fp32_launches=d.value)
 
     def set_option(self, option, value):
-        """kfbi_set_option: OPT_CUDA_GRAPHS, OPT_CLUSTER_GMRES or OPT_PDL to 0 / 1."""
+        """kfbi_set_option: one of the OPT_* constants (values as the header states)."""
         _check(self.lib.kfbi_set_option(self.handle, int(option), int(value)), "kfbi_set_option")
 
     def get_option(self, option):
-        """kfbi_get_option: OPT_CUDA_GRAPHS, OPT_CLUSTER_GMRES, OPT_LAST_CLUSTER or OPT_PDL."""
+        """kfbi_get_option: the current value of one of the OPT_* constants."""
         v = ctypes.c_int()
         _check(self.lib.kfbi_get_option(self.handle, int(option), ctypes.byref(v)), "kfbi_get_option")
         return v.value

@@ -96,6 +96,32 @@ def test_apply_parity(boxbc, kappa, layer, seed, N, n):
     assert rel(g.cpu().numpy(), ru) < 1e-11
 
 
+@pytest.mark.parametrize("layer", [0, 1])
+def test_freespace_box_table_and_direct_quadrature(layer):
+    """The free-space box data through the per-interface kernel table (default) and through
+    the direct quadrature agree with the oracle, also after the interface changes its node
+    count within the same context (the table is rebuilt with the new row length)."""
+    p = W.random_problem(12, N=128, n=131, box=1.5)
+    q = W.random_problem(13, N=128, n=97, box=1.5)
+    ctx = K.Context(p.N, p.box, 0.0, K.BOX_FREESPACE_DL, 0, max_nodes=p.n)
+    assert ctx.get_option(K.OPT_BOX_MATRIX) == 1
+    for prob in (p, q):
+        ctx.set_interface(dev(prob.xy))
+        ref = OK.Kfbi(prob.N, prob.box, 0.0, OK.BOX_FREESPACE_DL).set_interface(prob.xy)
+        dens = W.random_density(112, prob.n)
+        rv, _, ru = ref.apply(layer, dens, want_dnormal=True)
+        for use in (1, 0, 1):
+            ctx.set_option(K.OPT_BOX_MATRIX, use)
+            assert ctx.get_option(K.OPT_BOX_MATRIX) == use
+            vals, _, g = ctx.apply(layer, dev(dens), dnormal=True, grid=True)
+            assert rel(vals.cpu().numpy(), rv) < 1e-11, use
+            assert rel(g.cpu().numpy(), ru) < 1e-11, use
+    other = K.Context(p.N, p.box, 0.0, K.BOX_DIRICHLET0, 0, max_nodes=p.n)
+    assert other.get_option(K.OPT_BOX_MATRIX) == 0
+    with pytest.raises(K.KfbiError):
+        other.set_option(K.OPT_BOX_MATRIX, 1)
+
+
 def test_double_layer_of_one_is_half():
     p = W.random_problem(21, N=128, n=128)
     ctx, _ = make(p, OK.BOX_DIRICHLET0)
@@ -157,7 +183,7 @@ def test_gmres_restart_and_not_converged():
 
 
 @pytest.mark.parametrize("graphs,cluster,pdl", [(1, 1, 1), (1, 0, 1), (0, 1, 1), (0, 0, 1), (1, 1, 0), (0, 1, 0)])
-@pytest.mark.parametrize("precision,restart", [(0, 100), (0, 10), (1, 100)])
+@pytest.mark.parametrize("precision,restart", [(0, 100), (0, 10), (1, 100), (1, 10)])
 def test_gmres_forms_agree_with_oracle(graphs, cluster, pdl, precision, restart):
     """The graph loop and the host-polled loop, the cluster and the five-kernel Gram-Schmidt
     step, with and without programmatic dependent launch: each reaches the oracle's GMRES
@@ -194,14 +220,16 @@ def test_gmres_cluster_long_restart_without_staged_hessenberg():
     assert rel(phi.cpu().numpy(), rphi) < 1e-9
 
 
-@pytest.mark.parametrize("graphs", [1, 0])
-def test_mixed_precision_refinement(graphs):
+@pytest.mark.parametrize("graphs,arn32", [(1, 1), (0, 1), (1, 0), (0, 0)])
+def test_mixed_precision_refinement(graphs, arn32):
     """FP32 grid applies inside GMRES, FP64 residual and refinement: density within 1e-9 of
     FP64. graphs = 1: the whole refinement is one graph launch (nested conditional loops);
-    0: the host-driven sweeps."""
+    0: the host-driven sweeps. arn32: the inner GMRES's Gram-Schmidt in float32 or float64."""
     p = W.config_small_laplace()
     ctx, ref = make(p, OK.BOX_DIRICHLET0, precision=K.MIXED)
     ctx.set_option(K.OPT_CUDA_GRAPHS, graphs)
+    ctx.set_option(K.OPT_FP32_ARNOLDI, arn32)
+    assert ctx.get_option(K.OPT_FP32_ARNOLDI) == arn32
     phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=1e-10, max_iter=300, restart=100)
     assert ctx.get_option(K.OPT_CUDA_GRAPHS) == graphs  # the graph form ran, no fallback
     rphi, _ = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), p.rhs, tol=1e-13)
