@@ -184,7 +184,7 @@ def test_gmres_restart_and_not_converged():
 
 
 @pytest.mark.parametrize("graphs,cluster,pdl", [(1, 1, 1), (1, 0, 1), (0, 1, 1), (0, 0, 1), (1, 1, 0), (0, 1, 0)])
-@pytest.mark.parametrize("precision,restart", [(0, 100), (0, 10), (1, 100), (1, 10)])
+@pytest.mark.parametrize("precision,restart", [(0, 100), (0, 10), (1, 100), (1, 4)])
 def test_gmres_forms_agree_with_oracle(graphs, cluster, pdl, precision, restart):
     """The graph loop and the host-polled loop, the cluster and the five-kernel Gram-Schmidt
     step, with and without programmatic dependent launch: each reaches the oracle's GMRES
