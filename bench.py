@@ -256,7 +256,7 @@ def batched_leg(torch, K, flush, reps=3):
     seq_s = time.perf_counter() - t0
     its = [i["iterations"] for i in infos]
     out = dict(workload="batched_256_uneven_N128-512_n64-512_kappa0-10-100", instances=len(probs),
-               precision="mixed (f32 grid applies, f64 GMRES/refinement)", tol=tol,
+               precision="mixed (f32 grid applies and inner Gram-Schmidt, f64 residual/refinement)", tol=tol,
                instances_per_s=len(probs) / (float(np.median(ms)) / 1e3), ms_per_batch=float(np.median(ms)),
                sequential_instances_per_s=len(probs) / seq_s,
                converged=int(sum(1 for i in infos if i["status"] == 0)),
@@ -588,7 +588,7 @@ def main():
                     warmup=args.warmup, ms_per_step=1e3 * total_s / args.steps, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype="f32+f64", data="synthetic",
                     config=dict(workload=WORKLOAD, grid=N, nodes=p.n, box=[-4, 4], sigma=SIGMA, J=J, dt=DT,
-                                tol=TOL, precision="mixed (f32 grid applies, f64 GMRES/residual/refinement)",
+                                tol=TOL, precision="mixed (f32 grid applies and inner Gram-Schmidt, f64 residual/refinement)",
                                 parallelism=f"replicas{world}", l2="flushed (512 MB write) before every timed step"),
                     applies_per_s=dict(mixed_f32_grid=mixed_applies, fp64=(fp64 or {}).get("applies_per_s")),
                     fp64_plain=fp64,
