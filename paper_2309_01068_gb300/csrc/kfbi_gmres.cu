@@ -686,39 +686,55 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
     gmf_close(ctl, rank, hcond, use_cond, cap, done);
     return;
   }
-  // Arnoldi step j: w = A v_j against V[0..j]
+  // Arnoldi step j: w = A v_j against V[0..j]. The global reads are issued together and
+  // consumed afterwards (one memory round trip, not one per array): the rotations and g_j,
+  // the first NB * GMF_THREADS values of the V slice, then the w slice.
   const int j = s_j;
   const int K = j + 1;
   {
+    static_assert(MAX_RESTART <= GMF_THREADS, "one rotation per thread");
+    constexpr int NB = sizeof(T) == 4 ? 16 : 8;
+    const int tid = (int)threadIdx.x;
     const int tot = K * len;
-    for (int t0 = 0; t0 < tot; t0 += 8 * GMF_THREADS) {
-      T buf[8];
+    double cs_r = 0.0, sn_r = 0.0, gj_r = 0.0, w_r = 0.0;
+    if (tid < j) {
+      cs_r = ctl->cs[tid];
+      sn_r = ctl->sn[tid];
+    }
+    if (tid == 0) gj_r = ctl->g[j];
+    for (int t0 = 0; t0 < tot; t0 += NB * GMF_THREADS) {
+      T buf[NB];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int t = t0 + u * GMF_THREADS + (int)threadIdx.x;
+      for (int u = 0; u < NB; ++u) {
+        const int t = t0 + u * GMF_THREADS + tid;
         if (t < tot) {
           const int k = t / len, i = t - k * len;
           buf[u] = V[(long)k * ldv + i0 + i];
         }
       }
+      if (t0 == 0) {
+        // V and the rotations were complete before the apply started; w is its output
+        pdl_wait();
+        if (tid < len) w_r = w[i0 + tid];
+      }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int t = t0 + u * GMF_THREADS + (int)threadIdx.x;
+      for (int u = 0; u < NB; ++u) {
+        const int t = t0 + u * GMF_THREADS + tid;
         if (t < tot) {
           const int k = t / len, i = t - k * len;
           sV[k * Rp + i] = buf[u];
         }
       }
     }
+    if (tot == 0) pdl_wait();
+    if (tid < j) {
+      scs[tid] = (T)cs_r;
+      ssn[tid] = (T)sn_r;
+    }
+    if (tid == 0) s_gj = (T)gj_r;
+    if (tid < len) sw[tid] = (T)w_r;
+    for (int i = tid + GMF_THREADS; i < len; i += GMF_THREADS) sw[i] = (T)w[i0 + i];
   }
-  for (int i = threadIdx.x; i < j; i += GMF_THREADS) {
-    scs[i] = (T)ctl->cs[i];
-    ssn[i] = (T)ctl->sn[i];
-  }
-  if (threadIdx.x == 0) s_gj = (T)ctl->g[j];
-  // everything above was complete before the apply started; w is the apply's output
-  pdl_wait();
-  for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = (T)w[i0 + i];
   __syncthreads();
   // two passes of classical Gram-Schmidt; the second also reduces ||w'||^2 (entry K)
   cta_dots(sV, Rp, sw, len, K, false, part[0]);
@@ -778,8 +794,6 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
     const T res = fabs(gj1);
     s_end = (res <= tolb || its >= s_maxit || brk || j + 1 == m) ? 1 : 0;
     if (rank == 0) {
-      double* Hc = ctl->H + (long)j * (m + 1);
-      for (int k = 0; k <= j + 1; ++k) Hc[k] = hcol[k];
       ctl->cs[j] = cj;
       ctl->sn[j] = sj;
       ctl->rinv[j] = rd;
@@ -792,6 +806,11 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
     }
   }
   __syncthreads();
+  if (rank == 0) {
+    // Hessenberg column j (rotated), written by all threads
+    double* Hc = ctl->H + (long)j * (m + 1);
+    for (int k = threadIdx.x; k <= j + 1; k += GMF_THREADS) Hc[k] = hcol[k];
+  }
   if (!s_end) {
     const T inv = s_inv;
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
@@ -842,8 +861,9 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
       gin_f[i0 + i] = (float)v;
     }
     const bool conv = s_trust && res <= tolb;
+    if (rank == 0)
+      for (int i = threadIdx.x; i < K; i += GMF_THREADS) ctl->y[i] = gy[i];
     if (rank == 0 && threadIdx.x == 0) {
-      for (int i = 0; i < K; ++i) ctl->y[i] = gy[i];
       ctl->k_end = K;
       ctl->cycles = s_cycles + 1;
       ctl->action = ACT_NONE;
