@@ -426,10 +426,11 @@ __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 template <typename T>
 __device__ __forceinline__ void cl_reduce(const T* part, T* out, int L, unsigned cs) {
   cl_sync();
-  const int per = GMF_THREADS / (int)cs;
+  const int lcs = __ffs((int)cs) - 1;  // cs is a power of two
+  const int per = GMF_THREADS >> lcs;
   for (int base = 0; base < L; base += per) {
-    const int idx = base + (int)(threadIdx.x / cs);
-    const unsigned c = threadIdx.x % cs;
+    const int idx = base + (int)(threadIdx.x >> lcs);
+    const unsigned c = threadIdx.x & (cs - 1);
     T v = idx < L ? cl_load(part + idx, c) : (T)0;
     for (unsigned o = cs >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (c == 0 && idx < L) out[idx] = v;
@@ -463,11 +464,11 @@ __device__ __forceinline__ int lanes_pow2(int x) {
 template <typename T>
 __device__ __forceinline__ void cta_dots(const T* sV, int Rp, const T* w, int len, int K, bool with_norm, T* p) {
   const int Kt = K + (with_norm ? 1 : 0);
-  const int G = lanes_pow2(GMF_THREADS / Kt);
+  const int G = lanes_pow2(GMF_THREADS / Kt), lg = __ffs(G) - 1;
   const int total = Kt * G;
   for (int base = 0; base < total; base += GMF_THREADS) {
     const int t = base + (int)threadIdx.x;
-    const int k = t / G, g = t % G;
+    const int k = t >> lg, g = t & (G - 1);
     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     if (t < total) {
       const T* row = k < K ? sV + k * Rp : w;
@@ -491,11 +492,11 @@ __device__ __forceinline__ void cta_dots(const T* sV, int Rp, const T* w, int le
 // lane g sums k = g, g + G, ... with four accumulators, then a shuffle tree.
 template <typename T>
 __device__ __forceinline__ void cta_combine(const T* sV, int Rp, const T* h, int K, int len, T* w, T sign) {
-  const int G = lanes_pow2(GMF_THREADS / (len > 0 ? len : 1));
+  const int G = lanes_pow2(GMF_THREADS / (len > 0 ? len : 1)), lg = __ffs(G) - 1;
   const int total = len * G;
   for (int base = 0; base < total; base += GMF_THREADS) {
     const int t = base + (int)threadIdx.x;
-    const int i = t / G, g = t % G;
+    const int i = t >> lg, g = t & (G - 1);
     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     if (t < total) {
       int k = g;
@@ -702,14 +703,26 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
       sn_r = ctl->sn[tid];
     }
     if (tid == 0) gj_r = ctl->g[j];
+    // element t of the slice is (k, i) = (t / len, t mod len); consecutive t of one thread
+    // differ by GMF_THREADS = qs len + rs, so (k, i) advance without a division
+    const int qs = len > 0 ? GMF_THREADS / len : 0, rs = GMF_THREADS - qs * len;
+    int kk = len > 0 ? tid / len : 0, ii = tid - kk * len;
     for (int t0 = 0; t0 < tot; t0 += NB * GMF_THREADS) {
       T buf[NB];
+      int so[NB];
 #pragma unroll
       for (int u = 0; u < NB; ++u) {
         const int t = t0 + u * GMF_THREADS + tid;
+        so[u] = -1;
         if (t < tot) {
-          const int k = t / len, i = t - k * len;
-          buf[u] = V[(long)k * ldv + i0 + i];
+          buf[u] = V[(long)kk * ldv + i0 + ii];
+          so[u] = kk * Rp + ii;
+        }
+        kk += qs;
+        ii += rs;
+        if (ii >= len) {
+          ii -= len;
+          kk += 1;
         }
       }
       if (t0 == 0) {
@@ -718,13 +731,8 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
         if (tid < len) w_r = w[i0 + tid];
       }
 #pragma unroll
-      for (int u = 0; u < NB; ++u) {
-        const int t = t0 + u * GMF_THREADS + tid;
-        if (t < tot) {
-          const int k = t / len, i = t - k * len;
-          sV[k * Rp + i] = buf[u];
-        }
-      }
+      for (int u = 0; u < NB; ++u)
+        if (so[u] >= 0) sV[so[u]] = buf[u];
     }
     if (tot == 0) pdl_wait();
     if (tid < j) {
