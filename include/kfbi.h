@@ -317,6 +317,11 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             its Gram-Schmidt passes, rotations and update in float32 when
  *                             the cluster form runs; 0: in float64. The float64 refinement
  *                             decides convergence either way.
+ *   KFBI_OPT_PUSH_REDUCE      1 (default): the cluster form combines its CTAs' partial sums by
+ *                             pushing them (bulk shared-memory copies to every CTA of the
+ *                             cluster, completed on each receiver's mbarrier) when the
+ *                             receive rows fit in shared memory; 0: a cluster barrier, then
+ *                             every CTA loads the partial sums from the others.
  * kfbi_set_option: value 0 or 1 unless stated. kfbi_get_option writes the value to *value (host).
  * Errors: ARG (unknown option, bad value, NULL, read-only option).
  */
@@ -328,7 +333,8 @@ enum {
   KFBI_OPT_CLUSTER_SIZE = 5,
   KFBI_OPT_COL_PAIRS = 6,
   KFBI_OPT_BOX_MATRIX = 7,
-  KFBI_OPT_FP32_ARNOLDI = 8
+  KFBI_OPT_FP32_ARNOLDI = 8,
+  KFBI_OPT_PUSH_REDUCE = 9
 };
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);

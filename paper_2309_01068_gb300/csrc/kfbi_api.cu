@@ -466,6 +466,9 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
     c->use_boxK = value != 0;
   } else if (option == KFBI_OPT_FP32_ARNOLDI) {
     c->arn32 = value != 0;
+  } else if (option == KFBI_OPT_PUSH_REDUCE) {
+    c->gmf_push = value != 0;
+    c->gmf = c->gmf32 = kfbi_ctx::GmfConfig{};
   } else if (option == KFBI_OPT_CUDA_GRAPHS) {
     c->use_graphs = value != 0;
   } else if (option == KFBI_OPT_CLUSTER_GMRES) {
@@ -490,6 +493,7 @@ kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
   else if (option == KFBI_OPT_COL_PAIRS) *value = c->col_P;
   else if (option == KFBI_OPT_BOX_MATRIX) *value = (c->boxK != nullptr && c->use_boxK) ? 1 : 0;
   else if (option == KFBI_OPT_FP32_ARNOLDI) *value = c->arn32 ? 1 : 0;
+  else if (option == KFBI_OPT_PUSH_REDUCE) *value = c->gmf_push ? 1 : 0;
   else return KFBI_ERR_ARG;
   return KFBI_OK;
 }

@@ -381,6 +381,8 @@ __global__ void k_gm_cond(GmresCtl* ctl, cudaGraphConditionalHandle h, int cap) 
 // with an explicit reduction when that difference cancels (below half of ||w'||^2).
 constexpr int GMF_THREADS = 512;
 constexpr int GMF_PART = MAX_RESTART + 2;
+// row stride of the partial-sum and receive buffers: a multiple of 16 bytes for either type
+constexpr int GMF_PART_P = (GMF_PART + 3) & ~3;
 
 // row stride of the staged V slice: >= R and 4 mod 16 doubles, so that the lane patterns of
 // the dot and combine steps touch each shared-memory bank at most twice per warp access
@@ -403,6 +405,78 @@ __device__ __forceinline__ void cl_sync() {
 }
 __device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+// ---- push reductions: every CTA copies its partial sums into a receive row of every CTA of
+// the cluster (bulk copies, shared::cta -> shared::cluster) that complete the transaction
+// count of the receiver's mbarrier; each CTA then waits on its own barrier only.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned cl_map(unsigned addr, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for phase 0 of a barrier; false when the bound ran out
+constexpr int GMF_WAIT_TRIES = 1 << 22;
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* b) {
+  for (int it = 0; it < GMF_WAIT_TRIES; ++it)
+    if (mbar_try(b, 0)) return true;
+  return false;
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_to_cluster(unsigned dst, unsigned src, unsigned bytes, unsigned mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "r"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+// L elements rounded up to a multiple of 16 bytes
+template <typename T>
+__host__ __device__ inline int gmf_pad(int L) {
+  constexpr int E = 16 / (int)sizeof(T);
+  return (L + E - 1) / E * E;
+}
+// element offset of the receive rows in the dynamic shared memory (after sV, sH, sw)
+__host__ __device__ inline size_t gmf_recv_off(int m, int Rp, int hs, int esz) {
+  const size_t e = (size_t)(m + 1) * Rp + (hs ? (size_t)(m + 1) * (m + 1) : 0) + Rp;
+  const size_t E = 16 / (size_t)esz;
+  return (e + E - 1) / E * E;
+}
+
+// out[0..L) = sum over the cluster's CTAs (rank order, the same in every CTA) of part[0..L).
+// part was written before a __syncthreads by threads that fenced their writes for the async
+// proxy; recv holds cs rows of GMF_PART_P; mbar expects cs * gmf_pad(L) elements. A wait that
+// runs out sets *err and the sums are not meaningful.
+template <typename T>
+__device__ __forceinline__ void cl_push_reduce(const T* part, T* recv, unsigned long long* mbar, T* out, int L,
+                                               unsigned cs, unsigned rank, int* err) {
+  if (threadIdx.x < cs) {
+    const unsigned dst = cl_map(smem_u32(recv + (size_t)rank * GMF_PART_P), threadIdx.x);
+    const unsigned mb = cl_map(smem_u32(mbar), threadIdx.x);
+    bulk_to_cluster(dst, smem_u32(part), (unsigned)(gmf_pad<T>(L) * sizeof(T)), mb);
+  }
+  if (!*(volatile int*)err && !mbar_wait0(mbar)) *(volatile int*)err = 1;
+  for (int idx = threadIdx.x; idx < L; idx += GMF_THREADS) {
+    T v = recv[idx];
+    for (unsigned r = 1; r < cs; ++r) v += recv[(size_t)r * GMF_PART_P + idx];
+    out[idx] = v;
+  }
+  __syncthreads();
+}
 __device__ __forceinline__ double cl_load(const double* p, unsigned rank) {
   unsigned a = (unsigned)__cvta_generic_to_shared(p), r;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
@@ -483,7 +557,10 @@ __device__ __forceinline__ void cta_dots(const T* sV, int Rp, const T* w, int le
     }
     T v = (a0 + a1) + (a2 + a3);
     for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (t < total && g == 0) p[k] = v;
+    if (t < total && g == 0) {
+      p[k] = v;
+      fence_proxy_async();  // p may be read next by a bulk copy
+    }
   }
   __syncthreads();
 }
@@ -594,11 +671,13 @@ __device__ __forceinline__ void gmf_close(GmresCtl* ctl, unsigned rank, cudaGrap
 template <typename T>
 __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V, int ldv, const double* w,
                                                             const double* b, double* x, double* gin, float* gin_f,
-                                                            int n, int R, int hsmem, cudaGraphConditionalHandle hcond,
-                                                            int use_cond, int cap) {
+                                                            int n, int R, int hsmem, int push,
+                                                            cudaGraphConditionalHandle hcond, int use_cond, int cap) {
   extern __shared__ __align__(16) unsigned char gmf_dyn[];
   T* dsm = (T*)gmf_dyn;
-  __shared__ T part[2][GMF_PART];
+  __shared__ __align__(16) T part[2][GMF_PART_P];
+  __shared__ __align__(8) unsigned long long s_mbar[3];
+  __shared__ int s_err;
   __shared__ T h1[GMF_PART], h2[GMF_PART], hcol[GMF_PART];
   __shared__ T scs[MAX_RESTART], ssn[MAX_RESTART], gy[MAX_RESTART + 1];
   __shared__ T red[GMF_THREADS / 32];
@@ -620,6 +699,7 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
     s_cycles = ctl->cycles;
     s_tol = ctl->tol;
     s_bnorm = ctl->bnorm;
+    s_err = 0;
   }
   __syncthreads();
   if (s_done) {
@@ -692,6 +772,23 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
   // the first NB * GMF_THREADS values of the V slice, then the w slice.
   const int j = s_j;
   const int K = j + 1;
+  // push reductions (push = 1): receive rows for pass 1 (reused by the explicit norm) and
+  // pass 2; the barriers expect every CTA's rows; the cluster barrier begun here tells the
+  // other CTAs (before their first copy) that these barriers are initialised
+  T* recv0 = dsm + gmf_recv_off(m, Rp, hsmem, (int)sizeof(T));
+  T* recv1 = recv0 + (size_t)cs * GMF_PART_P;
+  if (push) {
+    if (threadIdx.x == 0) {
+      mbar_init(&s_mbar[0], 1);
+      mbar_init(&s_mbar[1], 1);
+      mbar_init(&s_mbar[2], 1);
+      fence_mbar_init();
+      mbar_arrive_expect(&s_mbar[0], cs * (unsigned)(gmf_pad<T>(K) * sizeof(T)));
+      mbar_arrive_expect(&s_mbar[1], cs * (unsigned)(gmf_pad<T>(K + 1) * sizeof(T)));
+      mbar_arrive_expect(&s_mbar[2], cs * (unsigned)(gmf_pad<T>(1) * sizeof(T)));
+    }
+    cl_arrive();
+  }
   {
     static_assert(MAX_RESTART <= GMF_THREADS, "one rotation per thread");
     constexpr int NB = sizeof(T) == 4 ? 16 : 8;
@@ -746,10 +843,18 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
   __syncthreads();
   // two passes of classical Gram-Schmidt; the second also reduces ||w'||^2 (entry K)
   cta_dots(sV, Rp, sw, len, K, false, part[0]);
-  cl_reduce(part[0], h1, K, cs);
+  if (push) {
+    cl_wait();  // every CTA's barriers are initialised
+    cl_push_reduce(part[0], recv0, &s_mbar[0], h1, K, cs, rank, &s_err);
+  } else {
+    cl_reduce(part[0], h1, K, cs);
+  }
   cta_combine(sV, Rp, h1, K, len, sw, (T)-1);
   cta_dots(sV, Rp, sw, len, K, true, part[1]);
-  cl_reduce(part[1], h2, K + 1, cs);
+  if (push)
+    cl_push_reduce(part[1], recv1, &s_mbar[1], h2, K + 1, cs, rank, &s_err);
+  else
+    cl_reduce(part[1], h2, K + 1, cs);
   cta_combine(sV, Rp, h2, K, len, sw, (T)-1);
   // concurrently: warp 0 forms ||w''||^2 = ||w'||^2 - ||h2||^2, warp 1 applies the previous
   // rotations to the Hessenberg column h1 + h2
@@ -774,10 +879,20 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
     T ss = 0;
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) ss += sw[i] * sw[i];
     ss = cta_sum(ss, red);
-    if (threadIdx.x == 0) part[0][0] = ss;
-    cl_reduce(part[0], &s_hn2, 1, cs);
+    if (threadIdx.x == 0) {
+      part[0][0] = ss;
+      fence_proxy_async();
+    }
+    if (push) {
+      // part[0] and recv0 are free: every CTA has received every pass-2 row, so every pass-1
+      // copy has completed
+      __syncthreads();
+      cl_push_reduce(part[0], recv0, &s_mbar[2], &s_hn2, 1, cs, rank, &s_err);
+    } else {
+      cl_reduce(part[0], &s_hn2, 1, cs);
+    }
   }
-  cl_arrive();  // the last read of another CTA's shared memory is done
+  cl_arrive();  // the last access to another CTA's shared memory is done
   // the new rotation from (hcol[j], ||w''||), with reciprocal square roots only:
   //   hn = ||w''||, den = sqrt(hcol[j]^2 + hn^2), c = hcol[j] / den, s = hn / den
   if (threadIdx.x == 0) {
@@ -812,6 +927,12 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
       ctl->hnorm = hn;
       ctl->breakdown = brk;
     }
+    if (s_err) {
+      // a reduction wait ran out: stop the solve with the timeout status
+      ctl->status = KFBI_ERR_TIMEOUT;
+      ctl->phase = PH_DONE;
+      ctl->done = 1;
+    }
   }
   __syncthreads();
   if (rank == 0) {
@@ -819,7 +940,9 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
     double* Hc = ctl->H + (long)j * (m + 1);
     for (int k = threadIdx.x; k <= j + 1; k += GMF_THREADS) Hc[k] = hcol[k];
   }
-  if (!s_end) {
+  if (s_err) {
+    done = 1;
+  } else if (!s_end) {
     const T inv = s_inv;
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
       const T v = sw[i] * inv;
@@ -886,7 +1009,7 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
     }
     done = conv ? 1 : 0;
   }
-  cl_wait();  // no CTA leaves while another still reads its shared memory
+  cl_wait();  // no CTA leaves while another may still read or copy from its shared memory
   gmf_close(ctl, rank, hcond, use_cond, cap, done);
 }
 // --------------------------------------------------------------------------- device-driven refinement
@@ -1076,11 +1199,15 @@ static kfbi_ctx::GmfConfig gmf_select_t(kfbi_ctx* c, int n, int m) {
     if (pick.cs) break;
     if (c->force_cs != 0 && cs != c->force_cs) continue;
     const int R = cdiv(n, cs), Rp = gmf_row_stride(R);
-    const size_t base = sizeof(T) * ((size_t)(m + 1) * Rp + Rp);
-    for (int hs : {1, 0}) {
-      const size_t smem = base + (hs ? sizeof(T) * (size_t)(m + 1) * (m + 1) : 0);
+    // push reductions first (their receive rows cost 2 cs GMF_PART_P elements), then the
+    // Hessenberg matrix staged for the back substitution
+    for (int opt = c->gmf_push ? 0 : 2; opt < 4 && !pick.cs; ++opt) {
+      const int push = opt < 2 ? 1 : 0, hs = (opt & 1) ? 0 : 1;
+      const size_t elems = push ? gmf_recv_off(m, Rp, hs, (int)sizeof(T)) + (size_t)2 * cs * GMF_PART_P
+                                : (size_t)(m + 1) * Rp + (hs ? (size_t)(m + 1) * (m + 1) : 0) + Rp;
+      const size_t smem = sizeof(T) * elems;
       if (smem > lim) continue;
-      kfbi_ctx::GmfConfig g{n, m, cs, R, hs, smem, sizeof(T) == 4 ? 1 : 0};
+      kfbi_ctx::GmfConfig g{n, m, cs, R, hs, smem, sizeof(T) == 4 ? 1 : 0, push};
       cudaLaunchAttribute attr[2];
       cudaLaunchConfig_t cfg = gmf_launch_config(c, g, attr);
       int nc = 0;
@@ -1124,10 +1251,10 @@ static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, c
     launched(c, 1);
     if (gf.f32)
       KFBI_TRY(cudaLaunchKernelEx(&cfg, k_gm_cluster<float>, c->gctl, c->gVf, ldv, (const double*)c->gw, b, x,
-                                  c->gin, c->gin_f, n, gf.R, gf.hsmem, hcond, use_cond, cap));
+                                  c->gin, c->gin_f, n, gf.R, gf.hsmem, gf.push, hcond, use_cond, cap));
     else
       KFBI_TRY(cudaLaunchKernelEx(&cfg, k_gm_cluster<double>, c->gctl, c->gV, ldv, (const double*)c->gw, b, x,
-                                  c->gin, c->gin_f, n, gf.R, gf.hsmem, hcond, use_cond, cap));
+                                  c->gin, c->gin_f, n, gf.R, gf.hsmem, gf.push, hcond, use_cond, cap));
     return KFBI_OK;
   }
   const int dblocks = c->gm_m + 1;

@@ -246,9 +246,11 @@ struct kfbi_ctx {
     int cs = 0, R = 0, hsmem = 0;
     size_t smem = 0;
     int f32 = 0;                // float32 Gram-Schmidt (k_gm_cluster<float>, basis gVf)
+    int push = 0;               // push reductions (bulk copies + mbarriers) between the CTAs
   } gmf, gmf32;                 // float64 and float32 forms
   float* gVf = nullptr;         // [(MAX_RESTART+1)][max_nodes] float32 basis (mixed precision)
   bool arn32 = true;            // KFBI_OPT_FP32_ARNOLDI
+  bool gmf_push = true;         // KFBI_OPT_PUSH_REDUCE
   // device-driven refinement: control block, rhs / iterate / normal-derivative copies, and
   // one graph per (BIE kind, with normal derivative) holding the nested refinement loop
   kfbi::IrCtl* irctl = nullptr;

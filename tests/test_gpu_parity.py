@@ -183,17 +183,21 @@ def test_gmres_restart_and_not_converged():
     assert info2["status"] == K.ERR_NOT_CONVERGED and info2["iterations"] == 2
 
 
-@pytest.mark.parametrize("graphs,cluster,pdl", [(1, 1, 1), (1, 0, 1), (0, 1, 1), (0, 0, 1), (1, 1, 0), (0, 1, 0)])
+@pytest.mark.parametrize("graphs,cluster,pdl,push", [(1, 1, 1, 1), (1, 0, 1, 1), (0, 1, 1, 1), (0, 0, 1, 1),
+                                                    (1, 1, 0, 1), (0, 1, 0, 1), (1, 1, 0, 0), (0, 1, 1, 0)])
 @pytest.mark.parametrize("precision,restart", [(0, 100), (0, 10), (1, 100), (1, 4)])
-def test_gmres_forms_agree_with_oracle(graphs, cluster, pdl, precision, restart):
+def test_gmres_forms_agree_with_oracle(graphs, cluster, pdl, push, precision, restart):
     """The graph loop and the host-polled loop, the cluster and the five-kernel Gram-Schmidt
-    step, with and without programmatic dependent launch: each reaches the oracle's GMRES
-    density (n = 131 leaves the last cluster slices ragged or empty)."""
+    step, with and without programmatic dependent launch, the cluster's push and pull
+    reductions: each reaches the oracle's GMRES density (n = 131 leaves the last cluster
+    slices ragged or empty)."""
     p = W.random_problem(61, N=128, n=131)
     ctx, ref = make(p, OK.BOX_DIRICHLET0, precision=precision)
     ctx.set_option(K.OPT_CUDA_GRAPHS, graphs)
     ctx.set_option(K.OPT_CLUSTER_GMRES, cluster)
     ctx.set_option(K.OPT_PDL, pdl)
+    ctx.set_option(K.OPT_PUSH_REDUCE, push)
+    assert ctx.get_option(K.OPT_PUSH_REDUCE) == push
     assert ctx.get_option(K.OPT_PDL) == pdl
     rhs = W.random_density(5, p.n)
     tol = 1e-12 if precision == 0 else 1e-10
@@ -206,6 +210,24 @@ def test_gmres_forms_agree_with_oracle(graphs, cluster, pdl, precision, restart)
     if restart < 100:
         assert info["restarts"] > 0
     assert rel(phi.cpu().numpy(), rphi) < (1e-9 if precision == 0 else 1e-8)
+
+
+@pytest.mark.parametrize("precision,push", [(0, 1), (0, 0)])
+def test_gmres_full_krylov_space(precision, push):
+    """n = 24 nodes and a tolerance no solve reaches: each cycle runs to j = n - 1, where the
+    new vector lies in the span of the basis to rounding (the explicit-norm reduction of the
+    Gram-Schmidt step, here through the push or the pull reductions); the run ends
+    NOT_CONVERGED at max_iter with the oracle's density."""
+    p = W.random_problem(71, N=64, n=24)
+    ctx, ref = make(p, OK.BOX_DIRICHLET0, precision=precision)
+    ctx.set_option(K.OPT_PUSH_REDUCE, push)
+    rhs = W.random_density(7, p.n)
+    phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(rhs), tol=1e-17, max_iter=60, restart=100)
+    assert ctx.get_option(K.OPT_LAST_CLUSTER) in (8, 16)
+    assert info["status"] == K.ERR_NOT_CONVERGED and info["iterations"] == 60
+    assert info["rel_residual"] < 1e-14
+    rphi, _ = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), rhs, tol=1e-15, restart=100)
+    assert rel(phi.cpu().numpy(), rphi) < 1e-12
 
 
 def test_gmres_cluster_long_restart_without_staged_hessenberg():
