@@ -166,11 +166,20 @@ __global__ void k_dens_coef(const T* phi, int n, const V2<T>* tw, const S_t* st,
 // [k0_l, k0_l + chunk) from e0 = e^{i k0_l alpha}, rotating by s1 = e^{i alpha}; the Nyquist
 // term uses q = e^{i n alpha / 2}), then every lane solves the 2x2 and 3x3 systems and holds
 // J = ([u], [u_x], [u_y], [u_xx], [u_yy], [u_xy]).
+// Shared-memory layout of the coefficients for it (jump_layout): c_0, then lane l's modes
+// [1 + l chunk, 1 + (l+1) chunk) from position 1 + l S, S = chunk rounded up to an odd
+// number so that the 32 lanes' simultaneous reads fall in distinct banks, then the Nyquist
+// coefficient at 1 + 32 S.
+__host__ __device__ inline int jump_chunk(int n) { return ((n - 1) / 2 + 31) / 32; }
+__host__ __device__ inline int jump_stride(int n) { const int c = jump_chunk(n); return (c & 1) ? c : c + 1; }
+__host__ __device__ inline int jump_layout_size(int n) { return 2 + 32 * jump_stride(n); }
+
+// lane_coef: this lane's modes k0, k0 + 1, ... (contiguous); c0 = c_0, nyq = c_{n/2} (even n)
 template <typename T, typename G>
-__device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, V2<T> e0, V2<T> s1, V2<T> q, const G& g,
-                                          int layer, T kappa, int lane, T J[6]) {
+__device__ __forceinline__ void jump_eval(const V2<T>* lane_coef, V2<T> c0, V2<T> cnyq, int n, V2<T> e0, V2<T> s1,
+                                          V2<T> q, const G& g, int layer, T kappa, int lane, T J[6]) {
   const int K = (n - 1) / 2;
-  const int chunk = (K + 31) / 32;
+  const int chunk = jump_chunk(n);
   int k0 = 1 + lane * chunk;
   int k1 = min(K + 1, k0 + chunk);
   T a = 0, b = 0, d = 0;
@@ -178,7 +187,7 @@ __device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, V2<T> e0, V2
     V2<T> e = e0;
     const V2<T> s = s1;
     for (int k = k0; k < k1; ++k) {
-      V2<T> ck = coef[k];
+      V2<T> ck = lane_coef[k - k0];
       T re = ck.x * e.x - ck.y * e.y;
       T im = ck.x * e.y + ck.y * e.x;
       T kk = (T)k;
@@ -188,12 +197,12 @@ __device__ __forceinline__ void jump_eval(const V2<T>* coef, int n, V2<T> e0, V2
       e = cmul(e, s);
     }
   }
-  a = (T)2 * wsum(a) + coef[0].x;
+  a = (T)2 * wsum(a) + c0.x;
   b = (T)2 * wsum(b);
   d = (T)2 * wsum(d);
   if ((n & 1) == 0) {
     T m = (T)(n / 2);
-    T nyq = coef[n / 2].x;
+    T nyq = cnyq.x;
     a += nyq * q.x;
     b -= m * nyq * q.y;
     d -= m * m * nyq * q.x;
@@ -240,18 +249,36 @@ __global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const G* tg, c
   pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
-  const V2<T>* sc = coef;
+  const int chunk = jump_chunk(n);
+  const V2<T>* lane_coef = coef + 1 + lane * chunk;
+  V2<T> c0, cnyq{0, 0};
   if (SMEM) {
     V2<T>* w = (V2<T>*)smem_raw;
-    const int nk = n / 2 + 1;
-    for (int k = threadIdx.x; k < nk; k += blockDim.x) w[k] = coef[k];
+    const int S = jump_stride(n), K = (n - 1) / 2;
+    for (int k = 1 + (int)threadIdx.x; k <= K; k += blockDim.x) {
+      const int l = (k - 1) / chunk;
+      w[1 + l * S + (k - 1 - l * chunk)] = coef[k];
+    }
+    if (threadIdx.x == 0) {
+      w[0] = coef[0];
+      if ((n & 1) == 0) w[1 + 32 * S] = coef[n / 2];
+    }
     __syncthreads();
-    sc = w;
+    lane_coef = w + 1 + lane * S;
+    c0 = w[0];
+    if ((n & 1) == 0) cnyq = w[1 + 32 * S];
+  } else {
+    c0 = coef[0];
+    if ((n & 1) == 0) cnyq = coef[n / 2];
   }
   if (t >= ntg) return;
   T J[6];
-  jump_eval<T, G>(sc, n, e0, s1, q, geo, layer, kappa, lane, J);
-  if (lane < 6) Jout[(long)t * 6 + lane] = J[lane];
+  jump_eval<T, G>(lane_coef, c0, cnyq, n, e0, s1, q, geo, layer, kappa, lane, J);
+  // lane < 6 stores J[lane] (selected without indexing the array, which stays in registers)
+  T v = J[5];
+#pragma unroll
+  for (int r = 4; r >= 0; --r) v = lane == r ? J[r] : v;
+  if (lane < 6) Jout[(long)t * 6 + lane] = v;
 }
 
 // Free-space box data (Sec. 4.1): g(p) = (1/n) sum_l phi_l (X_l - p).(y_a, -x_a)_l / |X_l - p|^2
@@ -691,29 +718,48 @@ __global__ void k_probe_values(int N, int dct, const int* prow_list, const int* 
                                const T* spec, const T* tab, float scale, T* pval, const int* skip) {
   const int j = prow_list[blockIdx.x];
   const int b = prow_ptr[j], e = prow_ptr[j + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // this warp's first probe column (set with the interface) before the wait
+  int pi_next = b + wid < e ? probe_i[b + wid] : 0;
   pdl_wait();
   pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   T* row = (T*)smem_raw;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    T v = spec[(long)j * N + k];
-    if ((dct && k == 0) || (!dct && k == N - 1)) v *= (T)0.5;
-    row[k] = v;
+  // the row's N values: four loads in flight per thread
+  constexpr int U = 4;
+  for (int k0 = threadIdx.x; k0 < N; k0 += U * blockDim.x) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * blockDim.x;
+      v[u] = k < N ? spec[(long)j * N + k] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * blockDim.x;
+      if (k < N) row[k] = ((dct && k == 0) || (!dct && k == N - 1)) ? v[u] * (T)0.5 : v[u];
+    }
   }
   __syncthreads();
   const int mask = 4 * N - 1;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int q = b + wid; q < e; q += nw) {
-    const int m = 2 * probe_i[q] + 1;
+    const int m = 2 * pi_next + 1;
+    pi_next = q + nw < e ? probe_i[q + nw] : 0;  // the next probe's column, in flight meanwhile
     const int step = (32 * m) & mask;
     int idx = dct ? ((lane * m + N) & mask) : (((lane + 1) * m) & mask);
-    T acc = 0;
-    for (int k = lane; k < N; k += 32) {
-      acc += row[k] * tsin(tab, idx, N, scale);
+    // two accumulators (terms k and k + 32) so that consecutive products do not wait on
+    // each other
+    T acc0 = 0, acc1 = 0;
+    int k = lane;
+    for (; k + 32 < N; k += 64) {
+      acc0 += row[k] * tsin(tab, idx, N, scale);
+      idx = (idx + step) & mask;
+      acc1 += row[k + 32] * tsin(tab, idx, N, scale);
       idx = (idx + step) & mask;
     }
-    acc = wsum(acc);
+    if (k < N) acc0 += row[k] * tsin(tab, idx, N, scale);
+    const T acc = wsum(acc0 + acc1);
     if (lane == 0) pval[q] = acc * ((T)2 / (T)N);
   }
 }
@@ -980,7 +1026,7 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   }
   const int ntg = ncr + n;
   using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
-  const size_t smj = (size_t)nk * sizeof(V2<T>);
+  const size_t smj = (size_t)jump_layout_size(n) * sizeof(V2<T>);
   if (smj <= SMEM_STAGE_MAX)
     KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, true>, dim3(cdiv((long)ntg * 32, 256)), dim3(256), smj, s,
                       (const V2<T>*)coef, n, ntg, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
