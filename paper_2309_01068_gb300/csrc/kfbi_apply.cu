@@ -396,10 +396,10 @@ __global__ void k_box_gemv(const T* K, const T* phi, int n, int rows, T* boxg, c
 // stage: N - 1 entries in all) so that neighbouring threads read neighbouring twiddles; the
 // inverse conjugates them (no 1/N). Returns the buffer with the result.
 //
-// Every sequence is stored with element e at position fsw(e) = e xor ((e >> 4) mod 16): a
-// permutation inside each aligned block of 16 that spreads the strided writes of the first
-// stages (dst[16 j + r] for consecutive j) over all banks, while runs of consecutive
-// elements stay conflict-free.
+// Input and output are in natural order. Only the buffer between the first and the second
+// stage is stored permuted, element e at fsw(e) = e xor ((e >> 4) mod 16) (a permutation
+// inside each aligned block of 16): the first stage's writes dst[R j + r] for consecutive j
+// then fall in distinct banks, and the second stage's reads stay conflict-free.
 __host__ __device__ inline int fft_radix_bits(int remaining_bits) { return remaining_bits >= 4 ? 4 : remaining_bits; }
 __device__ __forceinline__ int fsw(int e) { return e ^ ((e >> 4) & 15); }
 
@@ -490,7 +490,7 @@ __device__ __forceinline__ void dft_r(V2<T>* x) {
   else dft2<T, INV>(x);
 }
 
-template <typename T, int R, bool INV>
+template <typename T, int R, bool INV, bool SW_IN, bool SW_OUT>
 __device__ __forceinline__ void fft_stage(const V2<T>* src, V2<T>* dst, int P, int N, int Ns, int lNs, int lNR,
                                           const V2<T>* tw) {
   constexpr int LR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
@@ -502,7 +502,7 @@ __device__ __forceinline__ void fft_stage(const V2<T>* src, V2<T>* dst, int P, i
     const int jm = j & (Ns - 1);
     V2<T> x[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = s[fsw(j + r * NR)];
+    for (int r = 0; r < R; ++r) x[r] = s[SW_IN ? fsw(j + r * NR) : j + r * NR];
     if (jm != 0) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -514,8 +514,18 @@ __device__ __forceinline__ void fft_stage(const V2<T>* src, V2<T>* dst, int P, i
     dft_r<T, R, INV>(x);
     const int o = ((j >> lNs) << (lNs + LR)) + jm;
 #pragma unroll
-    for (int r = 0; r < R; ++r) d[fsw(o + r * Ns)] = x[r];
+    for (int r = 0; r < R; ++r) d[SW_OUT ? fsw(o + r * Ns) : o + r * Ns] = x[r];
   }
+}
+
+template <typename T, bool INV, bool SW_IN, bool SW_OUT>
+__device__ __forceinline__ void fft_stage_r(int lR, const V2<T>* src, V2<T>* dst, int P, int N, int Ns, int lNs,
+                                            const V2<T>* tw) {
+  const int lNR = __ffs(N) - 1 - lR;
+  if (lR == 4) fft_stage<T, 16, INV, SW_IN, SW_OUT>(src, dst, P, N, Ns, lNs, lNR, tw);
+  else if (lR == 3) fft_stage<T, 8, INV, SW_IN, SW_OUT>(src, dst, P, N, Ns, lNs, lNR, tw);
+  else if (lR == 2) fft_stage<T, 4, INV, SW_IN, SW_OUT>(src, dst, P, N, Ns, lNs, lNR, tw);
+  else fft_stage<T, 2, INV, SW_IN, SW_OUT>(src, dst, P, N, Ns, lNs, lNR, tw);
 }
 
 template <typename T, bool INV>
@@ -523,13 +533,12 @@ __device__ V2<T>* fft_run(V2<T>* a, V2<T>* b, int P, int N, int logN, const V2<T
   V2<T>* src = a;
   V2<T>* dst = b;
   int Ns = 1, lNs = 0, off = 0;
-  while (Ns < N) {
+  for (int stage = 0; Ns < N; ++stage) {
     const int lR = fft_radix_bits(logN - lNs);
-    const int lNR = logN - lR;
-    if (lR == 4) fft_stage<T, 16, INV>(src, dst, P, N, Ns, lNs, lNR, stw + off);
-    else if (lR == 3) fft_stage<T, 8, INV>(src, dst, P, N, Ns, lNs, lNR, stw + off);
-    else if (lR == 2) fft_stage<T, 4, INV>(src, dst, P, N, Ns, lNs, lNR, stw + off);
-    else fft_stage<T, 2, INV>(src, dst, P, N, Ns, lNs, lNR, stw + off);
+    const bool last = lNs + lR == logN;
+    if (stage == 0 && !last) fft_stage_r<T, INV, false, true>(lR, src, dst, P, N, Ns, lNs, stw + off);
+    else if (stage == 1) fft_stage_r<T, INV, true, false>(lR, src, dst, P, N, Ns, lNs, stw + off);
+    else fft_stage_r<T, INV, false, false>(lR, src, dst, P, N, Ns, lNs, stw + off);
     __syncthreads();
     V2<T>* tmp = src;
     src = dst;
@@ -546,9 +555,8 @@ __device__ V2<T>* fft_stockham(V2<T>* a, V2<T>* b, int P, int N, int logN, const
   return inverse ? fft_run<T, true>(a, b, P, N, logN, stw) : fft_run<T, false>(a, b, P, N, logN, stw);
 }
 
-// position of sample j in the Makhoul reordering v[n] = x[2n], v[N-1-n] = x[2n+1], in the
-// FFT's shared-memory order
-__device__ __forceinline__ int mk_pos(int j, int N) { return fsw((j & 1) ? N - 1 - (j >> 1) : (j >> 1)); }
+// position of sample j in the Makhoul reordering v[n] = x[2n], v[N-1-n] = x[2n+1]
+__device__ __forceinline__ int mk_pos(int j, int N) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
 
 // pi / (2N) in float32, the argument unit of tsin
 __device__ __forceinline__ float qscale(int N) { return 1.57079632679489662f / (float)N; }
@@ -569,8 +577,8 @@ __device__ __forceinline__ void stage_twiddles(const V2<T>* tw, V2<T>* sTw, int 
 // (c, s) = (cos, sin)(pi m / (2N)); the rotation at N - m is (sin, cos) of the same angle.
 template <typename T>
 __device__ __forceinline__ void dct_post(const V2<T>* z, int N, int m, T c, T s, V2<T>& Xm, V2<T>& XNm) {
-  V2<T> Z = z[fsw(m)];
-  V2<T> Zr = z[fsw((N - m) & (N - 1))];
+  V2<T> Z = z[m];
+  V2<T> Zr = z[(N - m) & (N - 1)];
   V2<T> Va{(T)0.5 * (Z.x + Zr.x), (T)0.5 * (Z.y - Zr.y)};
   V2<T> Vb{(T)0.5 * (Z.y + Zr.y), (T)-0.5 * (Z.x - Zr.x)};
   Xm = V2<T>{c * Va.x + s * Va.y, c * Vb.x + s * Vb.y};
@@ -750,22 +758,25 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
     for (int t = threadIdx.x; t < N; t += blockDim.x) w[t] = lam[t];
     for (int m = threadIdx.x; m <= N / 2; m += blockDim.x) dct_cs<T>(tab, N, m, sCs[m].x, sCs[m].y);
   }
-  const int tot = N * W;
+  // unit t = (row j, pair p): the two columns of the pair are adjacent in spec, so one
+  // 2-element load per unit
+  const int lP = lw - 1;
+  const int tot = N * P;
   for (int t0 = 0; t0 < tot; t0 += 8 * (int)blockDim.x) {
-    T buf[8];
+    V2<T> buf[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int t = t0 + u * (int)blockDim.x + (int)threadIdx.x;
-      if (t < tot) buf[u] = spec[(long)(t >> lw) * N + k0 + (t & (W - 1))];
+      if (t < tot) buf[u] = *(const V2<T>*)&spec[(long)(t >> lP) * N + k0 + 2 * (t & (P - 1))];
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int t = t0 + u * (int)blockDim.x + (int)threadIdx.x;
       if (t < tot) {
-        const int j = t >> lw, c = t & (W - 1);
-        T v = buf[u];
-        if (!dct && (j & 1)) v = -v;
-        ((T*)&A[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] = v;
+        const int j = t >> lP;
+        V2<T> v = buf[u];
+        if (!dct && (j & 1)) v = V2<T>{-v.x, -v.y};
+        A[(long)(t & (P - 1)) * N + mk_pos(j, N)] = v;
       }
     }
   }
@@ -795,18 +806,18 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
       }
       V2<T> Zm, ZNm;
       dct_pre<T>(N, m, cs.x, cs.y, Gm, GNm, Zm, ZNm);
-      y[fsw(m)] = Zm;
-      if (m > 0 && m < half) y[fsw(N - m)] = ZNm;
+      y[m] = Zm;
+      if (m > 0 && m < half) y[N - m] = ZNm;
     }
   }
   __syncthreads();
   V2<T>* Z = fft_stockham<T>(Y, X, P, N, logN, sTw, true);
   const T invN = (T)1 / (T)N;
   for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-    const int j = t >> lw, c = t & (W - 1);
-    T v = ((const T*)&Z[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] * invN;
-    if (!dct && (j & 1)) v = -v;
-    spec[(long)j * N + k0 + c] = v;
+    const int j = t >> lP;
+    V2<T> v = Z[(long)(t & (P - 1)) * N + mk_pos(j, N)];
+    const T f = (!dct && (j & 1)) ? -invN : invN;
+    *(V2<T>*)&spec[(long)j * N + k0 + 2 * (t & (P - 1))] = V2<T>{v.x * f, v.y * f};
   }
 }
 
@@ -914,8 +925,8 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
       T cm, sm;
       dct_cs<T>(tab, N, m, cm, sm);
       dct_pre<T>(N, m, cm, sm, Gm, GNm, Zm, ZNm);
-      A[fsw(m)] = Zm;
-      if (m > 0 && m < half) A[fsw(N - m)] = ZNm;
+      A[m] = Zm;
+      if (m > 0 && m < half) A[N - m] = ZNm;
     }
     __syncthreads();
     V2<T>* Z = fft_stockham<T>(A, B, 1, N, logN, tw, true);
