@@ -47,11 +47,11 @@ __global__ void k_init_tables(int N, double h, int neumann, double* tab, float* 
   }
 }
 
-__global__ void k_stage_twiddles(int N, int Ns, int R, int off, const double* tw, double* out, float* out_f) {
+__global__ void k_stage_twiddles(int N, int Ns, int off, const double* tw, double* out, float* out_f) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (R - 1) * Ns) return;
+  if (t >= 3 * Ns) return;
   int r = t / Ns + 1, jm = t - (r - 1) * Ns;
-  long m = (long)r * jm * (N / (R * Ns));  // < N
+  long m = (long)r * jm * (N / (4 * Ns));  // < N
   out[2 * (off + t)] = tw[2 * m];
   out[2 * (off + t) + 1] = tw[2 * m + 1];
   out_f[2 * (off + t)] = (float)tw[2 * m];
@@ -232,18 +232,14 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   k_init_tables<<<cdiv(4L * N, 256), 256, 0, c->own>>>(N, c->h, boxbc == KFBI_BOX_NEUMANN0, c->sintab, c->sintab_f,
                                                      c->lam, c->lam_f, c->twN, c->twN_f);
   KFBI_TRY(cudaGetLastError());
-  // staged twiddles of the Stockham FFT: for each stage with radix R (16 while four bits of
-  // log2 N remain, then 8, 4 or 2) and span Ns, w^{r jm N / (R Ns)} at [off + (r-1) Ns + jm],
-  // r = 1..R-1
+  // staged twiddles of the Stockham FFT: for each radix-4 stage with span Ns (first stage
+  // radix 2 when log2 N is odd), w^{r jm N / (4 Ns)} at [off + (r-1) Ns + jm], r = 1..3
   {
-    int off = 0, lNs = 0;
-    for (int Ns = 1; Ns < N;) {
-      const int rem = c->logN - lNs, lR = rem >= 4 ? 4 : rem, R = 1 << lR;
-      k_stage_twiddles<<<cdiv((long)(R - 1) * Ns, 256), 256, 0, c->own>>>(N, Ns, R, off, c->twN, c->stw_d, c->stw);
+    int off = 0;
+    for (int Ns = (c->logN & 1) ? 2 : 1; Ns < N; Ns <<= 2) {
+      k_stage_twiddles<<<cdiv(3L * Ns, 256), 256, 0, c->own>>>(N, Ns, off, c->twN, c->stw_d, c->stw);
       launched(c, 1);
-      off += (R - 1) * Ns;
-      Ns <<= lR;
-      lNs += lR;
+      off += 3 * Ns;
     }
   }
   KFBI_TRY(cudaGetLastError());

@@ -388,171 +388,61 @@ __global__ void k_box_gemv(const T* K, const T* phi, int n, int rows, T* boxg, c
 
 // --------------------------------------------------------------------------- FFT core
 // Stockham autosort FFT of P length-N sequences in shared memory (natural order in and
-// out), radix 16 while at least four bits of log2 N remain, then one radix-8, -4 or -2
-// stage (fft_radix). Stage with span Ns and radix R: item j reads src[j + r N/R],
-// multiplies by w^{r (j mod Ns) N/(Ns R)}, does the R-point DFT and writes
-// dst[(j/Ns) Ns R + (j mod Ns) + r Ns]. stw holds, stage by stage, w^{r jm N / (R Ns)} at
-// [off + (r-1) Ns + jm] (w = e^{-2 pi i / N}, r = 1..R-1, off advancing by (R-1) Ns per
-// stage: N - 1 entries in all) so that neighbouring threads read neighbouring twiddles; the
-// inverse conjugates them (no 1/N). Returns the buffer with the result.
-//
-// Input and output are in natural order. Only the buffer between the first and the second
-// stage is stored permuted, element e at fsw(e) = e xor ((e >> 4) mod 16) (a permutation
-// inside each aligned block of 16): the first stage's writes dst[R j + r] for consecutive j
-// then fall in distinct banks, and the second stage's reads stay conflict-free.
-__host__ __device__ inline int fft_radix_bits(int remaining_bits) { return remaining_bits >= 4 ? 4 : remaining_bits; }
-__device__ __forceinline__ int fsw(int e) { return e ^ ((e >> 4) & 15); }
-
-// multiplication by -i (forward) or +i (inverse)
-template <typename T, bool INV>
-__device__ __forceinline__ V2<T> mul_mi(V2<T> a) {
-  return INV ? V2<T>{-a.y, a.x} : V2<T>{a.y, -a.x};
-}
-// multiplication by the constant (c, INV ? s : -s)
-template <typename T, bool INV>
-__device__ __forceinline__ V2<T> mul_cs(V2<T> a, T c, T s) {
-  const T sg = INV ? s : -s;
-  return V2<T>{a.x * c - a.y * sg, a.x * sg + a.y * c};
-}
-
-// in-place DFTs of length 2, 4, 8, 16 (natural order in and out), e^{-2 pi i n k / R} forward
-template <typename T, bool INV>
-__device__ __forceinline__ void dft2(V2<T>* x) {
-  const V2<T> a = x[0];
-  x[0] = cadd(a, x[1]);
-  x[1] = csub(a, x[1]);
-}
-template <typename T, bool INV>
-__device__ __forceinline__ void dft4(V2<T>& x0, V2<T>& x1, V2<T>& x2, V2<T>& x3) {
-  const V2<T> a0 = cadd(x0, x2), a1 = csub(x0, x2), a2 = cadd(x1, x3), a3 = mul_mi<T, INV>(csub(x1, x3));
-  x0 = cadd(a0, a2);
-  x1 = cadd(a1, a3);
-  x2 = csub(a0, a2);
-  x3 = csub(a1, a3);
-}
-template <typename T, bool INV>
-__device__ __forceinline__ void dft4(V2<T>* x) {
-  dft4<T, INV>(x[0], x[1], x[2], x[3]);
-}
-template <typename T, bool INV>
-__device__ __forceinline__ void dft8(V2<T>* x) {
-  // even and odd halves, then X_k = E_k + w8^k O_k, X_{k+4} = E_k - w8^k O_k
-  const T h = (T)0.70710678118654752440;  // cos(pi/4)
-  V2<T> e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6];
-  V2<T> o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
-  dft4<T, INV>(e0, e1, e2, e3);
-  dft4<T, INV>(o0, o1, o2, o3);
-  o1 = mul_cs<T, INV>(o1, h, h);
-  o2 = mul_mi<T, INV>(o2);
-  o3 = mul_cs<T, INV>(o3, -h, h);
-  x[0] = cadd(e0, o0);
-  x[4] = csub(e0, o0);
-  x[1] = cadd(e1, o1);
-  x[5] = csub(e1, o1);
-  x[2] = cadd(e2, o2);
-  x[6] = csub(e2, o2);
-  x[3] = cadd(e3, o3);
-  x[7] = csub(e3, o3);
-}
-template <typename T, bool INV>
-__device__ __forceinline__ void dft16(V2<T>* x) {
-  // n = n1 + 4 n2, k = k1 + 4 k2: four DFT4 over n2, twiddles w16^{n1 k1}, four DFT4 over n1
-  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;  // cos, sin(pi/8)
-  const T h = (T)0.70710678118654752440;
-#pragma unroll
-  for (int n1 = 0; n1 < 4; ++n1) dft4<T, INV>(x[n1], x[n1 + 4], x[n1 + 8], x[n1 + 12]);
-  // now x[n1 + 4 k1] = Y[n1][k1]
-  x[5] = mul_cs<T, INV>(x[5], c1, s1);     // w^1
-  x[9] = mul_cs<T, INV>(x[9], h, h);       // w^2
-  x[13] = mul_cs<T, INV>(x[13], s1, c1);   // w^3
-  x[6] = mul_cs<T, INV>(x[6], h, h);       // w^2
-  x[10] = mul_mi<T, INV>(x[10]);           // w^4
-  x[14] = mul_cs<T, INV>(x[14], -h, h);    // w^6
-  x[7] = mul_cs<T, INV>(x[7], s1, c1);     // w^3
-  x[11] = mul_cs<T, INV>(x[11], -h, h);    // w^6
-  x[15] = mul_cs<T, INV>(x[15], -c1, -s1); // w^9
-#pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) dft4<T, INV>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
-  // x[4 k1 + k2] = X[k1 + 4 k2]: transpose the 4 x 4 block into natural order
-  V2<T> t;
-  t = x[1]; x[1] = x[4]; x[4] = t;
-  t = x[2]; x[2] = x[8]; x[8] = t;
-  t = x[3]; x[3] = x[12]; x[12] = t;
-  t = x[6]; x[6] = x[9]; x[9] = t;
-  t = x[7]; x[7] = x[13]; x[13] = t;
-  t = x[11]; x[11] = x[14]; x[14] = t;
-}
-template <typename T, int R, bool INV>
-__device__ __forceinline__ void dft_r(V2<T>* x) {
-  if constexpr (R == 16) dft16<T, INV>(x);
-  else if constexpr (R == 8) dft8<T, INV>(x);
-  else if constexpr (R == 4) dft4<T, INV>(x);
-  else dft2<T, INV>(x);
-}
-
-template <typename T, int R, bool INV, bool SW_IN, bool SW_OUT>
-__device__ __forceinline__ void fft_stage(const V2<T>* src, V2<T>* dst, int P, int N, int Ns, int lNs, int lNR,
-                                          const V2<T>* tw) {
-  constexpr int LR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
-  const int NR = N >> LR;
-  for (int t = threadIdx.x; t < P * NR; t += blockDim.x) {
-    const int p = t >> lNR, j = t & (NR - 1);
-    const V2<T>* s = src + (long)p * N;
-    V2<T>* d = dst + (long)p * N;
-    const int jm = j & (Ns - 1);
-    V2<T> x[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) x[r] = s[SW_IN ? fsw(j + r * NR) : j + r * NR];
-    if (jm != 0) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        V2<T> w = tw[(r - 1) * Ns + jm];
-        if (INV) w.y = -w.y;
-        x[r] = cmul(x[r], w);
-      }
-    }
-    dft_r<T, R, INV>(x);
-    const int o = ((j >> lNs) << (lNs + LR)) + jm;
-#pragma unroll
-    for (int r = 0; r < R; ++r) d[SW_OUT ? fsw(o + r * Ns) : o + r * Ns] = x[r];
-  }
-}
-
-template <typename T, bool INV, bool SW_IN, bool SW_OUT>
-__device__ __forceinline__ void fft_stage_r(int lR, const V2<T>* src, V2<T>* dst, int P, int N, int Ns, int lNs,
-                                            const V2<T>* tw) {
-  const int lNR = __ffs(N) - 1 - lR;
-  if (lR == 4) fft_stage<T, 16, INV, SW_IN, SW_OUT>(src, dst, P, N, Ns, lNs, lNR, tw);
-  else if (lR == 3) fft_stage<T, 8, INV, SW_IN, SW_OUT>(src, dst, P, N, Ns, lNs, lNR, tw);
-  else if (lR == 2) fft_stage<T, 4, INV, SW_IN, SW_OUT>(src, dst, P, N, Ns, lNs, lNR, tw);
-  else fft_stage<T, 2, INV, SW_IN, SW_OUT>(src, dst, P, N, Ns, lNs, lNR, tw);
-}
-
-template <typename T, bool INV>
-__device__ V2<T>* fft_run(V2<T>* a, V2<T>* b, int P, int N, int logN, const V2<T>* stw) {
-  V2<T>* src = a;
-  V2<T>* dst = b;
-  int Ns = 1, lNs = 0, off = 0;
-  for (int stage = 0; Ns < N; ++stage) {
-    const int lR = fft_radix_bits(logN - lNs);
-    const bool last = lNs + lR == logN;
-    if (stage == 0 && !last) fft_stage_r<T, INV, false, true>(lR, src, dst, P, N, Ns, lNs, stw + off);
-    else if (stage == 1) fft_stage_r<T, INV, true, false>(lR, src, dst, P, N, Ns, lNs, stw + off);
-    else fft_stage_r<T, INV, false, false>(lR, src, dst, P, N, Ns, lNs, stw + off);
-    __syncthreads();
-    V2<T>* tmp = src;
-    src = dst;
-    dst = tmp;
-    off += ((1 << lR) - 1) * Ns;
-    Ns <<= lR;
-    lNs += lR;
-  }
-  return src;
-}
-
+// out): one radix-2 stage when log2 N is odd, then radix-4 stages. Stage with span Ns and
+// radix R: item j reads src[j + r N/R], multiplies by w^{r (j mod Ns) N/(Ns R)}, does the
+// R-point DFT and writes dst[(j/Ns) Ns R + (j mod Ns) + r Ns]. stw holds, stage by stage,
+// w^{r jm N / (4 Ns)} at [off + (r-1) Ns + jm] (w = e^{-2 pi i / N}, r = 1..3, off advancing by
+// 3 Ns per stage) so that neighbouring threads read neighbouring twiddles; the inverse
+// conjugates them (no 1/N). Returns the buffer with the result.
 template <typename T>
 __device__ V2<T>* fft_stockham(V2<T>* a, V2<T>* b, int P, int N, int logN, const V2<T>* stw, bool inverse) {
-  return inverse ? fft_run<T, true>(a, b, P, N, logN, stw) : fft_run<T, false>(a, b, P, N, logN, stw);
+  V2<T>* src = a;
+  V2<T>* dst = b;
+  int Ns = 1;
+  if (logN & 1) {
+    const int h = N >> 1;
+    for (int t = threadIdx.x; t < P * h; t += blockDim.x) {
+      int p = t >> (logN - 1), j = t & (h - 1);
+      const V2<T>* s = src + (long)p * N;
+      V2<T>* d = dst + (long)p * N;
+      V2<T> v0 = s[j], v1 = s[j + h];
+      d[2 * j] = cadd(v0, v1);
+      d[2 * j + 1] = csub(v0, v1);
+    }
+    __syncthreads();
+    V2<T>* tmp = src; src = dst; dst = tmp;
+    Ns = 2;
+  }
+  const int q = N >> 2;
+  const int lq = logN - 2;
+  int off = 0;
+  for (; Ns < N; off += 3 * Ns, Ns <<= 2) {
+    const int lNs = __ffs(Ns) - 1;
+    for (int t = threadIdx.x; t < P * q; t += blockDim.x) {
+      int p = t >> lq, j = t & (q - 1);
+      const V2<T>* s = src + (long)p * N;
+      V2<T>* d = dst + (long)p * N;
+      int jm = j & (Ns - 1);
+      V2<T> v0 = s[j], v1 = s[j + q], v2 = s[j + 2 * q], v3 = s[j + 3 * q];
+      if (jm != 0) {
+        V2<T> w1 = stw[off + jm], w2 = stw[off + Ns + jm], w3 = stw[off + 2 * Ns + jm];
+        if (inverse) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; }
+        v1 = cmul(v1, w1);
+        v2 = cmul(v2, w2);
+        v3 = cmul(v3, w3);
+      }
+      V2<T> a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), t3 = csub(v1, v3);
+      V2<T> a3 = inverse ? V2<T>{-t3.y, t3.x} : V2<T>{t3.y, -t3.x};  // (+/- i)(v1 - v3)
+      int o = ((j >> lNs) << (lNs + 2)) + jm;
+      d[o] = cadd(a0, a2);
+      d[o + Ns] = cadd(a1, a3);
+      d[o + 2 * Ns] = csub(a0, a2);
+      d[o + 3 * Ns] = csub(a1, a3);
+    }
+    __syncthreads();
+    V2<T>* tmp = src; src = dst; dst = tmp;
+  }
+  return src;
 }
 
 // position of sample j in the Makhoul reordering v[n] = x[2n], v[N-1-n] = x[2n+1]
@@ -561,8 +451,12 @@ __device__ __forceinline__ int mk_pos(int j, int N) { return (j & 1) ? N - 1 - (
 // pi / (2N) in float32, the argument unit of tsin
 __device__ __forceinline__ float qscale(int N) { return 1.57079632679489662f / (float)N; }
 
-// number of staged twiddles of fft_stockham for N = 2^logN
-__host__ __device__ inline int staged_count(int N, int) { return N > 1 ? N - 1 : 0; }
+// number of staged twiddles of fft_stockham for N = 2^logN (at most N)
+__host__ __device__ inline int staged_count(int N, int logN) {
+  int c = 0;
+  for (int Ns = (logN & 1) ? 2 : 1; Ns < N; Ns <<= 2) c += 3 * Ns;
+  return c;
+}
 
 // copies the staged twiddles to shared memory (before the block's first __syncthreads)
 template <typename T>
@@ -1035,12 +929,10 @@ static int col_pairs(int N, int override_P = 0) {
   return P < 1 ? 1 : P;
 }
 
-// one radix-8 item per thread: P N / 8 threads, at least a warp, at most 512 (register
-// budget of the radix-16 stages); the radix-16 stages use half of them, the last (radix 2
-// to 8) stage all
+// one radix-4 item per thread and stage: P N / 4 threads (at least a warp, at most 1024)
 static int col_threads(int N, int P) {
-  int t = P * N / 8;
-  return t < 32 ? 32 : (t > 512 ? 512 : t);
+  int t = P * N / 4;
+  return t < 32 ? 32 : (t > 1024 ? 1024 : t);
 }
 
 template <typename T>
@@ -1265,22 +1157,19 @@ constexpr size_t NOALLOC_HEAD = 32;  // doubles reserved for flags, keeps the gr
 constexpr size_t NOALLOC_DOUBLES = NOALLOC_HEAD + (size_t)NOALLOC_MAX_N * NOALLOC_MAX_N + 8 * (size_t)NOALLOC_MAX_N;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
 
-// staged Stockham twiddle t (layout of fft_stockham): w^{r jm N / (R Ns)} = e^{-2 pi i r jm / (R Ns)}
+// staged Stockham twiddle t (layout of fft_stockham): w^{r jm N / (4 Ns)} = e^{-i pi r jm / (2 Ns)}
 __device__ bool staged_twiddle(int N, int logN, int t, double* re, double* im) {
-  int off = 0, lNs = 0;
-  for (int Ns = 1; Ns < N;) {
-    const int lR = fft_radix_bits(logN - lNs), R = 1 << lR;
-    if (t < off + (R - 1) * Ns) {
+  int off = 0;
+  for (int Ns = (logN & 1) ? 2 : 1; Ns < N; Ns <<= 2) {
+    if (t < off + 3 * Ns) {
       int r = (t - off) / Ns + 1, jm = (t - off) % Ns;
       double sn, cs;
-      sincospi(2.0 * (double)(r * jm) / (double)(R * Ns), &sn, &cs);
+      sincospi((double)(r * jm) / (2.0 * Ns), &sn, &cs);
       *re = cs;
       *im = -sn;
       return true;
     }
-    off += (R - 1) * Ns;
-    Ns <<= lR;
-    lNs += lR;
+    off += 3 * Ns;
   }
   return false;
 }
