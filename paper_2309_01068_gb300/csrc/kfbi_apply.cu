@@ -559,12 +559,6 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
   __shared__ T sv[ROW_CAP];
   const int j = blockIdx.x;
   const int b = row_ptr[j], e = row_ptr[j + 1];
-  // free-space box data of this row (west and east cells), read alongside the row pointers
-  T w = 0, ea = 0;
-  if (boxg != nullptr) {
-    w = boxg[j];
-    ea = boxg[N + j];
-  }
   const int per = (N + ROW_THREADS - 1) / ROW_THREADS;
   T acc[16];
 #pragma unroll
@@ -602,8 +596,11 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
       acc[q] = a;
     }
   }
+  T w = 0, ea = 0;
   const T* face = nullptr;
   if (boxg != nullptr) {
+    w = boxg[j];
+    ea = boxg[N + j];
     if (j == 0) face = facespec;
     else if (j == N - 1) face = facespec + N;
   }
@@ -652,25 +649,22 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
     for (int t = threadIdx.x; t < N; t += blockDim.x) w[t] = lam[t];
     for (int m = threadIdx.x; m <= N / 2; m += blockDim.x) dct_cs<T>(tab, N, m, sCs[m].x, sCs[m].y);
   }
-  // unit t = (row j, pair p): the two columns of the pair are adjacent in spec, so one
-  // 2-element load per unit
-  const int lP = lw - 1;
-  const int tot = N * P;
+  const int tot = N * W;
   for (int t0 = 0; t0 < tot; t0 += 8 * (int)blockDim.x) {
-    V2<T> buf[8];
+    T buf[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int t = t0 + u * (int)blockDim.x + (int)threadIdx.x;
-      if (t < tot) buf[u] = *(const V2<T>*)&spec[(long)(t >> lP) * N + k0 + 2 * (t & (P - 1))];
+      if (t < tot) buf[u] = spec[(long)(t >> lw) * N + k0 + (t & (W - 1))];
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int t = t0 + u * (int)blockDim.x + (int)threadIdx.x;
       if (t < tot) {
-        const int j = t >> lP;
-        V2<T> v = buf[u];
-        if (!dct && (j & 1)) v = V2<T>{-v.x, -v.y};
-        A[(long)(t & (P - 1)) * N + mk_pos(j, N)] = v;
+        const int j = t >> lw, c = t & (W - 1);
+        T v = buf[u];
+        if (!dct && (j & 1)) v = -v;
+        ((T*)&A[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] = v;
       }
     }
   }
@@ -708,10 +702,10 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
   V2<T>* Z = fft_stockham<T>(Y, X, P, N, logN, sTw, true);
   const T invN = (T)1 / (T)N;
   for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-    const int j = t >> lP;
-    V2<T> v = Z[(long)(t & (P - 1)) * N + mk_pos(j, N)];
-    const T f = (!dct && (j & 1)) ? -invN : invN;
-    *(V2<T>*)&spec[(long)j * N + k0 + 2 * (t & (P - 1))] = V2<T>{v.x * f, v.y * f};
+    const int j = t >> lw, c = t & (W - 1);
+    T v = ((const T*)&Z[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] * invN;
+    if (!dct && (j & 1)) v = -v;
+    spec[(long)j * N + k0 + c] = v;
   }
 }
 
