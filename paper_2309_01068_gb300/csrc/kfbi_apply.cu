@@ -712,56 +712,50 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
 // Probe values: inverse transform along x evaluated only at the interpolation points,
 //   u[j][i] = (2/N) sum_k w_k spec[j][k] sin(pi (k+1)(2i+1)/(2N)), w_{N-1} = 1/2  (DST-III)
 //   u[j][i] = (2/N) sum_k w_k spec[j][k] cos(pi k (2i+1)/(2N)), w_0 = 1/2        (DCT-III)
-// one block per grid row that holds probes, one warp per probe.
+// one warp per probe q (row probe_j[q], column probe_i[q]): lane l sums the modes
+// 4 l + 128 t + c (c < 4) read straight from the spectral grid (L2-resident after the column
+// solve), so that every warp has the same work however the probes fall in the rows.
 template <typename T>
-__global__ void k_probe_values(int N, int dct, const int* prow_list, const int* prow_ptr, const int* probe_i,
-                               const T* spec, const T* tab, float scale, T* pval, const int* skip) {
-  const int j = prow_list[blockIdx.x];
-  const int b = prow_ptr[j], e = prow_ptr[j + 1];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // this warp's first probe column (set with the interface) before the wait
-  int pi_next = b + wid < e ? probe_i[b + wid] : 0;
+__global__ void k_probe_values(int N, int dct, int n_probe, const int* probe_j, const int* probe_i, const T* spec,
+                               const T* tab, float scale, T* pval, const int* skip) {
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  // the probe's position (set with the interface) before the wait
+  int j = 0, i = 0;
+  if (q < n_probe) {
+    j = probe_j[q];
+    i = probe_i[q];
+  }
   pdl_wait();
   pdl_trigger();
-  if (*skip) return;
-  extern __shared__ unsigned char smem_raw[];
-  T* row = (T*)smem_raw;
-  // the row's N values: four loads in flight per thread
-  constexpr int U = 4;
-  for (int k0 = threadIdx.x; k0 < N; k0 += U * blockDim.x) {
-    T v[U];
+  if (*skip || q >= n_probe) return;
+  const int mask = 4 * N - 1, m = 2 * i + 1;
+  const T* row = spec + (long)j * N;
+  const int step = (128 * m) & mask;
+  int idx = dct ? ((4 * lane * m + N) & mask) : (((4 * lane + 1) * m) & mask);
+  T acc[4] = {0, 0, 0, 0};
+#pragma unroll 2
+  for (int k0 = 4 * lane; k0 < N; k0 += 128) {
+    T v[4];
+    if constexpr (sizeof(T) == 4) {
+      const float4 f = *(const float4*)(row + k0);
+      v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+    } else {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = k0 + u * blockDim.x;
-      v[u] = k < N ? spec[(long)j * N + k] : (T)0;
+      for (int c = 0; c < 4; ++c) v[c] = row[k0 + c];
     }
+    if (dct && k0 == 0) v[0] *= (T)0.5;
+    if (!dct && k0 + 4 == N) v[3] *= (T)0.5;
+    int id = idx;
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = k0 + u * blockDim.x;
-      if (k < N) row[k] = ((dct && k == 0) || (!dct && k == N - 1)) ? v[u] * (T)0.5 : v[u];
+    for (int c = 0; c < 4; ++c) {
+      acc[c] += v[c] * tsin(tab, id, N, scale);
+      id = (id + m) & mask;
     }
+    idx = (idx + step) & mask;
   }
-  __syncthreads();
-  const int mask = 4 * N - 1;
-  for (int q = b + wid; q < e; q += nw) {
-    const int m = 2 * pi_next + 1;
-    pi_next = q + nw < e ? probe_i[q + nw] : 0;  // the next probe's column, in flight meanwhile
-    const int step = (32 * m) & mask;
-    int idx = dct ? ((lane * m + N) & mask) : (((lane + 1) * m) & mask);
-    // two accumulators (terms k and k + 32) so that consecutive products do not wait on
-    // each other
-    T acc0 = 0, acc1 = 0;
-    int k = lane;
-    for (; k + 32 < N; k += 64) {
-      acc0 += row[k] * tsin(tab, idx, N, scale);
-      idx = (idx + step) & mask;
-      acc1 += row[k + 32] * tsin(tab, idx, N, scale);
-      idx = (idx + step) & mask;
-    }
-    if (k < N) acc0 += row[k] * tsin(tab, idx, N, scale);
-    const T acc = wsum(acc0 + acc1);
-    if (lane == 0) pval[q] = acc * ((T)2 / (T)N);
-  }
+  const T s = wsum((acc[0] + acc[1]) + (acc[2] + acc[3]));
+  if (lane == 0) pval[q] = s * ((T)2 / (T)N);
 }
 
 // Dense transforms along x of row pairs (grid output and the plain box solve).
@@ -1039,10 +1033,10 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
                                              face, tab, scale, spec, skip);
   launched(c, 1);
   KFBI_CHECK(launch_col_solve<T>(c, spec, skip));
-  if (c->n_prow > 0) {
-    KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(c->n_prow), dim3(256), sizeof(T) * (size_t)N, s, N, dct,
-                      (const int*)c->prow_list, (const int*)c->prow_ptr, (const int*)c->probe_i, (const T*)spec, tab,
-                      scale, pval, skip));
+  if (c->n_probe > 0) {
+    KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(cdiv((long)c->n_probe * 32, 256)), dim3(256), 0, s, N, dct,
+                      c->n_probe, (const int*)c->probe_j, (const int*)c->probe_i, (const T*)spec, tab, scale, pval,
+                      skip));
     launched(c, 1);
   }
   if (grid != nullptr) KFBI_CHECK(launch_row_dense<T>(c, 1, nullptr, spec, grid));

@@ -539,7 +539,7 @@ __global__ void k_probe_count(int N, const int* probe_mark, int* cnt) {
   if (lane == 0) cnt[j] = c;
 }
 
-__global__ void k_probe_emit(int N, int* probe_mark, const int* prow_ptr, int* probe_i) {
+__global__ void k_probe_emit(int N, int* probe_mark, const int* prow_ptr, int* probe_i, int* probe_j) {
   int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (j >= N) return;
@@ -551,6 +551,7 @@ __global__ void k_probe_emit(int N, int* probe_mark, const int* prow_ptr, int* p
     if (on) {
       int slot = base + __popc(mask & ((1u << lane) - 1u));
       probe_i[slot] = i;
+      probe_j[slot] = j;
       probe_mark[(long)j * N + i] = slot + 1;
     }
     base += __popc(mask);
@@ -676,7 +677,7 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
                                          c->probe_mark, c->flags);
   k_probe_count<<<wblocks, 256, 0, s>>>(N, c->probe_mark, c->prow_cnt);
   k_scan<<<1, 1024, 0, s>>>(c->prow_cnt, c->prow_ptr, N);
-  k_probe_emit<<<wblocks, 256, 0, s>>>(N, c->probe_mark, c->prow_ptr, c->probe_i);
+  k_probe_emit<<<wblocks, 256, 0, s>>>(N, c->probe_mark, c->prow_ptr, c->probe_i, c->probe_j);
   k_stencil_map<<<cdiv(n, 128), 128, 0, s>>>(n, c->probe_mark, c->stencil, c->stencil_f);
   k_npack<<<cdiv(n, 128), 128, 0, s>>>(n, c->xy, c->tgeo + ncr, (double4_32a*)c->npack, (float4*)c->npack_f);
   k_prow_list<<<1, 32, 0, s>>>(N, c->prow_cnt, c->prow_list, c->counts);

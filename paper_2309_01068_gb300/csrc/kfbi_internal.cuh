@@ -199,6 +199,7 @@ struct kfbi_ctx {
   int* prow_cnt = nullptr;      // [N + 1]
   int* prow_ptr = nullptr;      // [N + 1]
   int* probe_i = nullptr;       // [6*max_nodes] column of each probe (row from prow_ptr)
+  int* probe_j = nullptr;       // [6*max_nodes] row of each probe
   int* flags = nullptr;         // device error flags
   int* counts = nullptr;        // device counters [8]
   int* host_counts = nullptr;   // pinned [8]
