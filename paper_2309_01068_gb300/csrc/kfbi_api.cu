@@ -158,9 +158,9 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->twn_f, 2 * (size_t)max_nodes));
   KFBI_CHECK(dalloc(&c->npack, 4 * (size_t)max_nodes));
   KFBI_CHECK(dalloc(&c->npack_f, 4 * (size_t)max_nodes));
-  if (boxbc == KFBI_BOX_FREESPACE_DL && (size_t)4 * N * max_nodes * 12 <= BOXK_MAX_BYTES) {
-    KFBI_CHECK(dalloc(&c->boxK, (size_t)4 * N * max_nodes));
-    KFBI_CHECK(dalloc(&c->boxK_f, (size_t)4 * N * max_nodes));
+  if (boxbc == KFBI_BOX_FREESPACE_DL && (size_t)4 * N * box_ld(max_nodes) * 12 <= BOXK_MAX_BYTES) {
+    KFBI_CHECK(dalloc(&c->boxK, (size_t)4 * N * box_ld(max_nodes)));
+    KFBI_CHECK(dalloc(&c->boxK_f, (size_t)4 * N * box_ld(max_nodes)));
   }
   KFBI_CHECK(dalloc(&c->prow_list, N + 1));
   KFBI_CHECK(dalloc(&c->facespec, 2 * (size_t)N));

@@ -344,46 +344,69 @@ __global__ void k_box_data(const T* phi, int n, const T4* npack, int N, double x
 //   K[w][l] = -2 / (h^2 n) ((X_l - p_w).(y_a, -x_a)_l) / |X_l - p_w|^2
 // (the trapezoidal double layer of Sec. 4.1 at p_w, pre-scaled as the right-hand side term
 // -2 g / h^2), so that boxg = K phi. Computed once per interface in float64 with a float32
-// copy; every apply then reads it (4N n values) instead of re-evaluating it.
-__global__ void k_box_matrix(int N, int n, const double4_32a* npack, double xmin, double xmax, double ymin,
+// copy, rows of box_ld(n) entries (zeros past n); every apply then reads it (4N n values)
+// instead of re-evaluating it.
+__global__ void k_box_matrix(int N, int n, int ld, const double4_32a* npack, double xmin, double xmax, double ymin,
                              double ymax, double h, double scale, double* K, float* Kf) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long)4 * N * n) return;
-  const int w = (int)(t / n), l = (int)(t - (long)w * n);
-  const int face = w / N, idx = w - face * N;
-  double px, py;
-  if (face == 0) { px = xmin; py = grid_coord(ymin, h, idx); }
-  else if (face == 1) { px = xmax; py = grid_coord(ymin, h, idx); }
-  else if (face == 2) { px = grid_coord(xmin, h, idx); py = ymin; }
-  else { px = grid_coord(xmin, h, idx); py = ymax; }
-  const double4_32a q = npack[l];
-  const double dx = q.x - px, dy = q.y - py;
-  const double k = scale * (dx * q.z + dy * q.w) / (dx * dx + dy * dy);
+  if (t >= (long)4 * N * ld) return;
+  const int w = (int)(t / ld), l = (int)(t - (long)w * ld);
+  double k = 0.0;
+  if (l < n) {
+    const int face = w / N, idx = w - face * N;
+    double px, py;
+    if (face == 0) { px = xmin; py = grid_coord(ymin, h, idx); }
+    else if (face == 1) { px = xmax; py = grid_coord(ymin, h, idx); }
+    else if (face == 2) { px = grid_coord(xmin, h, idx); py = ymin; }
+    else { px = grid_coord(xmin, h, idx); py = ymax; }
+    const double4_32a q = npack[l];
+    const double dx = q.x - px, dy = q.y - py;
+    k = scale * (dx * q.z + dy * q.w) / (dx * dx + dy * dy);
+  }
   K[t] = k;
   Kf[t] = (float)k;
 }
 
-// boxg[w] = sum_l K[w][l] phi_l: one warp per face point, coalesced rows, four accumulators
-template <typename T>
-__global__ void k_box_gemv(const T* K, const T* phi, int n, int rows, T* boxg, const int* skip) {
+// four consecutive table or density values (16-byte aligned for float, 32 for double)
+__device__ __forceinline__ void load4(const float* p, float v[4]) {
+  const float4 f = *(const float4*)p;
+  v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+}
+__device__ __forceinline__ void load4(const double* p, double v[4]) {
+  const double2 a = ((const double2*)p)[0], b = ((const double2*)p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+// boxg[w] = sum_l K[w][l] phi_l: one warp per face point; lane l takes nodes 4 l + 128 t + c
+// with one 16-byte table load per four nodes (VEC: phi read the same way, else per value),
+// then the nodes past the last full group of four one by one
+template <typename T, bool VEC>
+__global__ void k_box_gemv(const T* K, int ld, const T* phi, int n, int rows, T* boxg, const int* skip) {
   pdl_wait();
   pdl_trigger();
   if (*skip) return;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= rows) return;
-  const T* row = K + (long)w * n;
-  T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-  int l = lane;
-  for (; l + 96 < n; l += 128) {
-    a0 += row[l] * phi[l];
-    a1 += row[l + 32] * phi[l + 32];
-    a2 += row[l + 64] * phi[l + 64];
-    a3 += row[l + 96] * phi[l + 96];
+  const T* row = K + (long)w * ld;
+  const int n4 = n & ~3;
+  T a[4] = {0, 0, 0, 0};
+#pragma unroll 2
+  for (int l = 4 * lane; l < n4; l += 128) {
+    T kv[4], pv[4];
+    load4(row + l, kv);
+    if (VEC) {
+      load4(phi + l, pv);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) pv[c] = phi[l + c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a[c] += kv[c] * pv[c];
   }
-  for (; l < n; l += 32) a0 += row[l] * phi[l];
-  T a = wsum((a0 + a1) + (a2 + a3));
-  if (lane == 0) boxg[w] = a;
+  if (n4 + lane < n) a[0] += row[n4 + lane] * phi[n4 + lane];
+  const T s = wsum((a[0] + a[1]) + (a[2] + a[3]));
+  if (lane == 0) boxg[w] = s;
 }
 
 // --------------------------------------------------------------------------- FFT core
@@ -995,10 +1018,13 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     KFBI_TRY(cudaStreamWaitEvent(s2, c->ev_fork, 0));
     const size_t smb = (size_t)n * sizeof(T4);
     const T bscale = (T)(-2.0 / (c->h * c->h * (double)n));
-    if (c->boxK_ok && c->use_boxK)
-      k_box_gemv<T><<<cdiv((long)4 * N * 32, 256), 256, 0, s2>>>(
-          sizeof(T) == 8 ? (const T*)c->boxK : (const T*)c->boxK_f, dens_t, n, 4 * N, boxg, skip);
-    else if (smb <= SMEM_STAGE_MAX)
+    if (c->boxK_ok && c->use_boxK) {
+      const T* Kt = sizeof(T) == 8 ? (const T*)c->boxK : (const T*)c->boxK_f;
+      if (((uintptr_t)dens_t & (4 * sizeof(T) - 1)) == 0)
+        k_box_gemv<T, true><<<cdiv((long)4 * N * 32, 256), 256, 0, s2>>>(Kt, box_ld(n), dens_t, n, 4 * N, boxg, skip);
+      else
+        k_box_gemv<T, false><<<cdiv((long)4 * N * 32, 256), 256, 0, s2>>>(Kt, box_ld(n), dens_t, n, 4 * N, boxg, skip);
+    } else if (smb <= SMEM_STAGE_MAX)
       k_box_data<T, T4, true><<<cdiv((long)4 * N * 32, 256), 256, smb, s2>>>(
           dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, bscale, boxg, skip);
     else
@@ -1097,9 +1123,9 @@ kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* densi
 }
 
 kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n) {
-  const long tot = (long)4 * c->N * n;
+  const long tot = (long)4 * c->N * box_ld(n);
   launched(c, 1);
-  k_box_matrix<<<cdiv(tot, 256), 256, 0, c->stream>>>(c->N, n, (const double4_32a*)c->npack, c->xmin, c->xmax,
+  k_box_matrix<<<cdiv(tot, 256), 256, 0, c->stream>>>(c->N, n, box_ld(n), (const double4_32a*)c->npack, c->xmin, c->xmax,
                                                        c->ymin, c->ymax, c->h, -2.0 / (c->h * c->h * (double)n),
                                                        c->boxK, c->boxK_f);
   KFBI_TRY(cudaGetLastError());

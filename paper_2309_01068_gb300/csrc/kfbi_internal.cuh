@@ -384,6 +384,9 @@ kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* densi
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u);
 // free-space box: fills boxK / boxK_f for the current interface (after the node data)
 constexpr size_t BOXK_MAX_BYTES = (size_t)1 << 30;
+// row stride of the table: node count rounded up to a multiple of 4 (16-byte rows), padded
+// with zeros
+__host__ __device__ inline int box_ld(int n) { return (n + 3) & ~3; }
 kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n);
 
 // graph building blocks shared by the single solve and the batch (kfbi_gmres.cu)
