@@ -39,7 +39,7 @@ def _compile(src, verbose):
 def build(jobs=None, verbose=False, force=False):
     """Compile every .cu translation unit in parallel and link libkfbi.so."""
     os.makedirs(BUILD, exist_ok=True)
-    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "kfbi_internal.cuh"),
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "kfbi_internal.cuh"), os.path.join(CSRC, "kfbi_fft.cuh"),
                                                        os.path.join(ROOT, "include", "kfbi.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

@@ -3,6 +3,7 @@
 // with their crossed arms (Sec. 4.2) and the 6-point interpolation stencils (Sec. 4.3).
 #include <cmath>
 
+#include "kfbi_fft.cuh"
 #include "kfbi_internal.cuh"
 
 namespace kfbi {
@@ -154,6 +155,77 @@ __global__ void k_fine_samples(const double2* coef, int n, int M, const double2*
     fine[2 * warp + 1] = y.f;
     if (x.f < xlo || x.f > xhi || y.f < ylo || y.f > yhi) atomicOr(flags, FLAG_OUTSIDE);
   }
+}
+
+// The same fine samples for a power-of-two n from eight inverse FFTs of length n (block r):
+// with C_k = cx_k + i cy_k over k in [-K, K] (c_{-k} = conj c_k) the curve is
+// x + i y = sum_k C_k e^{i k alpha} + (nx + i ny) cos(n alpha / 2), and at
+// alpha = 2 pi (8 q + r) / (8 n)
+//   X(alpha_{8q+r}) = sum_k [C_k e^{2 pi i k r / (8n)}] e^{2 pi i k q / n}
+//                     + (nx + i ny) cos(pi r / 8) (-1)^q,
+// an inverse DFT of length n over q once the Nyquist term sits at index n/2. twn[m] =
+// e^{2 pi i m / n} gives the FFT's staged twiddles, twM[m] = e^{2 pi i m / (8n)} the shifts.
+// Shared memory: A[n] | B[n] | staged twiddles[n] (complex float64).
+__global__ void k_fine_fft(const double2* coef, int n, int logn, const double2* twn, const double2* twM, double* fine,
+                           double xlo, double xhi, double ylo, double yhi, int* flags) {
+  extern __shared__ double2 fsm[];
+  V2<double>* A = (V2<double>*)fsm;
+  V2<double>* B = A + n;
+  V2<double>* stw = B + n;
+  const int r = blockIdx.x, M = 8 * n, nk = n / 2 + 1, K = (n - 1) / 2;
+  const double2* cx = coef;
+  const double2* cy = coef + nk;
+  // staged twiddles of fft_stockham with w = e^{-2 pi i / n} = conj twn[1]: for its stage
+  // with span Ns, entry off + (r' - 1) Ns + jm holds w^{r' jm n / (4 Ns)}
+  const int cnt = staged_count(n, logn);
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    int off = 0, Ns = (logn & 1) ? 2 : 1;
+    while (t >= off + 3 * Ns) {
+      off += 3 * Ns;
+      Ns <<= 2;
+    }
+    const int rr = (t - off) / Ns + 1, jm = (t - off) - (rr - 1) * Ns;
+    const double2 w = twn[(long)rr * jm * (n / (4 * Ns))];
+    stw[t] = V2<double>{w.x, -w.y};
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    V2<double> v{0.0, 0.0};
+    if (k == 0) {
+      v = V2<double>{cx[0].x, cy[0].x};
+    } else if (k <= K) {
+      const double2 a = cx[k], b = cy[k];
+      const double2 e = twM[((long)k * r) % M];
+      const V2<double> ck{a.x - b.y, a.y + b.x};
+      v = cmul(ck, V2<double>{e.x, e.y});
+    } else if (k >= n - K) {
+      const int kk = n - k;  // mode -kk
+      const double2 a = cx[kk], b = cy[kk];
+      const double2 e = twM[((long)kk * r) % M];
+      const V2<double> ck{a.x + b.y, b.x - a.y};
+      v = cmul(ck, V2<double>{e.x, -e.y});
+    } else {
+      // k = n/2 (even n): the Nyquist term
+      const double cr = twM[((long)(n / 2) * r) % M].x;  // cos(pi r / 8)
+      v = V2<double>{cx[n / 2].x * cr, cy[n / 2].x * cr};
+    }
+    A[k] = v;
+  }
+  __syncthreads();
+  const V2<double>* X = fft_stockham<double>(A, B, 1, n, logn, stw, true);
+  bool out = false;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    const V2<double> z = X[q];
+    const long s = 8L * q + r;
+    fine[2 * s] = z.x;
+    fine[2 * s + 1] = z.y;
+    out |= z.x < xlo || z.x > xhi || z.y < ylo || z.y > yhi;
+  }
+  if (out) atomicOr(flags, FLAG_OUTSIDE);
+}
+
+kfbi_status geometry_setup_attributes() {
+  KFBI_TRY(cudaFuncSetAttribute(k_fine_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_FFT_SMEM));
+  return KFBI_OK;
 }
 
 // per fine segment s -> s+1 (cyclic) and kind: number of grid lines crossed.
@@ -630,9 +702,16 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   k_dft_real<<<cdiv((long)2 * nk * 32, 256), 256, 0, s>>>(c->xy, 2, 2, n, (const double2*)c->twn,
                                                           (double2*)c->icoef);
   double mg = BOX_MARGIN * h;
-  k_fine_samples<<<cdiv((long)M * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, M, (const double2*)c->twM, c->fine,
-                                                         c->xmin + mg, c->xmax - mg, c->ymin + mg,
-                                                         c->ymax - mg, c->flags);
+  const int logn = ilog2_exact(n);
+  const size_t fsm = 3 * sizeof(double2) * (size_t)n;
+  if (logn >= 4 && fsm <= FINE_FFT_SMEM && SUBSAMPLES == 8)
+    k_fine_fft<<<SUBSAMPLES, 256, fsm, s>>>((const double2*)c->icoef, n, logn, (const double2*)c->twn,
+                                            (const double2*)c->twM, c->fine, c->xmin + mg, c->xmax - mg,
+                                            c->ymin + mg, c->ymax - mg, c->flags);
+  else
+    k_fine_samples<<<cdiv((long)M * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, M, (const double2*)c->twM,
+                                                           c->fine, c->xmin + mg, c->xmax - mg, c->ymin + mg,
+                                                           c->ymax - mg, c->flags);
   k_seg_count<<<cdiv(2 * M, 256), 256, 0, s>>>(c->fine, M, c->xmin, c->ymin, h, N, c->seg_count);
   k_scan<<<1, 1024, 0, s>>>(c->seg_count, c->seg_off, 2 * M);
   KFBI_TRY(cudaMemcpyAsync(&c->host_counts[0], c->seg_off + 2 * M, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -328,6 +328,8 @@ inline int ilog2(int v) {
   while ((1 << l) < v) ++l;
   return l;
 }
+// log2 v for a power of two v >= 1, else -1
+inline int ilog2_exact(int v) { return v >= 1 && (v & (v - 1)) == 0 ? ilog2(v) : -1; }
 
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
@@ -388,6 +390,9 @@ constexpr size_t BOXK_MAX_BYTES = (size_t)1 << 30;
 // with zeros
 __host__ __device__ inline int box_ld(int n) { return (n + 3) & ~3; }
 kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n);
+// largest dynamic shared memory of the FFT-based fine sampling (node counts up to 4096)
+constexpr size_t FINE_FFT_SMEM = 3 * 16 * (size_t)4096;
+kfbi_status geometry_setup_attributes();
 
 // graph building blocks shared by the single solve and the batch (kfbi_gmres.cu)
 kfbi_status cap_begin(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd);
