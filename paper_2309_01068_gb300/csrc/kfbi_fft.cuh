@@ -30,33 +30,8 @@ __device__ __forceinline__ V2<T> csub(V2<T> a, V2<T> b) {
 // w^{r jm N / (4 Ns)} at [off + (r-1) Ns + jm] (w = e^{-2 pi i / N}, r = 1..3, off advancing by
 // 3 Ns per stage) so that neighbouring threads read neighbouring twiddles; the inverse
 // conjugates them (no 1/N). Returns the buffer with the result.
-// radix-4 butterfly of item j with span Ns (lNs = log2 Ns); s and d point at the sequence
-template <typename T, bool INV>
-__device__ __forceinline__ void fft_bfly4(const V2<T>* s, V2<T>* d, int j, int q, int Ns, int lNs, const V2<T>* tw) {
-  const int jm = j & (Ns - 1);
-  V2<T> v0 = s[j], v1 = s[j + q], v2 = s[j + 2 * q], v3 = s[j + 3 * q];
-  if (jm != 0) {
-    V2<T> w1 = tw[jm], w2 = tw[Ns + jm], w3 = tw[2 * Ns + jm];
-    if (INV) {
-      w1.y = -w1.y;
-      w2.y = -w2.y;
-      w3.y = -w3.y;
-    }
-    v1 = cmul(v1, w1);
-    v2 = cmul(v2, w2);
-    v3 = cmul(v3, w3);
-  }
-  const V2<T> a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), t3 = csub(v1, v3);
-  const V2<T> a3 = INV ? V2<T>{-t3.y, t3.x} : V2<T>{t3.y, -t3.x};  // (+/- i)(v1 - v3)
-  const int o = ((j >> lNs) << (lNs + 2)) + jm;
-  d[o] = cadd(a0, a2);
-  d[o + Ns] = cadd(a1, a3);
-  d[o + 2 * Ns] = csub(a0, a2);
-  d[o + 3 * Ns] = csub(a1, a3);
-}
-
-template <typename T, bool INV>
-__device__ __forceinline__ V2<T>* fft_run(V2<T>* a, V2<T>* b, int P, int N, int logN, const V2<T>* stw) {
+template <typename T>
+__device__ V2<T>* fft_stockham(V2<T>* a, V2<T>* b, int P, int N, int logN, const V2<T>* stw, bool inverse) {
   V2<T>* src = a;
   V2<T>* dst = b;
   int Ns = 1;
@@ -64,8 +39,8 @@ __device__ __forceinline__ V2<T>* fft_run(V2<T>* a, V2<T>* b, int P, int N, int 
     const int h = N >> 1;
     for (int t = threadIdx.x; t < P * h; t += blockDim.x) {
       int p = t >> (logN - 1), j = t & (h - 1);
-      const V2<T>* s = src + p * N;
-      V2<T>* d = dst + p * N;
+      const V2<T>* s = src + (long)p * N;
+      V2<T>* d = dst + (long)p * N;
       V2<T> v0 = s[j], v1 = s[j + h];
       d[2 * j] = cadd(v0, v1);
       d[2 * j + 1] = csub(v0, v1);
@@ -77,32 +52,33 @@ __device__ __forceinline__ V2<T>* fft_run(V2<T>* a, V2<T>* b, int P, int N, int 
   const int q = N >> 2;
   const int lq = logN - 2;
   int off = 0;
-  if ((int)blockDim.x == P * q) {
-    // one butterfly per thread in every stage: its sequence and item do not change
-    const int t = threadIdx.x, base = (t >> lq) * N, j = t & (q - 1);
-    for (; Ns < N; off += 3 * Ns, Ns <<= 2) {
-      fft_bfly4<T, INV>(src + base, dst + base, j, q, Ns, __ffs(Ns) - 1, stw + off);
-      __syncthreads();
-      V2<T>* tmp = src; src = dst; dst = tmp;
-    }
-    return src;
-  }
   for (; Ns < N; off += 3 * Ns, Ns <<= 2) {
     const int lNs = __ffs(Ns) - 1;
     for (int t = threadIdx.x; t < P * q; t += blockDim.x) {
-      const int base = (t >> lq) * N;
-      fft_bfly4<T, INV>(src + base, dst + base, t & (q - 1), q, Ns, lNs, stw + off);
+      int p = t >> lq, j = t & (q - 1);
+      const V2<T>* s = src + (long)p * N;
+      V2<T>* d = dst + (long)p * N;
+      int jm = j & (Ns - 1);
+      V2<T> v0 = s[j], v1 = s[j + q], v2 = s[j + 2 * q], v3 = s[j + 3 * q];
+      if (jm != 0) {
+        V2<T> w1 = stw[off + jm], w2 = stw[off + Ns + jm], w3 = stw[off + 2 * Ns + jm];
+        if (inverse) { w1.y = -w1.y; w2.y = -w2.y; w3.y = -w3.y; }
+        v1 = cmul(v1, w1);
+        v2 = cmul(v2, w2);
+        v3 = cmul(v3, w3);
+      }
+      V2<T> a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), t3 = csub(v1, v3);
+      V2<T> a3 = inverse ? V2<T>{-t3.y, t3.x} : V2<T>{t3.y, -t3.x};  // (+/- i)(v1 - v3)
+      int o = ((j >> lNs) << (lNs + 2)) + jm;
+      d[o] = cadd(a0, a2);
+      d[o + Ns] = cadd(a1, a3);
+      d[o + 2 * Ns] = csub(a0, a2);
+      d[o + 3 * Ns] = csub(a1, a3);
     }
     __syncthreads();
     V2<T>* tmp = src; src = dst; dst = tmp;
   }
   return src;
-}
-
-template <typename T>
-__device__ __forceinline__ V2<T>* fft_stockham(V2<T>* a, V2<T>* b, int P, int N, int logN, const V2<T>* stw,
-                                               bool inverse) {
-  return inverse ? fft_run<T, true>(a, b, P, N, logN, stw) : fft_run<T, false>(a, b, P, N, logN, stw);
 }
 
 // number of staged twiddles of fft_stockham for N = 2^logN (at most N)
