@@ -88,4 +88,21 @@ __host__ __device__ inline int staged_count(int N, int logN) {
   return c;
 }
 
+// staged twiddles of fft_stockham for a length-n transform built from the roots
+// roots[m] = e^{2 pi i m / n}: entry off + (r - 1) Ns + jm of the stage with span Ns holds
+// w^{r jm n / (4 Ns)}, w = e^{-2 pi i / n} = conj roots[1]
+__device__ __forceinline__ void stage_twiddles_from_roots(const double2* roots, V2<double>* stw, int n, int logn) {
+  const int cnt = staged_count(n, logn);
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    int off = 0, Ns = (logn & 1) ? 2 : 1;
+    while (t >= off + 3 * Ns) {
+      off += 3 * Ns;
+      Ns <<= 2;
+    }
+    const int r = (t - off) / Ns + 1, jm = (t - off) - (r - 1) * Ns;
+    const double2 w = roots[(long)r * jm * (n / (4 * Ns))];
+    stw[t] = V2<double>{w.x, -w.y};
+  }
+}
+
 }  // namespace kfbi

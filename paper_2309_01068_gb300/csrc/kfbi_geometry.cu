@@ -175,19 +175,7 @@ __global__ void k_fine_fft(const double2* coef, int n, int logn, const double2* 
   const int r = blockIdx.x, M = 8 * n, nk = n / 2 + 1, K = (n - 1) / 2;
   const double2* cx = coef;
   const double2* cy = coef + nk;
-  // staged twiddles of fft_stockham with w = e^{-2 pi i / n} = conj twn[1]: for its stage
-  // with span Ns, entry off + (r' - 1) Ns + jm holds w^{r' jm n / (4 Ns)}
-  const int cnt = staged_count(n, logn);
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    int off = 0, Ns = (logn & 1) ? 2 : 1;
-    while (t >= off + 3 * Ns) {
-      off += 3 * Ns;
-      Ns <<= 2;
-    }
-    const int rr = (t - off) / Ns + 1, jm = (t - off) - (rr - 1) * Ns;
-    const double2 w = twn[(long)rr * jm * (n / (4 * Ns))];
-    stw[t] = V2<double>{w.x, -w.y};
-  }
+  stage_twiddles_from_roots(twn, stw, n, logn);
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     V2<double> v{0.0, 0.0};
     if (k == 0) {
