@@ -71,8 +71,6 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
   cudaFree(c->cr_kind); cudaFree(c->cr_line); cudaFree(c->cr_seg); cudaFree(c->cr_first);
   cudaFree(c->cr_alpha); cudaFree(c->cr_xi); cudaFree(c->tgeo); cudaFree(c->tgeo_f); cudaFree(c->irr);
   cudaFree(c->tstart); cudaFree(c->tstart_f); cudaFree(c->jumps);
-  cudaFree(c->corr_d); cudaFree(c->corr_f); cudaFree(c->corr_si);
-  c->corr_d = nullptr; c->corr_f = nullptr; c->corr_si = nullptr;
   c->cr_kind = c->cr_line = c->cr_seg = c->cr_first = nullptr;
   c->cr_alpha = c->cr_xi = nullptr;
   c->tgeo = nullptr; c->tgeo_f = nullptr; c->irr = nullptr;
@@ -88,9 +86,6 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
   KFBI_CHECK(dalloc(&c->tgeo_f, (size_t)cap + c->max_nodes));
   int cap_irr = 2 * cap + 64;
   KFBI_CHECK(dalloc(&c->irr, cap_irr));
-  KFBI_CHECK(dalloc(&c->corr_d, cap_irr));
-  KFBI_CHECK(dalloc(&c->corr_f, cap_irr));
-  KFBI_CHECK(dalloc(&c->corr_si, cap_irr));
   KFBI_CHECK(dalloc(&c->tstart, 2 * (size_t)TSTART_STRIDE * ((size_t)cap + c->max_nodes)));
   KFBI_CHECK(dalloc(&c->tstart_f, 2 * (size_t)TSTART_STRIDE * ((size_t)cap + c->max_nodes)));
   KFBI_CHECK(dalloc(&c->jumps, 6 * ((size_t)cap + c->max_nodes)));
@@ -102,7 +97,7 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
 static void free_all(kfbi_ctx* c) {
   void* ptrs[] = {c->sintab, c->sintab_f, c->lam, c->lam_f, c->twN, c->twN_f, c->xy, c->twn, c->icoef, c->fine, c->twM,
                   c->seg_count, c->seg_off, c->cr_kind, c->cr_line, c->cr_seg, c->cr_first, c->cr_alpha, c->cr_xi,
-                  c->tgeo, c->tgeo_f, c->stencil_f, c->dens_f, c->stw, c->stw_d, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->corr_d, c->corr_f, c->corr_si, c->stencil,
+                  c->tgeo, c->tgeo_f, c->stencil_f, c->dens_f, c->stw, c->stw_d, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->stencil,
                   c->probe_mark, c->prow_cnt, c->prow_ptr, c->probe_i, c->probe_j, c->flags, c->counts, c->dcoef, c->dint,
                   c->boxg, c->facespec, c->spec, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack, c->boxK, c->boxK_f,
                   c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gVf, c->gpart, c->gw,

@@ -396,7 +396,7 @@ __global__ void k_box_gemv(const T* K, int ld, const T* phi, int n, int rows, T*
 __device__ __forceinline__ int mk_pos(int j, int N) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
 
 // pi / (2N) in float32, the argument unit of tsin
-__host__ __device__ __forceinline__ float qscale(int N) { return 1.57079632679489662f / (float)N; }
+__device__ __forceinline__ float qscale(int N) { return 1.57079632679489662f / (float)N; }
 
 // copies the staged twiddles to shared memory (before the block's first __syncthreads)
 template <typename T>
@@ -559,45 +559,14 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
   }
 }
 
-// Right-hand-side correction of every irregular node (the per-node part of k_row_forward):
-//   C = sign/h^2 sum_arms (J0 + d J1 + d^2/2 J2), and si = 2 i + 1. The column kernel then
-// forms the row transform of the corrected right-hand side itself.
-template <typename T>
-__global__ void k_corrections(int nirr, const IrrNode* irr, const T* J, T inv_h2, T* cv, int* csi, const int* skip) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  pdl_wait();
-  pdl_trigger();
-  if (*skip || t >= nirr) return;
-  const IrrNode& node = irr[t];
-  T sum = 0;
-  for (int a = 0; a < 4; ++a) {
-    int tg = node.target[a];
-    if (tg < 0) continue;
-    const T* jj = J + (long)tg * 6;
-    T d = irr_d(node, a, T(0));
-    T j1 = a < 2 ? jj[1] : jj[2];
-    T j2 = a < 2 ? jj[3] : jj[4];
-    sum += jj[0] + d * j1 + (T)0.5 * d * d * j2;
-  }
-  csi[t] = 2 * node.i + 1;
-  cv[t] = irr_sign(node, T(0)) * inv_h2 * sum;
-}
-
 // --------------------------------------------------------------------------- column solve
 // For each column k of spec (x-mode k): forward transform along y, divide by
 // lam_y(l) + lam_x(k) - kappa, inverse transform along y, in place. A block owns P column
 // pairs; pair p holds columns (k0 + 2p, k0 + 2p + 1) as the real and imaginary parts of
 // one complex FFT. Two shared buffers alternate between the FFT stages.
-//
-// Input: with row_ptr = nullptr the row-transformed right-hand side in spec; otherwise the
-// block forms it for its columns k: spec[j][k] = sum over the irregular nodes q of row j of
-// cv[q] S_k(csi[q]) (S_k the DST-II/DCT-II basis from the sine table), plus, for free-space
-// box data, w_j S_k(0) + e_j S_k(N-1) (west and east cells, boxg) and the face rows'
-// transforms (face) at j = 0 and N - 1. Output in spec either way.
 template <typename T>
 __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, const T* tab, const T* lam,
-                            T kappa, T* spec, const int* row_ptr, const T* cv, const int* csi, const T* boxg,
-                            const T* face, float scale, const int* skip) {
+                            T kappa, T* spec, const int* skip) {
   pdl_wait();
   pdl_trigger();
   if (*skip) return;
@@ -626,26 +595,7 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int t = t0 + u * (int)blockDim.x + (int)threadIdx.x;
-      if (t >= tot) continue;
-      const int j = t >> lw, k = k0 + (t & (W - 1));
-      if (row_ptr == nullptr) {
-        buf[u] = spec[(long)j * N + k];
-        continue;
-      }
-      T a = 0;
-      const int qe = row_ptr[j + 1];
-      if (dct)
-        for (int q = row_ptr[j]; q < qe; ++q) a += cv[q] * tsin(tab, k * csi[q] + N, N, scale);
-      else
-        for (int q = row_ptr[j]; q < qe; ++q) a += cv[q] * tsin(tab, (k + 1) * csi[q], N, scale);
-      if (boxg != nullptr) {
-        const T w = boxg[j], ea = boxg[N + j];
-        if (dct) a += w * tsin(tab, k + N, N, scale) + ea * tsin(tab, k * (2 * N - 1) + N, N, scale);
-        else a += w * tsin(tab, k + 1, N, scale) + ea * tsin(tab, (k + 1) * (2 * N - 1), N, scale);
-        if (j == 0) a += face[k];
-        else if (j == N - 1) a += face[N + k];
-      }
-      buf[u] = a;
+      if (t < tot) buf[u] = spec[(long)(t >> lw) * N + k0 + (t & (W - 1))];
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -913,11 +863,8 @@ static int col_threads(int N, int P) {
   return t < 32 ? 32 : (t > 1024 ? 1024 : t);
 }
 
-// rows = true: the column kernel forms the row transform from the irregular-node corrections
-// and the box data (apply); false: spec holds it (dense right-hand side)
 template <typename T>
-static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip, bool rows = false,
-                                    const T* boxg = nullptr, const T* face = nullptr) {
+static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
   const int N = c->N;
   const int P = col_pairs<T>(N, c->col_P);
   size_t smem = col_smem<T>(N, P);
@@ -925,9 +872,7 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip, bool 
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
   KFBI_TRY(launch_k(c->use_pdl && !rec, k_col_solve<T>, dim3(N / (2 * P)), dim3(col_threads(N, P)), smem, c->stream, N,
                     c->logN, P, (int)(c->boxbc == KFBI_BOX_NEUMANN0), Tabs<T>::stw(c), Tabs<T>::sin(c), Tabs<T>::lam(c),
-                    (T)c->kappa, spec, rows ? (const int*)c->row_ptr : nullptr,
-                    rows ? (sizeof(T) == 8 ? (const T*)c->corr_d : (const T*)c->corr_f) : nullptr,
-                    (const int*)c->corr_si, boxg, face, qscale(N), skip));
+                    (T)c->kappa, spec, skip));
   launched(c, 1);
   if (rec) {
     KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used + 1], c->stream));
@@ -1026,14 +971,11 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, false>, dim3(cdiv((long)ntg * 32, 256)), dim3(256), 0, s,
                       (const V2<T>*)coef, n, ntg, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
   launched(c, 2);
-  T* cv = sizeof(T) == 8 ? (T*)c->corr_d : (T*)c->corr_f;
-  if (c->n_irr > 0) {
-    KFBI_TRY(launch_k(c->use_pdl, k_corrections<T>, dim3(cdiv(c->n_irr, 256)), dim3(256), 0, s, c->n_irr,
-                      (const IrrNode*)c->irr, (const T*)J, (T)(1.0 / (c->h * c->h)), cv, c->corr_si, skip));
-    launched(c, 1);
-  }
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
-  KFBI_CHECK(launch_col_solve<T>(c, spec, skip, true, fs ? (const T*)boxg : nullptr, (const T*)face));
+  k_row_forward<T><<<N, ROW_THREADS, 0, s>>>(N, dct, c->row_ptr, c->irr, J, (T)(1.0 / (c->h * c->h)), fs ? boxg : nullptr,
+                                             face, tab, scale, spec, skip);
+  launched(c, 1);
+  KFBI_CHECK(launch_col_solve<T>(c, spec, skip));
   if (c->n_probe > 0) {
     KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(cdiv((long)c->n_probe * 32, 256)), dim3(256), 0, s, N, dct,
                       c->n_probe, (const int*)c->probe_j, (const int*)c->probe_i, (const T*)spec, tab, scale, pval,
@@ -1221,8 +1163,7 @@ static kfbi_status grid_solve_noalloc_impl(int N, double h, double kappa, int bo
   const int P = col_pairs<double>(N);
   size_t sm_col = col_smem<double>(N, P);  // <= 28 KB for N <= 512
   k_col_solve<double><<<N / (2 * P), col_threads(N, P), sm_col, s>>>(N, logN, P, dct, (const V2<double>*)tw, tab, lam,
-                                                                  kappa, spec, nullptr, nullptr, nullptr, nullptr,
-                                                                  nullptr, 0.0f, flag);
+                                                                  kappa, spec, flag);
   k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 1, (const V2<double>*)tw, tab, nullptr, spec, u);
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;

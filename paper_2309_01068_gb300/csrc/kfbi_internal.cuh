@@ -190,11 +190,6 @@ struct kfbi_ctx {
   int* rowcnt = nullptr;        // [N + 1]
   int* row_ptr = nullptr;       // [N + 1]
   kfbi::IrrNode* irr = nullptr; // [cap_irr]
-  // per irregular node (row-major, rows by row_ptr): its right-hand-side correction C (Sec.
-  // 4.2, float64 and float32) and 2 i + 1 (the column's argument factor of the sine table)
-  double* corr_d = nullptr;     // [cap_irr]
-  float* corr_f = nullptr;      // [cap_irr]
-  int* corr_si = nullptr;       // [cap_irr]
   kfbi::Stencil* stencil = nullptr;  // [max_nodes]
   kfbi::StencilF* stencil_f = nullptr;
   float* dens_f = nullptr;      // [max_nodes] float32 copy of the apply's density
