@@ -299,11 +299,12 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             only that size (the five-kernel form when it does not fit).
  *   KFBI_OPT_COL_PAIRS        0 (default, 2): column pairs per block of the float32 column
  *                             transform kernel, 1, 2 or 4 (bounded by its shared memory).
- *   KFBI_OPT_PDL              0 (default): plain stream order; 1: consecutive kernels of an
- *                             apply and of a GMRES iteration use programmatic dependent launch
- *                             (a kernel starts while its predecessor finishes and waits on the
- *                             device before it reads the predecessor's output). Batch graphs
- *                             are always built without it.
+ *   KFBI_OPT_PDL              1 (default): consecutive kernels of an apply and of a GMRES
+ *                             iteration use programmatic dependent launch (a kernel is
+ *                             scheduled as its predecessor's blocks exit, reads its static
+ *                             inputs, and waits on the device before it reads the
+ *                             predecessor's output); 0: plain stream order. Batch graphs are
+ *                             always built without it.
  *   KFBI_OPT_BOX_MATRIX       1 (default): with KFBI_BOX_FREESPACE_DL, kfbi_set_interface
  *                             tabulates the box quadrature's kernel between the interface
  *                             nodes and the 4 N face points (4 N max_nodes values in float64

@@ -79,7 +79,6 @@ __device__ __forceinline__ float irr_sign(const IrrNode& q, float) { return q.si
 
 __global__ void k_to_float(const double* a, float* b, int n, const int* skip) {
   pdl_wait();
-  pdl_trigger();
   if (*skip) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -95,7 +94,6 @@ template <typename T, bool SMEM, typename S_t>
 __global__ void k_dens_coef(const T* phi, int n, const V2<T>* tw, const S_t* st, V2<T>* coef, T* dint,
                             const int* skip) {
   pdl_wait();
-  pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   __shared__ T red[32];
@@ -229,7 +227,6 @@ __global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const G* tg, c
     q = ts[33];
   }
   pdl_wait();
-  pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   const int chunk = jump_chunk(n);
@@ -271,7 +268,6 @@ template <typename T, typename T4, bool SMEM>
 __global__ void k_box_data(const T* phi, int n, const T4* npack, int N, double xmin, double xmax, double ymin,
                            double ymax, double h, T scale, T* boxg, const int* skip) {
   pdl_wait();
-  pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   T4* sp = (T4*)smem_raw;  // (x, y, phi y_a, -phi x_a)
@@ -366,7 +362,6 @@ __device__ __forceinline__ void load4(const double* p, double v[4]) {
 template <typename T, bool VEC>
 __global__ void k_box_gemv(const T* K, int ld, const T* phi, int n, int rows, T* boxg, const int* skip) {
   pdl_wait();
-  pdl_trigger();
   if (*skip) return;
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -444,7 +439,6 @@ template <typename T>
 __global__ void k_face_dst(int N, int logN, int dct, const V2<T>* tw, const T* tab, const T* boxg, T* out,
                            const int* skip) {
   pdl_wait();
-  pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
@@ -493,7 +487,6 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
                                                             const T* facespec, const T* tab, float scale, T* spec,
                                                             const int* skip) {
   pdl_wait();
-  pdl_trigger();
   if (*skip) return;
   __shared__ int si[ROW_CAP];
   __shared__ T sv[ROW_CAP];
@@ -568,7 +561,6 @@ template <typename T>
 __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, const T* tab, const T* lam,
                             T kappa, T* spec, const int* skip) {
   pdl_wait();
-  pdl_trigger();
   if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
@@ -667,7 +659,6 @@ __global__ void k_probe_values(int N, int dct, int n_probe, const int* probe_j, 
     i = probe_i[q];
   }
   pdl_wait();
-  pdl_trigger();
   if (*skip || q >= n_probe) return;
   const int mask = 4 * N - 1, m = 2 * i + 1;
   const T* row = spec + (long)j * N;
@@ -794,7 +785,6 @@ __global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const
     }
   }
   pdl_wait();
-  pdl_trigger();
   if (*skip) return;
   if (p >= n) return;
   const T* J = Jn ? Jn + (long)p * 6 : nullptr;

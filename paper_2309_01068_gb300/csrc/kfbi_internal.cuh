@@ -269,7 +269,7 @@ struct kfbi_ctx {
     int f32 = 0;
   } irgraph[3][2];
   bool gm_cluster = true;       // allow the cluster form
-  bool use_pdl = false;         // programmatic dependent launch between the kernels of a body
+  bool use_pdl = true;          // programmatic dependent launch between the kernels of a body
   int force_cs = 0;             // cluster size of the Gram-Schmidt kernel: 0 automatic, 8 or 16
   int col_P = 0;                // column pairs per block of the float32 column kernel (0 automatic)
   int cfg_version = 0;          // bumped by every option that changes the launched kernels
@@ -336,14 +336,15 @@ inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 inline void launched(kfbi_ctx* c, int k) { c->launches += k; }
 
 // Programmatic dependent launch: a kernel launched with launch_k(pdl = true) may start while
-// the previous kernel in its stream is still running. It first reads only data that was
+// the previous kernel in its stream is finishing (its blocks are scheduled as the previous
+// kernel's blocks exit; no kernel signals its successor earlier, which measured slower: the
+// early blocks took SM slots from the running kernel). It first reads only data that was
 // complete before that kernel started (tables, geometry, the control block), then waits with
-// pdl_wait() for the previous kernel to finish and its writes to be visible, and lets its own
-// successor start with pdl_trigger(). Every kernel calls pdl_wait() before it reads or writes
-// anything its predecessor touches and before it returns, so a finished kernel implies that
-// all kernels before it have finished. Without the attribute both are no-ops.
+// pdl_wait() for the previous kernel to finish and its writes to be visible. Every kernel calls
+// pdl_wait() before it reads or writes anything its predecessor touches and before it
+// returns, so a finished kernel implies that all kernels before it have finished. Without the
+// attribute pdl_wait() is a no-op.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_k(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
