@@ -93,17 +93,17 @@ __global__ void k_to_float(const double* a, float* b, int n, const int* skip) {
 template <typename T, bool SMEM, typename S_t>
 __global__ void k_dens_coef(const T* phi, int n, const V2<T>* tw, const S_t* st, V2<T>* coef, T* dint,
                             const int* skip) {
-  pdl_wait();
-  if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   __shared__ T red[32];
   V2<T>* stw = (V2<T>*)smem_raw;
   T* sphi = (T*)(stw + n);
+  // the twiddles are fixed with the interface: staged before the wait for the previous kernel
+  if (SMEM)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) stw[j] = tw[j];
+  pdl_wait();
+  if (*skip) return;
   if (SMEM) {
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      stw[j] = tw[j];
-      sphi[j] = phi[j];
-    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) sphi[j] = phi[j];
     __syncthreads();
   }
   int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -438,13 +438,13 @@ __device__ __forceinline__ void dct_cs(const T* tab, int N, int m, T& c, T& s) {
 template <typename T>
 __global__ void k_face_dst(int N, int logN, int dct, const V2<T>* tw, const T* tab, const T* boxg, T* out,
                            const int* skip) {
-  pdl_wait();
-  if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
   V2<T>* B = A + N;
   V2<T>* sTw = B + N;  // staged twiddles (one global round trip instead of one per stage)
-  stage_twiddles(tw, sTw, staged_count(N, logN));
+  stage_twiddles(tw, sTw, staged_count(N, logN));  // fixed with the context: before the wait
+  pdl_wait();
+  if (*skip) return;
   const T* gs = boxg + 2 * N;
   const T* gn = boxg + 3 * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -479,6 +479,27 @@ __global__ void k_face_dst(int N, int logN, int dct, const V2<T>* tw, const T* t
 //   C = sign/h^2 sum_arms (J0 + d J1 + d^2/2 J2), J1, J2 = ([u_x], [u_xx]) on horizontal
 //   arms and ([u_y], [u_yy]) on vertical arms, sign = -1 at an Omega+ node, +1 at Omega-.
 constexpr int ROW_CAP = 512;
+
+// the fields of an irregular node that its correction needs, in registers
+template <typename T>
+struct IrrRegs {
+  int tg[4];
+  T d[4];
+  T sign;
+  int i;
+};
+template <typename T>
+__device__ __forceinline__ IrrRegs<T> irr_regs(const IrrNode& q) {
+  IrrRegs<T> r;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    r.tg[a] = q.target[a];
+    r.d[a] = irr_d(q, a, T(0));
+  }
+  r.sign = irr_sign(q, T(0));
+  r.i = q.i;
+  return r;
+}
 constexpr int ROW_THREADS = 256;  // N <= 4096 gives at most 16 outputs per thread
 
 template <typename T>
@@ -486,12 +507,16 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
                                                             const T* J, T inv_h2, const T* boxg,
                                                             const T* facespec, const T* tab, float scale, T* spec,
                                                             const int* skip) {
-  pdl_wait();
-  if (*skip) return;
   __shared__ int si[ROW_CAP];
   __shared__ T sv[ROW_CAP];
   const int j = blockIdx.x;
+  // the row's irregular nodes are fixed with the interface: this thread's first one is read
+  // before the wait for the previous kernel (the jumps it needs come after)
   const int b = row_ptr[j], e = row_ptr[j + 1];
+  IrrRegs<T> first{};
+  if ((int)threadIdx.x < e - b) first = irr_regs<T>(irr[b + threadIdx.x]);
+  pdl_wait();
+  if (*skip) return;
   const int per = (N + ROW_THREADS - 1) / ROW_THREADS;
   T acc[16];
 #pragma unroll
@@ -500,19 +525,20 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
     int cnt = min(ROW_CAP, e - c0);
     __syncthreads();
     for (int t = threadIdx.x; t < cnt; t += ROW_THREADS) {
-      const IrrNode& node = irr[c0 + t];
+      const IrrRegs<T> node = (c0 == b && t == (int)threadIdx.x) ? first : irr_regs<T>(irr[c0 + t]);
       T sum = 0;
+#pragma unroll
       for (int a = 0; a < 4; ++a) {
-        int tg = node.target[a];
+        const int tg = node.tg[a];
         if (tg < 0) continue;
         const T* jj = J + (long)tg * 6;
-        T d = irr_d(node, a, T(0));
-        T j1 = a < 2 ? jj[1] : jj[2];
-        T j2 = a < 2 ? jj[3] : jj[4];
+        const T d = node.d[a];
+        const T j1 = a < 2 ? jj[1] : jj[2];
+        const T j2 = a < 2 ? jj[3] : jj[4];
         sum += jj[0] + d * j1 + (T)0.5 * d * d * j2;
       }
       si[t] = 2 * node.i + 1;
-      sv[t] = irr_sign(node, T(0)) * inv_h2 * sum;
+      sv[t] = node.sign * inv_h2 * sum;
     }
     __syncthreads();
 #pragma unroll
@@ -560,8 +586,6 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
 template <typename T>
 __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, const T* tab, const T* lam,
                             T kappa, T* spec, const int* skip) {
-  pdl_wait();
-  if (*skip) return;
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
   V2<T>* B = A + (long)P * N;
@@ -572,15 +596,18 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
   const T* sLam = STAGE ? (const T*)(sCs + N / 2 + 1) : lam;  // eigenvalues
   const int k0 = blockIdx.x * (2 * P);
   const int W = 2 * P, lw = __ffs(W) - 1;
-  // every global read of the block is issued here, before the first barrier: the column
-  // data through a register buffer (eight loads in flight per thread), the twiddles and
-  // the eigenvalues straight into shared memory
+  // every global read of the block is issued before the first barrier: the grid's tables
+  // (twiddles, eigenvalues, DCT rotations, fixed with the context) straight into shared
+  // memory before the wait for the previous kernel, then the column data through a register
+  // buffer (eight loads in flight per thread)
   stage_twiddles(tw, sTw, nst);
   if (STAGE) {
     T* w = (T*)(sCs + N / 2 + 1);
     for (int t = threadIdx.x; t < N; t += blockDim.x) w[t] = lam[t];
     for (int m = threadIdx.x; m <= N / 2; m += blockDim.x) dct_cs<T>(tab, N, m, sCs[m].x, sCs[m].y);
   }
+  pdl_wait();
+  if (*skip) return;
   const int tot = N * W;
   for (int t0 = 0; t0 < tot; t0 += 8 * (int)blockDim.x) {
     T buf[8];
@@ -945,8 +972,10 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   }
   const size_t smd = (size_t)n * (sizeof(V2<T>) + sizeof(T));
   if (smd <= SMEM_STAGE_MAX) {
-    k_dens_coef<T, true><<<cdiv((long)nk * 32, 256), 256, smd, s>>>(dens_t, n, Tabs<T>::twn(c), Tabs<T>::stencil(c),
-                                                                    coef, want_int ? dint_t : nullptr, skip);
+    using SD = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(c))>::type>::type;
+    KFBI_TRY(launch_k(c->use_pdl, k_dens_coef<T, true, SD>, dim3(cdiv((long)nk * 32, 256)), dim3(256), smd, s,
+                      (const T*)dens_t, n, Tabs<T>::twn(c), Tabs<T>::stencil(c), (V2<T>*)coef,
+                      (T*)(want_int ? dint_t : nullptr), skip));
   } else {
     k_dens_coef<T, false><<<cdiv((long)nk * 32, 256), 256, 0, s>>>(dens_t, n, Tabs<T>::twn(c), Tabs<T>::stencil(c),
                                                                    coef, want_int ? dint_t : nullptr, skip);
@@ -962,8 +991,9 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
                       (const V2<T>*)coef, n, ntg, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
   launched(c, 2);
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
-  k_row_forward<T><<<N, ROW_THREADS, 0, s>>>(N, dct, c->row_ptr, c->irr, J, (T)(1.0 / (c->h * c->h)), fs ? boxg : nullptr,
-                                             face, tab, scale, spec, skip);
+  KFBI_TRY(launch_k(c->use_pdl, k_row_forward<T>, dim3(N), dim3(ROW_THREADS), 0, s, N, dct, (const int*)c->row_ptr,
+                    (const IrrNode*)c->irr, (const T*)J, (T)(1.0 / (c->h * c->h)), (const T*)(fs ? boxg : nullptr),
+                    (const T*)face, tab, scale, spec, skip));
   launched(c, 1);
   KFBI_CHECK(launch_col_solve<T>(c, spec, skip));
   if (c->n_probe > 0) {
