@@ -325,25 +325,41 @@ __global__ void k_box_data(const T* phi, int n, const T4* npack, int N, double x
 // -2 g / h^2), so that boxg = K phi. Computed once per interface in float64 with a float32
 // copy, rows of box_ld(n) entries (zeros past n); every apply then reads it (4N n values)
 // instead of re-evaluating it.
+// Thread per (node column l, face, chunk of BOXK_CHUNK face points): the node's offset along
+// the face normal and its products are formed once, each entry then costs a few float64
+// operations and one correctly rounded reciprocal (__drcp_rn).
+constexpr int BOXK_CHUNK = 64;
 __global__ void k_box_matrix(int N, int n, int ld, const double4_32a* npack, double xmin, double xmax, double ymin,
                              double ymax, double h, double scale, double* K, float* Kf) {
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long)4 * N * ld) return;
-  const int w = (int)(t / ld), l = (int)(t - (long)w * ld);
-  double k = 0.0;
-  if (l < n) {
-    const int face = w / N, idx = w - face * N;
-    double px, py;
-    if (face == 0) { px = xmin; py = grid_coord(ymin, h, idx); }
-    else if (face == 1) { px = xmax; py = grid_coord(ymin, h, idx); }
-    else if (face == 2) { px = grid_coord(xmin, h, idx); py = ymin; }
-    else { px = grid_coord(xmin, h, idx); py = ymax; }
-    const double4_32a q = npack[l];
-    const double dx = q.x - px, dy = q.y - py;
-    k = scale * (dx * q.z + dy * q.w) / (dx * dx + dy * dy);
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int face = blockIdx.y;
+  const int i0 = blockIdx.z * BOXK_CHUNK, i1 = min(N, i0 + BOXK_CHUNK);
+  if (l >= ld) return;
+  double* Kr = K + (long)face * N * ld + l;
+  float* Kfr = Kf + (long)face * N * ld + l;
+  if (l >= n) {
+    for (int idx = i0; idx < i1; ++idx) {
+      Kr[(long)idx * ld] = 0.0;
+      Kfr[(long)idx * ld] = 0.0f;
+    }
+    return;
   }
-  K[t] = k;
-  Kf[t] = (float)k;
+  const double4_32a q = npack[l];
+  // west/east faces: x fixed (offset a along x), y = grid_coord(ymin, h, idx) varies;
+  // south/north faces: y fixed, x varies. (q.z, q.w) = (y_a, -x_a) of the node.
+  const bool vert = face < 2;
+  const double a = vert ? q.x - (face == 0 ? xmin : xmax) : q.y - (face == 2 ? ymin : ymax);
+  const double na = a * (vert ? q.z : q.w);  // normal-offset part of the numerator
+  const double a2 = a * a;
+  const double bq = vert ? q.y : q.x, bz = vert ? q.w : q.z, lo = vert ? ymin : xmin;
+  for (int idx = i0; idx < i1; ++idx) {
+    const double t = bq - grid_coord(lo, h, idx);  // offset along the face
+    const double num = fma(t, bz, na);
+    const double den = fma(t, t, a2);
+    const double k = scale * num * __drcp_rn(den);
+    Kr[(long)idx * ld] = k;
+    Kfr[(long)idx * ld] = (float)k;
+  }
 }
 
 // four consecutive table or density values (16-byte aligned for float, 32 for double)
@@ -1060,9 +1076,10 @@ kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* densi
 }
 
 kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n) {
-  const long tot = (long)4 * c->N * box_ld(n);
+  const int ld = box_ld(n);
   launched(c, 1);
-  k_box_matrix<<<cdiv(tot, 256), 256, 0, c->stream>>>(c->N, n, box_ld(n), (const double4_32a*)c->npack, c->xmin, c->xmax,
+  const dim3 grid(cdiv(ld, 128), 4, cdiv(c->N, BOXK_CHUNK));
+  k_box_matrix<<<grid, 128, 0, c->stream>>>(c->N, n, ld, (const double4_32a*)c->npack, c->xmin, c->xmax,
                                                        c->ymin, c->ymax, c->h, -2.0 / (c->h * c->h * (double)n),
                                                        c->boxK, c->boxK_f);
   KFBI_TRY(cudaGetLastError());
