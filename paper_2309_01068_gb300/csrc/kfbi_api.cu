@@ -230,7 +230,6 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->gev, max_nodes));
   KFBI_CHECK(apply_setup_attributes(c));
   KFBI_CHECK(geometry_setup_attributes());
-  KFBI_CHECK(step_setup_attributes());
   launched(c, 1);
   k_init_tables<<<cdiv(4L * N, 256), 256, 0, c->own>>>(N, c->h, boxbc == KFBI_BOX_NEUMANN0, c->sintab, c->sintab_f,
                                                      c->lam, c->lam_f, c->twN, c->twN_f);

@@ -394,7 +394,6 @@ kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n);
 // largest dynamic shared memory of the FFT-based fine sampling (node counts up to 4096)
 constexpr size_t FINE_FFT_SMEM = 3 * 16 * (size_t)4096;
 kfbi_status geometry_setup_attributes();
-kfbi_status step_setup_attributes();
 
 // graph building blocks shared by the single solve and the batch (kfbi_gmres.cu)
 kfbi_status cap_begin(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd);

@@ -8,7 +8,6 @@
 // transforms are direct DFTs with exact twiddle indexing (one warp per output).
 #include <cmath>
 
-#include "kfbi_fft.cuh"
 #include "kfbi_internal.cuh"
 
 namespace kfbi {
@@ -102,52 +101,6 @@ __global__ void k_st_idft(const double2* coef, int nf, int n, const double2* tw,
   }
   acc = warp_sum(acc);
   if (lane == 0) out[(long)j * stride + q] = acc;
-}
-
-// The same two transforms for a power-of-two n as one shared-memory FFT of length n per
-// function (block q); shared memory A[n] | B[n] | staged twiddles[n] (complex float64).
-__global__ void k_st_dft_fft(const double* f, int stride, int n, int logn, const double2* tw, double2* coef) {
-  extern __shared__ double2 ssm[];
-  V2<double>* A = (V2<double>*)ssm;
-  V2<double>* B = A + n;
-  V2<double>* stw = B + n;
-  const int q = blockIdx.x, nk = n / 2 + 1;
-  stage_twiddles_from_roots(tw, stw, n, logn);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) A[j] = V2<double>{f[(long)j * stride + q], 0.0};
-  __syncthreads();
-  const V2<double>* X = fft_stockham<double>(A, B, 1, n, logn, stw, false);
-  const double inv = 1.0 / (double)n;
-  for (int k = threadIdx.x; k < nk; k += blockDim.x) coef[q * nk + k] = make_double2(X[k].x * inv, X[k].y * inv);
-}
-
-// inverse: the Hermitian spectrum A_k = C_k, A_{n-k} = conj C_k (0 < k < n/2), A_0 and the
-// Nyquist entry real parts, C_k = mult_k c_k, then one inverse FFT
-__global__ void k_st_idft_fft(const double2* coef, int n, int logn, const double2* tw, int mode, double* out,
-                              int stride) {
-  extern __shared__ double2 ssm[];
-  V2<double>* A = (V2<double>*)ssm;
-  V2<double>* B = A + n;
-  V2<double>* stw = B + n;
-  const int q = blockIdx.x, nk = n / 2 + 1, h = n / 2;
-  const double2* c = coef + q * nk;
-  stage_twiddles_from_roots(tw, stw, n, logn);
-  for (int k = threadIdx.x; k <= h; k += blockDim.x) {
-    double2 ck = c[k];
-    if (mode == MODE_D1) {
-      ck = k == h ? make_double2(0.0, 0.0) : make_double2(-(double)k * ck.y, (double)k * ck.x);
-    } else if (mode == MODE_INT) {
-      ck = (k == 0 || k == h) ? make_double2(0.0, 0.0) : make_double2(ck.y / (double)k, -ck.x / (double)k);
-    }
-    if (k == 0 || k == h) {
-      A[k] = V2<double>{ck.x, 0.0};
-    } else {
-      A[k] = V2<double>{ck.x, ck.y};
-      A[n - k] = V2<double>{ck.x, -ck.y};
-    }
-  }
-  __syncthreads();
-  const V2<double>* X = fft_stockham<double>(A, B, 1, n, logn, stw, true);
-  for (int j = threadIdx.x; j < n; j += blockDim.x) out[(long)j * stride + q] = X[j].x;
 }
 
 // X_a = (L / 2 pi)(cos theta, sin theta), theta = alpha + eta
@@ -367,30 +320,6 @@ __global__ void k_twiddles_n_step(int n, double2* tw) {
 
 static int wb(long warps) { return cdiv(warps * 32, 256); }
 
-// the forward and inverse transforms of nf functions: FFTs for a power-of-two n (16 to 4096),
-// else the warp-per-output sums
-static void st_dft(cudaStream_t s, const double* f, int stride, int nf, int n, const double2* tw, double2* coef) {
-  const int logn = ilog2_exact(n);
-  if (logn >= 4 && 3 * sizeof(double2) * (size_t)n <= FINE_FFT_SMEM)
-    k_st_dft_fft<<<nf, 256, 3 * sizeof(double2) * (size_t)n, s>>>(f, stride, n, logn, tw, coef);
-  else
-    k_st_dft<<<wb((long)nf * (n / 2 + 1)), 256, 0, s>>>(f, stride, nf, n, tw, coef);
-}
-static void st_idft(cudaStream_t s, const double2* coef, int nf, int n, const double2* tw, int mode, double* out,
-                    int stride) {
-  const int logn = ilog2_exact(n);
-  if (logn >= 4 && 3 * sizeof(double2) * (size_t)n <= FINE_FFT_SMEM)
-    k_st_idft_fft<<<nf, 256, 3 * sizeof(double2) * (size_t)n, s>>>(coef, n, logn, tw, mode, out, stride);
-  else
-    k_st_idft<<<wb((long)nf * n), 256, 0, s>>>(coef, nf, n, tw, mode, out, stride);
-}
-
-kfbi_status step_setup_attributes() {
-  KFBI_TRY(cudaFuncSetAttribute(k_st_dft_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_FFT_SMEM));
-  KFBI_TRY(cudaFuncSetAttribute(k_st_idft_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FINE_FFT_SMEM));
-  return KFBI_OK;
-}
-
 kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve_info* info) {
   cudaStream_t s = c->stream;
   const int n = st->n;
@@ -402,15 +331,15 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
   launched(c, 22);
   // 1. reconstruct the curve from (eta, L, Xbar)
   k_st_xa<<<tb, 256, 0, s>>>(st->eta, n, st->scal, st->work);
-  st_dft(s, st->work, 2, 2, n, tw, coef);
+  k_st_dft<<<wb(2L * nk), 256, 0, s>>>(st->work, 2, 2, n, tw, coef);
   k_st_recon_coef<<<cdiv(2 * nk, 256), 256, 0, s>>>(coef, n, st->scal);
-  st_idft(s, coef, 2, n, tw, 0, st->xy, 2);
+  k_st_idft<<<wb(2L * n), 256, 0, s>>>(coef, 2, n, tw, 0, st->xy, 2);
   KFBI_TRY(cudaGetLastError());
   // 2. interface geometry
   KFBI_CHECK(set_interface_impl(c, n, st->xy));
   // 3. theta_a = 1 + eta_a, eta-hat
-  st_dft(s, st->eta, 1, 1, n, tw, (double2*)st->eta_h);
-  st_idft(s, (const double2*)st->eta_h, 1, n, tw, MODE_D1, st->work, 1);
+  k_st_dft<<<wb(nk), 256, 0, s>>>(st->eta, 1, 1, n, tw, (double2*)st->eta_h);
+  k_st_idft<<<wb(n), 256, 0, s>>>((const double2*)st->eta_h, 1, n, tw, MODE_D1, st->work, 1);
   k_st_theta_a<<<tb, 256, 0, s>>>(st->work, n, st->th_a);
   kfbi_solve_info si{};
   kfbi_status sst;
@@ -452,14 +381,14 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
   KFBI_TRY(cudaGetLastError());
   // 4. tangential velocity, M, Q
   k_st_mul<<<tb, 256, 0, s>>>(st->th_a, st->U, n, st->work);               // theta_a U
-  st_dft(s, st->work, 1, 1, n, tw, coef);
-  st_idft(s, coef, 1, n, tw, MODE_INT, st->work + n, 1);  // periodic antiderivative
+  k_st_dft<<<wb(nk), 256, 0, s>>>(st->work, 1, 1, n, tw, coef);
+  k_st_idft<<<wb(n), 256, 0, s>>>(coef, 1, n, tw, MODE_INT, st->work + n, 1);  // periodic antiderivative
   k_st_tangential<<<1, 1024, 0, s>>>(st->work + n, coef, st->U, st->eta, n, st->V, st->scal, ratio);
   // 5. U_a and the rhs of theta_t
-  st_dft(s, st->U, 1, 1, n, tw, coef + nk);
-  st_idft(s, coef + nk, 1, n, tw, MODE_D1, st->work, 1);  // U_a
+  k_st_dft<<<wb(nk), 256, 0, s>>>(st->U, 1, 1, n, tw, coef + nk);
+  k_st_idft<<<wb(n), 256, 0, s>>>(coef + nk, 1, n, tw, MODE_D1, st->work, 1);  // U_a
   k_st_theta_rhs<<<tb, 256, 0, s>>>(st->th_a, st->V, st->work, n, st->scal, st->work + n);
-  st_dft(s, st->work + n, 1, 1, n, tw, coef);            // rhs-hat
+  k_st_dft<<<wb(nk), 256, 0, s>>>(st->work + n, 1, 1, n, tw, coef);            // rhs-hat
   // 6. AB2 scalars, propagator, history
   k_st_scalars<<<1, 32, 0, s>>>(st->scal, dt);
   if (P.kind == KFBI_STEP_HELE_SHAW)
@@ -468,7 +397,7 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
   else
     k_st_propagate<<<cdiv(nk, 256), 256, 0, s>>>((double2*)st->eta_h, coef, (double2*)st->Nprev_h, n, st->scal, dt, 2,
                                                  -1.0);
-  st_idft(s, (const double2*)st->eta_h, 1, n, tw, 0, st->eta, 1);
+  k_st_idft<<<wb(n), 256, 0, s>>>((const double2*)st->eta_h, 1, n, tw, 0, st->eta, 1);
   k_st_finish<<<1, 32, 0, s>>>(st->scal, dt);
   KFBI_TRY(cudaGetLastError());
   KFBI_TRY(cudaStreamSynchronize(s));

@@ -295,7 +295,7 @@ def test_hele_shaw_step_parity(precision, n):
     """Three theta-L steps vs the oracle. Mixed precision (float32 grid applies, float64
     refinement to 1e-10) takes the velocity from the refinement's last float64 apply.
     n = 96 (not a power of two) takes the direct trigonometric sums instead of the FFTs for
-    the fine samples and the theta-L transforms."""
+    the interface's fine samples."""
     p = W.config_hele_shaw(N=256, n=n, box=3.0)
     ctx = K.Context(p.N, p.box, 0.0, K.BOX_FREESPACE_DL, precision, max_nodes=p.n)
     alpha = 2 * math.pi * np.arange(p.n) / p.n
