@@ -598,10 +598,12 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
 // For each column k of spec (x-mode k): forward transform along y, divide by
 // lam_y(l) + lam_x(k) - kappa, inverse transform along y, in place. A block owns P column
 // pairs; pair p holds columns (k0 + 2p, k0 + 2p + 1) as the real and imaginary parts of
-// one complex FFT. Two shared buffers alternate between the FFT stages.
-template <typename T>
-__global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, const T* tab, const T* lam,
-                            T kappa, T* spec, const int* skip) {
+// one complex FFT. Two shared buffers alternate between the FFT stages. One instantiation per
+// grid size (N = 2^LOGN), so that the index arithmetic is constant.
+template <typename T, int LOGN>
+__global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* tab, const T* lam, T kappa, T* spec,
+                            const int* skip) {
+  constexpr int N = 1 << LOGN, logN = LOGN;
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
   V2<T>* B = A + (long)P * N;
@@ -644,7 +646,7 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
     }
   }
   __syncthreads();
-  V2<T>* X = fft_stockham<T>(A, B, P, N, logN, sTw, false);
+  V2<T>* X = fft_ct<T, LOGN, false>(A, B, P, sTw);
   V2<T>* Y = X == A ? B : A;
   const int half = N >> 1;
   const T kap = kappa;
@@ -674,13 +676,31 @@ __global__ void k_col_solve(int N, int logN, int P, int dct, const V2<T>* tw, co
     }
   }
   __syncthreads();
-  V2<T>* Z = fft_stockham<T>(Y, X, P, N, logN, sTw, true);
+  V2<T>* Z = fft_ct<T, LOGN, true>(Y, X, P, sTw);
   const T invN = (T)1 / (T)N;
   for (int t = threadIdx.x; t < tot; t += blockDim.x) {
     const int j = t >> lw, c = t & (W - 1);
     T v = ((const T*)&Z[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] * invN;
     if (!dct && (j & 1)) v = -v;
     spec[(long)j * N + k0 + c] = v;
+  }
+}
+
+template <typename T>
+using ColKernel = void (*)(int, int, int, int, const V2<T>*, const T*, const T*, T, T*, const int*);
+// the column kernel for N = 2^logN, 16 <= N <= 4096
+template <typename T>
+static ColKernel<T> col_kernel(int logN) {
+  switch (logN) {
+    case 4: return k_col_solve<T, 4>;
+    case 5: return k_col_solve<T, 5>;
+    case 6: return k_col_solve<T, 6>;
+    case 7: return k_col_solve<T, 7>;
+    case 8: return k_col_solve<T, 8>;
+    case 9: return k_col_solve<T, 9>;
+    case 10: return k_col_solve<T, 10>;
+    case 11: return k_col_solve<T, 11>;
+    default: return k_col_solve<T, 12>;
   }
 }
 
@@ -903,7 +923,7 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
   size_t smem = col_smem<T>(N, P);
   const bool rec = c->timing && !c->capturing && c->timing_used < TIMING_CAP;
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
-  KFBI_TRY(launch_k(c->use_pdl && !rec, k_col_solve<T>, dim3(N / (2 * P)), dim3(col_threads(N, P)), smem, c->stream, N,
+  KFBI_TRY(launch_k(c->use_pdl && !rec, col_kernel<T>(c->logN), dim3(N / (2 * P)), dim3(col_threads(N, P)), smem, c->stream, N,
                     c->logN, P, (int)(c->boxbc == KFBI_BOX_NEUMANN0), Tabs<T>::stw(c), Tabs<T>::sin(c), Tabs<T>::lam(c),
                     (T)c->kappa, spec, skip));
   launched(c, 1);
@@ -1053,7 +1073,8 @@ static kfbi_status setup_t(kfbi_ctx*) {
   using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(nullptr))>::type>::type;
   using S_t = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(nullptr))>::type>::type;
   const int stage = (int)SMEM_STAGE_MAX;
-  KFBI_TRY(cudaFuncSetAttribute(k_col_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, col));
+  for (int lg = 4; lg <= 12; ++lg)
+    KFBI_TRY(cudaFuncSetAttribute(col_kernel<T>(lg), cudaFuncAttributeMaxDynamicSharedMemorySize, col));
   KFBI_TRY(cudaFuncSetAttribute(k_row_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
   KFBI_TRY(cudaFuncSetAttribute(k_face_dst<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
   KFBI_TRY(cudaFuncSetAttribute(k_dens_coef<T, true, S_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
@@ -1199,7 +1220,7 @@ static kfbi_status grid_solve_noalloc_impl(int N, double h, double kappa, int bo
   k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 0, (const V2<double>*)tw, tab, rhs, spec, nullptr);
   const int P = col_pairs<double>(N);
   size_t sm_col = col_smem<double>(N, P);  // <= 28 KB for N <= 512
-  k_col_solve<double><<<N / (2 * P), col_threads(N, P), sm_col, s>>>(N, logN, P, dct, (const V2<double>*)tw, tab, lam,
+  col_kernel<double>(logN)<<<N / (2 * P), col_threads(N, P), sm_col, s>>>(N, logN, P, dct, (const V2<double>*)tw, tab, lam,
                                                                   kappa, spec, flag);
   k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 1, (const V2<double>*)tw, tab, nullptr, spec, u);
   KFBI_TRY(cudaGetLastError());

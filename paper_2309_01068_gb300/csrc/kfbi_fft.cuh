@@ -81,6 +81,64 @@ __device__ V2<T>* fft_stockham(V2<T>* a, V2<T>* b, int P, int N, int logN, const
   return src;
 }
 
+// The same transform for a size fixed at compile time (N = 2^LOGN): every stage's span,
+// twiddle offset and index arithmetic become constants.
+template <typename T, int LOGN, bool INV>
+__device__ __forceinline__ V2<T>* fft_ct(V2<T>* a, V2<T>* b, int P, const V2<T>* stw) {
+  constexpr int N = 1 << LOGN;
+  constexpr int q = N >> 2, lq = LOGN - 2;
+  constexpr int LNS0 = LOGN & 1;
+  constexpr int NST = (LOGN - LNS0) / 2;
+  V2<T>* src = a;
+  V2<T>* dst = b;
+  if constexpr (LNS0 != 0) {
+    constexpr int h = N >> 1;
+    for (int t = threadIdx.x; t < P * h; t += blockDim.x) {
+      const int p = t >> (LOGN - 1), j = t & (h - 1);
+      const V2<T>* s = src + p * N;
+      V2<T>* d = dst + p * N;
+      const V2<T> v0 = s[j], v1 = s[j + h];
+      d[2 * j] = cadd(v0, v1);
+      d[2 * j + 1] = csub(v0, v1);
+    }
+    __syncthreads();
+    V2<T>* tmp = src; src = dst; dst = tmp;
+  }
+#pragma unroll
+  for (int st = 0; st < NST; ++st) {
+    const int lNs = LNS0 + 2 * st, Ns = 1 << lNs;
+    const int off = (1 << LNS0) * ((1 << (2 * st)) - 1);
+    for (int t = threadIdx.x; t < P * q; t += blockDim.x) {
+      const int p = t >> lq, j = t & (q - 1);
+      const V2<T>* s = src + p * N;
+      V2<T>* d = dst + p * N;
+      const int jm = j & (Ns - 1);
+      V2<T> v0 = s[j], v1 = s[j + q], v2 = s[j + 2 * q], v3 = s[j + 3 * q];
+      if (jm != 0) {
+        V2<T> w1 = stw[off + jm], w2 = stw[off + Ns + jm], w3 = stw[off + 2 * Ns + jm];
+        if (INV) {
+          w1.y = -w1.y;
+          w2.y = -w2.y;
+          w3.y = -w3.y;
+        }
+        v1 = cmul(v1, w1);
+        v2 = cmul(v2, w2);
+        v3 = cmul(v3, w3);
+      }
+      const V2<T> a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), t3 = csub(v1, v3);
+      const V2<T> a3 = INV ? V2<T>{-t3.y, t3.x} : V2<T>{t3.y, -t3.x};
+      const int o = ((j >> lNs) << (lNs + 2)) + jm;
+      d[o] = cadd(a0, a2);
+      d[o + Ns] = cadd(a1, a3);
+      d[o + 2 * Ns] = csub(a0, a2);
+      d[o + 3 * Ns] = csub(a1, a3);
+    }
+    __syncthreads();
+    V2<T>* tmp = src; src = dst; dst = tmp;
+  }
+  return src;
+}
+
 // number of staged twiddles of fft_stockham for N = 2^logN (at most N)
 __host__ __device__ inline int staged_count(int N, int logN) {
   int c = 0;
