@@ -531,6 +531,13 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
   const int b = row_ptr[j], e = row_ptr[j + 1];
   IrrRegs<T> first{};
   if ((int)threadIdx.x < e - b) first = irr_regs<T>(irr[b + threadIdx.x]);
+  // free-space box data of the row (west and east cells): complete before this kernel
+  // starts (the stream waited for the side stream that forms it)
+  T w = 0, ea = 0;
+  if (boxg != nullptr) {
+    w = boxg[j];
+    ea = boxg[N + j];
+  }
   pdl_wait();
   if (*skip) return;
   const int per = (N + ROW_THREADS - 1) / ROW_THREADS;
@@ -571,11 +578,8 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
       acc[q] = a;
     }
   }
-  T w = 0, ea = 0;
   const T* face = nullptr;
   if (boxg != nullptr) {
-    w = boxg[j];
-    ea = boxg[N + j];
     if (j == 0) face = facespec;
     else if (j == N - 1) face = facespec + N;
   }
