@@ -23,6 +23,14 @@ void note_cuda_error(cudaError_t e, const char* what, const char* file, int line
 // sin(pi m / (2N)) for m < 4N; box eigenvalues -4 sin^2(pi (k + s) / (2N)) / h^2 with s = 1
 // (Dirichlet-0, DST-II mode k) or s = 0 (Neumann-0, DCT-II mode k); FFT twiddles
 // e^{-2 pi i m / N} for m < N.
+// rinv[k][l] = 1 / (lam[l] + lam[k] - kappa)
+__global__ void k_rinv(int N, const double* lam, double kappa, double* rinv) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)N * N) return;
+  const int k = (int)(t / N), l = (int)(t - (long)k * N);
+  rinv[t] = 1.0 / (lam[l] + lam[k] - kappa);
+}
+
 __global__ void k_init_tables(int N, double h, int neumann, double* tab, float* tab_f, double* lam, float* lam_f,
                               double* tw, float* tw_f) {
   int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,7 +105,7 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
 static void free_all(kfbi_ctx* c) {
   void* ptrs[] = {c->sintab, c->sintab_f, c->lam, c->lam_f, c->twN, c->twN_f, c->xy, c->twn, c->icoef, c->fine, c->twM,
                   c->seg_count, c->seg_off, c->cr_kind, c->cr_line, c->cr_seg, c->cr_first, c->cr_alpha, c->cr_xi,
-                  c->tgeo, c->tgeo_f, c->stencil_f, c->dens_f, c->stw, c->stw_d, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->stencil,
+                  c->tgeo, c->tgeo_f, c->rinv, c->stencil_f, c->dens_f, c->stw, c->stw_d, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->stencil,
                   c->probe_mark, c->prow_cnt, c->prow_ptr, c->probe_i, c->probe_j, c->flags, c->counts, c->dcoef, c->dint,
                   c->boxg, c->facespec, c->spec, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack, c->boxK, c->boxK_f,
                   c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gVf, c->gpart, c->gw,
@@ -150,6 +158,7 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->sintab, 4 * (size_t)N));
   KFBI_CHECK(dalloc(&c->sintab_f, 4 * (size_t)N));
   KFBI_CHECK(dalloc(&c->lam, N));
+  if ((size_t)N * N * sizeof(double) <= RINV_MAX_BYTES) KFBI_CHECK(dalloc(&c->rinv, (size_t)N * N));
   KFBI_CHECK(dalloc(&c->lam_f, N));
   KFBI_CHECK(dalloc(&c->twN, 2 * (size_t)N));
   KFBI_CHECK(dalloc(&c->twN_f, 2 * (size_t)N));
@@ -234,6 +243,10 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   k_init_tables<<<cdiv(4L * N, 256), 256, 0, c->own>>>(N, c->h, boxbc == KFBI_BOX_NEUMANN0, c->sintab, c->sintab_f,
                                                      c->lam, c->lam_f, c->twN, c->twN_f);
   KFBI_TRY(cudaGetLastError());
+  if (c->rinv != nullptr) {
+    launched(c, 1);
+    k_rinv<<<cdiv((long)N * N, 256), 256, 0, c->own>>>(N, c->lam, kappa, c->rinv);
+  }
   // staged twiddles of the Stockham FFT: for each radix-4 stage with span Ns (first stage
   // radix 2 when log2 N is odd), w^{r jm N / (4 Ns)} at [off + (r-1) Ns + jm], r = 1..3
   {

@@ -606,7 +606,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
 // grid size (N = 2^LOGN), so that the index arithmetic is constant.
 template <typename T, int LOGN>
 __global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* tab, const T* lam, T kappa, T* spec,
-                            const int* skip) {
+                            const T* rinv, const int* skip) {
   constexpr int N = 1 << LOGN, logN = LOGN;
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
@@ -664,14 +664,24 @@ __global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* 
       else dct_cs<T>(tab, N, m, cs.x, cs.y);
       V2<T> Xm, XNm;
       dct_post<T>(x, N, m, cs.x, cs.y, Xm, XNm);
-      const T ly = sLam[dct ? m : N - 1 - m];
-      V2<T> Gm{fdiv_t(Xm.x, ly + lx0), fdiv_t(Xm.y, ly + lx1)};
-      V2<T> GNm{0, 0};
-      if (m == half) {
-        GNm = Gm;
-      } else if (m > 0) {
-        const T ly2 = sLam[dct ? N - m : m - 1];
-        GNm = V2<T>{fdiv_t(XNm.x, ly2 + lx0), fdiv_t(XNm.y, ly2 + lx1)};
+      const int l1 = dct ? m : N - 1 - m, l2 = dct ? N - m : m - 1;
+      V2<T> Gm, GNm{0, 0};
+      if (sizeof(T) == 8 && rinv != nullptr) {
+        // float64: products with the context's reciprocal table instead of divisions
+        const T* r0 = rinv + (long)(k0 + 2 * p) * N;
+        const T* r1 = r0 + N;
+        Gm = V2<T>{Xm.x * r0[l1], Xm.y * r1[l1]};
+        if (m == half) GNm = Gm;
+        else if (m > 0) GNm = V2<T>{XNm.x * r0[l2], XNm.y * r1[l2]};
+      } else {
+        const T ly = sLam[l1];
+        Gm = V2<T>{fdiv_t(Xm.x, ly + lx0), fdiv_t(Xm.y, ly + lx1)};
+        if (m == half) {
+          GNm = Gm;
+        } else if (m > 0) {
+          const T ly2 = sLam[l2];
+          GNm = V2<T>{fdiv_t(XNm.x, ly2 + lx0), fdiv_t(XNm.y, ly2 + lx1)};
+        }
       }
       V2<T> Zm, ZNm;
       dct_pre<T>(N, m, cs.x, cs.y, Gm, GNm, Zm, ZNm);
@@ -691,7 +701,7 @@ __global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* 
 }
 
 template <typename T>
-using ColKernel = void (*)(int, int, int, int, const V2<T>*, const T*, const T*, T, T*, const int*);
+using ColKernel = void (*)(int, int, int, int, const V2<T>*, const T*, const T*, T, T*, const T*, const int*);
 // the column kernel for N = 2^logN, 16 <= N <= 4096
 template <typename T>
 static ColKernel<T> col_kernel(int logN) {
@@ -929,7 +939,7 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
   KFBI_TRY(launch_k(c->use_pdl && !rec, col_kernel<T>(c->logN), dim3(N / (2 * P)), dim3(col_threads(N, P)), smem, c->stream, N,
                     c->logN, P, (int)(c->boxbc == KFBI_BOX_NEUMANN0), Tabs<T>::stw(c), Tabs<T>::sin(c), Tabs<T>::lam(c),
-                    (T)c->kappa, spec, skip));
+                    (T)c->kappa, spec, sizeof(T) == 8 ? (const T*)c->rinv : nullptr, skip));
   launched(c, 1);
   if (rec) {
     KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used + 1], c->stream));
@@ -1225,7 +1235,7 @@ static kfbi_status grid_solve_noalloc_impl(int N, double h, double kappa, int bo
   const int P = col_pairs<double>(N);
   size_t sm_col = col_smem<double>(N, P);  // <= 28 KB for N <= 512
   col_kernel<double>(logN)<<<N / (2 * P), col_threads(N, P), sm_col, s>>>(N, logN, P, dct, (const V2<double>*)tw, tab, lam,
-                                                                  kappa, spec, flag);
+                                                                  kappa, spec, nullptr, flag);
   k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 1, (const V2<double>*)tw, tab, nullptr, spec, u);
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;

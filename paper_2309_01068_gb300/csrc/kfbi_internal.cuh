@@ -144,6 +144,9 @@ struct kfbi_ctx {
   double* sintab = nullptr;   // [4N] sin(pi m / (2N))
   float* sintab_f = nullptr;
   double* lam = nullptr;      // [N] 1-D eigenvalues of the box operator
+  // [N][N] 1 / (lam[l] + lam[k] - kappa) (row k = x-mode): the float64 column solve's
+  // divisions as products (allocated when N^2 doubles fit RINV_MAX_BYTES)
+  double* rinv = nullptr;
   float* lam_f = nullptr;
   double* twN = nullptr;      // [N] complex: e^{-2 pi i m / N}, m < N
   float* twN_f = nullptr;
@@ -387,6 +390,7 @@ kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* densi
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u);
 // free-space box: fills boxK / boxK_f for the current interface (after the node data)
 constexpr size_t BOXK_MAX_BYTES = (size_t)1 << 30;
+constexpr size_t RINV_MAX_BYTES = (size_t)1 << 27;
 // row stride of the table: node count rounded up to a multiple of 4 (16-byte rows), padded
 // with zeros
 __host__ __device__ inline int box_ld(int n) { return (n + 3) & ~3; }
