@@ -165,17 +165,43 @@ __device__ __forceinline__ void jump_eval(const V2<T>* lane_coef, V2<T> c0, V2<T
   int k1 = min(K + 1, k0 + chunk);
   T a = 0, b = 0, d = 0;
   if (k0 < k1) {
-    V2<T> e = e0;
-    const V2<T> s = s1;
-    for (int k = k0; k < k1; ++k) {
-      V2<T> ck = lane_coef[k - k0];
-      T re = ck.x * e.x - ck.y * e.y;
-      T im = ck.x * e.y + ck.y * e.x;
-      T kk = (T)k;
-      a += re;
-      b -= kk * im;
-      d -= kk * kk * re;
-      e = cmul(e, s);
+    if constexpr (sizeof(T) == 8) {
+      // float64: four interleaved rotations (modes k0 + 4 i + r) and accumulators, so that
+      // each dependency chain is a quarter as long (float64 latency is long on this part)
+      const V2<T> s2 = cmul(s1, s1), s4 = cmul(s2, s2);
+      V2<T> e[4] = {e0, cmul(e0, s1), cmul(e0, s2), cmul(cmul(e0, s2), s1)};
+      T aa[4] = {0, 0, 0, 0}, bb[4] = {0, 0, 0, 0}, dd[4] = {0, 0, 0, 0};
+      for (int k = k0; k < k1; k += 4) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (k + r < k1) {
+            const V2<T> ck = lane_coef[k + r - k0];
+            const T re = ck.x * e[r].x - ck.y * e[r].y;
+            const T im = ck.x * e[r].y + ck.y * e[r].x;
+            const T kk = (T)(k + r);
+            aa[r] += re;
+            bb[r] -= kk * im;
+            dd[r] -= kk * kk * re;
+            e[r] = cmul(e[r], s4);
+          }
+        }
+      }
+      a = (aa[0] + aa[1]) + (aa[2] + aa[3]);
+      b = (bb[0] + bb[1]) + (bb[2] + bb[3]);
+      d = (dd[0] + dd[1]) + (dd[2] + dd[3]);
+    } else {
+      V2<T> e = e0;
+      const V2<T> s = s1;
+      for (int k = k0; k < k1; ++k) {
+        V2<T> ck = lane_coef[k - k0];
+        T re = ck.x * e.x - ck.y * e.y;
+        T im = ck.x * e.y + ck.y * e.x;
+        T kk = (T)k;
+        a += re;
+        b -= kk * im;
+        d -= kk * kk * re;
+        e = cmul(e, s);
+      }
     }
   }
   a = (T)2 * wsum(a) + c0.x;
