@@ -99,6 +99,7 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
   KFBI_CHECK(dalloc(&c->jumps, 6 * ((size_t)cap + c->max_nodes)));
   c->cap_cross = cap;
   c->cap_irr = cap_irr;
+  c->layout_version += 1;
   return KFBI_OK;
 }
 

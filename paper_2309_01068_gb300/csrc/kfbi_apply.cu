@@ -238,8 +238,11 @@ __device__ __forceinline__ void jump_eval(const V2<T>* lane_coef, V2<T> c0, V2<T
 // Jumps at every target (crossings, then nodes), one warp per target; the block stages the
 // density coefficients in shared memory first (SMEM = true; large n reads them from global memory). J[t] = ([u], [u_x], [u_y], [u_xx], [u_yy], [u_xy]).
 template <typename T, typename G, bool SMEM>
-__global__ void k_target_jumps(const V2<T>* coef, int n, int ntg, const G* tg, const V2<T>* tstart, int layer,
+__global__ void k_target_jumps(const V2<T>* coef, int n, const int* ncr, const G* tg, const V2<T>* tstart, int layer,
                                T kappa, T* Jout, const int* skip) {
+  // targets: the interface's crossings (count on the device, so that a captured launch stays
+  // valid for the next interface) and its n nodes; the grid covers the crossing capacity
+  const int ntg = *ncr + n;
   int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   // geometry and twiddle starts of this target (set with the interface) before the wait
@@ -751,8 +754,10 @@ static ColKernel<T> col_kernel(int logN) {
 // 4 l + 128 t + c (c < 4) read straight from the spectral grid (L2-resident after the column
 // solve), so that every warp has the same work however the probes fall in the rows.
 template <typename T>
-__global__ void k_probe_values(int N, int dct, int n_probe, const int* probe_j, const int* probe_i, const T* spec,
-                               const T* tab, float scale, T* pval, const int* skip) {
+__global__ void k_probe_values(int N, int dct, const int* nprobe, const int* probe_j, const int* probe_i,
+                               const T* spec, const T* tab, float scale, T* pval, const int* skip) {
+  // the probe count is on the device (the grid covers 6 n, the most an interface can have)
+  const int n_probe = *nprobe;
   const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   // the probe's position (set with the interface) before the wait
@@ -863,8 +868,9 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
 //   out = a x + b value + c int(x) ds   (a, b, c select the boundary integral operator)
 // in the arithmetic type T (a = eps_v[p] when eps_v is given) and stored as float64.
 template <typename T, typename S_t>
-__global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const T* x_in, const double* eps_v, T ca,
-                         T cb, T cc, const T* dint, double* out, double* dnormal, const int* skip) {
+__global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jall, const int* ncr, const T* x_in,
+                         const double* eps_v, T ca, T cb, T cc, const T* dint, double* out, double* dnormal,
+                         const int* skip) {
   int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   // this lane's stencil point (set with the interface) before the wait
@@ -890,7 +896,8 @@ __global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jn, const
   pdl_wait();
   if (*skip) return;
   if (p >= n) return;
-  const T* J = Jn ? Jn + (long)p * 6 : nullptr;
+  // the nodes' jumps follow the crossings' (their count is on the device)
+  const T* J = Jall ? Jall + ((long)*ncr + p) * 6 : nullptr;
   T v = 0, gx = 0, gy = 0;
   if (m < 6) {
     T u = pval[probe];
@@ -991,7 +998,7 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   const long long l0 = c->launches;
   using T4 = typename std::conditional<sizeof(T) == 8, double4_32a, float4>::type;
   cudaStream_t s = c->stream;
-  const int N = c->N, n = c->n, ncr = c->n_cross;
+  const int N = c->N, n = c->n;
   const int dct = c->boxbc == KFBI_BOX_NEUMANN0;
   const bool fs = c->boxbc == KFBI_BOX_FREESPACE_DL;
   const T* tab = Tabs<T>::sin(c);
@@ -1056,15 +1063,18 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     k_dens_coef<T, false><<<cdiv((long)nk * 32, 256), 256, 0, s>>>(dens_t, n, Tabs<T>::twn(c), Tabs<T>::stencil(c),
                                                                    coef, want_int ? dint_t : nullptr, skip);
   }
-  const int ntg = ncr + n;
+  // launch shapes from capacities and device counts: the same launches serve every interface
+  // of this layout (a captured graph is kept across interfaces)
+  const int* d_ncr = c->seg_off + 2 * SUBSAMPLES * n;
+  const int ntg_cap = c->cap_cross + n;
   using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
   const size_t smj = (size_t)jump_layout_size(n) * sizeof(V2<T>);
   if (smj <= SMEM_STAGE_MAX)
-    KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, true>, dim3(cdiv((long)ntg * 32, 256)), dim3(256), smj, s,
-                      (const V2<T>*)coef, n, ntg, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
+    KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, true>, dim3(cdiv((long)ntg_cap * 32, 256)), dim3(256), smj, s,
+                      (const V2<T>*)coef, n, d_ncr, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
   else
-    KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, false>, dim3(cdiv((long)ntg * 32, 256)), dim3(256), 0, s,
-                      (const V2<T>*)coef, n, ntg, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
+    KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, false>, dim3(cdiv((long)ntg_cap * 32, 256)), dim3(256), 0, s,
+                      (const V2<T>*)coef, n, d_ncr, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
   launched(c, 2);
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   KFBI_TRY(launch_k(c->use_pdl, k_row_forward<T>, dim3(N), dim3(ROW_THREADS), 0, s, N, dct, (const int*)c->row_ptr,
@@ -1072,12 +1082,10 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
                     (const T*)face, tab, scale, spec, skip));
   launched(c, 1);
   KFBI_CHECK(launch_col_solve<T>(c, spec, skip));
-  if (c->n_probe > 0) {
-    KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(cdiv((long)c->n_probe * 32, 256)), dim3(256), 0, s, N, dct,
-                      c->n_probe, (const int*)c->probe_j, (const int*)c->probe_i, (const T*)spec, tab, scale, pval,
-                      skip));
-    launched(c, 1);
-  }
+  KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(cdiv((long)6 * n * 32, 256)), dim3(256), 0, s, N, dct,
+                    (const int*)(c->prow_ptr + N), (const int*)c->probe_j, (const int*)c->probe_i, (const T*)spec, tab,
+                    scale, pval, skip));
+  launched(c, 1);
   if (grid != nullptr) KFBI_CHECK(launch_row_dense<T>(c, 1, nullptr, spec, grid));
   using S_t = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(c))>::type>::type;
   T ca = 0, cb = 1, cc = 0;
@@ -1087,7 +1095,7 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   else if (bie_kind == KFBI_BIE_HS_EXTERIOR_MDL) { ca = (T)-0.5; cc = 1; xin = dens_t; }
   else if (bie_kind == KFBI_BIE_STEFAN_SL) { cb = -1; ev = eps_v; xin = dens_t; }
   KFBI_TRY(launch_k(c->use_pdl, k_interp<T, S_t>, dim3(cdiv((long)n * 32, 256)), dim3(256), 0, s, n,
-                    Tabs<T>::stencil(c), (const T*)pval, (const T*)(J + (long)ncr * 6), xin, ev, ca, cb, cc,
+                    Tabs<T>::stencil(c), (const T*)pval, (const T*)J, d_ncr, xin, ev, ca, cb, cc,
                     (const T*)(want_int ? dint_t : nullptr), values, dnormal, skip));
   launched(c, 1);
   c->per_apply_launches[sizeof(T) == 4 ? 1 : 0] = (int)(c->launches - l0);
@@ -1168,8 +1176,9 @@ kfbi_status interp_grid_enqueue(kfbi_ctx* c, const double* grid, double* values)
   double* pval = c->probe_val;
   launched(c, 2);
   k_gather_probes<<<c->N, 128, 0, s>>>(c->N, c->prow_ptr, c->probe_i, grid, pval);
-  k_interp<double><<<cdiv((long)c->n * 32, 256), 256, 0, s>>>(c->n, c->stencil, pval, nullptr, nullptr, nullptr, 0.0,
-                                                               1.0, 0.0, nullptr, values, nullptr, c->zero_flag);
+  k_interp<double><<<cdiv((long)c->n * 32, 256), 256, 0, s>>>(c->n, c->stencil, pval, nullptr, nullptr, nullptr,
+                                                               nullptr, 0.0, 1.0, 0.0, nullptr, values, nullptr,
+                                                               c->zero_flag);
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
 }

@@ -763,6 +763,7 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
     KFBI_CHECK(box_matrix_enqueue(c, n));
     c->boxK_ok = true;
   }
+  if (c->n != n) c->layout_version += 1;
   c->n = n;
   c->have_iface = true;
   c->iface_version += 1;

@@ -1317,7 +1317,7 @@ static kfbi_status build_graph(kfbi_ctx* c, kfbi_ctx::SolveGraph& G, int kind, b
     cudaGetLastError();
     return st;
   }
-  G.version = c->iface_version;
+  G.version = c->layout_version;
   return KFBI_OK;
 }
 
@@ -1363,7 +1363,7 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   if (c->use_graphs && !c->timing) {
     kfbi_ctx::SolveGraph& G = c->sgraph[kind][fp32 ? 1 : 0];
     kfbi_status st = KFBI_OK;
-    if (G.exec == nullptr || G.version != c->iface_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
+    if (G.exec == nullptr || G.version != c->layout_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
         G.cfg != c->cfg_version || G.f32 != gf.f32) {
       st = build_graph(c, G, kind, fp32, eps_v, b, x, cap, gf);
       G.m = m;
@@ -1508,7 +1508,7 @@ static kfbi_status solve_ir_graph(kfbi_ctx* c, int kind, const double* rhs, doub
   const int cap = body_cap(max_iter, m);
   const int max_sweeps = IR_MAX_SWEEPS;
   kfbi_ctx::IrGraph& G = c->irgraph[kind][dnormal != nullptr ? 1 : 0];
-  if (G.exec == nullptr || G.version != c->iface_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
+  if (G.exec == nullptr || G.version != c->layout_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
       G.cap != cap || G.cfg != c->cfg_version || G.f32 != gf.f32) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
     if (G.graph) cudaGraphDestroy(G.graph);
@@ -1529,7 +1529,7 @@ static kfbi_status solve_ir_graph(kfbi_ctx* c, int kind, const double* rhs, doub
       cudaGetLastError();
       return KFBI_OK;  // not used
     }
-    G.version = c->iface_version;
+    G.version = c->layout_version;
     G.m = m;
     G.cs = gf.cs;
     G.pdl = c->use_pdl;

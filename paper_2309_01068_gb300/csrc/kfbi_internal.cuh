@@ -279,6 +279,9 @@ struct kfbi_ctx {
   int gmf_last_cs = 0;          // cluster size used by the last GMRES run
   size_t gmf_smem_max[2] = {0, 0};  // per element type (double, float): 0 = not queried, 1 = unavailable
   long iface_version = 0;
+  // bumped when an interface changes what a captured apply launches (node count, buffer
+  // capacities); graphs keyed on it survive set_interface otherwise
+  long layout_version = 0;
   bool use_graphs = true;
   bool capturing = false;
   double* gev = nullptr;        // [max_nodes] eps_V copy for the Stefan operator

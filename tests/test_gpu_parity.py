@@ -230,6 +230,27 @@ def test_gmres_full_krylov_space(precision, push):
     assert rel(phi.cpu().numpy(), rphi) < 1e-12
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_graph_reused_across_interfaces(precision):
+    """A solve's captured graph is kept when the next interface has the same node count (the
+    launches read crossing and probe counts on the device): solves on three interfaces with
+    different crossing counts in one context each match the oracle."""
+    probs = [W.random_problem(s, N=128, n=128) for s in (81, 82, 83)]
+    ctx = K.Context(128, probs[0].box, 0.0, K.BOX_DIRICHLET0, precision, max_nodes=128)
+    crossings = set()
+    for p in probs:
+        ctx.set_interface(dev(p.xy))
+        crossings.add(ctx.stats()["crossings"])
+        ref = OK.Kfbi(p.N, p.box, 0.0, OK.BOX_DIRICHLET0).set_interface(p.xy)
+        tol = 1e-12 if precision == 0 else 1e-10
+        phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=tol, max_iter=300, restart=100)
+        assert ctx.get_option(K.OPT_CUDA_GRAPHS) == 1
+        rphi, _ = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), p.rhs, tol=1e-13)
+        assert info["status"] == 0
+        assert rel(phi.cpu().numpy(), rphi) < (1e-9 if precision == 0 else 1e-8)
+    assert len(crossings) > 1
+
+
 def test_gmres_cluster_long_restart_without_staged_hessenberg():
     """Restart 200: the Hessenberg matrix does not fit in the cluster's shared memory beside
     V, so the back substitution reads it from global memory; density vs the oracle."""
