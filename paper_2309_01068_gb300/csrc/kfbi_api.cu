@@ -108,7 +108,7 @@ static void free_all(kfbi_ctx* c) {
                   c->seg_count, c->seg_off, c->cr_kind, c->cr_line, c->cr_seg, c->cr_first, c->cr_alpha, c->cr_xi,
                   c->tgeo, c->tgeo_f, c->rinv, c->stencil_f, c->dens_f, c->stw, c->stw_d, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->stencil,
                   c->probe_mark, c->prow_cnt, c->prow_ptr, c->probe_i, c->probe_j, c->flags, c->counts, c->dcoef, c->dint,
-                  c->boxg, c->facespec, c->edge_s, c->edge_s_f, c->spec, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack, c->boxK, c->boxK_f,
+                  c->boxg, c->facespec, c->spec, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack, c->boxK, c->boxK_f,
                   c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gVf, c->gpart, c->gw,
                   c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag, c->irctl, c->ir_b, c->ir_x, c->ir_dn};
   for (void* p : ptrs)
@@ -174,8 +174,6 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   }
   KFBI_CHECK(dalloc(&c->prow_list, N + 1));
   KFBI_CHECK(dalloc(&c->facespec, 2 * (size_t)N));
-  KFBI_CHECK(dalloc(&c->edge_s, 2 * (size_t)N));
-  KFBI_CHECK(dalloc(&c->edge_s_f, 2 * (size_t)N));
   KFBI_CHECK(dalloc(&c->icoef, 4 * (size_t)nk));
   KFBI_CHECK(dalloc(&c->fine, 2 * (size_t)M));
   KFBI_CHECK(dalloc(&c->twM, 2 * (size_t)M));
@@ -246,7 +244,6 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   k_init_tables<<<cdiv(4L * N, 256), 256, 0, c->own>>>(N, c->h, boxbc == KFBI_BOX_NEUMANN0, c->sintab, c->sintab_f,
                                                      c->lam, c->lam_f, c->twN, c->twN_f);
   KFBI_TRY(cudaGetLastError());
-  KFBI_CHECK(edge_sines_enqueue(c, c->own));
   if (c->rinv != nullptr) {
     launched(c, 1);
     k_rinv<<<cdiv((long)N * N, 256), 256, 0, c->own>>>(N, c->lam, kappa, c->rinv);

@@ -550,8 +550,8 @@ constexpr int ROW_THREADS = 256;  // N <= 4096 gives at most 16 outputs per thre
 template <typename T>
 __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, const int* row_ptr, const IrrNode* irr,
                                                             const T* J, T inv_h2, const T* boxg,
-                                                            const T* facespec, const T* es, const T* tab, float scale,
-                                                            T* spec, const int* skip) {
+                                                            const T* facespec, const T* tab, float scale, T* spec,
+                                                            const int* skip) {
   __shared__ int si[ROW_CAP];
   __shared__ T sv[ROW_CAP];
   const int j = blockIdx.x;
@@ -619,7 +619,8 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
     if (k >= N) break;
     T a = acc[q];
     if (boxg != nullptr) {
-      a += w * es[k] + ea * es[N + k];
+      if (dct) a += w * tsin(tab, k + N, N, scale) + ea * tsin(tab, k * (2 * N - 1) + N, N, scale);
+      else a += w * tsin(tab, k + 1, N, scale) + ea * tsin(tab, (k + 1) * (2 * N - 1), N, scale);
       if (face != nullptr) a += face[k];
     }
     spec[(long)j * N + k] = a;
@@ -1078,8 +1079,7 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   KFBI_TRY(launch_k(c->use_pdl, k_row_forward<T>, dim3(N), dim3(ROW_THREADS), 0, s, N, dct, (const int*)c->row_ptr,
                     (const IrrNode*)c->irr, (const T*)J, (T)(1.0 / (c->h * c->h)), (const T*)(fs ? boxg : nullptr),
-                    (const T*)face, sizeof(T) == 8 ? (const T*)c->edge_s : (const T*)c->edge_s_f, tab, scale, spec,
-                    skip));
+                    (const T*)face, tab, scale, spec, skip));
   launched(c, 1);
   KFBI_CHECK(launch_col_solve<T>(c, spec, skip));
   KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(cdiv((long)6 * n * 32, 256)), dim3(256), 0, s, N, dct,
@@ -1142,25 +1142,6 @@ kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* densi
   if (skip == nullptr) skip = c->zero_flag;
   if (fp32) return apply_t<float>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip, density_f);
   return apply_t<double>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip, nullptr);
-}
-
-// S_k(0) and S_k(N-1) of the row transform (DST-II or DCT-II), k = 0..N-1, in float64 from
-// the sine table and in float32 through tsin as the float32 row kernel evaluates them
-__global__ void k_edge_sines(int N, int dct, const double* tab, double* es, float* es_f) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  const int i0 = dct ? k + N : k + 1, i1 = dct ? k * (2 * N - 1) + N : (k + 1) * (2 * N - 1);
-  es[k] = tsin(tab, i0, N, 0.0f);
-  es[N + k] = tsin(tab, i1, N, 0.0f);
-  es_f[k] = tsin((const float*)nullptr, i0, N, qscale(N));
-  es_f[N + k] = tsin((const float*)nullptr, i1, N, qscale(N));
-}
-
-kfbi_status edge_sines_enqueue(kfbi_ctx* c, cudaStream_t s) {
-  launched(c, 1);
-  k_edge_sines<<<cdiv(c->N, 256), 256, 0, s>>>(c->N, c->boxbc == KFBI_BOX_NEUMANN0, c->sintab, c->edge_s, c->edge_s_f);
-  KFBI_TRY(cudaGetLastError());
-  return KFBI_OK;
 }
 
 kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n) {

@@ -212,10 +212,6 @@ struct kfbi_ctx {
   double* dint = nullptr;       // [1] integral of the density
   double* boxg = nullptr;       // [4N] free-space box data
   double* facespec = nullptr;   // [2N] transformed south / north face rows
-  // [2][N] the row transform's basis at the west and east cells, S_k(0) and S_k(N-1)
-  // (float64 from the sine table, float32 as the float32 kernels evaluate it)
-  double* edge_s = nullptr;
-  float* edge_s_f = nullptr;
   double* jumps = nullptr;      // [cap_cross + max_nodes][6] jumps at the targets (T)
   double* spec = nullptr;       // [N][N] row-transformed grid (T)
   double* probe_val = nullptr;  // [6*max_nodes] (T)
@@ -402,7 +398,6 @@ constexpr size_t RINV_MAX_BYTES = (size_t)1 << 27;
 // with zeros
 __host__ __device__ inline int box_ld(int n) { return (n + 3) & ~3; }
 kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n);
-kfbi_status edge_sines_enqueue(kfbi_ctx* c, cudaStream_t s);
 // largest dynamic shared memory of the FFT-based fine sampling (node counts up to 4096)
 constexpr size_t FINE_FFT_SMEM = 3 * 16 * (size_t)4096;
 kfbi_status geometry_setup_attributes();
