@@ -128,15 +128,33 @@ __global__ void k_dft_real(const double* f, int stride, int nf, int n, const dou
   int nk = n / 2 + 1;
   if (warp >= nk * nf) return;
   int q = warp / nk, k = warp - q * nk;
-  double re = 0.0, im = 0.0;
-  for (int j = lane; j < n; j += 32) {
-    double v = f[(long)j * stride + q];
-    double2 w = tw[(int)(((long)k * j) % n)];
-    re += v * w.x;
-    im -= v * w.y;
+  // twiddle index k j mod n advanced by k 32 mod n (no division in the loop); two
+  // accumulator pairs shorten the float64 dependency chains
+  int idx = (int)(((long)k * lane) % n);
+  const int step = (int)(((long)k * 32) % n);
+  double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+  int j = lane;
+  for (; j + 32 < n; j += 64) {
+    const double v0 = f[(long)j * stride + q], v1 = f[(long)(j + 32) * stride + q];
+    const double2 w0 = tw[idx];
+    idx += step;
+    if (idx >= n) idx -= n;
+    const double2 w1 = tw[idx];
+    idx += step;
+    if (idx >= n) idx -= n;
+    re0 += v0 * w0.x;
+    im0 -= v0 * w0.y;
+    re1 += v1 * w1.x;
+    im1 -= v1 * w1.y;
   }
-  re = warp_sum(re);
-  im = warp_sum(im);
+  if (j < n) {
+    const double v = f[(long)j * stride + q];
+    const double2 w = tw[idx];
+    re0 += v * w.x;
+    im0 -= v * w.y;
+  }
+  const double re = warp_sum(re0 + re1);
+  const double im = warp_sum(im0 + im1);
   if (lane == 0) coef[q * nk + k] = make_double2(re / n, im / n);
 }
 
