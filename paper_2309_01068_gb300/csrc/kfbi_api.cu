@@ -128,6 +128,8 @@ static void free_all(kfbi_ctx* c) {
     }
   if (c->gev) cudaFree(c->gev);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_boxK) cudaEventDestroy(c->ev_boxK);
+  if (c->ev_boxK0) cudaEventDestroy(c->ev_boxK0);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->aux) cudaStreamDestroy(c->aux);
   if (c->own) cudaStreamDestroy(c->own);
@@ -235,6 +237,8 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   c->user_default = true;
   c->stream = c->own;
   KFBI_TRY(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  KFBI_TRY(cudaEventCreateWithFlags(&c->ev_boxK, cudaEventDisableTiming));
+  KFBI_TRY(cudaEventCreateWithFlags(&c->ev_boxK0, cudaEventDisableTiming));
   KFBI_TRY(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   KFBI_CHECK(ensure_cross_capacity(c, 4096));
   KFBI_CHECK(dalloc(&c->gev, max_nodes));

@@ -1147,11 +1147,23 @@ kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* densi
 kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n) {
   const int ld = box_ld(n);
   launched(c, 1);
+  // on the aux stream after the node data: the applies' box products also run there (stream
+  // order), graph launches and the next interface wait on ev_boxK (box_table_join)
+  KFBI_TRY(cudaEventRecord(c->ev_boxK0, c->stream));
+  KFBI_TRY(cudaStreamWaitEvent(c->aux, c->ev_boxK0, 0));
   const dim3 grid(cdiv(ld, 128), 4, cdiv(c->N, BOXK_CHUNK));
-  k_box_matrix<<<grid, 128, 0, c->stream>>>(c->N, n, ld, (const double4_32a*)c->npack, c->xmin, c->xmax,
-                                                       c->ymin, c->ymax, c->h, -2.0 / (c->h * c->h * (double)n),
-                                                       c->boxK, c->boxK_f);
+  k_box_matrix<<<grid, 128, 0, c->aux>>>(c->N, n, ld, (const double4_32a*)c->npack, c->xmin, c->xmax, c->ymin,
+                                         c->ymax, c->h, -2.0 / (c->h * c->h * (double)n), c->boxK, c->boxK_f);
   KFBI_TRY(cudaGetLastError());
+  KFBI_TRY(cudaEventRecord(c->ev_boxK, c->aux));
+  c->boxK_pending = true;
+  return KFBI_OK;
+}
+
+kfbi_status box_table_join(kfbi_ctx* c, cudaStream_t s) {
+  if (!c->boxK_pending) return KFBI_OK;
+  KFBI_TRY(cudaStreamWaitEvent(s, c->ev_boxK, 0));
+  if (s == c->stream) c->boxK_pending = false;
   return KFBI_OK;
 }
 

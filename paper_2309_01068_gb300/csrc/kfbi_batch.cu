@@ -214,6 +214,7 @@ static kfbi_status batch_solve_impl(kfbi_batch* b, int kind, const double* const
   if (!fresh) KFBI_CHECK(batch_build(b, kind, rhs, x, tol, max_iter, restart));
   KFBI_TRY(cudaEventRecord(b->ev, b->user));
   KFBI_TRY(cudaStreamWaitEvent(b->own, b->ev, 0));
+  for (int i = 0; i < b->count; ++i) KFBI_CHECK(box_table_join(b->ctx[i], b->own));
   KFBI_TRY(cudaGraphLaunch(b->exec, b->own));
   KFBI_TRY(cudaStreamSynchronize(b->own));
   const bool mixed = b->precision == KFBI_MIXED;

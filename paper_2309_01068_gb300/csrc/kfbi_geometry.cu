@@ -694,6 +694,7 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   const int M = SUBSAMPLES * n;
   const int nk = n / 2 + 1;
   c->have_iface = false;
+  KFBI_CHECK(box_table_join(c, s));  // the previous table may still read the node data
 
   KFBI_TRY(cudaMemcpyAsync(c->xy, xy_in, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, s));
   KFBI_TRY(cudaMemsetAsync(c->flags, 0, sizeof(int), s));

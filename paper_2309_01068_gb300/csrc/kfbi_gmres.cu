@@ -1372,6 +1372,7 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
       G.cfg = c->cfg_version;
       G.f32 = gf.f32;
     }
+    if (st == KFBI_OK) st = box_table_join(c, s);
     if (st == KFBI_OK && cudaGraphLaunch(G.exec, s) == cudaSuccess) {
       graphed = true;
     } else {
@@ -1542,6 +1543,7 @@ static kfbi_status solve_ir_graph(kfbi_ctx* c, int kind, const double* rhs, doub
   KFBI_TRY(cudaMemcpyAsync(c->ir_x, x, bytes, cudaMemcpyDeviceToDevice, s));
   k_ir_init<<<1, 32, 0, s>>>(c->irctl, tol, max_iter, max_sweeps, max_sweeps + 2);
   KFBI_TRY(cudaGetLastError());
+  KFBI_CHECK(box_table_join(c, s));
   KFBI_TRY(cudaGraphLaunch(G.exec, s));
   *used = true;
   KFBI_TRY(cudaMemcpyAsync(x, c->ir_x, bytes, cudaMemcpyDeviceToDevice, s));

@@ -169,6 +169,10 @@ struct kfbi_ctx {
   double* boxK = nullptr;
   float* boxK_f = nullptr;
   bool boxK_ok = false;         // filled for the current interface
+  // the table is built on the aux stream (overlapping the work that follows set_interface);
+  // ev_boxK marks its completion, boxK_pending until the main stream has waited on it
+  cudaEvent_t ev_boxK = nullptr, ev_boxK0 = nullptr;
+  bool boxK_pending = false;
   bool use_boxK = true;         // KFBI_OPT_BOX_MATRIX
   int* prow_list = nullptr;     // [N] rows that hold interpolation probes
   int n_prow = 0;
@@ -398,6 +402,9 @@ constexpr size_t RINV_MAX_BYTES = (size_t)1 << 27;
 // with zeros
 __host__ __device__ inline int box_ld(int n) { return (n + 3) & ~3; }
 kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n);
+// makes stream s wait for a box table still being built (before a graph launch or an
+// interface change); no-op otherwise
+kfbi_status box_table_join(kfbi_ctx* c, cudaStream_t s);
 // largest dynamic shared memory of the FFT-based fine sampling (node counts up to 4096)
 constexpr size_t FINE_FFT_SMEM = 3 * 16 * (size_t)4096;
 kfbi_status geometry_setup_attributes();
