@@ -1066,7 +1066,7 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   // launch shapes from capacities and device counts: the same launches serve every interface
   // of this layout (a captured graph is kept across interfaces)
   const int* d_ncr = c->seg_off + 2 * SUBSAMPLES * n;
-  const int ntg_cap = c->cap_cross + n;
+  const int ntg_cap = c->ncr_grid + n;
   using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
   const size_t smj = (size_t)jump_layout_size(n) * sizeof(V2<T>);
   if (smj <= SMEM_STAGE_MAX)

@@ -783,6 +783,12 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
     c->boxK_ok = true;
   }
   if (c->n != n) c->layout_version += 1;
+  if (c->n_cross > c->ncr_grid) {
+    // the jump launches cover a quarter more crossings than this interface has, so that the
+    // next interfaces of a moving curve reuse them
+    c->ncr_grid = c->n_cross + c->n_cross / 4 + 64;
+    c->layout_version += 1;
+  }
   c->n = n;
   c->have_iface = true;
   c->iface_version += 1;

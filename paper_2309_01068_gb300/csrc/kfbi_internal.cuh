@@ -286,6 +286,7 @@ struct kfbi_ctx {
   // bumped when an interface changes what a captured apply launches (node count, buffer
   // capacities); graphs keyed on it survive set_interface otherwise
   long layout_version = 0;
+  int ncr_grid = 0;             // crossings the captured jump launches cover (with headroom)
   bool use_graphs = true;
   bool capturing = false;
   double* gev = nullptr;        // [max_nodes] eps_V copy for the Stefan operator
