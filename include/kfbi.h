@@ -323,6 +323,10 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             cluster, completed on each receiver's mbarrier) when the
  *                             receive rows fit in shared memory; 0: a cluster barrier, then
  *                             every CTA loads the partial sums from the others.
+ *   KFBI_OPT_FUSE_INTERP      1 (default): with the float32 Gram-Schmidt kernel, each CTA
+ *                             forms its slice of A v from the apply's probe values and jumps
+ *                             (the apply's interpolation step, same arithmetic) instead of a
+ *                             separate interpolation kernel; 0: the separate kernel.
  * kfbi_set_option: value 0 or 1 unless stated. kfbi_get_option writes the value to *value (host).
  * Errors: ARG (unknown option, bad value, NULL, read-only option).
  */
@@ -335,7 +339,8 @@ enum {
   KFBI_OPT_COL_PAIRS = 6,
   KFBI_OPT_BOX_MATRIX = 7,
   KFBI_OPT_FP32_ARNOLDI = 8,
-  KFBI_OPT_PUSH_REDUCE = 9
+  KFBI_OPT_PUSH_REDUCE = 9,
+  KFBI_OPT_FUSE_INTERP = 10
 };
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);

@@ -994,7 +994,8 @@ static kfbi_status launch_row_dense(kfbi_ctx* c, int inverse, const double* rhs,
 
 template <typename T>
 static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double* values, double* dnormal,
-                           double* grid, int bie_kind, const double* eps_v, const int* skip, const float* density_f) {
+                           double* grid, int bie_kind, const double* eps_v, const int* skip, const float* density_f,
+                           bool skip_interp) {
   const long long l0 = c->launches;
   using T4 = typename std::conditional<sizeof(T) == 8, double4_32a, float4>::type;
   cudaStream_t s = c->stream;
@@ -1094,10 +1095,12 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   if (bie_kind == KFBI_BIE_INTERIOR_DL) { ca = (T)0.5; xin = dens_t; }
   else if (bie_kind == KFBI_BIE_HS_EXTERIOR_MDL) { ca = (T)-0.5; cc = 1; xin = dens_t; }
   else if (bie_kind == KFBI_BIE_STEFAN_SL) { cb = -1; ev = eps_v; xin = dens_t; }
-  KFBI_TRY(launch_k(c->use_pdl, k_interp<T, S_t>, dim3(cdiv((long)n * 32, 256)), dim3(256), 0, s, n,
-                    Tabs<T>::stencil(c), (const T*)pval, (const T*)J, d_ncr, xin, ev, ca, cb, cc,
-                    (const T*)(want_int ? dint_t : nullptr), values, dnormal, skip));
-  launched(c, 1);
+  if (!skip_interp) {
+    KFBI_TRY(launch_k(c->use_pdl, k_interp<T, S_t>, dim3(cdiv((long)n * 32, 256)), dim3(256), 0, s, n,
+                      Tabs<T>::stencil(c), (const T*)pval, (const T*)J, d_ncr, xin, ev, ca, cb, cc,
+                      (const T*)(want_int ? dint_t : nullptr), values, dnormal, skip));
+    launched(c, 1);
+  }
   c->per_apply_launches[sizeof(T) == 4 ? 1 : 0] = (int)(c->launches - l0);
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -1138,10 +1141,26 @@ kfbi_status apply_setup_attributes(kfbi_ctx* c) {
 
 // bie_kind < 0: plain layer potential
 kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* density, double* values, double* dnormal,
-                          double* grid, int bie_kind, const double* eps_v, const int* skip, const float* density_f) {
+                          double* grid, int bie_kind, const double* eps_v, const int* skip, const float* density_f,
+                          bool skip_interp) {
   if (skip == nullptr) skip = c->zero_flag;
-  if (fp32) return apply_t<float>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip, density_f);
-  return apply_t<double>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip, nullptr);
+  if (fp32)
+    return apply_t<float>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip, density_f, skip_interp);
+  return apply_t<double>(c, layer, density, values, dnormal, grid, bie_kind, eps_v, skip, nullptr, false);
+}
+
+InterpArgs<float> interp_args_f32(kfbi_ctx* c, int bie_kind, const double* eps_v, const float* density_f) {
+  // the same choices as apply_t<float> makes for its k_interp launch
+  InterpArgs<float> a;
+  a.st = c->stencil_f;
+  a.pval = (const float*)c->probe_val;
+  a.Jall = (const float*)c->jumps;
+  a.ncr = c->seg_off + 2 * SUBSAMPLES * c->n;
+  a.dint = bie_kind == KFBI_BIE_HS_EXTERIOR_MDL ? (const float*)(c->dint + 4) : nullptr;
+  if (bie_kind == KFBI_BIE_INTERIOR_DL) { a.ca = 0.5f; a.x_in = density_f; }
+  else if (bie_kind == KFBI_BIE_HS_EXTERIOR_MDL) { a.ca = -0.5f; a.cc = 1.0f; a.x_in = density_f; }
+  else if (bie_kind == KFBI_BIE_STEFAN_SL) { a.cb = -1.0f; a.eps_v = eps_v; a.x_in = density_f; }
+  return a;
 }
 
 kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n) {

@@ -664,6 +664,23 @@ __device__ __forceinline__ void gmf_close(GmresCtl* ctl, unsigned rank, cudaGrap
   if (use_cond) cudaGraphSetConditional(hcond, done ? 0u : 1u);
 }
 
+// sw[i] = A v at node i0 + i for i < len: formed here from the apply's probe values and
+// jumps (ia.st != nullptr; the apply then stops before its interpolation kernel) or read from
+// the apply's output w. One warp per node for the former. Ends with __syncthreads.
+template <typename T>
+__device__ __forceinline__ void gmf_w_slice(const InterpArgs<T>& ia, const double* w, int i0, int len, T* sw) {
+  if (ia.st != nullptr) {
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = wid; i < len; i += GMF_THREADS / 32) {
+      const T v = interp_bie_value(ia, i0 + i, lane);
+      if (lane == 0) sw[i] = v;
+    }
+  } else {
+    for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = (T)w[i0 + i];
+  }
+  __syncthreads();
+}
+
 // Dynamic shared memory: sV[(m+1) Rp] | sH[(m+1)(m+1)] (hsmem) | sw[Rp], elements of T.
 // T is the arithmetic of the Gram-Schmidt passes, the rotations and the update of x, and the
 // type of the stored basis V: double, or float for the inner solve of the mixed-precision
@@ -671,7 +688,7 @@ __device__ __forceinline__ void gmf_close(GmresCtl* ctl, unsigned rank, cudaGrap
 template <typename T>
 __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V, int ldv, const double* w,
                                                             const double* b, double* x, double* gin, float* gin_f,
-                                                            int n, int R, int hsmem, int push,
+                                                            int n, int R, int hsmem, int push, InterpArgs<T> ia,
                                                             cudaGraphConditionalHandle hcond, int use_cond, int cap) {
   extern __shared__ __align__(16) unsigned char gmf_dyn[];
   T* dsm = (T*)gmf_dyn;
@@ -716,9 +733,10 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
   if (s_phase == PH_RESID) {
     // r = b - A x, ||r||; restart from r / ||r|| unless converged or out of iterations
     pdl_wait();
+    gmf_w_slice(ia, w, i0, len, sw);
     T ss = 0;
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
-      const T r = (T)(b[i0 + i] - w[i0 + i]);
+      const T r = (T)(b[i0 + i] - (double)sw[i]);
       sw[i] = r;
       ss += r * r;
     }
@@ -825,7 +843,7 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
       if (t0 == 0) {
         // V and the rotations were complete before the apply started; w is its output
         pdl_wait();
-        if (tid < len) w_r = w[i0 + tid];
+        if (ia.st == nullptr && tid < len) w_r = w[i0 + tid];
       }
 #pragma unroll
       for (int u = 0; u < NB; ++u)
@@ -837,9 +855,12 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
       ssn[tid] = (T)sn_r;
     }
     if (tid == 0) s_gj = (T)gj_r;
-    if (tid < len) sw[tid] = (T)w_r;
-    for (int i = tid + GMF_THREADS; i < len; i += GMF_THREADS) sw[i] = (T)w[i0 + i];
+    if (ia.st == nullptr) {
+      if (tid < len) sw[tid] = (T)w_r;
+      for (int i = tid + GMF_THREADS; i < len; i += GMF_THREADS) sw[i] = (T)w[i0 + i];
+    }
   }
+  if (ia.st != nullptr) gmf_w_slice(ia, w, i0, len, sw);
   __syncthreads();
   // two passes of classical Gram-Schmidt; the second also reduces ||w'||^2 (entry K)
   cta_dots(sV, Rp, sw, len, K, false, part[0]);
@@ -1243,18 +1264,24 @@ static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, c
   const int n = c->n;
   const int* done = &c->gctl->done;
   int layer = kind == KFBI_BIE_STEFAN_SL ? KFBI_SINGLE : KFBI_DOUBLE;
-  KFBI_CHECK(apply_enqueue(c, layer, fp32, c->gin, c->gw, nullptr, nullptr, kind, eps_v, done, c->gin_f));
+  // the float32 Gram-Schmidt kernel forms A v itself from the apply's probe values and jumps
+  // (the apply then stops before its interpolation kernel)
+  const bool fuse = gf.cs > 0 && gf.f32 && fp32 && c->fuse_interp;
+  KFBI_CHECK(apply_enqueue(c, layer, fp32, c->gin, c->gw, nullptr, nullptr, kind, eps_v, done, c->gin_f, fuse));
   const int ldv = c->max_nodes;
   if (gf.cs > 0) {
     cudaLaunchAttribute attr[2];
     cudaLaunchConfig_t cfg = gmf_launch_config(c, gf, attr);
     launched(c, 1);
-    if (gf.f32)
+    if (gf.f32) {
+      const InterpArgs<float> ia = fuse ? interp_args_f32(c, kind, eps_v, c->gin_f) : InterpArgs<float>{};
       KFBI_TRY(cudaLaunchKernelEx(&cfg, k_gm_cluster<float>, c->gctl, c->gVf, ldv, (const double*)c->gw, b, x,
-                                  c->gin, c->gin_f, n, gf.R, gf.hsmem, gf.push, hcond, use_cond, cap));
-    else
+                                  c->gin, c->gin_f, n, gf.R, gf.hsmem, gf.push, ia, hcond, use_cond, cap));
+    } else {
       KFBI_TRY(cudaLaunchKernelEx(&cfg, k_gm_cluster<double>, c->gctl, c->gV, ldv, (const double*)c->gw, b, x,
-                                  c->gin, c->gin_f, n, gf.R, gf.hsmem, gf.push, hcond, use_cond, cap));
+                                  c->gin, c->gin_f, n, gf.R, gf.hsmem, gf.push, InterpArgs<double>{}, hcond, use_cond,
+                                  cap));
+    }
     return KFBI_OK;
   }
   const int dblocks = c->gm_m + 1;

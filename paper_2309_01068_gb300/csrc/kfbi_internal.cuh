@@ -89,6 +89,56 @@ struct StencilF {
   float w;
 };
 
+template <typename T>
+struct StencilOf;
+template <>
+struct StencilOf<double> {
+  using type = Stencil;
+};
+template <>
+struct StencilOf<float> {
+  using type = StencilF;
+};
+
+// Inputs of the interpolation and boundary-integral epilogue of an apply (the last step of
+// k_interp), so that a consumer of the apply's values can form them itself; st = nullptr:
+// not in use.
+template <typename T>
+struct InterpArgs {
+  const typename StencilOf<T>::type* st = nullptr;
+  const T* pval = nullptr;    // probe values
+  const T* Jall = nullptr;    // jumps of the crossings, then of the nodes
+  const int* ncr = nullptr;   // crossing count (device)
+  const T* x_in = nullptr;    // density (identity term)
+  const double* eps_v = nullptr;
+  const T* dint = nullptr;    // density integral (Hele-Shaw operator)
+  T ca = 0, cb = 1, cc = 0;
+};
+
+// The value k_interp writes for node p: b_m = u(q_m) + [q_m in Omega-] C(q_m), v+ = r0.b,
+// value = v+ - [u]/2, out = a x + b value + c int(x) ds, in the same operation order. Called by
+// all 32 lanes of a warp (lanes 0..5 take the stencil points); the result is valid in lane 0.
+template <typename T>
+__device__ __forceinline__ T interp_bie_value(const InterpArgs<T>& a, int p, int lane) {
+  const typename StencilOf<T>::type& S = a.st[p];
+  const T* J = a.Jall ? a.Jall + ((long)*a.ncr + p) * 6 : nullptr;
+  T v = 0;
+  if (lane < 6) {
+    const T dx = (T)S.dx[lane], dy = (T)S.dy[lane];
+    T u = a.pval[S.probe[lane]];
+    if (J != nullptr && S.minus[lane]) {
+      u += J[0] + dx * J[1] + dy * J[2] + (T)0.5 * dx * dx * J[3] + dx * dy * J[5] + (T)0.5 * dy * dy * J[4];
+    }
+    v = (T)S.r0[lane] * u;
+  }
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (J != nullptr) v -= (T)0.5 * J[0];
+  T out = a.cb * v;
+  if (a.x_in != nullptr) out += (a.eps_v != nullptr ? (T)a.eps_v[p] : a.ca) * a.x_in[p];
+  if (a.dint != nullptr) out += a.cc * (*a.dint);
+  return out;
+}
+
 // GMRES control block in device memory. The scalar header comes first so that the host
 // can poll it without copying the arrays.
 struct GmresCtl {
@@ -259,6 +309,7 @@ struct kfbi_ctx {
   float* gVf = nullptr;         // [(MAX_RESTART+1)][max_nodes] float32 basis (mixed precision)
   bool arn32 = true;            // KFBI_OPT_FP32_ARNOLDI
   bool gmf_push = true;         // KFBI_OPT_PUSH_REDUCE
+  bool fuse_interp = true;      // KFBI_OPT_FUSE_INTERP
   // device-driven refinement: control block, rhs / iterate / normal-derivative copies, and
   // one graph per (BIE kind, with normal derivative) holding the nested refinement loop
   kfbi::IrCtl* irctl = nullptr;
@@ -394,7 +445,10 @@ kfbi_status apply_setup_attributes(kfbi_ctx* c);
 kfbi_status ensure_cross_capacity(kfbi_ctx* c, int n_cross);
 kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* density, double* values,
                           double* dnormal, double* grid, int bie_kind, const double* eps_v,
-                          const int* skip_flag, const float* density_f = nullptr);
+                          const int* skip_flag, const float* density_f = nullptr, bool skip_interp = false);
+// the interpolation inputs of a float32 apply of the density density_f (what its k_interp
+// would read), for a consumer that forms the values itself (skip_interp = true)
+InterpArgs<float> interp_args_f32(kfbi_ctx* c, int bie_kind, const double* eps_v, const float* density_f);
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u);
 // free-space box: fills boxK / boxK_f for the current interface (after the node data)
 constexpr size_t BOXK_MAX_BYTES = (size_t)1 << 30;

@@ -22,6 +22,7 @@ OPT_CUDA_GRAPHS, OPT_CLUSTER_GMRES, OPT_LAST_CLUSTER, OPT_PDL, OPT_CLUSTER_SIZE,
 OPT_BOX_MATRIX = 7
 OPT_FP32_ARNOLDI = 8
 OPT_PUSH_REDUCE = 9
+OPT_FUSE_INTERP = 10
 MLP_FEATURES, MLP_MODES = 47, 16
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2

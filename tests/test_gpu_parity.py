@@ -251,6 +251,30 @@ def test_solve_graph_reused_across_interfaces(precision):
     assert len(crossings) > 1
 
 
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_fused_interpolation_is_the_separate_kernel(kind):
+    """Mixed precision: the float32 Gram-Schmidt kernel forming A v from the apply's probe
+    values and jumps gives bit for bit the iterates of the separate interpolation kernel
+    (same arithmetic), for the three boundary integral equations; and matches the oracle."""
+    boxbc = {0: 0, 1: 2, 2: 1}[kind]
+    kappa = 40.0 if kind == 2 else 0.0
+    p = W.random_problem(91 + kind, N=128, n=120, box=1.0 if kind != 1 else 1.5)
+    ctx, ref = make(p, boxbc, precision=K.MIXED, kappa=kappa)
+    ev = np.full(p.n, 0.3)
+    rhs = W.random_density(17, p.n)
+    out = []
+    for fuse in (1, 0):
+        ctx.set_option(K.OPT_FUSE_INTERP, fuse)
+        assert ctx.get_option(K.OPT_FUSE_INTERP) == fuse
+        phi, info = ctx.solve_bie(kind, dev(rhs), tol=1e-10, max_iter=300, restart=100,
+                                  eps_v=dev(ev) if kind == 2 else None)
+        assert info["status"] == 0
+        out.append((phi.clone(), info["iterations"]))
+    assert torch.equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    rphi, _ = gmres(lambda v: ref.bie_matvec(kind, v, eps_v=ev), rhs, tol=1e-13)
+    assert rel(out[0][0].cpu().numpy(), rphi) < 1e-8
+
+
 def test_gmres_cluster_long_restart_without_staged_hessenberg():
     """Restart 200: the Hessenberg matrix does not fit in the cluster's shared memory beside
     V, so the back substitution reads it from global memory; density vs the oracle."""
