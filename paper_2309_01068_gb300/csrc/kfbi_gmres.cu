@@ -666,14 +666,16 @@ __device__ __forceinline__ void gmf_close(GmresCtl* ctl, unsigned rank, cudaGrap
 
 // sw[i] = A v at node i0 + i for i < len: formed here from the apply's probe values and
 // jumps (ia.st != nullptr; the apply then stops before its interpolation kernel) or read from
-// the apply's output w. One warp per node for the former. Ends with __syncthreads.
+// the apply's output w. Eight lanes per node for the former. Ends with __syncthreads.
 template <typename T>
 __device__ __forceinline__ void gmf_w_slice(const InterpArgs<T>& ia, const double* w, int i0, int len, T* sw) {
   if (ia.st != nullptr) {
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = wid; i < len; i += GMF_THREADS / 32) {
-      const T v = interp_bie_value(ia, i0 + i, lane);
-      if (lane == 0) sw[i] = v;
+    // 8 lanes per node (6 stencil points), GMF_THREADS / 8 nodes at a time
+    const int m = threadIdx.x & 7;
+    for (int base = 0; base < len; base += GMF_THREADS / 8) {
+      const int i = base + (int)(threadIdx.x >> 3);
+      const T v = interp_bie_value(ia, i0 + i, m, i < len);
+      if (m == 0 && i < len) sw[i] = v;
     }
   } else {
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) sw[i] = (T)w[i0 + i];

@@ -117,21 +117,27 @@ struct InterpArgs {
 
 // The value k_interp writes for node p: b_m = u(q_m) + [q_m in Omega-] C(q_m), v+ = r0.b,
 // value = v+ - [u]/2, out = a x + b value + c int(x) ds, in the same operation order. Called by
-// all 32 lanes of a warp (lanes 0..5 take the stencil points); the result is valid in lane 0.
+// the 8 lanes of an aligned lane group (lanes m = 0..5 of the group take the stencil points;
+// every lane of the warp calls it, active = false for a group without a node); the result
+// is valid in the group's lane 0.
 template <typename T>
-__device__ __forceinline__ T interp_bie_value(const InterpArgs<T>& a, int p, int lane) {
-  const typename StencilOf<T>::type& S = a.st[p];
-  const T* J = a.Jall ? a.Jall + ((long)*a.ncr + p) * 6 : nullptr;
+__device__ __forceinline__ T interp_bie_value(const InterpArgs<T>& a, int p, int m, bool active) {
   T v = 0;
-  if (lane < 6) {
-    const T dx = (T)S.dx[lane], dy = (T)S.dy[lane];
-    T u = a.pval[S.probe[lane]];
-    if (J != nullptr && S.minus[lane]) {
-      u += J[0] + dx * J[1] + dy * J[2] + (T)0.5 * dx * dx * J[3] + dx * dy * J[5] + (T)0.5 * dy * dy * J[4];
+  const T* J = nullptr;
+  if (active) {
+    const typename StencilOf<T>::type& S = a.st[p];
+    J = a.Jall ? a.Jall + ((long)*a.ncr + p) * 6 : nullptr;
+    if (m < 6) {
+      const T dx = (T)S.dx[m], dy = (T)S.dy[m];
+      T u = a.pval[S.probe[m]];
+      if (J != nullptr && S.minus[m]) {
+        u += J[0] + dx * J[1] + dy * J[2] + (T)0.5 * dx * dx * J[3] + dx * dy * J[5] + (T)0.5 * dy * dy * J[4];
+      }
+      v = (T)S.r0[m] * u;
     }
-    v = (T)S.r0[lane] * u;
   }
-  for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, 8);
+  if (!active) return 0;
   if (J != nullptr) v -= (T)0.5 * J[0];
   T out = a.cb * v;
   if (a.x_in != nullptr) out += (a.eps_v != nullptr ? (T)a.eps_v[p] : a.ca) * a.x_in[p];
