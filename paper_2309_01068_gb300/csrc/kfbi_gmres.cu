@@ -668,13 +668,21 @@ __device__ __forceinline__ void gmf_close(GmresCtl* ctl, unsigned rank, cudaGrap
 // jumps (ia.st != nullptr; the apply then stops before its interpolation kernel) or read from
 // the apply's output w. Eight lanes per node for the former. Ends with __syncthreads.
 template <typename T>
-__device__ __forceinline__ void gmf_w_slice(const InterpArgs<T>& ia, const double* w, int i0, int len, T* sw) {
+__device__ __forceinline__ InterpPre<T> gmf_w_pre(const InterpArgs<T>& ia, int i0, int len) {
+  const int i = (int)(threadIdx.x >> 3);
+  return ia.st != nullptr ? interp_pre(ia, i0 + i, (int)(threadIdx.x & 7), i < len) : InterpPre<T>{};
+}
+// pre: this thread's interp_pre for the first GMF_THREADS / 8 nodes (gmf_w_pre)
+template <typename T>
+__device__ __forceinline__ void gmf_w_slice(const InterpArgs<T>& ia, const InterpPre<T>& pre, const double* w, int i0,
+                                            int len, T* sw) {
   if (ia.st != nullptr) {
     // 8 lanes per node (6 stencil points), GMF_THREADS / 8 nodes at a time
     const int m = threadIdx.x & 7;
     for (int base = 0; base < len; base += GMF_THREADS / 8) {
       const int i = base + (int)(threadIdx.x >> 3);
-      const T v = interp_bie_value(ia, i0 + i, m, i < len);
+      const InterpPre<T> q = base == 0 ? pre : interp_pre(ia, i0 + i, m, i < len);
+      const T v = interp_finish(ia, q, i0 + i, m, i < len);
       if (m == 0 && i < len) sw[i] = v;
     }
   } else {
@@ -688,7 +696,7 @@ __device__ __forceinline__ void gmf_w_slice(const InterpArgs<T>& ia, const doubl
 // type of the stored basis V: double, or float for the inner solve of the mixed-precision
 // refinement (its operator is the float32 apply; the control block stays double).
 template <typename T>
-__global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V, int ldv, const double* w,
+__global__ void __launch_bounds__(GMF_THREADS, 1) k_gm_cluster(GmresCtl* ctl, T* V, int ldv, const double* w,
                                                             const double* b, double* x, double* gin, float* gin_f,
                                                             int n, int R, int hsmem, int push, InterpArgs<T> ia,
                                                             cudaGraphConditionalHandle hcond, int use_cond, int cap) {
@@ -734,8 +742,9 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
   int done = 0;
   if (s_phase == PH_RESID) {
     // r = b - A x, ||r||; restart from r / ||r|| unless converged or out of iterations
+    const InterpPre<T> pre = gmf_w_pre(ia, i0, len);
     pdl_wait();
-    gmf_w_slice(ia, w, i0, len, sw);
+    gmf_w_slice(ia, pre, w, i0, len, sw);
     T ss = 0;
     for (int i = threadIdx.x; i < len; i += GMF_THREADS) {
       const T r = (T)(b[i0 + i] - (double)sw[i]);
@@ -792,6 +801,7 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
   // the first NB * GMF_THREADS values of the V slice, then the w slice.
   const int j = s_j;
   const int K = j + 1;
+  const InterpPre<T> pre = gmf_w_pre(ia, i0, len);  // fixed with the interface: before the wait
   // push reductions (push = 1): receive rows for pass 1 (reused by the explicit norm) and
   // pass 2; the barriers expect every CTA's rows; the cluster barrier begun here tells the
   // other CTAs (before their first copy) that these barriers are initialised
@@ -862,7 +872,7 @@ __global__ void __launch_bounds__(GMF_THREADS) k_gm_cluster(GmresCtl* ctl, T* V,
       for (int i = tid + GMF_THREADS; i < len; i += GMF_THREADS) sw[i] = (T)w[i0 + i];
     }
   }
-  if (ia.st != nullptr) gmf_w_slice(ia, w, i0, len, sw);
+  if (ia.st != nullptr) gmf_w_slice(ia, pre, w, i0, len, sw);
   __syncthreads();
   // two passes of classical Gram-Schmidt; the second also reduces ||w'||^2 (entry K)
   cta_dots(sV, Rp, sw, len, K, false, part[0]);

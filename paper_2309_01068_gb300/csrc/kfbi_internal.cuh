@@ -116,25 +116,44 @@ struct InterpArgs {
 };
 
 // The value k_interp writes for node p: b_m = u(q_m) + [q_m in Omega-] C(q_m), v+ = r0.b,
-// value = v+ - [u]/2, out = a x + b value + c int(x) ds, in the same operation order. Called by
-// the 8 lanes of an aligned lane group (lanes m = 0..5 of the group take the stencil points;
-// every lane of the warp calls it, active = false for a group without a node); the result
-// is valid in the group's lane 0.
+// value = v+ - [u]/2, out = a x + b value + c int(x) ds, in the same operation order. Computed
+// by the 8 lanes of an aligned lane group (lanes m = 0..5 of the group take the stencil
+// points; every lane of the warp takes part, active = false for a group without a node); the
+// result is valid in the group's lane 0. interp_pre reads what the interface fixed (the
+// stencil point, the node's jump row), so that it can run before the wait for the apply;
+// interp_finish reads the apply's probe values and jumps and combines.
 template <typename T>
-__device__ __forceinline__ T interp_bie_value(const InterpArgs<T>& a, int p, int m, bool active) {
-  T v = 0;
+struct InterpPre {
+  int probe = 0, minus = 0;
+  T dx = 0, dy = 0, r0 = 0;
   const T* J = nullptr;
-  if (active) {
-    const typename StencilOf<T>::type& S = a.st[p];
-    J = a.Jall ? a.Jall + ((long)*a.ncr + p) * 6 : nullptr;
-    if (m < 6) {
-      const T dx = (T)S.dx[m], dy = (T)S.dy[m];
-      T u = a.pval[S.probe[m]];
-      if (J != nullptr && S.minus[m]) {
-        u += J[0] + dx * J[1] + dy * J[2] + (T)0.5 * dx * dx * J[3] + dx * dy * J[5] + (T)0.5 * dy * dy * J[4];
-      }
-      v = (T)S.r0[m] * u;
+};
+template <typename T>
+__device__ __forceinline__ InterpPre<T> interp_pre(const InterpArgs<T>& a, int p, int m, bool active) {
+  InterpPre<T> q;
+  if (!active) return q;
+  const typename StencilOf<T>::type& S = a.st[p];
+  q.J = a.Jall ? a.Jall + ((long)*a.ncr + p) * 6 : nullptr;
+  if (m < 6) {
+    q.probe = S.probe[m];
+    q.minus = S.minus[m];
+    q.dx = (T)S.dx[m];
+    q.dy = (T)S.dy[m];
+    q.r0 = (T)S.r0[m];
+  }
+  return q;
+}
+template <typename T>
+__device__ __forceinline__ T interp_finish(const InterpArgs<T>& a, const InterpPre<T>& q, int p, int m, bool active) {
+  T v = 0;
+  const T* J = q.J;
+  if (active && m < 6) {
+    const T dx = q.dx, dy = q.dy;
+    T u = a.pval[q.probe];
+    if (J != nullptr && q.minus) {
+      u += J[0] + dx * J[1] + dy * J[2] + (T)0.5 * dx * dx * J[3] + dx * dy * J[5] + (T)0.5 * dy * dy * J[4];
     }
+    v = q.r0 * u;
   }
   for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, 8);
   if (!active) return 0;
