@@ -327,6 +327,10 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             forms its slice of A v from the apply's probe values and jumps
  *                             (the apply's interpolation step, same arithmetic) instead of a
  *                             separate interpolation kernel; 0: the separate kernel.
+ *   KFBI_OPT_FUSE_DFT         1 (default): float32 applies with a power-of-two node count
+ *                             (16..4096) form the density's Fourier coefficients inside the
+ *                             jump kernel (a shared-memory FFT in every block) instead of a
+ *                             separate DFT kernel; 0: the separate kernel.
  * kfbi_set_option: value 0 or 1 unless stated. kfbi_get_option writes the value to *value (host).
  * Errors: ARG (unknown option, bad value, NULL, read-only option).
  */
@@ -340,7 +344,8 @@ enum {
   KFBI_OPT_BOX_MATRIX = 7,
   KFBI_OPT_FP32_ARNOLDI = 8,
   KFBI_OPT_PUSH_REDUCE = 9,
-  KFBI_OPT_FUSE_INTERP = 10
+  KFBI_OPT_FUSE_INTERP = 10,
+  KFBI_OPT_FUSE_DFT = 11
 };
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);

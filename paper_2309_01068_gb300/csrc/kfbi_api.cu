@@ -488,6 +488,8 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
     c->arn32 = value != 0;
   } else if (option == KFBI_OPT_FUSE_INTERP) {
     c->fuse_interp = value != 0;
+  } else if (option == KFBI_OPT_FUSE_DFT) {
+    c->fuse_dft = value != 0;
   } else if (option == KFBI_OPT_PUSH_REDUCE) {
     c->gmf_push = value != 0;
     c->gmf = c->gmf32 = kfbi_ctx::GmfConfig{};
@@ -517,6 +519,7 @@ kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
   else if (option == KFBI_OPT_FP32_ARNOLDI) *value = c->arn32 ? 1 : 0;
   else if (option == KFBI_OPT_PUSH_REDUCE) *value = c->gmf_push ? 1 : 0;
   else if (option == KFBI_OPT_FUSE_INTERP) *value = c->fuse_interp ? 1 : 0;
+  else if (option == KFBI_OPT_FUSE_DFT) *value = c->fuse_dft ? 1 : 0;
   else return KFBI_ERR_ARG;
   return KFBI_OK;
 }

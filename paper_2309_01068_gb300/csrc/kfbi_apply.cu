@@ -7,8 +7,11 @@
 // Data flow of one apply (N x N grid, spectral grid `spec` row-major [j][k]):
 //   k_dens_coef      density Fourier coefficients (DFT, exact twiddle indexing)
 //   k_target_jumps   jumps at every crossing and node from the coefficients
+//   k_jumps_fft      (float32, power-of-two n) both of the above in one kernel, the
+//                    coefficients by a shared-memory FFT in every block
 //   k_box_data       free-space box data on the four faces (Hele-Shaw box only)
-//   k_face_dst       DST-II along x of the two dense face rows (Hele-Shaw box only)
+//   k_face_dst       DST-II along x of the two dense face rows (Hele-Shaw box only; with the
+//                    box table its face rows are pre-transformed and this kernel is skipped)
 //   k_row_forward    per row: corrections at its irregular nodes + box terms -> DST along x
 //   k_col_solve      per column: DST along y, divide by the eigenvalue, inverse along y
 //   k_probe_values   inverse along x only at the interpolation points
@@ -290,6 +293,119 @@ __global__ void k_target_jumps(const V2<T>* coef, int n, const int* ncr, const G
   if (lane < 6) Jout[(long)t * 6 + lane] = v;
 }
 
+// The jumps of k_target_jumps with the density's coefficients formed inside every block, for
+// the float32 inner applies with a power-of-two node count n <= 4096 (in place of k_dens_coef
+// + k_target_jumps: one launch and one global round trip fewer per apply). Each block takes
+// the length-n FFT of the density in shared memory (c_k = X_k / n, the same coefficients as
+// the DFT of k_dens_coef up to rounding order), lays them out as k_target_jumps does and
+// evaluates its eight targets; block 0 also forms int phi ds. Shared memory: two buffers of
+// max(n, jump layout) complex values and the staged FFT twiddles (at most 96 KB at n = 4096).
+__host__ __device__ inline int jfft_buf(int n) {
+  const int l = jump_layout_size(n);
+  return n > l ? n : l;
+}
+__host__ __device__ inline size_t jfft_smem(int n, int logn) {
+  return sizeof(V2<float>) * (2 * (size_t)jfft_buf(n) + (size_t)staged_count(n, logn));
+}
+constexpr int JFFT_THREADS = 256;
+constexpr int JFFT_PER = 4096 / JFFT_THREADS;  // density values per thread at most
+
+template <typename G, typename S_t>
+__global__ void __launch_bounds__(JFFT_THREADS)
+    k_jumps_fft(const float* phi, int n, int logn, const V2<float>* twn, const S_t* st, float* dint, const int* ncr,
+                const G* tg, const V2<float>* tstart, int layer, float kappa, float* Jout, const int* skip) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ float red[JFFT_THREADS / 32];
+  const int L = jfft_buf(n);
+  V2<float>* A = (V2<float>*)smem_raw;
+  V2<float>* B = A + L;
+  V2<float>* stw = B + L;
+  const int ntg = *ncr + n;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if ((int)blockIdx.x * (JFFT_THREADS / 32) >= ntg) {
+    pdl_wait();  // no target in this block (the grid covers the crossing capacity)
+    return;
+  }
+  // fixed with the interface, read before the wait: the target's geometry and twiddle starts,
+  // the FFT's staged twiddles w^{r jm n / (4 Ns)} = conj(e^{2 pi i r jm / (4 Ns)}) from the
+  // node roots, and (block 0) the arclength weights of the density integral
+  G geo{};
+  V2<float> e0{}, s1{}, q{};
+  if (t < ntg) {
+    geo = tg[t];
+    const V2<float>* ts = tstart + (long)t * TSTART_STRIDE;
+    e0 = ts[lane];
+    s1 = ts[32];
+    q = ts[33];
+  }
+  const int cnt = staged_count(n, logn);
+  for (int i = threadIdx.x; i < cnt; i += JFFT_THREADS) {
+    int off = 0, Ns = (logn & 1) ? 2 : 1;
+    while (i >= off + 3 * Ns) {
+      off += 3 * Ns;
+      Ns <<= 2;
+    }
+    const int r = (i - off) / Ns + 1, jm = (i - off) - (r - 1) * Ns;
+    const V2<float> w = twn[r * jm * (n / (4 * Ns))];
+    stw[i] = V2<float>{w.x, -w.y};
+  }
+  const bool want_int = blockIdx.x == 0 && dint != nullptr;
+  float wt[JFFT_PER];
+#pragma unroll
+  for (int u = 0; u < JFFT_PER; ++u) {
+    const int j = threadIdx.x + u * JFFT_THREADS;
+    wt[u] = (want_int && j < n) ? st[j].w : 0.0f;
+  }
+  pdl_wait();
+  // the density and the skip flag in one round trip
+  float v[JFFT_PER];
+#pragma unroll
+  for (int u = 0; u < JFFT_PER; ++u) {
+    const int j = threadIdx.x + u * JFFT_THREADS;
+    v[u] = j < n ? phi[j] : 0.0f;
+  }
+  if (*skip) return;
+  if (want_int) {
+    float s = 0.0f;
+#pragma unroll
+    for (int u = 0; u < JFFT_PER; ++u) s += v[u] * wt[u];
+    s = wsum(s);
+    if (lane == 0) red[threadIdx.x >> 5] = s;
+  }
+#pragma unroll
+  for (int u = 0; u < JFFT_PER; ++u) {
+    const int j = threadIdx.x + u * JFFT_THREADS;
+    if (j < n) A[j] = V2<float>{v[u], 0.0f};
+  }
+  __syncthreads();
+  if (want_int && threadIdx.x < 32) {
+    float s = threadIdx.x < JFFT_THREADS / 32 ? red[threadIdx.x] : 0.0f;
+    s = wsum(s);
+    if (threadIdx.x == 0) *dint = s;
+  }
+  const V2<float>* X = fft_stockham<float>(A, B, 1, n, logn, stw, false);
+  V2<float>* w = X == A ? B : A;
+  const float inv_n = 1.0f / (float)n;
+  const int S = jump_stride(n), K = (n - 1) / 2, chunk = jump_chunk(n);
+  for (int k = 1 + (int)threadIdx.x; k <= K; k += JFFT_THREADS) {
+    const int l = (k - 1) / chunk;
+    w[1 + l * S + (k - 1 - l * chunk)] = V2<float>{X[k].x * inv_n, X[k].y * inv_n};
+  }
+  if (threadIdx.x == 0) {
+    w[0] = V2<float>{X[0].x * inv_n, X[0].y * inv_n};
+    w[1 + 32 * S] = V2<float>{X[n / 2].x * inv_n, X[n / 2].y * inv_n};  // n is even
+  }
+  __syncthreads();
+  if (t >= ntg) return;
+  float J[6];
+  jump_eval<float, G>(w + 1 + lane * S, w[0], w[1 + 32 * S], n, e0, s1, q, geo, layer, kappa, lane, J);
+  float o = J[5];
+#pragma unroll
+  for (int r = 4; r >= 0; --r) o = lane == r ? J[r] : o;
+  if (lane < 6) Jout[(long)t * 6 + lane] = o;
+}
+
 // Free-space box data (Sec. 4.1): g(p) = (1/n) sum_l phi_l (X_l - p).(y_a, -x_a)_l / |X_l - p|^2
 // at the 4N face midpoints (west, east, south, north), stored pre-scaled as the
 // right-hand side term -2 g / h^2. npack[l] = (x, y, y_a, -x_a) of node l.
@@ -511,6 +627,54 @@ __global__ void k_face_dst(int N, int logN, int dct, const V2<T>* tw, const T* t
       int kNm = dct ? N - m : m - 1;
       out[kNm] = XNm.x;
       out[N + kNm] = XNm.y;
+    }
+  }
+}
+
+// The free-space box table's south and north rows replaced by their DST-II along the face,
+// node column by node column: row 2N + k becomes sum_i S_k(i) K[2N + i][l] (S_k as in the row
+// transform below) and row 3N + k the same for the north face. The box product K phi then
+// yields the two dense face rows' x-transforms directly, so no apply needs k_face_dst.
+// One block per node column: the column's south and north values as one complex FFT
+// (Makhoul reordering, as k_face_dst), in float64, written to both tables.
+__global__ void k_box_face_table(int N, int logN, int ld, const V2<double>* tw, const double* tab, double* K,
+                                 float* Kf) {
+  extern __shared__ unsigned char smem_raw[];
+  V2<double>* A = (V2<double>*)smem_raw;
+  V2<double>* B = A + N;
+  V2<double>* sTw = B + N;
+  stage_twiddles(tw, sTw, staged_count(N, logN));
+  const long l = blockIdx.x;
+  double* ks = K + (long)2 * N * ld + l;
+  double* kn = K + (long)3 * N * ld + l;
+  float* fs = Kf + (long)2 * N * ld + l;
+  float* fn = Kf + (long)3 * N * ld + l;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double a = ks[(long)i * ld], b = kn[(long)i * ld];
+    if (i & 1) {
+      a = -a;
+      b = -b;
+    }
+    A[mk_pos(i, N)] = V2<double>{a, b};
+  }
+  __syncthreads();
+  const V2<double>* X = fft_stockham<double>(A, B, 1, N, logN, sTw, false);
+  for (int m = threadIdx.x; m <= N / 2; m += blockDim.x) {
+    V2<double> Xm, XNm;
+    double cm, sm;
+    dct_cs<double>(tab, N, m, cm, sm);
+    dct_post<double>(X, N, m, cm, sm, Xm, XNm);
+    const long km = (long)(N - 1 - m) * ld;
+    ks[km] = Xm.x;
+    kn[km] = Xm.y;
+    fs[km] = (float)Xm.x;
+    fn[km] = (float)Xm.y;
+    if (m > 0 && m < N / 2) {
+      const long kNm = (long)(m - 1) * ld;
+      ks[kNm] = XNm.x;
+      kn[kNm] = XNm.y;
+      fs[kNm] = (float)XNm.x;
+      fn[kNm] = (float)XNm.y;
     }
   }
 }
@@ -1028,6 +1192,10 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   } else {
     dens_t = (const T*)density;
   }
+  // with the box table, its south and north rows hold the face rows' transforms (the box
+  // product writes them to boxg[2N, 4N), which the row transform adds to rows 0 and N - 1)
+  const bool face_from_table = fs && c->boxK_ok && c->use_boxK;
+  if (face_from_table) face = boxg + 2 * N;
   if (fs) {
     // the box quadrature and its face transform depend only on the density: they run on the
     // side stream while the coefficients and jumps are formed, and join before the row transform
@@ -1036,7 +1204,7 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     KFBI_TRY(cudaStreamWaitEvent(s2, c->ev_fork, 0));
     const size_t smb = (size_t)n * sizeof(T4);
     const T bscale = (T)(-2.0 / (c->h * c->h * (double)n));
-    if (c->boxK_ok && c->use_boxK) {
+    if (face_from_table) {
       const T* Kt = sizeof(T) == 8 ? (const T*)c->boxK : (const T*)c->boxK_f;
       if (((uintptr_t)dens_t & (4 * sizeof(T) - 1)) == 0)
         k_box_gemv<T, true><<<cdiv((long)4 * N * 32, 256), 256, 0, s2>>>(Kt, box_ld(n), dens_t, n, 4 * N, boxg, skip);
@@ -1048,35 +1216,52 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     else
       k_box_data<T, T4, false><<<cdiv((long)4 * N * 32, 256), 256, 0, s2>>>(
           dens_t, n, Tabs<T>::npack(c), N, c->xmin, c->xmax, c->ymin, c->ymax, c->h, bscale, boxg, skip);
-    size_t smf = 3 * sizeof(V2<T>) * (size_t)N;
-    KFBI_TRY(launch_k(c->use_pdl, k_face_dst<T>, dim3(1), dim3(256), smf, s2, N, c->logN, dct, Tabs<T>::stw(c), tab,
-                      (const T*)boxg, face, skip));
+    if (!face_from_table) {
+      size_t smf = 3 * sizeof(V2<T>) * (size_t)N;
+      KFBI_TRY(launch_k(c->use_pdl, k_face_dst<T>, dim3(1), dim3(256), smf, s2, N, c->logN, dct, Tabs<T>::stw(c),
+                        tab, (const T*)boxg, face, skip));
+    }
     KFBI_TRY(cudaEventRecord(c->ev_join, s2));
-    launched(c, 2);
-  }
-  const size_t smd = (size_t)n * (sizeof(V2<T>) + sizeof(T));
-  if (smd <= SMEM_STAGE_MAX) {
-    using SD = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(c))>::type>::type;
-    KFBI_TRY(launch_k(c->use_pdl, k_dens_coef<T, true, SD>, dim3(cdiv((long)nk * 32, 256)), dim3(256), smd, s,
-                      (const T*)dens_t, n, Tabs<T>::twn(c), Tabs<T>::stencil(c), (V2<T>*)coef,
-                      (T*)(want_int ? dint_t : nullptr), skip));
-  } else {
-    k_dens_coef<T, false><<<cdiv((long)nk * 32, 256), 256, 0, s>>>(dens_t, n, Tabs<T>::twn(c), Tabs<T>::stencil(c),
-                                                                   coef, want_int ? dint_t : nullptr, skip);
+    launched(c, face_from_table ? 1 : 2);
   }
   // launch shapes from capacities and device counts: the same launches serve every interface
   // of this layout (a captured graph is kept across interfaces)
   const int* d_ncr = c->seg_off + 2 * SUBSAMPLES * n;
   const int ntg_cap = c->ncr_grid + n;
   using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
-  const size_t smj = (size_t)jump_layout_size(n) * sizeof(V2<T>);
-  if (smj <= SMEM_STAGE_MAX)
-    KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, true>, dim3(cdiv((long)ntg_cap * 32, 256)), dim3(256), smj, s,
-                      (const V2<T>*)coef, n, d_ncr, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
-  else
-    KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, false>, dim3(cdiv((long)ntg_cap * 32, 256)), dim3(256), 0, s,
-                      (const V2<T>*)coef, n, d_ncr, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
-  launched(c, 2);
+  using SD = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(c))>::type>::type;
+  bool fused = false;
+  if constexpr (sizeof(T) == 4) {
+    // float32, power-of-two n: coefficients and jumps in one kernel
+    if (c->fuse_dft && n >= 16 && n <= 4096 && (n & (n - 1)) == 0) {
+      const int logn = ilog2(n);
+      KFBI_TRY(launch_k(c->use_pdl, k_jumps_fft<G, SD>, dim3(cdiv((long)ntg_cap * 32, JFFT_THREADS)),
+                        dim3(JFFT_THREADS), jfft_smem(n, logn), s, (const float*)dens_t, n, logn, Tabs<T>::twn(c),
+                        Tabs<T>::stencil(c), (float*)(want_int ? dint_t : nullptr), d_ncr, Tabs<T>::geo(c),
+                        Tabs<T>::tstart(c), layer, (float)c->kappa, (float*)J, skip));
+      launched(c, 1);
+      fused = true;
+    }
+  }
+  if (!fused) {
+    const size_t smd = (size_t)n * (sizeof(V2<T>) + sizeof(T));
+    if (smd <= SMEM_STAGE_MAX) {
+      KFBI_TRY(launch_k(c->use_pdl, k_dens_coef<T, true, SD>, dim3(cdiv((long)nk * 32, 256)), dim3(256), smd, s,
+                        (const T*)dens_t, n, Tabs<T>::twn(c), Tabs<T>::stencil(c), (V2<T>*)coef,
+                        (T*)(want_int ? dint_t : nullptr), skip));
+    } else {
+      k_dens_coef<T, false><<<cdiv((long)nk * 32, 256), 256, 0, s>>>(dens_t, n, Tabs<T>::twn(c), Tabs<T>::stencil(c),
+                                                                     coef, want_int ? dint_t : nullptr, skip);
+    }
+    const size_t smj = (size_t)jump_layout_size(n) * sizeof(V2<T>);
+    if (smj <= SMEM_STAGE_MAX)
+      KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, true>, dim3(cdiv((long)ntg_cap * 32, 256)), dim3(256), smj, s,
+                        (const V2<T>*)coef, n, d_ncr, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
+    else
+      KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, false>, dim3(cdiv((long)ntg_cap * 32, 256)), dim3(256), 0, s,
+                        (const V2<T>*)coef, n, d_ncr, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
+    launched(c, 2);
+  }
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   KFBI_TRY(launch_k(c->use_pdl, k_row_forward<T>, dim3(N), dim3(ROW_THREADS), 0, s, N, dct, (const int*)c->row_ptr,
                     (const IrrNode*)c->irr, (const T*)J, (T)(1.0 / (c->h * c->h)), (const T*)(fs ? boxg : nullptr),
@@ -1131,10 +1316,14 @@ static kfbi_status setup_t(kfbi_ctx*) {
   KFBI_TRY(cudaFuncSetAttribute(k_dens_coef<T, true, S_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
   KFBI_TRY(cudaFuncSetAttribute(k_box_data<T, T4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
   KFBI_TRY(cudaFuncSetAttribute(k_target_jumps<T, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
+  if constexpr (sizeof(T) == 4)
+    KFBI_TRY(cudaFuncSetAttribute(k_jumps_fft<G, S_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
   return KFBI_OK;
 }
 
 kfbi_status apply_setup_attributes(kfbi_ctx* c) {
+  KFBI_TRY(cudaFuncSetAttribute(k_box_face_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(3 * sizeof(V2<double>) * (size_t)MAX_GRID_N)));
   KFBI_CHECK(setup_t<double>(c));
   return setup_t<float>(c);
 }
@@ -1165,7 +1354,7 @@ InterpArgs<float> interp_args_f32(kfbi_ctx* c, int bie_kind, const double* eps_v
 
 kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n) {
   const int ld = box_ld(n);
-  launched(c, 1);
+  launched(c, 2);
   // on the aux stream after the node data: the applies' box products also run there (stream
   // order), graph launches and the next interface wait on ev_boxK (box_table_join)
   KFBI_TRY(cudaEventRecord(c->ev_boxK0, c->stream));
@@ -1173,6 +1362,8 @@ kfbi_status box_matrix_enqueue(kfbi_ctx* c, int n) {
   const dim3 grid(cdiv(ld, 128), 4, cdiv(c->N, BOXK_CHUNK));
   k_box_matrix<<<grid, 128, 0, c->aux>>>(c->N, n, ld, (const double4_32a*)c->npack, c->xmin, c->xmax, c->ymin,
                                          c->ymax, c->h, -2.0 / (c->h * c->h * (double)n), c->boxK, c->boxK_f);
+  k_box_face_table<<<n, 256, 3 * sizeof(V2<double>) * (size_t)c->N, c->aux>>>(
+      c->N, c->logN, ld, Tabs<double>::stw(c), Tabs<double>::sin(c), c->boxK, c->boxK_f);
   KFBI_TRY(cudaGetLastError());
   KFBI_TRY(cudaEventRecord(c->ev_boxK, c->aux));
   c->boxK_pending = true;

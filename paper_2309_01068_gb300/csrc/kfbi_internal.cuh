@@ -335,6 +335,7 @@ struct kfbi_ctx {
   bool arn32 = true;            // KFBI_OPT_FP32_ARNOLDI
   bool gmf_push = true;         // KFBI_OPT_PUSH_REDUCE
   bool fuse_interp = true;      // KFBI_OPT_FUSE_INTERP
+  bool fuse_dft = true;         // KFBI_OPT_FUSE_DFT
   // device-driven refinement: control block, rhs / iterate / normal-derivative copies, and
   // one graph per (BIE kind, with normal derivative) holding the nested refinement loop
   kfbi::IrCtl* irctl = nullptr;

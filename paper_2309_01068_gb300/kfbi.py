@@ -23,6 +23,7 @@ OPT_BOX_MATRIX = 7
 OPT_FP32_ARNOLDI = 8
 OPT_PUSH_REDUCE = 9
 OPT_FUSE_INTERP = 10
+OPT_FUSE_DFT = 11
 MLP_FEATURES, MLP_MODES = 47, 16
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2

@@ -140,7 +140,7 @@ def _dataset(ctx, seeds, n=None):
     return torch.cat(feats), torch.cat(targets), probs
 
 
-def test_trained_warm_start_saves_gmres_iterations():
+def test_trained_warm_start_lowers_initial_residual():
     ctx = K.Context(256, (-1.0, 1.0, -1.0, 1.0), 0.0, K.BOX_DIRICHLET0, K.FP64, max_nodes=512)
     X, T, _ = _dataset(ctx, range(1000, 1080))
     rows = X.shape[0]

@@ -275,6 +275,38 @@ def test_fused_interpolation_is_the_separate_kernel(kind):
     assert rel(out[0][0].cpu().numpy(), rphi) < 1e-8
 
 
+@pytest.mark.parametrize("kind,N,n", [(0, 256, 256), (1, 128, 128), (2, 128, 64), (1, 128, 96)])
+def test_fused_dft_jumps_match_separate_kernels(kind, N, n):
+    """KFBI_OPT_FUSE_DFT: float32 applies whose jump kernel takes the density's Fourier
+    coefficients (App. A.1 interpolant) from an FFT in every block agree with the separate DFT
+    kernel to float32 rounding, and their mixed solves match the oracle; n = 96 (not a power
+    of two) keeps the separate kernels, so the two settings give the same bits."""
+    boxbc = {0: 0, 1: 2, 2: 1}[kind]
+    kappa = 40.0 if kind == 2 else 0.0
+    p = W.random_problem(95 + kind, N=N, n=n, box=1.0 if kind != 1 else 1.5)
+    ctx, ref = make(p, boxbc, precision=K.MIXED, kappa=kappa)
+    ev = np.full(p.n, 0.3)
+    evd = dev(ev) if kind == 2 else None
+    x = W.random_density(19, p.n)
+    ys, phis = [], []
+    for fuse in (1, 0):
+        ctx.set_option(K.OPT_FUSE_DFT, fuse)
+        assert ctx.get_option(K.OPT_FUSE_DFT) == fuse
+        ys.append(ctx.bie_apply(kind, dev(x), eps_v=evd).cpu().numpy())
+        phi, info = ctx.solve_bie(kind, dev(x), tol=1e-10, max_iter=300, eps_v=evd)
+        assert info["status"] == 0
+        phis.append(phi.cpu().numpy())
+    d = rel(ys[0], ys[1])
+    print(f"kind {kind}, n {n}: fused vs separate float32 apply, max difference / max |value| = {d:.3e}")
+    if n & (n - 1):
+        assert d == 0.0
+    else:
+        assert d < 5e-5
+    rphi, _ = gmres(lambda v: ref.bie_matvec(kind, v, eps_v=ev), x, tol=1e-13)
+    for phi in phis:
+        assert rel(phi, rphi) < 1e-8
+
+
 def test_gmres_cluster_long_restart_without_staged_hessenberg():
     """Restart 200: the Hessenberg matrix does not fit in the cluster's shared memory beside
     V, so the back substitution reads it from global memory; density vs the oracle."""
@@ -309,6 +341,39 @@ def test_mixed_precision_refinement(graphs, arn32):
     assert info2["status"] == K.ERR_NOT_CONVERGED
 
 
+def test_mixed_form_keeps_second_order():
+    """u = D phi on the grid converges to e^x sin y at O(h^2) (Sec. 4.2, Sec. 4.3) when phi
+    comes from the mixed form (float32 grid applies, float64 refinement to 1e-10): the same
+    errors as from the float64 form, N = 64 .. 512 (node spacing 1.6 h)."""
+    errs, errs64, hs = [], [], []
+    for N in (64, 128, 256, 512):
+        p = W.config_small_laplace(N=N, n=max(64, N))
+        c64 = K.Context(p.N, p.box, 0.0, K.BOX_DIRICHLET0, K.FP64, max_nodes=p.n)
+        cmx = K.Context(p.N, p.box, 0.0, K.BOX_DIRICHLET0, K.MIXED, max_nodes=p.n)
+        for c in (c64, cmx):
+            c.set_interface(dev(p.xy))
+        rhs = dev(p.rhs)
+        phim, im = cmx.solve_bie(K.BIE_INTERIOR_DL, rhs, tol=1e-10, max_iter=600)
+        phi64, i64 = c64.solve_bie(K.BIE_INTERIOR_DL, rhs, tol=1e-10, max_iter=600)
+        assert im["status"] == 0 and i64["status"] == 0
+        h = (p.box[1] - p.box[0]) / N
+        x = p.box[0] + (np.arange(N) + 0.5) * h
+        y = p.box[2] + (np.arange(N) + 0.5) * h
+        X, Y = np.meshgrid(x, y)
+        exact = np.exp(X) * np.sin(Y)
+        inside = c64.sides().cpu().numpy() == 1
+        for phi, out in ((phim, errs), (phi64, errs64)):
+            _, _, u = c64.apply(K.DOUBLE, phi, grid=True)
+            out.append(np.abs(u.cpu().numpy() - exact)[inside].max())
+        hs.append(h)
+        cmx.close()
+        c64.close()
+    slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    assert slope > 1.8, (errs, slope)
+    for a, b in zip(errs, errs64):
+        assert abs(a - b) <= 0.01 * b, (errs, errs64)
+
+
 def test_interp_grid_and_box_solve_neumann():
     p = W.random_problem(51, N=128, n=96)
     ctx, ref = make(p, OK.BOX_NEUMANN0, kappa=20.0)
@@ -332,6 +397,36 @@ def test_hele_shaw_full_size_apply():
     assert np.array_equal(ctx.sides().cpu().numpy(), ref.cl.side)
     assert rel(vals.cpu().numpy(), rv) < 1e-11
     assert rel(dn.cpu().numpy(), rdn) < 1e-9
+
+
+def test_hele_shaw_full_size_mixed():
+    """The timed configuration: 1024^2, 1024 nodes, free-space box data, mixed form.
+
+    (1) One float32 apply (the inner GMRES operator) vs the oracle's float64 apply: within
+    2e-4 of max |value| (measured 3.9e-5). The float32 row transform's sines (absolute error
+    below 4e-7) multiply corrections of size |J|/h^2 at about 1500 irregular nodes; each such
+    error is a point source of strength ~4e-7 |J| in the solve, and their independent
+    contributions add up to sqrt(1500) ~ 40 times that at a node. (2) A mixed solve of the Hele-Shaw operator (Sec. 3.1) to
+    1e-8: its density's residual under the float64 operator of a separate float64 context
+    (pinned to the oracle at this size above) is within the tolerance."""
+    p = W.config_hele_shaw()
+    cmx, ref = make(p, OK.BOX_FREESPACE_DL, precision=K.MIXED)
+    dens = W.random_density(77, p.n, modes=20)
+    vals, _, _ = cmx.apply(K.DOUBLE, dev(dens))
+    rv, _, _ = ref.apply(OK.LAYER_DOUBLE, dens)
+    err32 = rel(vals.cpu().numpy(), rv)
+    print(f"float32 apply at 1024^2: max error / max |value| = {err32:.3e}")
+    assert err32 < 2e-4
+    rhs = dev(np.log(np.hypot(p.xy[:, 0], p.xy[:, 1])))  # J ln|x|, J = 1
+    phi, info = cmx.solve_bie(K.BIE_HS_EXTERIOR_MDL, rhs, tol=1e-8, max_iter=600)
+    assert info["status"] == 0 and info["rel_residual"] <= 1e-8
+    c64 = K.Context(p.N, p.box, 0.0, K.BOX_FREESPACE_DL, K.FP64, max_nodes=p.n)
+    c64.set_interface(dev(p.xy))
+    r = rhs - c64.bie_apply(K.BIE_HS_EXTERIOR_MDL, phi)
+    assert float(torch.linalg.norm(r) / torch.linalg.norm(rhs)) <= 1.5e-8
+    print(f"mixed solve at 1024^2: {info['iterations']} iterations, {info['refinements']} sweeps")
+    c64.close()
+    cmx.close()
 
 
 # ------------------------------------------------------------------- time steps
