@@ -474,11 +474,12 @@ __global__ void k_irr_emit(int N, double xmin, double ymin, double h, const uint
 // Also stores, per target, the twiddle starts of the per-apply density evaluation: lane l's
 // e^{i k0_l alpha} (k0_l = 1 + l chunk, chunk = ceil(K / 32)), then e^{i alpha} and
 // e^{i n alpha / 2}, in float64 and float32.
-__global__ void k_target_geo(const double2* coef, int n, int ncr, const double* cr_alpha, const double2* twn,
-                             TargetGeo* tg, TargetGeoF* tg_f, double2* tstart, float2* tstart_f) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// Targets [t_begin, t_end) of the ncr + n (crossings, then nodes), one warp each.
+__global__ void k_target_geo(const double2* coef, int n, int ncr, int t_begin, int t_end, const double* cr_alpha,
+                             const double2* twn, TargetGeo* tg, TargetGeoF* tg_f, double2* tstart, float2* tstart_f) {
+  int warp = t_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
-  if (warp >= ncr + n) return;
+  if (warp >= t_end) return;
   int nk = n / 2 + 1;
   double a = warp < ncr ? cr_alpha[warp] : (TWO_PI * (double)(warp - ncr)) / (double)n;
   // crossings: sincos at alpha; nodes alpha_j = 2 pi j / n: the node twiddle table
@@ -729,6 +730,17 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   KFBI_CHECK(ensure_cross_capacity(c, ncr));
   c->n_cross = ncr;
 
+  // the nodes' geometry and packed node data depend on the interpolant only: formed now, so
+  // that the free-space box table (aux stream, the longest part of an interface) is built
+  // while the crossings, sides, irregular nodes and stencils are found on this stream
+  c->boxK_ok = false;
+  launched(c, 2);
+  k_target_geo<<<cdiv((long)n * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, ncr, ncr, ncr + n, c->cr_alpha,
+                                                       (const double2*)c->twn, c->tgeo, c->tgeo_f,
+                                                       (double2*)c->tstart, (float2*)c->tstart_f);
+  k_npack<<<cdiv(n, 128), 128, 0, s>>>(n, c->xy, c->tgeo + ncr, (double4_32a*)c->npack, (float4*)c->npack_f);
+  if (c->boxK != nullptr) KFBI_CHECK(box_matrix_enqueue(c, n));
+
   launched(c, 4 + (ncr > 0 ? 2 : 0));
   k_emit_pairs<<<cdiv(2 * M, 256), 256, 0, s>>>(c->fine, M, c->xmin, c->ymin, h, N, c->seg_off, c->cr_kind,
                                                 c->cr_line, c->cr_seg);
@@ -752,22 +764,21 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   if (nirr > c->cap_irr) return KFBI_ERR_CAPACITY;
   c->n_irr = nirr;
 
-  launched(c, 7);
+  launched(c, 6 + (ncr > 0 ? 1 : 0));
   k_irr_emit<<<wblocks, 256, 0, s>>>(N, c->xmin, c->ymin, h, c->side, c->hcount, c->vcount, c->hid, c->vid,
                                      c->cr_xi, c->row_ptr, c->irr);
-  k_target_geo<<<cdiv((long)(ncr + n) * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, ncr, c->cr_alpha,
-                                                               (const double2*)c->twn, c->tgeo, c->tgeo_f,
-                                                               (double2*)c->tstart,
-                                                               (float2*)c->tstart_f);
+  if (ncr > 0)
+    k_target_geo<<<cdiv((long)ncr * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, ncr, 0, ncr, c->cr_alpha,
+                                                           (const double2*)c->twn, c->tgeo, c->tgeo_f,
+                                                           (double2*)c->tstart, (float2*)c->tstart_f);
   k_stencil<<<cdiv(n, 128), 128, 0, s>>>(n, c->xy, c->xmin, c->ymin, h, N, c->side, c->tgeo + ncr, c->stencil,
                                          c->probe_mark, c->flags);
   k_probe_count<<<wblocks, 256, 0, s>>>(N, c->probe_mark, c->prow_cnt);
   k_scan<<<1, 1024, 0, s>>>(c->prow_cnt, c->prow_ptr, N);
   k_probe_emit<<<wblocks, 256, 0, s>>>(N, c->probe_mark, c->prow_ptr, c->probe_i, c->probe_j);
   k_stencil_map<<<cdiv(n, 128), 128, 0, s>>>(n, c->probe_mark, c->stencil, c->stencil_f);
-  k_npack<<<cdiv(n, 128), 128, 0, s>>>(n, c->xy, c->tgeo + ncr, (double4_32a*)c->npack, (float4*)c->npack_f);
   k_prow_list<<<1, 32, 0, s>>>(N, c->prow_cnt, c->prow_list, c->counts);
-  launched(c, 2);
+  launched(c, 1);
   KFBI_TRY(cudaGetLastError());
   KFBI_TRY(cudaMemcpyAsync(&c->host_counts[0], c->prow_ptr + N, sizeof(int), cudaMemcpyDeviceToHost, s));
   KFBI_TRY(cudaMemcpyAsync(&c->host_counts[1], c->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -777,11 +788,7 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   if (c->host_counts[1] & FLAG_UNDERRES) return KFBI_ERR_UNDERRESOLVED;
   c->n_probe = c->host_counts[0];
   c->n_prow = c->host_counts[2];
-  c->boxK_ok = false;
-  if (c->boxK != nullptr) {
-    KFBI_CHECK(box_matrix_enqueue(c, n));
-    c->boxK_ok = true;
-  }
+  c->boxK_ok = c->boxK != nullptr;  // enqueued above
   if (c->n != n) c->layout_version += 1;
   if (c->n_cross > c->ncr_grid) {
     // the jump launches cover a quarter more crossings than this interface has, so that the
