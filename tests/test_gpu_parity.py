@@ -500,6 +500,33 @@ def test_errors():
     assert e.value.status == K.ERR_CAPACITY
 
 
+def test_freespace_context_recovers_after_rejected_interface():
+    """The free-space box table is built on a side stream as soon as the nodes' geometry is
+    known, before the interface can still be rejected (UNDERRESOLVED is found later). A
+    rejected interface leaves no interface in use, and the next valid one gets its own
+    table: the apply matches the oracle."""
+    bad = W.equal_arclength(W.polar(0.5, [(13, 0.45, 0.0)]), 256)["xy"]
+    box = (-1.5, 1.5, -1.5, 1.5)
+    with pytest.raises(OK.Underresolved):
+        OK.Kfbi(16, box, 0.0, OK.BOX_FREESPACE_DL).set_interface(bad)
+    ctx = K.Context(16, box, 0.0, K.BOX_FREESPACE_DL, K.FP64, max_nodes=256)
+    with pytest.raises(K.KfbiError) as e:
+        ctx.set_interface(dev(bad))
+    assert e.value.status == K.ERR_UNDERRESOLVED
+    with pytest.raises(K.KfbiError) as e:
+        ctx.apply(K.DOUBLE, torch.ones(256, dtype=torch.float64, device="cuda"))
+    assert e.value.status == K.ERR_STATE
+    p = W.random_problem(14, N=16, n=64, box=1.5)
+    ctx.set_interface(dev(p.xy))
+    ref = OK.Kfbi(p.N, p.box, 0.0, OK.BOX_FREESPACE_DL).set_interface(p.xy)
+    dens = W.random_density(15, p.n)
+    vals, _, _ = ctx.apply(K.DOUBLE, dev(dens))
+    rv, _, _ = ref.apply(OK.LAYER_DOUBLE, dens)
+    assert ctx.get_option(K.OPT_BOX_MATRIX) == 1
+    assert rel(vals.cpu().numpy(), rv) < 1e-11
+    ctx.close()
+
+
 def test_checkpoint_resume_bit_exact():
     """Writing back a read state and stepping reproduces the original step exactly."""
     p = W.config_hele_shaw(N=256, n=128, box=3.0)
