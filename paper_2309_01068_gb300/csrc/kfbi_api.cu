@@ -108,7 +108,7 @@ static void free_all(kfbi_ctx* c) {
                   c->seg_count, c->seg_off, c->cr_kind, c->cr_line, c->cr_seg, c->cr_first, c->cr_alpha, c->cr_xi,
                   c->tgeo, c->tgeo_f, c->rinv, c->stencil_f, c->dens_f, c->stw, c->stw_d, c->hcount, c->vcount, c->hid, c->vid, c->side, c->rowcnt, c->row_ptr, c->irr, c->stencil,
                   c->probe_mark, c->prow_cnt, c->prow_ptr, c->probe_i, c->probe_j, c->flags, c->counts, c->dcoef, c->dint,
-                  c->boxg, c->facespec, c->spec, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack, c->boxK, c->boxK_f,
+                  c->boxg, c->facespec, c->spec, c->rowinfo, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack, c->boxK, c->boxK_f,
                   c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gVf, c->gpart, c->gw,
                   c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag, c->irctl, c->ir_b, c->ir_x, c->ir_dn};
   for (void* p : ptrs)
@@ -205,6 +205,7 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->dint, 8));
   KFBI_CHECK(dalloc(&c->boxg, 4 * (size_t)N));
   KFBI_CHECK(dalloc(&c->spec, NN));
+  KFBI_CHECK(dalloc(&c->rowinfo, 2 * (size_t)N));
   KFBI_CHECK(dalloc(&c->probe_val, 6 * (size_t)max_nodes));
   KFBI_CHECK(dalloc(&c->tmp_vals, max_nodes));
   KFBI_CHECK(dalloc(&c->gctl, 1));

@@ -33,6 +33,12 @@ __device__ __forceinline__ T wsum(T v) {
 
 __device__ __forceinline__ float fdiv_t(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv_t(double a, double b) { return a / b; }
+template <typename T>
+__device__ __forceinline__ T qnan();
+template <>
+__device__ __forceinline__ float qnan<float>() { return __int_as_float(0x7fc00000); }
+template <>
+__device__ __forceinline__ double qnan<double>() { return __longlong_as_double(0x7ff8000000000000LL); }
 
 // largest dynamic shared memory a kernel stages its inputs in (bytes); larger inputs are read
 // from global memory
@@ -715,7 +721,7 @@ template <typename T>
 __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, const int* row_ptr, const IrrNode* irr,
                                                             const T* J, T inv_h2, const T* boxg,
                                                             const T* facespec, const T* tab, float scale, T* spec,
-                                                            const int* skip) {
+                                                            V2<T>* rowinfo, const int* skip) {
   __shared__ int si[ROW_CAP];
   __shared__ T sv[ROW_CAP];
   const int j = blockIdx.x;
@@ -733,6 +739,18 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
   }
   pdl_wait();
   if (*skip) return;
+  // rowinfo: a row without irregular nodes (other than a dense face row) holds only the box
+  // terms w S_k(0) + e S_k(N-1) (zero without box data); its pair (w, e) is stored for the
+  // column kernel, which forms the row itself, instead of its N values. Written rows are
+  // marked by a NaN in the first entry.
+  if (rowinfo != nullptr) {
+    const bool face_row = boxg != nullptr && (j == 0 || j == N - 1);
+    if (e == b && !face_row) {
+      if (threadIdx.x == 0) rowinfo[j] = V2<T>{w, ea};
+      return;
+    }
+    if (threadIdx.x == 0) rowinfo[j] = V2<T>{qnan<T>(), (T)0};
+  }
   const int per = (N + ROW_THREADS - 1) / ROW_THREADS;
   T acc[16];
 #pragma unroll
@@ -799,7 +817,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
 // grid size (N = 2^LOGN), so that the index arithmetic is constant.
 template <typename T, int LOGN>
 __global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* tab, const T* lam, T kappa, T* spec,
-                            const T* rinv, const int* skip) {
+                            const T* rinv, const V2<T>* rowinfo, const int* skip) {
   constexpr int N = 1 << LOGN, logN = LOGN;
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
@@ -821,15 +839,33 @@ __global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* 
     for (int t = threadIdx.x; t < N; t += blockDim.x) w[t] = lam[t];
     for (int m = threadIdx.x; m <= N / 2; m += blockDim.x) dct_cs<T>(tab, N, m, sCs[m].x, sCs[m].y);
   }
+  // rows the row transform did not write (rowinfo, see k_row_forward) are w S_k(0) + e S_k(N-1)
+  // for this thread's column k (blockDim is a multiple of W, so every element it loads is in
+  // the same column)
+  T s0 = 0, sN = 0;
+  if (rowinfo != nullptr) {
+    const int k = k0 + ((int)threadIdx.x & (W - 1));
+    if (dct) {
+      s0 = tsin(tab, k + N, N, qscale(N));
+      sN = tsin(tab, k * (2 * N - 1) + N, N, qscale(N));
+    } else {
+      s0 = tsin(tab, k + 1, N, qscale(N));
+      sN = tsin(tab, (k + 1) * (2 * N - 1), N, qscale(N));
+    }
+  }
   pdl_wait();
   if (*skip) return;
   const int tot = N * W;
   for (int t0 = 0; t0 < tot; t0 += 8 * (int)blockDim.x) {
     T buf[8];
+    V2<T> rbuf[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int t = t0 + u * (int)blockDim.x + (int)threadIdx.x;
-      if (t < tot) buf[u] = spec[(long)(t >> lw) * N + k0 + (t & (W - 1))];
+      if (t < tot) {
+        buf[u] = spec[(long)(t >> lw) * N + k0 + (t & (W - 1))];
+        if (rowinfo != nullptr) rbuf[u] = rowinfo[t >> lw];
+      }
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -837,6 +873,7 @@ __global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* 
       if (t < tot) {
         const int j = t >> lw, c = t & (W - 1);
         T v = buf[u];
+        if (rowinfo != nullptr && rbuf[u].x == rbuf[u].x) v = rbuf[u].x * s0 + rbuf[u].y * sN;
         if (!dct && (j & 1)) v = -v;
         ((T*)&A[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] = v;
       }
@@ -894,7 +931,8 @@ __global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* 
 }
 
 template <typename T>
-using ColKernel = void (*)(int, int, int, int, const V2<T>*, const T*, const T*, T, T*, const T*, const int*);
+using ColKernel = void (*)(int, int, int, int, const V2<T>*, const T*, const T*, T, T*, const T*, const V2<T>*,
+                           const int*);
 // the column kernel for N = 2^logN, 16 <= N <= 4096
 template <typename T>
 static ColKernel<T> col_kernel(int logN) {
@@ -1128,7 +1166,7 @@ static int col_threads(int N, int P) {
 }
 
 template <typename T>
-static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
+static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const V2<T>* rowinfo, const int* skip) {
   const int N = c->N;
   const int P = col_pairs<T>(N, c->col_P);
   size_t smem = col_smem<T>(N, P);
@@ -1136,7 +1174,7 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const int* skip) {
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
   KFBI_TRY(launch_k(c->use_pdl && !rec, col_kernel<T>(c->logN), dim3(N / (2 * P)), dim3(col_threads(N, P)), smem, c->stream, N,
                     c->logN, P, (int)(c->boxbc == KFBI_BOX_NEUMANN0), Tabs<T>::stw(c), Tabs<T>::sin(c), Tabs<T>::lam(c),
-                    (T)c->kappa, spec, sizeof(T) == 8 ? (const T*)c->rinv : nullptr, skip));
+                    (T)c->kappa, spec, sizeof(T) == 8 ? (const T*)c->rinv : nullptr, rowinfo, skip));
   launched(c, 1);
   if (rec) {
     KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used + 1], c->stream));
@@ -1265,9 +1303,9 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   KFBI_TRY(launch_k(c->use_pdl, k_row_forward<T>, dim3(N), dim3(ROW_THREADS), 0, s, N, dct, (const int*)c->row_ptr,
                     (const IrrNode*)c->irr, (const T*)J, (T)(1.0 / (c->h * c->h)), (const T*)(fs ? boxg : nullptr),
-                    (const T*)face, tab, scale, spec, skip));
+                    (const T*)face, tab, scale, spec, (V2<T>*)c->rowinfo, skip));
   launched(c, 1);
-  KFBI_CHECK(launch_col_solve<T>(c, spec, skip));
+  KFBI_CHECK(launch_col_solve<T>(c, spec, (const V2<T>*)c->rowinfo, skip));
   KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(cdiv((long)6 * n * 32, 256)), dim3(256), 0, s, N, dct,
                     (const int*)(c->prow_ptr + N), (const int*)c->probe_j, (const int*)c->probe_i, (const T*)spec, tab,
                     scale, pval, skip));
@@ -1380,7 +1418,7 @@ kfbi_status box_table_join(kfbi_ctx* c, cudaStream_t s) {
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u) {
   double* spec = c->spec;
   KFBI_CHECK(launch_row_dense<double>(c, 0, rhs, spec, nullptr));
-  KFBI_CHECK(launch_col_solve<double>(c, spec, c->zero_flag));
+  KFBI_CHECK(launch_col_solve<double>(c, spec, nullptr, c->zero_flag));
   KFBI_CHECK(launch_row_dense<double>(c, 1, nullptr, spec, u));
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
@@ -1492,7 +1530,7 @@ static kfbi_status grid_solve_noalloc_impl(int N, double h, double kappa, int bo
   const int P = col_pairs<double>(N);
   size_t sm_col = col_smem<double>(N, P);  // <= 28 KB for N <= 512
   col_kernel<double>(logN)<<<N / (2 * P), col_threads(N, P), sm_col, s>>>(N, logN, P, dct, (const V2<double>*)tw, tab, lam,
-                                                                  kappa, spec, nullptr, flag);
+                                                                  kappa, spec, nullptr, nullptr, flag);
   k_row_dense<double><<<N / 2, 256, sm_row, s>>>(N, logN, dct, 1, (const V2<double>*)tw, tab, nullptr, spec, u);
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;

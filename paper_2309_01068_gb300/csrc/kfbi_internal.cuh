@@ -293,6 +293,7 @@ struct kfbi_ctx {
   double* facespec = nullptr;   // [2N] transformed south / north face rows
   double* jumps = nullptr;      // [cap_cross + max_nodes][6] jumps at the targets (T)
   double* spec = nullptr;       // [N][N] row-transformed grid (T)
+  double* rowinfo = nullptr;    // [N] (w, e) of rows the row transform left to the column kernel (T pairs)
   double* probe_val = nullptr;  // [6*max_nodes] (T)
   double* tmp_vals = nullptr;   // [max_nodes]
 
