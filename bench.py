@@ -565,6 +565,17 @@ def main():
                     mean_gmres_iterations=float(np.mean([i["iterations"] for i in infos64])),
                     applies_per_s=fp64_applies,
                     col_kernel_mean_us=1e3 * tim64["fp64_ms"] / max(tim64["fp64_launches"], 1))
+        # accuracy of the mixed form on this workload: one step of each form from the same
+        # state; the float64 form is the one the parity tests pin to the oracle
+        outs = []
+        for state in (st, st64):
+            state.write(eta=ckpt["eta"], density=ckpt["density"], nhat=ckpt["nhat"], scalars=ckpt["scalars"])
+            state.step(DT)
+            outs.append(state.read(T=False))
+        dm, d64 = outs[0]["density"], outs[1]["density"]
+        fp64["mixed_vs_fp64_one_step"] = dict(
+            density_rel_diff=float((dm - d64).abs().max() / d64.abs().max()),
+            eta_max_abs_diff=float((outs[0]["eta"] - outs[1]["eta"]).abs().max()))
         st64.close()
         ctx64.close()
 
