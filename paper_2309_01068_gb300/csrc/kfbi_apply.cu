@@ -816,7 +816,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_forward(int N, int dct, con
 // one complex FFT. Two shared buffers alternate between the FFT stages. One instantiation per
 // grid size (N = 2^LOGN), so that the index arithmetic is constant.
 template <typename T, int LOGN>
-__global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* tab, const T* lam, T kappa, T* spec,
+__global__ void __launch_bounds__(1024) k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* tab, const T* lam, T kappa, T* spec,
                             const T* rinv, const V2<T>* rowinfo, const int* skip) {
   constexpr int N = 1 << LOGN, logN = LOGN;
   extern __shared__ unsigned char smem_raw[];
@@ -842,8 +842,10 @@ __global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* 
   // rows the row transform did not write (rowinfo, see k_row_forward) are w S_k(0) + e S_k(N-1)
   // for this thread's column k (blockDim is a multiple of W, so every element it loads is in
   // the same column)
+  // (float32 only: the float64 kernel must keep its registers within the 1024-thread launch)
+  constexpr bool ROWS = sizeof(T) == 4;
   T s0 = 0, sN = 0;
-  if (rowinfo != nullptr) {
+  if (ROWS && rowinfo != nullptr) {
     const int k = k0 + ((int)threadIdx.x & (W - 1));
     if (dct) {
       s0 = tsin(tab, k + N, N, qscale(N));
@@ -864,7 +866,7 @@ __global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* 
       const int t = t0 + u * (int)blockDim.x + (int)threadIdx.x;
       if (t < tot) {
         buf[u] = spec[(long)(t >> lw) * N + k0 + (t & (W - 1))];
-        if (rowinfo != nullptr) rbuf[u] = rowinfo[t >> lw];
+        if (ROWS && rowinfo != nullptr) rbuf[u] = rowinfo[t >> lw];
       }
     }
 #pragma unroll
@@ -873,7 +875,7 @@ __global__ void k_col_solve(int, int, int P, int dct, const V2<T>* tw, const T* 
       if (t < tot) {
         const int j = t >> lw, c = t & (W - 1);
         T v = buf[u];
-        if (rowinfo != nullptr && rbuf[u].x == rbuf[u].x) v = rbuf[u].x * s0 + rbuf[u].y * sN;
+        if (ROWS && rowinfo != nullptr && rbuf[u].x == rbuf[u].x) v = rbuf[u].x * s0 + rbuf[u].y * sN;
         if (!dct && (j & 1)) v = -v;
         ((T*)&A[(long)(c >> 1) * N + mk_pos(j, N)])[c & 1] = v;
       }
@@ -1209,6 +1211,8 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   T* boxg = (T*)c->boxg;
   T* face = (T*)c->facespec;
   T* spec = (T*)c->spec;
+  // rows without irregular nodes left to the column kernel: float32 applies only
+  V2<T>* rowinfo = sizeof(T) == 4 ? (V2<T>*)c->rowinfo : nullptr;
   T* J = (T*)c->jumps;
   // the density integral of the Hele-Shaw operator, in the apply's type (float64 slot 0 or a
   // float32 slot in the same buffer)
@@ -1303,9 +1307,9 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
   KFBI_TRY(launch_k(c->use_pdl, k_row_forward<T>, dim3(N), dim3(ROW_THREADS), 0, s, N, dct, (const int*)c->row_ptr,
                     (const IrrNode*)c->irr, (const T*)J, (T)(1.0 / (c->h * c->h)), (const T*)(fs ? boxg : nullptr),
-                    (const T*)face, tab, scale, spec, (V2<T>*)c->rowinfo, skip));
+                    (const T*)face, tab, scale, spec, rowinfo, skip));
   launched(c, 1);
-  KFBI_CHECK(launch_col_solve<T>(c, spec, (const V2<T>*)c->rowinfo, skip));
+  KFBI_CHECK(launch_col_solve<T>(c, spec, rowinfo, skip));
   KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(cdiv((long)6 * n * 32, 256)), dim3(256), 0, s, N, dct,
                     (const int*)(c->prow_ptr + N), (const int*)c->probe_j, (const int*)c->probe_i, (const T*)spec, tab,
                     scale, pval, skip));

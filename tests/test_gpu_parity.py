@@ -429,6 +429,48 @@ def test_hele_shaw_full_size_mixed():
     cmx.close()
 
 
+# ------------------------------------------------------------------- largest grid (N = 4096)
+@pytest.mark.parametrize("boxbc,kappa", [(0, 0.0), (1, 3000.0)])
+def test_grid_solve_largest_grid(boxbc, kappa):
+    """N = 4096: the column kernel's 1024-thread launch (float64)."""
+    C = np.random.default_rng(40 + boxbc).standard_normal((4096, 4096))
+    ctx = K.Context(4096, (-2.0, 2.0, -2.0, 2.0), kappa, boxbc, K.FP64, max_nodes=64)
+    u = ctx.grid_solve(dev(C)).cpu().numpy()
+    ref = OK.solve_grid(OK.Grid(4096, (-2, 2, -2, 2)), C, kappa, boxbc)
+    assert rel(u, ref) < 1e-12
+    ctx.close()
+
+
+def test_apply_and_solve_largest_grid():
+    """N = 4096, free-space box, 512 nodes: the float64 apply vs the oracle, the float32 apply
+    (1024-thread column launches, in-block FFT jumps, row-restricted transform) within the
+    float32 bound of the 1024^2 test; then a Stefan single-layer solve (Neumann box,
+    kappa = 3000) in both forms at tol 1e-10 (the equation is well conditioned)."""
+    p = W.random_problem(61, N=4096, n=512, box=1.5)
+    ref = OK.Kfbi(p.N, p.box, 0.0, OK.BOX_FREESPACE_DL).set_interface(p.xy)
+    dens = W.random_density(62, p.n)
+    rv, _, _ = ref.apply(OK.LAYER_DOUBLE, dens)
+    for precision, tol in ((K.FP64, 1e-11), (K.MIXED, 2e-4)):
+        ctx = K.Context(p.N, p.box, 0.0, K.BOX_FREESPACE_DL, precision, max_nodes=p.n)
+        ctx.set_interface(dev(p.xy))
+        vals, _, _ = ctx.apply(K.DOUBLE, dev(dens))
+        err = rel(vals.cpu().numpy(), rv)
+        print(f"4096^2 apply, precision {precision}: max error / max |value| = {err:.3e}")
+        assert err < tol
+        ctx.close()
+    ev = np.full(p.n, 0.3)
+    rhs = dev(W.random_density(63, p.n))
+    phis = []
+    for precision in (K.FP64, K.MIXED):
+        ctx = K.Context(p.N, p.box, 3000.0, K.BOX_NEUMANN0, precision, max_nodes=p.n)
+        ctx.set_interface(dev(p.xy))
+        phi, info = ctx.solve_bie(K.BIE_STEFAN_SL, rhs, tol=1e-10, max_iter=300, eps_v=dev(ev))
+        assert info["status"] == 0
+        phis.append(phi.cpu().numpy())
+        ctx.close()
+    assert rel(phis[1], phis[0]) < 1e-8
+
+
 # ------------------------------------------------------------------- time steps
 @pytest.mark.parametrize("precision,n", [(0, 128), (1, 128), (0, 96)])
 def test_hele_shaw_step_parity(precision, n):
