@@ -958,7 +958,8 @@ static ColKernel<T> col_kernel(int logN) {
 // 4 l + 128 t + c (c < 4) read straight from the spectral grid (L2-resident after the column
 // solve), so that every warp has the same work however the probes fall in the rows.
 template <typename T>
-__global__ void k_probe_values(int N, int dct, const int* nprobe, const int* probe_j, const int* probe_i,
+__global__ void __launch_bounds__(256, 4) k_probe_values(int N, int dct, const int* nprobe, const int* probe_j,
+                                                         const int* probe_i,
                                const T* spec, const T* tab, float scale, T* pval, const int* skip) {
   // the probe count is on the device (the grid covers 6 n, the most an interface can have)
   const int n_probe = *nprobe;
@@ -977,7 +978,7 @@ __global__ void k_probe_values(int N, int dct, const int* nprobe, const int* pro
   const int step = (128 * m) & mask;
   int idx = dct ? ((4 * lane * m + N) & mask) : (((4 * lane + 1) * m) & mask);
   T acc[4] = {0, 0, 0, 0};
-#pragma unroll 2
+#pragma unroll 8  // all eight 16-byte row loads of a lane in flight at N = 1024
   for (int k0 = 4 * lane; k0 < N; k0 += 128) {
     T v[4];
     if constexpr (sizeof(T) == 4) {
