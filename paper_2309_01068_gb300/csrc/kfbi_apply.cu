@@ -299,7 +299,8 @@ __global__ void k_target_jumps(const V2<T>* coef, int n, const int* ncr, const G
   if (lane < 6) Jout[(long)t * 6 + lane] = v;
 }
 
-// The jumps of k_target_jumps with the density's coefficients formed inside every block, for
+// The jumps of k_target_jumps (App. A.1, Table 2) with the density's Fourier coefficients (the
+// trigonometric interpolant of the nodal density) formed inside every block, for
 // the float32 inner applies with a power-of-two node count n <= 4096 (in place of k_dens_coef
 // + k_target_jumps: one launch and one global round trip fewer per apply). Each block takes
 // the length-n FFT of the density in shared memory (c_k = X_k / n, the same coefficients as
@@ -637,7 +638,8 @@ __global__ void k_face_dst(int N, int logN, int dct, const V2<T>* tw, const T* t
   }
 }
 
-// The free-space box table's south and north rows replaced by their DST-II along the face,
+// The free-space box table's (Sec. 4.1) south and north rows replaced by their DST-II along the
+// face (the transform of the fast solve, Sec. 4.2),
 // node column by node column: row 2N + k becomes sum_i S_k(i) K[2N + i][l] (S_k as in the row
 // transform below) and row 3N + k the same for the north face. The box product K phi then
 // yields the two dense face rows' x-transforms directly, so no apply needs k_face_dst.
