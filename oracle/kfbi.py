@@ -16,7 +16,7 @@ grid-based boundary integral method for moving interface problems":
                         boundary operator = average of the one-sided limits
   Sec. 3                boundary integral operators of the three BIEs
 
-Readings where the paper is silent or garbled (each listed in the design doc):
+Readings where the paper is silent or garbled (the CUDA path takes the same ones):
   R1  cell-centred grid x_i = xmin + (i + 1/2) h (the paper's Sec. 4.2 is node-centred);
       Dirichlet-0 box -> DST-II, Neumann-0 box -> DCT-II, both exact for the 5-point matrix.
   R2  interface functions use the global trigonometric interpolant through the nodes at

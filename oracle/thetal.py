@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 State: eta = theta - alpha at the nodes (Sec. 5.3 remark), length L, mean position
 Xbar, and the Adams-Bashforth history (M, Q, N-hat, L at the previous level).
 
-Readings (listed in DESIGN.md):
+Readings where the paper is silent or its printed formulas are in error (the CUDA path takes the same ones):
   T1  L_t = + int theta_a U da (Sec. 5.1); the sign printed in the Adams-Bashforth
       formula of Sec. 5.3 and its missing factor 1/2 are taken as typos:
       L^{n+1} = L^n + (tau/2)(3 M^n - M^{n-1}), M = int theta_a U da; same for Xbar.
