@@ -403,7 +403,7 @@ def test_hele_shaw_full_size_mixed():
     """The timed configuration: 1024^2, 1024 nodes, free-space box data, mixed form.
 
     (1) One float32 apply (the inner GMRES operator) vs the oracle's float64 apply: within
-    2e-4 of max |value| (measured 3.9e-5). The float32 row transform's sines (absolute error
+    2e-4 of max |value| (measured 2.8e-5). The float32 row transform's sines (absolute error
     below 4e-7) multiply corrections of size |J|/h^2 at about 1500 irregular nodes; each such
     error is a point source of strength ~4e-7 |J| in the solve, and their independent
     contributions add up to sqrt(1500) ~ 40 times that at a node. (2) A mixed solve of the Hele-Shaw operator (Sec. 3.1) to
