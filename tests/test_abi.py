@@ -53,3 +53,22 @@ def test_no_oracle_import_in_product():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", src).replace("oracles", ""), f
+
+
+def test_binding_constants_match_header():
+    """Every KFBI_* enumerator the header gives a value has that value in the binding, under
+    the same name without the KFBI_ prefix, so the Python side cannot drift from the C side."""
+    from paper_2309_01068_gb300 import kfbi
+
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "kfbi.h")).read(), flags=re.S)
+    pairs = re.findall(r"\bKFBI_([A-Z0-9_]+)\s*=\s*(\d+)", text)
+    assert len(pairs) >= 30
+    checked = 0
+    for name, value in pairs:
+        if hasattr(kfbi, name):
+            assert getattr(kfbi, name) == int(value), name
+            checked += 1
+    for name in ("OK", "ERR_ARG", "ERR_CAPACITY", "BOX_FREESPACE_DL", "MIXED", "DOUBLE", "BIE_STEFAN_SL",
+                 "OPT_FUSE_INTERP", "OPT_FUSE_DFT"):
+        assert hasattr(kfbi, name), name
+    assert checked >= 25
