@@ -129,7 +129,7 @@ def _advance(st: State, U, dt, stiff_symbol_fn):
         M_prev, Q_prev, N_prev, L_prev = st.M_prev, st.Q_prev, st.N_prev, st.L_prev
     L_new = L + 0.5 * dt * (3.0 * M - M_prev)
     e1, e2 = st_propagators(stiff_symbol_fn, dt, L_prev, L, L_new)
-    eta_h_new = e1 * eta_h + 0.5 * dt * (3.0 * e1 * N_h - e2 * N_prev)
+    eta_h_new = ssd_ab2(eta_h, N_h, N_prev, e1, e2, dt)
     Xbar_new = st.Xbar + 0.5 * dt * (3.0 * Q - Q_prev)
     st.M_prev, st.Q_prev, st.N_prev, st.L_prev = M, Q, N_h, L
     st.eta = np.fft.ifft(eta_h_new).real
@@ -139,6 +139,14 @@ def _advance(st: State, U, dt, stiff_symbol_fn):
     st.steps += 1
     st.last.update(M=M, Q=Q, U=U, V=V)
     return st
+
+
+def ssd_ab2(eta_h, N_h, N_prev, e1, e2, dt):
+    """The semi-implicit update of Sec. 5.3 in Fourier space: the stiff part is integrated
+    exactly by the propagators e1 = e_k(t_n, t_{n+1}), e2 = e_k(t_{n-1}, t_{n+1}), the
+    remainder N by second-order Adams-Bashforth:
+    eta^{n+1} = e1 eta^n + (dt/2)(3 e1 N^n - e2 N^{n-1})."""
+    return e1 * eta_h + 0.5 * dt * (3.0 * e1 * N_h - e2 * N_prev)
 
 
 def st_propagators(stiff_symbol_fn, dt, L_prev, L, L_new):
