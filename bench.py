@@ -58,6 +58,77 @@ def shard(count, rank, world):
     return list(range(start, start + base + (1 if rank < extra else 0)))
 
 
+def bench_config(world=1):
+    """The workload's config: the same dict in both arms' lines."""
+    return dict(workload=WORKLOAD, grid=1024, nodes=1024, box=[-4, 4], sigma=SIGMA, J=J, dt=DT, tol=TOL,
+                parallelism=f"replicas{world}", l2="flushed (512 MB write) before every timed step")
+
+
+def host_cpu():
+    """Model, cores and threads of the host CPU (lscpu when present, else /proc/cpuinfo)."""
+    info = dict(logical_cpus=os.cpu_count())
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            k, v = k.strip(), v.strip()
+            if k in ("Architecture", "Model name", "CPU(s)", "Thread(s) per core", "Core(s) per socket", "Socket(s)",
+                     "CPU max MHz", "Vendor ID"):
+                info[k] = v
+    except (OSError, subprocess.SubprocessError):
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    info["model"] = ln.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return info
+
+
+def oracle_sample(budget_s, max_applies):
+    """One bounded oracle sample of the workload in this process: one set_interface and up to
+    max_applies BIE applies within budget_s seconds. Returns (t_set, t_app, applies)."""
+    import workloads as W
+    from oracle import kfbi as OK
+    from oracle import thetal as OT
+
+    p = workload()
+    st = OT.state_from_nodes(p.xy, p.theta, p.L)
+    s = OK.Kfbi(p.N, p.box, 0.0, OK.BOX_FREESPACE_DL)
+    t0 = time.perf_counter()
+    s.set_interface(OT.reconstruct(st.eta, st.L, st.Xbar))
+    t_set = time.perf_counter() - t0
+    phi = W.random_density(3, p.n)
+    t1 = time.perf_counter()
+    napp = 0
+    while True:
+        s.bie_matvec(OK.BIE_HS_EXTERIOR_MDL, phi)
+        napp += 1
+        if time.perf_counter() - t1 > budget_s - t_set or napp >= max_applies:
+            break
+    return t_set, (time.perf_counter() - t1) / napp, napp
+
+
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def oracle_sample_subprocess(budget_s, max_applies, one_core):
+    """oracle_sample in a fresh interpreter: with one_core, every BLAS/OpenMP pool is limited to
+    one thread (scipy.fft runs one worker either way: the oracle passes no workers)."""
+    env = dict(os.environ)
+    if one_core:
+        for v in THREAD_VARS:
+            env[v] = "1"
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench.oracle_sample({budget_s}, {max_applies})))")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-500:])
+    t_set, t_app, napp = json.loads(r.stdout.strip().splitlines()[-1])
+    return t_set, t_app, napp
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,11 +326,15 @@ def batched_leg(torch, K, flush, reps=3):
     torch.cuda.synchronize()
     seq_s = time.perf_counter() - t0
     its = [i["iterations"] for i in infos]
+    conv = int(sum(1 for i in infos if i["status"] == 0))
     out = dict(workload="batched_256_uneven_N128-512_n64-512_kappa0-10-100", instances=len(probs),
                precision="mixed (f32 grid applies and inner Gram-Schmidt, f64 residual/refinement)", tol=tol,
-               instances_per_s=len(probs) / (float(np.median(ms)) / 1e3), ms_per_batch=float(np.median(ms)),
-               sequential_instances_per_s=len(probs) / seq_s,
-               converged=int(sum(1 for i in infos if i["status"] == 0)),
+               converged_solves_per_s=conv / (float(np.median(ms)) / 1e3),
+               note=(f"solves that reached tol only; {len(probs) - conv} instances stop unconverged at max_iter "
+                     f"(node spacing below the cell width) and are timed but not counted"),
+               ms_per_batch=float(np.median(ms)),
+               sequential_converged_solves_per_s=conv / seq_s,
+               converged=conv,
                mean_iterations=float(np.mean(its)), max_iterations=int(max(its)),
                max_rel_residual=float(max(i["rel_residual"] for i in infos)),
                autotune=dict(seconds=tune_s, best_ms=tuned_ms,
@@ -376,77 +451,87 @@ def stefan_leg(torch, K, steps=3, N=2048, n=2048, tol=1e-9, compare_fp64=True):
                 statuses=[i["status"] for i in infos], mixed_vs_fp64_one_step=err)
 
 
-def cpu_baseline(iters_per_solve, budget_s=25.0):
-    """The oracle as it stands on the host cores: a bounded sample of the same workload."""
+def col_kernel_sizes(torch, K, reps=40):
+    """Column kernel time per launch by grid size for both float32 forms (register FFTs and
+    the shared-memory Stockham kernel): CUDA events around each launch, float32 applies of a
+    Neumann-box context with a 256-node star."""
     import numpy as np
 
     import workloads as W
-    from oracle import kfbi as OK
-    from oracle import thetal as OT
 
-    p = workload()
-    st = OT.state_from_nodes(p.xy, p.theta, p.L)
-    s = OK.Kfbi(p.N, p.box, 0.0, OK.BOX_FREESPACE_DL)
-    t0 = time.perf_counter()
-    X = OT.reconstruct(st.eta, st.L, st.Xbar)
-    s.set_interface(X)
-    t_set = time.perf_counter() - t0
-    phi = W.random_density(3, p.n)
-    t1 = time.perf_counter()
-    napp = 0
-    while True:
-        s.bie_matvec(OK.BIE_HS_EXTERIOR_MDL, phi)
-        napp += 1
-        if time.perf_counter() - t1 > budget_s - t_set or napp >= 40:
-            break
-    t_app = (time.perf_counter() - t1) / napp
-    per_solve = t_set + iters_per_solve * t_app
-    del np
-    return dict(value=1.0 / per_solve, unit="solves/s", cores=os.cpu_count(), kind="oracle",
-                sample=(f"oracle (numpy/scipy FP64) on the host: one set_interface ({t_set:.2f} s) and {napp} "
-                        f"BIE applies ({t_app:.3f} s each) of the {WORKLOAD} workload, scaled to one solve of "
-                        f"{iters_per_solve:.1f} applies (the GPU run's mean GMRES count) + set_interface"),
-                applies_per_s=1.0 / t_app)
+    out = {}
+    for N in (128, 256, 512, 1024, 2048, 4096):
+        p = W.random_problem(17, N=N, n=256, kappa=30.0, boxbc=W.BOX_NEUMANN0)
+        ctx = K.Context(N, p.box, 30.0, K.BOX_NEUMANN0, K.MIXED, max_nodes=p.n)
+        ctx.set_interface(torch.tensor(p.xy, dtype=torch.float64, device="cuda"))
+        dens = torch.ones(p.n, dtype=torch.float64, device="cuda")
+        vals = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        row = {}
+        for reg in (1, 0):
+            if N > 1024 and reg == 1:
+                continue
+            ctx.set_option(K.OPT_COL_REG, reg)
+            for _ in range(5):
+                ctx.apply_into(K.DOUBLE, dens, vals)
+            ctx.timing(True)
+            for _ in range(reps):
+                ctx.apply_into(K.DOUBLE, dens, vals)
+            t = ctx.timing()
+            ctx.timing(False)
+            us = 1e3 * t["fp32_ms"] / max(t["fp32_launches"], 1)
+            row["register" if reg else "stockham"] = dict(us=us, hbm_frac=(8.0 * N * N) / (us * 1e-6) / 1e9 / 6754.1)
+        out[str(N)] = row
+        ctx.close()
+    return out
+
+
+def cpu_baseline(iters_per_solve, budget_s=12.0):
+    """The oracle as it stands on the host cores: a bounded sample of the same workload (one
+    set_interface and a few BIE applies), on one core and on all cores, each in a fresh
+    process; a solve is one set_interface plus the GPU run's mean GMRES count of applies."""
+    legs = {}
+    for name, one in (("one_core", True), ("all_cores", False)):
+        t_set, t_app, napp = oracle_sample_subprocess(budget_s, 30, one)
+        legs[name] = dict(t_set_s=t_set, t_apply_s=t_app, applies=napp,
+                          solves_per_s=1.0 / (t_set + iters_per_solve * t_app), applies_per_s=1.0 / t_app)
+    allc = legs["all_cores"]
+    return dict(value=allc["solves_per_s"], unit="solves/s", cores=os.cpu_count(), kind="oracle",
+                sample=(f"oracle (numpy/scipy FP64) on the host: one set_interface ({allc['t_set_s']:.2f} s) and "
+                        f"{allc['applies']} BIE applies ({allc['t_apply_s']:.3f} s each) of the {WORKLOAD} workload, "
+                        f"scaled to one solve of {iters_per_solve:.1f} applies (the GPU run's mean GMRES count) + "
+                        f"set_interface; all cores = BLAS on every core, scipy.fft on one worker"),
+                one_core=legs["one_core"], all_cores=allc, host=host_cpu(), basis="extrapolated from the sample")
 
 
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The CPU oracle on the host cores (the reference arm). Each step is a bounded sample of
+    the workload, measured as it runs: one oracle set_interface and one BIE apply (about half
+    a second). The line's value converts the measured sample to the metric's unit, one solve =
+    one set_interface + ITERS applies; ms_per_step is the measured sample time."""
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
         return 0
     import numpy as np
 
-    import workloads as W
-    from oracle import kfbi as OK
-    from oracle import thetal as OT
-
-    p = workload()
-    st = OT.state_from_nodes(p.xy, p.theta, p.L)
-    s = OK.Kfbi(p.N, p.box, 0.0, OK.BOX_FREESPACE_DL)
-    phi = W.random_density(3, p.n)
-    iters = 90.0  # GMRES applies per solve of this workload at 1e-8 (measured on both paths)
-
-    def sample():
-        t0 = time.perf_counter()
-        s.set_interface(OT.reconstruct(st.eta, st.L, st.Xbar))
-        t_set = time.perf_counter() - t0
-        t1 = time.perf_counter()
-        s.bie_matvec(OK.BIE_HS_EXTERIOR_MDL, phi)
-        t_app = time.perf_counter() - t1
-        return t_set + iters * t_app, t_set, t_app
-
+    iters = 90.0  # GMRES applies per solve of this workload at 1e-8 (the GPU runs' mean)
     for _ in range(args.warmup):
-        sample()
-    per = [sample() for _ in range(args.steps)]
-    per_solve = float(np.mean([q[0] for q in per]))
-    value = 1.0 / per_solve
+        oracle_sample(0.0, 1)
+    per = [oracle_sample(0.0, 1) for _ in range(args.steps)]
+    t_set = float(np.mean([q[0] for q in per]))
+    t_app = float(np.mean([q[1] for q in per]))
+    value = 1.0 / (t_set + iters * t_app)
     line = dict(impl="reference", metric=METRIC, value=value, unit="solves/s", n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=per_solve * 1e3, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=WORKLOAD, grid=1024, nodes=1024, tol=TOL, precision="fp64"),
+                warmup=args.warmup, ms_per_step=1e3 * (t_set + t_app), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", precision="fp64 (the CPU oracle)",
+                config=bench_config(args.gpus),
+                value_basis=(f"extrapolated: measured per step one set_interface ({t_set:.3f} s) + one BIE apply "
+                             f"({t_app:.3f} s); value = 1 / (set_interface + {iters:.0f} applies), the applies a "
+                             f"solve of this workload takes; ms_per_step is the measured sample"),
+                applies_per_s=1.0 / t_app,
                 cpu_baseline=dict(value=value, unit="solves/s", cores=os.cpu_count(), kind="oracle",
                                   sample=(f"each step: one oracle set_interface + one BIE apply of {WORKLOAD}, "
-                                          f"scaled to {iters:.0f} applies per solve")),
+                                          f"scaled to {iters:.0f} applies per solve"), host=host_cpu()),
                 e2e=dict(value=value, unit="solves/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
     return 0
@@ -475,6 +560,8 @@ def main():
     K.load()
     p = workload()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    # ALU roofs of this GPU (float32 and float64 FMA), measured by the library's probe kernel
+    alu = dict(fp32_tflops=K.alu_peak(0), fp64_tflops=K.alu_peak(1))
 
     # ---- headline: mixed precision
     ctx, st = make_state(K, torch, p, K.MIXED)
@@ -570,6 +657,14 @@ def main():
                     algorithmic_bytes_per_launch=bytes_per_launch, launches=tim["fp32_launches"],
                     mean_launch_us=f32_ms * 1e3,
                     peak_source="MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s")
+    # the same kernel against the float32 FMA roof: forward and inverse real transforms of N
+    # columns of length N, 2.5 M log2 M flops each (split-radix count of a real FFT)
+    flops_per_launch = 2 * N * 2.5 * N * math.log2(N)
+    if achieved and alu.get("fp32_tflops"):
+        a_tf = flops_per_launch / (f32_ms * 1e-3) / 1e12
+        roofline["alu"] = dict(bound="alu", achieved=a_tf, peak=alu["fp32_tflops"], unit="TFLOP/s",
+                               frac=a_tf / alu["fp32_tflops"], algorithmic_flops_per_launch=flops_per_launch,
+                               peak_source="kfbi_alu_peak float32 FMA probe on this GPU (of measured)")
 
     # ---- float64 plain form on the same workload
     fp64 = None
@@ -582,10 +677,16 @@ def main():
         ms64, infos64 = run_steps(torch, ctx64, st64, k64, flush)
         tim64 = ctx64.timing()
         fp64_applies = time_applies(torch, K, ctx64, reps=20)
+        col64_us = 1e3 * tim64["fp64_ms"] / max(tim64["fp64_launches"], 1)
         fp64 = dict(solves_per_s=k64 / (sum(ms64) / 1e3), steps=k64,
                     mean_gmres_iterations=float(np.mean([i["iterations"] for i in infos64])),
-                    applies_per_s=fp64_applies,
-                    col_kernel_mean_us=1e3 * tim64["fp64_ms"] / max(tim64["fp64_launches"], 1))
+                    applies_per_s=fp64_applies, col_kernel_mean_us=col64_us)
+        if tim64["fp64_launches"] and alu.get("fp64_tflops"):
+            a64 = flops_per_launch / (col64_us * 1e-6) / 1e12
+            fp64["col_kernel_roofline"] = dict(
+                bound="alu", achieved=a64, peak=alu["fp64_tflops"], unit="TFLOP/s", frac=a64 / alu["fp64_tflops"],
+                hbm_frac=(2.0 * N * N * 8) / (col64_us * 1e-6) / 1e9 / hbm_peak,
+                peak_source="kfbi_alu_peak float64 FMA probe on this GPU (of measured)")
         # accuracy of the mixed form on this workload: one step of each form from the same
         # state; the float64 form is the one the parity tests pin to the oracle
         outs = []
@@ -607,7 +708,8 @@ def main():
     # ---- further workloads (reported beside the headline, never part of it)
     extras = {}
     if rank == 0 and not args.profile and not args.no_extras:
-        for name, leg in (("batched", lambda: batched_leg(torch, K, flush)), ("warm_start", lambda: warmstart_leg(torch, K)),
+        for name, leg in (("col_kernel_sizes", lambda: col_kernel_sizes(torch, K)),
+                          ("batched", lambda: batched_leg(torch, K, flush)), ("warm_start", lambda: warmstart_leg(torch, K)),
                           ("stefan", lambda: stefan_leg(torch, K)),
                           ("stefan_4096", lambda: stefan_leg(torch, K, N=4096, n=4096, tol=1e-8, compare_fp64=False))):
             try:
@@ -620,16 +722,16 @@ def main():
         line = dict(metric=METRIC, value=value, unit="solves/s", n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=1e3 * total_s / args.steps, higher_is_better=True,
                     scaling="weak", vs_baseline=None, dtype="f32+f64", data="synthetic",
-                    config=dict(workload=WORKLOAD, grid=N, nodes=p.n, box=[-4, 4], sigma=SIGMA, J=J, dt=DT,
-                                tol=TOL, precision="mixed (f32 grid applies and inner Gram-Schmidt, f64 residual/refinement)",
-                                parallelism=f"replicas{world}", l2="flushed (512 MB write) before every timed step"),
+                    precision="mixed (f32 grid applies and inner Gram-Schmidt, f64 residual/refinement)",
+                    config=bench_config(world),
                     applies_per_s=dict(mixed_f32_grid=mixed_applies, fp64=(fp64 or {}).get("applies_per_s")),
                     fp64_plain=fp64,
                     speedup_vs_fp64=(value / world / fp64["solves_per_s"]) if fp64 else None,
                     gmres=dict(mean_iterations=float(np.mean(iters)), max_iterations=int(max(iters)),
                                max_rel_residual=float(max(i["rel_residual"] for i in infos)),
                                refinements=float(np.mean([i["refinements"] for i in infos]))),
-                    wall_s=t_wall, roofline=roofline, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+                    wall_s=t_wall, roofline=roofline, alu_peaks_tflops=alu, cpu_baseline=cpu, e2e=e2e,
+                    gpu_launches=int(launches),
                     clocks=clocks, **extras)
         print(json.dumps(line))
     st.close()

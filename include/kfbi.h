@@ -22,7 +22,8 @@
  *             Interface functions (densities) are [n] float64 nodal values; their
  *             derivatives come from the global trigonometric interpolant.
  * Errors:     every call returns a kfbi_status; nothing else crosses the ABI. After an
- *             error other than KFBI_ERR_NOT_CONVERGED the outputs are unspecified.
+ *             error other than KFBI_ERR_NOT_CONVERGED or (from kfbi_solve_bie)
+ *             KFBI_ERR_TIMEOUT the outputs are unspecified.
  * Precision:  KFBI_FP64 runs every step in float64. KFBI_MIXED runs the grid part of the
  *             inner applies (jumps, corrections, transforms, interpolation) in float32
  *             and keeps float64 for GMRES (Arnoldi, Givens, least squares), the outer
@@ -150,7 +151,8 @@ kfbi_status kfbi_bie_apply(kfbi_ctx* ctx, int kind, const double* eps_v, const d
  *   density   device [n] float64: initial guess in, solution out
  *   info      host pointer, filled on return (may be NULL)
  * Synchronises the stream. Errors: ARG, STATE, NOT_CONVERGED (best iterate returned),
- * TIMEOUT, CUDA.
+ * TIMEOUT (a device-side loop bound was reached, KFBI_OPT_BODY_CAP / KFBI_OPT_SWEEP_CAP;
+ * the iterate described there is returned and `info` is filled), CUDA.
  */
 kfbi_status kfbi_solve_bie(kfbi_ctx* ctx, int kind, const double* eps_v, const double* rhs, double tol,
                            int max_iter, int restart, double* density, kfbi_solve_info* info);
@@ -203,13 +205,21 @@ typedef struct {
   /* Hele-Shaw (Sec. 2.1, 3.1): surface tension sigma, injection rate J */
   double sigma, J;
   /* Stefan (Sec. 2.2, 3.2): undercooling St, eps_C = eps_c (1 - eps_aniso cos(fold
-     (theta - pi/2))), constant eps_V > 0 (small-scale decomposition case I) */
+     (theta - pi/2))), constant eps_V >= 0. eps_V > 0: second-kind equation, small-scale
+     decomposition case I (stiff part lambda_1 (2 pi/L)^2 theta_aa, lambda_1 = max |eps_C/eps_V|);
+     eps_V = 0: first-kind equation -S psi = -eps_C kappa - T1, case II (stiff part
+     lambda_2 (2 pi/L)^3 H[theta_aaa], lambda_2 = max |2 eps_C|), Sec. 5.2.2 and 5.3 */
   double St, eps_c, eps_aniso, eps_v;
   int fold;
   /* GMRES controls of the per-step BIE solve */
   double tol;
   int max_iter, restart;
+  /* KFBI_SCHEME_SEMI_IMPLICIT (0): the stiff part by its propagator, the rest by
+     Adams-Bashforth (Sec. 5.3); KFBI_SCHEME_EXPLICIT (1): Adams-Bashforth on the whole
+     right-hand side, no stiff part split off (the comparison scheme of Sec. 6.2.2) */
+  int scheme;
 } kfbi_thetal_params;
+enum { KFBI_SCHEME_SEMI_IMPLICIT = 0, KFBI_SCHEME_EXPLICIT = 1 };
 
 /*
  * kfbi_thetal_create -- device state for the context's grid from equal-arclength nodes.
@@ -264,7 +274,9 @@ const char* kfbi_status_string(kfbi_status s);
  * Scratch: one static device array of about 2.1 MB in libkfbi, which every GPU that loads
  * the library holds until the process exits. The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture. All calls share the array and each call rewrites it
+ * call before any stream capture. The address is kept for the life of the process: a
+ * device reset (cudaDeviceReset) between calls is not supported. All calls share the array
+ * and each call rewrites it
  * completely, so calls that overlap on the GPU (different streams or host threads) race:
  * serialise them. Asynchronous. Errors: ARG, CAPACITY, SINGULAR, CUDA.
  */
@@ -331,6 +343,21 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             (16..4096) form the density's Fourier coefficients inside the
  *                             jump kernel (a shared-memory FFT in every block) instead of a
  *                             separate DFT kernel; 0: the separate kernel.
+ *   KFBI_OPT_COL_REG          0 (default): the float32 column solve runs the shared-memory
+ *                             radix-4 Stockham kernel; 1 (grids with N <= 1024): every FFT is
+ *                             held in registers by one group of B lanes (an A-point DFT per lane,
+ *                             one transpose through shared memory, B-point DFTs; N = A B).
+ *   KFBI_OPT_BODY_CAP         0 (default): the device-side GMRES loop (the body count of the
+ *                             graph's WHILE node, or of the host-driven loop) stops after
+ *                             2 max_iter + 2 max_iter / restart + 8 bodies; a value > 0 sets
+ *                             that bound instead. A solve that reaches it returns
+ *                             KFBI_ERR_TIMEOUT with the iterate of its last completed restart
+ *                             cycle in `density` (the initial guess if none completed); the
+ *                             context stays usable.
+ *   KFBI_OPT_SWEEP_CAP        0 (default): the refinement loop of KFBI_MIXED stops after 14
+ *                             sweeps (two more than the 12 it may take); a value > 0 sets that
+ *                             bound instead. A solve that reaches it returns KFBI_ERR_TIMEOUT
+ *                             with the refined iterate of its last sweep in `density`.
  * kfbi_set_option: value 0 or 1 unless stated. kfbi_get_option writes the value to *value (host).
  * Errors: ARG (unknown option, bad value, NULL, read-only option).
  */
@@ -345,7 +372,10 @@ enum {
   KFBI_OPT_FP32_ARNOLDI = 8,
   KFBI_OPT_PUSH_REDUCE = 9,
   KFBI_OPT_FUSE_INTERP = 10,
-  KFBI_OPT_FUSE_DFT = 11
+  KFBI_OPT_FUSE_DFT = 11,
+  KFBI_OPT_BODY_CAP = 12,
+  KFBI_OPT_SWEEP_CAP = 13,
+  KFBI_OPT_COL_REG = 14
 };
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);
@@ -448,6 +478,17 @@ kfbi_status kfbi_batch_autotune(kfbi_batch* batch, int kind, const double* const
 
 /* Number of kernels this context has launched since creation (host output). */
 kfbi_status kfbi_launch_count(kfbi_ctx* ctx, long long* count);
+
+/*
+ * kfbi_alu_peak -- measured fused multiply-add throughput of this GPU, the denominator of the
+ * ALU roofline fractions the benchmark reports (not in the paper). kind 0: float32 FMA,
+ * 1: float64 FMA. Launches a probe kernel (eight independent FMA chains per thread, eight
+ * 256-thread blocks per SM) four times on `stream` (cudaStream_t as void*; the first launch
+ * warms up), times each with CUDA events and writes the best rate in TFLOP/s (2 flops per
+ * FMA) to *tflops (host). Synchronises the stream; allocates nothing on the device.
+ * Errors: ARG, CUDA.
+ */
+kfbi_status kfbi_alu_peak(int kind, double* tflops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,9 @@ Readings where the paper is silent or garbled (the CUDA path takes the same ones
       alpha_j = 2 pi j / n (Sec. 5 remark: spectral interface operations); for even n the
       Nyquist mode is the real term c cos(n alpha / 2).
   R3  crossings: bracket sign changes of (coordinate - line) on 8 sub-samples per node
-      interval, Newton with bisection safeguard until |step| <= 1e-15.
+      interval, Newton with bisection safeguard until |step| <= 1e-15. A crossing within
+      1e-10 h of a grid node is placed on the node and on the arm that leaves the node toward
+      the outside of the curve: a node on the curve is in the closed interior.
   R4  a node is in Omega+ iff an odd number of its row's crossings lie strictly left of
       it; an arm with two crossings (the curve dips between two same-side nodes) gets no
       correction; three or more crossings on an arm, or a vertical arm whose crossing
@@ -50,6 +52,7 @@ BIE_INTERIOR_DL, BIE_HS_EXTERIOR_MDL, BIE_STEFAN_SL = 0, 1, 2
 
 SUBSAMPLES = 8          # R3
 NEWTON_TOL = 1e-15      # R3
+SNAP_TOL = 1e-10        # R3 tie-break, in cells
 NEWTON_MAXIT = 60
 BOX_MARGIN_CELLS = 3.0  # the interface must stay this many cells inside the box
 
@@ -214,6 +217,17 @@ def find_crossings(iface: Interface, grid: Grid):
         t = _roots(iface.X, axis, lo, hi, lines_v[li], pos[seg, li])
         xi = iface.X.eval(t, 0)[:, 1 - axis]
         first = np.searchsorted(along_v, xi, side="right")
+        # tie-break: a crossing within SNAP_TOL h of a node lies on the node, on the arm toward
+        # the outside (outward normal (y_a, -x_a): +x on a horizontal line when y_a > 0, +y on a
+        # vertical line when x_a < 0), so the node is in the closed interior
+        lo_along = grid.xmin if kind == 0 else grid.ymin
+        l = np.clip(np.rint((xi - lo_along) / h - 0.5).astype(np.int64), 0, grid.N - 1)
+        near = np.abs(xi - along_v[l]) <= SNAP_TOL * h
+        if np.any(near):
+            d = iface.X.eval(t, 1)[:, axis]
+            out_plus = d > 0.0 if kind == 0 else d < 0.0
+            xi = np.where(near, along_v[l], xi)
+            first = np.where(near, np.where(out_plus, l + 1, l), first)
         kinds.append(np.full(t.shape, kind))
         lines.append(li)
         alphas.append(t)

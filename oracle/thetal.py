@@ -12,7 +12,10 @@ Readings where the paper is silent or its printed formulas are in error (the CUD
   T2  theta_t = (2 pi / L)(theta_a V - U_a) (Sec. 5.1); N = that minus the stiff part.
   T3  Hele-Shaw stiff part L2 with lambda_2 = sigma (Sec. 5.2.1): symbol -sigma (2pi/L)^3 |k|^3.
       Stefan case I (eps_V > 0) stiff part L1, lambda_1 = max |eps_C / eps_V| (Sec. 5.3):
-      symbol -lambda_1 (2pi/L)^2 k^2.
+      symbol -lambda_1 (2pi/L)^2 k^2. Stefan case II (eps_V = 0, the first-kind equation of
+      Sec. 5.2.2) stiff part L2, lambda_2 = max |2 eps_C|: symbol -lambda_2 (2pi/L)^3 |k|^3.
+      The explicit Adams-Bashforth scheme of the stability test (Sec. 6.2.2) is the same update
+      with no stiff part (symbol 0: both propagators 1, N the whole right-hand side).
   T4  first step: the history equals the current level (M^{-1} = M^0, ...).
   T5  reconstruction: X_a = (L/2pi)(cos theta, sin theta) with its mean removed (closure),
       integrated spectrally, shifted so that the node mean is Xbar; Nyquist mode dropped.
@@ -172,6 +175,17 @@ def stefan_symbol(n, lam1):
     return lambda L: -lam1 * (TWO_PI / L) ** 2 * k ** 2
 
 
+def stefan_symbol_case2(n, lam2):
+    """Case II (eps_V = 0): third-order stiffness -lam2 (2 pi / L)^3 |k|^3 (Sec. 5.2.2, 5.3)."""
+    k = np.abs(wavenumbers(n))
+    return lambda L: -lam2 * (TWO_PI / L) ** 3 * k ** 3
+
+
+def no_symbol(n):
+    """The explicit scheme: no stiff part is split off."""
+    return lambda L: np.zeros(n)
+
+
 def hs_step(solver: K.Kfbi, st: State, dt, sigma, J, tol=1e-8, restart=100, max_iter=500):
     """One Hele-Shaw time step (Sec. 3.1 BIE, Sec. 5.2.1 SSD, Sec. 5.3 scheme).
 
@@ -204,11 +218,13 @@ def stefan_eps_c(theta, eps, aniso, fold):
 
 
 def stefan_step(solver: K.Kfbi, st: State, dt, St, eps_c, eps_aniso, fold, eps_v,
-                tol=1e-8, restart=100, max_iter=500):
-    """One Stefan time step (Sec. 3.2 split T = T1 + T2, Sec. 5.2.2 case I, Sec. 5.3).
+                tol=1e-8, restart=100, max_iter=500, scheme="semi-implicit"):
+    """One Stefan time step (Sec. 3.2 split T = T1 + T2, Sec. 5.2.2 cases I and II, Sec. 5.3).
 
     (Delta_h - c^2) T1 = (T^{n-1} - 4 T^n)/(2 tau) in the Neumann box;
     eps_V psi - S psi = -eps_C kappa - T1 on Gamma; U = psi; T^{n+1} = T1 - (S psi)_h.
+    eps_V > 0: case I stiff part; eps_V = 0: case II (first-kind equation, third-order stiff part).
+    scheme "explicit": the Adams-Bashforth scheme without the stiff part (Sec. 6.2.2).
     """
     n = st.eta.shape[0]
     alpha = TWO_PI * np.arange(n) / n
@@ -233,9 +249,20 @@ def stefan_step(solver: K.Kfbi, st: State, dt, St, eps_c, eps_aniso, fold, eps_v
     T_new = T1 - Sgrid
     st.T_prev, st.T = st.T, T_new
     st.density = psi
-    lam1 = float(np.max(np.abs(ec / ev)))
-    st.last.update(info=info, X=X, rhs=rhs, psi=psi, lam1=lam1)
-    return _advance(st, psi, dt, stefan_symbol(n, lam1))
+    if eps_v > 0.0:
+        lam1 = float(np.max(np.abs(ec / ev)))
+        sym = stefan_symbol(n, lam1)
+        st.last.update(lam1=lam1)
+    else:
+        lam2 = float(np.max(np.abs(2.0 * ec)))
+        sym = stefan_symbol_case2(n, lam2)
+        st.last.update(lam2=lam2)
+    if scheme == "explicit":
+        sym = no_symbol(n)
+    elif scheme != "semi-implicit":
+        raise ValueError(scheme)
+    st.last.update(info=info, X=X, rhs=rhs, psi=psi)
+    return _advance(st, psi, dt, sym)
 
 
 def area(X):

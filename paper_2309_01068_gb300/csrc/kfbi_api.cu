@@ -1,3 +1,4 @@
+#include <algorithm>
 // C ABI of libkfbi (include/kfbi.h): context lifetime, constant tables and the entry
 // points that validate arguments and enqueue the kernels of the other translation units.
 #include <cmath>
@@ -481,6 +482,13 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
     c->cfg_version += 1;
     return KFBI_OK;
   }
+  if (option == KFBI_OPT_BODY_CAP || option == KFBI_OPT_SWEEP_CAP) {
+    if (value < 0) return KFBI_ERR_ARG;
+    if (option == KFBI_OPT_BODY_CAP) c->body_cap_set = value;
+    else c->sweep_cap_set = value;
+    c->cfg_version += 1;
+    return KFBI_OK;
+  }
   if (value != 0 && value != 1) return KFBI_ERR_ARG;
   if (option == KFBI_OPT_BOX_MATRIX) {
     if (value == 1 && c->boxK == nullptr) return KFBI_ERR_CAPACITY;
@@ -491,6 +499,8 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
     c->fuse_interp = value != 0;
   } else if (option == KFBI_OPT_FUSE_DFT) {
     c->fuse_dft = value != 0;
+  } else if (option == KFBI_OPT_COL_REG) {
+    c->col_reg = value != 0;
   } else if (option == KFBI_OPT_PUSH_REDUCE) {
     c->gmf_push = value != 0;
     c->gmf = c->gmf32 = kfbi_ctx::GmfConfig{};
@@ -521,6 +531,9 @@ kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
   else if (option == KFBI_OPT_PUSH_REDUCE) *value = c->gmf_push ? 1 : 0;
   else if (option == KFBI_OPT_FUSE_INTERP) *value = c->fuse_interp ? 1 : 0;
   else if (option == KFBI_OPT_FUSE_DFT) *value = c->fuse_dft ? 1 : 0;
+  else if (option == KFBI_OPT_COL_REG) *value = c->col_reg ? 1 : 0;
+  else if (option == KFBI_OPT_BODY_CAP) *value = c->body_cap_set;
+  else if (option == KFBI_OPT_SWEEP_CAP) *value = c->sweep_cap_set;
   else return KFBI_ERR_ARG;
   return KFBI_OK;
 }
@@ -555,6 +568,63 @@ kfbi_status kfbi_timing_read(kfbi_ctx* c, double* ms_fp64, int* launches_fp64, d
   if (ms_fp32) *ms_fp32 = ms[1];
   if (launches_fp32) *launches_fp32 = cnt[1];
   return KFBI_OK;
+}
+
+}  // extern "C"
+
+// ALU peak probe: every thread runs eight independent fused multiply-add chains
+// x <- x a + b (a = 0.999, b = 0.001: bounded values); the sum is stored only when it equals a
+// value it never takes, so the compiler keeps every operation and nothing is written.
+template <typename T>
+static __global__ void __launch_bounds__(256) k_fma_peak(T* out, T a, T b, int iters) {
+  T x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = (T)(threadIdx.x + j) * (T)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = fma(x[j], a, b);
+  }
+  T s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  if (s == (T)-1234.5) out[blockIdx.x] = s;
+}
+
+template <typename T>
+static kfbi_status alu_peak_t(double* tflops, cudaStream_t s, int iters) {
+  int dev = 0, sms = 0;
+  KFBI_TRY(cudaGetDevice(&dev));
+  KFBI_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256;
+  cudaEvent_t e0, e1;
+  KFBI_TRY(cudaEventCreate(&e0));
+  KFBI_TRY(cudaEventCreate(&e1));
+  double best = 0.0;
+  for (int rep = 0; rep < 4; ++rep) {  // the first launch warms up
+    KFBI_TRY(cudaEventRecord(e0, s));
+    k_fma_peak<T><<<blocks, threads, 0, s>>>(nullptr, (T)0.999, (T)0.001, iters);
+    KFBI_TRY(cudaEventRecord(e1, s));
+    KFBI_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    KFBI_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    const double flops = 2.0 * 32.0 * iters * (double)blocks * threads;
+    if (rep > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  KFBI_TRY(cudaGetLastError());
+  *tflops = best;
+  return KFBI_OK;
+}
+
+extern "C" {
+
+kfbi_status kfbi_alu_peak(int kind, double* tflops, void* stream) {
+  if (tflops == nullptr || (kind != 0 && kind != 1)) return KFBI_ERR_ARG;
+  if (kind == 0) return alu_peak_t<float>(tflops, (cudaStream_t)stream, 8192);
+  return alu_peak_t<double>(tflops, (cudaStream_t)stream, 256);
 }
 
 kfbi_status kfbi_launch_count(kfbi_ctx* c, long long* count) {

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "kfbi_fft.cuh"
 #include "kfbi_internal.cuh"
@@ -953,6 +954,291 @@ static ColKernel<T> col_kernel(int logN) {
   }
 }
 
+// --------------------------------------------------------------------------- column solve, FFTs in registers
+// The float32 column solve for N = A B <= 1024 with every FFT held in registers: B lanes own a
+// column pair (two real columns as one complex sequence, Makhoul reordering as above) and each
+// lane keeps A of its N points. Four-step decomposition of the length-N transform,
+//   X[k1 + A k2] = sum_t W_B^{t k2} W_N^{t k1} sum_a v[t + B a] W_A^{a k1},
+// so an FFT is an A-point DFT in registers, a twiddle, one transpose through shared memory
+// (within the lanes' own warp: __syncwarp only) and B-point DFTs in registers. The inverse runs
+// the same steps in mirror order and leaves the points in the layout they were loaded in. The
+// DCT/DST post- and pre-processing pairs bin m with bin N - m, which another lane of the group
+// holds: one shuffle per register brings it over.
+
+// sine and cosine of 2 pi k / M for compile-time k, M (Taylor series after reduction to
+// [-pi, pi]; evaluated by the compiler)
+constexpr double CT_PI = 3.14159265358979323846;
+constexpr double ct_angle(int k, int M) {
+  int r = k % M;
+  if (2 * r > M) r -= M;
+  return 2.0 * CT_PI * (double)r / (double)M;
+}
+constexpr double ct_sin(double x) {
+  double t = x, s = x;
+  for (int i = 1; i < 24; ++i) {
+    t = -t * x * x / ((2.0 * i) * (2.0 * i + 1.0));
+    s += t;
+  }
+  return s;
+}
+constexpr double ct_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int i = 1; i < 24; ++i) {
+    t = -t * x * x / ((2.0 * i - 1.0) * (2.0 * i));
+    s += t;
+  }
+  return s;
+}
+
+using V2f = V2<float>;
+
+// b times e^{-2 pi i K / M} (forward) or e^{+2 pi i K / M} (inverse), K and M constants
+template <int K, int M, bool INV>
+__device__ __forceinline__ V2f ct_twiddle(V2f b) {
+  if constexpr (K % M == 0) {
+    return b;
+  } else if constexpr (4 * (K % M) == M) {
+    return INV ? V2f{-b.y, b.x} : V2f{b.y, -b.x};
+  } else if constexpr (2 * (K % M) == M) {
+    return V2f{-b.x, -b.y};
+  } else {
+    constexpr float c = (float)ct_cos(ct_angle(K, M));
+    constexpr float s = (float)(INV ? ct_sin(ct_angle(K, M)) : -ct_sin(ct_angle(K, M)));
+    return V2f{b.x * c - b.y * s, b.x * s + b.y * c};
+  }
+}
+
+// one radix-2 Stockham stage of span NS on R points held in registers: item j takes x[j] and
+// x[j + R/2], multiplies the second by w^{(j mod NS)} (w = e^{-+ 2 pi i / (2 NS)}) and writes the
+// sum and difference to y[(j / NS) 2 NS + j mod NS] and the same + NS
+template <int R, int NS, bool INV, int J>
+__device__ __forceinline__ void rg_bfly(const V2f (&x)[R], V2f (&y)[R]) {
+  constexpr int jm = J % NS;
+  constexpr int o = (J / NS) * 2 * NS + jm;
+  const V2f a = x[J];
+  const V2f b = ct_twiddle<jm, 2 * NS, INV>(x[J + R / 2]);
+  y[o] = V2f{a.x + b.x, a.y + b.y};
+  y[o + NS] = V2f{a.x - b.x, a.y - b.y};
+}
+template <int R, int NS, bool INV, int... J>
+__device__ __forceinline__ void rg_stage(const V2f (&x)[R], V2f (&y)[R], std::integer_sequence<int, J...>) {
+  (rg_bfly<R, NS, INV, J>(x, y), ...);
+}
+// length-R DFT (R a power of two) of the points x[0..R) in place, natural order in and out
+template <int R, bool INV, int NS = 1>
+__device__ __forceinline__ void rg_dft(V2f (&x)[R]) {
+  if constexpr (NS < R) {
+    V2f y[R];
+    rg_stage<R, NS, INV>(x, y, std::make_integer_sequence<int, R / 2>{});
+#pragma unroll
+    for (int i = 0; i < R; ++i) x[i] = y[i];
+    rg_dft<R, INV, 2 * NS>(x);
+  }
+}
+// the same on the sub-array x[O .. O + R) of a longer register array
+template <int R, bool INV, int O, int L>
+__device__ __forceinline__ void rg_dft_at(V2f (&x)[L]) {
+  V2f t[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) t[i] = x[O + i];
+  rg_dft<R, INV>(t);
+#pragma unroll
+  for (int i = 0; i < R; ++i) x[O + i] = t[i];
+}
+template <int R, bool INV, int L, int... Q>
+__device__ __forceinline__ void rg_dft_each(V2f (&x)[L], std::integer_sequence<int, Q...>) {
+  (rg_dft_at<R, INV, Q * R, L>(x), ...);
+}
+
+// grid split of the register column kernel: N = A B, A = 2^ceil(logN / 2) points per lane,
+// B = 2^floor(logN / 2) lanes per column pair, F column pairs (F B threads) per block
+template <int LOGN>
+struct ColRegPlan {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int A = 1 << ((LOGN + 1) / 2);
+  static constexpr int B = 1 << (LOGN / 2);
+  static constexpr int F0 = 128 / B;
+  static constexpr int F = F0 < N / 2 ? F0 : N / 2;
+  static constexpr int THREADS = F * B;
+  static constexpr int TPAD = (A * (B + 1) > B * (A + 1) ? A * (B + 1) : B * (A + 1));  // transpose buffer
+  static constexpr size_t SMEM = sizeof(V2f) * ((size_t)N + (N / 2 + 1) + (size_t)N + (size_t)F * TPAD) +
+                                 sizeof(float) * (size_t)N;
+};
+
+// row of the spectral grid that Makhoul position p holds (inverse of mk_pos)
+__device__ __forceinline__ int mk_row(int p, int N) { return p < N / 2 ? 2 * p : 2 * N - 1 - 2 * p; }
+
+template <int LOGN>
+__global__ void __launch_bounds__(ColRegPlan<LOGN>::THREADS) k_col_solve_reg(int dct, const V2f* twN, const float* tab,
+                                                                             const float* lam, float kappa, float* spec,
+                                                                             const V2f* rowinfo, const int* skip) {
+  using P = ColRegPlan<LOGN>;
+  constexpr int N = P::N, A = P::A, B = P::B, Q = A / B;
+  extern __shared__ unsigned char smem_raw[];
+  V2f* sTw = (V2f*)smem_raw;            // e^{-2 pi i m / N}, m < N
+  V2f* sRow = sTw + N;                  // rows' box-data pairs (w, e), NaN in w for written rows
+  V2f* sCs = sRow + N;                  // (cos, sin)(pi m / (2N)), m <= N/2
+  V2f* sX = sCs + (N / 2 + 1);          // transpose buffers, TPAD per column pair
+  float* sLam = (float*)(sX + P::F * P::TPAD);
+  const int f = (int)threadIdx.x / B;   // column pair of this lane group
+  const int t = (int)threadIdx.x % B;   // lane within the group
+  const int k0 = (blockIdx.x * P::F + f) * 2;
+  V2f* S = sX + f * P::TPAD;
+  // tables fixed with the context, before the wait for the previous kernel
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    sTw[i] = twN[i];
+    sLam[i] = lam[i];
+  }
+  for (int m = threadIdx.x; m <= N / 2; m += blockDim.x) dct_cs<float>(tab, N, m, sCs[m].x, sCs[m].y);
+  // rows the row transform left out: w S_k(0) + e S_k(N-1) for this lane's two columns
+  V2f s0 = {0.f, 0.f}, sN = {0.f, 0.f};
+  if (rowinfo != nullptr) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int k = k0 + c;
+      float a, b;
+      if (dct) {
+        a = tsin(tab, k + N, N, qscale(N));
+        b = tsin(tab, k * (2 * N - 1) + N, N, qscale(N));
+      } else {
+        a = tsin(tab, k + 1, N, qscale(N));
+        b = tsin(tab, (k + 1) * (2 * N - 1), N, qscale(N));
+      }
+      if (c == 0) { s0.x = a; sN.x = b; } else { s0.y = a; sN.y = b; }
+    }
+  }
+  pdl_wait();
+  if (*skip) return;
+  // the lane's points v[t + B a], a < A: all loads in flight, then the row pairs staged
+  V2f x[A];
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    const int j = mk_row(t + B * a, N);
+    x[a] = *(const V2f*)(spec + (long)j * N + k0);
+  }
+  if (rowinfo != nullptr)
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sRow[i] = rowinfo[i];
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    const int j = mk_row(t + B * a, N);
+    V2f v = x[a];
+    if (rowinfo != nullptr) {
+      const V2f r = sRow[j];
+      if (r.x == r.x) v = V2f{r.x * s0.x + r.y * sN.x, r.x * s0.y + r.y * sN.y};
+    }
+    if (!dct && (j & 1)) v = V2f{-v.x, -v.y};
+    x[a] = v;
+  }
+  // ---- forward FFT: A-point DFTs, twiddle, transpose, B-point DFTs
+  rg_dft<A, false>(x);
+#pragma unroll
+  for (int k1 = 1; k1 < A; ++k1) x[k1] = cmul(x[k1], sTw[(t * k1) & (N - 1)]);
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) S[k1 * (B + 1) + t] = x[k1];
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int b = 0; b < B; ++b) x[q * B + b] = S[(t + B * q) * (B + 1) + b];
+  rg_dft_each<B, false, A>(x, std::make_integer_sequence<int, Q>{});
+  // lane t now holds X[m], m = (t + B q) + A k2, at register q B + k2
+  // ---- bins N - m from the partner lane (B - t) mod B: register A - 1 - r there (lane 0 pairs
+  // within itself)
+  V2f z[A];
+  const int src = (B - t) & (B - 1);
+#pragma unroll
+  for (int r = 0; r < A; ++r) {
+    V2f v;
+    v.x = __shfl_sync(0xffffffffu, x[A - 1 - r].x, src, B);
+    v.y = __shfl_sync(0xffffffffu, x[A - 1 - r].y, src, B);
+    const int r0 = r < B ? ((B - r) & (B - 1)) : (A - 1 - r + B);
+    z[r] = t == 0 ? x[r0] : v;
+  }
+  // ---- DCT post-processing, eigenvalue division, pre-processing of the inverse, per bin
+  const float lx0 = sLam[k0] - kappa, lx1 = sLam[k0 + 1] - kappa;
+  constexpr int half = N / 2;
+#pragma unroll
+  for (int r = 0; r < A; ++r) {
+    const int m = (t + B * (r / B)) + A * (r % B);
+    const bool lo = m <= half;
+    const int mm = lo ? m : N - m;          // the bin the post-processing is written for
+    const V2f Zm = lo ? x[r] : z[r];        // Z[mm]
+    const V2f ZNm = lo ? z[r] : x[r];       // Z[N - mm]
+    const V2f cs = sCs[mm];
+    V2f Xm, XNm;
+    {
+      const V2f Va{0.5f * (Zm.x + ZNm.x), 0.5f * (Zm.y - ZNm.y)};
+      const V2f Vb{0.5f * (Zm.y + ZNm.y), -0.5f * (Zm.x - ZNm.x)};
+      Xm = V2f{cs.x * Va.x + cs.y * Va.y, cs.x * Vb.x + cs.y * Vb.y};
+      XNm = V2f{cs.y * Va.x - cs.x * Va.y, cs.y * Vb.x - cs.x * Vb.y};
+    }
+    const int l1 = dct ? mm : N - 1 - mm;
+    const float ly = sLam[l1];
+    V2f Gm{__fdividef(Xm.x, ly + lx0), __fdividef(Xm.y, ly + lx1)};
+    V2f GNm{0.f, 0.f};
+    if (mm == half) {
+      GNm = Gm;
+    } else if (mm > 0) {
+      const float ly2 = sLam[dct ? N - mm : mm - 1];
+      GNm = V2f{__fdividef(XNm.x, ly2 + lx0), __fdividef(XNm.y, ly2 + lx1)};
+    }
+    V2f Zo, ZNo;
+    dct_pre<float>(N, mm, cs.x, cs.y, Gm, GNm, Zo, ZNo);
+    z[r] = lo ? Zo : ZNo;
+  }
+  // ---- inverse FFT: B-point DFTs, twiddle, transpose, A-point DFTs
+  rg_dft_each<B, true, A>(z, std::make_integer_sequence<int, Q>{});
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int n1 = 1; n1 < B; ++n1) {
+      const V2f w = sTw[((t + B * q) * n1) & (N - 1)];
+      z[q * B + n1] = cmul(z[q * B + n1], V2f{w.x, -w.y});
+    }
+  __syncwarp();  // the forward transpose's reads are complete
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int n1 = 0; n1 < B; ++n1) S[n1 * (A + 1) + t + B * q] = z[q * B + n1];
+  __syncwarp();
+#pragma unroll
+  for (int k1 = 0; k1 < A; ++k1) z[k1] = S[t * (A + 1) + k1];
+  rg_dft<A, true>(z);
+  // lane t holds v'[t + B n2] at register n2: back to the rows, scaled by 1/N
+  constexpr float invN = 1.0f / (float)N;
+#pragma unroll
+  for (int a = 0; a < A; ++a) {
+    const int j = mk_row(t + B * a, N);
+    float s = invN;
+    if (!dct && (j & 1)) s = -s;
+    *(float2*)(spec + (long)j * N + k0) = make_float2(z[a].x * s, z[a].y * s);
+  }
+}
+
+using ColRegKernel = void (*)(int, const V2f*, const float*, const float*, float, float*, const V2f*, const int*);
+// the register column kernel and its launch shape for N = 2^logN, 16 <= N <= 1024
+static ColRegKernel col_reg_kernel(int logN, int* threads, int* pairs, size_t* smem) {
+  switch (logN) {
+#define KFBI_COLREG(L)                     \
+  case L:                                  \
+    *threads = ColRegPlan<L>::THREADS;     \
+    *pairs = ColRegPlan<L>::F;             \
+    *smem = ColRegPlan<L>::SMEM;           \
+    return k_col_solve_reg<L>;
+    KFBI_COLREG(4)
+    KFBI_COLREG(5)
+    KFBI_COLREG(6)
+    KFBI_COLREG(7)
+    KFBI_COLREG(8)
+    KFBI_COLREG(9)
+    KFBI_COLREG(10)
+#undef KFBI_COLREG
+    default:
+      return nullptr;
+  }
+}
+
 // Probe values: inverse transform along x evaluated only at the interpolation points,
 //   u[j][i] = (2/N) sum_k w_k spec[j][k] sin(pi (k+1)(2i+1)/(2N)), w_{N-1} = 1/2  (DST-III)
 //   u[j][i] = (2/N) sum_k w_k spec[j][k] cos(pi k (2i+1)/(2N)), w_0 = 1/2        (DCT-III)
@@ -1173,13 +1459,24 @@ static int col_threads(int N, int P) {
 template <typename T>
 static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const V2<T>* rowinfo, const int* skip) {
   const int N = c->N;
-  const int P = col_pairs<T>(N, c->col_P);
-  size_t smem = col_smem<T>(N, P);
   const bool rec = c->timing && !c->capturing && c->timing_used < TIMING_CAP;
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
-  KFBI_TRY(launch_k(c->use_pdl && !rec, col_kernel<T>(c->logN), dim3(N / (2 * P)), dim3(col_threads(N, P)), smem, c->stream, N,
-                    c->logN, P, (int)(c->boxbc == KFBI_BOX_NEUMANN0), Tabs<T>::stw(c), Tabs<T>::sin(c), Tabs<T>::lam(c),
-                    (T)c->kappa, spec, sizeof(T) == 8 ? (const T*)c->rinv : nullptr, rowinfo, skip));
+  int rthreads = 0, rpairs = 0;
+  size_t rsmem = 0;
+  ColRegKernel rk = nullptr;
+  if constexpr (sizeof(T) == 4)
+    if (c->col_reg) rk = col_reg_kernel(c->logN, &rthreads, &rpairs, &rsmem);
+  if (rk != nullptr) {
+    KFBI_TRY(launch_k(c->use_pdl && !rec, rk, dim3(N / (2 * rpairs)), dim3(rthreads), rsmem, c->stream,
+                      (int)(c->boxbc == KFBI_BOX_NEUMANN0), (const V2f*)Tabs<float>::twN(c), Tabs<float>::sin(c),
+                      Tabs<float>::lam(c), (float)c->kappa, (float*)spec, (const V2f*)rowinfo, skip));
+  } else {
+    const int P = col_pairs<T>(N, c->col_P);
+    size_t smem = col_smem<T>(N, P);
+    KFBI_TRY(launch_k(c->use_pdl && !rec, col_kernel<T>(c->logN), dim3(N / (2 * P)), dim3(col_threads(N, P)), smem,
+                      c->stream, N, c->logN, P, (int)(c->boxbc == KFBI_BOX_NEUMANN0), Tabs<T>::stw(c), Tabs<T>::sin(c),
+                      Tabs<T>::lam(c), (T)c->kappa, spec, sizeof(T) == 8 ? (const T*)c->rinv : nullptr, rowinfo, skip));
+  }
   launched(c, 1);
   if (rec) {
     KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used + 1], c->stream));
@@ -1361,8 +1658,15 @@ static kfbi_status setup_t(kfbi_ctx*) {
   KFBI_TRY(cudaFuncSetAttribute(k_dens_coef<T, true, S_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
   KFBI_TRY(cudaFuncSetAttribute(k_box_data<T, T4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
   KFBI_TRY(cudaFuncSetAttribute(k_target_jumps<T, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
-  if constexpr (sizeof(T) == 4)
+  if constexpr (sizeof(T) == 4) {
     KFBI_TRY(cudaFuncSetAttribute(k_jumps_fft<G, S_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
+    for (int lg = 4; lg <= 10; ++lg) {
+      int th = 0, pr = 0;
+      size_t sm = 0;
+      ColRegKernel rk = col_reg_kernel(lg, &th, &pr, &sm);
+      KFBI_TRY(cudaFuncSetAttribute(rk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    }
+  }
   return KFBI_OK;
 }
 

@@ -316,9 +316,11 @@ __global__ void k_newton(const double2* coef, int n, int M, const double* fine, 
   double t = lo + (lv - flo) / (fhi - flo) * (hi - lo);
   if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
   double prev = 1.0;
+  double fp_last = 0.0;  // derivative of the compared coordinate at the last iterate
   for (int it = 0; it < NEWTON_MAXIT; ++it) {
     TrigSums v = trig_warp(cc, n, t, lane, false);
     double f = v.f - lv, fp = v.f1;
+    fp_last = fp;
     if (f == 0.0) break;  // exactly on the line: t is the root (no step, no bisection)
     bool same = (f >= 0.0) == pos_lo;
     if (same) lo = t; else hi = t;
@@ -339,9 +341,23 @@ __global__ void k_newton(const double2* coef, int n, int M, const double* fine, 
   }
   TrigSums o = trig_warp(co, n, t, lane, false);
   if (lane == 0) {
-    int first = count_le(kind == 0 ? xmin : ymin, h, N, o.f);
+    const double lo0 = kind == 0 ? xmin : ymin;
+    double xi = o.f;
+    int first = count_le(lo0, h, N, xi);
+    // tie-break: a crossing on a grid node (within SNAP_TOL h) is placed on the node and on the
+    // arm toward the outside, so that the node is in the closed interior. The outward normal
+    // (y_a, -x_a) points to +x on a horizontal line when y_a > 0, to +y on a vertical line
+    // when x_a < 0.
+    int l = (int)rint((xi - lo0) / h - 0.5);
+    l = l < 0 ? 0 : (l > N - 1 ? N - 1 : l);
+    const double gc = grid_coord(lo0, h, l);
+    if (fabs(xi - gc) <= SNAP_TOL * h) {
+      xi = gc;
+      const bool out_plus = kind == 0 ? fp_last > 0.0 : fp_last < 0.0;
+      first = out_plus ? l + 1 : l;
+    }
     cr_alpha[warp] = t;
-    cr_xi[warp] = o.f;
+    cr_xi[warp] = xi;
     cr_first[warp] = first;
     if (first <= 0 || first >= N) atomicOr(flags, FLAG_OUTSIDE);
   }

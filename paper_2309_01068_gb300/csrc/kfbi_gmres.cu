@@ -1314,6 +1314,12 @@ static kfbi_status body(kfbi_ctx* c, int kind, bool fp32, const double* eps_v, c
 
 int body_cap(int max_iter, int m) { return 2 * max_iter + 2 * (max_iter / m) + 8; }
 
+// loop caps of a context: the derived ones unless KFBI_OPT_BODY_CAP / KFBI_OPT_SWEEP_CAP set them
+static int ctx_body_cap(const kfbi_ctx* c, int max_iter, int m) {
+  return c->body_cap_set > 0 ? c->body_cap_set : body_cap(max_iter, m);
+}
+static int ctx_sweep_cap(const kfbi_ctx* c) { return c->sweep_cap_set > 0 ? c->sweep_cap_set : IR_MAX_SWEEPS + 2; }
+
 kfbi_status cap_begin(kfbi_ctx* c, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd);
 kfbi_status cap_end(kfbi_ctx* c, std::vector<cudaGraphNode_t>* sinks);
 kfbi_status add_while(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd, cudaGraphConditionalHandle h,
@@ -1374,7 +1380,7 @@ kfbi_status gmres_start_enqueue(kfbi_ctx* c, double tol, int max_iter, int m) {
 }
 
 kfbi_status ir_start_enqueue(kfbi_ctx* c, double tol, int max_iter) {
-  k_ir_init<<<1, 32, 0, c->stream>>>(c->irctl, tol, max_iter, IR_MAX_SWEEPS, IR_MAX_SWEEPS + 2);
+  k_ir_init<<<1, 32, 0, c->stream>>>(c->irctl, tol, max_iter, IR_MAX_SWEEPS, ctx_sweep_cap(c));
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
 }
@@ -1390,7 +1396,7 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
   if (m > MAX_RESTART) m = MAX_RESTART;
   if (m < 1) m = 1;
   c->gm_m = m;
-  const int cap = body_cap(max_iter, m);
+  const int cap = ctx_body_cap(c, max_iter, m);
   const kfbi_ctx::GmfConfig gf = gmf_select(c, n, m, fp32);
   c->gmf_last_cs = gf.cs;
   const size_t hdr = offsetof(GmresCtl, g);
@@ -1403,8 +1409,9 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
     kfbi_ctx::SolveGraph& G = c->sgraph[kind][fp32 ? 1 : 0];
     kfbi_status st = KFBI_OK;
     if (G.exec == nullptr || G.version != c->layout_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
-        G.cfg != c->cfg_version || G.f32 != gf.f32) {
+        G.cfg != c->cfg_version || G.f32 != gf.f32 || G.cap != cap) {
       st = build_graph(c, G, kind, fp32, eps_v, b, x, cap, gf);
+      G.cap = cap;
       G.m = m;
       G.cs = gf.cs;
       G.pdl = c->use_pdl;
@@ -1432,7 +1439,10 @@ static kfbi_status gmres_run(kfbi_ctx* c, int kind, bool fp32, const double* eps
       KFBI_TRY(cudaMemcpyAsync(c->host_gctl, c->gctl, hdr, cudaMemcpyDeviceToHost, s));
       KFBI_TRY(cudaStreamSynchronize(s));
       if (c->host_gctl->done) break;
-      if (launched_bodies > cap) return KFBI_ERR_TIMEOUT;
+      if (launched_bodies > cap) {  // backstop: the bodies themselves stop at the cap
+        c->host_gctl->status = KFBI_ERR_TIMEOUT;
+        break;
+      }
       chunk = chunk < 8 ? chunk * 2 : 8;
     }
   }
@@ -1545,7 +1555,7 @@ static kfbi_status solve_ir_graph(kfbi_ctx* c, int kind, const double* rhs, doub
   c->gm_m = m;
   const kfbi_ctx::GmfConfig gf = gmf_select(c, n, m, true);
   c->gmf_last_cs = gf.cs;
-  const int cap = body_cap(max_iter, m);
+  const int cap = ctx_body_cap(c, max_iter, m);
   const int max_sweeps = IR_MAX_SWEEPS;
   kfbi_ctx::IrGraph& G = c->irgraph[kind][dnormal != nullptr ? 1 : 0];
   if (G.exec == nullptr || G.version != c->layout_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
@@ -1580,7 +1590,7 @@ static kfbi_status solve_ir_graph(kfbi_ctx* c, int kind, const double* rhs, doub
   const size_t bytes = sizeof(double) * n;
   KFBI_TRY(cudaMemcpyAsync(c->ir_b, rhs, bytes, cudaMemcpyDeviceToDevice, s));
   KFBI_TRY(cudaMemcpyAsync(c->ir_x, x, bytes, cudaMemcpyDeviceToDevice, s));
-  k_ir_init<<<1, 32, 0, s>>>(c->irctl, tol, max_iter, max_sweeps, max_sweeps + 2);
+  k_ir_init<<<1, 32, 0, s>>>(c->irctl, tol, max_iter, max_sweeps, ctx_sweep_cap(c));
   KFBI_TRY(cudaGetLastError());
   KFBI_CHECK(box_table_join(c, s));
   KFBI_TRY(cudaGraphLaunch(G.exec, s));
@@ -1655,6 +1665,7 @@ kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const dou
       rel = bn > 0 ? rn / bn : 0.0;
       if (rel <= tol) { st = KFBI_OK; break; }
       if (total_its >= max_iter || sweeps > max_sweeps) { st = KFBI_ERR_NOT_CONVERGED; break; }
+      if (sweeps > ctx_sweep_cap(c)) { st = KFBI_ERR_TIMEOUT; break; }
       double inner = 0.5 * tol / rel;
       if (inner < 1e-7) inner = 1e-7;
       if (inner > 0.5) inner = 0.5;
@@ -1662,11 +1673,11 @@ kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const dou
       double irel = 0.0;
       KFBI_CHECK(gmres_run(c, kind, true, ev, c->gb, c->gx, inner, max_iter - total_its, restart, true, true, &its,
                            &cyc, &irel, &ist));
-      if (ist == KFBI_ERR_TIMEOUT) return KFBI_ERR_TIMEOUT;
       total_its += its;
       total_cyc += cyc;
       k_axpy_zero<<<cdiv(n, 256), 256, 0, s>>>(x, c->gx, n);
       launched(c, 1);
+      if (ist == KFBI_ERR_TIMEOUT) { st = KFBI_ERR_TIMEOUT; break; }
     }
     out.iterations = total_its;
     out.restarts = total_cyc > sweeps - 1 ? total_cyc - (sweeps - 1) : 0;

@@ -34,6 +34,9 @@ constexpr double TWO_PI = 6.28318530717958647692;
 constexpr int SUBSAMPLES = 8;        // fine samples per node interval for the crossing search
 constexpr int NEWTON_MAXIT = 60;
 constexpr double NEWTON_TOL = 1e-15;
+// a crossing closer than SNAP_TOL h to a grid node is placed on the node, and on the arm that
+// leaves the node toward the outside of the curve: a node on the curve is in the closed interior
+constexpr double SNAP_TOL = 1e-10;
 constexpr double BOX_MARGIN = 3.0;   // interface must stay 3h inside the box
 constexpr int MAX_RESTART = 200;
 constexpr int TIMING_CAP = 8192;
@@ -323,6 +326,7 @@ struct kfbi_ctx {
     int cfg = -1;           // cfg_version it was built with
     int body_launches = 0;  // kernels per replayed body
     int f32 = 0;            // built with the float32 Gram-Schmidt kernel
+    int cap = 0;            // body cap baked into the loop test
   } sgraph[3][2];
   // cluster form of the GMRES body (k_gm_cluster) for the last (n, m); cs = 0: multi-kernel
   struct GmfConfig {
@@ -357,6 +361,9 @@ struct kfbi_ctx {
   bool use_pdl = true;          // programmatic dependent launch between the kernels of a body
   int force_cs = 0;             // cluster size of the Gram-Schmidt kernel: 0 automatic, 8 or 16
   int col_P = 0;                // column pairs per block of the float32 column kernel (0 automatic)
+  bool col_reg = false;         // float32 column solve with register FFTs (N <= 1024), KFBI_OPT_COL_REG
+  int body_cap_set = 0;         // GMRES loop body cap (0: derived from max_iter), KFBI_OPT_BODY_CAP
+  int sweep_cap_set = 0;        // refinement loop body cap (0: sweeps + 2), KFBI_OPT_SWEEP_CAP
   int cfg_version = 0;          // bumped by every option that changes the launched kernels
   int gmf_last_cs = 0;          // cluster size used by the last GMRES run
   size_t gmf_smem_max[2] = {0, 0};  // per element type (double, float): 0 = not queried, 1 = unavailable

@@ -195,7 +195,8 @@ __global__ void k_st_stefan_rhs(const double* eta, const double* th_a, const dou
   double curv = (TWO_PI / scal[SC_L]) * th_a[j];
   rhs[j] = -ec * curv - T1n[j];
   epsv[j] = eps_v;
-  ratio[j] = fabs(ec / eps_v);
+  // lambda_1 = max |eps_C / eps_V| (case I) or lambda_2 = max |2 eps_C| (case II, eps_V = 0)
+  ratio[j] = eps_v > 0.0 ? fabs(ec / eps_v) : fabs(2.0 * ec);
 }
 
 // T = 0 in Omega+ (the seed at the melt temperature), St outside
@@ -305,14 +306,15 @@ __device__ __forceinline__ double stiff(double lam, double L, int p, double k) {
 }
 
 // N-hat = FFT(rhs) - s(L^n) eta-hat; eta-hat^{n+1} = e1 eta-hat + dt/2 (3 e1 N-hat - e2 N-hat^{n-1});
-// history shift (Sec. 5.3)
+// history shift (Sec. 5.3). explicit_ != 0: no stiff part (s = 0, e1 = e2 = 1), the
+// Adams-Bashforth comparison scheme of Sec. 6.2.2.
 __global__ void k_st_propagate(double2* eta_h, const double2* rhs_h, double2* Nprev, int n, double* scal, double dt,
-                               int p, double lam_fixed) {
+                               int p, double lam_fixed, int explicit_) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   int nk = n / 2 + 1;
   if (k >= nk) return;
   bool first = scal[SC_STEPS] == 0.0;
-  double lam = lam_fixed > 0.0 ? lam_fixed : scal[SC_LAM];
+  double lam = explicit_ ? 0.0 : (lam_fixed > 0.0 ? lam_fixed : scal[SC_LAM]);
   double L = scal[SC_L], Ln = scal[SC_LNEW], Lp = scal[SC_LPREV];
   double sn = stiff(lam, L, p, k), snew = stiff(lam, Ln, p, k), sp = stiff(lam, Lp, p, k);
   double e1 = exp(0.5 * dt * (sn + snew));
@@ -417,12 +419,13 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
   k_st_dft<<<wb(nk), 256, 0, s>>>(st->work + n, 1, 1, n, tw, coef);            // rhs-hat
   // 6. AB2 scalars, propagator, history
   k_st_scalars<<<1, 32, 0, s>>>(st->scal, dt);
+  const int expl = P.scheme == KFBI_SCHEME_EXPLICIT ? 1 : 0;
   if (P.kind == KFBI_STEP_HELE_SHAW)
     k_st_propagate<<<cdiv(nk, 256), 256, 0, s>>>((double2*)st->eta_h, coef, (double2*)st->Nprev_h, n, st->scal, dt, 3,
-                                                 P.sigma);
-  else
-    k_st_propagate<<<cdiv(nk, 256), 256, 0, s>>>((double2*)st->eta_h, coef, (double2*)st->Nprev_h, n, st->scal, dt, 2,
-                                                 -1.0);
+                                                 P.sigma, expl);
+  else  // Stefan case I (second order) or II (eps_V = 0, third order); lambda from k_st_tangential
+    k_st_propagate<<<cdiv(nk, 256), 256, 0, s>>>((double2*)st->eta_h, coef, (double2*)st->Nprev_h, n, st->scal, dt,
+                                                 P.eps_v > 0.0 ? 2 : 3, -1.0, expl);
   k_st_idft<<<wb(n), 256, 0, s>>>((const double2*)st->eta_h, 1, n, tw, 0, st->eta, 1);
   k_st_finish<<<1, 32, 0, s>>>(st->scal, dt);
   KFBI_TRY(cudaGetLastError());
@@ -504,7 +507,8 @@ kfbi_status kfbi_thetal_create(kfbi_ctx* c, int n, const double* eta, double L, 
   if (n < 8 || n > c->max_nodes || !(L > 0.0)) return KFBI_ERR_ARG;
   if (prm->kind != KFBI_STEP_HELE_SHAW && prm->kind != KFBI_STEP_STEFAN) return KFBI_ERR_ARG;
   if (prm->kind == KFBI_STEP_HELE_SHAW && c->boxbc != KFBI_BOX_FREESPACE_DL) return KFBI_ERR_ARG;
-  if (prm->kind == KFBI_STEP_STEFAN && (c->boxbc != KFBI_BOX_NEUMANN0 || !(prm->eps_v > 0.0))) return KFBI_ERR_ARG;
+  if (prm->kind == KFBI_STEP_STEFAN && (c->boxbc != KFBI_BOX_NEUMANN0 || !(prm->eps_v >= 0.0))) return KFBI_ERR_ARG;
+  if (prm->scheme != KFBI_SCHEME_SEMI_IMPLICIT && prm->scheme != KFBI_SCHEME_EXPLICIT) return KFBI_ERR_ARG;
   if (!(prm->tol > 0.0) || prm->max_iter < 1 || prm->restart < 1 || prm->restart > MAX_RESTART) return KFBI_ERR_ARG;
   kfbi_thetal* st = new kfbi_thetal();
   kfbi_status s = thetal_create_impl(c, n, eta, L, xbar, prm, st);

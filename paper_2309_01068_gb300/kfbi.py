@@ -24,6 +24,7 @@ OPT_FP32_ARNOLDI = 8
 OPT_PUSH_REDUCE = 9
 OPT_FUSE_INTERP = 10
 OPT_FUSE_DFT = 11
+OPT_BODY_CAP, OPT_SWEEP_CAP, OPT_COL_REG = 12, 13, 14
 MLP_FEATURES, MLP_MODES = 47, 16
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2
@@ -31,6 +32,7 @@ FP64, MIXED = 0, 1
 SINGLE, DOUBLE = 0, 1
 BIE_INTERIOR_DL, BIE_HS_EXTERIOR_MDL, BIE_STEFAN_SL = 0, 1, 2
 STEP_HELE_SHAW, STEP_STEFAN = 0, 1
+SCHEME_SEMI_IMPLICIT, SCHEME_EXPLICIT = 0, 1
 
 
 class KfbiError(RuntimeError):
@@ -57,7 +59,7 @@ class ThetaLParams(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("sigma", ctypes.c_double), ("J", ctypes.c_double),
                 ("St", ctypes.c_double), ("eps_c", ctypes.c_double), ("eps_aniso", ctypes.c_double),
                 ("eps_v", ctypes.c_double), ("fold", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("restart", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("restart", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 _lib = None
@@ -109,6 +111,7 @@ _SIGNATURES = {
     "kfbi_batch_autotune": (_I, [_P, _I, _P, _D, _I, _I, ctypes.POINTER(_D)]),
     "kfbi_get_option": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "kfbi_grid_solve_noalloc": (_I, [_I, _D, _D, _I, _P, _P, _P]),
+    "kfbi_alu_peak": (_I, [_I, ctypes.POINTER(_D), _P]),
 }
 
 
@@ -243,13 +246,15 @@ class Context:
         return y
 
     def solve_bie(self, kind, rhs, density=None, tol=1e-10, max_iter=500, restart=100, eps_v=None):
-        """Returns (density, info dict); density is updated in place when given."""
+        """Returns (density, info dict); density is updated in place when given. A solve that
+        stops unconverged (ERR_NOT_CONVERGED) or at a loop bound (ERR_TIMEOUT) returns its
+        iterate with that status in info["status"]; other errors raise."""
         self._sync_stream()
         x = density if density is not None else torch.zeros_like(rhs)
         info = SolveInfo()
         _check(self.lib.kfbi_solve_bie(self.handle, kind, _ptr(eps_v), _f64(rhs, (self.n,)), float(tol),
                                        int(max_iter), int(restart), _f64(x, (self.n,)), ctypes.byref(info)),
-               "kfbi_solve_bie", allow=(ERR_NOT_CONVERGED,))
+               "kfbi_solve_bie", allow=(ERR_NOT_CONVERGED, ERR_TIMEOUT))
         return x, info.as_dict()
 
     def grid_solve(self, rhs, out=None):
@@ -497,11 +502,17 @@ class Batch:
 
 def grid_solve_noalloc(rhs, h, kappa=0.0, boxbc=BOX_DIRICHLET0, out=None):
     """kfbi_grid_solve_noalloc: the box solve without any device allocation in the library
-    (its scratch is a static device array; N <= 512). `out` may be preallocated."""
+    (its scratch is a static device array; N <= 512). `out` may be preallocated (float64,
+    N x N, on the device of rhs; it may be rhs itself); anything else raises ValueError before
+    the library is called."""
     lib = load()
     N = rhs.shape[0]
+    rp = _f64(rhs, (N, N))
     u = out if out is not None else torch.empty_like(rhs)
-    _check(lib.kfbi_grid_solve_noalloc(N, float(h), float(kappa), int(boxbc), _f64(rhs, (N, N)), _ptr(u), _stream()),
+    up = _f64(u, (N, N))
+    if u.device != rhs.device:
+        raise ValueError(f"out is on {u.device}, rhs on {rhs.device}")
+    _check(lib.kfbi_grid_solve_noalloc(N, float(h), float(kappa), int(boxbc), rp, up, _stream()),
            "kfbi_grid_solve_noalloc")
     return u
 
@@ -510,12 +521,12 @@ class ThetaL:
     """kfbi_thetal_create / kfbi_step / kfbi_thetal_read on a context."""
 
     def __init__(self, ctx: Context, eta, L, xbar, kind, tol=1e-8, max_iter=500, restart=100, sigma=0.0, J=0.0,
-                 St=0.0, eps_c=0.0, eps_aniso=0.0, eps_v=0.0, fold=4):
+                 St=0.0, eps_c=0.0, eps_aniso=0.0, eps_v=0.0, fold=4, scheme=SCHEME_SEMI_IMPLICIT):
         self.ctx = ctx
         self.lib = ctx.lib
         self.n = eta.shape[0]
         p = ThetaLParams(kind=kind, sigma=sigma, J=J, St=St, eps_c=eps_c, eps_aniso=eps_aniso, eps_v=eps_v,
-                         fold=fold, tol=tol, max_iter=max_iter, restart=restart)
+                         fold=fold, tol=tol, max_iter=max_iter, restart=restart, scheme=scheme)
         xb = (ctypes.c_double * 2)(float(xbar[0]), float(xbar[1]))
         h = ctypes.c_void_p()
         ctx._sync_stream()
@@ -569,3 +580,11 @@ class ThetaL:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+
+def alu_peak(kind):
+    """kfbi_alu_peak: measured FMA throughput in TFLOP/s (kind 0 float32, 1 float64)."""
+    lib = load()
+    v = ctypes.c_double()
+    _check(lib.kfbi_alu_peak(int(kind), ctypes.byref(v), _stream()), "kfbi_alu_peak")
+    return v.value

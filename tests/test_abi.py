@@ -69,6 +69,6 @@ def test_binding_constants_match_header():
             assert getattr(kfbi, name) == int(value), name
             checked += 1
     for name in ("OK", "ERR_ARG", "ERR_CAPACITY", "BOX_FREESPACE_DL", "MIXED", "DOUBLE", "BIE_STEFAN_SL",
-                 "OPT_FUSE_INTERP", "OPT_FUSE_DFT"):
+                 "OPT_FUSE_INTERP", "OPT_FUSE_DFT", "OPT_BODY_CAP", "OPT_SWEEP_CAP"):
         assert hasattr(kfbi, name), name
     assert checked >= 25

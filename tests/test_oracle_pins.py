@@ -287,3 +287,45 @@ def test_outside_box_and_underresolved():
     nodes = W.equal_arclength(shape, 256)
     with pytest.raises((K.Underresolved, K.OutsideBox)):
         K.Kfbi(16, (-1, 1, -1, 1), 0.0, K.BOX_DIRICHLET0).set_interface(nodes["xy"])
+
+
+# ---------------------------------------------------------------- classification edge cases (R3, R4)
+def circle_through_node(N, i, j, R, angle_deg, n=256):
+    """Nodes of a circle of radius R that passes through grid node (i, j) at the given polar angle."""
+    grid = K.Grid(N, (-1.0, 1.0, -1.0, 1.0))
+    th = math.radians(angle_deg)
+    cx, cy = grid.x[i] - R * math.cos(th), grid.y[j] - R * math.sin(th)
+    a = 2 * math.pi * (np.arange(n) + 0.37 / 8) / n + th   # no bracket sample on the grid node
+    return np.stack([cx + R * np.cos(a), cy + R * np.sin(a)], -1)
+
+
+@pytest.mark.parametrize("angle", [-30.0, 150.0, 60.0, -120.0])
+def test_node_on_the_curve_is_in_the_closed_interior(angle):
+    """A grid node on the curve (to rounding) lies in Omega+ and its row and column
+    crossings sit on the arms that leave it toward the outside, whatever the quadrant."""
+    N, i, j = 64, 30, 33
+    s = K.Kfbi(N, (-1, 1, -1, 1), 0.0, K.BOX_DIRICHLET0).set_interface(circle_through_node(N, i, j, 0.4, angle))
+    assert s.cl.side[j, i] == 1
+    on = np.abs(s.cr.xi - np.where(s.cr.kind == 0, s.grid.x[i], s.grid.y[j])) == 0.0
+    assert on.sum() == 2                            # one row and one column crossing snapped onto it
+    v, _, u = s.apply(K.LAYER_DOUBLE, np.ones(s.iface.n))
+    assert np.abs(u - s.cl.side).max() < 1e-12      # D1 is still the indicator (Gauss)
+
+
+def test_arm_crossed_twice_gets_no_correction():
+    """A circle whose top rises just above a grid line between two nodes crosses that arm twice;
+    both ends are outside, the arm carries no correction and D1 is still the indicator (R4)."""
+    N = 64
+    h = 2.0 / N
+    j = 40
+    yl = -1.0 + (j + 0.5) * h
+    xc = -1.0 + 20.0 * h                    # the midpoint of the arm (19, j)-(20, j)
+    R = 0.5
+    a = 2 * math.pi * np.arange(256) / 256
+    xy = np.stack([xc + R * np.cos(a), yl - R + 2e-5 + R * np.sin(a)], -1)
+    s = K.Kfbi(N, (-1, 1, -1, 1), 0.0, K.BOX_DIRICHLET0).set_interface(xy)
+    i = int(np.searchsorted(s.grid.x, xc))
+    assert s.cl.hcount[j, i] == 2 and s.cl.hid[j, i] == -1
+    assert s.cl.side[j, i - 1] == 0 and s.cl.side[j, i] == 0
+    _, _, u = s.apply(K.LAYER_DOUBLE, np.ones(s.iface.n))
+    assert np.abs(u - s.cl.side).max() < 1e-12

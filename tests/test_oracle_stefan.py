@@ -251,3 +251,102 @@ def test_time_discrete_scheme_is_second_order_from_consistent_history():
         res[tau] = m.R
     e = [abs(res[t] - res[tf]) for t in (2e-3, 1e-3, 5e-4)]
     assert e[0] / e[1] > 3.2 and e[1] / e[2] > 2.8, e
+
+
+# ---------------------------------------------------------------- case II and the explicit scheme
+def test_stefan_case2_symbol_is_high_mode_limit_of_linear_rate():
+    """Case II (eps_V = 0): the first-kind equation on a circle gives U_k = -eps_C kappa_k /
+    (R I_k(cR) K_k(cR)); R I_k K_k -> R / (2k) for k >> cR, so the rate tends to
+    -2 eps_C k^3 / R^3, the symbol -lambda_2 (2 pi / L)^3 |k|^3 with lambda_2 = max |2 eps_C|."""
+    R, eps_c, c, n = 0.3, 3e-3, math.sqrt(3000.0), 16384
+    L = 2 * math.pi * R
+    nd = W.equal_arclength(W.polar(R, []), 64)
+    st = T.state_from_nodes(nd["xy"], nd["theta"], nd["L"])
+    T.stefan_step(K.Kfbi(64, (-1, 1, -1, 1), c * c, K.BOX_NEUMANN0), st, 1.5 / (c * c), -0.5, eps_c, 0.0, 4, 0.0,
+                  tol=1e-10)
+    assert "lam2" in st.last and "lam1" not in st.last
+    sym = T.stefan_symbol_case2(n, st.last["lam2"])(L)
+    prev = None
+    for k in (64, 512, 2048, 8000):
+        ik_kk = float(mpmath.besseli(k, c * R) * mpmath.besselk(k, c * R))
+        rate = -eps_c * (k * k - 1) / R ** 2 / (R * ik_kk)
+        err = abs(sym[k] / rate - 1.0)
+        if prev is not None:
+            assert err < prev
+        prev = err
+    assert prev < 1e-3
+
+
+def test_stefan_first_kind_on_circle_closed_form():
+    """eps_V = 0: -S psi = cos k a on a circle gives psi = cos k a / (R I_k(cR) K_k(cR))."""
+    R, kap, n, k = 0.5, 900.0, 128, 3
+    c = math.sqrt(kap)
+    xy, a = circle_nodes(R, n)
+    exact = np.cos(k * a) / (R * sp.ive(k, c * R) * sp.kve(k, c * R))
+    errs = []
+    for N in (128, 256):
+        s = K.Kfbi(N, (-2, 2, -2, 2), kap, K.BOX_NEUMANN0).set_interface(xy)
+        psi, info = gmres(lambda x: s.bie_matvec(K.BIE_STEFAN_SL, x, eps_v=np.zeros(n)), np.cos(k * a), tol=1e-12)
+        assert info["converged"]
+        errs.append(np.abs(psi - exact).max() / np.abs(exact).max())
+    # the first-kind solve carries the grid's O(h^2) error of S without the damping of eps_V
+    assert errs[0] < 0.2 and errs[1] < 0.3 * errs[0], errs
+
+
+def test_stefan_case2_steps_match_radial_reference():
+    """eps_V = 0 (Gibbs-Thomson without kinetics): two steps from a smooth history on a circle
+    agree with the radial reference."""
+    tau, N, n, k0 = 1e-3, 128, 128, 10
+    rad = RadialStefan(R0, ST, EPS_C, 0.0)
+    for _ in range(k0):
+        rad.step(tau)
+    st, s, r = _warm_state(rad, N, n, tau, k0)
+    for _ in range(2):
+        R_old = st.L / (2 * math.pi)
+        T.stefan_step(s, st, tau, ST, EPS_C, 0.0, 4, 0.0, tol=1e-12)
+        rad.step(tau)
+        assert abs(st.density.mean() - rad.U_prev) < 1e-2 * abs(rad.U_prev)
+        assert abs(st.L / (2 * math.pi) - rad.R) < 1e-3 * rad.R
+        mask = (np.abs(r - R_old) > 3 * s.grid.h) & (r < 0.9)
+        assert np.abs(st.T - rad.at(r))[mask].max() < 2e-3 * abs(ST)
+
+
+def _high_modes(st):
+    n = st.eta.shape[0]
+    eh = np.fft.fft(st.eta) / n
+    return float(np.abs(eh[n // 4: n - n // 4 + 1]).max())
+
+
+def _stability_run(tau, steps, scheme):
+    """The stability test of Sec. 6.2.2 at half its resolution: eps_V = 0, eps_C = 0.05,
+    r = 1 + 0.02 cos 4a in (-2, 2)^2 with 64 nodes on a 128^2 grid, St = -0.5. Returns the
+    high-mode amplitudes of eta per step, stopping early when the curve stops being
+    representable on the grid."""
+    nd = W.equal_arclength(W.polar(1.0, [(4, 0.02, 0.0)]), 64)
+    st = T.state_from_nodes(nd["xy"], nd["theta"], nd["L"])
+    s = K.Kfbi(128, (-2, 2, -2, 2), 1.5 / tau, K.BOX_NEUMANN0)
+    amps = []
+    for _ in range(steps):
+        try:
+            T.stefan_step(s, st, tau, -0.5, 0.05, 0.0, 4, 0.0, tol=1e-10, scheme="explicit" if scheme else
+                          "semi-implicit")
+        except (K.Underresolved, K.OutsideBox):
+            amps.append(math.inf)
+            break
+        amps.append(_high_modes(st))
+    return amps
+
+
+def test_explicit_scheme_is_unstable_above_its_limit_and_semi_implicit_is_not():
+    """Third-order stiffness of case II (Sec. 6.2.2): the top mode k = n/2 of the first-kind
+    Stefan equation on the circle decays at about 2 eps_C k^2 c / R^2 (c = sqrt(3 / (2 tau)) >> k / R:
+    R I_k K_k ~ 1 / (2c)), so Adams-Bashforth without the stiff part needs
+    tau 2 eps_C k^2 sqrt(1.5 tau) < 1, tau < 6.4e-5 for k = 32: at 2e-4 the high modes grow
+    until the curve breaks within a few steps; at 2.5e-5 they decay; the semi-implicit scheme
+    at 1e-2 (160x the explicit limit) keeps them small and bounded."""
+    bad = _stability_run(2e-4, 8, True)
+    assert bad[-1] == math.inf or bad[-1] > 1.0, bad
+    good = _stability_run(2.5e-5, 20, True)
+    assert all(np.isfinite(good)) and good[-1] < good[0] and max(good) < 0.1, good
+    semi = _stability_run(1e-2, 8, False)
+    assert all(np.isfinite(semi)) and max(semi) < 1e-3, semi

@@ -53,3 +53,33 @@ def test_noalloc_rejects_sizes_beyond_maximum():
     with pytest.raises(K.KfbiError) as e:
         K.grid_solve_noalloc(torch.zeros((64, 64), dtype=torch.float64, device="cuda"), 0.1, 0.0, K.BOX_NEUMANN0)
     assert e.value.status == K.ERR_SINGULAR
+
+
+def test_noalloc_in_place_and_on_a_side_stream():
+    """rhs and u may alias; a call on a non-default stream, synchronised, gives the same result."""
+    N, box, kappa = 128, (-1.0, 1.0, -1.0, 1.0), 3.0
+    h = (box[1] - box[0]) / N
+    ctx = K.Context(N, box, kappa, K.BOX_DIRICHLET0, K.FP64, max_nodes=64)
+    rng = np.random.default_rng(7)
+    rhs = torch.tensor(rng.standard_normal((N, N)), dtype=torch.float64, device="cuda")
+    ref = ctx.grid_solve(rhs.clone())
+    buf = rhs.clone()
+    u = K.grid_solve_noalloc(buf, h, kappa, K.BOX_DIRICHLET0, out=buf)
+    torch.cuda.synchronize()
+    assert u.data_ptr() == buf.data_ptr()
+    assert rel(u, ref) < 1e-12
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        u2 = K.grid_solve_noalloc(rhs, h, kappa, K.BOX_DIRICHLET0)
+    side.synchronize()
+    assert rel(u2, ref) < 1e-12
+    ctx.close()
+
+
+def test_noalloc_rejects_a_wrong_output_before_the_call():
+    rhs = torch.zeros((64, 64), dtype=torch.float64, device="cuda")
+    for bad in (torch.zeros((64, 64), dtype=torch.float32, device="cuda"),
+                torch.zeros((32, 64), dtype=torch.float64, device="cuda"),
+                torch.zeros((64 * 64,), dtype=torch.float64, device="cuda")):
+        with pytest.raises(ValueError):
+            K.grid_solve_noalloc(rhs, 1.0 / 32, out=bad)
