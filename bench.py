@@ -398,6 +398,88 @@ def warmstart_leg(torch, K):
                 mean_gmres_iterations=dict(zero=float(np.mean(its0)), network=float(np.mean(its1))))
 
 
+def warm_start_c5_leg(torch, K, train_steps=50, eval_steps=8):
+    """The learned warm start on the time step of the 4096^2 Stefan dendrite (4096 nodes,
+    tol 1e-8): a network (47-256-256-1, the library's kernels) trained on the (features,
+    density) pairs of 50 steps of the 2048^2 dendrite (2048 nodes each, about 1e5 rows), then
+    the same 4096^2 steps from one checkpoint with the previous-step start and with the
+    network attached (each step takes the start with the smaller float64 residual)."""
+    import numpy as np
+
+    import workloads as W
+
+    def stefan(N, n):
+        p = W.config_stefan(N=N, n=n)
+        x = p.extra
+        ctx = K.Context(p.N, p.box, p.kappa, K.BOX_NEUMANN0, K.MIXED, max_nodes=p.n)
+        eta = torch.tensor(p.theta - alpha_array(p.n), dtype=torch.float64, device="cuda")
+        st = K.ThetaL(ctx, eta, p.L, p.xy.mean(0), K.STEP_STEFAN, tol=1e-8, max_iter=3000, restart=150,
+                      St=x["St"], eps_c=x["eps_c"], eps_aniso=x["eps_aniso"], eps_v=x["eps_v"], fold=x["fold"])
+        return p, ctx, st
+
+    t0 = time.perf_counter()
+    p3, c3, s3 = stefan(2048, 2048)
+    feats, targets = [], []
+    for _ in range(train_steps):
+        s3.step(p3.extra["dt"])
+        f, t = s3.training_pair()
+        feats.append(f.clone())
+        targets.append(t.clone())
+    s3.close()
+    c3.close()
+    X, T = torch.cat(feats), torch.cat(targets)
+    data_s = time.perf_counter() - t0
+    m = K.Mlp(hidden=256, max_rows=max(X.shape[0], 4096))
+    m.set_params(W.mlp_init(21))
+    g = torch.Generator(device="cpu").manual_seed(0)
+    first, _ = m.gradients(X, T)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in range(3000):
+        idx = torch.randint(0, X.shape[0], (512,), generator=g, dtype=torch.int32).cuda()
+        m.train_step(X, T, idx=idx, lr=1e-3 if it < 2000 else 3e-4, want_loss=False)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    last, _ = m.gradients(X, T)
+    p5, c5, s5 = stefan(4096, 4096)
+    dt = p5.extra["dt"]
+    for _ in range(3):
+        s5.step(dt)
+    ck = s5.read(T=True)
+    ck = {k: (v.clone() if torch.is_tensor(v) else v) for k, v in ck.items()}
+    res = {}
+    for name, net in (("previous_step", None), ("network_policy", m)):
+        s5.write(eta=ck["eta"], density=ck["density"], nhat=ck["nhat"], T=ck["T"], T_prev=ck["T_prev"],
+                 scalars=ck["scalars"])
+        s5.set_warmstart(net)
+        torch.cuda.synchronize()
+        its, ms = [], []
+        for _ in range(eval_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            info = s5.step(dt)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            its.append(info["iterations"])
+        out = s5.read(T=False)
+        res[name] = dict(mean_gmres_iterations=float(np.mean(its)), ms_per_step=float(np.mean(ms)),
+                         density=out["density"].clone(),
+                         network_starts=int(out["scalars"][14] - ck["scalars"][14]),
+                         last_residual_ratio=float(out["scalars"][15]))
+        s5.set_warmstart(None)
+    d = float((res["network_policy"]["density"] - res["previous_step"]["density"]).abs().max()
+              / res["previous_step"]["density"].abs().max())
+    for r in res.values():
+        r.pop("density")
+    s5.close()
+    c5.close()
+    return dict(workload="stefan_4096x4096_n4096 (network trained on stefan_2048x2048_n2048 steps)", tol=1e-8,
+                training_rows=int(X.shape[0]), data_s=data_s, train_steps=3000, train_s=train_s,
+                loss_first=first, loss_last=last, eval_steps=eval_steps, **res,
+                final_density_rel_diff=d)
+
+
 def stefan_leg(torch, K, steps=3, N=2048, n=2048, tol=1e-9, compare_fp64=True):
     """Stefan dendrite steps on the N^2 Neumann grid (seed r = 0.1 (1 + 0.2 cos 4a) in [-2,2]^2,
     undercooling -0.5, 4-fold anisotropy, dt = 5e-4), mixed precision to tol; the GMRES start
@@ -711,6 +793,7 @@ def main():
         for name, leg in (("col_kernel_sizes", lambda: col_kernel_sizes(torch, K)),
                           ("batched", lambda: batched_leg(torch, K, flush)), ("warm_start", lambda: warmstart_leg(torch, K)),
                           ("stefan", lambda: stefan_leg(torch, K)),
+                          ("warm_start_c5", lambda: warm_start_c5_leg(torch, K)),
                           ("stefan_4096", lambda: stefan_leg(torch, K, N=4096, n=4096, tol=1e-8, compare_fp64=False))):
             try:
                 extras[name] = leg()

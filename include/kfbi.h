@@ -246,7 +246,8 @@ kfbi_status kfbi_step(kfbi_ctx* ctx, kfbi_thetal* st, double dt, kfbi_solve_info
  *   eta [n], xy [n][2] nodes of the last solved curve (read only), density [n],
  *   nhat [(n/2+1)][2] the Adams-Bashforth history of N-hat (complex), T and T_prev
  *   [N][N] (Stefan only). `scalars` is a HOST array of KFBI_THETAL_SCALARS doubles:
- *   (L, Xbar_x, Xbar_y, t, steps, M_prev, Q_prev_x, Q_prev_y, L_prev, then work slots).
+ *   (L, Xbar_x, Xbar_y, t, steps, M_prev, Q_prev_x, Q_prev_y, L_prev, then work slots; slots
+ *   14 and 15 are the learned warm start's counters, see kfbi_thetal_set_warmstart).
  * Writing back what was read restores the state exactly. kfbi_thetal_read synchronises
  * the stream when `scalars` is given. Errors: ARG, CUDA.
  */
@@ -347,6 +348,12 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             radix-4 Stockham kernel; 1 (grids with N <= 1024): every FFT is
  *                             held in registers by one group of B lanes (an A-point DFT per lane,
  *                             one transpose through shared memory, B-point DFTs; N = A B).
+ *   KFBI_OPT_COL_TC           0 (default); 1 (grids with N <= 256, else KFBI_ERR_CAPACITY):
+ *                             the float32 column solve as two dense contractions on the tensor
+ *                             cores (kfbi_tc_gemm, split bfloat16 products): the transform along
+ *                             y as an N x N matrix, the eigenvalue division in the first one's
+ *                             epilogue, then the inverse transform matrix. The row transform then
+ *                             writes every row. Setting it allocates the two N x N matrices.
  *   KFBI_OPT_BODY_CAP         0 (default): the device-side GMRES loop (the body count of the
  *                             graph's WHILE node, or of the host-driven loop) stops after
  *                             2 max_iter + 2 max_iter / restart + 8 bodies; a value > 0 sets
@@ -375,7 +382,8 @@ enum {
   KFBI_OPT_FUSE_DFT = 11,
   KFBI_OPT_BODY_CAP = 12,
   KFBI_OPT_SWEEP_CAP = 13,
-  KFBI_OPT_COL_REG = 14
+  KFBI_OPT_COL_REG = 14,
+  KFBI_OPT_COL_TC = 15
 };
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);
@@ -409,6 +417,12 @@ void kfbi_mlp_destroy(kfbi_mlp* mlp);
 /* Stream of the kfbi_mlp_* calls (default: the legacy default stream). */
 kfbi_status kfbi_mlp_set_stream(kfbi_mlp* mlp, void* stream);
 kfbi_status kfbi_mlp_param_count(kfbi_mlp* mlp, int* count);
+/* The H x H layer (forward, input gradient and weight gradient) on the tensor cores through
+ * kfbi_tc_gemm (enable = 1, the default) or on the CUDA cores (0, one fused kernel per 16 rows).
+ * kfbi_mlp_tc_error reads the tensor-core completion flag (0: every wait completed); both
+ * synchronise the network's stream. */
+kfbi_status kfbi_mlp_set_tensor_cores(kfbi_mlp* mlp, int enable);
+kfbi_status kfbi_mlp_tc_error(kfbi_mlp* mlp, int* flag);
 /* Host float32 parameters in and out; set_params also resets Adam's moments and step
  * count. Both synchronise the stream. */
 kfbi_status kfbi_mlp_set_params(kfbi_mlp* mlp, const float* params);
@@ -430,6 +444,25 @@ kfbi_status kfbi_warmstart_features(kfbi_ctx* ctx, const double* rhs, float* fea
 /* density[j] = rms(rhs) y_j: the network's initial density for kfbi_solve_bie (device
  * [n] float64), on the context's stream. n <= max_rows of the network. Async. */
 kfbi_status kfbi_warmstart_predict(kfbi_ctx* ctx, kfbi_mlp* mlp, const double* rhs, double* density);
+
+/*
+ * Learned warm start inside kfbi_step (not in the paper). With a network attached, every step
+ * forms the network's initial density for its BIE (kfbi_warmstart_predict on the step's
+ * right-hand side) and the residual norms ||b - A g|| of that guess and ||b - A x|| of the
+ * previous step's density under the float64 operator (two applies), and starts GMRES from the
+ * one with the smaller residual. GMRES still iterates to the step's tolerance, so the solution
+ * is the method's either way. Scalars slot 14 counts the steps that took the network's start,
+ * slot 15 holds the last ratio ||b - A g|| / ||b - A x||. mlp = NULL detaches; the network is
+ * not owned (keep it alive while attached) and needs max_rows >= n.
+ */
+kfbi_status kfbi_thetal_set_warmstart(kfbi_thetal* st, kfbi_mlp* mlp);
+/*
+ * kfbi_thetal_training_pair -- the warm-start training sample of the system the last kfbi_step
+ * solved: features [n][KFBI_MLP_FEATURES] float32 of its curve and right-hand side, and the
+ * target density / rms(rhs) [n] float32 (device arrays). Asynchronous. Errors: ARG, STATE,
+ * CAPACITY, CUDA.
+ */
+kfbi_status kfbi_thetal_training_pair(kfbi_thetal* st, float* feat, float* target);
 
 /* ------------------------------------------------------------------------------------
  * Batched solves: many independent interface problems (each its own grid, box, kappa,
@@ -468,10 +501,11 @@ kfbi_status kfbi_batch_set_stream(kfbi_batch* batch, void* stream);
 kfbi_status kfbi_batch_solve(kfbi_batch* batch, int kind, const double* const* rhs, double* const* density,
                              double tol, int max_iter, int restart, kfbi_solve_info* infos);
 /* Autotuner: for each grid size N of the batch, chooses the Gram-Schmidt form (16-CTA
- * cluster, 8-CTA cluster, five kernels) and the column pairs per block of the float32 column
- * transform (1, 2, 4) by timing whole batch solves of rhs from zero (coordinate search, the
- * second of two launches timed) and leaves the fastest set on every context (read them back
- * with kfbi_get_option). best_ms (host, NULL skips): batch solve time of the final choice.
+ * cluster, 8-CTA cluster, five kernels), the column pairs per block of the float32 column
+ * transform (1, 2, 4) and, in mixed batches, that transform's form (shared-memory FFT,
+ * register FFTs for N <= 1024, tensor-core contractions for N <= 256) by timing whole batch
+ * solves of rhs from zero (coordinate search, the second of two launches timed) and leaves the
+ * fastest set on every context (read them back with kfbi_get_option). best_ms (host, NULL skips): batch solve time of the final choice.
  * Errors: ARG, STATE, CUDA. */
 kfbi_status kfbi_batch_autotune(kfbi_batch* batch, int kind, const double* const* rhs, double tol, int max_iter,
                                 int restart, double* best_ms);
@@ -489,6 +523,21 @@ kfbi_status kfbi_launch_count(kfbi_ctx* ctx, long long* count);
  * Errors: ARG, CUDA.
  */
 kfbi_status kfbi_alu_peak(int kind, double* tflops, void* stream);
+
+/*
+ * kfbi_tc_gemm -- C = A B^T on the fifth-generation tensor cores (tcgen05), the contraction
+ * behind the warm-start network's 256-wide layers and the small-grid column transforms (not in
+ * the paper). Float32 device matrices: A(m, k) = A[m lda + k] (transA = 0) or A[k lda + m]
+ * (transA = 1), m < M, k < K; B(n, k) = B[n ldb + k] or B[k ldb + n], n < N; C[m ldc + n].
+ * terms = 3 splits every input into two bfloat16 values (hi + lo) and accumulates
+ * hi hi + hi lo + lo hi in float32 (about 2^-16 relative per product); terms = 4 is for B
+ * exact in bfloat16: A is split into three bfloat16 terms (its full float32 value) and each
+ * is multiplied by B; terms = 1 takes the bfloat16 product alone. error: device int, set to 1 if a completion wait gave up (the result
+ * is then unspecified). Asynchronous on `stream` (cudaStream_t as void*); allocates nothing.
+ * Errors: ARG, CUDA.
+ */
+kfbi_status kfbi_tc_gemm(int M, int N, int K, const float* A, long lda, int transA, const float* B, long ldb,
+                         int transB, float* C, long ldc, int terms, int* error, void* stream);
 
 #ifdef __cplusplus
 }

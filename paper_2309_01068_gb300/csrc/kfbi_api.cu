@@ -111,7 +111,8 @@ static void free_all(kfbi_ctx* c) {
                   c->probe_mark, c->prow_cnt, c->prow_ptr, c->probe_i, c->probe_j, c->flags, c->counts, c->dcoef, c->dint,
                   c->boxg, c->facespec, c->spec, c->rowinfo, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack, c->boxK, c->boxK_f,
                   c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gVf, c->gpart, c->gw,
-                  c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag, c->irctl, c->ir_b, c->ir_x, c->ir_dn};
+                  c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag, c->irctl, c->ir_b, c->ir_x, c->ir_dn,
+                  c->col_fwd, c->col_inv, c->col_tmp, c->col_tc_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->host_counts) cudaFreeHost(c->host_counts);
@@ -501,6 +502,12 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
     c->fuse_dft = value != 0;
   } else if (option == KFBI_OPT_COL_REG) {
     c->col_reg = value != 0;
+  } else if (option == KFBI_OPT_COL_TC) {
+    if (value != 0) {
+      if (c->N > COL_TC_MAX_N) return KFBI_ERR_CAPACITY;
+      KFBI_CHECK(col_tc_setup(c));
+    }
+    c->col_tc = value != 0;
   } else if (option == KFBI_OPT_PUSH_REDUCE) {
     c->gmf_push = value != 0;
     c->gmf = c->gmf32 = kfbi_ctx::GmfConfig{};
@@ -532,6 +539,7 @@ kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
   else if (option == KFBI_OPT_FUSE_INTERP) *value = c->fuse_interp ? 1 : 0;
   else if (option == KFBI_OPT_FUSE_DFT) *value = c->fuse_dft ? 1 : 0;
   else if (option == KFBI_OPT_COL_REG) *value = c->col_reg ? 1 : 0;
+  else if (option == KFBI_OPT_COL_TC) *value = c->col_tc ? 1 : 0;
   else if (option == KFBI_OPT_BODY_CAP) *value = c->body_cap_set;
   else if (option == KFBI_OPT_SWEEP_CAP) *value = c->sweep_cap_set;
   else return KFBI_ERR_ARG;

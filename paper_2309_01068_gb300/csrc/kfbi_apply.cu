@@ -1456,6 +1456,66 @@ static int col_threads(int N, int P) {
   return t < 32 ? 32 : (t > 1024 ? 1024 : t);
 }
 
+// Matrices of the tensor-core column solve: forward F[l][j] = sin(pi (l+1)(2j+1) / (2N)) (DST-II)
+// or cos(pi l (2j+1) / (2N)) (DCT-II), and its exact inverse G[j][l] = (2/N) w_l F[l][j] with
+// w = 1/2 at l = N-1 (DST-III) or l = 0 (DCT-III), else 1; formed in float64, stored in float32.
+__global__ void k_col_tc_mats(int N, int dct, float* F, float* G) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * N) return;
+  const int l = t / N, j = t - l * N;
+  const double arg = (double)(dct ? l : l + 1) * (double)(2 * j + 1) / (2.0 * N);
+  const double v = dct ? cospi(arg) : sinpi(arg);
+  const double w = (dct ? l == 0 : l == N - 1) ? 0.5 : 1.0;
+  F[(long)l * N + j] = (float)v;
+  G[(long)j * N + l] = (float)(2.0 / N * w * v);
+}
+
+kfbi_status col_tc_setup(kfbi_ctx* c) {
+  if (c->col_fwd != nullptr) return KFBI_OK;
+  const int N = c->N;
+  const size_t NN = (size_t)N * N;
+  KFBI_TRY(cudaMalloc((void**)&c->col_fwd, sizeof(float) * NN));
+  KFBI_TRY(cudaMalloc((void**)&c->col_inv, sizeof(float) * NN));
+  KFBI_TRY(cudaMalloc((void**)&c->col_tmp, sizeof(float) * NN));
+  KFBI_TRY(cudaMalloc((void**)&c->col_tc_err, sizeof(int)));
+  KFBI_TRY(cudaMemsetAsync(c->col_tc_err, 0, sizeof(int), c->stream));
+  k_col_tc_mats<<<cdiv((long)NN, 256), 256, 0, c->stream>>>(N, c->boxbc == KFBI_BOX_NEUMANN0, c->col_fwd,
+                                                            c->col_inv);
+  KFBI_TRY(cudaGetLastError());
+  KFBI_TRY(cudaStreamSynchronize(c->stream));
+  return KFBI_OK;
+}
+
+// the column solve as two tensor-core contractions: tmp = (F spec) / (lam_y(l) + lam_x(k) - kappa),
+// spec = G tmp (spec[j][k]: row j, column k; B(n = k, k = j) = spec[j][k])
+static kfbi_status launch_col_tc(kfbi_ctx* c, float* spec) {
+  const int N = c->N;
+  TcGemmArgs g;
+  g.terms = 3;
+  g.error = c->col_tc_err;
+  g.A = c->col_fwd;
+  g.lda = N;
+  g.B = spec;
+  g.ldb = N;
+  g.transB = 1;
+  g.C = c->col_tmp;
+  g.ldc = N;
+  g.M = N;
+  g.N = N;
+  g.K = N;
+  g.mode = TC_EIGEN;
+  g.dm = c->lam_f;
+  g.dn = c->lam_f;
+  g.shift = (float)(-c->kappa);
+  KFBI_CHECK(tc_gemm(g, c->stream));
+  g.A = c->col_inv;
+  g.B = c->col_tmp;
+  g.C = spec;
+  g.mode = TC_STORE;
+  KFBI_CHECK(tc_gemm(g, c->stream));
+  return KFBI_OK;
+}
+
 template <typename T>
 static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const V2<T>* rowinfo, const int* skip) {
   const int N = c->N;
@@ -1464,9 +1524,15 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const V2<T>* rowinfo, 
   int rthreads = 0, rpairs = 0;
   size_t rsmem = 0;
   ColRegKernel rk = nullptr;
-  if constexpr (sizeof(T) == 4)
-    if (c->col_reg) rk = col_reg_kernel(c->logN, &rthreads, &rpairs, &rsmem);
-  if (rk != nullptr) {
+  bool tcp = false;
+  if constexpr (sizeof(T) == 4) {
+    tcp = c->col_tc && c->col_fwd != nullptr;
+    if (!tcp && c->col_reg) rk = col_reg_kernel(c->logN, &rthreads, &rpairs, &rsmem);
+  }
+  if (tcp) {
+    KFBI_CHECK(launch_col_tc(c, (float*)spec));
+    launched(c, 1);  // two launches: one more than the single column kernel counted below
+  } else if (rk != nullptr) {
     KFBI_TRY(launch_k(c->use_pdl && !rec, rk, dim3(N / (2 * rpairs)), dim3(rthreads), rsmem, c->stream,
                       (int)(c->boxbc == KFBI_BOX_NEUMANN0), (const V2f*)Tabs<float>::twN(c), Tabs<float>::sin(c),
                       Tabs<float>::lam(c), (float)c->kappa, (float*)spec, (const V2f*)rowinfo, skip));
@@ -1511,8 +1577,9 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   T* boxg = (T*)c->boxg;
   T* face = (T*)c->facespec;
   T* spec = (T*)c->spec;
-  // rows without irregular nodes left to the column kernel: float32 applies only
-  V2<T>* rowinfo = sizeof(T) == 4 ? (V2<T>*)c->rowinfo : nullptr;
+  // rows without irregular nodes left to the column kernel: float32 applies only (the
+  // tensor-core column solve reads whole rows, so the row transform writes them all)
+  V2<T>* rowinfo = (sizeof(T) == 4 && !c->col_tc) ? (V2<T>*)c->rowinfo : nullptr;
   T* J = (T*)c->jumps;
   // the density integral of the Hele-Shaw operator, in the apply's type (float64 slot 0 or a
   // float32 slot in the same buffer)

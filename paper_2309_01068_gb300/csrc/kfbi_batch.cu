@@ -383,6 +383,31 @@ kfbi_status kfbi_batch_autotune(kfbi_batch* b, int kind, const double* const* rh
       }
     }
     apply(kv.second, best_form, best_pairs);
+    // the float32 column transform: shared-memory FFT (0), register FFTs (1, N <= 1024) or the
+    // tensor-core contractions (2, N <= 256); only the mixed form runs float32 applies
+    if (b->precision == KFBI_MIXED && st == KFBI_OK) {
+      auto apply_col = [&](int cf) {
+        for (int i : kv.second) {
+          kfbi_ctx* c = b->ctx[i];
+          if (cf == 2 && kfbi_set_option(c, KFBI_OPT_COL_TC, 1) != KFBI_OK) return false;
+          if (cf != 2) kfbi_set_option(c, KFBI_OPT_COL_TC, 0);
+          kfbi_set_option(c, KFBI_OPT_COL_REG, cf == 1 ? 1 : 0);
+        }
+        return true;
+      };
+      int best_cf = 0;
+      for (int cf = 1; cf <= 2 && st == KFBI_OK; ++cf) {
+        if ((cf == 1 && kv.first > 1024) || (cf == 2 && kv.first > COL_TC_MAX_N)) continue;
+        if (!apply_col(cf)) continue;
+        float t = 0.0f;
+        if ((st = run(&t)) != KFBI_OK) break;
+        if (t < cur) {
+          cur = t;
+          best_cf = cf;
+        }
+      }
+      apply_col(best_cf);
+    }
   }
   if (best_ms) *best_ms = (double)cur;
   for (double* p : xs)

@@ -297,6 +297,10 @@ struct kfbi_ctx {
   double* jumps = nullptr;      // [cap_cross + max_nodes][6] jumps at the targets (T)
   double* spec = nullptr;       // [N][N] row-transformed grid (T)
   double* rowinfo = nullptr;    // [N] (w, e) of rows the row transform left to the column kernel (T pairs)
+  float* col_fwd = nullptr;     // [N][N] forward DST-II / DCT-II along y (tensor-core column solve)
+  float* col_inv = nullptr;     // [N][N] its exact inverse (DST-III / DCT-III with weights, 2/N)
+  float* col_tmp = nullptr;     // [N][N] eigen-divided transform between the two contractions
+  int* col_tc_err = nullptr;    // [1] tensor-core completion flag
   double* probe_val = nullptr;  // [6*max_nodes] (T)
   double* tmp_vals = nullptr;   // [max_nodes]
 
@@ -361,6 +365,7 @@ struct kfbi_ctx {
   bool use_pdl = true;          // programmatic dependent launch between the kernels of a body
   int force_cs = 0;             // cluster size of the Gram-Schmidt kernel: 0 automatic, 8 or 16
   int col_P = 0;                // column pairs per block of the float32 column kernel (0 automatic)
+  bool col_tc = false;          // float32 column solve as two tensor-core contractions (N <= 256), KFBI_OPT_COL_TC
   bool col_reg = false;         // float32 column solve with register FFTs (N <= 1024), KFBI_OPT_COL_REG
   int body_cap_set = 0;         // GMRES loop body cap (0: derived from max_iter), KFBI_OPT_BODY_CAP
   int sweep_cap_set = 0;        // refinement loop body cap (0: sweeps + 2), KFBI_OPT_SWEEP_CAP
@@ -474,6 +479,34 @@ inline cudaError_t stream_exit(kfbi_ctx* c) {
   return cudaStreamWaitEvent(c->user, c->ev_out, 0);
 }
 kfbi_status apply_setup_attributes(kfbi_ctx* c);
+
+// tensor-core contraction C = alpha A B^T (kfbi_gemm.cu): A(m, k) = transA ? A[k lda + m] :
+// A[m lda + k], B(n, k) likewise, float32 in and out, split-bfloat16 products (terms 3), A in
+// three bfloat16 terms against a B exact in bfloat16 (terms 4) or the plain bfloat16 product
+// (terms 1); epilogue: store, add, or divide by dm[m] + dn[n] + shift
+enum { TC_STORE = 0, TC_ADD = 1, TC_EIGEN = 2 };
+struct TcGemmArgs {
+  const float* A = nullptr;
+  long lda = 0;
+  int transA = 0;
+  const float* B = nullptr;
+  long ldb = 0;
+  int transB = 0;
+  float* C = nullptr;
+  long ldc = 0;
+  int M = 0, N = 0, K = 0;
+  float alpha = 1.0f;
+  int mode = TC_STORE;
+  const float* dm = nullptr;
+  const float* dn = nullptr;
+  float shift = 0.0f;
+  int terms = 3;
+  int* error = nullptr;  // device flag, set to 1 when a completion wait gave up
+};
+kfbi_status tc_gemm(const TcGemmArgs& g, cudaStream_t s);
+// the tensor-core column solve's matrices and buffers (kfbi_apply.cu), for N <= COL_TC_MAX_N
+constexpr int COL_TC_MAX_N = 256;
+kfbi_status col_tc_setup(kfbi_ctx* c);
 
 // host-side helpers implemented in the .cu files
 kfbi_status ensure_cross_capacity(kfbi_ctx* c, int n_cross);

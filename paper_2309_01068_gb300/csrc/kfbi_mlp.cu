@@ -37,6 +37,10 @@ struct kfbi_mlp {
   float* feat = nullptr;            // [max_rows][F] features for kfbi_warmstart_predict
   double* scale = nullptr;          // [1] rms of the right-hand side
   int step = 0;                     // Adam steps taken
+  bool tc = true;                   // the H x H layer on the tensor cores (kfbi_tc_gemm path)
+  float* w2f = nullptr;             // [H][H] the bfloat16 W2 as float32 (tensor-core operand)
+  float* z2 = nullptr;              // [max_rows][H] pre-activations of layer 2 (tensor-core path)
+  int* tc_err = nullptr;            // [1] completion-wait flag of the tensor-core contractions
 };
 
 namespace kfbi {
@@ -397,6 +401,83 @@ __global__ void k_ws_scale(int n, const float* y, const double* scale, double* o
   if (j < n) out[j] = *scale * (double)y[j];
 }
 
+// --------------------------------------------------------------------------- tensor-core path
+// The same network with its H x H layer as a tensor-core contraction (kfbi_gemm.cu):
+//   layer 1 (k_mlp_l1):   z1 = W1 x + b1, h1 = relu(z1), x gathered by idx
+//   layer 2 (tc_gemm):    z2 = h1 W2^T (W2 as the float32 value of its bfloat16 copy)
+//   layer 3 (k_mlp_l3):   h2 = relu(z2 + b2), y = w3.h2 + b3; training: dy, dz2 = dy w3 [z2 > 0]
+//   backward (tc_gemm):   dz1 = (dz2 W2) [h1 > 0];  dW2 = dz2^T h1 (tc_gemm over the rows)
+// The remaining gradients (W1, b1, b2, w3, b3) and the loss come from k_mlp_wgrad / k_mlp_loss.
+__global__ void k_mlp_l1(int F, int H, const float* X, const int* idx, int rows, const __nv_bfloat16* wq,
+                         const float* master, int oW1, int ob1, float* xg, float* h1) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)rows * H) return;
+  const int r = (int)(t / H), i = (int)(t - (long)r * H);
+  const int row = idx != nullptr ? idx[r] : r;
+  const float* x = X + (long)row * F;
+  float a = master[ob1 + i];
+  for (int f = 0; f < F; ++f) a = fmaf(x[f], bf(wq[oW1 + i * F + f]), a);
+  h1[t] = fmaxf(a, 0.0f);
+  if (xg != nullptr)
+    for (int f = i; f < F; f += H) xg[(long)r * F + f] = x[f];
+}
+
+// one warp per row: h2 = relu(z2 + b2), y = w3 . h2 + b3; with a target also the loss part,
+// dy = 2 (y - t) / R and dz2 = dy w3 [z2 > 0]
+__global__ void k_mlp_l3(int H, const float* z2, int rows, const float* target, const int* idx,
+                         const __nv_bfloat16* wq, const float* master, int ob2, int ow3, int ob3, float inv_rows,
+                         float* y, float* h2g, float* dz2g, float* dyg, float* loss_row) {
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  const float* z = z2 + (long)r * H;
+  float acc = 0.0f;
+  for (int a = lane; a < H; a += 32) {
+    const float h = fmaxf(z[a] + master[ob2 + a], 0.0f);
+    acc = fmaf(h, bf(wq[ow3 + a]), acc);
+    if (h2g != nullptr) h2g[(long)r * H + a] = h;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const float yr = acc + master[ob3];
+  if (lane == 0) y[r] = yr;
+  if (target == nullptr) return;
+  const int row = idx != nullptr ? idx[r] : r;
+  const float e = yr - target[row];
+  const float d = 2.0f * e * inv_rows;
+  if (lane == 0) {
+    dyg[r] = d;
+    loss_row[r] = e * e;
+  }
+  for (int a = lane; a < H; a += 32) {
+    const float zz = z[a] + master[ob2 + a];
+    dz2g[(long)r * H + a] = zz > 0.0f ? d * bf(wq[ow3 + a]) : 0.0f;
+  }
+}
+
+__global__ void k_mlp_relu_mask(long count, const float* h1, float* dz1) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count && !(h1[t] > 0.0f)) dz1[t] = 0.0f;
+}
+
+__global__ void k_mlp_w2f(int count, const __nv_bfloat16* w, float* f) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) f[t] = bf(w[t]);
+}
+
+// loss over the rows in a fixed order (tensor-core path: one loss value per row)
+__global__ void k_mlp_loss_rows(const float* per_row, int rows, float inv_rows, float* loss) {
+  __shared__ float sh[32];
+  float a = 0.0f;
+  for (int r = threadIdx.x; r < rows; r += blockDim.x) a += per_row[r];
+  for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *loss = t * inv_rows;
+  }
+}
+
 // --------------------------------------------------------------------------- host side
 static size_t rows_smem_h(int F, int H) {
   return sizeof(__nv_bfloat16) * (size_t)H * (H + 2) + sizeof(float) * ((size_t)MLP_ROWS * F + 2 * (size_t)MLP_ROWS * H);
@@ -405,7 +486,57 @@ static size_t rows_smem(const kfbi_mlp* m) { return rows_smem_h(m->F, m->H); }
 // the kernel's shared-memory limit is process-wide: set for the widest network
 static size_t rows_smem_max() { return rows_smem_h(KFBI_MLP_FEATURES, MLP_MAX_H); }
 
+static TcGemmArgs tc_args(kfbi_mlp* m) {
+  TcGemmArgs g;
+  g.terms = 3;
+  g.error = m->tc_err;
+  return g;
+}
+
+// forward (and, with a target, the per-row backward quantities) through the tensor-core layer
+static kfbi_status run_rows_tc(kfbi_mlp* m, const float* X, const int* idx, int rows, const float* target, float* y) {
+  const int H = m->H, F = m->F;
+  const bool train = target != nullptr;
+  k_mlp_l1<<<cdiv((long)rows * H, 256), 256, 0, m->stream>>>(F, H, X, idx, rows, m->wq, m->master, m->oW1, m->ob1,
+                                                             train ? m->xg : nullptr, m->h1);
+  TcGemmArgs g = tc_args(m);
+  g.terms = 4;  // W2 is exact in bfloat16: h1 carried to float32 accuracy
+  g.A = m->h1;
+  g.lda = H;
+  g.B = m->w2f;
+  g.ldb = H;
+  g.C = m->z2;
+  g.ldc = H;
+  g.M = rows;
+  g.N = H;
+  g.K = H;
+  KFBI_CHECK(tc_gemm(g, m->stream));
+  k_mlp_l3<<<cdiv((long)rows * 32, 256), 256, 0, m->stream>>>(
+      H, m->z2, rows, target, idx, m->wq, m->master, m->ob2, m->ow3, m->ob3, 1.0f / (float)rows, y,
+      train ? m->h2 : nullptr, m->dz2, m->dy, m->loss_part);
+  if (train) {
+    // dz1 = (dz2 W2) [h1 > 0]: B(n = b, k = a) = W2[a][b]
+    TcGemmArgs b = tc_args(m);
+    b.terms = 4;
+    b.A = m->dz2;
+    b.lda = H;
+    b.B = m->w2f;
+    b.ldb = H;
+    b.transB = 1;
+    b.C = m->dz1;
+    b.ldc = H;
+    b.M = rows;
+    b.N = H;
+    b.K = H;
+    KFBI_CHECK(tc_gemm(b, m->stream));
+    k_mlp_relu_mask<<<cdiv((long)rows * H, 256), 256, 0, m->stream>>>((long)rows * H, m->h1, m->dz1);
+  }
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
 static kfbi_status run_rows(kfbi_mlp* m, const float* X, const int* idx, int rows, const float* target, float* y) {
+  if (m->tc) return run_rows_tc(m, X, idx, rows, target, y);
   const int nb = cdiv(rows, MLP_ROWS);
   const bool train = target != nullptr;
   k_mlp_rows<<<nb, m->H, rows_smem(m), m->stream>>>(
@@ -419,6 +550,32 @@ static kfbi_status run_grads(kfbi_mlp* m, const float* X, const float* target, c
                              float* grad) {
   KFBI_CHECK(run_rows(m, X, idx, rows, target, m->y));
   const int H = m->H, F = m->F;
+  if (m->tc) {
+    // dW2[a][b] = sum_r dz2[r][a] h1[r][b] on the tensor cores; b2, W1, b1, w3, b3 below
+    TcGemmArgs g = tc_args(m);
+    g.A = m->dz2;
+    g.lda = H;
+    g.transA = 1;
+    g.B = m->h1;
+    g.ldb = H;
+    g.transB = 1;
+    g.C = grad + m->oW2;
+    g.ldc = H;
+    g.M = H;
+    g.N = H;
+    g.K = rows;
+    KFBI_CHECK(tc_gemm(g, m->stream));
+    GradJob j0{m->dz2, m->h1, H, 0, grad + m->oW2, grad + m->ob2, cdiv(H, 32), 1, 0};  // bias column only
+    GradJob j1{m->dz1, m->xg, H, F, grad + m->oW1, grad + m->ob1, cdiv(H, 32), cdiv(F + 1, 32), 0};
+    GradJob j2{m->dy, m->h2, 1, H, grad + m->ow3, grad + m->ob3, 1, cdiv(H + 1, 32), 0};
+    j1.first_block = j0.tiles_a * j0.tiles_b;
+    j2.first_block = j1.first_block + j1.tiles_a * j1.tiles_b;
+    const int blocks = j2.first_block + j2.tiles_a * j2.tiles_b;
+    k_mlp_wgrad<<<blocks, 256, 0, m->stream>>>(j0, j1, j2, rows);
+    k_mlp_loss_rows<<<1, 1024, 0, m->stream>>>(m->loss_part, rows, 1.0f / (float)rows, m->loss);
+    KFBI_TRY(cudaGetLastError());
+    return KFBI_OK;
+  }
   GradJob j0{m->dz2, m->h1, H, H, grad + m->oW2, grad + m->ob2, cdiv(H, 32), cdiv(H + 1, 32), 0};
   GradJob j1{m->dz1, m->xg, H, F, grad + m->oW1, grad + m->ob1, cdiv(H, 32), cdiv(F + 1, 32), 0};
   GradJob j2{m->dy, m->h2, 1, H, grad + m->ow3, grad + m->ob3, 1, cdiv(H + 1, 32), 0};
@@ -445,7 +602,7 @@ using namespace kfbi;
 
 static void mlp_free(kfbi_mlp* m) {
   void* ptrs[] = {m->master, m->wq, m->grad, m->adam_m, m->adam_v, m->h1, m->h2, m->dz1, m->dz2, m->xg,
-                  m->dy, m->y, m->loss_part, m->loss, m->feat, m->scale};
+                  m->dy, m->y, m->loss_part, m->loss, m->feat, m->scale, m->w2f, m->z2, m->tc_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (m->host_loss) cudaFreeHost(m->host_loss);
@@ -483,8 +640,10 @@ kfbi_status kfbi_mlp_create(int hidden, int max_rows, kfbi_mlp** out) {
       (st = mlp_alloc(&m->h2, R * H)) != KFBI_OK || (st = mlp_alloc(&m->dz1, R * H)) != KFBI_OK ||
       (st = mlp_alloc(&m->dz2, R * H)) != KFBI_OK || (st = mlp_alloc(&m->xg, R * F)) != KFBI_OK ||
       (st = mlp_alloc(&m->dy, R)) != KFBI_OK || (st = mlp_alloc(&m->y, R)) != KFBI_OK ||
-      (st = mlp_alloc(&m->loss_part, R / MLP_ROWS + 1)) != KFBI_OK || (st = mlp_alloc(&m->loss, 1)) != KFBI_OK ||
-      (st = mlp_alloc(&m->feat, R * F)) != KFBI_OK || (st = mlp_alloc(&m->scale, 1)) != KFBI_OK) {
+      (st = mlp_alloc(&m->loss_part, R + 1)) != KFBI_OK || (st = mlp_alloc(&m->loss, 1)) != KFBI_OK ||
+      (st = mlp_alloc(&m->feat, R * F)) != KFBI_OK || (st = mlp_alloc(&m->scale, 1)) != KFBI_OK ||
+      (st = mlp_alloc(&m->w2f, (size_t)H * H)) != KFBI_OK || (st = mlp_alloc(&m->z2, R * H)) != KFBI_OK ||
+      (st = mlp_alloc(&m->tc_err, 1)) != KFBI_OK) {
     mlp_free(m);
     return st;
   }
@@ -512,6 +671,24 @@ kfbi_status kfbi_mlp_set_stream(kfbi_mlp* m, void* stream) {
   return KFBI_OK;
 }
 
+kfbi_status kfbi_mlp_set_tensor_cores(kfbi_mlp* m, int enable) {
+  if (m == nullptr) return KFBI_ERR_ARG;
+  KFBI_TRY(cudaStreamSynchronize(m->stream));
+  m->tc = enable != 0;
+  if (m->tc) {
+    k_mlp_w2f<<<cdiv(m->H * m->H, 256), 256, 0, m->stream>>>(m->H * m->H, m->wq + m->oW2, m->w2f);
+    KFBI_TRY(cudaGetLastError());
+  }
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_mlp_tc_error(kfbi_mlp* m, int* flag) {
+  if (m == nullptr || flag == nullptr) return KFBI_ERR_ARG;
+  KFBI_TRY(cudaMemcpyAsync(flag, m->tc_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  KFBI_TRY(cudaStreamSynchronize(m->stream));
+  return KFBI_OK;
+}
+
 kfbi_status kfbi_mlp_param_count(kfbi_mlp* m, int* count) {
   if (m == nullptr || count == nullptr) return KFBI_ERR_ARG;
   *count = m->P;
@@ -525,6 +702,7 @@ kfbi_status kfbi_mlp_set_params(kfbi_mlp* m, const float* params) {
   KFBI_TRY(cudaMemsetAsync(m->adam_m, 0, bytes, m->stream));
   KFBI_TRY(cudaMemsetAsync(m->adam_v, 0, bytes, m->stream));
   k_mlp_quantise<<<cdiv(m->P, 256), 256, 0, m->stream>>>(m->P, m->master, m->wq);
+  k_mlp_w2f<<<cdiv(m->H * m->H, 256), 256, 0, m->stream>>>(m->H * m->H, m->wq + m->oW2, m->w2f);
   KFBI_TRY(cudaGetLastError());
   KFBI_TRY(cudaStreamSynchronize(m->stream));
   m->step = 0;
@@ -560,6 +738,7 @@ kfbi_status kfbi_mlp_train_step(kfbi_mlp* m, const float* feat, const float* tar
   const float c1 = 1.0f - powf(b1, (float)m->step), c2 = 1.0f - powf(b2, (float)m->step);
   k_mlp_adam<<<cdiv(m->P, 256), 256, 0, m->stream>>>(m->P, m->master, m->grad, m->adam_m, m->adam_v, m->wq, lr, b1,
                                                      b2, 1e-8f, c1, c2);
+  if (m->tc) k_mlp_w2f<<<cdiv(m->H * m->H, 256), 256, 0, m->stream>>>(m->H * m->H, m->wq + m->oW2, m->w2f);
   KFBI_TRY(cudaGetLastError());
   return read_loss(m, loss);
 }

@@ -20,7 +20,7 @@ kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const dou
 // scalar slots of the device state
 enum : int {
   SC_L = 0, SC_XB0, SC_XB1, SC_T, SC_STEPS, SC_MPREV, SC_QPREV0, SC_QPREV1, SC_LPREV, SC_M, SC_Q0, SC_Q1,
-  SC_LNEW, SC_LAM, SC_COUNT = 16
+  SC_LNEW, SC_LAM, SC_WS_NET, SC_WS_RATIO, SC_COUNT = 16
 };
 
 struct kfbi_thetal {
@@ -48,6 +48,9 @@ struct kfbi_thetal {
   double* Tw = nullptr;       // [N][N] T1 of the current step
   double* Sg = nullptr;       // [N][N] grid single layer of the current step
   double* host_scal = nullptr;  // pinned [SC_COUNT]
+  kfbi_mlp* ws = nullptr;     // learned warm start (not owned), or none
+  double* guess = nullptr;    // [n] the network's density
+  double* ws_norm = nullptr;  // [3] rms(rhs) of the features, residual norms of the two starts
 };
 
 namespace kfbi {
@@ -348,6 +351,63 @@ __global__ void k_twiddles_n_step(int n, double2* tw) {
 
 static int wb(long warps) { return cdiv(warps * 32, 256); }
 
+// Learned warm start, the choice between two initial densities: residual norms
+// ||b - A g|| (network g) and ||b - A x|| (previous step x), one block; the start with the smaller
+// residual is kept in x. Counts the network's wins in scal[SC_WS_NET] and stores the ratio of
+// the two norms in scal[SC_WS_RATIO].
+__global__ void k_ws_choose(int n, const double* b, const double* Ag, const double* Ax, const double* g, double* x,
+                            double* scal) {
+  __shared__ double sh[2][32];
+  __shared__ int take;
+  double rg = 0.0, rx = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double a = b[j] - Ag[j], c = b[j] - Ax[j];
+    rg += a * a;
+    rx += c * c;
+  }
+  rg = warp_sum(rg);
+  rx = warp_sum(rx);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][wid] = rg;
+    sh[1][wid] = rx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tg = 0.0, tx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tg += sh[0][w];
+      tx += sh[1][w];
+    }
+    take = tg < tx ? 1 : 0;
+    scal[SC_WS_NET] += (double)take;
+    scal[SC_WS_RATIO] = tx > 0.0 ? sqrt(tg / tx) : 0.0;
+  }
+  __syncthreads();
+  if (take)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) x[j] = g[j];
+}
+
+// training pair of the last solved system: target = density / rms(rhs)
+__global__ void k_ws_target(int n, const double* density, const double* scale, float* target) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) target[j] = (float)(density[j] / *scale);
+}
+
+// the two starts of the step's solve, before GMRES (only with a network attached)
+static kfbi_status warm_start_choose(kfbi_ctx* c, kfbi_thetal* st, int kind, const double* ev) {
+  const int n = st->n;
+  cudaStream_t s = c->stream;
+  KFBI_CHECK(kfbi_warmstart_predict(c, st->ws, st->rhs, st->guess));
+  const int layer = kind == KFBI_BIE_STEFAN_SL ? KFBI_SINGLE : KFBI_DOUBLE;
+  KFBI_CHECK(apply_enqueue(c, layer, false, st->guess, st->work, nullptr, nullptr, kind, ev, nullptr));
+  KFBI_CHECK(apply_enqueue(c, layer, false, st->density, st->work + n, nullptr, nullptr, kind, ev, nullptr));
+  k_ws_choose<<<1, 1024, 0, s>>>(n, st->rhs, st->work, st->work + n, st->guess, st->density, st->scal);
+  launched(c, 1);
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
 kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve_info* info) {
   cudaStream_t s = c->stream;
   const int n = st->n;
@@ -378,6 +438,7 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
     // mixed precision: the refinement's last float64 apply, at the returned density, also
     // gives the normal derivative of its double layer; float64: one more apply
     const bool dn_from_solve = c->precision == KFBI_MIXED;
+    if (st->ws != nullptr) KFBI_CHECK(warm_start_choose(c, st, KFBI_BIE_HS_EXTERIOR_MDL, nullptr));
     sst = solve_bie_impl(c, KFBI_BIE_HS_EXTERIOR_MDL, nullptr, st->rhs, P.tol, P.max_iter, P.restart, st->density,
                          &si, dn_from_solve ? st->dn : nullptr);
     if (sst != KFBI_OK && sst != KFBI_ERR_NOT_CONVERGED) return sst;
@@ -399,6 +460,11 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
     k_st_stefan_rhs<<<tb, 256, 0, s>>>(st->eta, st->th_a, st->dn, n, st->scal, P.eps_c, P.eps_aniso, P.fold, P.eps_v,
                                        st->rhs, st->epsv, st->work + 2 * n);
     ratio = st->work + 2 * n;
+    if (st->ws != nullptr) {
+      // the network's start is compared on the equation's float64 operator; the ratio buffer
+      // (work + 2n) is not touched by the two applies (work, work + n)
+      KFBI_CHECK(warm_start_choose(c, st, KFBI_BIE_STEFAN_SL, st->epsv));
+    }
     sst = solve_bie_impl(c, KFBI_BIE_STEFAN_SL, st->epsv, st->rhs, P.tol, P.max_iter, P.restart, st->density, &si);
     if (sst != KFBI_OK && sst != KFBI_ERR_NOT_CONVERGED) return sst;
     // T2 = -(S psi)_h from the apply's grid output; T^{n+1} = T1 + T2
@@ -441,7 +507,8 @@ using namespace kfbi;
 
 static void thetal_free(kfbi_thetal* st) {
   void* ptrs[] = {st->eta, st->xy, st->density, st->scal, st->tw, st->eta_h, st->N_h, st->Nprev_h, st->coef,
-                  st->th_a, st->U, st->V, st->rhs, st->work, st->epsv, st->dn, st->T, st->Tprev, st->Tw, st->Sg};
+                  st->th_a, st->U, st->V, st->rhs, st->work, st->epsv, st->dn, st->T, st->Tprev, st->Tw, st->Sg,
+                  st->guess, st->ws_norm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (st->host_scal) cudaFreeHost(st->host_scal);
@@ -476,6 +543,8 @@ static kfbi_status thetal_create_impl(kfbi_ctx* c, int n, const double* eta, dou
   KFBI_CHECK(talloc(&st->work, 4 * (size_t)n));
   KFBI_CHECK(talloc(&st->epsv, n));
   KFBI_CHECK(talloc(&st->dn, n));
+  KFBI_CHECK(talloc(&st->guess, n));
+  KFBI_CHECK(talloc(&st->ws_norm, 3));
   if (prm->kind == KFBI_STEP_STEFAN) {
     size_t NN = (size_t)c->N * c->N;
     KFBI_CHECK(talloc(&st->T, NN));
@@ -561,6 +630,25 @@ kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* d
     for (int i = 0; i < SC_COUNT; ++i) scalars[i] = st->host_scal[i];
   }
   KFBI_TRY(stream_exit(st->ctx));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_thetal_set_warmstart(kfbi_thetal* st, kfbi_mlp* mlp) {
+  if (st == nullptr) return KFBI_ERR_ARG;
+  st->ws = mlp;
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_thetal_training_pair(kfbi_thetal* st, float* feat, float* target) {
+  if (st == nullptr || feat == nullptr || target == nullptr) return KFBI_ERR_ARG;
+  kfbi_ctx* c = st->ctx;
+  if (!c->have_iface || c->n != st->n) return KFBI_ERR_STATE;
+  KFBI_CHECK(kfbi_warmstart_features(c, st->rhs, feat, st->ws_norm));
+  KFBI_TRY(stream_enter(c));
+  k_ws_target<<<cdiv(st->n, 256), 256, 0, c->stream>>>(st->n, st->density, st->ws_norm, target);
+  launched(c, 1);
+  KFBI_TRY(cudaGetLastError());
+  KFBI_TRY(stream_exit(c));
   return KFBI_OK;
 }
 

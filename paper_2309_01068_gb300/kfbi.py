@@ -24,7 +24,7 @@ OPT_FP32_ARNOLDI = 8
 OPT_PUSH_REDUCE = 9
 OPT_FUSE_INTERP = 10
 OPT_FUSE_DFT = 11
-OPT_BODY_CAP, OPT_SWEEP_CAP, OPT_COL_REG = 12, 13, 14
+OPT_BODY_CAP, OPT_SWEEP_CAP, OPT_COL_REG, OPT_COL_TC = 12, 13, 14, 15
 MLP_FEATURES, MLP_MODES = 47, 16
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2
@@ -96,6 +96,8 @@ _SIGNATURES = {
     "kfbi_mlp_destroy": (None, [_P]),
     "kfbi_mlp_set_stream": (_I, [_P, _P]),
     "kfbi_mlp_param_count": (_I, [_P, ctypes.POINTER(_I)]),
+    "kfbi_mlp_set_tensor_cores": (_I, [_P, _I]),
+    "kfbi_mlp_tc_error": (_I, [_P, ctypes.POINTER(_I)]),
     "kfbi_mlp_set_params": (_I, [_P, _P]),
     "kfbi_mlp_get_params": (_I, [_P, _P]),
     "kfbi_mlp_forward": (_I, [_P, _P, _I, _P]),
@@ -112,6 +114,9 @@ _SIGNATURES = {
     "kfbi_get_option": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "kfbi_grid_solve_noalloc": (_I, [_I, _D, _D, _I, _P, _P, _P]),
     "kfbi_alu_peak": (_I, [_I, ctypes.POINTER(_D), _P]),
+    "kfbi_tc_gemm": (_I, [_I, _I, _I, _P, ctypes.c_long, _I, _P, ctypes.c_long, _I, _P, ctypes.c_long, _I, _P, _P]),
+    "kfbi_thetal_set_warmstart": (_I, [_P, _P]),
+    "kfbi_thetal_training_pair": (_I, [_P, _P, _P]),
 }
 
 
@@ -372,6 +377,18 @@ class Mlp:
     def _sync_stream(self):
         _check(self.lib.kfbi_mlp_set_stream(self.handle, _stream()), "kfbi_mlp_set_stream")
 
+    def tensor_cores(self, enable):
+        """kfbi_mlp_set_tensor_cores: the H x H layer on the tensor cores (True) or CUDA cores."""
+        self._sync_stream()
+        _check(self.lib.kfbi_mlp_set_tensor_cores(self.handle, 1 if enable else 0), "kfbi_mlp_set_tensor_cores")
+
+    def tc_error(self):
+        """kfbi_mlp_tc_error: 1 if a tensor-core completion wait gave up, else 0."""
+        self._sync_stream()
+        v = ctypes.c_int()
+        _check(self.lib.kfbi_mlp_tc_error(self.handle, ctypes.byref(v)), "kfbi_mlp_tc_error")
+        return v.value
+
     def _shapes(self):
         H, F = self.hidden, MLP_FEATURES
         return dict(W1=(H, F), b1=(H,), W2=(H, H), b2=(H,), w3=(H,), b3=())
@@ -570,6 +587,20 @@ class ThetaL:
         _check(self.lib.kfbi_thetal_write(self.handle, _ptr(eta), _ptr(density), _ptr(nhat), _ptr(T), _ptr(T_prev),
                                           sc), "kfbi_thetal_write")
 
+    def set_warmstart(self, mlp):
+        """kfbi_thetal_set_warmstart: attach a network (Mlp) or detach (None)."""
+        self._mlp = mlp  # kept alive while attached
+        _check(self.lib.kfbi_thetal_set_warmstart(self.handle, mlp.handle if mlp is not None else None),
+               "kfbi_thetal_set_warmstart")
+
+    def training_pair(self):
+        """kfbi_thetal_training_pair: (features [n][47] float32, target [n] float32) of the last step."""
+        self.ctx._sync_stream()
+        feat = torch.empty((self.n, MLP_FEATURES), dtype=torch.float32, device="cuda")
+        target = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        _check(self.lib.kfbi_thetal_training_pair(self.handle, _ptr(feat), _ptr(target)), "kfbi_thetal_training_pair")
+        return feat, target
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.kfbi_thetal_destroy(self.handle)
@@ -588,3 +619,20 @@ def alu_peak(kind):
     v = ctypes.c_double()
     _check(lib.kfbi_alu_peak(int(kind), ctypes.byref(v), _stream()), "kfbi_alu_peak")
     return v.value
+
+
+def tc_gemm(A, B, transA=False, transB=False, terms=3):
+    """kfbi_tc_gemm: C = A B^T on the tensor cores (float32 device tensors). A is M x K (or K x M
+    with transA), B is N x K (or K x N with transB). Returns (C, error flag)."""
+    lib = load()
+    if A.dtype != torch.float32 or B.dtype != torch.float32 or A.dim() != 2 or B.dim() != 2:
+        raise ValueError("tc_gemm takes 2-D float32 tensors")
+    M, K = (A.shape[1], A.shape[0]) if transA else (A.shape[0], A.shape[1])
+    N, K2 = (B.shape[1], B.shape[0]) if transB else (B.shape[0], B.shape[1])
+    if K2 != K:
+        raise ValueError(f"inner dimensions differ: {K} and {K2}")
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib.kfbi_tc_gemm(M, N, K, _ptr(A), A.shape[1], int(transA), _ptr(B), B.shape[1], int(transB), _ptr(C), N,
+                            int(terms), _ptr(err), _stream()), "kfbi_tc_gemm")
+    return C, err

@@ -168,6 +168,10 @@ def test_trained_warm_start_lowers_initial_residual():
         assert relnorm(phi1.cpu().numpy(), phi0.cpu().numpy()) < 1e-8
         its0.append(i0["iterations"])
         its1.append(i1["iterations"])
-    assert np.median(r1) < 0.3, r1
     print(f"warm start: median initial residual {np.median(r1):.3e} (zero start 1), GMRES iterations "
           f"zero start {np.mean(its0):.2f}, network start {np.mean(its1):.2f}")
+    assert np.median(r1) < 0.3, r1
+    # what the start buys on these well-conditioned second-kind equations: measured 11.7 vs 10.8
+    # iterations (no gain; a start at 1e-2..1e-1 does not shorten the iteration); asserted as
+    # no worse than one and a half iterations per solve on average
+    assert np.mean(its1) <= np.mean(its0) + 1.5, (its0, its1)
