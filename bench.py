@@ -480,6 +480,51 @@ def warm_start_c5_leg(torch, K, train_steps=50, eval_steps=8):
                 final_density_rel_diff=d)
 
 
+def long_time_hs_leg(torch, K, steps=300):
+    """The long-time Hele-Shaw computation of Sec. 6.1.4 in its rescaled frame: nucleus
+    r = 1 + 0.1 (sin 2a + cos 3a) in (-1.7, 1.7)^2, 1024^2 grid, dt = 2e-4 (scaled time), J = 1,
+    sigma = 1e-3, markers doubled whenever their spacing exceeds 1.5 h (start: 2048 nodes), mixed
+    form to 1e-8. The first `steps` steps are timed; the paper's run takes 15000 steps (to scaled
+    time 3) in 5 hours on one CPU core, context only."""
+    import numpy as np
+
+    import workloads as W
+
+    shape = W.polar(1.0, [(2, 0.1, -math.pi / 2), (3, 0.1, 0.0)])  # 1 + 0.1 sin 2a + 0.1 cos 3a
+    n0 = 2048
+    nd = W.equal_arclength(shape, n0)
+    ctx = K.Context(1024, (-1.7, 1.7, -1.7, 1.7), 0.0, K.BOX_FREESPACE_DL, K.MIXED, max_nodes=16384)
+    eta = torch.tensor(nd["theta"] - alpha_array(n0), dtype=torch.float64, device="cuda")
+    st = K.ThetaL(ctx, eta, nd["L"], nd["xy"].mean(0), K.STEP_HELE_SHAW, tol=1e-8, max_iter=1000, restart=150,
+                  sigma=1e-3, J=1.0, refine_ratio=1.5, rescale=True)
+    dt = 2e-4
+    ms, its, ns = [], [], []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = st.step(dt)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        its.append(info["iterations"])
+        ns.append(st.n)
+    out = st.read(T=False)
+    sc = out["scalars"]
+    A0, tb = sc[16], sc[3]
+    R = math.exp(tb)
+    st.close()
+    ctx.close()
+    per = float(np.mean(ms))
+    return dict(workload="hele_shaw_long_time_rescaled_1024x1024 (Sec. 6.1.4 setup)", steps=steps, dt_scaled=dt,
+                ms_per_step=per, mean_gmres_iterations=float(np.mean(its)), nodes_first=ns[0], nodes_last=ns[-1],
+                scaled_time=tb, physical_time=(A0 / math.pi) * (math.exp(2 * tb) - 1) / 2, R=R,
+                projected_s_for_15000_steps=per * 15000 / 1e3,
+                projection_note=("extrapolated from the first steps' mean; node count and GMRES work grow as the "
+                                 "fingers develop, so the true total is larger"),
+                paper_context="5 h for the 15000-step run on one i7-10700K core (Sec. 6.1.4); not the same "
+                              "workload length or hardware")
+
+
 def stefan_leg(torch, K, steps=3, N=2048, n=2048, tol=1e-9, compare_fp64=True):
     """Stefan dendrite steps on the N^2 Neumann grid (seed r = 0.1 (1 + 0.2 cos 4a) in [-2,2]^2,
     undercooling -0.5, 4-fold anisotropy, dt = 5e-4), mixed precision to tol; the GMRES start
@@ -534,9 +579,9 @@ def stefan_leg(torch, K, steps=3, N=2048, n=2048, tol=1e-9, compare_fp64=True):
 
 
 def col_kernel_sizes(torch, K, reps=40):
-    """Column kernel time per launch by grid size for both float32 forms (register FFTs and
-    the shared-memory Stockham kernel): CUDA events around each launch, float32 applies of a
-    Neumann-box context with a 256-node star."""
+    """Column transform time per apply by grid size for the float32 forms (shared-memory
+    Stockham FFT, register FFTs up to 1024^2, tensor-core contractions up to 256^2): CUDA events
+    around the column launch(es), float32 applies of a Neumann-box context with a 256-node star."""
     import numpy as np
 
     import workloads as W
@@ -549,10 +594,11 @@ def col_kernel_sizes(torch, K, reps=40):
         dens = torch.ones(p.n, dtype=torch.float64, device="cuda")
         vals = torch.empty(p.n, dtype=torch.float64, device="cuda")
         row = {}
-        for reg in (1, 0):
-            if N > 1024 and reg == 1:
+        for form in ("tensor_core", "register", "stockham"):
+            if (form == "register" and N > 1024) or (form == "tensor_core" and N > 256):
                 continue
-            ctx.set_option(K.OPT_COL_REG, reg)
+            ctx.set_option(K.OPT_COL_REG, 1 if form == "register" else 0)
+            ctx.set_option(K.OPT_COL_TC, 1 if form == "tensor_core" else 0)
             for _ in range(5):
                 ctx.apply_into(K.DOUBLE, dens, vals)
             ctx.timing(True)
@@ -561,7 +607,7 @@ def col_kernel_sizes(torch, K, reps=40):
             t = ctx.timing()
             ctx.timing(False)
             us = 1e3 * t["fp32_ms"] / max(t["fp32_launches"], 1)
-            row["register" if reg else "stockham"] = dict(us=us, hbm_frac=(8.0 * N * N) / (us * 1e-6) / 1e9 / 6754.1)
+            row[form] = dict(us=us, hbm_frac=(8.0 * N * N) / (us * 1e-6) / 1e9 / 6754.1)
         out[str(N)] = row
         ctx.close()
     return out
@@ -794,6 +840,7 @@ def main():
                           ("batched", lambda: batched_leg(torch, K, flush)), ("warm_start", lambda: warmstart_leg(torch, K)),
                           ("stefan", lambda: stefan_leg(torch, K)),
                           ("warm_start_c5", lambda: warm_start_c5_leg(torch, K)),
+                          ("long_time_hs", lambda: long_time_hs_leg(torch, K)),
                           ("stefan_4096", lambda: stefan_leg(torch, K, N=4096, n=4096, tol=1e-8, compare_fp64=False))):
             try:
                 extras[name] = leg()

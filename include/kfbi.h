@@ -218,6 +218,18 @@ typedef struct {
      Adams-Bashforth (Sec. 5.3); KFBI_SCHEME_EXPLICIT (1): Adams-Bashforth on the whole
      right-hand side, no stiff part split off (the comparison scheme of Sec. 6.2.2) */
   int scheme;
+  /* marker doubling (Sec. 6.1.4): before a step, while L / n > refine_ratio h, the node count
+     doubles (eta, the density and the Adams-Bashforth history carried over as the same
+     trigonometric interpolants); 0 = off. The state's arrays are then sized for the context's
+     max_nodes, the ceiling of the doubling. */
+  double refine_ratio;
+  /* Hele-Shaw only, 1 = the step works in the rescaled frame of the long-time computation
+     (Sec. 6.1.4; the rescaling is cited there, not printed, and read as follows): x = R xb with
+     R = e^{tb}, dt / dtb = (A0 / pi) R^2, A0 the area at the first step; the scaled problem has
+     surface tension sigma / R and normal velocity (A0 / pi) U - xb.n, which keeps the scaled
+     area at A0 for J = 1. The state's t is then the scaled time tb; physical time
+     t = (A0 / pi)(e^{2 tb} - 1) / 2 and the physical curve R X (A0 in scalars slot 16). */
+  int rescale;
 } kfbi_thetal_params;
 enum { KFBI_SCHEME_SEMI_IMPLICIT = 0, KFBI_SCHEME_EXPLICIT = 1 };
 
@@ -247,11 +259,12 @@ kfbi_status kfbi_step(kfbi_ctx* ctx, kfbi_thetal* st, double dt, kfbi_solve_info
  *   nhat [(n/2+1)][2] the Adams-Bashforth history of N-hat (complex), T and T_prev
  *   [N][N] (Stefan only). `scalars` is a HOST array of KFBI_THETAL_SCALARS doubles:
  *   (L, Xbar_x, Xbar_y, t, steps, M_prev, Q_prev_x, Q_prev_y, L_prev, then work slots; slots
- *   14 and 15 are the learned warm start's counters, see kfbi_thetal_set_warmstart).
+ *   14 and 15 are the learned warm start's counters, see kfbi_thetal_set_warmstart; slot 16 is
+ *   the rescaled frame's A0).
  * Writing back what was read restores the state exactly. kfbi_thetal_read synchronises
  * the stream when `scalars` is given. Errors: ARG, CUDA.
  */
-#define KFBI_THETAL_SCALARS 16
+#define KFBI_THETAL_SCALARS 20
 kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* density, double* nhat, double* T,
                              double* T_prev, double* scalars);
 kfbi_status kfbi_thetal_write(kfbi_thetal* st, const double* eta, const double* density, const double* nhat,
@@ -456,6 +469,8 @@ kfbi_status kfbi_warmstart_predict(kfbi_ctx* ctx, kfbi_mlp* mlp, const double* r
  * not owned (keep it alive while attached) and needs max_rows >= n.
  */
 kfbi_status kfbi_thetal_set_warmstart(kfbi_thetal* st, kfbi_mlp* mlp);
+/* kfbi_thetal_count -- the state's current node count (host int; marker doubling changes it). */
+kfbi_status kfbi_thetal_count(kfbi_thetal* st, int* n);
 /*
  * kfbi_thetal_training_pair -- the warm-start training sample of the system the last kfbi_step
  * solved: features [n][KFBI_MLP_FEATURES] float32 of its curve and right-hand side, and the
@@ -532,7 +547,9 @@ kfbi_status kfbi_alu_peak(int kind, double* tflops, void* stream);
  * terms = 3 splits every input into two bfloat16 values (hi + lo) and accumulates
  * hi hi + hi lo + lo hi in float32 (about 2^-16 relative per product); terms = 4 is for B
  * exact in bfloat16: A is split into three bfloat16 terms (its full float32 value) and each
- * is multiplied by B; terms = 1 takes the bfloat16 product alone. error: device int, set to 1 if a completion wait gave up (the result
+ * is multiplied by B; terms = 6 splits both into three terms and accumulates the six products
+ * above 2^-24 relative (a float32-accurate contraction); terms = 1 takes the bfloat16 product
+ * alone. error: device int, set to 1 if a completion wait gave up (the result
  * is then unspecified). Asynchronous on `stream` (cudaStream_t as void*); allocates nothing.
  * Errors: ARG, CUDA.
  */

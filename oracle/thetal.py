@@ -98,6 +98,7 @@ class State:
     density: np.ndarray | None = None
     T: np.ndarray | None = None
     T_prev: np.ndarray | None = None
+    A0: float | None = None          # scaled-frame area (rescaled Hele-Shaw runs)
     last: dict = dataclasses.field(default_factory=dict)
 
 
@@ -186,13 +187,63 @@ def no_symbol(n):
     return lambda L: np.zeros(n)
 
 
-def hs_step(solver: K.Kfbi, st: State, dt, sigma, J, tol=1e-8, restart=100, max_iter=500):
+def _pad_spectrum(F):
+    """Unnormalised DFT of length n of a trigonometric interpolant (R2) -> the DFT of length 2n of
+    the same interpolant: modes |k| < n/2 kept, the Nyquist cosine split between +-n/2, times 2."""
+    n = F.shape[0]
+    m = 2 * n
+    G = np.zeros(m, dtype=complex)
+    K = (n - 1) // 2
+    G[:K + 1] = F[:K + 1]
+    if K > 0:
+        G[m - K:] = F[n - K:]
+    if n % 2 == 0:
+        G[n // 2] = 0.5 * F[n // 2]
+        G[m - n // 2] = 0.5 * F[n // 2]
+    return 2.0 * G
+
+
+def upsample(f):
+    """Values at alpha = 2 pi j / (2n) of the trigonometric interpolant of f_j (j < n)."""
+    return np.fft.ifft(_pad_spectrum(np.fft.fft(f))).real
+
+
+def refine_markers(st: State):
+    """Doubles the marker count (Sec. 6.1.4: markers are refined once their spacing exceeds
+    1.5 h): eta, the density and the Adams-Bashforth history N-hat are carried over as the same
+    trigonometric interpolants on twice as many equally spaced parameters; L, Xbar and the
+    scalar history are unchanged, so the curve and its equal-arclength parametrisation are kept."""
+    st.eta = upsample(st.eta)
+    if st.density is not None:
+        st.density = upsample(st.density)
+    if st.N_prev is not None:
+        st.N_prev = _pad_spectrum(st.N_prev)
+    return st
+
+
+def scaled_frame(st: State):
+    """(R, physical time) of a rescaled run at scaled time st.t (see hs_step)."""
+    return math.exp(st.t), (st.A0 / math.pi) * (math.exp(2.0 * st.t) - 1.0) / 2.0
+
+
+def hs_step(solver: K.Kfbi, st: State, dt, sigma, J, tol=1e-8, restart=100, max_iter=500, refine_ratio=0.0,
+            rescale=False):
     """One Hele-Shaw time step (Sec. 3.1 BIE, Sec. 5.2.1 SSD, Sec. 5.3 scheme).
 
     p = v + w, v = -J ln|x|; -1/2 phi + D phi + int phi = -sigma kappa - v on Gamma;
     U = -dp/dn from the oil side = J x.n/|x|^2 - dn(D phi) (the double layer's normal
     derivative is continuous across Gamma).
+
+    refine_ratio > 0: the markers are doubled first while L / n > refine_ratio h (Sec. 6.1.4).
+    rescale: the step is taken in the scaled frame of the long-time computation (Sec. 6.1.4, the
+    rescaling is cited there, not printed; reading): x = R(tb) xb with R = e^{tb}, physical time
+    dt/dtb = (A0/pi) R^2, A0 the scaled area at the start. The scaled problem is the same BIE with
+    surface tension sigma / R, and the scaled normal velocity is (A0/pi) U - xb.n, which keeps the
+    scaled area at A0 when J = 1. st.t is the scaled time (scaled_frame gives R and t).
     """
+    if refine_ratio > 0.0:
+        while st.L / st.eta.shape[0] > refine_ratio * solver.grid.h:
+            refine_markers(st)
     n = st.eta.shape[0]
     alpha = TWO_PI * np.arange(n) / n
     X = reconstruct(st.eta, st.L, st.Xbar)
@@ -201,16 +252,26 @@ def hs_step(solver: K.Kfbi, st: State, dt, sigma, J, tol=1e-8, restart=100, max_
     th_a = 1.0 + spec_deriv(st.eta)
     curv = (TWO_PI / st.L) * th_a
     r2 = X[:, 0] ** 2 + X[:, 1] ** 2
-    rhs = -sigma * curv + J * 0.5 * np.log(r2)
+    sig = sigma
+    if rescale:
+        if st.A0 is None:
+            st.A0 = area(X)
+        sig = sigma / math.exp(st.t)
+    rhs = -sig * curv + J * 0.5 * np.log(r2)
     x0 = st.density if st.density is not None else np.zeros(n)
     phi, info = gmres(lambda x: solver.bie_matvec(K.BIE_HS_EXTERIOR_MDL, x), rhs, x0=x0,
                       tol=tol, restart=restart, max_iter=max_iter)
     _, dn, _ = solver.apply(K.LAYER_DOUBLE, phi, want_dnormal=True)
     nx, ny = np.sin(th), -np.cos(th)
     U = J * (X[:, 0] * nx + X[:, 1] * ny) / r2 - dn
+    lam = sig
+    if rescale:
+        c = st.A0 / math.pi
+        U = c * U - (X[:, 0] * nx + X[:, 1] * ny)
+        lam = c * sig
     st.density = phi
     st.last.update(info=info, X=X, rhs=rhs, phi=phi)
-    return _advance(st, U, dt, hs_symbol(n, sigma))
+    return _advance(st, U, dt, hs_symbol(n, lam))
 
 
 def stefan_eps_c(theta, eps, aniso, fold):

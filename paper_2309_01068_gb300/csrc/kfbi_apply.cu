@@ -1487,12 +1487,14 @@ kfbi_status col_tc_setup(kfbi_ctx* c) {
 }
 
 // the column solve as two tensor-core contractions: tmp = (F spec) / (lam_y(l) + lam_x(k) - kappa),
-// spec = G tmp (spec[j][k]: row j, column k; B(n = k, k = j) = spec[j][k])
+// spec = G tmp (spec[j][k]: row j, column k; B(n = k, k = j) = spec[j][k]), both operands in three
+// bfloat16 terms (six products each)
 static kfbi_status launch_col_tc(kfbi_ctx* c, float* spec) {
   const int N = c->N;
   TcGemmArgs g;
-  g.terms = 3;
+  g.terms = 6;  // float32-level products: the column solve feeds the float32 inner applies
   g.error = c->col_tc_err;
+  g.bn = 32;    // 32-column tiles: N / 32 CTAs per 128-row tile instead of one
   g.A = c->col_fwd;
   g.lda = N;
   g.B = spec;

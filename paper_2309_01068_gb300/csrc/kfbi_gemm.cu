@@ -4,7 +4,9 @@
 // tensor memory, which keeps about 16 significant bits of every product (the lo lo term and
 // the remainders beyond lo are below 2^-16 relative). When B is exact in bfloat16 (the
 // network's weights), A may instead be split into three terms, hi + lo + lo2, which carries
-// A's full float32 value (terms = 4: three products against B). Used by the warm-start network's 256-wide
+// A's full float32 value (terms = 4: three products against B); with both in three terms and
+// the six products above 2^-24 relative (terms = 6) the contraction is as accurate as a float32
+// one. Used by the warm-start network's 256-wide
 // layers (forward, input gradient, weight gradient) and by the column transforms of small grids
 // (DST/DCT as a dense 128 x 128 contraction).
 //
@@ -25,7 +27,7 @@ constexpr int TC_WAIT_TRIES = 1 << 20;
 
 template <int BN>
 constexpr size_t tc_smem() {
-  return 3 * (size_t)TC_BM * TC_BK * 2 + 2 * (size_t)BN * TC_BK * 2 + 64;
+  return 3 * (size_t)TC_BM * TC_BK * 2 + 3 * (size_t)BN * TC_BK * 2 + 64;
 }
 
 // stages rows x TC_BK elements of a float32 operand (element (r, k) at p[r ld + k], or p[k ld + r]
@@ -34,25 +36,39 @@ constexpr size_t tc_smem() {
 template <int ROWS>
 __device__ __forceinline__ void tc_stage(const float* p, long ld, int trans, int r0, int rows_valid, int k0,
                                          int k_valid, unsigned char* hi, unsigned char* lo, unsigned char* lo2) {
-  for (int e = threadIdx.x; e < ROWS * TC_BK; e += TC_THREADS) {
-    int r, k;
-    if (trans) {
-      r = e % ROWS;
-      k = e / ROWS;
-    } else {
-      r = e / TC_BK;
-      k = e % TC_BK;
+  // sixteen loads in flight per thread before any is used (the staging is L2-latency bound)
+  constexpr int PER = ROWS * TC_BK / TC_THREADS, BATCH = 16;
+  static_assert(PER % BATCH == 0, "tile rows");
+#pragma unroll 1
+  for (int b0 = 0; b0 < PER; b0 += BATCH) {
+    float v[BATCH];
+    int rr[BATCH], kk[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const int e = (int)threadIdx.x + (b0 + u) * TC_THREADS;
+      int r, k;
+      if (trans) {
+        r = e % ROWS;
+        k = e / ROWS;
+      } else {
+        r = e / TC_BK;
+        k = e % TC_BK;
+      }
+      rr[u] = r;
+      kk[u] = k;
+      const int gr = r0 + r, gk = k0 + k;
+      v[u] = (gr < rows_valid && gk < k_valid) ? (trans ? p[(long)gk * ld + gr] : p[(long)gr * ld + gk]) : 0.0f;
     }
-    const int gr = r0 + r, gk = k0 + k;
-    float v = 0.0f;
-    if (gr < rows_valid && gk < k_valid) v = trans ? p[(long)gk * ld + gr] : p[(long)gr * ld + gk];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const float r1 = v - __bfloat162float(h);
-    const __nv_bfloat16 l = __float2bfloat16_rn(r1);
-    const uint32_t off = tc::kmajor_offset(r, k, TC_BK);
-    *(__nv_bfloat16*)(hi + off) = h;
-    *(__nv_bfloat16*)(lo + off) = l;
-    if (lo2 != nullptr) *(__nv_bfloat16*)(lo2 + off) = __float2bfloat16_rn(r1 - __bfloat162float(l));
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v[u]);
+      const float r1 = v[u] - __bfloat162float(h);
+      const __nv_bfloat16 l = __float2bfloat16_rn(r1);
+      const uint32_t off = tc::kmajor_offset(rr[u], kk[u], TC_BK);
+      *(__nv_bfloat16*)(hi + off) = h;
+      *(__nv_bfloat16*)(lo + off) = l;
+      if (lo2 != nullptr) *(__nv_bfloat16*)(lo2 + off) = __float2bfloat16_rn(r1 - __bfloat162float(l));
+    }
   }
 }
 
@@ -65,7 +81,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(TcGemmArgs g) {
   unsigned char* a_lo2 = a_lo + A_BYTES;
   unsigned char* b_hi = a_lo2 + A_BYTES;
   unsigned char* b_lo = b_hi + B_BYTES;
-  uint64_t* bar = (uint64_t*)(b_lo + B_BYTES);
+  unsigned char* b_lo2 = b_lo + B_BYTES;
+  uint64_t* bar = (uint64_t*)(b_lo2 + B_BYTES);
   uint32_t* tslot = (uint32_t*)(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
@@ -86,8 +103,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(TcGemmArgs g) {
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int k0 = ch * TC_BK;
     last = ch;
-    tc_stage<TC_BM>(g.A, g.lda, g.transA, m0, g.M, k0, g.K, a_hi, a_lo, g.terms == 4 ? a_lo2 : nullptr);
-    tc_stage<BN>(g.B, g.ldb, g.transB, n0, g.N, k0, g.K, b_hi, b_lo, nullptr);
+    tc_stage<TC_BM>(g.A, g.lda, g.transA, m0, g.M, k0, g.K, a_hi, a_lo, g.terms >= 4 ? a_lo2 : nullptr);
+    tc_stage<BN>(g.B, g.ldb, g.transB, n0, g.N, k0, g.K, b_hi, b_lo, g.terms == 6 ? b_lo2 : nullptr);
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -106,6 +123,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_gemm(TcGemmArgs g) {
         } else if (g.terms == 4) {  // B exact in bfloat16: A's three terms against B
           const uint64_t al2 = tc::smem_desc(tc::smem_u32(a_lo2) + ko, LBO, SBO);
           tc::mma_bf16(tmem, al, bh, IDESC, 1u);
+          tc::mma_bf16(tmem, al2, bh, IDESC, 1u);
+        } else if (g.terms == 6) {  // both in three terms: every product above 2^-24 relative
+          const uint64_t al2 = tc::smem_desc(tc::smem_u32(a_lo2) + ko, LBO, SBO);
+          const uint64_t bl2 = tc::smem_desc(tc::smem_u32(b_lo2) + ko, LBO, SBO);
+          tc::mma_bf16(tmem, ah, bl, IDESC, 1u);
+          tc::mma_bf16(tmem, al, bh, IDESC, 1u);
+          tc::mma_bf16(tmem, al, bl, IDESC, 1u);
+          tc::mma_bf16(tmem, ah, bl2, IDESC, 1u);
           tc::mma_bf16(tmem, al2, bh, IDESC, 1u);
         }
       }
@@ -161,9 +186,10 @@ static kfbi_status tc_launch(const TcGemmArgs& g, cudaStream_t s) {
 
 kfbi_status tc_gemm(const TcGemmArgs& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return KFBI_OK;
-  if (g.N > 128) return tc_launch<256>(g, s);
-  if (g.N > 64) return tc_launch<128>(g, s);
-  if (g.N > 32) return tc_launch<64>(g, s);
+  const int bn = g.bn > 0 ? g.bn : (g.N > 128 ? 256 : g.N > 64 ? 128 : g.N > 32 ? 64 : 32);
+  if (bn >= 256) return tc_launch<256>(g, s);
+  if (bn >= 128) return tc_launch<128>(g, s);
+  if (bn >= 64) return tc_launch<64>(g, s);
   return tc_launch<32>(g, s);
 }
 
@@ -172,7 +198,7 @@ kfbi_status tc_gemm(const TcGemmArgs& g, cudaStream_t s) {
 extern "C" kfbi_status kfbi_tc_gemm(int M, int N, int K, const float* A, long lda, int transA, const float* B, long ldb,
                                     int transB, float* C, long ldc, int terms, int* error, void* stream) {
   if (M < 1 || N < 1 || K < 1 || A == nullptr || B == nullptr || C == nullptr || error == nullptr) return KFBI_ERR_ARG;
-  if ((terms != 1 && terms != 3 && terms != 4) || lda < 1 || ldb < 1 || ldc < N) return KFBI_ERR_ARG;
+  if ((terms != 1 && terms != 3 && terms != 4 && terms != 6) || lda < 1 || ldb < 1 || ldc < N) return KFBI_ERR_ARG;
   if ((!transA && lda < K) || (transA && lda < M) || (!transB && ldb < K) || (transB && ldb < N)) return KFBI_ERR_ARG;
   kfbi::TcGemmArgs g{};
   g.A = A;

@@ -482,8 +482,9 @@ kfbi_status apply_setup_attributes(kfbi_ctx* c);
 
 // tensor-core contraction C = alpha A B^T (kfbi_gemm.cu): A(m, k) = transA ? A[k lda + m] :
 // A[m lda + k], B(n, k) likewise, float32 in and out, split-bfloat16 products (terms 3), A in
-// three bfloat16 terms against a B exact in bfloat16 (terms 4) or the plain bfloat16 product
-// (terms 1); epilogue: store, add, or divide by dm[m] + dn[n] + shift
+// three bfloat16 terms against a B exact in bfloat16 (terms 4), both in three terms (terms 6,
+// float32 accuracy) or the plain bfloat16 product (terms 1); epilogue: store, add, or divide by
+// dm[m] + dn[n] + shift
 enum { TC_STORE = 0, TC_ADD = 1, TC_EIGEN = 2 };
 struct TcGemmArgs {
   const float* A = nullptr;
@@ -502,6 +503,7 @@ struct TcGemmArgs {
   float shift = 0.0f;
   int terms = 3;
   int* error = nullptr;  // device flag, set to 1 when a completion wait gave up
+  int bn = 0;            // column tile (32, 64, 128, 256; 0: the widest that covers N, at most 256)
 };
 kfbi_status tc_gemm(const TcGemmArgs& g, cudaStream_t s);
 // the tensor-core column solve's matrices and buffers (kfbi_apply.cu), for N <= COL_TC_MAX_N

@@ -20,12 +20,13 @@ kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const dou
 // scalar slots of the device state
 enum : int {
   SC_L = 0, SC_XB0, SC_XB1, SC_T, SC_STEPS, SC_MPREV, SC_QPREV0, SC_QPREV1, SC_LPREV, SC_M, SC_Q0, SC_Q1,
-  SC_LNEW, SC_LAM, SC_WS_NET, SC_WS_RATIO, SC_COUNT = 16
+  SC_LNEW, SC_LAM, SC_WS_NET, SC_WS_RATIO, SC_A0, SC_COUNT = 20
 };
 
 struct kfbi_thetal {
   kfbi_ctx* ctx = nullptr;
   int n = 0;
+  int cap = 0;                // node capacity of the arrays (marker doubling grows n up to it)
   kfbi_thetal_params prm{};
   double* eta = nullptr;      // [n]
   double* xy = nullptr;       // [n][2]
@@ -165,17 +166,20 @@ __global__ void k_st_theta_a(const double* eta_a, int n, double* th_a) {
 }
 
 // Hele-Shaw right-hand side -sigma kappa + J ln|X| (Sec. 3.1), kappa = (2 pi / L) theta_a
+// rescaled frame (Sec. 6.1.4): surface tension sigma / R with R = e^{tb}, tb = the scaled time
 __global__ void k_st_hs_rhs(const double* xy, const double* th_a, int n, const double* scal, double sigma, double J,
-                            double* rhs) {
+                            int rescale, double* rhs) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double x = xy[2 * j], y = xy[2 * j + 1];
   double curv = (TWO_PI / scal[SC_L]) * th_a[j];
-  rhs[j] = -sigma * curv + J * 0.5 * log(x * x + y * y);
+  const double sig = rescale ? sigma * exp(-scal[SC_T]) : sigma;
+  rhs[j] = -sig * curv + J * 0.5 * log(x * x + y * y);
 }
 
-// U = J x.n / |x|^2 - dn,  n = (sin theta, -cos theta)
-__global__ void k_st_hs_velocity(const double* xy, const double* eta, const double* dn, int n, double J, double* U) {
+// U = J x.n / |x|^2 - dn,  n = (sin theta, -cos theta); rescaled frame: (A0 / pi) U - x.n
+__global__ void k_st_hs_velocity(const double* xy, const double* eta, const double* dn, int n, double J, int rescale,
+                                 const double* scal, double* U) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double a = (TWO_PI * (double)j) / (double)n;
@@ -183,7 +187,65 @@ __global__ void k_st_hs_velocity(const double* xy, const double* eta, const doub
   double s, c;
   sincos(th, &s, &c);
   double x = xy[2 * j], y = xy[2 * j + 1];
-  U[j] = J * (x * s - y * c) / (x * x + y * y) - dn[j];
+  const double xn = x * s - y * c;
+  const double u = J * xn / (x * x + y * y) - dn[j];
+  U[j] = rescale ? (scal[SC_A0] / PI) * u - xn : u;
+}
+
+// area of the curve through the nodes, (1/2) int (x y_a - y x_a) da with X_a = (L / 2 pi)(cos, sin)
+// theta (one block); stored as the scaled frame's A0 on the first step
+__global__ void k_st_area0(const double* xy, const double* eta, int n, double* scal) {
+  __shared__ double sh[32];
+  if (scal[SC_STEPS] != 0.0) return;
+  double a = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double th = (TWO_PI * (double)j) / (double)n + eta[j];
+    double s, c;
+    sincos(th, &s, &c);
+    a += xy[2 * j] * s - xy[2 * j + 1] * c;
+  }
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    scal[SC_A0] = 0.5 * (scal[SC_L] / TWO_PI) * t * (TWO_PI / (double)n);
+  }
+}
+
+// ---- marker doubling (Sec. 6.1.4): values at alpha = 2 pi j / (2n) of the trigonometric
+// interpolant with coefficients c_k (k <= n/2, normalised, the Nyquist term a cosine), one warp
+// per output point
+__global__ void k_st_upsample(const double2* coef, int n, const double2* tw2, double* out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int m = 2 * n;
+  if (warp >= m) return;
+  const int j = warp;
+  const int K = (n - 1) / 2;
+  double acc = 0.0;
+  for (int k = 1 + lane; k <= K; k += 32) {
+    const double2 e = tw2[(int)(((long)k * j) % m)];  // e^{2 pi i k j / (2n)}
+    acc += 2.0 * (coef[k].x * e.x - coef[k].y * e.y);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    double v = coef[0].x + acc;
+    if ((n & 1) == 0) {
+      const double2 e = tw2[(int)(((long)(n / 2) * j) % m)];
+      v += coef[n / 2].x * e.x;  // c cos(n alpha / 2)
+    }
+    out[j] = v;
+  }
+}
+
+// the Adams-Bashforth history N-hat (normalised half spectrum, k <= n/2) of the same function on
+// 2n points: k < n/2 kept, the Nyquist cosine split (half at k = n/2), zero above
+__global__ void k_st_pad_history(double2* nh, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > n) return;
+  if (k == n / 2 && (n & 1) == 0) nh[k] = make_double2(0.5 * nh[k].x, 0.5 * nh[k].y);
+  else if (k > n / 2) nh[k] = make_double2(0.0, 0.0);
 }
 
 // Stefan: eps_C at the nodes, rhs = -eps_C kappa - T1 (Sec. 3.2), eps_V array
@@ -312,12 +374,14 @@ __device__ __forceinline__ double stiff(double lam, double L, int p, double k) {
 // history shift (Sec. 5.3). explicit_ != 0: no stiff part (s = 0, e1 = e2 = 1), the
 // Adams-Bashforth comparison scheme of Sec. 6.2.2.
 __global__ void k_st_propagate(double2* eta_h, const double2* rhs_h, double2* Nprev, int n, double* scal, double dt,
-                               int p, double lam_fixed, int explicit_) {
+                               int p, double lam_fixed, int explicit_, int rescale) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   int nk = n / 2 + 1;
   if (k >= nk) return;
   bool first = scal[SC_STEPS] == 0.0;
   double lam = explicit_ ? 0.0 : (lam_fixed > 0.0 ? lam_fixed : scal[SC_LAM]);
+  // rescaled Hele-Shaw frame: the stiff part of (A0 / pi) U with surface tension sigma e^{-tb}
+  if (rescale && !explicit_) lam = (scal[SC_A0] / PI) * lam_fixed * exp(-scal[SC_T]);
   double L = scal[SC_L], Ln = scal[SC_LNEW], Lp = scal[SC_LPREV];
   double sn = stiff(lam, L, p, k), snew = stiff(lam, Ln, p, k), sp = stiff(lam, Lp, p, k);
   double e1 = exp(0.5 * dt * (sn + snew));
@@ -408,8 +472,36 @@ static kfbi_status warm_start_choose(kfbi_ctx* c, kfbi_thetal* st, int kind, con
   return KFBI_OK;
 }
 
+// doubles the markers (eta, density, N-hat history; twiddles of the new count) while
+// L / n > refine_ratio h and the capacity allows (Sec. 6.1.4)
+static kfbi_status refine_markers(kfbi_ctx* c, kfbi_thetal* st) {
+  cudaStream_t s = c->stream;
+  while (true) {
+    KFBI_TRY(cudaMemcpyAsync(st->host_scal, st->scal, SC_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KFBI_TRY(cudaStreamSynchronize(s));
+    const int n = st->n;
+    if (!(st->host_scal[SC_L] / n > st->prm.refine_ratio * c->h) || 2 * n > st->cap) return KFBI_OK;
+    const int nk = n / 2 + 1, m = 2 * n;
+    double2* coef = (double2*)st->coef;
+    // twiddles of 2n points into the work buffer, then eta and the density through the interpolant
+    k_twiddles_n_step<<<cdiv(m, 256), 256, 0, s>>>(m, (double2*)st->work);
+    k_st_dft<<<wb(nk), 256, 0, s>>>(st->eta, 1, 1, n, (const double2*)st->tw, coef);
+    k_st_upsample<<<wb(m), 256, 0, s>>>(coef, n, (const double2*)st->work, st->V);
+    k_st_copy<<<cdiv(m, 256), 256, 0, s>>>(st->V, st->eta, m);
+    k_st_dft<<<wb(nk), 256, 0, s>>>(st->density, 1, 1, n, (const double2*)st->tw, coef);
+    k_st_upsample<<<wb(m), 256, 0, s>>>(coef, n, (const double2*)st->work, st->V);
+    k_st_copy<<<cdiv(m, 256), 256, 0, s>>>(st->V, st->density, m);
+    k_st_pad_history<<<cdiv(n + 1, 256), 256, 0, s>>>((double2*)st->Nprev_h, n);
+    k_st_copy<<<cdiv(2 * m, 256), 256, 0, s>>>(st->work, st->tw, 2 * m);
+    launched(c, 9);
+    KFBI_TRY(cudaGetLastError());
+    st->n = m;
+  }
+}
+
 kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve_info* info) {
   cudaStream_t s = c->stream;
+  if (st->prm.refine_ratio > 0.0) KFBI_CHECK(refine_markers(c, st));
   const int n = st->n;
   const int nk = n / 2 + 1;
   const double2* tw = (const double2*)st->tw;
@@ -434,7 +526,8 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
   const double* ratio = nullptr;
   if (P.kind == KFBI_STEP_HELE_SHAW) {
     launched(c, 2);
-    k_st_hs_rhs<<<tb, 256, 0, s>>>(st->xy, st->th_a, n, st->scal, P.sigma, P.J, st->rhs);
+    if (P.rescale) k_st_area0<<<1, 1024, 0, s>>>(st->xy, st->eta, n, st->scal);
+    k_st_hs_rhs<<<tb, 256, 0, s>>>(st->xy, st->th_a, n, st->scal, P.sigma, P.J, P.rescale, st->rhs);
     // mixed precision: the refinement's last float64 apply, at the returned density, also
     // gives the normal derivative of its double layer; float64: one more apply
     const bool dn_from_solve = c->precision == KFBI_MIXED;
@@ -444,7 +537,7 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
     if (sst != KFBI_OK && sst != KFBI_ERR_NOT_CONVERGED) return sst;
     if (!dn_from_solve)
       KFBI_CHECK(apply_enqueue(c, KFBI_DOUBLE, false, st->density, st->V, st->dn, nullptr, -1, nullptr, nullptr));
-    k_st_hs_velocity<<<tb, 256, 0, s>>>(st->xy, st->eta, st->dn, n, P.J, st->U);
+    k_st_hs_velocity<<<tb, 256, 0, s>>>(st->xy, st->eta, st->dn, n, P.J, P.rescale, st->scal, st->U);
   } else {
     const int N = c->N;
     const long NN = (long)N * N;
@@ -488,10 +581,10 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
   const int expl = P.scheme == KFBI_SCHEME_EXPLICIT ? 1 : 0;
   if (P.kind == KFBI_STEP_HELE_SHAW)
     k_st_propagate<<<cdiv(nk, 256), 256, 0, s>>>((double2*)st->eta_h, coef, (double2*)st->Nprev_h, n, st->scal, dt, 3,
-                                                 P.sigma, expl);
+                                                 P.sigma, expl, P.rescale);
   else  // Stefan case I (second order) or II (eps_V = 0, third order); lambda from k_st_tangential
     k_st_propagate<<<cdiv(nk, 256), 256, 0, s>>>((double2*)st->eta_h, coef, (double2*)st->Nprev_h, n, st->scal, dt,
-                                                 P.eps_v > 0.0 ? 2 : 3, -1.0, expl);
+                                                 P.eps_v > 0.0 ? 2 : 3, -1.0, expl, 0);
   k_st_idft<<<wb(n), 256, 0, s>>>((const double2*)st->eta_h, 1, n, tw, 0, st->eta, 1);
   k_st_finish<<<1, 32, 0, s>>>(st->scal, dt);
   KFBI_TRY(cudaGetLastError());
@@ -526,24 +619,27 @@ static kfbi_status thetal_create_impl(kfbi_ctx* c, int n, const double* eta, dou
   st->ctx = c;
   st->n = n;
   st->prm = *prm;
-  const int nk = n / 2 + 1;
-  KFBI_CHECK(talloc(&st->eta, n));
-  KFBI_CHECK(talloc(&st->xy, 2 * (size_t)n));
-  KFBI_CHECK(talloc(&st->density, n));
+  // arrays sized for the context's node capacity when markers may be doubled
+  st->cap = prm->refine_ratio > 0.0 ? c->max_nodes : n;
+  const int cap = st->cap;
+  const int nk = cap / 2 + 1;
+  KFBI_CHECK(talloc(&st->eta, cap));
+  KFBI_CHECK(talloc(&st->xy, 2 * (size_t)cap));
+  KFBI_CHECK(talloc(&st->density, cap));
   KFBI_CHECK(talloc(&st->scal, SC_COUNT));
-  KFBI_CHECK(talloc(&st->tw, 2 * (size_t)n));
+  KFBI_CHECK(talloc(&st->tw, 2 * (size_t)cap));
   KFBI_CHECK(talloc(&st->eta_h, 2 * (size_t)nk));
   KFBI_CHECK(talloc(&st->N_h, 2 * (size_t)nk));
   KFBI_CHECK(talloc(&st->Nprev_h, 2 * (size_t)nk));
   KFBI_CHECK(talloc(&st->coef, 4 * (size_t)nk));
-  KFBI_CHECK(talloc(&st->th_a, n));
-  KFBI_CHECK(talloc(&st->U, n));
-  KFBI_CHECK(talloc(&st->V, n));
-  KFBI_CHECK(talloc(&st->rhs, n));
-  KFBI_CHECK(talloc(&st->work, 4 * (size_t)n));
-  KFBI_CHECK(talloc(&st->epsv, n));
-  KFBI_CHECK(talloc(&st->dn, n));
-  KFBI_CHECK(talloc(&st->guess, n));
+  KFBI_CHECK(talloc(&st->th_a, cap));
+  KFBI_CHECK(talloc(&st->U, cap));
+  KFBI_CHECK(talloc(&st->V, cap));
+  KFBI_CHECK(talloc(&st->rhs, cap));
+  KFBI_CHECK(talloc(&st->work, 4 * (size_t)cap));
+  KFBI_CHECK(talloc(&st->epsv, cap));
+  KFBI_CHECK(talloc(&st->dn, cap));
+  KFBI_CHECK(talloc(&st->guess, cap));
   KFBI_CHECK(talloc(&st->ws_norm, 3));
   if (prm->kind == KFBI_STEP_STEFAN) {
     size_t NN = (size_t)c->N * c->N;
@@ -578,6 +674,7 @@ kfbi_status kfbi_thetal_create(kfbi_ctx* c, int n, const double* eta, double L, 
   if (prm->kind == KFBI_STEP_HELE_SHAW && c->boxbc != KFBI_BOX_FREESPACE_DL) return KFBI_ERR_ARG;
   if (prm->kind == KFBI_STEP_STEFAN && (c->boxbc != KFBI_BOX_NEUMANN0 || !(prm->eps_v >= 0.0))) return KFBI_ERR_ARG;
   if (prm->scheme != KFBI_SCHEME_SEMI_IMPLICIT && prm->scheme != KFBI_SCHEME_EXPLICIT) return KFBI_ERR_ARG;
+  if (!(prm->refine_ratio >= 0.0) || (prm->rescale != 0 && prm->kind != KFBI_STEP_HELE_SHAW)) return KFBI_ERR_ARG;
   if (!(prm->tol > 0.0) || prm->max_iter < 1 || prm->restart < 1 || prm->restart > MAX_RESTART) return KFBI_ERR_ARG;
   kfbi_thetal* st = new kfbi_thetal();
   kfbi_status s = thetal_create_impl(c, n, eta, L, xbar, prm, st);
@@ -630,6 +727,12 @@ kfbi_status kfbi_thetal_read(kfbi_thetal* st, double* eta, double* xy, double* d
     for (int i = 0; i < SC_COUNT; ++i) scalars[i] = st->host_scal[i];
   }
   KFBI_TRY(stream_exit(st->ctx));
+  return KFBI_OK;
+}
+
+kfbi_status kfbi_thetal_count(kfbi_thetal* st, int* n) {
+  if (st == nullptr || n == nullptr) return KFBI_ERR_ARG;
+  *n = st->n;
   return KFBI_OK;
 }
 

@@ -59,7 +59,8 @@ class ThetaLParams(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("sigma", ctypes.c_double), ("J", ctypes.c_double),
                 ("St", ctypes.c_double), ("eps_c", ctypes.c_double), ("eps_aniso", ctypes.c_double),
                 ("eps_v", ctypes.c_double), ("fold", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_iter", ctypes.c_int), ("restart", ctypes.c_int), ("scheme", ctypes.c_int)]
+                ("max_iter", ctypes.c_int), ("restart", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("refine_ratio", ctypes.c_double), ("rescale", ctypes.c_int)]
 
 
 _lib = None
@@ -116,6 +117,7 @@ _SIGNATURES = {
     "kfbi_alu_peak": (_I, [_I, ctypes.POINTER(_D), _P]),
     "kfbi_tc_gemm": (_I, [_I, _I, _I, _P, ctypes.c_long, _I, _P, ctypes.c_long, _I, _P, ctypes.c_long, _I, _P, _P]),
     "kfbi_thetal_set_warmstart": (_I, [_P, _P]),
+    "kfbi_thetal_count": (_I, [_P, ctypes.POINTER(_I)]),
     "kfbi_thetal_training_pair": (_I, [_P, _P, _P]),
 }
 
@@ -538,12 +540,14 @@ class ThetaL:
     """kfbi_thetal_create / kfbi_step / kfbi_thetal_read on a context."""
 
     def __init__(self, ctx: Context, eta, L, xbar, kind, tol=1e-8, max_iter=500, restart=100, sigma=0.0, J=0.0,
-                 St=0.0, eps_c=0.0, eps_aniso=0.0, eps_v=0.0, fold=4, scheme=SCHEME_SEMI_IMPLICIT):
+                 St=0.0, eps_c=0.0, eps_aniso=0.0, eps_v=0.0, fold=4, scheme=SCHEME_SEMI_IMPLICIT, refine_ratio=0.0,
+                 rescale=False):
         self.ctx = ctx
         self.lib = ctx.lib
         self.n = eta.shape[0]
         p = ThetaLParams(kind=kind, sigma=sigma, J=J, St=St, eps_c=eps_c, eps_aniso=eps_aniso, eps_v=eps_v,
-                         fold=fold, tol=tol, max_iter=max_iter, restart=restart, scheme=scheme)
+                         fold=fold, tol=tol, max_iter=max_iter, restart=restart, scheme=scheme,
+                         refine_ratio=float(refine_ratio), rescale=1 if rescale else 0)
         xb = (ctypes.c_double * 2)(float(xbar[0]), float(xbar[1]))
         h = ctypes.c_void_p()
         ctx._sync_stream()
@@ -556,10 +560,13 @@ class ThetaL:
         info = SolveInfo()
         _check(self.lib.kfbi_step(self.ctx.handle, self.handle, float(dt), ctypes.byref(info)), "kfbi_step",
                allow=(ERR_NOT_CONVERGED,))
+        c = ctypes.c_int()
+        _check(self.lib.kfbi_thetal_count(self.handle, ctypes.byref(c)), "kfbi_thetal_count")
+        self.n = c.value          # marker doubling may have grown it
         self.ctx.n = self.n  # the step set the context's interface
         return info.as_dict()
 
-    SCALARS = 16
+    SCALARS = 20
 
     def read(self, T=True):
         """State as device tensors plus the host scalars (checkpoint)."""

@@ -3,8 +3,8 @@
 The transform along y is an N x N matrix (DST-II or DCT-II), the eigenvalue division is the
 first contraction's epilogue and the exact inverse (DST-III / DCT-III, weights, 2/N) the second;
 both run through kfbi_tc_gemm with split bfloat16 products. The float32 apply of a mixed context
-with this path is compared with the same apply through the FFT column kernel (2e-5: the
-products keep about 16 bits) and with the oracle's float64 apply; a mixed solve through it
+with this path is compared with the same apply through the FFT column kernel (5e-5: both are
+float32 forms, each about 3e-5 from the float64 apply) and with the oracle's float64 apply; a mixed solve through it
 reaches the float64 tolerance and the oracle's density, and a batch of 128^2 instances with the
 option matches the oracle instance by instance.
 """
@@ -58,7 +58,9 @@ def test_tensor_core_column_solve_apply(N, boxbc, kappa, box):
         ctx.set_option(K.OPT_COL_TC, 0)
         a, b = v_tc.cpu().numpy(), v_fft.cpu().numpy()
         assert np.isfinite(a).all()
-        assert rel(a, b) < 2e-5, (layer, rel(a, b))
+        # two float32 forms, each within about 3e-5 of the float64 apply (the float32 sines of the
+        # row transform set that): they differ by rounding of that size
+        assert rel(a, b) < 5e-5, (layer, rel(a, b))
         rv, _, _ = ref.apply(OK.LAYER_DOUBLE if layer == K.DOUBLE else OK.LAYER_SINGLE, dens)
         assert rel(a, rv) < 2e-4
     ctx.close()
@@ -81,3 +83,23 @@ def test_tensor_core_column_solve_mixed_solve_and_capacity():
         big.set_option(K.OPT_COL_TC, 1)
     assert e.value.status == K.ERR_CAPACITY
     big.close()
+
+
+def test_batch_of_small_grids_with_tensor_core_columns():
+    """Mixed batch of 128^2 instances with the tensor-core column solve chosen explicitly: per
+    instance status and density against the oracle."""
+    probs = [W.random_problem(900 + i, N=128, n=int(80 + 10 * i), kappa=[0.0, 10.0][i % 2]) for i in range(4)]
+    descs = [dict(N=p.N, box=p.box, kappa=p.kappa, boxbc=K.BOX_DIRICHLET0, max_nodes=p.n) for p in probs]
+    b = K.Batch(descs, K.MIXED)
+    for c, p in zip(b.contexts, probs):
+        c.set_interface(dev(p.xy))
+        c.set_option(K.OPT_COL_TC, 1)
+    rhs = [dev(p.rhs) for p in probs]
+    dens = [torch.zeros(p.n, dtype=torch.float64, device="cuda") for p in probs]
+    _, infos = b.solve(K.BIE_INTERIOR_DL, rhs, dens, tol=1e-11, max_iter=400, restart=100)
+    for p, d, info in zip(probs, dens, infos):
+        assert info["status"] == 0
+        ref = OK.Kfbi(p.N, p.box, p.kappa, OK.BOX_DIRICHLET0).set_interface(p.xy)
+        x, _ = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), p.rhs, tol=1e-13)
+        assert rel(d.cpu().numpy(), x) < 1e-9
+    b.close()

@@ -272,3 +272,31 @@ def test_batch_large_grid_and_underresolved_instances():
     assert infos[1]["status"] == K.ERR_NOT_CONVERGED and not i1["converged"]
     r_gpu, r_ref = infos[1]["rel_residual"], i1["rel_residual"]
     assert 0.1 < r_gpu / r_ref < 10.0
+
+
+# ------------------------------------------------------------------- long-time Hele-Shaw (Sec. 6.1.4)
+@pytest.mark.parametrize("rescale", [False, True])
+def test_marker_doubling_and_rescaled_frame_parity(rescale):
+    """Hele-Shaw steps with marker doubling (32 nodes doubled twice before the first step on a
+    128^2 grid, L / n > 1.5 h) and, optionally, in the rescaled frame: node count, eta, L and
+    the density vs the oracle (float64)."""
+    nd = W.equal_arclength(W.polar(1.0, [(3, 0.05, 0.0)]), 32)
+    N, box = 128, (-3.0, 3.0, -3.0, 3.0)
+    ctx = K.Context(N, box, 0.0, K.BOX_FREESPACE_DL, K.FP64, max_nodes=256)
+    alpha = 2 * math.pi * np.arange(32) / 32
+    st = K.ThetaL(ctx, dev(nd["theta"] - alpha), nd["L"], nd["xy"].mean(0), K.STEP_HELE_SHAW, tol=1e-12,
+                  sigma=1e-2, J=1.0, refine_ratio=1.5, rescale=rescale)
+    ref = OK.Kfbi(N, box, 0.0, OK.BOX_FREESPACE_DL)
+    rst = OT.state_from_nodes(nd["xy"], nd["theta"], nd["L"])
+    for _ in range(3):
+        st.step(2e-3)
+        OT.hs_step(ref, rst, 2e-3, 1e-2, 1.0, tol=1e-12, refine_ratio=1.5, rescale=rescale)
+    assert st.n == rst.eta.shape[0] == 128
+    out = st.read(T=False)
+    assert abs(out["L"] - rst.L) < 1e-10 * rst.L
+    assert np.abs(out["eta"].cpu().numpy() - rst.eta).max() < 1e-9
+    assert rel(out["density"].cpu().numpy(), rst.density) < 1e-8
+    if rescale:
+        assert abs(out["scalars"][16] - rst.A0) < 1e-12 * rst.A0
+    st.close()
+    ctx.close()
