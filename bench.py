@@ -141,6 +141,9 @@ def parse():
                     help="skip the batched (256 instances), warm-start and Stefan measurements")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (for short profiler runs): no e2e, applies, fp64 or cpu legs")
+    ap.add_argument("--baselines", action="store_true",
+                    help="one JSON line of the per-config table: the oracle on one core and on all cores and the "
+                         "GPU forms for configs 1-5 (several minutes of host time)")
     return ap.parse_args()
 
 
@@ -594,11 +597,12 @@ def col_kernel_sizes(torch, K, reps=40):
         dens = torch.ones(p.n, dtype=torch.float64, device="cuda")
         vals = torch.empty(p.n, dtype=torch.float64, device="cuda")
         row = {}
-        for form in ("tensor_core", "register", "stockham"):
+        for form in ("tensor_core", "register", "stockham_p1", "stockham_p4", "stockham"):
             if (form == "register" and N > 1024) or (form == "tensor_core" and N > 256):
                 continue
             ctx.set_option(K.OPT_COL_REG, 1 if form == "register" else 0)
             ctx.set_option(K.OPT_COL_TC, 1 if form == "tensor_core" else 0)
+            ctx.set_option(K.OPT_COL_PAIRS, 1 if form == "stockham_p1" else (4 if form == "stockham_p4" else 0))
             for _ in range(5):
                 ctx.apply_into(K.DOUBLE, dens, vals)
             ctx.timing(True)
@@ -665,11 +669,112 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------- per-config table
+ORACLE_CONFIG_CODE = """
+import sys, json, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import workloads as W
+from oracle import kfbi as OK
+from oracle.gmres import gmres
+which = {which!r}
+out = {{}}
+if which == "c1":
+    p = W.config_small_laplace()
+    t0 = time.perf_counter()
+    s = OK.Kfbi(p.N, p.box, 0.0, OK.BOX_DIRICHLET0).set_interface(p.xy)
+    x, info = gmres(lambda v: s.bie_matvec(OK.BIE_INTERIOR_DL, v), p.rhs, tol=1e-10)
+    out = dict(solve_s=time.perf_counter() - t0, iterations=info["iterations"])
+    t0 = time.perf_counter()
+    for _ in range(5):
+        s.bie_matvec(OK.BIE_INTERIOR_DL, x)
+    out["apply_s"] = (time.perf_counter() - t0) / 5
+elif which == "c4":
+    probs = W.config_batched(256)
+    pick = [0, 1, 2, 3]
+    t0 = time.perf_counter()
+    its = []
+    for i in pick:
+        p = probs[i]
+        s = OK.Kfbi(p.N, p.box, p.kappa, OK.BOX_DIRICHLET0).set_interface(p.xy)
+        x, info = gmres(lambda v: s.bie_matvec(OK.BIE_INTERIOR_DL, v), p.rhs, tol=1e-8, max_iter=300)
+        its.append(info["iterations"])
+    out = dict(solve_s_per_instance=(time.perf_counter() - t0) / len(pick), instances=[int(i) for i in pick],
+               iterations=its, grids=[probs[i].N for i in pick])
+else:
+    N, n, box, kap, bc, kind = dict(c2=(1024, 1024, 4.0, 0.0, OK.BOX_FREESPACE_DL, OK.BIE_HS_EXTERIOR_MDL),
+                                    c3=(2048, 2048, 2.0, 3000.0, OK.BOX_NEUMANN0, OK.BIE_STEFAN_SL),
+                                    c5=(4096, 4096, 2.0, 3000.0, OK.BOX_NEUMANN0, OK.BIE_STEFAN_SL))[which]
+    p = W.config_hele_shaw(N=N, n=n, box=box) if which == "c2" else W.config_stefan(N=N, n=n, box=box)
+    t0 = time.perf_counter()
+    s = OK.Kfbi(N, p.box, kap, bc).set_interface(p.xy)
+    t_set = time.perf_counter() - t0
+    phi = W.random_density(3, n)
+    ev = np.full(n, 2e-3)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        s.bie_matvec(kind, phi, eps_v=ev)
+    out = dict(set_interface_s=t_set, apply_s=(time.perf_counter() - t0) / 2)
+print(json.dumps(out))
+"""
+
+
+def oracle_config(which, one_core):
+    env = dict(os.environ)
+    if one_core:
+        for v in THREAD_VARS:
+            env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", ORACLE_CONFIG_CODE.format(root=ROOT, which=which)], capture_output=True,
+                       text=True, env=env, timeout=3600)
+    if r.returncode != 0:
+        return dict(error=r.stderr[-400:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_baselines():
+    """Per-config numbers for the baseline table: the oracle on one core and on all cores (full
+    solves for configs 1 and 4, a set_interface and two applies for configs 2, 3 and 5, whose
+    solves are then extrapolated by the GPU runs' iteration counts), and the GPU forms."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2309_01068_gb300 import build
+    from paper_2309_01068_gb300 import kfbi as K
+
+    build.build()
+    K.load()
+    out = dict(host=host_cpu())
+    for which in ("c1", "c2", "c3", "c4", "c5"):
+        out[which] = dict(oracle_one_core=oracle_config(which, True), oracle_all_cores=oracle_config(which, False))
+        print(f"[baselines] {which}: {out[which]}", file=sys.stderr)
+    # GPU, config 1: solves/s and applies/s, float64 and mixed
+    p = W.config_small_laplace()
+    for name, prec in (("fp64", K.FP64), ("mixed", K.MIXED)):
+        ctx = K.Context(p.N, p.box, 0.0, K.BOX_DIRICHLET0, prec, max_nodes=p.n)
+        ctx.set_interface(torch.tensor(p.xy, dtype=torch.float64, device="cuda"))
+        rhs = torch.tensor(p.rhs, dtype=torch.float64, device="cuda")
+        ctx.solve_bie(K.BIE_INTERIOR_DL, rhs, tol=1e-10, max_iter=400)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 50
+        for _ in range(reps):
+            _, info = ctx.solve_bie(K.BIE_INTERIOR_DL, rhs, tol=1e-10, max_iter=400)
+        torch.cuda.synchronize()
+        out["c1"]["gpu_" + name] = dict(solves_per_s=reps / (time.perf_counter() - t0), iterations=info["iterations"],
+                                        applies_per_s=time_applies(torch, K, ctx))
+        ctx.close()
+    print(json.dumps(out))
+    return 0
+
+
 # --------------------------------------------------------------------------- main arm
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.baselines:
+        return run_baselines()
     rank, world, local = dist_env()
     import numpy as np
     import torch
