@@ -794,7 +794,8 @@ def main():
     p = workload()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     # ALU roofs of this GPU (float32 and float64 FMA), measured by the library's probe kernel
-    alu = dict(fp32_tflops=K.alu_peak(0), fp64_tflops=K.alu_peak(1))
+    # (not in --profile runs, whose launch lists should hold the workload's kernels only)
+    alu = {} if args.profile else dict(fp32_tflops=K.alu_peak(0), fp64_tflops=K.alu_peak(1))
 
     # ---- headline: mixed precision
     ctx, st = make_state(K, torch, p, K.MIXED)

@@ -200,8 +200,8 @@ def test_gmres_forms_agree_with_oracle(graphs, cluster, pdl, push, precision, re
     assert ctx.get_option(K.OPT_PUSH_REDUCE) == push
     assert ctx.get_option(K.OPT_PDL) == pdl
     rhs = W.random_density(5, p.n)
-    tol = 1e-12 if precision == 0 else 1e-10
-    phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(rhs), tol=tol, max_iter=400, restart=restart)
+    tol = 1e-13 if precision == 0 else 1e-11
+    phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(rhs), tol=tol, max_iter=600, restart=restart)
     cs = ctx.get_option(K.OPT_LAST_CLUSTER)
     assert (cs in (8, 16)) if cluster else cs == 0
     assert ctx.get_option(K.OPT_CUDA_GRAPHS) == graphs  # the graph form was not given up
@@ -209,7 +209,9 @@ def test_gmres_forms_agree_with_oracle(graphs, cluster, pdl, push, precision, re
     assert info["status"] == 0 and info["rel_residual"] <= tol
     if restart < 100:
         assert info["restarts"] > 0
-    assert rel(phi.cpu().numpy(), rphi) < (1e-9 if precision == 0 else 1e-8)
+    # both solved to 1e-13 (float64) the densities differ by rounding: the 1e-10 interface-density
+    # target; the mixed form refined to 1e-11 is held to the 1e-9 target of refinement
+    assert rel(phi.cpu().numpy(), rphi) < (1e-10 if precision == 0 else 1e-9)
 
 
 @pytest.mark.parametrize("precision,push", [(0, 1), (0, 0)])
@@ -242,12 +244,12 @@ def test_solve_graph_reused_across_interfaces(precision):
         ctx.set_interface(dev(p.xy))
         crossings.add(ctx.stats()["crossings"])
         ref = OK.Kfbi(p.N, p.box, 0.0, OK.BOX_DIRICHLET0).set_interface(p.xy)
-        tol = 1e-12 if precision == 0 else 1e-10
-        phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=tol, max_iter=300, restart=100)
+        tol = 1e-13 if precision == 0 else 1e-11
+        phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=tol, max_iter=400, restart=100)
         assert ctx.get_option(K.OPT_CUDA_GRAPHS) == 1
         rphi, _ = gmres(lambda v: ref.bie_matvec(OK.BIE_INTERIOR_DL, v), p.rhs, tol=1e-13)
         assert info["status"] == 0
-        assert rel(phi.cpu().numpy(), rphi) < (1e-9 if precision == 0 else 1e-8)
+        assert rel(phi.cpu().numpy(), rphi) < (1e-10 if precision == 0 else 1e-9)
     assert len(crossings) > 1
 
 
