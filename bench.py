@@ -266,9 +266,9 @@ def time_applies(torch, K, ctx, reps=50):
     return reps / (e0.elapsed_time(e1) / 1e3)
 
 
-def traffic_record(kernel_src):
+def traffic_record(kernel_src, name):
     """DRAM traffic per launch from a committed ncu summary, if taken on this kernel source."""
-    path = os.path.join(ROOT, "profiles", "k_col_solve_traffic.json")
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
@@ -581,39 +581,46 @@ def stefan_leg(torch, K, steps=3, N=2048, n=2048, tol=1e-9, compare_fp64=True):
                 statuses=[i["status"] for i in infos], mixed_vs_fp64_one_step=err)
 
 
-def col_kernel_sizes(torch, K, reps=40):
-    """Column transform time per apply by grid size for the float32 forms (shared-memory
-    Stockham FFT, register FFTs up to 1024^2, tensor-core contractions up to 256^2): CUDA events
-    around the column launch(es), float32 applies of a Neumann-box context with a 256-node star."""
-    import numpy as np
+# column forms of the size sweep: (name, COL_RADIX4 bits, COL_PAIRS, COL_REG, COL_TC)
+COL_FORMS = (("radix16", 0, 0, 0, 0), ("radix16_p1", 0, 1, 0, 0), ("radix16_p2", 0, -2, 0, 0), ("radix4", 3, 0, 0, 0),
+             ("radix4_p1", 3, 1, 0, 0), ("radix4_p4", 3, 4, 0, 0), ("register", 0, 0, 1, 0),
+             ("tensor_core", 0, 0, 0, 1))
 
+
+def col_kernel_sizes(torch, K, hbm_peak, reps=200):
+    """Column transform time per launch by grid size for every column form (register-resident
+    radix-16 with its pair counts, shared-memory radix-4 Stockham with 1, 2, 4 pairs, four-step
+    register FFTs up to 1024^2, tensor-core contractions up to 256^2) in float32, and the radix-16
+    and radix-4 kernels in float64: kfbi_time_column (CUDA events around `reps` launches back to
+    back, warm L2) on a Neumann-box context with a 256-node star after one apply."""
     import workloads as W
 
     out = {}
     for N in (128, 256, 512, 1024, 2048, 4096):
         p = W.random_problem(17, N=N, n=256, kappa=30.0, boxbc=W.BOX_NEUMANN0)
-        ctx = K.Context(N, p.box, 30.0, K.BOX_NEUMANN0, K.MIXED, max_nodes=p.n)
-        ctx.set_interface(torch.tensor(p.xy, dtype=torch.float64, device="cuda"))
-        dens = torch.ones(p.n, dtype=torch.float64, device="cuda")
-        vals = torch.empty(p.n, dtype=torch.float64, device="cuda")
         row = {}
-        for form in ("tensor_core", "register", "stockham_p1", "stockham_p4", "stockham"):
-            if (form == "register" and N > 1024) or (form == "tensor_core" and N > 256):
-                continue
-            ctx.set_option(K.OPT_COL_REG, 1 if form == "register" else 0)
-            ctx.set_option(K.OPT_COL_TC, 1 if form == "tensor_core" else 0)
-            ctx.set_option(K.OPT_COL_PAIRS, 1 if form == "stockham_p1" else (4 if form == "stockham_p4" else 0))
-            for _ in range(5):
+        for prec in (K.MIXED, K.FP64):
+            ctx = K.Context(N, p.box, 30.0, K.BOX_NEUMANN0, prec, max_nodes=p.n)
+            ctx.set_interface(torch.tensor(p.xy, dtype=torch.float64, device="cuda"))
+            dens = torch.ones(p.n, dtype=torch.float64, device="cuda")
+            vals = torch.empty(p.n, dtype=torch.float64, device="cuda")
+            f32 = prec == K.MIXED
+            for form, r4, pairs, reg, tc in COL_FORMS:
+                if (reg and N > 1024) or (tc and N > 256) or (not f32 and (reg or tc or pairs > 0)):
+                    continue
+                if not f32 and r4 == 0 and N > 2048:  # no float64 radix-16 kernel at 4096^2
+                    continue
+                ctx.set_option(K.OPT_COL_REG, reg)
+                ctx.set_option(K.OPT_COL_TC, tc)
+                ctx.set_option(K.OPT_COL_RADIX4, r4)
+                ctx.set_option(K.OPT_COL_PAIRS, min(16, 2 * max(1, 512 // N)) if pairs < 0 else pairs)
                 ctx.apply_into(K.DOUBLE, dens, vals)
-            ctx.timing(True)
-            for _ in range(reps):
-                ctx.apply_into(K.DOUBLE, dens, vals)
-            t = ctx.timing()
-            ctx.timing(False)
-            us = 1e3 * t["fp32_ms"] / max(t["fp32_launches"], 1)
-            row[form] = dict(us=us, hbm_frac=(8.0 * N * N) / (us * 1e-6) / 1e9 / 6754.1)
+                us = ctx.time_column(f32, reps if f32 else max(reps // 4, 5))
+                elt = 4.0 if f32 else 8.0
+                row[(form if f32 else "fp64_" + form)] = dict(
+                    us=us, hbm_frac=(2 * elt * N * N) / (us * 1e-6) / 1e9 / hbm_peak)
+            ctx.close()
         out[str(N)] = row
-        ctx.close()
     return out
 
 
@@ -883,13 +890,28 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_per_launch / (f32_ms * 1e-3) / 1e9 if tim["fp32_launches"] else None
-    tr = traffic_record(os.path.join(ROOT, "paper_2309_01068_gb300", "csrc", "kfbi_apply.cu"))
-    roofline = dict(kernel="k_col_solve<float> (column forward DST-II, eigen divide, inverse DST)",
+    csrc = os.path.join(ROOT, "paper_2309_01068_gb300", "csrc")
+    if ctx.get_option(K.OPT_COL_RADIX4) & 1:
+        kname = "k_col_solve<float> (radix-4 shared-memory Stockham: column DST-II, eigen divide, inverse DST)"
+        tr = traffic_record(os.path.join(csrc, "kfbi_apply.cu"), "k_col_solve_traffic.json")
+    else:
+        kname = (f"k_col_fft<float,{int(math.log2(N))},P> (register-resident radix-16 column solve: DST-II, "
+                 "eigen divide, inverse DST)")
+        tr = traffic_record(os.path.join(csrc, "kfbi_colfft.cu"), "k_col_fft_traffic.json")
+    # the same kernel back to back (kfbi_time_column: warm L2, programmatic dependent launch as
+    # in the GMRES loop, no event between launches)
+    # (not in --profile runs, whose launch lists should hold the workload's kernels only)
+    b2b = None
+    if not args.profile:
+        b2b_us = ctx.time_column(True, 400)
+        b2b = dict(us=b2b_us, achieved=bytes_per_launch / (b2b_us * 1e-6) / 1e9,
+                   frac=bytes_per_launch / (b2b_us * 1e-6) / 1e9 / hbm_peak, launches=400)
+    roofline = dict(kernel=kname,
                     bound="hbm", achieved=achieved, peak=hbm_peak, unit="GB/s",
                     frac=(achieved / hbm_peak) if achieved else None,
                     traffic=(tr["dram_bytes_per_launch"] if tr else None),
                     algorithmic_bytes_per_launch=bytes_per_launch, launches=tim["fp32_launches"],
-                    mean_launch_us=f32_ms * 1e3,
+                    mean_launch_us=f32_ms * 1e3, back_to_back=b2b,
                     peak_source="MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s")
     # the same kernel against the float32 FMA roof: forward and inverse real transforms of N
     # columns of length N, 2.5 M log2 M flops each (split-radix count of a real FFT)
@@ -942,7 +964,7 @@ def main():
     # ---- further workloads (reported beside the headline, never part of it)
     extras = {}
     if rank == 0 and not args.profile and not args.no_extras:
-        for name, leg in (("col_kernel_sizes", lambda: col_kernel_sizes(torch, K)),
+        for name, leg in (("col_kernel_sizes", lambda: col_kernel_sizes(torch, K, hbm_peak)),
                           ("batched", lambda: batched_leg(torch, K, flush)), ("warm_start", lambda: warmstart_leg(torch, K)),
                           ("stefan", lambda: stefan_leg(torch, K)),
                           ("warm_start_c5", lambda: warm_start_c5_leg(torch, K)),

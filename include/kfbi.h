@@ -323,8 +323,13 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             five-kernel form).
  *   KFBI_OPT_CLUSTER_SIZE     0 (default): the cluster form takes 16 CTAs, else 8; 8 or 16:
  *                             only that size (the five-kernel form when it does not fit).
- *   KFBI_OPT_COL_PAIRS        0 (default, 2): column pairs per block of the float32 column
- *                             transform kernel, 1, 2 or 4 (bounded by its shared memory).
+ *   KFBI_OPT_COL_PAIRS        0 (default): column pairs per block of the column transform;
+ *                             values 0, 1, 2, 4, 8, 16. Radix-4 kernel: 2 by default (float64: 1),
+ *                             else the value bounded by 4 and by its shared memory. Radix-16
+ *                             kernel: instantiated for PMIN = max(1, 512 / N) (one warp per block
+ *                             at least), 2 PMIN and, while a block stays within 256 threads,
+ *                             4 PMIN; it runs the largest of these not above the value (PMIN if
+ *                             none), the largest of all by default.
  *   KFBI_OPT_PDL              1 (default): consecutive kernels of an apply and of a GMRES
  *                             iteration use programmatic dependent launch (a kernel is
  *                             scheduled as its predecessor's blocks exit, reads its static
@@ -357,16 +362,26 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             (16..4096) form the density's Fourier coefficients inside the
  *                             jump kernel (a shared-memory FFT in every block) instead of a
  *                             separate DFT kernel; 0: the separate kernel.
- *   KFBI_OPT_COL_REG          0 (default): the float32 column solve runs the shared-memory
- *                             radix-4 Stockham kernel; 1 (grids with N <= 1024): every FFT is
- *                             held in registers by one group of B lanes (an A-point DFT per lane,
- *                             one transpose through shared memory, B-point DFTs; N = A B).
+ *   KFBI_OPT_COL_RADIX4       2 (default): float32 applies (grids with N >= 32) run the
+ *                             register-resident radix-16 column kernel, float64 applies the
+ *                             shared-memory radix-4 Stockham kernel. In the radix-16 kernel each
+ *                             column pair is owned by N/16 threads holding 16 points through the
+ *                             forward FFT, the eigenvalue division and the inverse (Stockham
+ *                             stages of radix 16, the last of radix 2, 4 or 8, through one
+ *                             shared-memory buffer). Bit 0 set (1, 3): float32 applies run the
+ *                             radix-4 kernel; bit 1 clear (0, 1): float64 applies run the
+ *                             radix-16 kernel. Values 0..3.
+ *   KFBI_OPT_COL_REG          0 (default); 1 (grids with N <= 1024): the float32 column solve
+ *                             holds every FFT in registers by one group of B lanes (an A-point
+ *                             DFT per lane, one transpose through shared memory, B-point DFTs;
+ *                             N = A B). Takes precedence over KFBI_OPT_COL_RADIX4.
  *   KFBI_OPT_COL_TC           0 (default); 1 (grids with N <= 256, else KFBI_ERR_CAPACITY):
  *                             the float32 column solve as two dense contractions on the tensor
  *                             cores (kfbi_tc_gemm, split bfloat16 products): the transform along
  *                             y as an N x N matrix, the eigenvalue division in the first one's
  *                             epilogue, then the inverse transform matrix. The row transform then
  *                             writes every row. Setting it allocates the two N x N matrices.
+ *                             Takes precedence over KFBI_OPT_COL_REG and KFBI_OPT_COL_RADIX4.
  *   KFBI_OPT_BODY_CAP         0 (default): the device-side GMRES loop (the body count of the
  *                             graph's WHILE node, or of the host-driven loop) stops after
  *                             2 max_iter + 2 max_iter / restart + 8 bodies; a value > 0 sets
@@ -396,7 +411,8 @@ enum {
   KFBI_OPT_BODY_CAP = 12,
   KFBI_OPT_SWEEP_CAP = 13,
   KFBI_OPT_COL_REG = 14,
-  KFBI_OPT_COL_TC = 15
+  KFBI_OPT_COL_TC = 15,
+  KFBI_OPT_COL_RADIX4 = 16
 };
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);
@@ -516,9 +532,10 @@ kfbi_status kfbi_batch_set_stream(kfbi_batch* batch, void* stream);
 kfbi_status kfbi_batch_solve(kfbi_batch* batch, int kind, const double* const* rhs, double* const* density,
                              double tol, int max_iter, int restart, kfbi_solve_info* infos);
 /* Autotuner: for each grid size N of the batch, chooses the Gram-Schmidt form (16-CTA
- * cluster, 8-CTA cluster, five kernels), the column pairs per block of the float32 column
- * transform (1, 2, 4) and, in mixed batches, that transform's form (shared-memory FFT,
- * register FFTs for N <= 1024, tensor-core contractions for N <= 256) by timing whole batch
+ * cluster, 8-CTA cluster, five kernels), the column pairs per block of the column transform
+ * (KFBI_OPT_COL_PAIRS 0, 1, 2, 4) and, in mixed batches, the float32 transform's form (radix-16
+ * register-resident kernel, four-step register FFTs for N <= 1024, tensor-core contractions for
+ * N <= 256, radix-4 shared-memory kernel: KFBI_OPT_COL_RADIX4 2 or 3) by timing whole batch
  * solves of rhs from zero (coordinate search, the second of two launches timed) and leaves the
  * fastest set on every context (read them back with kfbi_get_option). best_ms (host, NULL skips): batch solve time of the final choice.
  * Errors: ARG, STATE, CUDA. */
@@ -527,6 +544,19 @@ kfbi_status kfbi_batch_autotune(kfbi_batch* batch, int kind, const double* const
 
 /* Number of kernels this context has launched since creation (host output). */
 kfbi_status kfbi_launch_count(kfbi_ctx* ctx, long long* count);
+
+/*
+ * kfbi_time_column -- mean duration of the column solve of the fast box solver (Sec. 4.2: DST/DCT
+ * along y, division by the eigenvalues, inverse) in the form the context's options select, for
+ * the roofline of the benchmark (not in the paper). fp32 = 1: the float32 kernel of the inner
+ * applies, 0: the float64 kernel. One warm-up launch, then `reps` (1..100000) launches back to
+ * back on the context's stream (programmatic dependent launch as in an apply) between two CUDA
+ * events; writes the elapsed time / reps in microseconds to *us_per_launch (host). The
+ * launches solve the context's spectral-grid scratch buffer in place: its contents are
+ * meaningless afterwards, and the next apply rewrites it. Synchronises the stream.
+ * Errors: ARG (NULL, reps out of range, fp32 not 0/1), STATE (during graph capture), CUDA.
+ */
+kfbi_status kfbi_time_column(kfbi_ctx* ctx, int fp32, int reps, double* us_per_launch);
 
 /*
  * kfbi_alu_peak -- measured fused multiply-add throughput of this GPU, the denominator of the

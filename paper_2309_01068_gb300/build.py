@@ -14,7 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkfbi.so")
-SOURCES = ["kfbi_api.cu", "kfbi_geometry.cu", "kfbi_apply.cu", "kfbi_gmres.cu", "kfbi_step.cu", "kfbi_mlp.cu", "kfbi_batch.cu", "kfbi_gemm.cu"]
+SOURCES = ["kfbi_api.cu", "kfbi_geometry.cu", "kfbi_apply.cu", "kfbi_colfft.cu", "kfbi_gmres.cu", "kfbi_step.cu", "kfbi_mlp.cu",
+           "kfbi_batch.cu", "kfbi_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -40,6 +41,7 @@ def build(jobs=None, verbose=False, force=False):
     """Compile every .cu translation unit in parallel and link libkfbi.so."""
     os.makedirs(BUILD, exist_ok=True)
     deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "kfbi_internal.cuh"), os.path.join(CSRC, "kfbi_fft.cuh"), os.path.join(CSRC, "kfbi_tc.cuh"),
+                                                       os.path.join(CSRC, "kfbi_dct.cuh"),
                                                        os.path.join(ROOT, "include", "kfbi.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)

@@ -21,6 +21,7 @@
 #include <type_traits>
 #include <utility>
 
+#include "kfbi_dct.cuh"
 #include "kfbi_fft.cuh"
 #include "kfbi_internal.cuh"
 
@@ -32,8 +33,6 @@ __device__ __forceinline__ T wsum(T v) {
   return v;
 }
 
-__device__ __forceinline__ float fdiv_t(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double fdiv_t(double a, double b) { return a / b; }
 template <typename T>
 __device__ __forceinline__ T qnan();
 template <>
@@ -71,15 +70,6 @@ struct Tabs<float> {
   static const V2<float>* tstart(const kfbi_ctx* c) { return (const V2<float>*)c->tstart_f; }
   static const float4* npack(const kfbi_ctx* c) { return (const float4*)c->npack_f; }
 };
-
-// sin(pi m / (2N)) for an integer m (4N-periodic): the table in float64; in float32 the SFU
-// sine after exact integer reduction of the argument to (-pi, pi] (absolute error < 4e-7)
-__device__ __forceinline__ double tsin(const double* tab, int m, int N, float) { return tab[m & (4 * N - 1)]; }
-__device__ __forceinline__ float tsin(const float*, int m, int N, float scale) {
-  int r = m & (4 * N - 1);
-  if (r > 2 * N) r -= 4 * N;
-  return __sinf((float)r * scale);
-}
 
 // per-type fields of an irregular node
 __device__ __forceinline__ double irr_d(const IrrNode& q, int a, double) { return q.d[a]; }
@@ -556,49 +546,10 @@ __global__ void k_box_gemv(const T* K, int ld, const T* phi, int n, int rows, T*
   if (lane == 0) boxg[w] = s;
 }
 
-// position of sample j in the Makhoul reordering v[n] = x[2n], v[N-1-n] = x[2n+1]
-__device__ __forceinline__ int mk_pos(int j, int N) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
-
-// pi / (2N) in float32, the argument unit of tsin
-__device__ __forceinline__ float qscale(int N) { return 1.57079632679489662f / (float)N; }
-
 // copies the staged twiddles to shared memory (before the block's first __syncthreads)
 template <typename T>
 __device__ __forceinline__ void stage_twiddles(const V2<T>* tw, V2<T>* sTw, int cnt) {
   for (int t = threadIdx.x; t < cnt; t += blockDim.x) sTw[t] = tw[t];
-}
-
-// DCT-II from the FFT of the reordered pair (sequence a in .x, b in .y), at m and N - m:
-// V_a[m] = (Z[m] + conj Z[N-m]) / 2, V_b[m] = (Z[m] - conj Z[N-m]) / (2i),
-// X'[m] = Re(e^{-i pi m / (2N)} V[m]); V[N-m] = conj V[m] for each real sequence.
-// For DST-II the caller stored (-1)^j x_j and mode l is DCT index N-1-l.
-// (c, s) = (cos, sin)(pi m / (2N)); the rotation at N - m is (sin, cos) of the same angle.
-template <typename T>
-__device__ __forceinline__ void dct_post(const V2<T>* z, int N, int m, T c, T s, V2<T>& Xm, V2<T>& XNm) {
-  V2<T> Z = z[m];
-  V2<T> Zr = z[(N - m) & (N - 1)];
-  V2<T> Va{(T)0.5 * (Z.x + Zr.x), (T)0.5 * (Z.y - Zr.y)};
-  V2<T> Vb{(T)0.5 * (Z.y + Zr.y), (T)-0.5 * (Z.x - Zr.x)};
-  Xm = V2<T>{c * Va.x + s * Va.y, c * Vb.x + s * Vb.y};
-  XNm = V2<T>{s * Va.x - c * Va.y, s * Vb.x - c * Vb.y};
-}
-
-// inverse of dct_post: V[m] = e^{i pi m/(2N)} (G[m] - i G[N-m]) per sequence, packed a + i b
-template <typename T>
-__device__ __forceinline__ void dct_pre(int N, int m, T c, T s, V2<T> Gm, V2<T> GNm, V2<T>& Zm, V2<T>& ZNm) {
-  V2<T> Va{c * Gm.x + s * GNm.x, s * Gm.x - c * GNm.x};
-  V2<T> Vb{c * Gm.y + s * GNm.y, s * Gm.y - c * GNm.y};
-  Zm = V2<T>{Va.x - Vb.y, Va.y + Vb.x};
-  V2<T> Wa{s * GNm.x + c * Gm.x, c * GNm.x - s * Gm.x};
-  V2<T> Wb{s * GNm.y + c * Gm.y, c * GNm.y - s * Gm.y};
-  ZNm = V2<T>{Wa.x - Wb.y, Wa.y + Wb.x};
-}
-
-// (cos, sin)(pi m / (2N)) from the sine table (float64) or the SFU (float32)
-template <typename T>
-__device__ __forceinline__ void dct_cs(const T* tab, int N, int m, T& c, T& s) {
-  c = tsin(tab, m + N, N, qscale(N));
-  s = tsin(tab, m, N, qscale(N));
 }
 
 // --------------------------------------------------------------------------- face rows
@@ -965,91 +916,6 @@ static ColKernel<T> col_kernel(int logN) {
 // DCT/DST post- and pre-processing pairs bin m with bin N - m, which another lane of the group
 // holds: one shuffle per register brings it over.
 
-// sine and cosine of 2 pi k / M for compile-time k, M (Taylor series after reduction to
-// [-pi, pi]; evaluated by the compiler)
-constexpr double CT_PI = 3.14159265358979323846;
-constexpr double ct_angle(int k, int M) {
-  int r = k % M;
-  if (2 * r > M) r -= M;
-  return 2.0 * CT_PI * (double)r / (double)M;
-}
-constexpr double ct_sin(double x) {
-  double t = x, s = x;
-  for (int i = 1; i < 24; ++i) {
-    t = -t * x * x / ((2.0 * i) * (2.0 * i + 1.0));
-    s += t;
-  }
-  return s;
-}
-constexpr double ct_cos(double x) {
-  double t = 1.0, s = 1.0;
-  for (int i = 1; i < 24; ++i) {
-    t = -t * x * x / ((2.0 * i - 1.0) * (2.0 * i));
-    s += t;
-  }
-  return s;
-}
-
-using V2f = V2<float>;
-
-// b times e^{-2 pi i K / M} (forward) or e^{+2 pi i K / M} (inverse), K and M constants
-template <int K, int M, bool INV>
-__device__ __forceinline__ V2f ct_twiddle(V2f b) {
-  if constexpr (K % M == 0) {
-    return b;
-  } else if constexpr (4 * (K % M) == M) {
-    return INV ? V2f{-b.y, b.x} : V2f{b.y, -b.x};
-  } else if constexpr (2 * (K % M) == M) {
-    return V2f{-b.x, -b.y};
-  } else {
-    constexpr float c = (float)ct_cos(ct_angle(K, M));
-    constexpr float s = (float)(INV ? ct_sin(ct_angle(K, M)) : -ct_sin(ct_angle(K, M)));
-    return V2f{b.x * c - b.y * s, b.x * s + b.y * c};
-  }
-}
-
-// one radix-2 Stockham stage of span NS on R points held in registers: item j takes x[j] and
-// x[j + R/2], multiplies the second by w^{(j mod NS)} (w = e^{-+ 2 pi i / (2 NS)}) and writes the
-// sum and difference to y[(j / NS) 2 NS + j mod NS] and the same + NS
-template <int R, int NS, bool INV, int J>
-__device__ __forceinline__ void rg_bfly(const V2f (&x)[R], V2f (&y)[R]) {
-  constexpr int jm = J % NS;
-  constexpr int o = (J / NS) * 2 * NS + jm;
-  const V2f a = x[J];
-  const V2f b = ct_twiddle<jm, 2 * NS, INV>(x[J + R / 2]);
-  y[o] = V2f{a.x + b.x, a.y + b.y};
-  y[o + NS] = V2f{a.x - b.x, a.y - b.y};
-}
-template <int R, int NS, bool INV, int... J>
-__device__ __forceinline__ void rg_stage(const V2f (&x)[R], V2f (&y)[R], std::integer_sequence<int, J...>) {
-  (rg_bfly<R, NS, INV, J>(x, y), ...);
-}
-// length-R DFT (R a power of two) of the points x[0..R) in place, natural order in and out
-template <int R, bool INV, int NS = 1>
-__device__ __forceinline__ void rg_dft(V2f (&x)[R]) {
-  if constexpr (NS < R) {
-    V2f y[R];
-    rg_stage<R, NS, INV>(x, y, std::make_integer_sequence<int, R / 2>{});
-#pragma unroll
-    for (int i = 0; i < R; ++i) x[i] = y[i];
-    rg_dft<R, INV, 2 * NS>(x);
-  }
-}
-// the same on the sub-array x[O .. O + R) of a longer register array
-template <int R, bool INV, int O, int L>
-__device__ __forceinline__ void rg_dft_at(V2f (&x)[L]) {
-  V2f t[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) t[i] = x[O + i];
-  rg_dft<R, INV>(t);
-#pragma unroll
-  for (int i = 0; i < R; ++i) x[O + i] = t[i];
-}
-template <int R, bool INV, int L, int... Q>
-__device__ __forceinline__ void rg_dft_each(V2f (&x)[L], std::integer_sequence<int, Q...>) {
-  (rg_dft_at<R, INV, Q * R, L>(x), ...);
-}
-
 // grid split of the register column kernel: N = A B, A = 2^ceil(logN / 2) points per lane,
 // B = 2^floor(logN / 2) lanes per column pair, F column pairs (F B threads) per block
 template <int LOGN>
@@ -1064,9 +930,6 @@ struct ColRegPlan {
   static constexpr size_t SMEM = sizeof(V2f) * ((size_t)N + (N / 2 + 1) + (size_t)N + (size_t)F * TPAD) +
                                  sizeof(float) * (size_t)N;
 };
-
-// row of the spectral grid that Makhoul position p holds (inverse of mk_pos)
-__device__ __forceinline__ int mk_row(int p, int N) { return p < N / 2 ? 2 * p : 2 * N - 1 - 2 * p; }
 
 template <int LOGN>
 __global__ void __launch_bounds__(ColRegPlan<LOGN>::THREADS) k_col_solve_reg(int dct, const V2f* twN, const float* tab,
@@ -1518,6 +1381,15 @@ static kfbi_status launch_col_tc(kfbi_ctx* c, float* spec) {
   return KFBI_OK;
 }
 
+// the column solve runs the register-resident radix-16 kernel (kfbi_colfft.cu) unless a
+// tensor-core, four-step register or radix-4 form is selected, or N < 32
+template <typename T>
+static bool col_uses_fft16(const kfbi_ctx* c) {
+  if (!col_fft_supported(c->logN, sizeof(T) == 4)) return false;
+  if (sizeof(T) == 4) return !c->col_tc && !c->col_reg && (c->col_radix4 & 1) == 0;
+  return (c->col_radix4 & 2) == 0;
+}
+
 template <typename T>
 static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const V2<T>* rowinfo, const int* skip) {
   const int N = c->N;
@@ -1534,6 +1406,8 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const V2<T>* rowinfo, 
   if (tcp) {
     KFBI_CHECK(launch_col_tc(c, (float*)spec));
     launched(c, 1);  // two launches: one more than the single column kernel counted below
+  } else if (col_uses_fft16<T>(c)) {
+    KFBI_CHECK(col_fft_launch(c, sizeof(T) == 4, spec, rowinfo, skip, c->use_pdl && !rec));
   } else if (rk != nullptr) {
     KFBI_TRY(launch_k(c->use_pdl && !rec, rk, dim3(N / (2 * rpairs)), dim3(rthreads), rsmem, c->stream,
                       (int)(c->boxbc == KFBI_BOX_NEUMANN0), (const V2f*)Tabs<float>::twN(c), Tabs<float>::sin(c),
@@ -1552,6 +1426,32 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const V2<T>* rowinfo, 
     c->timing_used += 1;
   }
   return KFBI_OK;
+}
+
+// back-to-back column solves on the context's spectral grid (see kfbi_time_column)
+static kfbi_status time_column(kfbi_ctx* c, bool fp32, int reps, double* us) {
+  const auto one = [&]() -> kfbi_status {
+    if (fp32) {
+      const V2<float>* ri = !c->col_tc ? (const V2<float>*)c->rowinfo : nullptr;
+      return launch_col_solve<float>(c, (float*)c->spec, ri, c->zero_flag);
+    }
+    const V2<double>* ri = col_uses_fft16<double>(c) ? (const V2<double>*)c->rowinfo : nullptr;
+    return launch_col_solve<double>(c, c->spec, ri, c->zero_flag);
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KFBI_TRY(cudaEventCreate(&e0));
+  kfbi_status st = cudaEventCreate(&e1) == cudaSuccess ? KFBI_OK : KFBI_ERR_CUDA;
+  if (st == KFBI_OK) st = one();  // warm-up: tables and grid in L2
+  if (st == KFBI_OK && cudaEventRecord(e0, c->stream) != cudaSuccess) st = KFBI_ERR_CUDA;
+  for (int i = 0; i < reps && st == KFBI_OK; ++i) st = one();
+  if (st == KFBI_OK && cudaEventRecord(e1, c->stream) != cudaSuccess) st = KFBI_ERR_CUDA;
+  float ms = 0.f;
+  if (st == KFBI_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    st = KFBI_ERR_CUDA;
+  if (st == KFBI_OK) *us = 1e3 * (double)ms / reps;
+  cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return st;
 }
 
 template <typename T>
@@ -1579,9 +1479,10 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   T* boxg = (T*)c->boxg;
   T* face = (T*)c->facespec;
   T* spec = (T*)c->spec;
-  // rows without irregular nodes left to the column kernel: float32 applies only (the
-  // tensor-core column solve reads whole rows, so the row transform writes them all)
-  V2<T>* rowinfo = (sizeof(T) == 4 && !c->col_tc) ? (V2<T>*)c->rowinfo : nullptr;
+  // rows without irregular nodes left to the column kernel: float32 applies, and float64
+  // applies whose column solve is the radix-16 kernel (the tensor-core column solve reads
+  // whole rows, so the row transform writes them all)
+  V2<T>* rowinfo = ((sizeof(T) == 4 && !c->col_tc) || col_uses_fft16<T>(c)) ? (V2<T>*)c->rowinfo : nullptr;
   T* J = (T*)c->jumps;
   // the density integral of the Hele-Shaw operator, in the apply's type (float64 slot 0 or a
   // float32 slot in the same buffer)
@@ -1743,6 +1644,7 @@ kfbi_status apply_setup_attributes(kfbi_ctx* c) {
   KFBI_TRY(cudaFuncSetAttribute(k_box_face_table, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(3 * sizeof(V2<double>) * (size_t)MAX_GRID_N)));
   KFBI_CHECK(setup_t<double>(c));
+  KFBI_CHECK(col_fft_setup_attributes());
   return setup_t<float>(c);
 }
 
@@ -1917,6 +1819,19 @@ static kfbi_status grid_solve_noalloc_impl(int N, double h, double kappa, int bo
 }
 
 }  // namespace kfbi
+
+extern "C" kfbi_status kfbi_time_column(kfbi_ctx* c, int fp32, int reps, double* us_per_launch) {
+  if (c == nullptr || us_per_launch == nullptr || reps < 1 || reps > 100000 || (fp32 != 0 && fp32 != 1))
+    return KFBI_ERR_ARG;
+  if (c->capturing) return KFBI_ERR_STATE;
+  const bool tm = c->timing;
+  c->timing = false;  // no per-launch events between the solves
+  KFBI_TRY(kfbi::stream_enter(c));
+  kfbi_status st = kfbi::time_column(c, fp32 != 0, reps, us_per_launch);
+  c->timing = tm;
+  KFBI_TRY(kfbi::stream_exit(c));
+  return st;
+}
 
 extern "C" kfbi_status kfbi_grid_solve_noalloc(int N, double h, double kappa, int boxbc, const double* rhs, double* u,
                                                void* stream) {

@@ -310,8 +310,10 @@ kfbi_status kfbi_batch_solve(kfbi_batch* b, int kind, const double* const* rhs, 
 }
 
 // Coordinate search over the launch shapes of each grid size N in the batch: the Gram-Schmidt
-// form (16-CTA cluster, 8-CTA cluster, five kernels) and the column pairs per block of the
-// float32 column transform (1, 2, 4). Each candidate is applied to every instance of that N
+// form (16-CTA cluster, 8-CTA cluster, five kernels), the column pairs per block of the column
+// transform (the kernel's default, 1, 2, 4) and, in the mixed form, the float32 column kernel
+// (radix-16, four-step register FFTs, tensor-core contractions, radix-4). Each candidate is
+// applied to every instance of that N
 // and timed on the whole batch solve (second of two launches, so graph building is not
 // timed); the fastest is kept. The solves run on scratch densities starting from zero.
 kfbi_status kfbi_batch_autotune(kfbi_batch* b, int kind, const double* const* rhs, double tol, int max_iter,
@@ -356,10 +358,10 @@ kfbi_status kfbi_batch_autotune(kfbi_batch* b, int kind, const double* const* rh
   };
   float cur = 0.0f;
   if (st == KFBI_OK) st = run(&cur);
-  const int forms[3] = {0, 1, 2}, pairs[3] = {1, 2, 4};
+  const int forms[3] = {0, 1, 2}, pairs[4] = {0, 1, 2, 4};
   for (auto& kv : classes) {
     if (st != KFBI_OK) break;
-    int best_form = 0, best_pairs = 2;
+    int best_form = 0, best_pairs = 0;
     apply(kv.second, best_form, best_pairs);
     if ((st = run(&cur)) != KFBI_OK) break;
     for (int f : forms) {
@@ -383,8 +385,9 @@ kfbi_status kfbi_batch_autotune(kfbi_batch* b, int kind, const double* const* rh
       }
     }
     apply(kv.second, best_form, best_pairs);
-    // the float32 column transform: shared-memory FFT (0), register FFTs (1, N <= 1024) or the
-    // tensor-core contractions (2, N <= 256); only the mixed form runs float32 applies
+    // the float32 column transform: radix-16 register-resident kernel (0), four-step register
+    // FFTs (1, N <= 1024), tensor-core contractions (2, N <= 256) or the radix-4 shared-memory
+    // kernel (3); only the mixed form runs float32 applies
     if (b->precision == KFBI_MIXED && st == KFBI_OK) {
       auto apply_col = [&](int cf) {
         for (int i : kv.second) {
@@ -392,11 +395,12 @@ kfbi_status kfbi_batch_autotune(kfbi_batch* b, int kind, const double* const* rh
           if (cf == 2 && kfbi_set_option(c, KFBI_OPT_COL_TC, 1) != KFBI_OK) return false;
           if (cf != 2) kfbi_set_option(c, KFBI_OPT_COL_TC, 0);
           kfbi_set_option(c, KFBI_OPT_COL_REG, cf == 1 ? 1 : 0);
+          kfbi_set_option(c, KFBI_OPT_COL_RADIX4, cf == 3 ? 3 : 2);
         }
         return true;
       };
       int best_cf = 0;
-      for (int cf = 1; cf <= 2 && st == KFBI_OK; ++cf) {
+      for (int cf = 1; cf <= 3 && st == KFBI_OK; ++cf) {
         if ((cf == 1 && kv.first > 1024) || (cf == 2 && kv.first > COL_TC_MAX_N)) continue;
         if (!apply_col(cf)) continue;
         float t = 0.0f;

@@ -367,6 +367,7 @@ struct kfbi_ctx {
   int col_P = 0;                // column pairs per block of the float32 column kernel (0 automatic)
   bool col_tc = false;          // float32 column solve as two tensor-core contractions (N <= 256), KFBI_OPT_COL_TC
   bool col_reg = false;         // float32 column solve with register FFTs (N <= 1024), KFBI_OPT_COL_REG
+  int col_radix4 = 2;           // KFBI_OPT_COL_RADIX4: bit 0 (float32) / bit 1 (float64) select the radix-4 kernel
   int body_cap_set = 0;         // GMRES loop body cap (0: derived from max_iter), KFBI_OPT_BODY_CAP
   int sweep_cap_set = 0;        // refinement loop body cap (0: sweeps + 2), KFBI_OPT_SWEEP_CAP
   int cfg_version = 0;          // bumped by every option that changes the launched kernels
@@ -509,6 +510,14 @@ kfbi_status tc_gemm(const TcGemmArgs& g, cudaStream_t s);
 // the tensor-core column solve's matrices and buffers (kfbi_apply.cu), for N <= COL_TC_MAX_N
 constexpr int COL_TC_MAX_N = 256;
 kfbi_status col_tc_setup(kfbi_ctx* c);
+
+// the column solve with register-resident radix-16 FFTs (kfbi_colfft.cu), 32 <= N <= 4096
+// (float64 up to 2048: larger tables do not fit one block's shared memory):
+// float32 (fp32) or float64 spectral grid `spec`, rows the row transform left out in `rowinfo`
+// (or nullptr), launched on c->stream with programmatic dependent launch when pdl is set
+bool col_fft_supported(int logN, bool fp32);
+kfbi_status col_fft_launch(kfbi_ctx* c, bool fp32, void* spec, const void* rowinfo, const int* skip, bool pdl);
+kfbi_status col_fft_setup_attributes();
 
 // host-side helpers implemented in the .cu files
 kfbi_status ensure_cross_capacity(kfbi_ctx* c, int n_cross);

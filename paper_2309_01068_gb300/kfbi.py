@@ -24,7 +24,7 @@ OPT_FP32_ARNOLDI = 8
 OPT_PUSH_REDUCE = 9
 OPT_FUSE_INTERP = 10
 OPT_FUSE_DFT = 11
-OPT_BODY_CAP, OPT_SWEEP_CAP, OPT_COL_REG, OPT_COL_TC = 12, 13, 14, 15
+OPT_BODY_CAP, OPT_SWEEP_CAP, OPT_COL_REG, OPT_COL_TC, OPT_COL_RADIX4 = 12, 13, 14, 15, 16
 MLP_FEATURES, MLP_MODES = 47, 16
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2
@@ -115,6 +115,7 @@ _SIGNATURES = {
     "kfbi_get_option": (_I, [_P, _I, ctypes.POINTER(_I)]),
     "kfbi_grid_solve_noalloc": (_I, [_I, _D, _D, _I, _P, _P, _P]),
     "kfbi_alu_peak": (_I, [_I, ctypes.POINTER(_D), _P]),
+    "kfbi_time_column": (_I, [_P, _I, _I, ctypes.POINTER(_D)]),
     "kfbi_tc_gemm": (_I, [_I, _I, _I, _P, ctypes.c_long, _I, _P, ctypes.c_long, _I, _P, ctypes.c_long, _I, _P, _P]),
     "kfbi_thetal_set_warmstart": (_I, [_P, _P]),
     "kfbi_thetal_count": (_I, [_P, ctypes.POINTER(_I)]),
@@ -313,6 +314,15 @@ class Context:
         _check(self.lib.kfbi_timing_read(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
                                          ctypes.byref(d)), "kfbi_timing_read")
         return dict(fp64_ms=a.value, fp64_launches=b.value, fp32_ms=c.value, fp32_launches=d.value)
+
+    def time_column(self, fp32=True, reps=200):
+        """kfbi_time_column: mean microseconds per column solve, `reps` launches back to back
+        (the spectral-grid scratch buffer is overwritten)."""
+        self._sync_stream()
+        v = ctypes.c_double()
+        _check(self.lib.kfbi_time_column(self.handle, 1 if fp32 else 0, int(reps), ctypes.byref(v)),
+               "kfbi_time_column")
+        return v.value
 
     def set_option(self, option, value):
         """kfbi_set_option: one of the OPT_* constants (values as the header states)."""

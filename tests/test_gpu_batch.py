@@ -88,7 +88,8 @@ def test_batch_autotune_choices_are_valid_and_results_unchanged():
     for c in b.contexts:
         assert c.get_option(K.OPT_CLUSTER_GMRES) in (0, 1)
         assert c.get_option(K.OPT_CLUSTER_SIZE) in (0, 8, 16)
-        assert c.get_option(K.OPT_COL_PAIRS) in (1, 2, 4)
+        assert c.get_option(K.OPT_COL_PAIRS) in (0, 1, 2, 4)
+        assert c.get_option(K.OPT_COL_RADIX4) in (2, 3)
     dens = [torch.zeros(p.n, dtype=torch.float64, device="cuda") for p in probs]
     st, infos = b.solve(K.BIE_INTERIOR_DL, rhs, dens, tol=1e-10, max_iter=400, restart=100)
     assert st == 0
