@@ -581,6 +581,34 @@ def stefan_leg(torch, K, steps=3, N=2048, n=2048, tol=1e-9, compare_fp64=True):
                 statuses=[i["status"] for i in infos], mixed_vs_fp64_one_step=err)
 
 
+def apply_forms_leg(torch, K, reps=300):
+    """Float32 apply of the Hele-Shaw 1024^2 workload with the row transform as its own kernel
+    (default) and formed inside the column kernel (KFBI_OPT_FUSE_ROWS): CUDA events around
+    `reps` applies back to back, warm L2."""
+    import workloads as W
+
+    p = W.config_hele_shaw()
+    ctx = K.Context(p.N, p.box, p.kappa, K.BOX_FREESPACE_DL, K.MIXED, max_nodes=p.n)
+    ctx.set_interface(torch.tensor(p.xy, dtype=torch.float64, device="cuda"))
+    dens = torch.tensor(W.random_density(3, p.n, modes=20), dtype=torch.float64, device="cuda")
+    vals = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    out = {}
+    for name, fr in (("separate_row_kernel", 0), ("rows_in_column_kernel", 1)):
+        ctx.set_option(K.OPT_FUSE_ROWS, fr)
+        for _ in range(20):
+            ctx.apply_into(K.DOUBLE, dens, vals)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            ctx.apply_into(K.DOUBLE, dens, vals)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = dict(us_per_apply=1e3 * e0.elapsed_time(e1) / reps)
+    ctx.close()
+    return out
+
+
 # column forms of the size sweep: (name, COL_RADIX4 bits, COL_PAIRS, COL_REG, COL_TC)
 COL_FORMS = (("radix16", 0, 0, 0, 0), ("radix16_p1", 0, 1, 0, 0), ("radix16_p2", 0, -2, 0, 0), ("radix4", 3, 0, 0, 0),
              ("radix4_p1", 3, 1, 0, 0), ("radix4_p4", 3, 4, 0, 0), ("register", 0, 0, 1, 0),
@@ -965,6 +993,7 @@ def main():
     extras = {}
     if rank == 0 and not args.profile and not args.no_extras:
         for name, leg in (("col_kernel_sizes", lambda: col_kernel_sizes(torch, K, hbm_peak)),
+                          ("apply_forms", lambda: apply_forms_leg(torch, K)),
                           ("batched", lambda: batched_leg(torch, K, flush)), ("warm_start", lambda: warmstart_leg(torch, K)),
                           ("stefan", lambda: stefan_leg(torch, K)),
                           ("warm_start_c5", lambda: warm_start_c5_leg(torch, K)),

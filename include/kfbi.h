@@ -371,6 +371,18 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             shared-memory buffer). Bit 0 set (1, 3): float32 applies run the
  *                             radix-4 kernel; bit 1 clear (0, 1): float64 applies run the
  *                             radix-16 kernel. Values 0..3.
+ *   KFBI_OPT_FUSE_ROWS        0 (default): the row transform is its own kernel. 1: float32
+ *                             applies whose jumps come from the fused jump kernel
+ *                             (KFBI_OPT_FUSE_DFT) and whose column solve is the radix-16 kernel
+ *                             form the row transform inside the column kernel: the jump kernel
+ *                             writes each crossed arm's correction, and the column kernel sums,
+ *                             for each of its rows, the corrections of the row's irregular nodes
+ *                             times the DST/DCT basis functions of its columns (tabulated in
+ *                             shared memory before the wait for the jump kernel), plus the box
+ *                             data; the row-transform kernel is not launched. Applies when the
+ *                             node capacity fits the column kernel's shared memory. Measured
+ *                             slower on the Hele-Shaw 1024^2 workload (37.2 against 32.7 us per
+ *                             float32 apply), hence off by default.
  *   KFBI_OPT_COL_REG          0 (default); 1 (grids with N <= 1024): the float32 column solve
  *                             holds every FFT in registers by one group of B lanes (an A-point
  *                             DFT per lane, one transpose through shared memory, B-point DFTs;
@@ -412,7 +424,8 @@ enum {
   KFBI_OPT_SWEEP_CAP = 13,
   KFBI_OPT_COL_REG = 14,
   KFBI_OPT_COL_TC = 15,
-  KFBI_OPT_COL_RADIX4 = 16
+  KFBI_OPT_COL_RADIX4 = 16,
+  KFBI_OPT_FUSE_ROWS = 17
 };
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);

@@ -80,6 +80,8 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
   cudaFree(c->cr_kind); cudaFree(c->cr_line); cudaFree(c->cr_seg); cudaFree(c->cr_first);
   cudaFree(c->cr_alpha); cudaFree(c->cr_xi); cudaFree(c->tgeo); cudaFree(c->tgeo_f); cudaFree(c->irr);
   cudaFree(c->tstart); cudaFree(c->tstart_f); cudaFree(c->jumps);
+  cudaFree(c->irr_ci); cudaFree(c->arm_slot); cudaFree(c->arm_rev); cudaFree(c->arm_coef);
+  c->irr_ci = nullptr; c->arm_slot = nullptr; c->arm_rev = nullptr; c->arm_coef = nullptr;
   c->cr_kind = c->cr_line = c->cr_seg = c->cr_first = nullptr;
   c->cr_alpha = c->cr_xi = nullptr;
   c->tgeo = nullptr; c->tgeo_f = nullptr; c->irr = nullptr;
@@ -95,6 +97,10 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
   KFBI_CHECK(dalloc(&c->tgeo_f, (size_t)cap + c->max_nodes));
   int cap_irr = 2 * cap + 64;
   KFBI_CHECK(dalloc(&c->irr, cap_irr));
+  KFBI_CHECK(dalloc(&c->irr_ci, cap_irr));
+  KFBI_CHECK(dalloc(&c->arm_slot, 4 * (size_t)cap_irr));
+  KFBI_CHECK(dalloc(&c->arm_rev, 2 * (size_t)cap));
+  KFBI_CHECK(dalloc(&c->arm_coef, 4 * (size_t)cap));
   KFBI_CHECK(dalloc(&c->tstart, 2 * (size_t)TSTART_STRIDE * ((size_t)cap + c->max_nodes)));
   KFBI_CHECK(dalloc(&c->tstart_f, 2 * (size_t)TSTART_STRIDE * ((size_t)cap + c->max_nodes)));
   KFBI_CHECK(dalloc(&c->jumps, 6 * ((size_t)cap + c->max_nodes)));
@@ -112,7 +118,8 @@ static void free_all(kfbi_ctx* c) {
                   c->boxg, c->facespec, c->spec, c->rowinfo, c->twn_f, c->tstart, c->tstart_f, c->jumps, c->npack, c->boxK, c->boxK_f,
                   c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gVf, c->gpart, c->gw,
                   c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag, c->irctl, c->ir_b, c->ir_x, c->ir_dn,
-                  c->col_fwd, c->col_inv, c->col_tmp, c->col_tc_err};
+                  c->col_fwd, c->col_inv, c->col_tmp, c->col_tc_err, c->irr_ci, c->arm_slot, c->arm_rev,
+                  c->arm_coef};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->host_counts) cudaFreeHost(c->host_counts);
@@ -506,6 +513,8 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
     c->fuse_interp = value != 0;
   } else if (option == KFBI_OPT_FUSE_DFT) {
     c->fuse_dft = value != 0;
+  } else if (option == KFBI_OPT_FUSE_ROWS) {
+    c->fuse_rows = value != 0;
   } else if (option == KFBI_OPT_COL_REG) {
     c->col_reg = value != 0;
   } else if (option == KFBI_OPT_COL_TC) {
@@ -547,6 +556,7 @@ kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
   else if (option == KFBI_OPT_COL_REG) *value = c->col_reg ? 1 : 0;
   else if (option == KFBI_OPT_COL_TC) *value = c->col_tc ? 1 : 0;
   else if (option == KFBI_OPT_COL_RADIX4) *value = c->col_radix4;
+  else if (option == KFBI_OPT_FUSE_ROWS) *value = c->fuse_rows ? 1 : 0;
   else if (option == KFBI_OPT_BODY_CAP) *value = c->body_cap_set;
   else if (option == KFBI_OPT_SWEEP_CAP) *value = c->sweep_cap_set;
   else return KFBI_ERR_ARG;

@@ -311,7 +311,8 @@ constexpr int JFFT_PER = 4096 / JFFT_THREADS;  // density values per thread at m
 template <typename G, typename S_t>
 __global__ void __launch_bounds__(JFFT_THREADS)
     k_jumps_fft(const float* phi, int n, int logn, const V2<float>* twn, const S_t* st, float* dint, const int* ncr,
-                const G* tg, const V2<float>* tstart, int layer, float kappa, float* Jout, const int* skip) {
+                const G* tg, const V2<float>* tstart, int layer, float kappa, float* Jout, const int* arm_rev,
+                const float2* arm_coef, float* arm_slot, const int* skip) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ float red[JFFT_THREADS / 32];
   const int L = jfft_buf(n);
@@ -330,12 +331,20 @@ __global__ void __launch_bounds__(JFFT_THREADS)
   // node roots, and (block 0) the arclength weights of the density integral
   G geo{};
   V2<float> e0{}, s1{}, q{};
+  // the arm this lane corrects (lanes 0, 1 of a crossing's warp; arm_slot set: the column
+  // kernel forms the row transform from these corrections)
+  int arm = -1;
+  float2 acoef{0.f, 0.f};
   if (t < ntg) {
     geo = tg[t];
     const V2<float>* ts = tstart + (long)t * TSTART_STRIDE;
     e0 = ts[lane];
     s1 = ts[32];
     q = ts[33];
+    if (arm_slot != nullptr && lane < 2 && t < *ncr) {
+      arm = arm_rev[2 * t + lane];
+      if (arm >= 0) acoef = arm_coef[2 * t + lane];
+    }
   }
   const int cnt = staged_count(n, logn);
   for (int i = threadIdx.x; i < cnt; i += JFFT_THREADS) {
@@ -402,6 +411,12 @@ __global__ void __launch_bounds__(JFFT_THREADS)
 #pragma unroll
   for (int r = 4; r >= 0; --r) o = lane == r ? J[r] : o;
   if (lane < 6) Jout[(long)t * 6 + lane] = o;
+  // the arm's correction sign / h^2 (J0 + d J1 + d^2 J2 / 2), J1, J2 the derivatives along it
+  if (arm >= 0) {
+    const bool xarm = (arm & 3) < 2;
+    const float d = acoef.x;
+    arm_slot[arm] = acoef.y * (J[0] + d * (xarm ? J[1] : J[2]) + 0.5f * d * d * (xarm ? J[3] : J[4]));
+  }
 }
 
 // Free-space box data (Sec. 4.1): g(p) = (1/n) sum_l phi_l (X_l - p).(y_a, -x_a)_l / |X_l - p|^2
@@ -1391,7 +1406,8 @@ static bool col_uses_fft16(const kfbi_ctx* c) {
 }
 
 template <typename T>
-static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const V2<T>* rowinfo, const int* skip) {
+static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const V2<T>* rowinfo, const int* skip,
+                                    const RowSrc* rows = nullptr) {
   const int N = c->N;
   const bool rec = c->timing && !c->capturing && c->timing_used < TIMING_CAP;
   if (rec) KFBI_TRY(cudaEventRecord(c->tev[2 * c->timing_used], c->stream));
@@ -1407,7 +1423,7 @@ static kfbi_status launch_col_solve(kfbi_ctx* c, T* spec, const V2<T>* rowinfo, 
     KFBI_CHECK(launch_col_tc(c, (float*)spec));
     launched(c, 1);  // two launches: one more than the single column kernel counted below
   } else if (col_uses_fft16<T>(c)) {
-    KFBI_CHECK(col_fft_launch(c, sizeof(T) == 4, spec, rowinfo, skip, c->use_pdl && !rec));
+    KFBI_CHECK(col_fft_launch(c, sizeof(T) == 4, spec, rowinfo, skip, c->use_pdl && !rec, rows));
   } else if (rk != nullptr) {
     KFBI_TRY(launch_k(c->use_pdl && !rec, rk, dim3(N / (2 * rpairs)), dim3(rthreads), rsmem, c->stream,
                       (int)(c->boxbc == KFBI_BOX_NEUMANN0), (const V2f*)Tabs<float>::twN(c), Tabs<float>::sin(c),
@@ -1543,14 +1559,20 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
   using SD = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(c))>::type>::type;
   bool fused = false;
+  // float32 with the jump kernel and the radix-16 column kernel: the jump kernel also writes
+  // each crossed arm's correction and the column kernel forms the row transform itself (no
+  // row-transform launch, no write and re-read of the spectral grid between them)
+  bool rows_in_col = false;
   if constexpr (sizeof(T) == 4) {
     // float32, power-of-two n: coefficients and jumps in one kernel
     if (c->fuse_dft && n >= 16 && n <= 4096 && (n & (n - 1)) == 0) {
+      rows_in_col = c->fuse_rows && col_uses_fft16<T>(c) && col_fft_rows_fit(c);
       const int logn = ilog2(n);
       KFBI_TRY(launch_k(c->use_pdl, k_jumps_fft<G, SD>, dim3(cdiv((long)ntg_cap * 32, JFFT_THREADS)),
                         dim3(JFFT_THREADS), jfft_smem(n, logn), s, (const float*)dens_t, n, logn, Tabs<T>::twn(c),
                         Tabs<T>::stencil(c), (float*)(want_int ? dint_t : nullptr), d_ncr, Tabs<T>::geo(c),
-                        Tabs<T>::tstart(c), layer, (float)c->kappa, (float*)J, skip));
+                        Tabs<T>::tstart(c), layer, (float)c->kappa, (float*)J, (const int*)c->arm_rev,
+                        (const float2*)c->arm_coef, rows_in_col ? c->arm_slot : nullptr, skip));
       launched(c, 1);
       fused = true;
     }
@@ -1575,11 +1597,21 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     launched(c, 2);
   }
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
-  KFBI_TRY(launch_k(c->use_pdl, k_row_forward<T>, dim3(N), dim3(ROW_THREADS), 0, s, N, dct, (const int*)c->row_ptr,
-                    (const IrrNode*)c->irr, (const T*)J, (T)(1.0 / (c->h * c->h)), (const T*)(fs ? boxg : nullptr),
-                    (const T*)face, tab, scale, spec, rowinfo, skip));
-  launched(c, 1);
-  KFBI_CHECK(launch_col_solve<T>(c, spec, rowinfo, skip));
+  if (rows_in_col) {
+    RowSrc rs;
+    rs.row_ptr = c->row_ptr;
+    rs.ci = c->irr_ci;
+    rs.slot = (const float4*)c->arm_slot;
+    rs.boxg = fs ? (const float*)boxg : nullptr;
+    rs.face = fs ? (const float*)face : nullptr;
+    KFBI_CHECK(launch_col_solve<T>(c, spec, nullptr, skip, &rs));
+  } else {
+    KFBI_TRY(launch_k(c->use_pdl, k_row_forward<T>, dim3(N), dim3(ROW_THREADS), 0, s, N, dct, (const int*)c->row_ptr,
+                      (const IrrNode*)c->irr, (const T*)J, (T)(1.0 / (c->h * c->h)), (const T*)(fs ? boxg : nullptr),
+                      (const T*)face, tab, scale, spec, rowinfo, skip));
+    launched(c, 1);
+    KFBI_CHECK(launch_col_solve<T>(c, spec, rowinfo, skip));
+  }
   KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(cdiv((long)6 * n * 32, 256)), dim3(256), 0, s, N, dct,
                     (const int*)(c->prow_ptr + N), (const int*)c->probe_j, (const int*)c->probe_i, (const T*)spec, tab,
                     scale, pval, skip));

@@ -263,11 +263,19 @@ __device__ __forceinline__ void srange(F&& f) {
   }
 }
 
-template <typename T, int LOGN, int P>
+// FR (float32): the kernel forms its input rows itself instead of reading the row transform's
+// output: row j of column k is
+//   sum over the row's irregular nodes t of sv_t S_k(2 i_t + 1) + w_j S_k(0) + e_j S_k(N-1)
+//   (+ the face row's transform for j = 0, N - 1),
+// S_k the DST-II (DCT-II) basis function, sv_t the sum of node t's four arm corrections, (w_j,
+// e_j) the free-space box data of the row. The row pointers and column factors (fixed with the
+// interface) are staged before the wait for the jump kernel, the corrections and box data after.
+template <typename T, int LOGN, int P, bool FR>
 __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const V2<T>* __restrict__ twN,
                                                                 const T* __restrict__ tab, const T* __restrict__ lam,
                                                                 T kappa, T* spec, const T* __restrict__ rinv,
-                                                                const V2<T>* __restrict__ rowinfo, const int* skip) {
+                                                                const V2<T>* __restrict__ rowinfo, RowSrc rs,
+                                                                const int* skip) {
   using PL = FPlan<LOGN>;
   constexpr int N = PL::N, TH = PL::TH, RL = PL::RL, G = 16 / RL, NST = PL::NST, NSL = N / RL;
   constexpr int PS = pair_stride<T, N, P>();
@@ -278,6 +286,43 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
   V2<T>* sT = reinterpret_cast<V2<T>*>(col_fft_smem) + P * PS;  // stage twiddles
   V2<T>* sRow = sT + PL::TW;                                     // rowinfo[j], j < N
   T* sLam = reinterpret_cast<T*>(sRow + N);                      // lam[l], l < N
+  int* sRp = reinterpret_cast<int*>(sLam + N);                   // FR: row pointers [N + 1] (N + 2 slots)
+  float* sSv = reinterpret_cast<float*>(sRp + N + 2);            // FR: sv_t [cap], cap even
+  float* sTab = sSv + rs.cap;                                    // FR: the block's sines [tab][2P], 8-byte aligned
+  int nirr = 0;
+  if constexpr (FR) {
+    // row pointers, and for the first rs.tab nodes the sines of the block's 2P columns
+    // S_k(2 i_t + 1) (the rest are evaluated as the rows are formed)
+    for (int t = threadIdx.x; t <= N; t += P * TH) sRp[t] = __ldg(rs.row_ptr + t);
+    nirr = __ldg(rs.row_ptr + N);
+    // node t's sines S_{kb + c}(ci), c < 2P: sin((kb + 1 + c) theta) (DST-II) or
+    // cos((kb + c) theta) (DCT-II), theta = pi ci / (2N), each from its exactly reduced integer
+    // argument (a rotation recurrence would cost float32 accuracy)
+    const int ntab = min(nirr, rs.tab);
+    const int kb = (int)blockIdx.x * (2 * P) + (dct ? 0 : 1);
+    const float qs = qscale(N);
+    constexpr int BATCH = 8;
+    for (int t0 = 0; t0 < ntab; t0 += BATCH * P * TH) {
+      int ci[BATCH];
+#pragma unroll
+      for (int i = 0; i < BATCH; ++i) {
+        const int t = t0 + (int)threadIdx.x + i * P * TH;
+        ci[i] = t < ntab ? __ldg(rs.ci + t) : 0;
+      }
+#pragma unroll
+      for (int i = 0; i < BATCH; ++i) {
+        const int t = t0 + (int)threadIdx.x + i * P * TH;
+        if (t < ntab) {
+          float v[2 * P];
+#pragma unroll
+          for (int c = 0; c < 2 * P; ++c) v[c] = tsin(tab, (kb + c) * ci[i] + (dct ? N : 0), N, qs);
+          float* dst = sTab + t * (2 * P);
+#pragma unroll
+          for (int c = 0; c < 2 * P; c += 2) *reinterpret_cast<float2*>(dst + c) = make_float2(v[c], v[c + 1]);
+        }
+      }
+    }
+  }
   // the tables (fixed with the context) go to shared memory before the wait for the row
   // transform; the first barrier below orders these writes before every read
   srange<1, NST>([&](auto si) { stage_table<T, LOGN, decltype(si)::value, P * TH>(twN, sT); });
@@ -300,7 +345,7 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
   const T* r1 = rinv != nullptr ? r0 + N : nullptr;
   // rows the row transform did not write (rowinfo): w S_k(0) + e S_k(N-1) for both columns
   V2<T> s0{(T)0, (T)0}, sN{(T)0, (T)0};
-  if (rowinfo != nullptr) {
+  if (rowinfo != nullptr || FR) {
     const float qs = qscale(N);
     if (dct) {
       s0 = V2<T>{tsin(tab, k0 + N, N, qs), tsin(tab, k0 + 1 + N, N, qs)};
@@ -316,15 +361,73 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
   // ---- stage 0: points u + r N/16 of the reordered pair (rows 2i for r < 8, 2N-1-2i above;
   // the DST takes (-1)^row of the odd rows)
   V2<T> x[16];
+  if constexpr (FR) {
+    // corrections and box data, once per block, then each of the thread's rows
+    for (int t0 = 0; t0 < nirr; t0 += 4 * P * TH) {
+      float4 v[4];
 #pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int i = u + r * TH;
-    const int row = r < 8 ? 2 * i : 2 * N - 1 - 2 * i;
-    x[r] = *reinterpret_cast<const V2<T>*>(spec + (long)row * N + k0);
+      for (int i = 0; i < 4; ++i) {
+        const int t = t0 + (int)threadIdx.x + i * P * TH;
+        if (t < nirr) v[i] = rs.slot[t];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int t = t0 + (int)threadIdx.x + i * P * TH;
+        if (t < nirr) sSv[t] = (v[i].x + v[i].y) + (v[i].z + v[i].w);
+      }
+    }
+    if (rs.boxg != nullptr)
+      for (int t = threadIdx.x; t < N; t += P * TH) sRow[t] = V2<T>{rs.boxg[t], rs.boxg[N + t]};
+    __syncthreads();
+    const float qs = qscale(N);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = u + r * TH;
+      const int row = r < 8 ? 2 * i : 2 * N - 1 - 2 * i;
+      T a0 = 0, a1 = 0;
+      const int e = sRp[row + 1];
+      const int et = min(e, rs.tab);
+      int t = sRp[row];
+      for (; t < et; ++t) {
+        const T sv = sSv[t];
+        const V2<T> sn = ld2(reinterpret_cast<const V2<T>*>(sTab + t * (2 * P) + 2 * p));
+        a0 += sv * sn.x;
+        a1 += sv * sn.y;
+      }
+      for (; t < e; ++t) {
+        const int ci = __ldg(rs.ci + t);
+        const T sv = sSv[t];
+        if (dct) {
+          a0 += sv * tsin(tab, k0 * ci + N, N, qs);
+          a1 += sv * tsin(tab, (k0 + 1) * ci + N, N, qs);
+        } else {
+          a0 += sv * tsin(tab, (k0 + 1) * ci, N, qs);
+          a1 += sv * tsin(tab, (k0 + 2) * ci, N, qs);
+        }
+      }
+      if (rs.boxg != nullptr) {
+        const V2<T> we = ld2(sRow + row);
+        a0 += we.x * s0.x + we.y * sN.x;
+        a1 += we.x * s0.y + we.y * sN.y;
+      }
+      if (rs.face != nullptr && (row == 0 || row == N - 1)) {
+        const T* f = rs.face + (row == 0 ? 0 : N);
+        a0 += f[k0];
+        a1 += f[k0 + 1];
+      }
+      x[r] = V2<T>{a0, a1};
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int i = u + r * TH;
+      const int row = r < 8 ? 2 * i : 2 * N - 1 - 2 * i;
+      x[r] = *reinterpret_cast<const V2<T>*>(spec + (long)row * N + k0);
+    }
   }
   // the rows' box-data pairs, once per block (the same for every column), while the column
   // loads are in flight
-  if (rowinfo != nullptr) {
+  if (!FR && rowinfo != nullptr) {
     constexpr int PER = (N + P * TH - 1) / (P * TH);
     V2<T> v[PER];
 #pragma unroll
@@ -342,7 +445,7 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
     V2<T> v = x[r];
-    if (rowinfo != nullptr) {
+    if (!FR && rowinfo != nullptr) {
       const int i = u + r * TH;
       const V2<T> ri = ld2(sRow + (r < 8 ? 2 * i : 2 * N - 1 - 2 * i));
       if (ri.x == ri.x) v = V2<T>{ri.x * s0.x + ri.y * sN.x, ri.x * s0.y + ri.y * sN.y};
@@ -434,18 +537,18 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
 
 template <typename T>
 struct FftSel {
-  void (*kernel)(int, const V2<T>*, const T*, const T*, T, T*, const T*, const V2<T>*, const int*) = nullptr;
+  void (*kernel)(int, const V2<T>*, const T*, const T*, T, T*, const T*, const V2<T>*, RowSrc, const int*) = nullptr;
   int threads = 0, pairs = 0;
-  size_t smem = 0;
+  size_t smem = 0;  // without the FR node arrays
 };
 
-template <typename T, int LOGN, int P>
+template <typename T, int LOGN, int P, bool FR>
 FftSel<T> fft_sel() {
   FftSel<T> s;
-  s.kernel = k_col_fft<T, LOGN, P>;
+  s.kernel = k_col_fft<T, LOGN, P, FR>;
   s.threads = P * FPlan<LOGN>::TH;
   s.pairs = P;
-  s.smem = fft_smem<T, LOGN, P>();
+  s.smem = fft_smem<T, LOGN, P>() + (FR ? sizeof(int) * ((1 << LOGN) + 2) : 0);
   return s;
 }
 
@@ -461,31 +564,36 @@ constexpr bool fft_fits() {
 }
 
 // the kernel for N = 2^logN with the largest instantiated pair count (PMIN, 2 PMIN, 4 PMIN) that
-// does not exceed `want`, or PMIN; no kernel when even PMIN does not fit
-template <typename T, int LOGN>
+// does not exceed `want`, or PMIN; no kernel when even PMIN does not fit. The FR form (rows
+// formed in the kernel) exists in float32 only.
+template <typename T, int LOGN, bool FR>
 FftSel<T> fft_sel_n(int want) {
   constexpr int P0 = pairs_min<LOGN>();
-  if constexpr (fft_fits<T, LOGN, 4 * P0>()) {
-    if (want >= 4 * P0) return fft_sel<T, LOGN, 4 * P0>();
+  if constexpr (FR && sizeof(T) != 4) {
+    return FftSel<T>{};
+  } else {
+    if constexpr (fft_fits<T, LOGN, 4 * P0>()) {
+      if (want >= 4 * P0) return fft_sel<T, LOGN, 4 * P0, FR>();
+    }
+    if constexpr (fft_fits<T, LOGN, 2 * P0>()) {
+      if (want >= 2 * P0) return fft_sel<T, LOGN, 2 * P0, FR>();
+    }
+    if constexpr (fft_fits<T, LOGN, P0>()) return fft_sel<T, LOGN, P0, FR>();
+    return FftSel<T>{};
   }
-  if constexpr (fft_fits<T, LOGN, 2 * P0>()) {
-    if (want >= 2 * P0) return fft_sel<T, LOGN, 2 * P0>();
-  }
-  if constexpr (fft_fits<T, LOGN, P0>()) return fft_sel<T, LOGN, P0>();
-  return FftSel<T>{};
 }
 
-template <typename T>
+template <typename T, bool FR>
 FftSel<T> fft_select(int logN, int want) {
   switch (logN) {
-    case 5: return fft_sel_n<T, 5>(want);
-    case 6: return fft_sel_n<T, 6>(want);
-    case 7: return fft_sel_n<T, 7>(want);
-    case 8: return fft_sel_n<T, 8>(want);
-    case 9: return fft_sel_n<T, 9>(want);
-    case 10: return fft_sel_n<T, 10>(want);
-    case 11: return fft_sel_n<T, 11>(want);
-    case 12: return fft_sel_n<T, 12>(want);
+    case 5: return fft_sel_n<T, 5, FR>(want);
+    case 6: return fft_sel_n<T, 6, FR>(want);
+    case 7: return fft_sel_n<T, 7, FR>(want);
+    case 8: return fft_sel_n<T, 8, FR>(want);
+    case 9: return fft_sel_n<T, 9, FR>(want);
+    case 10: return fft_sel_n<T, 10, FR>(want);
+    case 11: return fft_sel_n<T, 11, FR>(want);
+    case 12: return fft_sel_n<T, 12, FR>(want);
     default: return FftSel<T>{};
   }
 }
@@ -498,33 +606,71 @@ inline int fft_want(const kfbi_ctx* c) { return c->col_P > 0 ? c->col_P : 64; }
 }  // namespace
 
 bool col_fft_supported(int logN, bool fp32) {
-  return fp32 ? fft_select<float>(logN, 1).kernel != nullptr : fft_select<double>(logN, 1).kernel != nullptr;
+  return fp32 ? fft_select<float, false>(logN, 1).kernel != nullptr
+              : fft_select<double, false>(logN, 1).kernel != nullptr;
 }
 
-kfbi_status col_fft_launch(kfbi_ctx* c, bool fp32, void* spec, const void* rowinfo, const int* skip, bool pdl) {
+// the FR kernel's node arrays: sv for the capacity, and the sine table for as many nodes as the
+// rest of the block's shared memory holds (at most the capacity)
+static bool rows_layout(const kfbi_ctx* c, FftSel<float>* sel, RowSrc* rs, size_t* smem) {
+  *sel = fft_select<float, true>(c->logN, fft_want(c));
+  if (sel->kernel == nullptr) return false;
+  const int cap = (c->cap_irr + 1) & ~1;  // even: the sine table after sv stays 8-byte aligned
+  const size_t base = sel->smem + sizeof(float) * (size_t)cap;
+  if (base > FFT_SMEM_MAX) return false;
+  const size_t per = sizeof(float) * 2 * (size_t)sel->pairs;
+  const size_t room = (FFT_SMEM_MAX - base) / per;
+  rs->cap = cap;
+  rs->tab = (int)(room < (size_t)cap ? room : (size_t)cap);
+  *smem = base + per * (size_t)rs->tab;
+  return true;
+}
+
+bool col_fft_rows_fit(const kfbi_ctx* c) {
+  FftSel<float> sel;
+  RowSrc rs;
+  size_t smem = 0;
+  return rows_layout(c, &sel, &rs, &smem);
+}
+
+kfbi_status col_fft_launch(kfbi_ctx* c, bool fp32, void* spec, const void* rowinfo, const int* skip, bool pdl,
+                           const RowSrc* rows) {
   const int N = c->N, dct = c->boxbc == KFBI_BOX_NEUMANN0;
   if (!col_fft_supported(c->logN, fp32)) return KFBI_ERR_ARG;
   if (fp32) {
-    const FftSel<float> s = fft_select<float>(c->logN, fft_want(c));
-    KFBI_TRY(launch_k(pdl, s.kernel, dim3(N / (2 * s.pairs)), dim3(s.threads), s.smem, c->stream, dct,
+    RowSrc rs{};
+    FftSel<float> s;
+    size_t smem = 0;
+    if (rows != nullptr) {
+      rs = *rows;
+      if (!rows_layout(c, &s, &rs, &smem)) return KFBI_ERR_ARG;
+    } else {
+      s = fft_select<float, false>(c->logN, fft_want(c));
+      smem = s.smem;
+    }
+    KFBI_TRY(launch_k(pdl, s.kernel, dim3(N / (2 * s.pairs)), dim3(s.threads), smem, c->stream, dct,
                       (const V2<float>*)c->twN_f, (const float*)c->sintab_f, (const float*)c->lam_f, (float)c->kappa,
-                      (float*)spec, (const float*)nullptr, (const V2<float>*)rowinfo, skip));
+                      (float*)spec, (const float*)nullptr, (const V2<float>*)rowinfo, rs, skip));
   } else {
-    const FftSel<double> s = fft_select<double>(c->logN, fft_want(c));
+    if (rows != nullptr) return KFBI_ERR_ARG;
+    const FftSel<double> s = fft_select<double, false>(c->logN, fft_want(c));
     KFBI_TRY(launch_k(pdl, s.kernel, dim3(N / (2 * s.pairs)), dim3(s.threads), s.smem, c->stream, dct,
                       (const V2<double>*)c->twN, (const double*)c->sintab, (const double*)c->lam, c->kappa,
-                      (double*)spec, (const double*)c->rinv, (const V2<double>*)rowinfo, skip));
+                      (double*)spec, (const double*)c->rinv, (const V2<double>*)rowinfo, RowSrc{}, skip));
   }
   return KFBI_OK;
 }
 
 kfbi_status col_fft_setup_attributes() {
   for (int lg = 5; lg <= 12; ++lg)
-    for (int want = 1; want <= 16; want *= 2) {
-      const FftSel<float> f = fft_select<float>(lg, want);
+    for (int want = 1; want <= 64; want *= 2) {
+      const FftSel<float> f = fft_select<float, false>(lg, want);
       if (f.kernel != nullptr)
         KFBI_TRY(cudaFuncSetAttribute(f.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem));
-      const FftSel<double> d = fft_select<double>(lg, want);
+      const FftSel<float> fr = fft_select<float, true>(lg, want);
+      if (fr.kernel != nullptr)
+        KFBI_TRY(cudaFuncSetAttribute(fr.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM_MAX));
+      const FftSel<double> d = fft_select<double, false>(lg, want);
       if (d.kernel != nullptr)
         KFBI_TRY(cudaFuncSetAttribute(d.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.smem));
     }

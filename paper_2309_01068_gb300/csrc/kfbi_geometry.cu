@@ -486,6 +486,26 @@ __global__ void k_irr_emit(int N, double xmin, double ymin, double h, const uint
   }
 }
 
+// The per-arm correction map of the float32 applies whose column kernel forms the row
+// transform itself: for irregular node t, 2 i + 1 (column factor of its sines), and for each
+// crossed arm a, the code 4 t + a and (d, sign / h^2) filed under the crossing (at most two
+// arms cut one crossing: the two ends of its grid segment)
+__global__ void k_arm_map(int nirr, const IrrNode* irr, float inv_h2, int* rev, float2* coef, int* ci) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nirr) return;
+  const IrrNode& q = irr[t];
+  ci[t] = 2 * q.i + 1;
+  const float sc = q.signf * inv_h2;
+  for (int a = 0; a < 4; ++a) {
+    const int cr = q.target[a];
+    if (cr < 0) continue;
+    const int code = 4 * t + a;
+    const int k = atomicCAS(&rev[2 * cr], -1, code) == -1 ? 0 : 1;
+    if (k == 1) rev[2 * cr + 1] = code;
+    coef[2 * cr + k] = make_float2(q.df[a], sc);
+  }
+}
+
 // geometry at every target (crossings, then nodes) and the inverse 3x3 jump matrix
 // Also stores, per target, the twiddle starts of the per-apply density evaluation: lane l's
 // e^{i k0_l alpha} (k0_l = 1 + l chunk, chunk = ceil(K / 32)), then e^{i alpha} and
@@ -783,6 +803,13 @@ kfbi_status set_interface_impl(kfbi_ctx* c, int n, const double* xy_in) {
   launched(c, 6 + (ncr > 0 ? 1 : 0));
   k_irr_emit<<<wblocks, 256, 0, s>>>(N, c->xmin, c->ymin, h, c->side, c->hcount, c->vcount, c->hid, c->vid,
                                      c->cr_xi, c->row_ptr, c->irr);
+  if (ncr > 0) KFBI_TRY(cudaMemsetAsync(c->arm_rev, 0xFF, sizeof(int) * 2 * (size_t)ncr, s));
+  if (nirr > 0) {
+    KFBI_TRY(cudaMemsetAsync(c->arm_slot, 0, sizeof(float) * 4 * (size_t)nirr, s));
+    k_arm_map<<<cdiv(nirr, 256), 256, 0, s>>>(nirr, c->irr, (float)(1.0 / (h * h)), c->arm_rev,
+                                             (float2*)c->arm_coef, c->irr_ci);
+    launched(c, 1);
+  }
   if (ncr > 0)
     k_target_geo<<<cdiv((long)ncr * 32, 256), 256, 0, s>>>((const double2*)c->icoef, n, ncr, 0, ncr, c->cr_alpha,
                                                            (const double2*)c->twn, c->tgeo, c->tgeo_f,

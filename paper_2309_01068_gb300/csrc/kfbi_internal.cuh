@@ -275,6 +275,16 @@ struct kfbi_ctx {
   int* rowcnt = nullptr;        // [N + 1]
   int* row_ptr = nullptr;       // [N + 1]
   kfbi::IrrNode* irr = nullptr; // [cap_irr]
+  // float32 applies with the row transform folded into the column kernel: per irregular node
+  // 2 i + 1 (the sine argument's column factor) and its four arm corrections
+  // sign / h^2 (J0 + d J1 + d^2 J2 / 2), written by the jump kernel (zero for arms without a
+  // crossing); per crossing the (4 node + arm) codes of the two arms it cuts (-1 if none) and
+  // their (d, sign / h^2)
+  int* irr_ci = nullptr;        // [cap_irr]
+  float* arm_slot = nullptr;    // [cap_irr][4]
+  int* arm_rev = nullptr;       // [cap_cross][2]
+  float* arm_coef = nullptr;    // [cap_cross][2][2]
+  bool fuse_rows = false;       // KFBI_OPT_FUSE_ROWS
   kfbi::Stencil* stencil = nullptr;  // [max_nodes]
   kfbi::StencilF* stencil_f = nullptr;
   float* dens_f = nullptr;      // [max_nodes] float32 copy of the apply's density
@@ -516,7 +526,21 @@ kfbi_status col_tc_setup(kfbi_ctx* c);
 // float32 (fp32) or float64 spectral grid `spec`, rows the row transform left out in `rowinfo`
 // (or nullptr), launched on c->stream with programmatic dependent launch when pdl is set
 bool col_fft_supported(int logN, bool fp32);
-kfbi_status col_fft_launch(kfbi_ctx* c, bool fp32, void* spec, const void* rowinfo, const int* skip, bool pdl);
+// the row transform's inputs, for the float32 column kernel that forms its rows itself
+// (rows = nullptr in col_fft_launch: the kernel reads the row transform's output)
+struct RowSrc {
+  const int* row_ptr = nullptr;   // [N + 1] irregular nodes by row
+  const int* ci = nullptr;        // [n_irr] 2 i + 1
+  const float4* slot = nullptr;   // [n_irr] the four arm corrections
+  const float* boxg = nullptr;    // [2N] w_j at j, e_j at N + j (free-space box), or nullptr
+  const float* face = nullptr;    // [2N] transforms of rows 0 and N - 1, or nullptr
+  int cap = 0;                    // node capacity of the shared-memory arrays (set by the launch)
+  int tab = 0;                    // nodes whose sines are tabulated in shared memory (set by the launch)
+};
+// whether the context's layout (grid size, node capacity) fits that kernel's shared memory
+bool col_fft_rows_fit(const kfbi_ctx* c);
+kfbi_status col_fft_launch(kfbi_ctx* c, bool fp32, void* spec, const void* rowinfo, const int* skip, bool pdl,
+                           const RowSrc* rows = nullptr);
 kfbi_status col_fft_setup_attributes();
 
 // host-side helpers implemented in the .cu files

@@ -108,3 +108,57 @@ def test_option_values():
         with pytest.raises(K.KfbiError):
             ctx.set_option(K.OPT_COL_RADIX4, bad)
     ctx.close()
+
+
+@pytest.mark.parametrize("N", [64, 256, 1024, 2048])
+@pytest.mark.parametrize("boxbc,kappa,box", BOXES)
+def test_rows_formed_in_the_column_kernel(N, boxbc, kappa, box):
+    """KFBI_OPT_FUSE_ROWS = 1: the float32 apply whose column kernel forms the row transform from
+    the arm corrections (one launch fewer) against the same apply with the separate row transform
+    (float32 both: rounding order only) and against the oracle's float64 apply."""
+    n = max(16, min(N, 512))
+    p = W.random_problem(700 + N, N=N, n=n, kappa=kappa, boxbc=boxbc, box=box)
+    ctx = K.Context(p.N, p.box, kappa, boxbc, K.MIXED, max_nodes=p.n)
+    ctx.set_interface(dev(p.xy))
+    assert ctx.get_option(K.OPT_FUSE_ROWS) == 0
+    ctx.set_option(K.OPT_FUSE_ROWS, 1)
+    dens = W.random_density(N + 3, p.n, modes=8)
+    ref = OK.Kfbi(p.N, p.box, kappa, boxbc).set_interface(p.xy)
+    layers = (K.DOUBLE,) if boxbc == OK.BOX_FREESPACE_DL else (K.DOUBLE, K.SINGLE)
+    for layer in layers:
+        l0 = ctx.launch_count()
+        vf, _, _ = ctx.apply(layer, dev(dens))
+        lf = ctx.launch_count() - l0
+        ctx.set_option(K.OPT_FUSE_ROWS, 0)
+        l0 = ctx.launch_count()
+        vs, _, _ = ctx.apply(layer, dev(dens))
+        ls = ctx.launch_count() - l0
+        ctx.set_option(K.OPT_FUSE_ROWS, 1)
+        assert lf == ls - 1, (lf, ls)
+        a, b = vf.cpu().numpy(), vs.cpu().numpy()
+        assert np.isfinite(a).all()
+        assert rel(a, b) < 2e-5, (layer, rel(a, b))
+        rv, _, _ = ref.apply(OK.LAYER_DOUBLE if layer == K.DOUBLE else OK.LAYER_SINGLE, dens)
+        assert rel(a, rv) < 2e-4, (layer, rel(a, rv))
+    ctx.close()
+
+
+def test_rows_formed_in_the_column_kernel_follow_the_interface():
+    """The arm map is rebuilt with every interface: a second interface on the same context
+    (different crossings and irregular nodes) gives the same apply as a fresh context."""
+    p1 = W.random_problem(801, N=256, n=256, kappa=0.0, boxbc=OK.BOX_DIRICHLET0)
+    p2 = W.random_problem(802, N=256, n=256, kappa=0.0, boxbc=OK.BOX_DIRICHLET0, R0=(0.25, 0.45))
+    ctx = K.Context(256, p1.box, 0.0, OK.BOX_DIRICHLET0, K.MIXED, max_nodes=256)
+    ctx.set_option(K.OPT_FUSE_ROWS, 1)
+    ctx.set_interface(dev(p1.xy))
+    dens = W.random_density(5, 256, modes=6)
+    ctx.apply(K.DOUBLE, dev(dens))
+    ctx.set_interface(dev(p2.xy))
+    v2, _, _ = ctx.apply(K.DOUBLE, dev(dens))
+    fresh = K.Context(256, p2.box, 0.0, OK.BOX_DIRICHLET0, K.MIXED, max_nodes=256)
+    fresh.set_option(K.OPT_FUSE_ROWS, 1)
+    fresh.set_interface(dev(p2.xy))
+    vf, _, _ = fresh.apply(K.DOUBLE, dev(dens))
+    assert np.array_equal(v2.cpu().numpy(), vf.cpu().numpy())
+    ctx.close()
+    fresh.close()
