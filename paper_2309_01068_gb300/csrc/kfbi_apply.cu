@@ -305,11 +305,11 @@ __host__ __device__ inline int jfft_buf(int n) {
 __host__ __device__ inline size_t jfft_smem(int n, int logn) {
   return sizeof(V2<float>) * (2 * (size_t)jfft_buf(n) + (size_t)staged_count(n, logn));
 }
-constexpr int JFFT_THREADS = 256;
+constexpr int JFFT_THREADS = 512;
 constexpr int JFFT_PER = 4096 / JFFT_THREADS;  // density values per thread at most
 
 template <typename G, typename S_t>
-__global__ void __launch_bounds__(JFFT_THREADS)
+__global__ void __launch_bounds__(JFFT_THREADS, 1)
     k_jumps_fft(const float* phi, int n, int logn, const V2<float>* twn, const S_t* st, float* dint, const int* ncr,
                 const G* tg, const V2<float>* tstart, int layer, float kappa, float* Jout, const int* arm_rev,
                 const float2* arm_coef, float* arm_slot, const int* skip) {
