@@ -643,14 +643,16 @@ def apply_forms_leg(torch, K, reps=300):
 
 
 # column forms of the size sweep: (name, COL_RADIX4 bits, COL_PAIRS, COL_REG, COL_TC)
-COL_FORMS = (("radix16", 0, 0, 0, 0), ("radix16_p1", 0, 1, 0, 0), ("radix16_p2", 0, -2, 0, 0), ("radix4", 3, 0, 0, 0),
+COL_FORMS = (("radix16", 0, 0, 0, 0), ("radix16_p1", 0, 1, 0, 0), ("radix16_p2", 0, -2, 0, 0),
+             ("radix16_16pt", 0, 0, 0, 0), ("radix4", 3, 0, 0, 0),
              ("radix4_p1", 3, 1, 0, 0), ("radix4_p4", 3, 4, 0, 0), ("register", 0, 0, 1, 0),
              ("tensor_core", 0, 0, 0, 1))
 
 
 def col_kernel_sizes(torch, K, hbm_peak, reps=200):
     """Column transform time per launch by grid size for every column form (register-resident
-    radix-16 with its pair counts, shared-memory radix-4 Stockham with 1, 2, 4 pairs, four-step
+    kernel with its pair counts, 8 points per thread up to 1024^2 by default and 16 as
+    `radix16_16pt`, shared-memory radix-4 Stockham with 1, 2, 4 pairs, four-step
     register FFTs up to 1024^2, tensor-core contractions up to 256^2) in float32, and the radix-16
     and radix-4 kernels in float64: kfbi_time_column (CUDA events around `reps` launches back to
     back, warm L2) on a Neumann-box context with a 256-node star after one apply."""
@@ -675,6 +677,7 @@ def col_kernel_sizes(torch, K, hbm_peak, reps=200):
                 ctx.set_option(K.OPT_COL_TC, tc)
                 ctx.set_option(K.OPT_COL_RADIX4, r4)
                 ctx.set_option(K.OPT_COL_PAIRS, min(16, 2 * max(1, 512 // N)) if pairs < 0 else pairs)
+                ctx.set_option(K.OPT_COL_POINTS, 16 if form == "radix16_16pt" else 0)
                 ctx.apply_into(K.DOUBLE, dens, vals)
                 us = ctx.time_column(f32, reps if f32 else max(reps // 4, 5))
                 elt = 4.0 if f32 else 8.0
@@ -956,8 +959,9 @@ def main():
         kname = "k_col_solve<float> (radix-4 shared-memory Stockham: column DST-II, eigen divide, inverse DST)"
         tr = traffic_record(os.path.join(csrc, "kfbi_apply.cu"), "k_col_solve_traffic.json")
     else:
-        kname = (f"k_col_fft<float,{int(math.log2(N))},P> (register-resident radix-16 column solve: DST-II, "
-                 "eigen divide, inverse DST)")
+        pt = ctx.get_option(K.OPT_COL_POINTS) or (8 if N <= 1024 else 16)
+        kname = (f"k_col_fft<float,{int(math.log2(N))},P,0,{pt}> (register-resident column solve, {pt} points "
+                 "per thread: DST-II, eigen divide, inverse DST)")
         tr = traffic_record(os.path.join(csrc, "kfbi_colfft.cu"), "k_col_fft_traffic.json")
     # the same kernel back to back (kfbi_time_column: warm L2, programmatic dependent launch as
     # in the GMRES loop, no event between launches)

@@ -490,6 +490,12 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
     c->cfg_version += 1;
     return KFBI_OK;
   }
+  if (option == KFBI_OPT_COL_POINTS) {
+    if (value != 0 && value != 8 && value != 16) return KFBI_ERR_ARG;
+    c->col_pt = value;
+    c->cfg_version += 1;
+    return KFBI_OK;
+  }
   if (option == KFBI_OPT_COL_RADIX4) {
     if (value < 0 || value > 3) return KFBI_ERR_ARG;
     c->col_radix4 = value;
@@ -556,6 +562,7 @@ kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
   else if (option == KFBI_OPT_COL_REG) *value = c->col_reg ? 1 : 0;
   else if (option == KFBI_OPT_COL_TC) *value = c->col_tc ? 1 : 0;
   else if (option == KFBI_OPT_COL_RADIX4) *value = c->col_radix4;
+  else if (option == KFBI_OPT_COL_POINTS) *value = c->col_pt;
   else if (option == KFBI_OPT_FUSE_ROWS) *value = c->fuse_rows ? 1 : 0;
   else if (option == KFBI_OPT_BODY_CAP) *value = c->body_cap_set;
   else if (option == KFBI_OPT_SWEEP_CAP) *value = c->sweep_cap_set;

@@ -27,16 +27,23 @@
 namespace kfbi {
 namespace {
 
-// Stage plan for N = 2^LOGN, 5 <= LOGN <= 12: LOGN / 4 + 1 Stockham stages of radix 16, except
-// the last (2, 4 or 8 for LOGN mod 4 = 1 or 0, 2, 3) and, for LOGN mod 4 = 0, the one before it
-// (8), so that the last radix leaves every thread at least two butterflies.
-template <int LOGN>
+// Stage plan for N = 2^LOGN, 5 <= LOGN <= 12, PT points per thread (16 or 8, B = log2 PT bits
+// per full stage): stage 0 of radix PT, then stages of radix PT, and a last stage of radix 2^b
+// with 1 <= b < B, so that every thread holds at least two last-stage butterflies; when the
+// remaining bits are a multiple of B, one stage of radix PT/2 comes before a last stage of radix
+// 2. PT = 16: N = 1024 is 16, 16, 4; PT = 8: 8, 8, 8, 2.
+template <int LOGN, int PT = 16>
 struct FPlan {
+  static_assert(PT == 8 || PT == 16, "8 or 16 points per thread");
   static constexpr int N = 1 << LOGN;
-  static constexpr int TH = N / 16;  // threads per column pair
-  static constexpr int NST = LOGN / 4 + 1;
-  static constexpr int RL = (LOGN % 4 == 2) ? 4 : (LOGN % 4 == 3) ? 8 : 2;
-  static constexpr int radix(int s) { return s == NST - 1 ? RL : (LOGN % 4 == 0 && s == NST - 2) ? 8 : 16; }
+  static constexpr int B = PT == 16 ? 4 : 3;
+  static constexpr int TH = N / PT;  // threads per column pair
+  static constexpr int RB = LOGN - B;
+  static constexpr bool EVEN = RB % B == 0;
+  static constexpr int NFULL = EVEN ? RB / B - 1 : RB / B;
+  static constexpr int NST = NFULL + (EVEN ? 3 : 2);
+  static constexpr int RL = 1 << (EVEN ? 1 : RB % B);
+  static constexpr int radix(int s) { return s == 0 ? PT : s == NST - 1 ? RL : (EVEN && s == NST - 2) ? PT / 2 : PT; }
   static constexpr int span(int s) {
     int p = 1;
     for (int i = 0; i < s; ++i) p *= radix(i);
@@ -53,9 +60,9 @@ struct FPlan {
 };
 
 // column pairs per block: at least one warp per block (PMIN), or twice that
-template <int LOGN>
+template <int LOGN, int PT>
 constexpr int pairs_min() {
-  return FPlan<LOGN>::TH >= 32 ? 1 : 32 / FPlan<LOGN>::TH;
+  return FPlan<LOGN, PT>::TH >= 32 ? 1 : 32 / FPlan<LOGN, PT>::TH;
 }
 
 // padded shared-memory index: one spare slot per 16, so that the stage-0 writes (stride 16)
@@ -75,9 +82,9 @@ constexpr int pair_stride() {
 
 // shared memory of a block: P pair buffers, the stage twiddles, the rows' box-data pairs, the
 // eigenvalues
-template <typename T, int LOGN, int P>
+template <typename T, int LOGN, int P, int PT>
 constexpr size_t fft_smem() {
-  return sizeof(V2<T>) * ((size_t)P * pair_stride<T, (1 << LOGN), P>() + FPlan<LOGN>::TW + (1 << LOGN)) +
+  return sizeof(V2<T>) * ((size_t)P * pair_stride<T, (1 << LOGN), P>() + FPlan<LOGN, PT>::TW + (1 << LOGN)) +
          sizeof(T) * (1 << LOGN);
 }
 
@@ -122,9 +129,9 @@ __device__ __forceinline__ void st2(V2<T>* p, V2<T> a) {
 
 // twiddle r of stage S for butterfly offset jm from the block's table: w^(r jm N / (Ns R)),
 // w = e^{-2 pi i / N}, or its conjugate (inverse)
-template <typename T, int LOGN, int S, bool INV>
+template <typename T, int LOGN, int PT, int S, bool INV>
 __device__ __forceinline__ V2<T> twid(const V2<T>* sT, int r, int jm) {
-  using PL = FPlan<LOGN>;
+  using PL = FPlan<LOGN, PT>;
   V2<T> w = ld2(sT + PL::tw_off(S) + (r - 1) * PL::span(S) + jm);
   if (INV) w.y = -w.y;
   return w;
@@ -132,9 +139,9 @@ __device__ __forceinline__ V2<T> twid(const V2<T>* sT, int r, int jm) {
 
 // stage S's part of the twiddle table, gathered from the table of w^m (m < N) by the block's
 // NT threads with all loads in flight before the stores
-template <typename T, int LOGN, int S, int NT>
+template <typename T, int LOGN, int PT, int S, int NT>
 __device__ __forceinline__ void stage_table(const V2<T>* twN, V2<T>* sT) {
-  using PL = FPlan<LOGN>;
+  using PL = FPlan<LOGN, PT>;
   constexpr int N = PL::N, R = PL::radix(S), NS = PL::span(S), WS = N / (NS * R);
   constexpr int CNT = (R - 1) * NS, PER = (CNT + NT - 1) / NT;
   V2<T> v[PER];
@@ -183,11 +190,11 @@ __device__ __forceinline__ void bin_pair(int m, int N, int dct, const T* tab, co
   dct_pre<T>(N, m, c, s, Gm, GNm, A, B);
 }
 
-// forward middle stage s: butterflies j = u + TH g (g < 16 / R), span Ns, radix R
-template <typename T, int LOGN, int S>
-__device__ __forceinline__ void stage_fwd(V2<T>* buf, V2<T> (&x)[16], int u, const V2<T>* sT) {
-  using PL = FPlan<LOGN>;
-  constexpr int N = PL::N, R = PL::radix(S), NS = PL::span(S), G = 16 / R, TH = PL::TH;
+// forward middle stage s: butterflies j = u + TH g (g < PT / R), span Ns, radix R
+template <typename T, int LOGN, int PT, int S>
+__device__ __forceinline__ void stage_fwd(V2<T>* buf, V2<T> (&x)[PT], int u, const V2<T>* sT) {
+  using PL = FPlan<LOGN, PT>;
+  constexpr int N = PL::N, R = PL::radix(S), NS = PL::span(S), G = PT / R, TH = PL::TH;
   V2<T> w[G][R];
   sfor<G>([&](auto gi) {
     constexpr int g = decltype(gi)::value;
@@ -195,7 +202,7 @@ __device__ __forceinline__ void stage_fwd(V2<T>* buf, V2<T> (&x)[16], int u, con
 #pragma unroll
     for (int r = 0; r < R; ++r) x[g * R + r] = ld2(buf + pidx(j + r * (N / R)));
 #pragma unroll
-    for (int r = 1; r < R; ++r) w[g][r] = twid<T, LOGN, S, false>(sT, r, jm);
+    for (int r = 1; r < R; ++r) w[g][r] = twid<T, LOGN, PT, S, false>(sT, r, jm);
   });
   __syncthreads();  // every read of the buffer is done before it is overwritten
   sfor<G>([&](auto gi) {
@@ -212,10 +219,10 @@ __device__ __forceinline__ void stage_fwd(V2<T>* buf, V2<T> (&x)[16], int u, con
 }
 
 // adjoint of stage_fwd<S> (inverse DFT, conjugate twiddle, scatter back)
-template <typename T, int LOGN, int S>
-__device__ __forceinline__ void stage_inv(V2<T>* buf, V2<T> (&x)[16], int u, const V2<T>* sT) {
-  using PL = FPlan<LOGN>;
-  constexpr int N = PL::N, R = PL::radix(S), NS = PL::span(S), G = 16 / R, TH = PL::TH;
+template <typename T, int LOGN, int PT, int S>
+__device__ __forceinline__ void stage_inv(V2<T>* buf, V2<T> (&x)[PT], int u, const V2<T>* sT) {
+  using PL = FPlan<LOGN, PT>;
+  constexpr int N = PL::N, R = PL::radix(S), NS = PL::span(S), G = PT / R, TH = PL::TH;
   V2<T> w[G][R];
   sfor<G>([&](auto gi) {
     constexpr int g = decltype(gi)::value;
@@ -224,7 +231,7 @@ __device__ __forceinline__ void stage_inv(V2<T>* buf, V2<T> (&x)[16], int u, con
 #pragma unroll
     for (int r = 0; r < R; ++r) x[g * R + r] = ld2(buf + pidx(base + r * NS));
 #pragma unroll
-    for (int r = 1; r < R; ++r) w[g][r] = twid<T, LOGN, S, true>(sT, r, jm);
+    for (int r = 1; r < R; ++r) w[g][r] = twid<T, LOGN, PT, S, true>(sT, r, jm);
   });
   __syncthreads();
   sfor<G>([&](auto gi) {
@@ -242,10 +249,10 @@ __device__ __forceinline__ void stage_inv(V2<T>* buf, V2<T> (&x)[16], int u, con
 // butterfly b of the last stage for thread u: j = u + TH b for b < G/2, and the mirror
 // images Ns - u - TH (b - G/2) for b >= G/2 (thread 0: Ns/2 in place of Ns), so that bin m and
 // bin N - m are in the same thread
-template <int LOGN, int B>
+template <int LOGN, int PT, int B>
 __device__ __forceinline__ int last_j(int u) {
-  using PL = FPlan<LOGN>;
-  constexpr int RL = PL::RL, G = 16 / RL, NSL = PL::N / RL, TH = PL::TH;
+  using PL = FPlan<LOGN, PT>;
+  constexpr int RL = PL::RL, G = PT / RL, NSL = PL::N / RL, TH = PL::TH;
   if constexpr (B < G / 2) {
     return u + TH * B;
   } else if constexpr (B == G / 2) {
@@ -270,14 +277,14 @@ __device__ __forceinline__ void srange(F&& f) {
 // S_k the DST-II (DCT-II) basis function, sv_t the sum of node t's four arm corrections, (w_j,
 // e_j) the free-space box data of the row. The row pointers and column factors (fixed with the
 // interface) are staged before the wait for the jump kernel, the corrections and box data after.
-template <typename T, int LOGN, int P, bool FR>
-__global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const V2<T>* __restrict__ twN,
+template <typename T, int LOGN, int P, bool FR, int PT>
+__global__ void __launch_bounds__(P * FPlan<LOGN, PT>::TH) k_col_fft(int dct, const V2<T>* __restrict__ twN,
                                                                 const T* __restrict__ tab, const T* __restrict__ lam,
                                                                 T kappa, T* spec, const T* __restrict__ rinv,
                                                                 const V2<T>* __restrict__ rowinfo, RowSrc rs,
                                                                 const int* skip) {
-  using PL = FPlan<LOGN>;
-  constexpr int N = PL::N, TH = PL::TH, RL = PL::RL, G = 16 / RL, NST = PL::NST, NSL = N / RL;
+  using PL = FPlan<LOGN, PT>;
+  constexpr int N = PL::N, TH = PL::TH, RL = PL::RL, G = PT / RL, NST = PL::NST, NSL = N / RL;
   constexpr int PS = pair_stride<T, N, P>();
   extern __shared__ float4 col_fft_smem[];
   const int p = (int)threadIdx.x % P, u = (int)threadIdx.x / P;
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
   }
   // the tables (fixed with the context) go to shared memory before the wait for the row
   // transform; the first barrier below orders these writes before every read
-  srange<1, NST>([&](auto si) { stage_table<T, LOGN, decltype(si)::value, P * TH>(twN, sT); });
+  srange<1, NST>([&](auto si) { stage_table<T, LOGN, PT, decltype(si)::value, P * TH>(twN, sT); });
   {
     constexpr int PER = (N + P * TH - 1) / (P * TH);
     T v[PER];
@@ -358,9 +365,9 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
   pdl_wait();
   if (*skip) return;
 
-  // ---- stage 0: points u + r N/16 of the reordered pair (rows 2i for r < 8, 2N-1-2i above;
+  // ---- stage 0: points u + r N/PT of the reordered pair (rows 2i for r < PT/2, 2N-1-2i above;
   // the DST takes (-1)^row of the odd rows)
-  V2<T> x[16];
+  V2<T> x[PT];
   if constexpr (FR) {
     // corrections and box data, once per block, then each of the thread's rows
     for (int t0 = 0; t0 < nirr; t0 += 4 * P * TH) {
@@ -381,9 +388,9 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
     __syncthreads();
     const float qs = qscale(N);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < PT; ++r) {
       const int i = u + r * TH;
-      const int row = r < 8 ? 2 * i : 2 * N - 1 - 2 * i;
+      const int row = r < PT / 2 ? 2 * i : 2 * N - 1 - 2 * i;
       T a0 = 0, a1 = 0;
       const int e = sRp[row + 1];
       const int et = min(e, rs.tab);
@@ -419,9 +426,9 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < PT; ++r) {
       const int i = u + r * TH;
-      const int row = r < 8 ? 2 * i : 2 * N - 1 - 2 * i;
+      const int row = r < PT / 2 ? 2 * i : 2 * N - 1 - 2 * i;
       x[r] = *reinterpret_cast<const V2<T>*>(spec + (long)row * N + k0);
     }
   }
@@ -443,32 +450,32 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < 16; ++r) {
+  for (int r = 0; r < PT; ++r) {
     V2<T> v = x[r];
     if (!FR && rowinfo != nullptr) {
       const int i = u + r * TH;
-      const V2<T> ri = ld2(sRow + (r < 8 ? 2 * i : 2 * N - 1 - 2 * i));
+      const V2<T> ri = ld2(sRow + (r < PT / 2 ? 2 * i : 2 * N - 1 - 2 * i));
       if (ri.x == ri.x) v = V2<T>{ri.x * s0.x + ri.y * sN.x, ri.x * s0.y + ri.y * sN.y};
     }
-    if (!dct && r >= 8) v = V2<T>{-v.x, -v.y};
+    if (!dct && r >= PT / 2) v = V2<T>{-v.x, -v.y};
     x[r] = v;
   }
-  rg_dft<16, false>(x);
+  rg_dft<PT, false>(x);
 #pragma unroll
-  for (int r = 0; r < 16; ++r) st2(buf + pidx(16 * u + r), x[r]);
+  for (int r = 0; r < PT; ++r) st2(buf + pidx(PT * u + r), x[r]);
   __syncthreads();
 
   // ---- middle stages
-  srange<1, NST - 1>([&](auto si) { stage_fwd<T, LOGN, decltype(si)::value>(buf, x, u, sT); });
+  srange<1, NST - 1>([&](auto si) { stage_fwd<T, LOGN, PT, decltype(si)::value>(buf, x, u, sT); });
 
   // ---- last stage: radix RL, span NSL; the outputs stay in registers, x[b RL + r] = bin j_b + r NSL
   sfor<G>([&](auto bi) {
     constexpr int b = decltype(bi)::value;
-    const int j = last_j<LOGN, b>(u);
+    const int j = last_j<LOGN, PT, b>(u);
 #pragma unroll
     for (int r = 0; r < RL; ++r) x[b * RL + r] = ld2(buf + pidx(j + r * NSL));
 #pragma unroll
-    for (int r = 1; r < RL; ++r) x[b * RL + r] = cmul(x[b * RL + r], twid<T, LOGN, NST - 1, false>(sT, r, j));
+    for (int r = 1; r < RL; ++r) x[b * RL + r] = cmul(x[b * RL + r], twid<T, LOGN, PT, NST - 1, false>(sT, r, j));
     rg_dft_at<RL, false, b * RL>(x);
   });
 
@@ -477,7 +484,7 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
   sfor<G / 2>([&](auto bi) {
     constexpr int b = decltype(bi)::value;
     if (b > 0 || u != 0) {
-      const int jl = last_j<LOGN, b>(u), jh = last_j<LOGN, b + G / 2>(u);
+      const int jl = last_j<LOGN, PT, b>(u), jh = last_j<LOGN, PT, b + G / 2>(u);
 #pragma unroll
       for (int r = 0; r < RL; ++r) {
         if (r < RL / 2)
@@ -509,28 +516,28 @@ __global__ void __launch_bounds__(P * FPlan<LOGN>::TH) k_col_fft(int dct, const 
   // ---- adjoint of the last stage: back to the positions it read (this thread's own)
   sfor<G>([&](auto bi) {
     constexpr int b = decltype(bi)::value;
-    const int j = last_j<LOGN, b>(u);
+    const int j = last_j<LOGN, PT, b>(u);
     rg_dft_at<RL, true, b * RL>(x);
 #pragma unroll
-    for (int r = 1; r < RL; ++r) x[b * RL + r] = cmul(x[b * RL + r], twid<T, LOGN, NST - 1, true>(sT, r, j));
+    for (int r = 1; r < RL; ++r) x[b * RL + r] = cmul(x[b * RL + r], twid<T, LOGN, PT, NST - 1, true>(sT, r, j));
 #pragma unroll
     for (int r = 0; r < RL; ++r) st2(buf + pidx(j + r * NSL), x[b * RL + r]);
   });
   __syncthreads();
 
   // ---- adjoints of the middle stages, last to first
-  srange<1, NST - 1>([&](auto si) { stage_inv<T, LOGN, NST - 1 - decltype(si)::value>(buf, x, u, sT); });
+  srange<1, NST - 1>([&](auto si) { stage_inv<T, LOGN, PT, NST - 1 - decltype(si)::value>(buf, x, u, sT); });
 
   // ---- adjoint of stage 0: positions 16 u + r -> points u + r N/16 -> rows, scaled by 1/N
 #pragma unroll
-  for (int r = 0; r < 16; ++r) x[r] = ld2(buf + pidx(16 * u + r));
-  rg_dft<16, true>(x);
+  for (int r = 0; r < PT; ++r) x[r] = ld2(buf + pidx(PT * u + r));
+  rg_dft<PT, true>(x);
   constexpr T invN = (T)1 / (T)N;
 #pragma unroll
-  for (int r = 0; r < 16; ++r) {
+  for (int r = 0; r < PT; ++r) {
     const int i = u + r * TH;
-    const int row = r < 8 ? 2 * i : 2 * N - 1 - 2 * i;
-    const T sc = (!dct && r >= 8) ? -invN : invN;
+    const int row = r < PT / 2 ? 2 * i : 2 * N - 1 - 2 * i;
+    const T sc = (!dct && r >= PT / 2) ? -invN : invN;
     st2(reinterpret_cast<V2<T>*>(spec + (long)row * N + k0), V2<T>{x[r].x * sc, x[r].y * sc});
   }
 }
@@ -542,13 +549,13 @@ struct FftSel {
   size_t smem = 0;  // without the FR node arrays
 };
 
-template <typename T, int LOGN, int P, bool FR>
+template <typename T, int LOGN, int P, bool FR, int PT>
 FftSel<T> fft_sel() {
   FftSel<T> s;
-  s.kernel = k_col_fft<T, LOGN, P, FR>;
-  s.threads = P * FPlan<LOGN>::TH;
+  s.kernel = k_col_fft<T, LOGN, P, FR, PT>;
+  s.threads = P * FPlan<LOGN, PT>::TH;
   s.pairs = P;
-  s.smem = fft_smem<T, LOGN, P>() + (FR ? sizeof(int) * ((1 << LOGN) + 2) : 0);
+  s.smem = fft_smem<T, LOGN, P, PT>() + (FR ? sizeof(int) * ((1 << LOGN) + 2) : 0);
   return s;
 }
 
@@ -556,47 +563,62 @@ FftSel<T> fft_sel() {
 constexpr size_t FFT_SMEM_MAX = 227 * 1024;
 
 // an instantiation exists for P pairs per block when N/2 pairs allow it, its shared memory fits
-// and (for P > 2 PMIN) the block stays within 256 threads
-template <typename T, int LOGN, int P>
+// and (for P > 2 PMIN) the block holds at most 4096 points (256 threads of 16, 512 of 8)
+template <typename T, int LOGN, int P, int PT>
 constexpr bool fft_fits() {
-  return P <= (1 << LOGN) / 2 && fft_smem<T, LOGN, P>() <= FFT_SMEM_MAX &&
-         (P <= 2 * pairs_min<LOGN>() || P * FPlan<LOGN>::TH <= 256);
+  return P <= (1 << LOGN) / 2 && fft_smem<T, LOGN, P, PT>() <= FFT_SMEM_MAX &&
+         (P <= 2 * pairs_min<LOGN, PT>() || P * (1 << LOGN) <= 4096);
 }
 
 // the kernel for N = 2^logN with the largest instantiated pair count (PMIN, 2 PMIN, 4 PMIN) that
 // does not exceed `want`, or PMIN; no kernel when even PMIN does not fit. The FR form (rows
-// formed in the kernel) exists in float32 only.
-template <typename T, int LOGN, bool FR>
+// formed in the kernel) and the 8-point form exist in float32 only, and not together; the
+// 8-point form for N <= 1024 (above it the 16-point form measured faster).
+template <typename T, int LOGN, bool FR, int PT>
 FftSel<T> fft_sel_n(int want) {
-  constexpr int P0 = pairs_min<LOGN>();
-  if constexpr (FR && sizeof(T) != 4) {
+  constexpr int P0 = pairs_min<LOGN, PT>();
+  if constexpr ((FR || PT == 8) && (sizeof(T) != 4 || (FR && PT == 8) || (PT == 8 && LOGN > 10))) {
     return FftSel<T>{};
   } else {
-    if constexpr (fft_fits<T, LOGN, 4 * P0>()) {
-      if (want >= 4 * P0) return fft_sel<T, LOGN, 4 * P0, FR>();
+    if constexpr (fft_fits<T, LOGN, 4 * P0, PT>()) {
+      if (want >= 4 * P0) return fft_sel<T, LOGN, 4 * P0, FR, PT>();
     }
-    if constexpr (fft_fits<T, LOGN, 2 * P0>()) {
-      if (want >= 2 * P0) return fft_sel<T, LOGN, 2 * P0, FR>();
+    if constexpr (fft_fits<T, LOGN, 2 * P0, PT>()) {
+      if (want >= 2 * P0) return fft_sel<T, LOGN, 2 * P0, FR, PT>();
     }
-    if constexpr (fft_fits<T, LOGN, P0>()) return fft_sel<T, LOGN, P0, FR>();
+    if constexpr (fft_fits<T, LOGN, P0, PT>()) return fft_sel<T, LOGN, P0, FR, PT>();
     return FftSel<T>{};
   }
 }
 
-template <typename T, bool FR>
-FftSel<T> fft_select(int logN, int want) {
+template <typename T, bool FR, int PT>
+FftSel<T> fft_select_pt(int logN, int want) {
   switch (logN) {
-    case 5: return fft_sel_n<T, 5, FR>(want);
-    case 6: return fft_sel_n<T, 6, FR>(want);
-    case 7: return fft_sel_n<T, 7, FR>(want);
-    case 8: return fft_sel_n<T, 8, FR>(want);
-    case 9: return fft_sel_n<T, 9, FR>(want);
-    case 10: return fft_sel_n<T, 10, FR>(want);
-    case 11: return fft_sel_n<T, 11, FR>(want);
-    case 12: return fft_sel_n<T, 12, FR>(want);
+    case 5: return fft_sel_n<T, 5, FR, PT>(want);
+    case 6: return fft_sel_n<T, 6, FR, PT>(want);
+    case 7: return fft_sel_n<T, 7, FR, PT>(want);
+    case 8: return fft_sel_n<T, 8, FR, PT>(want);
+    case 9: return fft_sel_n<T, 9, FR, PT>(want);
+    case 10: return fft_sel_n<T, 10, FR, PT>(want);
+    case 11: return fft_sel_n<T, 11, FR, PT>(want);
+    case 12: return fft_sel_n<T, 12, FR, PT>(want);
     default: return FftSel<T>{};
   }
 }
+
+// points per thread 8 where that form exists (pt = 8), else 16
+template <typename T, bool FR>
+FftSel<T> fft_select(int logN, int want, int pt = 16) {
+  if (pt == 8) {
+    const FftSel<T> s = fft_select_pt<T, FR, 8>(logN, want);
+    if (s.kernel != nullptr) return s;
+  }
+  return fft_select_pt<T, FR, 16>(logN, want);
+}
+
+// KFBI_OPT_COL_POINTS: 0 chooses 8 points per thread up to N = 1024 (twice the warps of the
+// 16-point form; measured 5-38 % faster there) and 16 above (5-7 % faster there)
+inline int fft_points(const kfbi_ctx* c) { return c->col_pt != 0 ? c->col_pt : (c->logN <= 10 ? 8 : 16); }
 
 // pair count asked for: the context's KFBI_OPT_COL_PAIRS, else the largest instantiated one
 // (4 PMIN up to N = 1024, 2 PMIN above: 2P float32 columns of 4 bytes per row segment, a whole
@@ -613,7 +635,7 @@ bool col_fft_supported(int logN, bool fp32) {
 // the FR kernel's node arrays: sv for the capacity, and the sine table for as many nodes as the
 // rest of the block's shared memory holds (at most the capacity)
 static bool rows_layout(const kfbi_ctx* c, FftSel<float>* sel, RowSrc* rs, size_t* smem) {
-  *sel = fft_select<float, true>(c->logN, fft_want(c));
+  *sel = fft_select<float, true>(c->logN, fft_want(c), fft_points(c));
   if (sel->kernel == nullptr) return false;
   const int cap = (c->cap_irr + 1) & ~1;  // even: the sine table after sv stays 8-byte aligned
   const size_t base = sel->smem + sizeof(float) * (size_t)cap;
@@ -645,7 +667,7 @@ kfbi_status col_fft_launch(kfbi_ctx* c, bool fp32, void* spec, const void* rowin
       rs = *rows;
       if (!rows_layout(c, &s, &rs, &smem)) return KFBI_ERR_ARG;
     } else {
-      s = fft_select<float, false>(c->logN, fft_want(c));
+      s = fft_select<float, false>(c->logN, fft_want(c), fft_points(c));
       smem = s.smem;
     }
     KFBI_TRY(launch_k(pdl, s.kernel, dim3(N / (2 * s.pairs)), dim3(s.threads), smem, c->stream, dct,
@@ -664,12 +686,14 @@ kfbi_status col_fft_launch(kfbi_ctx* c, bool fp32, void* spec, const void* rowin
 kfbi_status col_fft_setup_attributes() {
   for (int lg = 5; lg <= 12; ++lg)
     for (int want = 1; want <= 64; want *= 2) {
-      const FftSel<float> f = fft_select<float, false>(lg, want);
-      if (f.kernel != nullptr)
-        KFBI_TRY(cudaFuncSetAttribute(f.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem));
-      const FftSel<float> fr = fft_select<float, true>(lg, want);
-      if (fr.kernel != nullptr)
-        KFBI_TRY(cudaFuncSetAttribute(fr.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM_MAX));
+      for (int pt = 8; pt <= 16; pt += 8) {
+        const FftSel<float> f = fft_select<float, false>(lg, want, pt);
+        if (f.kernel != nullptr)
+          KFBI_TRY(cudaFuncSetAttribute(f.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f.smem));
+        const FftSel<float> fr = fft_select<float, true>(lg, want, pt);
+        if (fr.kernel != nullptr)
+          KFBI_TRY(cudaFuncSetAttribute(fr.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FFT_SMEM_MAX));
+      }
       const FftSel<double> d = fft_select<double, false>(lg, want);
       if (d.kernel != nullptr)
         KFBI_TRY(cudaFuncSetAttribute(d.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)d.smem));

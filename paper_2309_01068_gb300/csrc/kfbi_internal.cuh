@@ -378,6 +378,7 @@ struct kfbi_ctx {
   bool col_tc = false;          // float32 column solve as two tensor-core contractions (N <= 256), KFBI_OPT_COL_TC
   bool col_reg = false;         // float32 column solve with register FFTs (N <= 1024), KFBI_OPT_COL_REG
   int col_radix4 = 2;           // KFBI_OPT_COL_RADIX4: bit 0 (float32) / bit 1 (float64) select the radix-4 kernel
+  int col_pt = 0;               // KFBI_OPT_COL_POINTS: points per thread of the float32 radix-16 kernel (0 auto, 8, 16)
   int body_cap_set = 0;         // GMRES loop body cap (0: derived from max_iter), KFBI_OPT_BODY_CAP
   int sweep_cap_set = 0;        // refinement loop body cap (0: sweeps + 2), KFBI_OPT_SWEEP_CAP
   int cfg_version = 0;          // bumped by every option that changes the launched kernels

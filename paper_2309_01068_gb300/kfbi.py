@@ -25,6 +25,7 @@ OPT_PUSH_REDUCE = 9
 OPT_FUSE_INTERP = 10
 OPT_FUSE_DFT = 11
 OPT_BODY_CAP, OPT_SWEEP_CAP, OPT_COL_REG, OPT_COL_TC, OPT_COL_RADIX4, OPT_FUSE_ROWS = 12, 13, 14, 15, 16, 17
+OPT_COL_POINTS = 18
 MLP_FEATURES, MLP_MODES = 47, 16
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2

@@ -5,8 +5,8 @@
   oracle's fast solve (Sec. 4.2) to 1e-12 for every power of two from 32 to 4096, both box types
   (DST-II and DCT-II columns) and both of the kernel's pair counts, and against the radix-4
   shared-memory kernel (the same arithmetic up to rounding order);
-- float32: the apply of a mixed context against the same apply through the radix-4 kernel (both
-  float32) and against the oracle's float64 apply, for the three boxes (the free-space box leaves
+- float32: the apply of a mixed context (16 and 8 points per thread, every pair count) against
+  the same apply through the radix-4 kernel (both float32) and against the oracle's float64 apply, for the three boxes (the free-space box leaves
   rows without irregular nodes to the column kernel, which forms them from their box data).
 """
 import numpy as np
@@ -86,6 +86,14 @@ def test_float32_apply_radix16(N, boxbc, kappa, box):
         ctx.set_option(K.OPT_COL_PAIRS, min(16, 2 * max(1, 512 // N)))
         v16c, _, _ = ctx.apply(layer, dev(dens))
         ctx.set_option(K.OPT_COL_PAIRS, 0)
+        ctx.set_option(K.OPT_COL_POINTS, 8)
+        v8, _, _ = ctx.apply(layer, dev(dens))
+        ctx.set_option(K.OPT_COL_PAIRS, 1)
+        v8b, _, _ = ctx.apply(layer, dev(dens))
+        ctx.set_option(K.OPT_COL_PAIRS, 0)
+        ctx.set_option(K.OPT_COL_POINTS, 16)
+        v16d, _, _ = ctx.apply(layer, dev(dens))
+        ctx.set_option(K.OPT_COL_POINTS, 0)
         ctx.set_option(K.OPT_COL_RADIX4, 3)
         v4, _, _ = ctx.apply(layer, dev(dens))
         ctx.set_option(K.OPT_COL_RADIX4, 2)
@@ -94,6 +102,9 @@ def test_float32_apply_radix16(N, boxbc, kappa, box):
         assert rel(a, c) < 2e-5, (layer, rel(a, c))
         assert rel(b, c) < 2e-5, (layer, rel(b, c))
         assert rel(v16c.cpu().numpy(), c) < 2e-5, layer
+        assert rel(v8.cpu().numpy(), c) < 2e-5, layer    # 8 points per thread
+        assert rel(v8b.cpu().numpy(), c) < 2e-5, layer
+        assert rel(v16d.cpu().numpy(), c) < 2e-5, layer  # 16 points per thread
         rv, _, _ = ref.apply(OK.LAYER_DOUBLE if layer == K.DOUBLE else OK.LAYER_SINGLE, dens)
         assert rel(a, rv) < 2e-4, (layer, rel(a, rv))
     ctx.close()
@@ -101,6 +112,12 @@ def test_float32_apply_radix16(N, boxbc, kappa, box):
 
 def test_option_values():
     ctx = K.Context(64, (-1.0, 1.0, -1.0, 1.0), 0.0, OK.BOX_DIRICHLET0, K.MIXED, max_nodes=64)
+    assert ctx.get_option(K.OPT_COL_POINTS) == 0
+    for v in (8, 16, 0):
+        ctx.set_option(K.OPT_COL_POINTS, v)
+        assert ctx.get_option(K.OPT_COL_POINTS) == v
+    with pytest.raises(K.KfbiError):
+        ctx.set_option(K.OPT_COL_POINTS, 4)
     for v in (0, 1, 2, 3):
         ctx.set_option(K.OPT_COL_RADIX4, v)
         assert ctx.get_option(K.OPT_COL_RADIX4) == v
