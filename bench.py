@@ -673,6 +673,8 @@ def col_kernel_sizes(torch, K, hbm_peak, reps=200):
                     continue
                 if not f32 and r4 == 0 and N > 2048:  # no float64 radix-16 kernel at 4096^2
                     continue
+                if not f32 and form == "radix16_16pt":  # float64 has the 16-point form only
+                    continue
                 ctx.set_option(K.OPT_COL_REG, reg)
                 ctx.set_option(K.OPT_COL_TC, tc)
                 ctx.set_option(K.OPT_COL_RADIX4, r4)
