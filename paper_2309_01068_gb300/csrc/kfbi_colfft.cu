@@ -5,9 +5,10 @@
 //
 // Two real columns k, k + 1 form one complex sequence (Makhoul reordering: a DCT-II of length
 // N is a complex FFT of length N plus a rotation of each bin pair m, N - m). Each column pair
-// is owned by N/16 threads that hold 16 points each through the whole solve:
-//   stage 0      radix-16 DFT of points u + r N/16, read straight from the grid rows
-//   stages 1..   Stockham stages of radix 16 (the last one of radix 2, 4 or 8) through one
+// is owned by N/PT threads that hold PT points each (PT = 16, or 8 for twice the warps on
+// grids up to 1024) through the whole solve:
+//   stage 0      radix-PT DFT of points u + r N/PT, read straight from the grid rows
+//   stages 1..   Stockham stages of radix PT (the last one of radix 2, 4 or 8) through one
 //                padded shared-memory buffer per pair
 //   last stage   its outputs, the bins j + r N/R, stay in registers; the thread's butterflies
 //                are chosen so that it also holds every partner bin N - m, so the DCT post-
@@ -16,8 +17,11 @@
 //   inverse      the adjoint of each stage in reverse order (inverse DFT, then the conjugate
 //                twiddle, reading where the forward stage wrote and writing where it read),
 //                ending in the rows of the grid.
-// N = 1024 takes three stages (16, 16, 4): four shared-memory round trips and six barriers per
-// solve, against ten radix-4 stages of the shared-memory Stockham kernel.
+// With 16 points, N = 1024 takes three stages (16, 16, 4): four shared-memory round trips and
+// six barriers per solve, against ten radix-4 stages of the shared-memory Stockham kernel; with
+// 8 points four stages (8, 8, 8, 2).
+// FR (float32, 16 points): the kernel also forms its input rows from the irregular-node
+// corrections instead of reading the row transform's output (KFBI_OPT_FUSE_ROWS).
 #include <type_traits>
 #include <utility>
 

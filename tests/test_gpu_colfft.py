@@ -179,3 +179,21 @@ def test_rows_formed_in_the_column_kernel_follow_the_interface():
     assert np.array_equal(v2.cpu().numpy(), vf.cpu().numpy())
     ctx.close()
     fresh.close()
+
+
+def test_time_column_leaves_applies_unchanged():
+    """kfbi_time_column times the selected column kernel on the context's spectral-grid scratch;
+    the next apply rewrites that buffer, so its result is bit-identical to the one before."""
+    p = W.random_problem(901, N=256, n=200, kappa=0.0, boxbc=OK.BOX_FREESPACE_DL, box=1.5)
+    ctx = K.Context(p.N, p.box, 0.0, OK.BOX_FREESPACE_DL, K.MIXED, max_nodes=p.n)
+    ctx.set_interface(dev(p.xy))
+    dens = dev(W.random_density(9, p.n, modes=6))
+    v1, _, _ = ctx.apply(K.DOUBLE, dens)
+    t32 = ctx.time_column(True, 20)
+    t64 = ctx.time_column(False, 5)
+    assert 0.0 < t32 < 1e4 and 0.0 < t64 < 1e5
+    v2, _, _ = ctx.apply(K.DOUBLE, dens)
+    assert np.array_equal(v1.cpu().numpy(), v2.cpu().numpy())
+    with pytest.raises(K.KfbiError):
+        ctx.time_column(True, 0)
+    ctx.close()
