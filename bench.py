@@ -266,6 +266,26 @@ def time_applies(torch, K, ctx, reps=50):
     return reps / (e0.elapsed_time(e1) / 1e3)
 
 
+def l2_copy_peak(torch, mib=24, reps=200):
+    """L2-resident copy bandwidth (GB/s, read + write bytes): a `mib` MiB tensor copied into
+    another one back to back (both fit the 129 MB L2 together), CUDA events, best of 3."""
+    n = mib * (1 << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(20):
+        b.copy_(a)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2.0 * 4 * n * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
+
+
 def traffic_record(kernel_src, name):
     """DRAM traffic per launch from a committed ncu summary, if taken on this kernel source."""
     path = os.path.join(ROOT, "profiles", name)
@@ -973,6 +993,10 @@ def main():
         b2b_us = ctx.time_column(True, 400)
         b2b = dict(us=b2b_us, achieved=bytes_per_launch / (b2b_us * 1e-6) / 1e9,
                    frac=bytes_per_launch / (b2b_us * 1e-6) / 1e9 / hbm_peak, launches=400)
+        # the grid is L2-resident inside GMRES: the same bytes against the L2 copy bandwidth
+        l2_gbs = l2_copy_peak(torch)
+        b2b["l2"] = dict(bound="l2", peak=l2_gbs, unit="GB/s", frac=b2b["achieved"] / l2_gbs,
+                         peak_source="torch copy of a 24 MiB float32 tensor, L2-resident, measured in this run")
     roofline = dict(kernel=kname,
                     bound="hbm", achieved=achieved, peak=hbm_peak, unit="GB/s",
                     frac=(achieved / hbm_peak) if achieved else None,
