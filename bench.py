@@ -1003,6 +1003,11 @@ def main():
                     traffic=(tr["dram_bytes_per_launch"] if tr else None),
                     algorithmic_bytes_per_launch=bytes_per_launch, launches=tim["fp32_launches"],
                     mean_launch_us=f32_ms * 1e3, back_to_back=b2b,
+                    traffic_in_loop=(dict(dram_bytes=float(np.mean([a + b for a, b in zip(tr["in_loop"]["dram_bytes_read"],
+                                                                                        tr["in_loop"]["dram_bytes_write"])])),
+                                          l2_bytes=float(np.mean(tr["in_loop"]["l2_bytes"])),
+                                          note="caches kept between launches, as in the GMRES loop")
+                                     if tr and "in_loop" in tr else None),
                     peak_source="MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6.8 TB/s")
     # the same kernel against the float32 FMA roof: forward and inverse real transforms of N
     # columns of length N, 2.5 M log2 M flops each (split-radix count of a real FFT)
