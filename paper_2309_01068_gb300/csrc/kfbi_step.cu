@@ -63,34 +63,38 @@ __global__ void k_st_dft(const double* f, int stride, int nf, int n, const doubl
   int nk = n / 2 + 1;
   if (warp >= nk * nf) return;
   int q = warp / nk, k = warp - q * nk;
-  // twiddle index k j mod n advanced by k 32 mod n (no division in the loop); two
+  // twiddle index k j mod n advanced by k 32 mod n (no division in the loop); four
   // accumulator pairs shorten the float64 dependency chains
   int idx = (int)(((long)k * lane) % n);
   const int step = (int)(((long)k * 32) % n);
-  double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+  double re[4] = {0.0, 0.0, 0.0, 0.0}, im[4] = {0.0, 0.0, 0.0, 0.0};
   int j = lane;
-  for (; j + 32 < n; j += 64) {
-    const double v0 = f[(long)j * stride + q], v1 = f[(long)(j + 32) * stride + q];
-    const double2 w0 = tw[idx];
-    idx += step;
-    if (idx >= n) idx -= n;
-    const double2 w1 = tw[idx];
-    idx += step;
-    if (idx >= n) idx -= n;
-    re0 += v0 * w0.x;
-    im0 -= v0 * w0.y;
-    re1 += v1 * w1.x;
-    im1 -= v1 * w1.y;
+  for (; j + 96 < n; j += 128) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double v = f[(long)(j + 32 * c) * stride + q];
+      const double2 w = tw[idx];
+      idx += step;
+      if (idx >= n) idx -= n;
+      re[c] += v * w.x;
+      im[c] -= v * w.y;
+    }
   }
-  if (j < n) {
-    const double v = f[(long)j * stride + q];
-    const double2 w = tw[idx];
-    re0 += v * w.x;
-    im0 -= v * w.y;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (j < n) {
+      const double v = f[(long)j * stride + q];
+      const double2 w = tw[idx];
+      idx += step;
+      if (idx >= n) idx -= n;
+      re[c] += v * w.x;
+      im[c] -= v * w.y;
+      j += 32;
+    }
   }
-  const double re = warp_sum(re0 + re1);
-  const double im = warp_sum(im0 + im1);
-  if (lane == 0) coef[q * nk + k] = make_double2(re / n, im / n);
+  const double re_s = warp_sum((re[0] + re[1]) + (re[2] + re[3]));
+  const double im_s = warp_sum((im[0] + im[1]) + (im[2] + im[3]));
+  if (lane == 0) coef[q * nk + k] = make_double2(re_s / n, im_s / n);
 }
 
 // spectral multipliers applied to coefficient sets (k = 0..n/2):
