@@ -363,16 +363,17 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             jump kernel (a shared-memory FFT in every block) instead of a
  *                             separate DFT kernel; 0: the separate kernel.
  *   KFBI_OPT_COL_RADIX4       2 (default): float32 applies (grids with N >= 32) run the
- *                             register-resident radix-16 column kernel, float64 applies the
- *                             shared-memory radix-4 Stockham kernel. In the radix-16 kernel each
+ *                             register-resident column kernel (radix-16 stages with 16 points per
+ *                             thread, radix-8 with 8: KFBI_OPT_COL_POINTS), float64 applies the
+ *                             shared-memory radix-4 Stockham kernel. In the register kernel each
  *                             column pair is owned by N/16 threads holding 16 points through the
  *                             forward FFT, the eigenvalue division and the inverse (Stockham
  *                             stages of radix 16, the last of radix 2, 4 or 8, through one
  *                             shared-memory buffer). Bit 0 set (1, 3): float32 applies run the
  *                             radix-4 kernel; bit 1 clear (0, 1): float64 applies run the
  *                             radix-16 kernel. Values 0..3.
- *   KFBI_OPT_COL_POINTS       0 (default), 8 or 16: points per thread of the float32 radix-16
- *                             column kernel. 8: N/8 threads per column pair (twice the warps),
+ *   KFBI_OPT_COL_POINTS       0 (default), 8 or 16: points per thread of the float32
+ *                             register-resident column kernel. 8: N/8 threads per column pair (twice the warps),
  *                             Stockham stages of radix 8 (the last of radix 2 or 4; N = 1024 is
  *                             8, 8, 8, 2), available for N <= 1024 (16 is used above). 0: 8 for
  *                             N <= 1024, 16 above (the faster form at each size).
