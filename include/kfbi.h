@@ -374,9 +374,10 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             radix-16 kernel. Values 0..3.
  *   KFBI_OPT_COL_POINTS       0 (default), 8 or 16: points per thread of the float32
  *                             register-resident column kernel. 8: N/8 threads per column pair
- *                             (twice the warps), Stockham stages of radix 8 (the last of radix 2 or 4; N = 1024 is
- *                             8, 8, 8, 2), available for N <= 1024 (16 is used above). 0: 8 for
- *                             N <= 1024, 16 above (the faster form at each size).
+ *                             (twice the warps), Stockham stages of radix 8 (the last of radix
+ *                             2 or 4; N = 1024 is 8, 8, 8, 2), available for N <= 1024 (16 is
+ *                             used above). 0: 8 for N <= 1024, 16 above (the faster form at each
+ *                             size).
  *   KFBI_OPT_FUSE_ROWS        0 (default): the row transform is its own kernel. 1: float32
  *                             applies whose jumps come from the fused jump kernel
  *                             (KFBI_OPT_FUSE_DFT) and whose column solve is the radix-16 kernel
