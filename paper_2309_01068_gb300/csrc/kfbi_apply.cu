@@ -1290,9 +1290,11 @@ __global__ void k_interp(int n, const S_t* st, const T* pval, const T* Jall, con
     gx -= (T)0.5 * J[1];
     gy -= (T)0.5 * J[2];
   }
+  // explicit fused multiply-adds: the Gram-Schmidt kernel that forms these values itself
+  // (interp_finish) rounds them in the same order, independent of compiler contraction
   T o = cb * v;
-  if (x_in != nullptr) o += (eps_v != nullptr ? (T)eps_v[p] : ca) * x_in[p];
-  if (dint != nullptr) o += cc * (*dint);
+  if (x_in != nullptr) o = fma(eps_v != nullptr ? (T)eps_v[p] : ca, x_in[p], o);
+  if (dint != nullptr) o = fma(cc, *dint, o);
   out[p] = (double)o;
   if (dnormal != nullptr) dnormal[p] = (double)(nx * gx + ny * gy);
 }

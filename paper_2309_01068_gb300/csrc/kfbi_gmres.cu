@@ -403,7 +403,11 @@ __device__ __forceinline__ unsigned cl_size() {
 __device__ __forceinline__ void cl_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+// arrive without release semantics: no use orders memory through the barrier itself (the
+// mbarriers' initialisation is published by fence.mbarrier_init, received copies complete on
+// the receiver's mbarrier, remote loads have returned before the arrive), so the arrive need
+// not wait for this thread's outstanding loads
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
 __device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 
 // ---- push reductions: every CTA copies its partial sums into a receive row of every CTA of
@@ -821,7 +825,7 @@ __global__ void __launch_bounds__(GMF_THREADS, 1) k_gm_cluster(GmresCtl* ctl, T*
   }
   {
     static_assert(MAX_RESTART <= GMF_THREADS, "one rotation per thread");
-    constexpr int NB = sizeof(T) == 4 ? 16 : 8;
+    constexpr int NB = 4;  // loads in flight per thread and pass (longer unrolls measured slower)
     const int tid = (int)threadIdx.x;
     const int tot = K * len;
     double cs_r = 0.0, sn_r = 0.0, gj_r = 0.0, w_r = 0.0;

@@ -161,9 +161,9 @@ __device__ __forceinline__ T interp_finish(const InterpArgs<T>& a, const InterpP
   for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, 8);
   if (!active) return 0;
   if (J != nullptr) v -= (T)0.5 * J[0];
-  T out = a.cb * v;
-  if (a.x_in != nullptr) out += (a.eps_v != nullptr ? (T)a.eps_v[p] : a.ca) * a.x_in[p];
-  if (a.dint != nullptr) out += a.cc * (*a.dint);
+  T out = a.cb * v;  // the same explicit fused multiply-adds as k_interp
+  if (a.x_in != nullptr) out = fma(a.eps_v != nullptr ? (T)a.eps_v[p] : a.ca, a.x_in[p], out);
+  if (a.dint != nullptr) out = fma(a.cc, *a.dint, out);
   return out;
 }
 
