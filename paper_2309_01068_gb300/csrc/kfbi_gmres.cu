@@ -878,21 +878,21 @@ __global__ void __launch_bounds__(GMF_THREADS, 1) k_gm_cluster(GmresCtl* ctl, T*
   }
   if (ia.st != nullptr) gmf_w_slice(ia, pre, w, i0, len, sw);
   __syncthreads();
-  // two passes of classical Gram-Schmidt; the second also reduces ||w'||^2 (entry K)
-  cta_dots(sV, Rp, sw, len, K, false, part[0]);
-  if (push) {
-    cl_wait();  // every CTA's barriers are initialised
-    cl_push_reduce(part[0], recv0, &s_mbar[0], h1, K, cs, rank, &s_err);
-  } else {
-    cl_reduce(part[0], h1, K, cs);
+  // two passes of classical Gram-Schmidt; the second also reduces ||w'||^2 (entry K). The
+  // passes are a loop that is not unrolled: the second runs the first one's instructions again
+  // (already fetched) instead of an inlined copy of its own
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    T* hp = pass == 0 ? h1 : h2;
+    cta_dots(sV, Rp, sw, len, K, pass == 1, part[pass]);
+    if (push) {
+      if (pass == 0) cl_wait();  // every CTA's barriers are initialised
+      cl_push_reduce(part[pass], pass == 0 ? recv0 : recv1, &s_mbar[pass], hp, K + pass, cs, rank, &s_err);
+    } else {
+      cl_reduce(part[pass], hp, K + pass, cs);
+    }
+    cta_combine(sV, Rp, hp, K, len, sw, (T)-1);
   }
-  cta_combine(sV, Rp, h1, K, len, sw, (T)-1);
-  cta_dots(sV, Rp, sw, len, K, true, part[1]);
-  if (push)
-    cl_push_reduce(part[1], recv1, &s_mbar[1], h2, K + 1, cs, rank, &s_err);
-  else
-    cl_reduce(part[1], h2, K + 1, cs);
-  cta_combine(sV, Rp, h2, K, len, sw, (T)-1);
   // concurrently: warp 0 forms ||w''||^2 = ||w'||^2 - ||h2||^2, warp 1 applies the previous
   // rotations to the Hessenberg column h1 + h2
   if (threadIdx.x < 32) {
