@@ -165,6 +165,22 @@ kfbi_status kfbi_solve_bie(kfbi_ctx* ctx, int kind, const double* eps_v, const d
 kfbi_status kfbi_grid_solve(kfbi_ctx* ctx, const double* rhs, double* u);
 
 /*
+ * kfbi_grid_solve_mixed -- the same box solve as kfbi_grid_solve for KFBI_MIXED contexts,
+ * by mixed-precision iterative refinement (not in the paper; Sec. 4.2's solve is its inner
+ * step): u = the float32 solve of rhs (row transforms, column solve and eigenvalue division on
+ * the float32 spectral grid with the float32 tables), then `sweeps` corrections
+ *   r = rhs - (Delta_h - kappa) u   (float64, five-point Laplacian with the box condition's
+ *                                    ghost values: u_{-1} = -u_0 for DST-II, u_0 for DCT-II),
+ *   u += the float32 solve of r     (r rounded to float32).
+ * Each sweep reduces the error of u by about the float32 solve's relative accuracy; two
+ * sweeps reach the float64 solve's accuracy on the Stefan workloads (tests).
+ *   rhs, u  device [N][N] float64, must not alias; sweeps 0..8. Asynchronous; uses the
+ *           context's spectral buffer. Errors: ARG (NULL, aliasing, sweeps out of range,
+ *           a KFBI_FP64 context), CUDA.
+ */
+kfbi_status kfbi_grid_solve_mixed(kfbi_ctx* ctx, const double* rhs, double* u, int sweeps);
+
+/*
  * kfbi_interp_grid -- values at the interface nodes of a smooth grid function by the
  * 6-point interpolation of Sec. 4.3 with zero jumps.
  *   grid    device [N][N] float64;  values  device [n] float64
@@ -401,6 +417,13 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             epilogue, then the inverse transform matrix. The row transform then
  *                             writes every row. Setting it allocates the two N x N matrices.
  *                             Takes precedence over KFBI_OPT_COL_REG and KFBI_OPT_COL_RADIX4.
+ *   KFBI_OPT_GRID_IR          2 (default), 0..8: in KFBI_MIXED contexts the Stefan step's two
+ *                             dense grid solves run by mixed-precision refinement with this many
+ *                             float64 correction sweeps: T1 as kfbi_grid_solve_mixed, and the
+ *                             single layer's grid values (T2) as the same solve with the
+ *                             corrected right-hand side of the float64 jumps at the irregular
+ *                             nodes (the apply's column solve and interface values are not
+ *                             formed). 0: float64 solves (kfbi_grid_solve and the float64 apply).
  *   KFBI_OPT_BODY_CAP         0 (default): the device-side GMRES loop (the body count of the
  *                             graph's WHILE node, or of the host-driven loop) stops after
  *                             2 max_iter + 2 max_iter / restart + 8 bodies; a value > 0 sets
@@ -433,7 +456,8 @@ enum {
   KFBI_OPT_COL_TC = 15,
   KFBI_OPT_COL_RADIX4 = 16,
   KFBI_OPT_FUSE_ROWS = 17,
-  KFBI_OPT_COL_POINTS = 18
+  KFBI_OPT_COL_POINTS = 18,
+  KFBI_OPT_GRID_IR = 19
 };
 kfbi_status kfbi_set_option(kfbi_ctx* ctx, int option, int value);
 kfbi_status kfbi_get_option(kfbi_ctx* ctx, int option, int* value);

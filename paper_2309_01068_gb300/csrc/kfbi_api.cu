@@ -81,7 +81,9 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
   cudaFree(c->cr_alpha); cudaFree(c->cr_xi); cudaFree(c->tgeo); cudaFree(c->tgeo_f); cudaFree(c->irr);
   cudaFree(c->tstart); cudaFree(c->tstart_f); cudaFree(c->jumps);
   cudaFree(c->irr_ci); cudaFree(c->arm_slot); cudaFree(c->arm_rev); cudaFree(c->arm_coef);
+  cudaFree(c->corr_val); cudaFree(c->corr_pos);
   c->irr_ci = nullptr; c->arm_slot = nullptr; c->arm_rev = nullptr; c->arm_coef = nullptr;
+  c->corr_val = nullptr; c->corr_pos = nullptr;
   c->cr_kind = c->cr_line = c->cr_seg = c->cr_first = nullptr;
   c->cr_alpha = c->cr_xi = nullptr;
   c->tgeo = nullptr; c->tgeo_f = nullptr; c->irr = nullptr;
@@ -99,6 +101,8 @@ kfbi_status ensure_cross_capacity(kfbi_ctx* c, int ncr) {
   KFBI_CHECK(dalloc(&c->irr, cap_irr));
   KFBI_CHECK(dalloc(&c->irr_ci, cap_irr));
   KFBI_CHECK(dalloc(&c->arm_slot, 4 * (size_t)cap_irr));
+  KFBI_CHECK(dalloc(&c->corr_val, cap_irr));
+  KFBI_CHECK(dalloc(&c->corr_pos, cap_irr));
   KFBI_CHECK(dalloc(&c->arm_rev, 2 * (size_t)cap));
   KFBI_CHECK(dalloc(&c->arm_coef, 4 * (size_t)cap));
   KFBI_CHECK(dalloc(&c->tstart, 2 * (size_t)TSTART_STRIDE * ((size_t)cap + c->max_nodes)));
@@ -119,7 +123,7 @@ static void free_all(kfbi_ctx* c) {
                   c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gVf, c->gpart, c->gw,
                   c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag, c->irctl, c->ir_b, c->ir_x, c->ir_dn,
                   c->col_fwd, c->col_inv, c->col_tmp, c->col_tc_err, c->irr_ci, c->arm_slot, c->arm_rev,
-                  c->arm_coef};
+                  c->arm_coef, c->corr_val, c->corr_pos};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->host_counts) cudaFreeHost(c->host_counts);
@@ -388,6 +392,15 @@ kfbi_status kfbi_grid_solve(kfbi_ctx* c, const double* rhs, double* u) {
   return st;
 }
 
+kfbi_status kfbi_grid_solve_mixed(kfbi_ctx* c, const double* rhs, double* u, int sweeps) {
+  if (!ctx_ok(c) || rhs == nullptr || u == nullptr || rhs == u || sweeps < 0 || sweeps > 8) return KFBI_ERR_ARG;
+  if (c->precision != KFBI_MIXED) return KFBI_ERR_ARG;
+  KFBI_TRY(stream_enter(c));
+  kfbi_status st = grid_solve_mixed_enqueue(c, rhs, u, sweeps);
+  KFBI_TRY(stream_exit(c));
+  return st;
+}
+
 kfbi_status kfbi_interp_grid(kfbi_ctx* c, const double* grid, double* values) {
   if (!ctx_ok(c) || grid == nullptr || values == nullptr) return KFBI_ERR_ARG;
   if (!c->have_iface) return KFBI_ERR_STATE;
@@ -490,6 +503,11 @@ kfbi_status kfbi_set_option(kfbi_ctx* c, int option, int value) {
     c->cfg_version += 1;
     return KFBI_OK;
   }
+  if (option == KFBI_OPT_GRID_IR) {
+    if (value < 0 || value > 8) return KFBI_ERR_ARG;
+    c->grid_ir = value;
+    return KFBI_OK;
+  }
   if (option == KFBI_OPT_COL_POINTS) {
     if (value != 0 && value != 8 && value != 16) return KFBI_ERR_ARG;
     c->col_pt = value;
@@ -563,6 +581,7 @@ kfbi_status kfbi_get_option(kfbi_ctx* c, int option, int* value) {
   else if (option == KFBI_OPT_COL_TC) *value = c->col_tc ? 1 : 0;
   else if (option == KFBI_OPT_COL_RADIX4) *value = c->col_radix4;
   else if (option == KFBI_OPT_COL_POINTS) *value = c->col_pt;
+  else if (option == KFBI_OPT_GRID_IR) *value = c->grid_ir;
   else if (option == KFBI_OPT_FUSE_ROWS) *value = c->fuse_rows ? 1 : 0;
   else if (option == KFBI_OPT_BODY_CAP) *value = c->body_cap_set;
   else if (option == KFBI_OPT_SWEEP_CAP) *value = c->sweep_cap_set;

@@ -1169,11 +1169,16 @@ __global__ void __launch_bounds__(256, 4) k_probe_values(int N, int dct, const i
 }
 
 // Dense transforms along x of row pairs (grid output and the plain box solve).
-// forward: spec[j][.] = DST-II/DCT-II of rhs[j][.] (rhs float64, mode order);
-// inverse: out[j][.] = exact inverse of spec[j][.] (out float64).
-template <typename T>
-__global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* tw, const T* tab, const double* rhs,
-                            T* spec, double* out) {
+// inverse = 0, forward: spec[j][.] = DST-II/DCT-II of rhs[j][.] (rhs float64 or float32, mode
+// order); inverse = 1: out[j][.] = exact inverse of spec[j][.] (out float64); inverse = 2: the
+// inverse added to out[j][.] (a correction of the mixed-precision grid solve).
+template <typename X>
+struct NoDeduce {
+  using type = X;
+};
+template <typename T, typename In = double>
+__global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* tw, const T* tab,
+                            const typename NoDeduce<In>::type* rhs, T* spec, double* out) {
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
   V2<T>* B = A + N;
@@ -1227,7 +1232,11 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
       int r = t / N, i = t - r * N;
       T v = ((const T*)&Z[mk_pos(i, N)])[r] * invN;
       if (!dct && (i & 1)) v = -v;
-      out[(long)(j0 + r) * N + i] = (double)v;
+      const long o = (long)(j0 + r) * N + i;
+      if (inverse == 2)
+        out[o] += (double)v;
+      else
+        out[o] = (double)v;
     }
   }
 }
@@ -1472,12 +1481,13 @@ static kfbi_status time_column(kfbi_ctx* c, bool fp32, int reps, double* us) {
   return st;
 }
 
-template <typename T>
-static kfbi_status launch_row_dense(kfbi_ctx* c, int inverse, const double* rhs, T* spec, double* out) {
+template <typename T, typename In = double>
+static kfbi_status launch_row_dense(kfbi_ctx* c, int inverse, const typename NoDeduce<In>::type* rhs, T* spec,
+                                    double* out) {
   const int N = c->N;
   size_t smem = 2 * sizeof(V2<T>) * (size_t)N;
-  k_row_dense<T><<<N / 2, 256, smem, c->stream>>>(N, c->logN, c->boxbc == KFBI_BOX_NEUMANN0, inverse, Tabs<T>::stw(c),
-                                                 Tabs<T>::sin(c), rhs, spec, out);
+  k_row_dense<T, In><<<N / 2, 256, smem, c->stream>>>(N, c->logN, c->boxbc == KFBI_BOX_NEUMANN0, inverse,
+                                                     Tabs<T>::stw(c), Tabs<T>::sin(c), rhs, spec, out);
   launched(c, 1);
   return KFBI_OK;
 }
@@ -1658,6 +1668,8 @@ static kfbi_status setup_t(kfbi_ctx*) {
   for (int lg = 4; lg <= 12; ++lg)
     KFBI_TRY(cudaFuncSetAttribute(col_kernel<T>(lg), cudaFuncAttributeMaxDynamicSharedMemorySize, col));
   KFBI_TRY(cudaFuncSetAttribute(k_row_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
+  if constexpr (sizeof(T) == 4)  // the float32 residual input of the mixed grid solve
+    KFBI_TRY((cudaFuncSetAttribute(k_row_dense<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, row)));
   KFBI_TRY(cudaFuncSetAttribute(k_face_dst<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
   KFBI_TRY(cudaFuncSetAttribute(k_dens_coef<T, true, S_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
   KFBI_TRY(cudaFuncSetAttribute(k_box_data<T, T4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
@@ -1736,6 +1748,155 @@ kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u) {
   KFBI_CHECK(launch_row_dense<double>(c, 0, rhs, spec, nullptr));
   KFBI_CHECK(launch_col_solve<double>(c, spec, nullptr, c->zero_flag));
   KFBI_CHECK(launch_row_dense<double>(c, 1, nullptr, spec, u));
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
+// r = rhs - (Delta_h - kappa) u, rounded to float32 (the right-hand side of a float32
+// correction solve). Delta_h is the five-point Laplacian whose eigenvectors the solve's
+// transforms are: cell-centred, with the ghost values of the box condition, u_{-1} = -u_0,
+// u_N = -u_{N-1} (DST-II, Dirichlet) or u_{-1} = u_0, u_N = u_{N-1} (DCT-II, Neumann); the
+// residual is formed in float64 (Sec. 4.2's operator; the refinement is not in the paper).
+__device__ __forceinline__ double grid_au(int N, int dct, double inv_h2, double kappa, const double* u, long idx) {
+  const int j = (int)(idx / N), i = (int)(idx - (long)j * N);
+  const double c = u[idx];
+  const double g = dct ? c : -c;  // ghost value across the box face
+  const double w = i > 0 ? u[idx - 1] : g;
+  const double e = i < N - 1 ? u[idx + 1] : g;
+  const double so = j > 0 ? u[idx - N] : g;
+  const double no = j < N - 1 ? u[idx + N] : g;
+  return ((w + e) + (so + no) - 4.0 * c) * inv_h2 - kappa * c;
+}
+// rhs = nullptr: a right-hand side that is zero here (the sparse corrections are put in by
+// k_resid_fix)
+__global__ void k_grid_resid(int N, int dct, double inv_h2, double kappa, const double* rhs, const double* u,
+                             float* r) {
+  const long NN = (long)N * N;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NN) return;
+  const double f = rhs != nullptr ? rhs[idx] : 0.0;
+  r[idx] = (float)(f - grid_au(N, dct, inv_h2, kappa, u, idx));
+}
+
+// The corrected right-hand side of the apply's grid solve at each irregular node (the value
+// k_row_forward transforms: sign / h^2 times the arms' J0 + d J1 + d^2 J2 / 2), with its grid
+// index; one block per row.
+__global__ void k_corr_nodes(int N, const int* row_ptr, const IrrNode* irr, const double* J, double inv_h2,
+                             double* cval, int* cpos) {
+  const int j = blockIdx.x;
+  const int b = row_ptr[j], e = row_ptr[j + 1];
+  for (int t = b + (int)threadIdx.x; t < e; t += blockDim.x) {
+    const IrrRegs<double> node = irr_regs<double>(irr[t]);
+    double sum = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int tg = node.tg[a];
+      if (tg < 0) continue;
+      const double* jj = J + (long)tg * 6;
+      const double d = node.d[a];
+      const double j1 = a < 2 ? jj[1] : jj[2];
+      const double j2 = a < 2 ? jj[3] : jj[4];
+      sum += jj[0] + d * j1 + 0.5 * d * d * j2;
+    }
+    cval[t] = node.sign * inv_h2 * sum;
+    cpos[t] = j * N + node.i;
+  }
+}
+// r[pos] = the correction (float32) at every irregular node (r zero elsewhere)
+__global__ void k_corr_scatter(const int* nirr, const double* cval, const int* cpos, float* r) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < *nirr) r[cpos[q]] = (float)cval[q];
+}
+// the residual at the irregular nodes, where the right-hand side is the correction
+__global__ void k_resid_fix(int N, int dct, double inv_h2, double kappa, const int* nirr, const double* cval,
+                            const int* cpos, const double* u, float* r) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= *nirr) return;
+  const long idx = cpos[q];
+  r[idx] = (float)(cval[q] - grid_au(N, dct, inv_h2, kappa, u, idx));
+}
+
+// Mixed-precision box solve: u = (Delta_h - kappa)^{-1} rhs by a float32 solve (rows, columns,
+// rows as in grid_solve_enqueue, float32 spectral grid and tables), then `sweeps` corrections:
+// r = rhs - (Delta_h - kappa) u in float64, u += the float32 solve of r. The float32 grid and
+// the residual share the float64 spectral buffer (N^2 floats each). rhs and u must not alias.
+kfbi_status grid_solve_mixed_enqueue(kfbi_ctx* c, const double* rhs, double* u, int sweeps) {
+  if (c->precision != KFBI_MIXED) return KFBI_ERR_ARG;
+  const int N = c->N;
+  const long NN = (long)N * N;
+  float* specf = (float*)c->spec;
+  float* r = specf + NN;
+  KFBI_CHECK(launch_row_dense<float>(c, 0, rhs, specf, nullptr));
+  KFBI_CHECK(launch_col_solve<float>(c, specf, nullptr, c->zero_flag));
+  KFBI_CHECK(launch_row_dense<float>(c, 1, nullptr, specf, u));
+  for (int sw = 0; sw < sweeps; ++sw) {
+    k_grid_resid<<<cdiv(NN, 256), 256, 0, c->stream>>>(N, c->boxbc == KFBI_BOX_NEUMANN0, 1.0 / (c->h * c->h), c->kappa,
+                                                        rhs, u, r);
+    launched(c, 1);
+    KFBI_CHECK((launch_row_dense<float, float>(c, 0, r, specf, nullptr)));
+    KFBI_CHECK(launch_col_solve<float>(c, specf, nullptr, c->zero_flag));
+    KFBI_CHECK(launch_row_dense<float>(c, 2, nullptr, specf, u));
+  }
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
+// Grid output of a layer potential (the apply's grid solve (Delta_h - kappa) u = C with the
+// corrected right-hand side C of its float64 jumps, Sec. 4.2) for KFBI_MIXED contexts without
+// box data: the float64 density coefficients and jumps, C at the irregular nodes (float64),
+// then the mixed-precision box solve of grid_solve_mixed_enqueue with C as a sparse
+// right-hand side: u = the float32 solve of C, `sweeps` times r = C - (Delta_h - kappa) u
+// (float64), u += the float32 solve of r. The interface values of the apply are not formed.
+kfbi_status apply_grid_mixed_enqueue(kfbi_ctx* c, int layer, const double* density, double* grid, int sweeps) {
+  if (c->precision != KFBI_MIXED || c->boxbc == KFBI_BOX_FREESPACE_DL) return KFBI_ERR_ARG;
+  using T = double;
+  cudaStream_t s = c->stream;
+  const int N = c->N, n = c->n, nk = n / 2 + 1;
+  const long NN = (long)N * N;
+  const int* skip = c->zero_flag;
+  const int dct = c->boxbc == KFBI_BOX_NEUMANN0;
+  const double inv_h2 = 1.0 / (c->h * c->h);
+  V2<T>* coef = (V2<T>*)c->dcoef;
+  T* J = (T*)c->jumps;
+  const int* d_ncr = c->seg_off + 2 * SUBSAMPLES * n;
+  const int ntg_cap = c->ncr_grid + n;
+  using G = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::geo(c))>::type>::type;
+  using SD = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(c))>::type>::type;
+  // the density's coefficients and the jumps at every target, as apply_t<double> forms them
+  const size_t smd = (size_t)n * (sizeof(V2<T>) + sizeof(T));
+  if (smd <= SMEM_STAGE_MAX)
+    KFBI_TRY(launch_k(c->use_pdl, k_dens_coef<T, true, SD>, dim3(cdiv((long)nk * 32, 256)), dim3(256), smd, s,
+                      density, n, Tabs<T>::twn(c), Tabs<T>::stencil(c), coef, (T*)nullptr, skip));
+  else
+    k_dens_coef<T, false><<<cdiv((long)nk * 32, 256), 256, 0, s>>>(density, n, Tabs<T>::twn(c), Tabs<T>::stencil(c),
+                                                                   coef, nullptr, skip);
+  const size_t smj = (size_t)jump_layout_size(n) * sizeof(V2<T>);
+  if (smj <= SMEM_STAGE_MAX)
+    KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, true>, dim3(cdiv((long)ntg_cap * 32, 256)), dim3(256), smj, s,
+                      (const V2<T>*)coef, n, d_ncr, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
+  else
+    KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, false>, dim3(cdiv((long)ntg_cap * 32, 256)), dim3(256), 0, s,
+                      (const V2<T>*)coef, n, d_ncr, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
+  // the corrections, scattered (float32) into the residual buffer
+  float* specf = (float*)c->spec;
+  float* r = specf + NN;
+  const int* nirr = c->row_ptr + N;  // irregular-node count (device)
+  const int qb = cdiv(c->cap_irr, 256);
+  k_corr_nodes<<<N, ROW_THREADS, 0, s>>>(N, c->row_ptr, (const IrrNode*)c->irr, J, inv_h2, c->corr_val, c->corr_pos);
+  KFBI_TRY(cudaMemsetAsync(r, 0, sizeof(float) * (size_t)NN, s));
+  k_corr_scatter<<<qb, 256, 0, s>>>(nirr, c->corr_val, c->corr_pos, r);
+  launched(c, 4);
+  KFBI_CHECK((launch_row_dense<float, float>(c, 0, r, specf, nullptr)));
+  KFBI_CHECK(launch_col_solve<float>(c, specf, nullptr, skip));
+  KFBI_CHECK(launch_row_dense<float>(c, 1, nullptr, specf, grid));
+  for (int sw = 0; sw < sweeps; ++sw) {
+    k_grid_resid<<<cdiv(NN, 256), 256, 0, s>>>(N, dct, inv_h2, c->kappa, nullptr, grid, r);
+    k_resid_fix<<<qb, 256, 0, s>>>(N, dct, inv_h2, c->kappa, nirr, c->corr_val, c->corr_pos, grid, r);
+    launched(c, 2);
+    KFBI_CHECK((launch_row_dense<float, float>(c, 0, r, specf, nullptr)));
+    KFBI_CHECK(launch_col_solve<float>(c, specf, nullptr, skip));
+    KFBI_CHECK(launch_row_dense<float>(c, 2, nullptr, specf, grid));
+  }
   KFBI_TRY(cudaGetLastError());
   return KFBI_OK;
 }

@@ -284,7 +284,10 @@ struct kfbi_ctx {
   float* arm_slot = nullptr;    // [cap_irr][4]
   int* arm_rev = nullptr;       // [cap_cross][2]
   float* arm_coef = nullptr;    // [cap_cross][2][2]
+  double* corr_val = nullptr;   // [cap_irr] correction at each irregular node (mixed grid output)
+  int* corr_pos = nullptr;      // [cap_irr] its grid index j N + i
   bool fuse_rows = false;       // KFBI_OPT_FUSE_ROWS
+  int grid_ir = 2;              // KFBI_OPT_GRID_IR: correction sweeps of mixed grid solves
   kfbi::Stencil* stencil = nullptr;  // [max_nodes]
   kfbi::StencilF* stencil_f = nullptr;
   float* dens_f = nullptr;      // [max_nodes] float32 copy of the apply's density
@@ -553,6 +556,8 @@ kfbi_status apply_enqueue(kfbi_ctx* c, int layer, bool fp32, const double* densi
 // would read), for a consumer that forms the values itself (skip_interp = true)
 InterpArgs<float> interp_args_f32(kfbi_ctx* c, int bie_kind, const double* eps_v, const float* density_f);
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u);
+kfbi_status grid_solve_mixed_enqueue(kfbi_ctx* c, const double* rhs, double* u, int sweeps);
+kfbi_status apply_grid_mixed_enqueue(kfbi_ctx* c, int layer, const double* density, double* grid, int sweeps);
 // free-space box: fills boxK / boxK_f for the current interface (after the node data)
 constexpr size_t BOXK_MAX_BYTES = (size_t)1 << 30;
 constexpr size_t RINV_MAX_BYTES = (size_t)1 << 27;

@@ -552,8 +552,17 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
     if (steps == 0.0) k_st_T0<<<gb, 256, 0, s>>>(c->side, NN, P.St, st->T, st->Tprev);
     launched(c, (steps == 0.0) + 3);
     k_st_bdf_rhs<<<gb, 256, 0, s>>>(st->T, st->Tprev, NN, dt, st->Tw);
-    KFBI_CHECK(grid_solve_enqueue(c, st->Tw, st->Tw));  // T1 in Tw
-    KFBI_CHECK(interp_grid_enqueue(c, st->Tw, st->dn));  // T1 at the nodes
+    // T1: in place by the float64 solve (T1 in Tw, the grid single layer later in Sg), or by
+    // the mixed-precision solve, which keeps its right-hand side (T1 in Sg, the single layer
+    // later in Tw)
+    const bool ir = c->precision == KFBI_MIXED && c->grid_ir > 0;
+    double* T1 = ir ? st->Sg : st->Tw;
+    double* S2 = ir ? st->Tw : st->Sg;
+    if (ir)
+      KFBI_CHECK(grid_solve_mixed_enqueue(c, st->Tw, T1, c->grid_ir));
+    else
+      KFBI_CHECK(grid_solve_enqueue(c, st->Tw, T1));
+    KFBI_CHECK(interp_grid_enqueue(c, T1, st->dn));  // T1 at the nodes
     k_st_stefan_rhs<<<tb, 256, 0, s>>>(st->eta, st->th_a, st->dn, n, st->scal, P.eps_c, P.eps_aniso, P.fold, P.eps_v,
                                        st->rhs, st->epsv, st->work + 2 * n);
     ratio = st->work + 2 * n;
@@ -565,8 +574,13 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
     sst = solve_bie_impl(c, KFBI_BIE_STEFAN_SL, st->epsv, st->rhs, P.tol, P.max_iter, P.restart, st->density, &si);
     if (sst != KFBI_OK && sst != KFBI_ERR_NOT_CONVERGED) return sst;
     // T2 = -(S psi)_h from the apply's grid output; T^{n+1} = T1 + T2
-    KFBI_CHECK(apply_enqueue(c, KFBI_SINGLE, false, st->density, st->V, nullptr, st->Sg, -1, nullptr, nullptr));
-    k_st_T_update<<<gb, 256, 0, s>>>(st->Tw, st->Sg, NN, st->T, st->Tprev);
+    // (mixed: the grid solve of the single layer by the same mixed-precision box solve, with
+    // its corrected right-hand side from the float64 jumps)
+    if (ir)
+      KFBI_CHECK(apply_grid_mixed_enqueue(c, KFBI_SINGLE, st->density, S2, c->grid_ir));
+    else
+      KFBI_CHECK(apply_enqueue(c, KFBI_SINGLE, false, st->density, st->V, nullptr, S2, -1, nullptr, nullptr));
+    k_st_T_update<<<gb, 256, 0, s>>>(T1, S2, NN, st->T, st->Tprev);
     k_st_copy<<<tb, 256, 0, s>>>(st->density, st->U, n);
   }
   KFBI_TRY(cudaGetLastError());

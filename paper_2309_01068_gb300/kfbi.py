@@ -26,6 +26,7 @@ OPT_FUSE_INTERP = 10
 OPT_FUSE_DFT = 11
 OPT_BODY_CAP, OPT_SWEEP_CAP, OPT_COL_REG, OPT_COL_TC, OPT_COL_RADIX4, OPT_FUSE_ROWS = 12, 13, 14, 15, 16, 17
 OPT_COL_POINTS = 18
+OPT_GRID_IR = 19
 MLP_FEATURES, MLP_MODES = 47, 16
 ERR_SINGULAR, ERR_TIMEOUT, ERR_STATE, ERR_CAPACITY = 6, 7, 8, 9
 BOX_DIRICHLET0, BOX_NEUMANN0, BOX_FREESPACE_DL = 0, 1, 2
@@ -78,6 +79,7 @@ _SIGNATURES = {
     "kfbi_bie_apply": (_I, [_P, _I, _P, _P, _P]),
     "kfbi_solve_bie": (_I, [_P, _I, _P, _P, _D, _I, _I, _P, ctypes.POINTER(SolveInfo)]),
     "kfbi_grid_solve": (_I, [_P, _P, _P]),
+    "kfbi_grid_solve_mixed": (_I, [_P, _P, _P, _I]),
     "kfbi_interp_grid": (_I, [_P, _P, _P]),
     "kfbi_interface_stats": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "kfbi_copy_sides": (_I, [_P, _P]),
@@ -270,6 +272,15 @@ class Context:
         self._sync_stream()
         u = out if out is not None else torch.empty_like(rhs)
         _check(self.lib.kfbi_grid_solve(self.handle, _f64(rhs, (self.N, self.N)), _ptr(u)), "kfbi_grid_solve")
+        return u
+
+    def grid_solve_mixed(self, rhs, sweeps=2, out=None):
+        """kfbi_grid_solve_mixed (KFBI_MIXED contexts): float32 box solves with `sweeps` float64
+        residual corrections; `out` must not be `rhs`."""
+        self._sync_stream()
+        u = out if out is not None else torch.empty_like(rhs)
+        _check(self.lib.kfbi_grid_solve_mixed(self.handle, _f64(rhs, (self.N, self.N)), _ptr(u), int(sweeps)),
+               "kfbi_grid_solve_mixed")
         return u
 
     def interp_grid(self, grid):
