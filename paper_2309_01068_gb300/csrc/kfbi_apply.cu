@@ -1486,7 +1486,9 @@ static kfbi_status launch_row_dense(kfbi_ctx* c, int inverse, const typename NoD
                                     double* out) {
   const int N = c->N;
   size_t smem = 2 * sizeof(V2<T>) * (size_t)N;
-  k_row_dense<T, In><<<N / 2, 256, smem, c->stream>>>(N, c->logN, c->boxbc == KFBI_BOX_NEUMANN0, inverse,
+  // float32: 512 threads per row pair (16 warps of latency hiding per block; 256 measured 3 %
+  // slower on the Stefan 4096^2 step)
+  k_row_dense<T, In><<<N / 2, sizeof(T) == 4 ? 512 : 256, smem, c->stream>>>(N, c->logN, c->boxbc == KFBI_BOX_NEUMANN0, inverse,
                                                      Tabs<T>::stw(c), Tabs<T>::sin(c), rhs, spec, out);
   launched(c, 1);
   return KFBI_OK;
@@ -1757,25 +1759,28 @@ kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u) {
 // transforms are: cell-centred, with the ghost values of the box condition, u_{-1} = -u_0,
 // u_N = -u_{N-1} (DST-II, Dirichlet) or u_{-1} = u_0, u_N = u_{N-1} (DCT-II, Neumann); the
 // residual is formed in float64 (Sec. 4.2's operator; the refinement is not in the paper).
-__device__ __forceinline__ double grid_au(int N, int dct, double inv_h2, double kappa, const double* u, long idx) {
-  const int j = (int)(idx / N), i = (int)(idx - (long)j * N);
+// f - (Delta_h - kappa) u at grid node (i, j) = f + (4 / h^2 + kappa) u_ij - (sum of the four
+// neighbours) / h^2, d4 = 4 / h^2 + kappa (five float64 operations: on this part the float64
+// rate, not memory, bounds a pass over the grid)
+__device__ __forceinline__ double grid_resid_at(int N, int dct, double inv_h2, double d4, double f, const double* u,
+                                                int i, int j) {
+  const long idx = (long)j * N + i;
   const double c = u[idx];
   const double g = dct ? c : -c;  // ghost value across the box face
   const double w = i > 0 ? u[idx - 1] : g;
   const double e = i < N - 1 ? u[idx + 1] : g;
   const double so = j > 0 ? u[idx - N] : g;
   const double no = j < N - 1 ? u[idx + N] : g;
-  return ((w + e) + (so + no) - 4.0 * c) * inv_h2 - kappa * c;
+  return fma(-inv_h2, (w + e) + (so + no), fma(d4, c, f));
 }
-// rhs = nullptr: a right-hand side that is zero here (the sparse corrections are put in by
-// k_resid_fix)
-__global__ void k_grid_resid(int N, int dct, double inv_h2, double kappa, const double* rhs, const double* u,
-                             float* r) {
-  const long NN = (long)N * N;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= NN) return;
+// one row per blockIdx.y; rhs = nullptr: a right-hand side that is zero here (the sparse
+// corrections are put in by k_resid_fix)
+__global__ void k_grid_resid(int N, int dct, double inv_h2, double d4, const double* rhs, const double* u, float* r) {
+  const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const long idx = (long)j * N + i;
   const double f = rhs != nullptr ? rhs[idx] : 0.0;
-  r[idx] = (float)(f - grid_au(N, dct, inv_h2, kappa, u, idx));
+  r[idx] = (float)grid_resid_at(N, dct, inv_h2, d4, f, u, i, j);
 }
 
 // The corrected right-hand side of the apply's grid solve at each irregular node (the value
@@ -1808,12 +1813,12 @@ __global__ void k_corr_scatter(const int* nirr, const double* cval, const int* c
   if (q < *nirr) r[cpos[q]] = (float)cval[q];
 }
 // the residual at the irregular nodes, where the right-hand side is the correction
-__global__ void k_resid_fix(int N, int dct, double inv_h2, double kappa, const int* nirr, const double* cval,
+__global__ void k_resid_fix(int N, int dct, double inv_h2, double d4, const int* nirr, const double* cval,
                             const int* cpos, const double* u, float* r) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= *nirr) return;
-  const long idx = cpos[q];
-  r[idx] = (float)(cval[q] - grid_au(N, dct, inv_h2, kappa, u, idx));
+  const int pos = cpos[q], j = pos / N, i = pos - j * N;
+  r[pos] = (float)grid_resid_at(N, dct, inv_h2, d4, cval[q], u, i, j);
 }
 
 // Mixed-precision box solve: u = (Delta_h - kappa)^{-1} rhs by a float32 solve (rows, columns,
@@ -1830,8 +1835,9 @@ kfbi_status grid_solve_mixed_enqueue(kfbi_ctx* c, const double* rhs, double* u, 
   KFBI_CHECK(launch_col_solve<float>(c, specf, nullptr, c->zero_flag));
   KFBI_CHECK(launch_row_dense<float>(c, 1, nullptr, specf, u));
   for (int sw = 0; sw < sweeps; ++sw) {
-    k_grid_resid<<<cdiv(NN, 256), 256, 0, c->stream>>>(N, c->boxbc == KFBI_BOX_NEUMANN0, 1.0 / (c->h * c->h), c->kappa,
-                                                        rhs, u, r);
+    const double inv_h2 = 1.0 / (c->h * c->h);
+    k_grid_resid<<<dim3(cdiv(N, 256), N), 256, 0, c->stream>>>(N, c->boxbc == KFBI_BOX_NEUMANN0, inv_h2,
+                                                               4.0 * inv_h2 + c->kappa, rhs, u, r);
     launched(c, 1);
     KFBI_CHECK((launch_row_dense<float, float>(c, 0, r, specf, nullptr)));
     KFBI_CHECK(launch_col_solve<float>(c, specf, nullptr, c->zero_flag));
@@ -1890,8 +1896,9 @@ kfbi_status apply_grid_mixed_enqueue(kfbi_ctx* c, int layer, const double* densi
   KFBI_CHECK(launch_col_solve<float>(c, specf, nullptr, skip));
   KFBI_CHECK(launch_row_dense<float>(c, 1, nullptr, specf, grid));
   for (int sw = 0; sw < sweeps; ++sw) {
-    k_grid_resid<<<cdiv(NN, 256), 256, 0, s>>>(N, dct, inv_h2, c->kappa, nullptr, grid, r);
-    k_resid_fix<<<qb, 256, 0, s>>>(N, dct, inv_h2, c->kappa, nirr, c->corr_val, c->corr_pos, grid, r);
+    const double d4 = 4.0 * inv_h2 + c->kappa;
+    k_grid_resid<<<dim3(cdiv(N, 256), N), 256, 0, s>>>(N, dct, inv_h2, d4, nullptr, grid, r);
+    k_resid_fix<<<qb, 256, 0, s>>>(N, dct, inv_h2, d4, nirr, c->corr_val, c->corr_pos, grid, r);
     launched(c, 2);
     KFBI_CHECK((launch_row_dense<float, float>(c, 0, r, specf, nullptr)));
     KFBI_CHECK(launch_col_solve<float>(c, specf, nullptr, skip));

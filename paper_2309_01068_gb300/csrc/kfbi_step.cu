@@ -277,11 +277,12 @@ __global__ void k_st_T0(const uint8_t* side, long NN, double St, double* T, doub
   Tprev[i] = v;
 }
 
-// rhs of the BDF2 step (T^{n-1} - 4 T^n) / (2 tau)
-__global__ void k_st_bdf_rhs(const double* T, const double* Tprev, long NN, double dt, double* out) {
+// rhs of the BDF2 step (T^{n-1} - 4 T^n) / (2 tau), as a product with 1 / (2 tau) (a float64
+// division per node made this pass bound by the float64 rate)
+__global__ void k_st_bdf_rhs(const double* T, const double* Tprev, long NN, double inv_2dt, double* out) {
   long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= NN) return;
-  out[i] = (Tprev[i] - 4.0 * T[i]) / (2.0 * dt);
+  out[i] = (Tprev[i] - 4.0 * T[i]) * inv_2dt;
 }
 
 // T^{n+1} = T1 - (S psi)_h; history shift
@@ -551,7 +552,7 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
     KFBI_TRY(cudaStreamSynchronize(s));
     if (steps == 0.0) k_st_T0<<<gb, 256, 0, s>>>(c->side, NN, P.St, st->T, st->Tprev);
     launched(c, (steps == 0.0) + 3);
-    k_st_bdf_rhs<<<gb, 256, 0, s>>>(st->T, st->Tprev, NN, dt, st->Tw);
+    k_st_bdf_rhs<<<gb, 256, 0, s>>>(st->T, st->Tprev, NN, 1.0 / (2.0 * dt), st->Tw);
     // T1: in place by the float64 solve (T1 in Tw, the grid single layer later in Sg), or by
     // the mixed-precision solve, which keeps its right-hand side (T1 in Sg, the single layer
     // later in Tw)
