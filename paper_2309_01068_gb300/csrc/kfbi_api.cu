@@ -123,7 +123,7 @@ static void free_all(kfbi_ctx* c) {
                   c->npack_f, c->prow_list, c->probe_val, c->tmp_vals, c->gctl, c->gV, c->gVf, c->gpart, c->gw,
                   c->gin, c->gin_f, c->gb, c->gx, c->gr, c->zero_flag, c->irctl, c->ir_b, c->ir_x, c->ir_dn,
                   c->col_fwd, c->col_inv, c->col_tmp, c->col_tc_err, c->irr_ci, c->arm_slot, c->arm_rev,
-                  c->arm_coef, c->corr_val, c->corr_pos};
+                  c->arm_coef, c->corr_val, c->corr_pos, c->ir_grid};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->host_counts) cudaFreeHost(c->host_counts);
@@ -218,6 +218,9 @@ static kfbi_status create_impl(int N, double xmin, double xmax, double ymin, dou
   KFBI_CHECK(dalloc(&c->dint, 8));
   KFBI_CHECK(dalloc(&c->boxg, 4 * (size_t)N));
   KFBI_CHECK(dalloc(&c->spec, NN));
+  // the solved grid of the float64 applies that refine with float32 solves (see apply_t)
+  if (c->precision == KFBI_MIXED && c->boxbc != KFBI_BOX_FREESPACE_DL && N >= IR_APPLY_MIN_N)
+    KFBI_CHECK(dalloc(&c->ir_grid, NN));
   KFBI_CHECK(dalloc(&c->rowinfo, 2 * (size_t)N));
   KFBI_CHECK(dalloc(&c->probe_val, 6 * (size_t)max_nodes));
   KFBI_CHECK(dalloc(&c->tmp_vals, max_nodes));

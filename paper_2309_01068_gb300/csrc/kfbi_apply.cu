@@ -1494,6 +1494,9 @@ static kfbi_status launch_row_dense(kfbi_ctx* c, int inverse, const typename NoD
   return KFBI_OK;
 }
 
+kfbi_status ir_solve_corrections(kfbi_ctx* c, const double* J, double* grid, int sweeps, const int* skip);
+__global__ void k_gather_probes(int N, const int* prow_ptr, const int* probe_i, const double* grid, double* pval);
+
 template <typename T>
 static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double* values, double* dnormal,
                            double* grid, int bie_kind, const double* eps_v, const int* skip, const float* density_f,
@@ -1611,7 +1614,16 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     launched(c, 2);
   }
   if (fs) KFBI_TRY(cudaStreamWaitEvent(s, c->ev_join, 0));
-  if (rows_in_col) {
+  // float64 applies of a mixed context on the largest grids (no box data): the grid solve by
+  // float32 solves with float64 residual sweeps from the corrections at the irregular nodes,
+  // and the probe values gathered from the solved grid
+  bool ir_apply = false;
+  if constexpr (sizeof(T) == 8) ir_apply = grid == nullptr && c->ir_grid != nullptr && c->grid_ir > 0;
+  if (ir_apply) {
+    KFBI_CHECK(ir_solve_corrections(c, (const double*)J, c->ir_grid, c->grid_ir, skip));
+    k_gather_probes<<<N, 128, 0, s>>>(N, c->prow_ptr, c->probe_i, c->ir_grid, (double*)pval);
+    launched(c, 1);
+  } else if (rows_in_col) {
     RowSrc rs;
     rs.row_ptr = c->row_ptr;
     rs.ci = c->irr_ci;
@@ -1626,10 +1638,12 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
     launched(c, 1);
     KFBI_CHECK(launch_col_solve<T>(c, spec, rowinfo, skip));
   }
-  KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(cdiv((long)6 * n * 32, 256)), dim3(256), 0, s, N, dct,
-                    (const int*)(c->prow_ptr + N), (const int*)c->probe_j, (const int*)c->probe_i, (const T*)spec, tab,
-                    scale, pval, skip));
-  launched(c, 1);
+  if (!ir_apply) {
+    KFBI_TRY(launch_k(c->use_pdl, k_probe_values<T>, dim3(cdiv((long)6 * n * 32, 256)), dim3(256), 0, s, N, dct,
+                      (const int*)(c->prow_ptr + N), (const int*)c->probe_j, (const int*)c->probe_i, (const T*)spec,
+                      tab, scale, pval, skip));
+    launched(c, 1);
+  }
   if (grid != nullptr) KFBI_CHECK(launch_row_dense<T>(c, 1, nullptr, spec, grid));
   using S_t = typename std::remove_cv<typename std::remove_pointer<decltype(Tabs<T>::stencil(c))>::type>::type;
   T ca = 0, cb = 1, cc = 0;
@@ -1850,18 +1864,14 @@ kfbi_status grid_solve_mixed_enqueue(kfbi_ctx* c, const double* rhs, double* u, 
 // Grid output of a layer potential (the apply's grid solve (Delta_h - kappa) u = C with the
 // corrected right-hand side C of its float64 jumps, Sec. 4.2) for KFBI_MIXED contexts without
 // box data: the float64 density coefficients and jumps, C at the irregular nodes (float64),
-// then the mixed-precision box solve of grid_solve_mixed_enqueue with C as a sparse
-// right-hand side: u = the float32 solve of C, `sweeps` times r = C - (Delta_h - kappa) u
-// (float64), u += the float32 solve of r. The interface values of the apply are not formed.
+// then the mixed-precision box solve with C as a sparse right-hand side
+// (ir_solve_corrections). The interface values of the apply are not formed.
 kfbi_status apply_grid_mixed_enqueue(kfbi_ctx* c, int layer, const double* density, double* grid, int sweeps) {
   if (c->precision != KFBI_MIXED || c->boxbc == KFBI_BOX_FREESPACE_DL) return KFBI_ERR_ARG;
   using T = double;
   cudaStream_t s = c->stream;
-  const int N = c->N, n = c->n, nk = n / 2 + 1;
-  const long NN = (long)N * N;
+  const int n = c->n, nk = n / 2 + 1;
   const int* skip = c->zero_flag;
-  const int dct = c->boxbc == KFBI_BOX_NEUMANN0;
-  const double inv_h2 = 1.0 / (c->h * c->h);
   V2<T>* coef = (V2<T>*)c->dcoef;
   T* J = (T*)c->jumps;
   const int* d_ncr = c->seg_off + 2 * SUBSAMPLES * n;
@@ -1883,7 +1893,23 @@ kfbi_status apply_grid_mixed_enqueue(kfbi_ctx* c, int layer, const double* densi
   else
     KFBI_TRY(launch_k(c->use_pdl, k_target_jumps<T, G, false>, dim3(cdiv((long)ntg_cap * 32, 256)), dim3(256), 0, s,
                       (const V2<T>*)coef, n, d_ncr, Tabs<T>::geo(c), Tabs<T>::tstart(c), layer, (T)c->kappa, J, skip));
-  // the corrections, scattered (float32) into the residual buffer
+  launched(c, 2);
+  KFBI_CHECK(ir_solve_corrections(c, J, grid, sweeps, skip));
+  KFBI_TRY(cudaGetLastError());
+  return KFBI_OK;
+}
+
+// The grid solve (Delta_h - kappa) u = C of an apply whose corrected right-hand side C is
+// nonzero only at the irregular nodes (float64 jumps J, no box data), by mixed-precision
+// refinement: C scattered (float32) into the residual buffer, u = its float32 solve, then
+// `sweeps` times r = C - (Delta_h - kappa) u (float64; C put in at the irregular nodes by
+// k_resid_fix), u += the float32 solve of r.
+kfbi_status ir_solve_corrections(kfbi_ctx* c, const double* J, double* grid, int sweeps, const int* skip) {
+  cudaStream_t s = c->stream;
+  const int N = c->N;
+  const long NN = (long)N * N;
+  const int dct = c->boxbc == KFBI_BOX_NEUMANN0;
+  const double inv_h2 = 1.0 / (c->h * c->h);
   float* specf = (float*)c->spec;
   float* r = specf + NN;
   const int* nirr = c->row_ptr + N;  // irregular-node count (device)
@@ -1891,7 +1917,7 @@ kfbi_status apply_grid_mixed_enqueue(kfbi_ctx* c, int layer, const double* densi
   k_corr_nodes<<<N, ROW_THREADS, 0, s>>>(N, c->row_ptr, (const IrrNode*)c->irr, J, inv_h2, c->corr_val, c->corr_pos);
   KFBI_TRY(cudaMemsetAsync(r, 0, sizeof(float) * (size_t)NN, s));
   k_corr_scatter<<<qb, 256, 0, s>>>(nirr, c->corr_val, c->corr_pos, r);
-  launched(c, 4);
+  launched(c, 2);
   KFBI_CHECK((launch_row_dense<float, float>(c, 0, r, specf, nullptr)));
   KFBI_CHECK(launch_col_solve<float>(c, specf, nullptr, skip));
   KFBI_CHECK(launch_row_dense<float>(c, 1, nullptr, specf, grid));

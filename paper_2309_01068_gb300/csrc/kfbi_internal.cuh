@@ -286,6 +286,7 @@ struct kfbi_ctx {
   float* arm_coef = nullptr;    // [cap_cross][2][2]
   double* corr_val = nullptr;   // [cap_irr] correction at each irregular node (mixed grid output)
   int* corr_pos = nullptr;      // [cap_irr] its grid index j N + i
+  double* ir_grid = nullptr;    // [N][N] solved grid of refined float64 applies (N >= IR_APPLY_MIN_N)
   bool fuse_rows = false;       // KFBI_OPT_FUSE_ROWS
   int grid_ir = 2;              // KFBI_OPT_GRID_IR: correction sweeps of mixed grid solves
   kfbi::Stencil* stencil = nullptr;  // [max_nodes]
@@ -558,6 +559,9 @@ InterpArgs<float> interp_args_f32(kfbi_ctx* c, int bie_kind, const double* eps_v
 kfbi_status grid_solve_enqueue(kfbi_ctx* c, const double* rhs, double* u);
 kfbi_status grid_solve_mixed_enqueue(kfbi_ctx* c, const double* rhs, double* u, int sweeps);
 kfbi_status apply_grid_mixed_enqueue(kfbi_ctx* c, int layer, const double* density, double* grid, int sweeps);
+// grids from this size on: the float64 applies of mixed contexts (no box data) solve their grid
+// by float32 solves with float64 residual sweeps (the float64 column solve is slower there)
+constexpr int IR_APPLY_MIN_N = 4096;
 // free-space box: fills boxK / boxK_f for the current interface (after the node data)
 constexpr size_t BOXK_MAX_BYTES = (size_t)1 << 30;
 constexpr size_t RINV_MAX_BYTES = (size_t)1 << 27;

@@ -135,3 +135,29 @@ def test_stefan_step_with_mixed_grid_solve():
     assert rel(a["T"], b["T"]) < 1e-9
     assert rel(a["density"], b["density"]) < 1e-6
     assert np.abs(a["eta"] - b["eta"]).max() < 1e-8
+
+
+def test_refined_float64_apply_on_the_largest_grid():
+    """N = 4096, Dirichlet box, interior double-layer problem in a mixed context: the float64
+    applies of the refinement solve their grid by float32 solves with float64 residual sweeps
+    (KFBI_OPT_GRID_IR = 2) or by the float64 column solve (0); both meet the 1e-11 residual
+    and give the same density to what that residual allows, and match the float64 context."""
+    import workloads as W
+
+    rng = np.random.default_rng(17)
+    p = W.interior_dirichlet(W.random_star(rng), 4096, 512, kappa=0.0, name="big")
+    dens = {}
+    for ir in (2, 0):
+        ctx = K.Context(p.N, p.box, 0.0, K.BOX_DIRICHLET0, K.MIXED, max_nodes=p.n)
+        ctx.set_option(K.OPT_GRID_IR, ir)
+        ctx.set_interface(dev(p.xy))
+        phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=1e-11, max_iter=300, restart=100)
+        assert info["status"] == 0 and info["rel_residual"] <= 1e-11
+        dens[ir] = phi.cpu().numpy()
+        ctx.close()
+    c64 = K.Context(p.N, p.box, 0.0, K.BOX_DIRICHLET0, K.FP64, max_nodes=p.n)
+    c64.set_interface(dev(p.xy))
+    phi64, info64 = c64.solve_bie(K.BIE_INTERIOR_DL, dev(p.rhs), tol=1e-11, max_iter=300, restart=100)
+    c64.close()
+    assert rel(dens[2], dens[0]) < 1e-9
+    assert rel(dens[2], phi64.cpu().numpy()) < 1e-9
