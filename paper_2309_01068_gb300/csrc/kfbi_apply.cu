@@ -1176,9 +1176,11 @@ template <typename X>
 struct NoDeduce {
   using type = X;
 };
-template <typename T, typename In = double>
-__global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* tw, const T* tab,
-                            const typename NoDeduce<In>::type* rhs, T* spec, double* out) {
+// the body of k_row_dense; CT > 0: N = 2^CT at compile time (constant index arithmetic and the
+// compile-time Stockham stages of fft_ct), CT = 0: N at run time
+template <typename T, typename In, int CT>
+__device__ __forceinline__ void row_dense_body(int N, int logN, int dct, int inverse, const V2<T>* tw, const T* tab,
+                                               const In* rhs, T* spec, double* out) {
   extern __shared__ unsigned char smem_raw[];
   V2<T>* A = (V2<T>*)smem_raw;
   V2<T>* B = A + N;
@@ -1192,7 +1194,11 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
       ((T*)&A[mk_pos(i, N)])[r] = v;
     }
     __syncthreads();
-    V2<T>* X = fft_stockham<T>(A, B, 1, N, logN, tw, false);
+    V2<T>* X;
+    if constexpr (CT > 0)
+      X = fft_ct<T, CT, false>(A, B, 1, tw);
+    else
+      X = fft_stockham<T>(A, B, 1, N, logN, tw, false);
     for (int m = threadIdx.x; m <= half; m += blockDim.x) {
       V2<T> Xm, XNm;
       T cm, sm;
@@ -1226,7 +1232,11 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
       if (m > 0 && m < half) A[N - m] = ZNm;
     }
     __syncthreads();
-    V2<T>* Z = fft_stockham<T>(A, B, 1, N, logN, tw, true);
+    V2<T>* Z;
+    if constexpr (CT > 0)
+      Z = fft_ct<T, CT, true>(A, B, 1, tw);
+    else
+      Z = fft_stockham<T>(A, B, 1, N, logN, tw, true);
     const T invN = (T)1 / (T)N;
     for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
       int r = t / N, i = t - r * N;
@@ -1238,6 +1248,35 @@ __global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* 
       else
         out[o] = (double)v;
     }
+  }
+}
+template <typename T, typename In = double>
+__global__ void k_row_dense(int N, int logN, int dct, int inverse, const V2<T>* tw, const T* tab,
+                            const typename NoDeduce<In>::type* rhs, T* spec, double* out) {
+  row_dense_body<T, In, 0>(N, logN, dct, inverse, tw, tab, rhs, spec, out);
+}
+// the same for N = 2^LOGN fixed at compile time (the float32 dense transforms of the mixed grid
+// solves and grid outputs)
+template <typename T, typename In, int LOGN>
+__global__ void __launch_bounds__(512) k_row_dense_ct(int dct, int inverse, const V2<T>* tw, const T* tab,
+                                                      const typename NoDeduce<In>::type* rhs, T* spec, double* out) {
+  row_dense_body<T, In, LOGN>(1 << LOGN, LOGN, dct, inverse, tw, tab, rhs, spec, out);
+}
+template <typename T, typename In>
+using RowDenseCt = void (*)(int, int, const V2<T>*, const T*, const In*, T*, double*);
+template <typename T, typename In>
+static RowDenseCt<T, In> row_dense_ct(int logN) {
+  switch (logN) {
+    case 4: return k_row_dense_ct<T, In, 4>;
+    case 5: return k_row_dense_ct<T, In, 5>;
+    case 6: return k_row_dense_ct<T, In, 6>;
+    case 7: return k_row_dense_ct<T, In, 7>;
+    case 8: return k_row_dense_ct<T, In, 8>;
+    case 9: return k_row_dense_ct<T, In, 9>;
+    case 10: return k_row_dense_ct<T, In, 10>;
+    case 11: return k_row_dense_ct<T, In, 11>;
+    case 12: return k_row_dense_ct<T, In, 12>;
+    default: return nullptr;
   }
 }
 
@@ -1488,6 +1527,15 @@ static kfbi_status launch_row_dense(kfbi_ctx* c, int inverse, const typename NoD
   size_t smem = 2 * sizeof(V2<T>) * (size_t)N;
   // float32: 512 threads per row pair (16 warps of latency hiding per block; 256 measured 3 %
   // slower on the Stefan 4096^2 step)
+  if constexpr (sizeof(T) == 4) {
+    const RowDenseCt<T, In> k = row_dense_ct<T, In>(c->logN);
+    if (k != nullptr) {
+      k<<<N / 2, 512, smem, c->stream>>>(c->boxbc == KFBI_BOX_NEUMANN0, inverse, Tabs<T>::stw(c), Tabs<T>::sin(c), rhs,
+                                         spec, out);
+      launched(c, 1);
+      return KFBI_OK;
+    }
+  }
   k_row_dense<T, In><<<N / 2, sizeof(T) == 4 ? 512 : 256, smem, c->stream>>>(N, c->logN, c->boxbc == KFBI_BOX_NEUMANN0, inverse,
                                                      Tabs<T>::stw(c), Tabs<T>::sin(c), rhs, spec, out);
   launched(c, 1);
@@ -1684,8 +1732,13 @@ static kfbi_status setup_t(kfbi_ctx*) {
   for (int lg = 4; lg <= 12; ++lg)
     KFBI_TRY(cudaFuncSetAttribute(col_kernel<T>(lg), cudaFuncAttributeMaxDynamicSharedMemorySize, col));
   KFBI_TRY(cudaFuncSetAttribute(k_row_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
-  if constexpr (sizeof(T) == 4)  // the float32 residual input of the mixed grid solve
+  if constexpr (sizeof(T) == 4) {  // the float32 residual input of the mixed grid solve
     KFBI_TRY((cudaFuncSetAttribute(k_row_dense<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, row)));
+    for (int lg = 4; lg <= 12; ++lg) {
+      KFBI_TRY((cudaFuncSetAttribute(row_dense_ct<T, double>(lg), cudaFuncAttributeMaxDynamicSharedMemorySize, row)));
+      KFBI_TRY((cudaFuncSetAttribute(row_dense_ct<T, float>(lg), cudaFuncAttributeMaxDynamicSharedMemorySize, row)));
+    }
+  }
   KFBI_TRY(cudaFuncSetAttribute(k_face_dst<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, row));
   KFBI_TRY(cudaFuncSetAttribute(k_dens_coef<T, true, S_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
   KFBI_TRY(cudaFuncSetAttribute(k_box_data<T, T4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage));
