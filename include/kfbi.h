@@ -425,8 +425,12 @@ kfbi_status kfbi_timing_read(kfbi_ctx* ctx, double* ms_fp64, int* launches_fp64,
  *                             nodes (the apply's column solve and interface values are not
  *                             formed). On grids with N >= 4096 and no box data, the float64
  *                             applies of the refinement (KFBI_MIXED solves) solve their grid the
- *                             same way and gather the probe values from it. 0: float64 solves
- *                             (kfbi_grid_solve and the float64 apply's column solve).
+ *                             same way and gather the probe values from it, with one sweep when
+ *                             the solve's tolerance is 1e-8 or looser (their error, about 5e-11 of
+ *                             the values, is then far below it; a test checks the returned
+ *                             density's residual under the float64 context's operator). 0:
+ *                             float64 solves (kfbi_grid_solve and the float64 apply's column
+ *                             solve).
  *   KFBI_OPT_BODY_CAP         0 (default): the device-side GMRES loop (the body count of the
  *                             graph's WHILE node, or of the host-driven loop) stops after
  *                             2 max_iter + 2 max_iter / restart + 8 bodies; a value > 0 sets

@@ -1668,7 +1668,8 @@ static kfbi_status apply_t(kfbi_ctx* c, int layer, const double* density, double
   bool ir_apply = false;
   if constexpr (sizeof(T) == 8) ir_apply = grid == nullptr && c->ir_grid != nullptr && c->grid_ir > 0;
   if (ir_apply) {
-    KFBI_CHECK(ir_solve_corrections(c, (const double*)J, c->ir_grid, c->grid_ir, skip));
+    const int sweeps = c->apply_sweeps > 0 ? c->apply_sweeps : c->grid_ir;
+    KFBI_CHECK(ir_solve_corrections(c, (const double*)J, c->ir_grid, sweeps, skip));
     k_gather_probes<<<N, 128, 0, s>>>(N, c->prow_ptr, c->probe_i, c->ir_grid, (double*)pval);
     launched(c, 1);
   } else if (rows_in_col) {

@@ -1563,7 +1563,7 @@ static kfbi_status solve_ir_graph(kfbi_ctx* c, int kind, const double* rhs, doub
   const int max_sweeps = IR_MAX_SWEEPS;
   kfbi_ctx::IrGraph& G = c->irgraph[kind][dnormal != nullptr ? 1 : 0];
   if (G.exec == nullptr || G.version != c->layout_version || G.m != m || G.cs != gf.cs || G.pdl != c->use_pdl ||
-      G.cap != cap || G.cfg != c->cfg_version || G.f32 != gf.f32) {
+      G.cap != cap || G.cfg != c->cfg_version || G.f32 != gf.f32 || G.asw != c->apply_sweeps) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
     if (G.graph) cudaGraphDestroy(G.graph);
     G.exec = nullptr;
@@ -1590,6 +1590,7 @@ static kfbi_status solve_ir_graph(kfbi_ctx* c, int kind, const double* rhs, doub
     G.cap = cap;
     G.cfg = c->cfg_version;
     G.f32 = gf.f32;
+    G.asw = c->apply_sweeps;
   }
   const size_t bytes = sizeof(double) * n;
   KFBI_TRY(cudaMemcpyAsync(c->ir_b, rhs, bytes, cudaMemcpyDeviceToDevice, s));
@@ -1628,6 +1629,13 @@ kfbi_status solve_bie_impl(kfbi_ctx* c, int kind, const double* eps_v, const dou
     ev = c->gev;
   }
   kfbi_solve_info out{};
+  // refined float64 applies of this solve (grids >= IR_APPLY_MIN_N): one correction sweep for
+  // a tolerance of IR_ONE_SWEEP_TOL or looser; reset when the solve returns
+  struct SweepScope {
+    kfbi_ctx* c;
+    ~SweepScope() { c->apply_sweeps = 0; }
+  } sweep_scope{c};
+  c->apply_sweeps = tol >= IR_ONE_SWEEP_TOL && c->grid_ir > 1 ? 1 : c->grid_ir;
   if (c->precision == KFBI_FP64) {
     int its = 0, cyc = 0, st = 0;
     double rel = 0.0;

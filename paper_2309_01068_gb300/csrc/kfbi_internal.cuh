@@ -289,6 +289,7 @@ struct kfbi_ctx {
   double* ir_grid = nullptr;    // [N][N] solved grid of refined float64 applies (N >= IR_APPLY_MIN_N)
   bool fuse_rows = false;       // KFBI_OPT_FUSE_ROWS
   int grid_ir = 2;              // KFBI_OPT_GRID_IR: correction sweeps of mixed grid solves
+  int apply_sweeps = 0;         // sweeps of refined float64 applies inside a mixed solve (0: grid_ir)
   kfbi::Stencil* stencil = nullptr;  // [max_nodes]
   kfbi::StencilF* stencil_f = nullptr;
   float* dens_f = nullptr;      // [max_nodes] float32 copy of the apply's density
@@ -374,6 +375,7 @@ struct kfbi_ctx {
     bool pdl = false;
     int inner_body_launches = 0;
     int f32 = 0;
+    int asw = -1;  // sweeps of the refined float64 applies captured in it
   } irgraph[3][2];
   bool gm_cluster = true;       // allow the cluster form
   bool use_pdl = true;          // programmatic dependent launch between the kernels of a body
@@ -562,6 +564,9 @@ kfbi_status apply_grid_mixed_enqueue(kfbi_ctx* c, int layer, const double* densi
 // grids from this size on: the float64 applies of mixed contexts (no box data) solve their grid
 // by float32 solves with float64 residual sweeps (the float64 column solve is slower there)
 constexpr int IR_APPLY_MIN_N = 4096;
+// a mixed solve to this tolerance or looser refines its float64 applies' grid solve with one
+// correction sweep (about 5e-11 of the values at 4096^2, below 1/100 of the tolerance)
+constexpr double IR_ONE_SWEEP_TOL = 1e-8;
 // free-space box: fills boxK / boxK_f for the current interface (after the node data)
 constexpr size_t BOXK_MAX_BYTES = (size_t)1 << 30;
 constexpr size_t RINV_MAX_BYTES = (size_t)1 << 27;

@@ -161,3 +161,30 @@ def test_refined_float64_apply_on_the_largest_grid():
     c64.close()
     assert rel(dens[2], dens[0]) < 1e-9
     assert rel(dens[2], phi64.cpu().numpy()) < 1e-9
+
+
+def test_refined_apply_with_one_sweep_meets_the_tolerance():
+    """A mixed solve to 1e-8 on a 4096^2 grid refines its float64 applies' grid solve with one
+    correction sweep: the returned density's residual under the float64 context's operator
+    (float64 column solve) still meets the tolerance, and the iteration count matches the
+    two-sweep form within one."""
+    import workloads as W
+
+    rng = np.random.default_rng(23)
+    p = W.interior_dirichlet(W.random_star(rng), 4096, 512, kappa=0.0, name="big")
+    c64 = K.Context(p.N, p.box, 0.0, K.BOX_DIRICHLET0, K.FP64, max_nodes=p.n)
+    c64.set_interface(dev(p.xy))
+    b = dev(p.rhs)
+    its = {}
+    for ir in (2, 0):
+        ctx = K.Context(p.N, p.box, 0.0, K.BOX_DIRICHLET0, K.MIXED, max_nodes=p.n)
+        ctx.set_option(K.OPT_GRID_IR, ir)
+        ctx.set_interface(dev(p.xy))
+        phi, info = ctx.solve_bie(K.BIE_INTERIOR_DL, b, tol=1e-8, max_iter=300, restart=100)
+        assert info["status"] == 0
+        its[ir] = info["iterations"]
+        r = b - c64.bie_apply(K.BIE_INTERIOR_DL, phi)
+        assert float(r.norm() / b.norm()) <= 1.05e-8, (ir, float(r.norm() / b.norm()))
+        ctx.close()
+    c64.close()
+    assert abs(its[2] - its[0]) <= 1, its
