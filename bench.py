@@ -141,6 +141,9 @@ def parse():
                     help="skip the batched (256 instances), warm-start and Stefan measurements")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (for short profiler runs): no e2e, applies, fp64 or cpu legs")
+    ap.add_argument("--profile-stefan", type=int, default=0, metavar="N",
+                    help="for profiler launch lists: three mixed Stefan steps on an N^2 grid with N nodes "
+                         "(tol 1e-8), CUDA graphs off so that every kernel of the solve is listed; no JSON line")
     ap.add_argument("--baselines", action="store_true",
                     help="one JSON line of the per-config table: the oracle on one core and on all cores and the "
                          "GPU forms for configs 1-5 (several minutes of host time)")
@@ -862,12 +865,43 @@ def run_baselines():
 
 
 # --------------------------------------------------------------------------- main arm
+def profile_stefan(N):
+    """Three mixed Stefan steps (seed, N^2 grid, N nodes, tol 1e-8) with the solve's CUDA graphs
+    off: the subject of a profiler's launch list (kernels inside conditional graph nodes are not
+    listed by it)."""
+    import torch
+
+    import workloads as W
+    from paper_2309_01068_gb300 import build
+    from paper_2309_01068_gb300 import kfbi as K
+
+    build.build()
+    K.load()
+    p = W.config_stefan(N=N, n=N)
+    x = p.extra
+    ctx = K.Context(p.N, p.box, p.kappa, K.BOX_NEUMANN0, K.MIXED, max_nodes=p.n)
+    ctx.set_option(K.OPT_CUDA_GRAPHS, 0)
+    eta = torch.tensor(p.theta - alpha_array(p.n), dtype=torch.float64, device="cuda")
+    st = K.ThetaL(ctx, eta, p.L, p.xy.mean(0), K.STEP_STEFAN, tol=1e-8, max_iter=3000, restart=150, St=x["St"],
+                  eps_c=x["eps_c"], eps_aniso=x["eps_aniso"], eps_v=x["eps_v"], fold=x["fold"])
+    for s in range(3):
+        info = st.step(x["dt"])
+        torch.cuda.synchronize()
+        print(f"[bench] stefan {N}: step {s}, {info['iterations']} GMRES iterations, status {info['status']}",
+              file=sys.stderr)
+    st.close()
+    ctx.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.baselines:
         return run_baselines()
+    if args.profile_stefan:
+        return profile_stefan(args.profile_stefan)
     rank, world, local = dist_env()
     import numpy as np
     import torch
