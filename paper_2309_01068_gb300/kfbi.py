@@ -271,7 +271,9 @@ class Context:
     def grid_solve(self, rhs, out=None):
         self._sync_stream()
         u = out if out is not None else torch.empty_like(rhs)
-        _check(self.lib.kfbi_grid_solve(self.handle, _f64(rhs, (self.N, self.N)), _ptr(u)), "kfbi_grid_solve")
+        # both checked for dtype and shape before the call: the library writes N x N float64
+        _check(self.lib.kfbi_grid_solve(self.handle, _f64(rhs, (self.N, self.N)), _f64(u, (self.N, self.N))),
+               "kfbi_grid_solve")
         return u
 
     def grid_solve_mixed(self, rhs, sweeps=2, out=None):
@@ -279,8 +281,8 @@ class Context:
         residual corrections; `out` must not be `rhs`."""
         self._sync_stream()
         u = out if out is not None else torch.empty_like(rhs)
-        _check(self.lib.kfbi_grid_solve_mixed(self.handle, _f64(rhs, (self.N, self.N)), _ptr(u), int(sweeps)),
-               "kfbi_grid_solve_mixed")
+        _check(self.lib.kfbi_grid_solve_mixed(self.handle, _f64(rhs, (self.N, self.N)), _f64(u, (self.N, self.N)),
+                                              int(sweeps)), "kfbi_grid_solve_mixed")
         return u
 
     def interp_grid(self, grid):

@@ -80,6 +80,13 @@ def test_grid_solve_mixed_smooth_rhs_and_arguments():
         ctx.grid_solve_mixed(r, 2, out=r)  # aliasing
     with pytest.raises(K.KfbiError):
         ctx.grid_solve_mixed(r, 9)
+    # a wrong output buffer is refused before the library is called
+    for bad in (torch.empty((N, N), dtype=torch.float32, device="cuda"),
+                torch.empty((N, N - 1), dtype=torch.float64, device="cuda")):
+        with pytest.raises(ValueError):
+            ctx.grid_solve_mixed(r, 2, out=bad)
+        with pytest.raises(ValueError):
+            ctx.grid_solve(r, out=bad)
     assert ctx.get_option(K.OPT_GRID_IR) == 2
     for v in (0, 1, 3, 2):
         ctx.set_option(K.OPT_GRID_IR, v)
