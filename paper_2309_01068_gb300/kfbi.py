@@ -180,6 +180,16 @@ def _f64(t, shape):
     return _ptr(t)
 
 
+def _opt_f64(t, shape):
+    return None if t is None else _f64(t, shape)
+
+
+def _f32(t, shape):
+    if t.dtype != torch.float32 or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected float32 tensor of shape {shape}, got {t.dtype} {tuple(t.shape)}")
+    return _ptr(t)
+
+
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -246,14 +256,18 @@ class Context:
         return vals, dn, g
 
     def apply_into(self, layer, density, values, dnormal=None, grid=None):
+        """The apply into caller buffers, each checked for dtype and shape before the call."""
         self._sync_stream()
-        _check(self.lib.kfbi_apply_layer_potential(self.handle, layer, _ptr(density), _ptr(values), _ptr(dnormal),
-                                                   _ptr(grid)), "kfbi_apply_layer_potential")
+        n, N = self.n, self.N
+        _check(self.lib.kfbi_apply_layer_potential(self.handle, layer, _f64(density, (n,)), _f64(values, (n,)),
+                                                   _opt_f64(dnormal, (n,)), _opt_f64(grid, (N, N))),
+               "kfbi_apply_layer_potential")
 
     def bie_apply(self, kind, x, eps_v=None, out=None):
         self._sync_stream()
         y = out if out is not None else torch.empty_like(x)
-        _check(self.lib.kfbi_bie_apply(self.handle, kind, _ptr(eps_v), _f64(x, (self.n,)), _ptr(y)), "kfbi_bie_apply")
+        _check(self.lib.kfbi_bie_apply(self.handle, kind, _opt_f64(eps_v, (self.n,)), _f64(x, (self.n,)),
+                                       _f64(y, (self.n,))), "kfbi_bie_apply")
         return y
 
     def solve_bie(self, kind, rhs, density=None, tol=1e-10, max_iter=500, restart=100, eps_v=None):
@@ -456,7 +470,8 @@ class Mlp:
         self._sync_stream()
         rows = feat.shape[0]
         y = out if out is not None else torch.empty(rows, dtype=torch.float32, device=feat.device)
-        _check(self.lib.kfbi_mlp_forward(self.handle, _ptr(feat), rows, _ptr(y)), "kfbi_mlp_forward")
+        _check(self.lib.kfbi_mlp_forward(self.handle, _f32(feat, (rows, MLP_FEATURES)), rows, _f32(y, (rows,))),
+               "kfbi_mlp_forward")
         return y
 
     def gradients(self, feat, target, idx=None):
