@@ -577,7 +577,7 @@ kfbi_status thetal_step_impl(kfbi_ctx* c, kfbi_thetal* st, double dt, kfbi_solve
     // T2 = -(S psi)_h from the apply's grid output; T^{n+1} = T1 + T2
     // (mixed: the grid solve of the single layer by the same mixed-precision box solve, with
     // its corrected right-hand side from the float64 jumps)
-    if (ir)
+    if (ir && c->boxbc != KFBI_BOX_FREESPACE_DL)  // (box data: the float64 apply)
       KFBI_CHECK(apply_grid_mixed_enqueue(c, KFBI_SINGLE, st->density, S2, c->grid_ir));
     else
       KFBI_CHECK(apply_enqueue(c, KFBI_SINGLE, false, st->density, st->V, nullptr, S2, -1, nullptr, nullptr));
